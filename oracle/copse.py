@@ -1,0 +1,493 @@
+"""COPSE in the CPU oracle: the forest compiler, plaintext classification, the
+vectorised inference circuit over slot vectors (cleartext) and over BGV
+ciphertexts (through ``oracle.bgv``).
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``, ``__graft_entry__.smoke()``
+and the CPU-baseline leg of ``bench.py``; the product never imports it.
+
+Each function names the part of the paper (Malik et al., "Vectorized Secure
+Evaluation of Decision Forests", PLDI'21) it follows.  Readings of passages the
+paper leaves open are stated where they are used.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import bgv as B
+
+
+# ---------------------------------------------------------------------------
+# Forest model and its serialisation (Section 5, "Input Representation"):
+# a line of label names, then one line per tree; a leaf gives its label index,
+# a branch gives its feature index, threshold, then left and right subtrees.
+# Token syntax (this implementation's): "l <label>" and "b <feature> <threshold>".
+# ---------------------------------------------------------------------------
+@dataclass
+class Node:
+    leaf: bool
+    label: int = -1
+    feature: int = -1
+    threshold: int = 0
+    left: "Node" = None
+    right: "Node" = None
+
+
+def parse_forest(text: str):
+    lines = [ln for ln in text.strip().splitlines() if ln.strip()]
+    if len(lines) < 2:
+        raise ValueError("forest needs a label line and at least one tree")
+    labels = lines[0].split()
+    trees = []
+    for ln in lines[1:]:
+        toks = ln.split()
+        pos = 0
+
+        def rec():
+            nonlocal pos
+            kind = toks[pos]
+            if kind == "l":
+                n = Node(True, label=int(toks[pos + 1]))
+                pos += 2
+                return n
+            if kind == "b":
+                n = Node(False, feature=int(toks[pos + 1]), threshold=int(toks[pos + 2]))
+                pos += 3
+                n.left = rec()
+                n.right = rec()
+                return n
+            raise ValueError(f"bad token {kind!r}")
+
+        t = rec()
+        if pos != len(toks):
+            raise ValueError("trailing tokens in tree line")
+        trees.append(t)
+    return labels, trees
+
+
+def classify_plain(trees, x):
+    """Plaintext evaluation (Section 2.1): at a branch compare x[f] < threshold;
+    false goes left, true goes right.  Returns one bit per leaf (leaves in
+    preorder, continued across trees), 1 for the leaf each tree reaches."""
+    bits = []
+    for t in trees:
+        def walk(n, on):
+            if n.leaf:
+                bits.append(1 if on else 0)
+                return
+            d = x[n.feature] < n.threshold
+            walk(n.left, on and not d)
+            walk(n.right, on and d)
+        walk(t, True)
+    return bits
+
+
+# ---------------------------------------------------------------------------
+# Compiler (Section 4.1-4.2)
+# ---------------------------------------------------------------------------
+@dataclass
+class Model:
+    n_features: int
+    precision: int
+    labels_per_leaf: list          # class index of each leaf (preorder)
+    br_feature: list               # f vector (Section 4.1.1)
+    br_threshold: list             # t vector
+    br_level: list                 # level of each branch (Section 4.1.1)
+    K: int                         # maximum multiplicity
+    q: int                         # quantised branching K * n_features
+    b: int                         # branching
+    L: int                         # number of leaves (slots of the result)
+    d: int                         # number of levels
+    thr_slot: list                 # padded threshold vector (sentinel 0)
+    slot_branch: list              # branch held by each padded slot, -1 = sentinel
+    R: np.ndarray                  # reshuffling matrix b x q
+    lvl: list                      # level matrices L x b, k = 1..d
+    mask: list                     # level masks, length L, k = 1..d
+    block: int = 0                 # slots per query block
+    extras: dict = field(default_factory=dict)
+
+    @property
+    def m1(self):                  # rows of the extended reshuffle: L + b - 1
+        return self.L + self.b - 1
+
+    @property
+    def pd(self):                  # slots that must hold the periodic decision vector
+        return self.m1 + self.q - 1
+
+
+def compile_forest(text: str, precision: int, n_features: int = 0, slots_per_row: int = 0) -> Model:
+    labels, trees = parse_forest(text)
+    # Section 4.1.1: branches and leaves indexed in preorder, continuing across trees.
+    br_f, br_t, br_lvl, leaf_cls = [], [], [], []
+    leaf_anc = []   # per leaf: list of (branch index, leaf is under its true child)
+
+    def walk(n, anc):
+        if n.leaf:
+            leaf_cls.append(n.label)
+            leaf_anc.append(list(anc))
+            return 0
+        i = len(br_f)
+        br_f.append(n.feature)
+        br_t.append(n.threshold)
+        br_lvl.append(0)
+        hl = walk(n.left, anc + [(i, False)])
+        hr = walk(n.right, anc + [(i, True)])
+        # level = branches on the longest path from the node to a label, itself included
+        br_lvl[i] = 1 + max(hl, hr)
+        return br_lvl[i]
+
+    for t in trees:
+        walk(t, [])
+    b = len(br_f)
+    if b == 0:
+        raise ValueError("forest has no branches")
+    if any(t < 0 or t >= (1 << precision) for t in br_t):
+        raise ValueError("threshold out of range for the precision")
+    nf = n_features if n_features else max(br_f) + 1
+    if max(br_f) >= nf or min(br_f) < 0:
+        raise ValueError("feature index out of range")
+    L, d = len(leaf_cls), max(br_lvl)
+    # Section 4.1.1: multiplicity, maximum multiplicity K, quantised branching q = K * n_features.
+    kappa = [br_f.count(f) for f in range(nf)]
+    K = max(kappa)
+    q = K * nf
+    # Section 4.2.1: thresholds grouped by feature, each group padded to K with S = 0.
+    # Reading: within a group, branches keep their preorder order.
+    thr_slot = [0] * q
+    slot_branch = [-1] * q
+    seen = [0] * nf
+    for i, f in enumerate(br_f):
+        s = K * f + seen[f]
+        seen[f] += 1
+        thr_slot[s] = br_t[i]
+        slot_branch[s] = i
+    # Section 4.2.2: R[i][j] = 1 iff padded slot j holds branch i.
+    R = np.zeros((b, q), dtype=np.int64)
+    for j, i in enumerate(slot_branch):
+        if i >= 0:
+            R[i, j] = 1
+    # Section 4.2.3-4.2.4: level matrices and masks.  For label l and level k pick
+    # the ancestor whose level is k, else the ancestor of greatest level below k
+    # ("the highest branch not exceeding that level"); reading where every
+    # ancestor is above k: pick the parent.  A leaf that is a whole tree has no
+    # ancestor: its row stays empty and its mask is 1.
+    lvl, mask = [], []
+    for k in range(1, d + 1):
+        M = np.zeros((L, b), dtype=np.int64)
+        mk = np.ones(L, dtype=np.int64)
+        for l, anc in enumerate(leaf_anc):
+            if not anc:
+                continue
+            exact = [(i, tr) for i, tr in anc if br_lvl[i] == k]
+            below = [(i, tr) for i, tr in anc if br_lvl[i] < k]
+            if exact:
+                i, tr = exact[0]
+            elif below:
+                i, tr = max(below, key=lambda a: br_lvl[a[0]])
+            else:
+                i, tr = anc[-1]
+            M[l, i] = 1
+            mk[l] = 0 if tr else 1     # 0 under the true path, 1 otherwise
+        lvl.append(M)
+        mask.append(mk)
+    m = Model(nf, precision, leaf_cls, br_f, br_t, br_lvl, K, q, b, L, d, thr_slot, slot_branch, R, lvl, mask)
+    need = m.pd
+    blk = 1
+    while blk < need:
+        blk <<= 1
+    m.block = blk
+    if slots_per_row and blk > slots_per_row:
+        raise ValueError("model does not fit one slot row")
+    return m
+
+
+# ---------------------------------------------------------------------------
+# Slot layout.  Query j owns block j (slots j*B .. j*B+B-1; a row of N/2 slots
+# holds N/(2B) blocks).  Inside a block the replicated feature vector
+# (Section 3.3, Step 0) repeats with period q over the first pd slots so that
+# rotations by up to q-1 and b-1 stay inside the block (the cyclic extension
+# of the diagonal method, Section 4.1.2).
+# ---------------------------------------------------------------------------
+def feature_planes(m: Model, queries, N: int):
+    """p bit-planes (Section 4.1.2) of the replicated feature vectors."""
+    nb = N // m.block
+    if len(queries) > nb:
+        raise ValueError("too many queries for one ciphertext")
+    planes = np.zeros((m.precision, N), dtype=np.int64)
+    pos = np.arange(m.pd)
+    feat_of = (pos % m.q) // m.K
+    for j, x in enumerate(queries):
+        x = np.asarray(x, dtype=np.int64)
+        vals = x[feat_of]
+        for i in range(m.precision):
+            planes[i, j * m.block + pos] = (vals >> i) & 1
+    return planes
+
+
+def tile_blocks(m: Model, block_vec, N: int):
+    """Repeat a per-block slot pattern (length <= block) in every block."""
+    v = np.zeros(m.block, dtype=np.int64)
+    v[: len(block_vec)] = block_vec
+    return np.tile(v, N // m.block)
+
+
+def threshold_planes(m: Model, N: int):
+    pos = np.arange(m.pd)
+    vals = np.asarray(m.thr_slot, dtype=np.int64)[pos % m.q]
+    return np.stack([tile_blocks(m, (vals >> i) & 1, N) for i in range(m.precision)])
+
+
+def generalized_diagonal(M: np.ndarray, i: int, rows: int) -> np.ndarray:
+    """d_i[j] = M[j mod m][(j + i) mod n], j < rows (Section 4.1.2, generalised
+    diagonals, with rows cyclically extended past m)."""
+    m, n = M.shape
+    j = np.arange(rows)
+    return M[j % m, (j + i) % n]
+
+
+def reshuffle_diagonals(m: Model):
+    """Nonzero diagonals of the extended reshuffle R_ext (rows L+b-1, row j = R[j mod b]):
+    multiplying by it leaves the branch vector repeated with period b, ready for
+    the level products without further rotation."""
+    out = {}
+    for i in range(m.q):
+        dg = generalized_diagonal(m.R, i, m.m1)
+        if dg.any():
+            out[i] = dg
+    return out
+
+
+def level_diagonals(m: Model, k: int, t: int):
+    """Signed diagonals of level k: (1 - 2 Mask_k) * d_i(Lvl_k), values in {0,1,t-1};
+    adding Mask_k afterwards computes Lvl_k * Branches XOR Mask_k (Section 4.2.4)
+    as m + (1-2m) z."""
+    out = {}
+    sgn = 1 - 2 * m.mask[k - 1]
+    for i in range(m.b):
+        dg = generalized_diagonal(m.lvl[k - 1], i, m.L)
+        if dg.any():
+            out[i] = (sgn * dg) % t
+    return out
+
+
+def rotation_sets(m: Model):
+    """Rotation amounts used by the reshuffle and by the level products (0 excluded)."""
+    rs = sorted(i for i in reshuffle_diagonals(m) if i)
+    ls = set()
+    for k in range(1, m.d + 1):
+        ls |= set(i for i in level_diagonals(m, k, 65537) if i)
+    return rs, sorted(ls)
+
+
+# ---------------------------------------------------------------------------
+# The circuit (Algorithm 1, Section 4.3), written once over an abstract
+# "engine" so that the cleartext slot simulation and the BGV evaluation follow
+# the same steps in the same order.
+# ---------------------------------------------------------------------------
+def pairwise(items, combine):
+    """Balanced reduction: combine adjacent pairs, carry an odd last element."""
+    while len(items) > 1:
+        nxt = [combine(items[k], items[k + 1], len(items) == 2) for k in range(0, len(items) - 1, 2)]
+        if len(items) % 2:
+            nxt.append(items[-1])
+        items = nxt
+    return items[0]
+
+
+def seccomp(E, X, Y_planes, p):
+    """SecComp (Section 4.1.2, Integer Comparison): D = [x < y] slotwise, bit-sliced,
+    most significant plane p-1.  The paper gives only operation counts; reading:
+    per plane lt_i = (1 - x_i) y_i and eq_i = [x_i == y_i], combined over planes
+    MSB-first by the associative operator
+        (lt_h, eq_h) o (lt_l, eq_l) = (lt_h + eq_h lt_l, eq_h eq_l)
+    as a balanced tree (ceil(log2 p) multiplicative levels).  With plaintext
+    thresholds, lt_i = y_i - y_i x_i and eq_i = (1 - y_i) + (2 y_i - 1) x_i."""
+    leaves = []
+    for i in reversed(range(p)):
+        y = Y_planes[i]
+        if E.encrypted_model:
+            xy = E.mul(X[i], y)
+            lt = E.sub(y, xy)
+            eq = E.add_const(E.sub(E.add(xy, xy), E.add(X[i], y)), 1)
+        else:
+            lt = E.affine(X[i], (-y) % E.t, y)
+            eq = E.affine(X[i], (2 * y - 1) % E.t, (1 - y) % E.t)
+        leaves.append((lt, eq))
+
+    def combine(hi, lo, root):
+        lt = E.add(hi[0], E.mul(hi[1], lo[0]))
+        eq = None if root else E.mul(hi[1], lo[1])
+        return (lt, eq)
+
+    return pairwise(leaves, combine)[0]
+
+
+def matmul(E, v, diags, add_vec=None):
+    """Diagonal method (Section 4.1.2, Matrix Multiplication): sum over the
+    nonzero diagonals of d_i * rot(v, i), plus an optional plaintext, then one
+    modulus switch."""
+    acc = None
+    for i in sorted(diags):
+        term = E.mul_plain(E.rot(v, i), diags[i])
+        acc = term if acc is None else E.add(acc, term)
+    if add_vec is not None:
+        acc = E.add_plain(acc, add_vec)
+    return E.rescale(acc)
+
+
+def infer(E, m: Model, X, N: int):
+    """Algorithm 1: SecComp, reshuffle, per-level product XOR mask, MultAll.
+    Reading: the level products use Branches (the reshuffled vector, as the
+    text of Section 4.3 says), not Decisions as the listing prints."""
+    t = E.t
+    Y = E.thresholds(m)
+    D = seccomp(E, X, Y, m.precision)
+    Rd = {i: tile_blocks(m, dg, N) for i, dg in reshuffle_diagonals(m).items()}
+    Br = matmul(E, D, Rd)
+    E.begin_shared_rotations(Br)
+    res = []
+    for k in range(1, m.d + 1):
+        Ld = {i: tile_blocks(m, dg, N) for i, dg in level_diagonals(m, k, t).items()}
+        res.append(matmul(E, Br, Ld, tile_blocks(m, m.mask[k - 1], N)))
+    E.end_shared_rotations()
+    return pairwise(res, lambda a, b, root: E.mul(a, b))
+
+
+class SlotEngine:
+    """Cleartext slot arithmetic mod t: the values the encrypted circuit must decrypt to."""
+
+    def __init__(self, N: int, t: int = B.T_DEFAULT, encrypted_model=False, model=None):
+        self.N, self.t, self.encrypted_model = N, t, encrypted_model
+
+    def thresholds(self, m):
+        return threshold_planes(m, self.N)
+
+    def rot(self, v, i):
+        h = self.N // 2
+        return np.concatenate([np.roll(v[:h], -i), np.roll(v[h:], -i)])
+
+    def mul(self, a, b):
+        return (a * b) % self.t
+
+    def mul_plain(self, a, p):
+        return (a * p) % self.t
+
+    def add(self, a, b):
+        return (a + b) % self.t
+
+    def sub(self, a, b):
+        return (a - b) % self.t
+
+    def add_const(self, a, c):
+        return (a + c) % self.t
+
+    def add_plain(self, a, p):
+        return (a + p) % self.t
+
+    def affine(self, x, mult, addv):
+        return (x * mult + addv) % self.t
+
+    def rescale(self, a):
+        return a
+
+    def begin_shared_rotations(self, v):
+        pass
+
+    def end_shared_rotations(self):
+        pass
+
+
+class BgvEngine:
+    """The same circuit on BGV ciphertexts with the canonical policy: after every
+    multiplication (ct x ct after relinearisation; after each affine plaintext
+    step and after each matrix product) drop one prime; before a binary
+    operation bring the operand at the higher level down.  Rotations of one
+    ciphertext by the same amount are computed once and reused."""
+
+    def __init__(self, bgv: B.Bgv, keys: B.Keys, encrypted_model=False, enc_model=None):
+        self.b, self.k = bgv, keys
+        self.P = bgv.P
+        self.N, self.t = self.P.N, self.P.t
+        self.encrypted_model = encrypted_model
+        self.enc_model = enc_model
+        self._memo_src = None
+        self._memo = {}
+        self.counts = {"rot": 0, "mul": 0, "mul_plain": 0, "modswitch_ops": 0}
+
+    def thresholds(self, m):
+        if self.encrypted_model:
+            return self.enc_model["thresholds"]
+        return threshold_planes(m, self.N)
+
+    def rot(self, v, i):
+        if i == 0:
+            return v
+        if self._memo_src is v and i in self._memo:
+            return self._memo[i]
+        g = B.galois_rot(self.P.logN, i)
+        r = self.b.rotate(v, g, self.k.gk[g])
+        self.counts["rot"] += 1
+        if self._memo_src is v:
+            self._memo[i] = r
+        return r
+
+    def begin_shared_rotations(self, v):
+        self._memo_src, self._memo = v, {}
+
+    def end_shared_rotations(self):
+        self._memo_src, self._memo = None, {}
+
+    def mul(self, a, b):
+        self.counts["mul"] += 1
+        return self.b.mul(a, b, self.k.rlk)
+
+    def mul_plain(self, a, p):
+        self.counts["mul_plain"] += 1
+        return self.b.mul_plain(a, B.encode(self.P, p))
+
+    def add(self, a, b):
+        return self.b.add(a, b)
+
+    def sub(self, a, b):
+        return self.b.sub(a, b)
+
+    def add_const(self, a, c):
+        return self.b.add_plain(a, B.encode(self.P, np.full(self.N, c)))
+
+    def add_plain(self, a, p):
+        return self.b.add_plain(a, B.encode(self.P, p))
+
+    def affine(self, x, mult, addv):
+        r = self.b.add_plain(self.b.mul_plain(x, B.encode(self.P, mult)), B.encode(self.P, addv))
+        return self.b.modswitch(r)
+
+    def rescale(self, a):
+        return self.b.modswitch(a)
+
+
+def galois_elements(m: Model, logN: int):
+    rs, ls = rotation_sets(m)
+    return sorted(set(B.galois_rot(logN, i) for i in rs + ls))
+
+
+def encrypt_queries(bgv: B.Bgv, keys: B.Keys, m: Model, queries, seed: int):
+    planes = feature_planes(m, queries, bgv.P.N)
+    return [bgv.encrypt_slots(keys.pk, planes[i], seed, i) for i in range(m.precision)]
+
+
+def decode_labels(m: Model, slots, n_queries: int):
+    """Result slots -> per query, one bit per leaf (Section 4.1.2, Classification Result)."""
+    out = []
+    for j in range(n_queries):
+        v = np.asarray(slots[j * m.block: j * m.block + m.L], dtype=np.int64)
+        out.append(v.tolist())
+    return out
+
+
+def levels_needed(m: Model, encrypted_model=False) -> int:
+    """Primes dropped by the circuit under the canonical policy (plaintext model):
+    1 (SecComp leaves) + ceil(log2 p) + 1 (reshuffle) + 1 (levels) + ceil(log2 d)."""
+    def clog2(x):
+        return (x - 1).bit_length() if x > 1 else 0
+    return (1 if not encrypted_model else 1) + clog2(m.precision) + 2 + clog2(m.d)

@@ -1,0 +1,17 @@
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def pytest_configure(config):
+    config.addinivalue_line("markers", "gpu: needs a CUDA GPU (sm_103a) and the built CUDA library")
+
+
+def read_golden(name):
+    """Golden fixture text without its '#' comment lines."""
+    path = os.path.join(ROOT, "tests", "golden", name)
+    with open(path) as f:
+        return "".join(ln for ln in f if not ln.lstrip().startswith("#"))
