@@ -1,0 +1,234 @@
+/*
+ * copse.h -- C ABI of the GB300 (sm_103a) COPSE secure decision-forest library.
+ *
+ * COPSE (Malik et al., "Vectorized Secure Evaluation of Decision Forests",
+ * PLDI'21) compiles a plaintext decision forest into vectorised structures
+ * (Section 4.2) and evaluates Algorithm 1 (Section 4.3) over packed BGV
+ * ciphertexts: SecComp of the replicated feature vector against the padded
+ * threshold vector, a reshuffle matrix-vector product, one product plus mask
+ * per level, and the product across levels.  The runtime interface follows
+ * Section 5 ("COPSE Runtime": encrypt models and feature vectors, run secure
+ * inference) and the workflow of Section 3.2.
+ *
+ * Conventions for every call:
+ *   - Status: 0 on success, a negative COPSE_E* code on failure; nothing
+ *     aborts.  copse_last_error() gives a message for the calling thread.
+ *   - Ownership: the library allocates and frees every handle; inputs are
+ *     copied or only read during the call; outputs go to caller-owned buffers
+ *     or to new handles the caller destroys with the matching *_destroy.
+ *   - Streams: `stream` is a cudaStream_t passed as void* (NULL = the legacy
+ *     default stream).  Calls that take host output buffers synchronise the
+ *     stream before returning; calls marked "async" only enqueue work.
+ *   - Device: handles are bound to the device of the context that made them;
+ *     the caller keeps that device current.
+ *   - Threads: one context per host thread; handles are not internally locked.
+ *
+ * Plaintext modulus: t = 65537 (prime, = 1 mod 2^17), N slots in two rows of
+ * N/2.  Slot values are bits; AND is a product, XOR a + b - 2ab.  The paper's
+ * BGV runs at plaintext modulus 2 in HElib; with a power-of-two ring degree
+ * that modulus gives a single slot, so t = 65537 carries the same bit circuit.
+ */
+#ifndef COPSE_H
+#define COPSE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int copse_status;
+#define COPSE_OK 0
+#define COPSE_EINVAL (-1)   /* bad argument, size or shape                      */
+#define COPSE_ENOMEM (-2)   /* device or host allocation failed                 */
+#define COPSE_EPARSE (-3)   /* malformed forest text                            */
+#define COPSE_ECUDA (-4)    /* a CUDA runtime call failed                       */
+#define COPSE_ENOKEY (-5)   /* a rotation key the model needs is missing        */
+#define COPSE_ELEVEL (-6)   /* the prime chain is too short for the circuit    */
+#define COPSE_EFIT (-7)     /* the model's slot block does not fit a slot row   */
+
+/* Ring and RNS parameters.  All primes are = 1 mod 2*N*t and below
+ * 2^prime_bits, chosen in decreasing order: n_primes ciphertext primes, then
+ * alpha = ceil(n_primes / dnum) special primes for hybrid key switching. */
+typedef struct copse_params {
+    uint32_t log_n;      /* ring degree N = 2^log_n, 4 <= log_n <= 14            */
+    uint32_t prime_bits; /* bit length of every prime, 36 <= prime_bits <= 60     */
+    uint32_t n_primes;   /* ciphertext primes L, 1 <= L <= 40                      */
+    uint32_t dnum;       /* key-switching digits, 1 <= dnum <= L                   */
+} copse_params;
+
+typedef struct copse_ctx copse_ctx;     /* device, prime tables, NTT tables            */
+typedef struct copse_model copse_model; /* compiled forest (host) + its device plaintexts */
+typedef struct copse_keys copse_keys;   /* secret and public key (the data owner's)   */
+typedef struct copse_evk copse_evk;     /* relinearisation and rotation keys (server) */
+typedef struct copse_ctbuf copse_ctbuf; /* an ordered set of device ciphertexts        */
+
+typedef struct copse_model_info {
+    uint32_t n_features;  /* features of a query                                   */
+    uint32_t precision;   /* p: bits of every feature and threshold (Section 4.1.2) */
+    uint32_t K;           /* maximum multiplicity (Section 4.1.1)                    */
+    uint32_t q;           /* quantised branching K * n_features                      */
+    uint32_t b;           /* branching: number of branch nodes                       */
+    uint32_t n_leaves;    /* L: slots of the result, one per leaf                    */
+    uint32_t depth;       /* d: number of levels                                     */
+    uint32_t n_trees;
+    uint32_t n_classes;   /* label names on the first line of the model text        */
+    uint32_t block;       /* slots per query block (power of two >= L+b+q-2)          */
+    uint32_t n_rot_reshuffle; /* nonzero rotation amounts of the reshuffle product   */
+    uint32_t n_rot_level;     /* nonzero rotation amounts shared by the level products */
+    uint32_t levels_used; /* primes the circuit drops: 3 + ceil(log2 p) + ceil(log2 d) */
+} copse_model_info;
+
+/* Message for the last failed call on this thread (never NULL). */
+const char *copse_last_error(void);
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context on CUDA device `device`: selects the primes, builds the
+ * NTT and base-conversion tables on the device.  EINVAL on out-of-range
+ * parameters, ECUDA/ENOMEM on device failure. */
+copse_status copse_ctx_create(const copse_params *params, int device, copse_ctx **out);
+void copse_ctx_destroy(copse_ctx *ctx);
+
+/* The n_primes + alpha primes (ciphertext primes first) into out[0..cap). */
+copse_status copse_ctx_primes(const copse_ctx *ctx, uint64_t *out, size_t cap, size_t *count);
+
+/* ---------------------------------------------------------------- models */
+
+/* Compile a forest (Section 5, "Input Representation"): the first line lists
+ * the label (class) names; each further line is one tree in preorder, a branch
+ * written "b <feature> <threshold>" followed by its left then right subtree, a
+ * leaf "l <class>".  A branch sends x[feature] < threshold to the right
+ * (true) child.  Builds the padded threshold vector, the reshuffling matrix,
+ * the level matrices and masks (Section 4.2) for rings of degree 2^log_n.
+ * Host only; touches no device.  n_features = 0 takes the largest feature
+ * index + 1.  EPARSE on malformed text, EINVAL on a threshold >= 2^precision,
+ * a feature >= n_features or a class index out of range, EFIT if the query
+ * block exceeds a slot row (N/2). */
+copse_status copse_compile_forest(const char *text, size_t len, uint32_t precision, uint32_t n_features,
+                                  uint32_t log_n, copse_model **out);
+void copse_model_destroy(copse_model *model);
+copse_status copse_model_info_get(const copse_model *model, copse_model_info *info);
+
+/* Compiled structures, for inspection and host-side parity tests.
+ *   thr_slot[q], slot_branch[q]: padded threshold vector and the branch each
+ *     padded slot holds (-1 = sentinel, Section 4.2.1);
+ *   R[b*q]: reshuffling matrix, row-major (Section 4.2.2);
+ *   lvl[d*L*b]: level matrices k = 1..d, row-major (Section 4.2.3);
+ *   mask[d*L]: level masks (Section 4.2.4);
+ *   br_level[b]: level of each branch (Section 4.1.1).
+ * Any pointer may be NULL to skip that array. */
+copse_status copse_model_export(const copse_model *model, uint32_t *thr_slot, int32_t *slot_branch, uint8_t *R,
+                                uint8_t *lvl, uint8_t *mask, uint32_t *br_level);
+
+/* Nonzero rotation amounts: reshuffle then level products, ascending in each. */
+copse_status copse_model_rotations(const copse_model *model, uint32_t *reshuffle, uint32_t *level);
+
+/* Plaintext classification (Section 2.1): one bit per leaf per query,
+ * out_bits[n_queries * n_leaves]; feats[n_queries * n_features] on the host. */
+copse_status copse_classify_plain(const copse_model *model, const uint32_t *feats, size_t n_queries,
+                                  uint8_t *out_bits);
+
+/* ---------------------------------------------------------------- keys */
+
+/* Generate the secret key, public key, relinearisation key and one rotation
+ * key for every rotation amount any of `models` uses, from the counter-based
+ * generator seeded with `seed`.  All keys stay in device memory.  Synchronous. */
+copse_status copse_keygen(copse_ctx *ctx, uint64_t seed, const copse_model *const *models, size_t n_models,
+                          copse_keys **keys, copse_evk **evk);
+void copse_keys_destroy(copse_keys *keys);
+void copse_evk_destroy(copse_evk *evk);
+
+/* Secret key coefficients (ternary, N values) to the host. */
+copse_status copse_keys_export_secret(const copse_keys *keys, int64_t *s);
+
+/* A switching key in coefficient form to the host, layout
+ * [digit][2][n_primes + alpha][N] (words = digits * 2 * (L+alpha) * N).
+ * galois = 0 selects the relinearisation key, else the key of that Galois
+ * element (3^k mod 2N for a rotation by k).  ENOKEY if absent. */
+copse_status copse_evk_export(const copse_evk *evk, uint64_t galois, uint64_t *out, size_t words);
+
+/* ---------------------------------------------------------------- data */
+
+/* Encrypt n_queries feature vectors for `model` (Section 3.3, Step 0):
+ * each feature is replicated K times, laid out periodically in the query's
+ * slot block, split into `precision` bit-planes (Section 4.1.2) and each plane
+ * encrypted under the public key with randomness from `seed` (plane i uses
+ * encryption index i).  feats[n_queries * n_features], values < 2^precision,
+ * host memory if feats_on_device = 0, else device memory.  At most
+ * N / block queries.  The new buffer holds `precision` ciphertexts.
+ * Async on `stream` when feats_on_device = 1. */
+copse_status copse_encrypt_features(copse_ctx *ctx, const copse_keys *keys, copse_model *model,
+                                    const uint32_t *feats, size_t n_queries, int feats_on_device, uint64_t seed,
+                                    copse_ctbuf **out, void *stream);
+
+/* Secure inference, Algorithm 1 (Section 4.3): SecComp, reshuffle, level
+ * products with masks, product across levels.  `feats` comes from
+ * copse_encrypt_features for the same model.  Output: one ciphertext whose
+ * slot block j holds query j's leaf bits.  Async on `stream`. */
+copse_status copse_infer(copse_ctx *ctx, const copse_evk *evk, copse_model *model, const copse_ctbuf *feats,
+                         copse_ctbuf **out, void *stream);
+
+/* Decrypt an inference result into out_bits[n_queries * n_leaves]: 1 for the
+ * leaf each tree selects, 0 elsewhere, 2 for a slot that is not a bit
+ * (noise overflow).  out_bits is host memory if out_on_device = 0 (the call
+ * then synchronises), else device memory (async). */
+copse_status copse_decrypt_labels(copse_ctx *ctx, const copse_keys *keys, const copse_model *model,
+                                  const copse_ctbuf *result, uint8_t *out_bits, size_t n_queries,
+                                  int out_on_device, void *stream);
+
+/* All N slot values (mod t, slot order: row 0 columns 0..N/2-1, then row 1)
+ * of ciphertext `index`, to host memory out_slots[N].  Synchronous. */
+copse_status copse_decrypt_slots(copse_ctx *ctx, const copse_keys *keys, const copse_ctbuf *buf, size_t index,
+                                 uint64_t *out_slots);
+
+/* ---------------------------------------------------------------- buffers */
+
+size_t copse_ctbuf_count(const copse_ctbuf *buf);
+/* Level (primes) and components of ciphertext `index`. */
+copse_status copse_ctbuf_shape(const copse_ctbuf *buf, size_t index, uint32_t *level, uint32_t *ncomp);
+/* Ciphertext `index` in coefficient form to the host, layout
+ * [component][prime][N], residues in [0, q_i).  Synchronous. */
+copse_status copse_ctbuf_export(copse_ctx *ctx, const copse_ctbuf *buf, size_t index, uint64_t *out, size_t words);
+/* New buffer of n_ct two-component ciphertexts at `level` from coefficient
+ * form host data, layout [ct][2][level][N].  Synchronous. */
+copse_status copse_ctbuf_import(copse_ctx *ctx, const uint64_t *in, size_t n_ct, uint32_t level,
+                                copse_ctbuf **out);
+void copse_ctbuf_destroy(copse_ctbuf *buf);
+
+/* ---------------------------------------------------------------- ring ops
+ * Single BGV operations on buffer entries, for per-operation checks.  All
+ * create a new one-ciphertext buffer and are async on `stream`. */
+
+/* a * b, relinearised, then one prime dropped (the multiply of Section 6). */
+copse_status copse_ct_mul(copse_ctx *ctx, const copse_evk *evk, const copse_ctbuf *a, size_t ia,
+                          const copse_ctbuf *b, size_t ib, copse_ctbuf **out, void *stream);
+/* Rotation of every slot row left by k (Section 4.1.2, Matrix Multiplication). */
+copse_status copse_ct_rotate(copse_ctx *ctx, const copse_evk *evk, const copse_ctbuf *a, size_t ia, uint32_t k,
+                             copse_ctbuf **out, void *stream);
+/* Drop the last prime. */
+copse_status copse_ct_modswitch(copse_ctx *ctx, const copse_ctbuf *a, size_t ia, copse_ctbuf **out, void *stream);
+/* a * plaintext + plaintext: slot vectors mul_slots[N], add_slots[N] (host,
+ * values mod t; add_slots may be NULL). */
+copse_status copse_ct_mul_plain(copse_ctx *ctx, const copse_ctbuf *a, size_t ia, const uint64_t *mul_slots,
+                                const uint64_t *add_slots, copse_ctbuf **out, void *stream);
+
+/* Forward (inverse = 0) or inverse negacyclic NTT, in place, of n_polys
+ * polynomials laid out [n_polys][n_res][N] in device memory, residue r taken
+ * modulo ciphertext prime r (n_res <= n_primes).  Coefficient order in,
+ * bit-reversed evaluation order out (and back).  Async. */
+copse_status copse_ntt(copse_ctx *ctx, uint64_t *data, size_t n_polys, uint32_t n_res, int inverse, void *stream);
+
+/* Negacyclic product c = a * b in Z_q[X]/(X^N + 1), coefficient form in and
+ * out, n_res residues per operand laid out [n_res][N] in device memory,
+ * residue r modulo ciphertext prime r.  Uses temporary device memory from
+ * the context's pool.  Async. */
+copse_status copse_poly_mul(copse_ctx *ctx, const uint64_t *a, const uint64_t *b, uint64_t *c, uint32_t n_res,
+                            void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* COPSE_H */

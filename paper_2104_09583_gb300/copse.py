@@ -1,0 +1,310 @@
+"""Thin Python binding of the C ABI in ``include/copse.h`` (ctypes).
+
+Argument marshalling only: every step of the secure-inference path runs in
+the CUDA library.  Functions keep the C names; handles are opaque
+``ctypes.c_void_p`` values that the caller releases with the matching
+``*_destroy``.  A nonzero status raises ``CopseError`` with the library's
+message.  If the shared library has not been built the import fails loudly;
+there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+import numpy as np
+
+from .build_lib import LIB as _LIB_PATH
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "copse.h")
+
+if not os.path.exists(_LIB_PATH):
+    raise ImportError(f"CUDA library {_LIB_PATH} is not built; run __graft_entry__.build()")
+
+_lib = C.CDLL(_LIB_PATH)
+
+STATUS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "EPARSE", -4: "ECUDA", -5: "ENOKEY", -6: "ELEVEL", -7: "EFIT"}
+
+
+class CopseError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+        self.name = STATUS.get(code, str(code))
+
+
+class copse_params(C.Structure):
+    _fields_ = [("log_n", C.c_uint32), ("prime_bits", C.c_uint32), ("n_primes", C.c_uint32), ("dnum", C.c_uint32)]
+
+
+class copse_model_info(C.Structure):
+    _fields_ = [(n, C.c_uint32) for n in (
+        "n_features", "precision", "K", "q", "b", "n_leaves", "depth", "n_trees", "n_classes", "block",
+        "n_rot_reshuffle", "n_rot_level", "levels_used")]
+
+
+vp = C.c_void_p
+pvp = C.POINTER(C.c_void_p)
+u64p = np.ctypeslib.ndpointer(dtype=np.uint64, flags="C_CONTIGUOUS")
+u32p = np.ctypeslib.ndpointer(dtype=np.uint32, flags="C_CONTIGUOUS")
+i64p = np.ctypeslib.ndpointer(dtype=np.int64, flags="C_CONTIGUOUS")
+i32p = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
+u8p = np.ctypeslib.ndpointer(dtype=np.uint8, flags="C_CONTIGUOUS")
+
+_SIG = {
+    "copse_last_error": (C.c_char_p, []),
+    "copse_ctx_create": (C.c_int, [C.POINTER(copse_params), C.c_int, pvp]),
+    "copse_ctx_destroy": (None, [vp]),
+    "copse_ctx_primes": (C.c_int, [vp, u64p, C.c_size_t, C.POINTER(C.c_size_t)]),
+    "copse_compile_forest": (C.c_int, [C.c_char_p, C.c_size_t, C.c_uint32, C.c_uint32, C.c_uint32, pvp]),
+    "copse_model_destroy": (None, [vp]),
+    "copse_model_info_get": (C.c_int, [vp, C.POINTER(copse_model_info)]),
+    "copse_model_export": (C.c_int, [vp, vp, vp, vp, vp, vp, vp]),
+    "copse_model_rotations": (C.c_int, [vp, vp, vp]),
+    "copse_classify_plain": (C.c_int, [vp, u32p, C.c_size_t, u8p]),
+    "copse_keygen": (C.c_int, [vp, C.c_uint64, C.POINTER(C.c_void_p), C.c_size_t, pvp, pvp]),
+    "copse_keys_destroy": (None, [vp]),
+    "copse_evk_destroy": (None, [vp]),
+    "copse_keys_export_secret": (C.c_int, [vp, i64p]),
+    "copse_evk_export": (C.c_int, [vp, C.c_uint64, u64p, C.c_size_t]),
+    "copse_encrypt_features": (C.c_int, [vp, vp, vp, vp, C.c_size_t, C.c_int, C.c_uint64, pvp, vp]),
+    "copse_infer": (C.c_int, [vp, vp, vp, vp, pvp, vp]),
+    "copse_decrypt_labels": (C.c_int, [vp, vp, vp, vp, vp, C.c_size_t, C.c_int, vp]),
+    "copse_decrypt_slots": (C.c_int, [vp, vp, vp, C.c_size_t, u64p]),
+    "copse_ctbuf_count": (C.c_size_t, [vp]),
+    "copse_ctbuf_shape": (C.c_int, [vp, C.c_size_t, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)]),
+    "copse_ctbuf_export": (C.c_int, [vp, vp, C.c_size_t, u64p, C.c_size_t]),
+    "copse_ctbuf_import": (C.c_int, [vp, u64p, C.c_size_t, C.c_uint32, pvp]),
+    "copse_ctbuf_destroy": (None, [vp]),
+    "copse_ct_mul": (C.c_int, [vp, vp, vp, C.c_size_t, vp, C.c_size_t, pvp, vp]),
+    "copse_ct_rotate": (C.c_int, [vp, vp, vp, C.c_size_t, C.c_uint32, pvp, vp]),
+    "copse_ct_modswitch": (C.c_int, [vp, vp, C.c_size_t, pvp, vp]),
+    "copse_ct_mul_plain": (C.c_int, [vp, vp, C.c_size_t, u64p, vp, pvp, vp]),
+    "copse_ntt": (C.c_int, [vp, vp, C.c_size_t, C.c_uint32, C.c_int, vp]),
+    "copse_poly_mul": (C.c_int, [vp, vp, vp, vp, C.c_uint32, vp]),
+}
+for _n, (_r, _a) in _SIG.items():
+    _f = getattr(_lib, _n)
+    _f.restype = _r
+    _f.argtypes = _a
+
+
+def declared_functions():
+    """Names of the functions include/copse.h declares."""
+    with open(HEADER) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(copse_[a-z0-9_]+)\s*\(", text)))
+
+
+def library():
+    return _lib
+
+
+def _check(st):
+    if st != 0:
+        raise CopseError(st, _lib.copse_last_error().decode())
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+# ---------------------------------------------------------------- context
+def copse_ctx_create(log_n, prime_bits, n_primes, dnum=3, device=0):
+    p = copse_params(log_n, prime_bits, n_primes, dnum)
+    h = C.c_void_p()
+    _check(_lib.copse_ctx_create(C.byref(p), device, C.byref(h)))
+    return h
+
+
+def copse_ctx_destroy(ctx):
+    _lib.copse_ctx_destroy(ctx)
+
+
+def copse_ctx_primes(ctx):
+    n = C.c_size_t()
+    buf = np.zeros(128, dtype=np.uint64)
+    _check(_lib.copse_ctx_primes(ctx, buf, buf.size, C.byref(n)))
+    return [int(x) for x in buf[: n.value]]
+
+
+# ---------------------------------------------------------------- models
+def copse_compile_forest(text, precision, n_features=0, log_n=14):
+    b = text.encode()
+    h = C.c_void_p()
+    _check(_lib.copse_compile_forest(b, len(b), precision, n_features, log_n, C.byref(h)))
+    return h
+
+
+def copse_model_destroy(m):
+    _lib.copse_model_destroy(m)
+
+
+def copse_model_info_get(m):
+    info = copse_model_info()
+    _check(_lib.copse_model_info_get(m, C.byref(info)))
+    return {n: getattr(info, n) for n, _ in copse_model_info._fields_}
+
+
+def copse_model_export(m):
+    i = copse_model_info_get(m)
+    q, b, L, d = i["q"], i["b"], i["n_leaves"], i["depth"]
+    thr = np.zeros(q, np.uint32)
+    sb = np.zeros(q, np.int32)
+    R = np.zeros(b * q, np.uint8)
+    lvl = np.zeros(max(d * L * b, 1), np.uint8)
+    mask = np.zeros(max(d * L, 1), np.uint8)
+    bl = np.zeros(b, np.uint32)
+    _check(_lib.copse_model_export(m, _ptr(thr), _ptr(sb), _ptr(R), _ptr(lvl), _ptr(mask), _ptr(bl)))
+    return {"thr_slot": thr, "slot_branch": sb, "R": R.reshape(b, q), "lvl": lvl[: d * L * b].reshape(d, L, b),
+            "mask": mask[: d * L].reshape(d, L), "br_level": bl}
+
+
+def copse_model_rotations(m):
+    i = copse_model_info_get(m)
+    a = np.zeros(max(i["n_rot_reshuffle"], 1), np.uint32)
+    b = np.zeros(max(i["n_rot_level"], 1), np.uint32)
+    _check(_lib.copse_model_rotations(m, _ptr(a), _ptr(b)))
+    return a[: i["n_rot_reshuffle"]].tolist(), b[: i["n_rot_level"]].tolist()
+
+
+def copse_classify_plain(m, feats):
+    feats = np.ascontiguousarray(feats, dtype=np.uint32)
+    i = copse_model_info_get(m)
+    n = feats.shape[0]
+    out = np.zeros(max(n * i["n_leaves"], 1), np.uint8)
+    _check(_lib.copse_classify_plain(m, feats.reshape(-1) if n else np.zeros(1, np.uint32), n, out))
+    return out[: n * i["n_leaves"]].reshape(n, i["n_leaves"])
+
+
+# ---------------------------------------------------------------- keys
+def copse_keygen(ctx, seed, models):
+    arr = (C.c_void_p * max(len(models), 1))(*[m.value for m in models])
+    k, e = C.c_void_p(), C.c_void_p()
+    _check(_lib.copse_keygen(ctx, seed, arr, len(models), C.byref(k), C.byref(e)))
+    return k, e
+
+
+def copse_keys_destroy(k):
+    _lib.copse_keys_destroy(k)
+
+
+def copse_evk_destroy(e):
+    _lib.copse_evk_destroy(e)
+
+
+def copse_keys_export_secret(k, n):
+    s = np.zeros(n, np.int64)
+    _check(_lib.copse_keys_export_secret(k, s))
+    return s
+
+
+def copse_evk_export(e, galois, words):
+    out = np.zeros(words, np.uint64)
+    _check(_lib.copse_evk_export(e, galois, out, words))
+    return out
+
+
+# ---------------------------------------------------------------- data
+def copse_encrypt_features(ctx, keys, model, feats, seed, stream=None, on_device=False, n_queries=None):
+    """feats: host numpy [n, n_features] (on_device=False) or a device pointer (int) with n_queries."""
+    h = C.c_void_p()
+    if on_device:
+        _check(_lib.copse_encrypt_features(ctx, keys, model, C.c_void_p(feats), n_queries, 1, seed, C.byref(h),
+                                           C.c_void_p(stream)))
+    else:
+        f = np.ascontiguousarray(feats, dtype=np.uint32)
+        _check(_lib.copse_encrypt_features(ctx, keys, model, _ptr(f), f.shape[0], 0, seed, C.byref(h),
+                                           C.c_void_p(stream)))
+    return h
+
+
+def copse_infer(ctx, evk, model, feats, stream=None):
+    h = C.c_void_p()
+    _check(_lib.copse_infer(ctx, evk, model, feats, C.byref(h), C.c_void_p(stream)))
+    return h
+
+
+def copse_decrypt_labels(ctx, keys, model, result, n_queries, stream=None, out_device_ptr=None):
+    if out_device_ptr is not None:
+        _check(_lib.copse_decrypt_labels(ctx, keys, model, result, C.c_void_p(out_device_ptr), n_queries, 1,
+                                         C.c_void_p(stream)))
+        return None
+    L = copse_model_info_get(model)["n_leaves"]
+    out = np.zeros(max(n_queries * L, 1), np.uint8)
+    _check(_lib.copse_decrypt_labels(ctx, keys, model, result, _ptr(out), n_queries, 0, C.c_void_p(stream)))
+    return out[: n_queries * L].reshape(n_queries, L)
+
+
+def copse_decrypt_slots(ctx, keys, buf, index, n):
+    out = np.zeros(n, np.uint64)
+    _check(_lib.copse_decrypt_slots(ctx, keys, buf, index, out))
+    return out
+
+
+# ---------------------------------------------------------------- buffers
+def copse_ctbuf_count(b):
+    return _lib.copse_ctbuf_count(b)
+
+
+def copse_ctbuf_shape(b, i):
+    lv, nc = C.c_uint32(), C.c_uint32()
+    _check(_lib.copse_ctbuf_shape(b, i, C.byref(lv), C.byref(nc)))
+    return lv.value, nc.value
+
+
+def copse_ctbuf_export(ctx, b, i, N):
+    lv, nc = copse_ctbuf_shape(b, i)
+    out = np.zeros(nc * lv * N, np.uint64)
+    _check(_lib.copse_ctbuf_export(ctx, b, i, out, out.size))
+    return out.reshape(nc, lv, N)
+
+
+def copse_ctbuf_import(ctx, cts):
+    """cts: numpy [n_ct, 2, level, N] coefficient residues."""
+    a = np.ascontiguousarray(cts, dtype=np.uint64)
+    h = C.c_void_p()
+    _check(_lib.copse_ctbuf_import(ctx, a.reshape(-1), a.shape[0], a.shape[2], C.byref(h)))
+    return h
+
+
+def copse_ctbuf_destroy(b):
+    _lib.copse_ctbuf_destroy(b)
+
+
+# ---------------------------------------------------------------- ring ops
+def copse_ct_mul(ctx, evk, a, ia, b, ib, stream=None):
+    h = C.c_void_p()
+    _check(_lib.copse_ct_mul(ctx, evk, a, ia, b, ib, C.byref(h), C.c_void_p(stream)))
+    return h
+
+
+def copse_ct_rotate(ctx, evk, a, ia, k, stream=None):
+    h = C.c_void_p()
+    _check(_lib.copse_ct_rotate(ctx, evk, a, ia, k, C.byref(h), C.c_void_p(stream)))
+    return h
+
+
+def copse_ct_modswitch(ctx, a, ia, stream=None):
+    h = C.c_void_p()
+    _check(_lib.copse_ct_modswitch(ctx, a, ia, C.byref(h), C.c_void_p(stream)))
+    return h
+
+
+def copse_ct_mul_plain(ctx, a, ia, mul_slots, add_slots=None, stream=None):
+    h = C.c_void_p()
+    m = np.ascontiguousarray(mul_slots, dtype=np.uint64)
+    ad = None if add_slots is None else np.ascontiguousarray(add_slots, dtype=np.uint64)
+    _check(_lib.copse_ct_mul_plain(ctx, a, ia, m, _ptr(ad), C.byref(h), C.c_void_p(stream)))
+    return h
+
+
+def copse_ntt(ctx, data_ptr, n_polys, n_res, inverse=False, stream=None):
+    _check(_lib.copse_ntt(ctx, C.c_void_p(data_ptr), n_polys, n_res, 1 if inverse else 0, C.c_void_p(stream)))
+
+
+def copse_poly_mul(ctx, a_ptr, b_ptr, c_ptr, n_res, stream=None):
+    _check(_lib.copse_poly_mul(ctx, C.c_void_p(a_ptr), C.c_void_p(b_ptr), C.c_void_p(c_ptr), n_res,
+                               C.c_void_p(stream)))

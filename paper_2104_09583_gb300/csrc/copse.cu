@@ -1,0 +1,513 @@
+// C-ABI entry points: models (compile, upload of the plaintext structures),
+// keys, feature encryption, Algorithm 1 of the paper (Section 4.3) on the
+// device, decryption, buffers and single ring operations.
+#include <algorithm>
+#include <cstring>
+#include <memory>
+
+#include "forest.h"
+#include "internal.cuh"
+
+namespace {
+
+uint32_t clog2u(uint32_t x) {
+    uint32_t r = 0;
+    while ((1u << r) < x) r++;
+    return r;
+}
+
+cudaStream_t as_stream(void *s) { return (cudaStream_t)s; }
+
+}  // namespace
+
+// Plaintext structures of one model encoded for one context (NTT domain, device).
+struct DeviceModel {
+    copse_ctx *ctx = nullptr;
+    int lvl_D = 0, lvl_B = 0;          // levels of Decisions and of Branches
+    u64 *store = nullptr;              // one allocation for every plaintext
+    // SecComp leaves, plane i: lt = x * lt_mul + lt_add, eq = x * eq_mul + eq_add (level L)
+    std::vector<const u64 *> lt_mul, lt_add, eq_mul, eq_add;
+    std::vector<uint32_t> rot_R;                    // reshuffle rotation amounts
+    std::vector<std::vector<const u64 *>> pt_R;     // [1][rot]
+    std::vector<uint32_t> rot_B;                    // level rotation amounts
+    std::vector<std::vector<const u64 *>> pt_B;     // [d][rot] (null = zero diagonal)
+    std::vector<const u64 *> mask;                  // [d]
+    ~DeviceModel() {
+        if (store) cudaFree(store);
+    }
+};
+
+struct copse_model {
+    CompiledForest f;
+    std::unique_ptr<DeviceModel> dev;
+};
+
+// ---------------------------------------------------------------- model upload
+static copse_status upload_model(copse_ctx *c, copse_model *m, cudaStream_t s) {
+    if (m->dev && m->dev->ctx == c) return COPSE_OK;
+    const CompiledForest &f = m->f;
+    if ((int)f.log_n != c->logN) { set_error("model compiled for another ring degree"); return COPSE_EINVAL; }
+    if ((uint32_t)c->L <= f.levels_used()) {
+        set_error("prime chain of " + std::to_string(c->L) + " is too short: the circuit drops " +
+                  std::to_string(f.levels_used()) + " primes");
+        return COPSE_ELEVEL;
+    }
+    auto D = std::make_unique<DeviceModel>();
+    D->ctx = c;
+    const int N = c->N, L = c->L, p = (int)f.precision, B = (int)f.block;
+    D->lvl_D = L - 1 - (int)clog2u(f.precision);
+    D->lvl_B = D->lvl_D - 1;
+    const u64 t = c->t;
+    // count plaintexts
+    const size_t nleaf = 4 * (size_t)p;
+    D->rot_R = f.rot_reshuffle;
+    D->rot_B = f.rot_level;
+    std::vector<uint8_t> dg8;
+    std::vector<uint64_t> dg64;
+    // level diagonal presence per (k, rot)
+    std::vector<std::vector<char>> lvl_nz(f.d, std::vector<char>(D->rot_B.size(), 0));
+    size_t nlvl = 0;
+    for (uint32_t k = 1; k <= f.d; k++)
+        for (size_t r = 0; r < D->rot_B.size(); r++) {
+            f.level_diagonal(k, D->rot_B[r], t, dg64);
+            bool nz = std::any_of(dg64.begin(), dg64.end(), [](uint64_t v) { return v != 0; });
+            lvl_nz[k - 1][r] = nz;
+            nlvl += nz;
+        }
+    const size_t words = (nleaf * L + D->rot_R.size() * D->lvl_D + (nlvl + f.d) * D->lvl_B) * (size_t)N;
+    CUDA_TRY(cudaMalloc(&D->store, std::max<size_t>(words, 1) * sizeof(u64)));
+    u64 *cur = D->store;
+    // SecComp leaf plaintexts over whole blocks (threshold bit 0 past the decisions)
+    {
+        std::vector<uint32_t> pat(nleaf * B);
+        for (int i = 0; i < p; i++) {
+            for (int x = 0; x < B; x++) {
+                uint32_t y = x < (int)f.pd() ? (f.thr_slot[x % f.q] >> i) & 1u : 0u;
+                pat[(0 * p + i) * (size_t)B + x] = y ? (uint32_t)(t - 1) : 0;    // lt: x * (-y) + y
+                pat[(1 * p + i) * (size_t)B + x] = y;
+                pat[(2 * p + i) * (size_t)B + x] = y ? 1u : (uint32_t)(t - 1);   // eq: x * (2y - 1) + (1 - y)
+                pat[(3 * p + i) * (size_t)B + x] = y ? 0u : 1u;
+            }
+        }
+        STATUS_TRY(encode_patterns(c, pat, (int)nleaf, B, B, L, cur, s));
+        for (int i = 0; i < p; i++) {
+            D->lt_mul.push_back(cur + ((size_t)(0 * p + i) * L) * N);
+            D->lt_add.push_back(cur + ((size_t)(1 * p + i) * L) * N);
+            D->eq_mul.push_back(cur + ((size_t)(2 * p + i) * L) * N);
+            D->eq_add.push_back(cur + ((size_t)(3 * p + i) * L) * N);
+        }
+        cur += nleaf * L * (size_t)N;
+    }
+    // reshuffle diagonals at the level of Decisions
+    {
+        const int m1 = (int)f.m1();
+        std::vector<uint32_t> pat(D->rot_R.size() * (size_t)m1);
+        for (size_t r = 0; r < D->rot_R.size(); r++) {
+            f.reshuffle_diagonal(D->rot_R[r], dg8);
+            for (int x = 0; x < m1; x++) pat[r * m1 + x] = dg8[x];
+        }
+        STATUS_TRY(encode_patterns(c, pat, (int)D->rot_R.size(), m1, B, D->lvl_D, cur, s));
+        D->pt_R.assign(1, std::vector<const u64 *>());
+        for (size_t r = 0; r < D->rot_R.size(); r++) D->pt_R[0].push_back(cur + r * D->lvl_D * (size_t)N);
+        cur += D->rot_R.size() * D->lvl_D * (size_t)N;
+    }
+    // level diagonals (signed, mask folded in) and masks at the level of Branches
+    {
+        const int Lf = (int)f.L;
+        std::vector<uint32_t> pat((nlvl + f.d) * (size_t)Lf);
+        size_t at = 0;
+        D->pt_B.assign(f.d, std::vector<const u64 *>(D->rot_B.size(), nullptr));
+        for (uint32_t k = 1; k <= f.d; k++)
+            for (size_t r = 0; r < D->rot_B.size(); r++) {
+                if (!lvl_nz[k - 1][r]) continue;
+                f.level_diagonal(k, D->rot_B[r], t, dg64);
+                for (int x = 0; x < Lf; x++) pat[at * Lf + x] = (uint32_t)dg64[x];
+                D->pt_B[k - 1][r] = cur + at * D->lvl_B * (size_t)N;
+                at++;
+            }
+        for (uint32_t k = 1; k <= f.d; k++) {
+            for (int x = 0; x < Lf; x++) pat[at * Lf + x] = f.mask[(size_t)(k - 1) * Lf + x];
+            D->mask.push_back(cur + at * D->lvl_B * (size_t)N);
+            at++;
+        }
+        STATUS_TRY(encode_patterns(c, pat, (int)at, Lf, B, D->lvl_B, cur, s));
+    }
+    CUDA_TRY(cudaStreamSynchronize(s));
+    m->dev = std::move(D);
+    return COPSE_OK;
+}
+
+// ---------------------------------------------------------------- models
+extern "C" copse_status copse_compile_forest(const char *text, size_t len, uint32_t precision, uint32_t n_features,
+                                             uint32_t log_n, copse_model **out) {
+    if (!out) { set_error("null output"); return COPSE_EINVAL; }
+    *out = nullptr;
+    auto m = std::make_unique<copse_model>();
+    std::string err;
+    int st = compile_forest(text, len, precision, n_features, log_n, m->f, err);
+    if (st) { set_error(err); return st; }
+    *out = m.release();
+    return COPSE_OK;
+}
+
+extern "C" void copse_model_destroy(copse_model *m) { delete m; }
+
+extern "C" copse_status copse_model_info_get(const copse_model *m, copse_model_info *info) {
+    if (!m || !info) { set_error("null argument"); return COPSE_EINVAL; }
+    const CompiledForest &f = m->f;
+    info->n_features = f.n_features;
+    info->precision = f.precision;
+    info->K = f.K;
+    info->q = f.q;
+    info->b = f.b;
+    info->n_leaves = f.L;
+    info->depth = f.d;
+    info->n_trees = (uint32_t)f.roots.size();
+    info->n_classes = (uint32_t)f.classes.size();
+    info->block = f.block;
+    uint32_t nr = 0, nl = 0;
+    for (uint32_t r : f.rot_reshuffle) nr += r != 0;
+    for (uint32_t r : f.rot_level) nl += r != 0;
+    info->n_rot_reshuffle = nr;
+    info->n_rot_level = nl;
+    info->levels_used = f.levels_used();
+    return COPSE_OK;
+}
+
+extern "C" copse_status copse_model_export(const copse_model *m, uint32_t *thr_slot, int32_t *slot_branch,
+                                           uint8_t *R, uint8_t *lvl, uint8_t *mask, uint32_t *br_level) {
+    if (!m) { set_error("null model"); return COPSE_EINVAL; }
+    const CompiledForest &f = m->f;
+    if (thr_slot) std::copy(f.thr_slot.begin(), f.thr_slot.end(), thr_slot);
+    if (slot_branch) std::copy(f.slot_branch.begin(), f.slot_branch.end(), slot_branch);
+    if (R) std::copy(f.R.begin(), f.R.end(), R);
+    if (lvl) std::copy(f.lvl.begin(), f.lvl.end(), lvl);
+    if (mask) std::copy(f.mask.begin(), f.mask.end(), mask);
+    if (br_level)
+        for (uint32_t i = 0; i < f.b; i++) br_level[i] = (uint32_t)f.br_level[i];
+    return COPSE_OK;
+}
+
+extern "C" copse_status copse_model_rotations(const copse_model *m, uint32_t *reshuffle, uint32_t *level) {
+    if (!m) { set_error("null model"); return COPSE_EINVAL; }
+    size_t a = 0, b = 0;
+    for (uint32_t r : m->f.rot_reshuffle)
+        if (r && reshuffle) reshuffle[a++] = r;
+    for (uint32_t r : m->f.rot_level)
+        if (r && level) level[b++] = r;
+    return COPSE_OK;
+}
+
+extern "C" copse_status copse_classify_plain(const copse_model *m, const uint32_t *feats, size_t n,
+                                             uint8_t *out_bits) {
+    if (!m || (n && (!feats || !out_bits))) { set_error("null argument"); return COPSE_EINVAL; }
+    for (size_t j = 0; j < n; j++) classify_plain(m->f, feats + j * m->f.n_features, out_bits + j * m->f.L);
+    return COPSE_OK;
+}
+
+// ---------------------------------------------------------------- keys
+extern "C" copse_status copse_keygen(copse_ctx *c, uint64_t seed, const copse_model *const *models, size_t n_models,
+                                     copse_keys **keys, copse_evk **evk) {
+    if (!c || !keys || !evk || (n_models && !models)) { set_error("null argument"); return COPSE_EINVAL; }
+    std::vector<u64> gal;
+    const u64 m2 = 2ull * c->N;
+    for (size_t i = 0; i < n_models; i++) {
+        const CompiledForest &f = models[i]->f;
+        if ((int)f.log_n != c->logN) { set_error("model compiled for another ring degree"); return COPSE_EINVAL; }
+        std::vector<uint32_t> rs = f.rot_reshuffle;
+        rs.insert(rs.end(), f.rot_level.begin(), f.rot_level.end());
+        for (uint32_t r : rs) {
+            if (!r) continue;
+            u64 g = 1, b = 3;
+            for (uint32_t e = r; e; e >>= 1, b = b * b % m2)
+                if (e & 1) g = g * b % m2;
+            if (std::find(gal.begin(), gal.end(), g) == gal.end()) gal.push_back(g);
+        }
+    }
+    std::sort(gal.begin(), gal.end());
+    CUDA_TRY(cudaSetDevice(c->device));
+    return keygen_dev(c, seed, gal, keys, evk);
+}
+
+extern "C" void copse_keys_destroy(copse_keys *k) {
+    if (!k) return;
+    cudaStreamSynchronize(0);
+    dev_free(k->s_hat, 0);
+    dev_free(k->pk, 0);
+    delete k;
+}
+
+extern "C" void copse_evk_destroy(copse_evk *e) {
+    if (!e) return;
+    cudaStreamSynchronize(0);
+    dev_free(e->rlk, 0);
+    for (u64 *p : e->gk) dev_free(p, 0);
+    delete e;
+}
+
+extern "C" copse_status copse_keys_export_secret(const copse_keys *k, int64_t *s) {
+    if (!k || !s) { set_error("null argument"); return COPSE_EINVAL; }
+    std::copy(k->s_host.begin(), k->s_host.end(), s);
+    return COPSE_OK;
+}
+
+extern "C" copse_status copse_evk_export(const copse_evk *e, uint64_t galois, uint64_t *out, size_t words) {
+    if (!e || !out) { set_error("null argument"); return COPSE_EINVAL; }
+    copse_ctx *c = e->ctx;
+    const u64 *key = galois == 0 ? e->rlk : e->find(galois);
+    if (!key) { set_error("no key for that Galois element"); return COPSE_ENOKEY; }
+    const size_t n = ksk_words(c);
+    if (words < n) { set_error("buffer too small"); return COPSE_EINVAL; }
+    u64 *tmp = nullptr;
+    STATUS_TRY(dev_alloc(c, (void **)&tmp, n * 8, 0));
+    CUDA_TRY(cudaMemcpyAsync(tmp, key, n * 8, cudaMemcpyDeviceToDevice, 0));
+    const int NB = c->L + c->alpha;
+    STATUS_TRY(ntt_inverse(c, NttBatch{tmp, (size_t)NB * c->N, 2 * c->ndig, 0, NB, NB, -1}, 0));
+    CUDA_TRY(cudaMemcpy(out, tmp, n * 8, cudaMemcpyDeviceToHost));
+    dev_free(tmp, 0);
+    CUDA_TRY(cudaStreamSynchronize(0));
+    return COPSE_OK;
+}
+
+// ---------------------------------------------------------------- data
+extern "C" copse_status copse_encrypt_features(copse_ctx *c, const copse_keys *k, copse_model *m,
+                                               const uint32_t *feats, size_t nq, int on_device, uint64_t seed,
+                                               copse_ctbuf **out, void *stream) {
+    if (!c || !k || !m || !out || (nq && !feats)) { set_error("null argument"); return COPSE_EINVAL; }
+    const CompiledForest &f = m->f;
+    if ((int)f.log_n != c->logN) { set_error("model compiled for another ring degree"); return COPSE_EINVAL; }
+    if (nq > (size_t)(c->N / f.block)) { set_error("more queries than slot blocks"); return COPSE_EINVAL; }
+    cudaStream_t s = as_stream(stream);
+    const uint32_t *d_feats = feats;
+    uint32_t *tmp = nullptr;
+    const size_t nfe = nq * f.n_features;
+    if (!on_device) {
+        for (size_t i = 0; i < nfe; i++)
+            if (f.precision < 32 && feats[i] >= (1u << f.precision)) { set_error("feature value needs more bits than the precision"); return COPSE_EINVAL; }
+        STATUS_TRY(dev_alloc(c, (void **)&tmp, std::max<size_t>(nfe, 1) * 4, s));
+        if (nfe) CUDA_TRY(cudaMemcpyAsync(tmp, feats, nfe * 4, cudaMemcpyHostToDevice, s));
+        d_feats = tmp;
+    }
+    auto buf = std::make_unique<copse_ctbuf>();
+    buf->ctx = c;
+    copse_status st = encrypt_planes(c, k, d_feats, (int)nq, (int)f.n_features, (int)f.K, (int)f.q, (int)f.pd(),
+                                     (int)f.block, (int)f.precision, seed, buf->cts, s);
+    if (tmp) dev_free(tmp, s);
+    if (st) return st;
+    *out = buf.release();
+    return COPSE_OK;
+}
+
+static copse_status infer_impl(copse_ctx *c, const copse_evk *evk, copse_model *m, const copse_ctbuf *feats,
+                               DCt *result, cudaStream_t s) {
+    STATUS_TRY(upload_model(c, m, s));
+    const DeviceModel &D = *m->dev;
+    const CompiledForest &f = m->f;
+    const int p = (int)f.precision;
+    if ((int)feats->cts.size() != p) { set_error("feature buffer does not hold one ciphertext per bit-plane"); return COPSE_EINVAL; }
+    for (const DCt &x : feats->cts)
+        if (x.level != c->L) { set_error("feature ciphertexts must be fresh"); return COPSE_EINVAL; }
+    struct Node { DCt lt, eq; };
+    // SecComp leaves, most significant plane first: lt = (1 - x) y, eq = [x == y]
+    std::vector<Node> nodes;
+    for (int i = p - 1; i >= 0; i--) {
+        Node nd;
+        DPt lm{c->L, (u64 *)D.lt_mul[i]}, la{c->L, (u64 *)D.lt_add[i]};
+        DPt em{c->L, (u64 *)D.eq_mul[i]}, ea{c->L, (u64 *)D.eq_add[i]};
+        STATUS_TRY(op_affine(c, feats->cts[i], lm, &la, &nd.lt, s));
+        STATUS_TRY(op_affine(c, feats->cts[i], em, &ea, &nd.eq, s));
+        nodes.push_back(nd);
+    }
+    // balanced combine (lt_h + eq_h lt_l, eq_h eq_l); no eq at the root
+    while (nodes.size() > 1) {
+        std::vector<Node> nx;
+        const bool root = nodes.size() == 2;
+        for (size_t k = 0; k + 1 < nodes.size(); k += 2) {
+            Node &hi = nodes[k], &lo = nodes[k + 1];
+            Node r;
+            DCt prod;
+            STATUS_TRY(op_mul(c, evk, hi.eq, lo.lt, &prod, s));
+            STATUS_TRY(op_add(c, hi.lt, prod, &r.lt, false, s));
+            ct_free(&prod, s);
+            if (!root) STATUS_TRY(op_mul(c, evk, hi.eq, lo.eq, &r.eq, s));
+            ct_free(&hi.lt, s);
+            ct_free(&hi.eq, s);
+            ct_free(&lo.lt, s);
+            ct_free(&lo.eq, s);
+            nx.push_back(r);
+        }
+        if (nodes.size() % 2) nx.push_back(nodes.back());
+        nodes.swap(nx);
+    }
+    DCt Dc = nodes[0].lt;
+    if (nodes[0].eq.data) ct_free(&nodes[0].eq, s);
+    if (Dc.level != D.lvl_D) { set_error("internal: unexpected level of the decision vector"); return COPSE_EINVAL; }
+    // reshuffle: Branches = R_ext * Decisions
+    std::vector<DCt> br;
+    STATUS_TRY(op_matmul(c, evk, Dc, D.rot_R, D.pt_R, {nullptr}, br, s));
+    ct_free(&Dc, s);
+    // levels: Lvl_k * Branches XOR Mask_k, rotations of Branches shared by every level
+    std::vector<DCt> lv;
+    STATUS_TRY(op_matmul(c, evk, br[0], D.rot_B, D.pt_B, D.mask, lv, s));
+    ct_free(&br[0], s);
+    // product across levels, balanced
+    while (lv.size() > 1) {
+        std::vector<DCt> nx;
+        for (size_t k = 0; k + 1 < lv.size(); k += 2) {
+            DCt r;
+            STATUS_TRY(op_mul(c, evk, lv[k], lv[k + 1], &r, s));
+            ct_free(&lv[k], s);
+            ct_free(&lv[k + 1], s);
+            nx.push_back(r);
+        }
+        if (lv.size() % 2) nx.push_back(lv.back());
+        lv.swap(nx);
+    }
+    *result = lv[0];
+    return COPSE_OK;
+}
+
+extern "C" copse_status copse_infer(copse_ctx *c, const copse_evk *evk, copse_model *m, const copse_ctbuf *feats,
+                                    copse_ctbuf **out, void *stream) {
+    if (!c || !evk || !m || !feats || !out) { set_error("null argument"); return COPSE_EINVAL; }
+    auto buf = std::make_unique<copse_ctbuf>();
+    buf->ctx = c;
+    DCt r;
+    STATUS_TRY(infer_impl(c, evk, m, feats, &r, as_stream(stream)));
+    buf->cts.push_back(r);
+    *out = buf.release();
+    return COPSE_OK;
+}
+
+extern "C" copse_status copse_decrypt_labels(copse_ctx *c, const copse_keys *k, const copse_model *m,
+                                             const copse_ctbuf *res, uint8_t *out_bits, size_t nq, int on_device,
+                                             void *stream) {
+    if (!c || !k || !m || !res || res->cts.empty() || (nq && !out_bits)) { set_error("null argument"); return COPSE_EINVAL; }
+    const CompiledForest &f = m->f;
+    if (nq > (size_t)(c->N / f.block)) { set_error("more queries than slot blocks"); return COPSE_EINVAL; }
+    cudaStream_t s = as_stream(stream);
+    u64 *slots = nullptr;
+    uint8_t *bits = on_device ? out_bits : nullptr;
+    STATUS_TRY(dev_alloc(c, (void **)&slots, (size_t)c->N * 8, s));
+    if (!on_device) STATUS_TRY(dev_alloc(c, (void **)&bits, std::max<size_t>(nq * f.L, 1), s));
+    STATUS_TRY(decrypt_slots_dev(c, k, res->cts[0], slots, s));
+    STATUS_TRY(extract_bits(c, slots, (int)nq, (int)f.block, (int)f.L, bits, s));
+    if (!on_device) {
+        CUDA_TRY(cudaMemcpyAsync(out_bits, bits, nq * f.L, cudaMemcpyDeviceToHost, s));
+        dev_free(bits, s);
+    }
+    dev_free(slots, s);
+    if (!on_device) CUDA_TRY(cudaStreamSynchronize(s));
+    return COPSE_OK;
+}
+
+extern "C" copse_status copse_decrypt_slots(copse_ctx *c, const copse_keys *k, const copse_ctbuf *buf, size_t index,
+                                            uint64_t *out_slots) {
+    if (!c || !k || !buf || !out_slots || index >= buf->cts.size()) { set_error("bad argument"); return COPSE_EINVAL; }
+    u64 *slots = nullptr;
+    STATUS_TRY(dev_alloc(c, (void **)&slots, (size_t)c->N * 8, 0));
+    STATUS_TRY(decrypt_slots_dev(c, k, buf->cts[index], slots, 0));
+    CUDA_TRY(cudaMemcpy(out_slots, slots, (size_t)c->N * 8, cudaMemcpyDeviceToHost));
+    dev_free(slots, 0);
+    CUDA_TRY(cudaStreamSynchronize(0));
+    return COPSE_OK;
+}
+
+// ---------------------------------------------------------------- buffers
+extern "C" size_t copse_ctbuf_count(const copse_ctbuf *b) { return b ? b->cts.size() : 0; }
+
+extern "C" copse_status copse_ctbuf_shape(const copse_ctbuf *b, size_t i, uint32_t *level, uint32_t *ncomp) {
+    if (!b || i >= b->cts.size()) { set_error("bad buffer index"); return COPSE_EINVAL; }
+    if (level) *level = (uint32_t)b->cts[i].level;
+    if (ncomp) *ncomp = (uint32_t)b->cts[i].ncomp;
+    return COPSE_OK;
+}
+
+extern "C" copse_status copse_ctbuf_export(copse_ctx *c, const copse_ctbuf *b, size_t i, uint64_t *out, size_t words) {
+    if (!c || !b || !out || i >= b->cts.size()) { set_error("bad argument"); return COPSE_EINVAL; }
+    const DCt &ct = b->cts[i];
+    if (words < (size_t)ct.ncomp * ct.level * c->N) { set_error("buffer too small"); return COPSE_EINVAL; }
+    return ct_to_coeff_host(c, ct, out, 0);
+}
+
+extern "C" copse_status copse_ctbuf_import(copse_ctx *c, const uint64_t *in, size_t n_ct, uint32_t level,
+                                           copse_ctbuf **out) {
+    if (!c || !in || !out || level < 1 || (int)level > c->L) { set_error("bad argument"); return COPSE_EINVAL; }
+    auto buf = std::make_unique<copse_ctbuf>();
+    buf->ctx = c;
+    for (size_t i = 0; i < n_ct; i++) {
+        DCt ct;
+        STATUS_TRY(ct_from_coeff_host(c, in + i * 2 * level * (size_t)c->N, (int)level, &ct, 0));
+        buf->cts.push_back(ct);
+    }
+    *out = buf.release();
+    return COPSE_OK;
+}
+
+extern "C" void copse_ctbuf_destroy(copse_ctbuf *b) {
+    if (!b) return;
+    cudaStreamSynchronize(0);
+    delete b;
+}
+
+// ---------------------------------------------------------------- ring ops
+static copse_status one(copse_ctx *c, DCt &r, copse_ctbuf **out) {
+    auto buf = std::make_unique<copse_ctbuf>();
+    buf->ctx = c;
+    buf->cts.push_back(r);
+    *out = buf.release();
+    return COPSE_OK;
+}
+
+extern "C" copse_status copse_ct_mul(copse_ctx *c, const copse_evk *evk, const copse_ctbuf *a, size_t ia,
+                                     const copse_ctbuf *b, size_t ib, copse_ctbuf **out, void *stream) {
+    if (!c || !evk || !a || !b || !out || ia >= a->cts.size() || ib >= b->cts.size()) { set_error("bad argument"); return COPSE_EINVAL; }
+    DCt r;
+    STATUS_TRY(op_mul(c, evk, a->cts[ia], b->cts[ib], &r, as_stream(stream)));
+    return one(c, r, out);
+}
+
+extern "C" copse_status copse_ct_rotate(copse_ctx *c, const copse_evk *evk, const copse_ctbuf *a, size_t ia,
+                                        uint32_t k, copse_ctbuf **out, void *stream) {
+    if (!c || !evk || !a || !out || ia >= a->cts.size()) { set_error("bad argument"); return COPSE_EINVAL; }
+    DCt r;
+    STATUS_TRY(op_rotate(c, evk, a->cts[ia], k, &r, as_stream(stream)));
+    return one(c, r, out);
+}
+
+extern "C" copse_status copse_ct_modswitch(copse_ctx *c, const copse_ctbuf *a, size_t ia, copse_ctbuf **out,
+                                           void *stream) {
+    if (!c || !a || !out || ia >= a->cts.size()) { set_error("bad argument"); return COPSE_EINVAL; }
+    DCt r;
+    STATUS_TRY(op_modswitch(c, a->cts[ia], &r, as_stream(stream)));
+    return one(c, r, out);
+}
+
+extern "C" copse_status copse_ct_mul_plain(copse_ctx *c, const copse_ctbuf *a, size_t ia, const uint64_t *mul_slots,
+                                           const uint64_t *add_slots, copse_ctbuf **out, void *stream) {
+    if (!c || !a || !mul_slots || !out || ia >= a->cts.size()) { set_error("bad argument"); return COPSE_EINVAL; }
+    cudaStream_t s = as_stream(stream);
+    const DCt &x = a->cts[ia];
+    const int N = c->N;
+    std::vector<uint32_t> pat((size_t)2 * N);
+    for (int i = 0; i < N; i++) {
+        pat[i] = (uint32_t)(mul_slots[i] % c->t);
+        pat[(size_t)N + i] = add_slots ? (uint32_t)(add_slots[i] % c->t) : 0;
+    }
+    u64 *pts = nullptr;
+    STATUS_TRY(dev_alloc(c, (void **)&pts, (size_t)2 * x.level * N * 8, s));
+    STATUS_TRY(encode_patterns(c, pat, 2, N, N, x.level, pts, s));
+    DPt mp{x.level, pts}, ap{x.level, pts + (size_t)x.level * N};
+    DCt r;
+    copse_status st = op_affine(c, x, mp, add_slots ? &ap : nullptr, &r, s);
+    dev_free(pts, s);
+    if (st) return st;
+    return one(c, r, out);
+}
+
+extern "C" copse_status copse_ntt(copse_ctx *c, uint64_t *data, size_t n_polys, uint32_t n_res, int inverse,
+                                  void *stream) {
+    if (!c || !data || n_res < 1 || (int)n_res > c->L) { set_error("bad argument"); return COPSE_EINVAL; }
+    NttBatch b{data, (size_t)n_res * c->N, (int)n_polys, 0, (int)n_res, (int)n_res, -1};
+    return inverse ? ntt_inverse(c, b, as_stream(stream)) : ntt_forward(c, b, as_stream(stream));
+}

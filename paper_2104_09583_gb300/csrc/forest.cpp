@@ -1,0 +1,251 @@
+// COPSE forest compiler (host).  Section references are to Malik et al.,
+// "Vectorized Secure Evaluation of Decision Forests" (PLDI'21).
+#include "forest.h"
+
+#include <algorithm>
+#include <cstring>
+#include <sstream>
+
+#include "../../include/copse.h"
+
+namespace {
+
+struct Parser {
+    std::vector<std::string> toks;
+    size_t pos = 0;
+    CompiledForest *f;
+    std::string err;
+
+    int node() {
+        if (pos >= toks.size()) { err = "tree line ends early"; return -1; }
+        const std::string &k = toks[pos];
+        ForestNode n;
+        if (k == "l") {
+            if (pos + 1 >= toks.size()) { err = "leaf without a class"; return -1; }
+            char *end = nullptr;
+            long c = strtol(toks[pos + 1].c_str(), &end, 10);
+            if (*end || c < 0) { err = "bad class index '" + toks[pos + 1] + "'"; return -1; }
+            n.leaf = true;
+            n.label = (int)c;
+            pos += 2;
+            f->nodes.push_back(n);
+            return (int)f->nodes.size() - 1;
+        }
+        if (k == "b") {
+            if (pos + 2 >= toks.size()) { err = "branch without feature and threshold"; return -1; }
+            char *e1 = nullptr, *e2 = nullptr;
+            long fe = strtol(toks[pos + 1].c_str(), &e1, 10);
+            long long th = strtoll(toks[pos + 2].c_str(), &e2, 10);
+            if (*e1 || *e2 || fe < 0 || th < 0 || th > 0xFFFFFFFFLL) { err = "bad branch fields"; return -1; }
+            n.leaf = false;
+            n.feature = (int)fe;
+            n.threshold = (uint32_t)th;
+            pos += 3;
+            f->nodes.push_back(n);
+            int me = (int)f->nodes.size() - 1;
+            int l = node();
+            if (l < 0) return -1;
+            int r = node();
+            if (r < 0) return -1;
+            f->nodes[me].left = l;
+            f->nodes[me].right = r;
+            return me;
+        }
+        err = "unexpected token '" + k + "'";
+        return -1;
+    }
+};
+
+uint32_t clog2(uint32_t x) {
+    uint32_t r = 0;
+    while ((1u << r) < x) r++;
+    return r;
+}
+
+}  // namespace
+
+uint32_t CompiledForest::levels_used() const { return 1 + clog2(precision) + 2 + clog2(d); }
+
+void CompiledForest::reshuffle_diagonal(uint32_t i, std::vector<uint8_t> &out) const {
+    // extended reshuffle: row x is R[x mod b]; diagonal entry x is R_ext[x][(x+i) mod q]
+    out.assign(m1(), 0);
+    for (uint32_t x = 0; x < m1(); x++) out[x] = R[(size_t)(x % b) * q + (x + i) % q];
+}
+
+void CompiledForest::level_diagonal(uint32_t k, uint32_t i, uint64_t t, std::vector<uint64_t> &out) const {
+    out.assign(L, 0);
+    const uint8_t *M = &lvl[(size_t)(k - 1) * L * b];
+    const uint8_t *mk = &mask[(size_t)(k - 1) * L];
+    for (uint32_t x = 0; x < L; x++) {
+        if (!M[(size_t)x * b + (x + i) % b]) continue;
+        out[x] = mk[x] ? t - 1 : 1;  // (1 - 2 mask) * entry, mod t
+    }
+}
+
+int compile_forest(const char *text, size_t len, uint32_t precision, uint32_t n_features, uint32_t log_n,
+                   CompiledForest &f, std::string &err) {
+    f = CompiledForest();
+    if (!text || precision < 1 || precision > 32 || log_n < 2 || log_n > 17) {
+        err = "invalid compile arguments";
+        return COPSE_EINVAL;
+    }
+    // Section 5, Input Representation: label names, then one tree per line
+    std::string s(text, len);
+    std::istringstream in(s);
+    std::string line;
+    std::vector<std::string> lines;
+    while (std::getline(in, line)) {
+        bool blank = line.find_first_not_of(" \t\r") == std::string::npos;
+        if (!blank) lines.push_back(line);
+    }
+    if (lines.size() < 2) {
+        err = "forest needs a label line and at least one tree";
+        return COPSE_EPARSE;
+    }
+    {
+        std::istringstream ls(lines[0]);
+        std::string w;
+        while (ls >> w) f.classes.push_back(w);
+    }
+    for (size_t li = 1; li < lines.size(); li++) {
+        Parser p;
+        p.f = &f;
+        std::istringstream ts(lines[li]);
+        std::string w;
+        while (ts >> w) p.toks.push_back(w);
+        int root = p.node();
+        if (root < 0) { err = "tree " + std::to_string(li) + ": " + p.err; return COPSE_EPARSE; }
+        if (p.pos != p.toks.size()) { err = "tree " + std::to_string(li) + ": trailing tokens"; return COPSE_EPARSE; }
+        f.roots.push_back(root);
+    }
+    // Section 4.1.1: preorder indices of branches and of labels, continued across trees
+    struct Anc { int br; bool right; };
+    std::vector<std::vector<Anc>> leaf_anc;
+    std::vector<int> node_br(f.nodes.size(), -1);
+    for (int root : f.roots) {
+        std::vector<std::pair<int, std::vector<Anc>>> stack;
+        stack.push_back({root, {}});
+        while (!stack.empty()) {
+            auto [n, anc] = stack.back();
+            stack.pop_back();
+            const ForestNode &nd = f.nodes[n];
+            if (nd.leaf) {
+                f.leaf_class.push_back(nd.label);
+                leaf_anc.push_back(anc);
+                continue;
+            }
+            int bi = (int)f.br_feature.size();
+            node_br[n] = bi;
+            f.br_feature.push_back(nd.feature);
+            f.br_threshold.push_back(nd.threshold);
+            f.br_level.push_back(0);
+            auto ra = anc, la = anc;
+            la.push_back({bi, false});
+            ra.push_back({bi, true});
+            stack.push_back({nd.right, ra});  // popped after the left subtree
+            stack.push_back({nd.left, la});
+        }
+    }
+    f.b = (uint32_t)f.br_feature.size();
+    f.L = (uint32_t)f.leaf_class.size();
+    if (f.b == 0) { err = "forest has no branches"; return COPSE_EINVAL; }
+    // level: branches on the longest path to a label, itself included (labels: 0)
+    {
+        std::vector<int> lev(f.nodes.size(), 0);
+        for (int n = (int)f.nodes.size() - 1; n >= 0; n--) {  // children follow parents in `nodes`
+            const ForestNode &nd = f.nodes[n];
+            if (!nd.leaf) lev[n] = 1 + std::max(lev[nd.left], lev[nd.right]);
+        }
+        for (size_t n = 0; n < f.nodes.size(); n++)
+            if (node_br[n] >= 0) f.br_level[node_br[n]] = lev[n];
+    }
+    f.d = (uint32_t)*std::max_element(f.br_level.begin(), f.br_level.end());
+    int maxf = *std::max_element(f.br_feature.begin(), f.br_feature.end());
+    f.n_features = n_features ? n_features : (uint32_t)maxf + 1;
+    if ((uint32_t)maxf >= f.n_features) { err = "feature index out of range"; return COPSE_EINVAL; }
+    f.precision = precision;
+    for (uint32_t th : f.br_threshold)
+        if (precision < 32 && th >= (1u << precision)) { err = "threshold needs more bits than the precision"; return COPSE_EINVAL; }
+    for (int c : f.leaf_class)
+        if (c >= (int)f.classes.size()) { err = "class index out of range"; return COPSE_EINVAL; }
+    // multiplicities, K, q = K * n_features
+    std::vector<uint32_t> kappa(f.n_features, 0);
+    for (int fe : f.br_feature) kappa[fe]++;
+    f.K = *std::max_element(kappa.begin(), kappa.end());
+    f.q = f.K * f.n_features;
+    // Section 4.2.1: thresholds grouped by feature in preorder, padded to K with S = 0
+    f.thr_slot.assign(f.q, 0);
+    f.slot_branch.assign(f.q, -1);
+    std::vector<uint32_t> seen(f.n_features, 0);
+    for (uint32_t i = 0; i < f.b; i++) {
+        uint32_t fe = (uint32_t)f.br_feature[i];
+        uint32_t slot = f.K * fe + seen[fe]++;
+        f.thr_slot[slot] = f.br_threshold[i];
+        f.slot_branch[slot] = (int32_t)i;
+    }
+    // Section 4.2.2: R[i][j] = 1 iff padded slot j holds branch i
+    f.R.assign((size_t)f.b * f.q, 0);
+    for (uint32_t j = 0; j < f.q; j++)
+        if (f.slot_branch[j] >= 0) f.R[(size_t)f.slot_branch[j] * f.q + j] = 1;
+    // Section 4.2.3-4.2.4.  Branch for label l at level k: the ancestor at level k;
+    // else the ancestor with the greatest level below k; else (every ancestor above
+    // k) the parent.  A leaf that is a whole tree keeps an empty row and mask 1.
+    f.lvl.assign((size_t)f.d * f.L * f.b, 0);
+    f.mask.assign((size_t)f.d * f.L, 1);
+    for (uint32_t k = 1; k <= f.d; k++) {
+        for (uint32_t l = 0; l < f.L; l++) {
+            const auto &anc = leaf_anc[l];
+            if (anc.empty()) continue;
+            int pick = -1, best_below = -1;
+            for (size_t a = 0; a < anc.size(); a++) {
+                int lv = f.br_level[anc[a].br];
+                if ((uint32_t)lv == k) pick = (int)a;
+                else if ((uint32_t)lv < k && (best_below < 0 || lv > f.br_level[anc[best_below].br])) best_below = (int)a;
+            }
+            if (pick < 0) pick = best_below >= 0 ? best_below : (int)anc.size() - 1;
+            f.lvl[((size_t)(k - 1) * f.L + l) * f.b + anc[pick].br] = 1;
+            f.mask[(size_t)(k - 1) * f.L + l] = anc[pick].right ? 0 : 1;
+        }
+    }
+    // slot layout
+    f.log_n = log_n;
+    uint32_t need = f.pd(), blk = 1;
+    while (blk < need) blk <<= 1;
+    f.block = blk;
+    if ((uint64_t)blk > (1ull << (log_n - 1))) {
+        err = "query block of " + std::to_string(blk) + " slots exceeds a slot row";
+        return COPSE_EFIT;
+    }
+    // nonzero diagonals
+    std::vector<uint8_t> dg;
+    for (uint32_t i = 0; i < f.q; i++) {
+        f.reshuffle_diagonal(i, dg);
+        if (std::any_of(dg.begin(), dg.end(), [](uint8_t v) { return v != 0; })) f.rot_reshuffle.push_back(i);
+    }
+    for (uint32_t i = 0; i < f.b; i++) {
+        bool nz = false;
+        for (uint32_t k = 0; k < f.d && !nz; k++)
+            for (uint32_t x = 0; x < f.L && !nz; x++)
+                nz = f.lvl[((size_t)k * f.L + x) * f.b + (x + i) % f.b] != 0;
+        if (nz) f.rot_level.push_back(i);
+    }
+    return 0;
+}
+
+void classify_plain(const CompiledForest &m, const uint32_t *x, uint8_t *bits) {
+    size_t leaf = 0;
+    for (int root : m.roots) {
+        // reached leaf of this tree
+        int n = root;
+        while (!m.nodes[n].leaf) n = x[m.nodes[n].feature] < m.nodes[n].threshold ? m.nodes[n].right : m.nodes[n].left;
+        // number the tree's leaves in preorder
+        std::vector<int> st{root};
+        while (!st.empty()) {
+            int c = st.back();
+            st.pop_back();
+            if (m.nodes[c].leaf) { bits[leaf++] = c == n ? 1 : 0; continue; }
+            st.push_back(m.nodes[c].right);
+            st.push_back(m.nodes[c].left);
+        }
+    }
+}

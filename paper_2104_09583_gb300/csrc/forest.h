@@ -1,0 +1,58 @@
+// Host-side COPSE forest compiler: parses the forest text and builds the
+// vectorised structures of Section 4.2 of the paper (padded threshold vector,
+// reshuffling matrix, level matrices and masks) plus the slot layout the
+// device circuit uses.  Pure C++; no CUDA.
+#pragma once
+
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+struct ForestNode {
+    bool leaf = true;
+    int label = -1;       // class index (leaf)
+    int feature = -1;     // branch
+    uint32_t threshold = 0;
+    int left = -1, right = -1;  // node indices
+};
+
+struct CompiledForest {
+    // forest
+    std::vector<std::string> classes;
+    std::vector<ForestNode> nodes;
+    std::vector<int> roots;
+    // Section 4.1.1
+    uint32_t n_features = 0, precision = 0, K = 0, q = 0, b = 0, L = 0, d = 0;
+    std::vector<int> br_feature, br_level;
+    std::vector<uint32_t> br_threshold;
+    std::vector<int> leaf_class;
+    // Section 4.2.1: padded threshold vector; slot_branch = -1 marks the sentinel S = 0
+    std::vector<uint32_t> thr_slot;
+    std::vector<int32_t> slot_branch;
+    // Section 4.2.2-4.2.4, row-major
+    std::vector<uint8_t> R;     // b x q
+    std::vector<uint8_t> lvl;   // d x L x b
+    std::vector<uint8_t> mask;  // d x L
+    // slot layout: query block size (power of two >= L + b - 1 + q - 1)
+    uint32_t block = 0;
+    uint32_t log_n = 0;
+    // nonzero diagonal indices
+    std::vector<uint32_t> rot_reshuffle;  // ascending, may include 0
+    std::vector<uint32_t> rot_level;      // union over levels, ascending, may include 0
+
+    uint32_t m1() const { return L + b - 1; }       // rows of the extended reshuffle
+    uint32_t pd() const { return m1() + q - 1; }    // slots carrying the periodic decisions
+    uint32_t levels_used() const;
+    // diagonal i of the extended reshuffle matrix, as a block-local slot vector
+    void reshuffle_diagonal(uint32_t i, std::vector<uint8_t> &out) const;
+    // signed diagonal i of level k (1-based), values in {0, 1, t-1}; block-local
+    void level_diagonal(uint32_t k, uint32_t i, uint64_t t, std::vector<uint64_t> &out) const;
+};
+
+// 0 on success; otherwise a COPSE_E* code and a message in `err`.
+int compile_forest(const char *text, size_t len, uint32_t precision, uint32_t n_features, uint32_t log_n,
+                   CompiledForest &out, std::string &err);
+
+// one bit per leaf for query x (x has n_features entries)
+void classify_plain(const CompiledForest &m, const uint32_t *x, uint8_t *bits);

@@ -1,0 +1,245 @@
+// Internal declarations of the GB300 COPSE library: device modular arithmetic,
+// the context's device tables, device ciphertexts and the kernel launchers.
+//
+// Residues are 64-bit words modulo primes q < 2^60.  Products with a constant
+// operand use Shoup's precomputed quotient (V. Shoup, NTL; D. Harvey, "Faster
+// arithmetic for number-theoretic transforms", 2014); products of two data
+// words use Barrett reduction of the 128-bit product (Handbook of Applied
+// Cryptography, Alg. 14.42).  Every kernel leaves its outputs fully reduced to
+// [0, q), so device data is bit-comparable with any other exact implementation.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/copse.h"
+
+typedef uint64_t u64;
+typedef int64_t i64;
+
+#define COPSE_MAX_PRIMES 64
+#define COPSE_T 65537ULL
+
+// ---------------------------------------------------------------- errors
+void set_error(const std::string &msg);
+#define CUDA_TRY(expr)                                                                           \
+    do {                                                                                         \
+        cudaError_t e__ = (expr);                                                                \
+        if (e__ != cudaSuccess) {                                                                \
+            set_error(std::string(#expr) + ": " + cudaGetErrorString(e__));                      \
+            return COPSE_ECUDA;                                                                  \
+        }                                                                                        \
+    } while (0)
+#define STATUS_TRY(expr)                                                                         \
+    do {                                                                                         \
+        copse_status s__ = (expr);                                                               \
+        if (s__ != COPSE_OK) return s__;                                                         \
+    } while (0)
+// after a kernel launch
+#define LAUNCH_CHECK() CUDA_TRY(cudaGetLastError())
+
+// ---------------------------------------------------------------- per-prime constants
+struct PrimeDev {
+    u64 q;
+    u64 mu;       // floor(2^(2*bits) / q): Barrett constant
+    u64 ninv;     // N^-1 mod q
+    u64 ninv_sh;  // its Shoup quotient floor(ninv * 2^64 / q)
+    u64 t_mod;    // t mod q
+    u64 t_mod_sh;
+    u64 r64;      // 2^64 mod q
+    u64 r64_sh;
+    uint32_t bits;  // bit length of q
+    uint32_t pad;
+};
+
+// value and Shoup quotient of a constant multiplier
+struct Shoup {
+    u64 w, wp;
+};
+
+// ---------------------------------------------------------------- device arithmetic
+__device__ __forceinline__ u64 add_mod(u64 a, u64 b, u64 q) {
+    u64 s = a + b;
+    return s >= q ? s - q : s;
+}
+__device__ __forceinline__ u64 sub_mod(u64 a, u64 b, u64 q) { return a >= b ? a - b : a + (q - b); }
+// a * w mod q in [0, 2q) for any a < 2^64 (w < q, wp = floor(w 2^64 / q))
+__device__ __forceinline__ u64 mul_shoup_lazy(u64 a, u64 w, u64 wp, u64 q) {
+    u64 h = __umul64hi(a, wp);
+    return a * w - h * q;
+}
+__device__ __forceinline__ u64 mul_shoup(u64 a, u64 w, u64 wp, u64 q) {
+    u64 r = mul_shoup_lazy(a, w, wp, q);
+    return r >= q ? r - q : r;
+}
+__device__ __forceinline__ u64 mul_shoup(u64 a, Shoup c, u64 q) { return mul_shoup(a, c.w, c.wp, q); }
+// (hi*2^64 + lo) mod q for hi*2^64 + lo < 2^(2*bits)
+__device__ __forceinline__ u64 barrett_wide(u64 hi, u64 lo, const PrimeDev &p) {
+    const int s = (int)p.bits;
+    u64 x1 = (hi << (65 - s)) | (lo >> (s - 1));
+    u64 plo = x1 * p.mu, phi = __umul64hi(x1, p.mu);
+    u64 qe = (phi << (63 - s)) | (plo >> (s + 1));
+    u64 r = lo - qe * p.q;
+    if (r >= p.q) r -= p.q;
+    if (r >= p.q) r -= p.q;
+    return r;
+}
+// a * b mod q for a, b < q
+__device__ __forceinline__ u64 mul_mod(u64 a, u64 b, const PrimeDev &p) {
+    return barrett_wide(__umul64hi(a, b), a * b, p);
+}
+// a signed small integer (|v| < q) as a residue
+__device__ __forceinline__ u64 from_signed(i64 v, u64 q) { return v < 0 ? q - (u64)(-v) : (u64)v; }
+__device__ __forceinline__ uint32_t bit_reverse(uint32_t x, int logN) { return __brev(x) >> (32 - logN); }
+
+// SplitMix64 (Steele, Lea, Flood, OOPSLA 2014) in counter form: output number
+// (stream * 2^40 + idx + 1) of the sequence whose state starts at `seed`.
+__device__ __forceinline__ u64 rng_word(u64 seed, u64 stream, u64 idx) {
+    u64 z = seed + 0x9E3779B97F4A7C15ULL * ((stream << 40) + idx + 1ULL);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+// ---------------------------------------------------------------- context
+// Base-conversion constants.  Primes are addressed by a global index g:
+// 0..L-1 ciphertext primes, L..L+alpha-1 special primes, L+alpha = t.
+// At level ell the extended basis lists q_0..q_{ell-1} then p_0..p_{alpha-1};
+// ext_prime(r) maps its position r to g.
+struct KsTables {
+    // ModUp at level ell, source prime i (< ell), digit of i = i / alpha:
+    //   modup_inv[ell][i]      = (prod of the other primes of the digit below ell)^-1 mod q_i
+    //   modup_hat[ell][i][g]   = (prod of the other primes of the digit below ell) mod prime g
+    //   modup_qhat[ell][i][g]  = q_i * modup_hat mod prime g  (correction for a negative centred digit)
+    Shoup *modup_inv;   // [(L+1) * L]
+    Shoup *modup_hat;   // [(L+1) * L * NP]
+    u64 *modup_qhat;    // [(L+1) * L * NP]
+    // ModDown: md_inv[k] = t^-1 * Phat_k^-1 mod p_k; md_hat[k][i] = Phat_k mod q_i;
+    // md_P[i] = P mod q_i; md_Pinv[i] = P^-1 mod q_i
+    Shoup *md_inv;      // [alpha]
+    Shoup *md_hat;      // [alpha * L]
+    u64 *md_P;          // [L]
+    Shoup *md_Pinv;     // [L]
+    // modulus switch dropping q_{ell-1}: ms_tinv[ell] = t^-1 mod q_{ell-1};
+    // ms_qinv[ell][i] = q_{ell-1}^-1 mod q_i
+    Shoup *ms_tinv;     // [L+1]
+    Shoup *ms_qinv;     // [(L+1) * L]
+    // gadget factor of key-switching keys: P mod q_i (i < L)
+};
+
+struct copse_ctx {
+    int device = 0;
+    int logN = 0, N = 0;
+    u64 t = COPSE_T;
+    int L = 0, alpha = 0, ndig = 0, dnum = 0, bits = 0;
+    int NP = 0;                       // L + alpha + 1 table entries (t last)
+    std::vector<u64> primes;          // L + alpha primes, then t
+    std::vector<PrimeDev> hprime;     // host copy of the prime constants
+    PrimeDev *d_prime = nullptr;      // [NP]
+    u64 *d_psi = nullptr;             // [NP][N] psi^brev(k)
+    u64 *d_psi_sh = nullptr;
+    u64 *d_ipsi = nullptr;            // [NP][N] psi^-brev(k)
+    u64 *d_ipsi_sh = nullptr;
+    uint32_t *d_slot_index = nullptr; // [N] NTT(mod t) position of slot s
+    KsTables ks{};
+    std::vector<void *> owned;        // device allocations freed with the context
+    cudaMemPool_t pool = nullptr;
+
+    int ext_prime(int ell, int r) const { return r < ell ? r : L + (r - ell); }
+    int t_index() const { return L + alpha; }
+};
+
+// device memory from the context's stream-ordered pool
+copse_status dev_alloc(copse_ctx *ctx, void **p, size_t bytes, cudaStream_t s);
+void dev_free(void *p, cudaStream_t s);
+
+// ---------------------------------------------------------------- ciphertexts
+// A ciphertext at level ell with ncomp components, each [ell][N] residues
+// (residue r modulo q_r), stored in the bit-reversed NTT (evaluation) domain.
+struct DCt {
+    int level = 0;
+    int ncomp = 2;
+    u64 *data = nullptr;
+};
+// a plaintext polynomial at `level` residues, NTT domain, [level][N]
+struct DPt {
+    int level = 0;
+    u64 *data = nullptr;
+};
+
+// ---------------------------------------------------------------- NTT
+// Batched NTTs.  Poly p's residue r (r in [r0, r0 + nr)) lives at
+// data + p * stride + r * N and is taken modulo prime ext_prime(ell, r), or
+// modulo global prime `fixed` when fixed >= 0.
+struct NttBatch {
+    u64 *data;
+    size_t stride;   // words between consecutive polys
+    int npoly;
+    int r0, nr;
+    int ell;
+    int fixed;
+};
+copse_status ntt_forward(copse_ctx *ctx, const NttBatch &b, cudaStream_t s);
+copse_status ntt_inverse(copse_ctx *ctx, const NttBatch &b, cudaStream_t s);
+
+// ---------------------------------------------------------------- keys
+struct copse_keys {
+    copse_ctx *ctx = nullptr;
+    std::vector<i64> s_host;  // ternary secret coefficients
+    u64 *s_hat = nullptr;     // [L+alpha][N] NTT domain, every global prime
+    u64 *pk = nullptr;        // [2][L][N] NTT domain
+};
+struct copse_evk {
+    copse_ctx *ctx = nullptr;
+    u64 *rlk = nullptr;                 // [ndig][2][L+alpha][N] NTT domain
+    std::vector<u64> galois;            // Galois elements with a key
+    std::vector<u64 *> gk;              // matching keys, same layout as rlk
+    const u64 *find(u64 g) const {
+        for (size_t i = 0; i < galois.size(); i++)
+            if (galois[i] == g) return gk[i];
+        return nullptr;
+    }
+};
+struct copse_ctbuf {
+    copse_ctx *ctx = nullptr;
+    std::vector<DCt> cts;
+    ~copse_ctbuf();
+};
+
+// ---------------------------------------------------------------- BGV operations (ring.cu)
+// All allocate outputs from the pool on stream s and enqueue work on s.
+size_t ksk_words(const copse_ctx *c);
+copse_status ct_alloc(copse_ctx *c, DCt *ct, int level, int ncomp, cudaStream_t s);
+void ct_free(DCt *ct, cudaStream_t s);
+copse_status ct_copy(copse_ctx *c, const DCt &in, DCt *out, cudaStream_t s);
+copse_status op_modswitch(copse_ctx *c, const DCt &in, DCt *out, cudaStream_t s);
+copse_status op_to_level(copse_ctx *c, DCt *ct, int level, cudaStream_t s);  // in place (replaces)
+copse_status op_add(copse_ctx *c, const DCt &a, const DCt &b, DCt *out, bool negate_b, cudaStream_t s);
+copse_status op_mul(copse_ctx *c, const copse_evk *evk, const DCt &a, const DCt &b, DCt *out, cudaStream_t s);
+copse_status op_affine(copse_ctx *c, const DCt &x, const DPt &mul, const DPt *add, DCt *out, cudaStream_t s);
+copse_status op_rotate(copse_ctx *c, const copse_evk *evk, const DCt &a, uint32_t k, DCt *out, cudaStream_t s);
+// Hoisted diagonal products: for each accumulator a, out[a] = modswitch(
+//   sum_k pt[a][k] * rot(v, rots[k]) + add[a]); pt[a][k] may be null (zero diagonal),
+// rots[k] = 0 means v itself.  pt pointers are NTT-domain [v.level][N].
+copse_status op_matmul(copse_ctx *c, const copse_evk *evk, const DCt &v, const std::vector<uint32_t> &rots,
+                       const std::vector<std::vector<const u64 *>> &pt, const std::vector<const u64 *> &add,
+                       std::vector<DCt> &out, cudaStream_t s);
+// encode host slot patterns: n patterns of `len` values mod t, repeated every
+// `period` slots (period divides N; len <= period), into NTT-domain plaintexts at `level`
+copse_status encode_patterns(copse_ctx *c, const std::vector<uint32_t> &patterns, int n, int len, int period,
+                             int level, u64 *out, cudaStream_t s);
+copse_status keygen_dev(copse_ctx *c, u64 seed, const std::vector<u64> &galois, copse_keys **keys, copse_evk **evk);
+// p planes for n queries: feats [n][nf] (device), layout of the model given by
+// K, q, pd, block
+copse_status encrypt_planes(copse_ctx *c, const copse_keys *k, const uint32_t *d_feats, int nq, int nf, int K,
+                            int q, int pd, int block, int p, u64 seed, std::vector<DCt> &out, cudaStream_t s);
+// decrypt to N slot values (device output, NTT(mod t) order remapped to slot order)
+copse_status decrypt_slots_dev(copse_ctx *c, const copse_keys *k, const DCt &ct, u64 *d_slots, cudaStream_t s);
+copse_status extract_bits(copse_ctx *c, const u64 *d_slots, int nq, int block, int L, uint8_t *d_bits,
+                          cudaStream_t s);
+// coefficient-form export/import of one ciphertext (device scratch, host buffer)
+copse_status ct_to_coeff_host(copse_ctx *c, const DCt &ct, u64 *host, cudaStream_t s);
+copse_status ct_from_coeff_host(copse_ctx *c, const u64 *host, int level, DCt *out, cudaStream_t s);

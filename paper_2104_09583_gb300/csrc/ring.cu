@@ -1,0 +1,943 @@
+// BGV ring operations on the device: sampling, key generation, encryption,
+// decryption, addition, plaintext and ciphertext products, hybrid key
+// switching (relinearisation and rotations, with one shared ModUp for all
+// rotations of one ciphertext), modulus switching, and slot encoding.
+//
+// Ciphertexts live in the bit-reversed NTT domain.  Key switching of a
+// polynomial x at level ell (primes q_0..q_{ell-1}, special primes
+// p_0..p_{alpha-1}, digits of alpha consecutive primes):
+//   ModUp:   y_j = sum_{i in digit j} [x_i * Qhat_i^-1]_{q_i} (centred) * Qhat_i
+//   inner:   (u0, u1) = sum_j y_j * ksk_j over q_0..q_{ell-1}, p_0..p_{alpha-1}
+//   ModDown: W = sum_k [u_k * t^-1 * Phat_k^-1]_{p_k} (centred) * Phat_k,
+//            out_i = (u_i - t*W) * P^-1 mod q_i
+// A rotation by Galois element g applies tau_g: X -> X^g to the ModUp output;
+// because the digits are centred, tau_g commutes with ModUp, so one ModUp
+// serves every rotation of the same ciphertext and the result equals
+// rotating first and key switching after.
+#include <algorithm>
+
+#include "internal.cuh"
+
+namespace {
+
+constexpr int TPB = 256;
+constexpr int MAX_ALPHA = 40;
+constexpr int MAX_ACC = 8;
+constexpr int CHUNK_ROT = 64;
+
+inline unsigned nblk(size_t n) { return (unsigned)((n + TPB - 1) / TPB); }
+
+// Position n of the bit-reversed NTT holds the evaluation at psi^(2 brev(n) + 1);
+// tau_g(a) there equals a at psi^((2 brev(n) + 1) g).
+__device__ __forceinline__ uint32_t galois_src(uint32_t n, u64 g, int logN) {
+    uint32_t e = 2u * bit_reverse(n, logN) + 1u;
+    uint32_t e2 = (uint32_t)(((u64)e * g) & ((2ull << logN) - 1));
+    return bit_reverse((e2 - 1u) >> 1, logN);
+}
+
+__global__ void k_add(const u64 *a, const u64 *b, u64 *out, int ncomp, int level, int logN, int neg,
+                      const PrimeDev *pr) {
+    size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    size_t n = (size_t)ncomp * level << logN;
+    if (e >= n) return;
+    int r = (int)((e >> logN) % level);
+    u64 q = pr[r].q;
+    out[e] = neg ? sub_mod(a[e], b[e], q) : add_mod(a[e], b[e], q);
+}
+
+// c0 += p (p: [level][N]) on component 0 only
+__global__ void k_add_plain(u64 *ct, const u64 *p, int level, int logN, const PrimeDev *pr) {
+    size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= ((size_t)level << logN)) return;
+    ct[e] = add_mod(ct[e], p[e], pr[e >> logN].q);
+}
+
+__global__ void k_tensor(const u64 *a, const u64 *b, u64 *out, int level, int logN, const PrimeDev *pr) {
+    size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    size_t n = (size_t)level << logN;
+    if (e >= n) return;
+    const PrimeDev P = pr[e >> logN];
+    u64 a0 = a[e], a1 = a[n + e], b0 = b[e], b1 = b[n + e];
+    out[e] = mul_mod(a0, b0, P);
+    out[n + e] = add_mod(mul_mod(a0, b1, P), mul_mod(a1, b0, P), P.q);
+    out[2 * n + e] = mul_mod(a1, b1, P);
+}
+
+__global__ void k_affine(const u64 *x, const u64 *m, const u64 *addp, u64 *out, int level, int logN,
+                         const PrimeDev *pr) {
+    size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    size_t n = (size_t)level << logN;
+    if (e >= 2 * n) return;
+    size_t k = e < n ? e : e - n;
+    const PrimeDev P = pr[k >> logN];
+    u64 v = mul_mod(x[e], m[k], P);
+    if (addp && e < n) v = add_mod(v, addp[k], P.q);
+    out[e] = v;
+}
+
+__global__ void k_mul_elem(const u64 *a, const u64 *b, u64 *out, int nres, int logN, const PrimeDev *pr) {
+    size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= ((size_t)nres << logN)) return;
+    out[e] = mul_mod(a[e], b[e], pr[e >> logN]);
+}
+
+__global__ void k_permute(const u64 *src, u64 *dst, int nres, u64 g, int logN) {
+    size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= ((size_t)nres << logN)) return;
+    size_t r = e >> logN;
+    uint32_t n = (uint32_t)(e & ((1u << logN) - 1));
+    dst[e] = src[(r << logN) + galois_src(n, g, logN)];
+}
+
+// ModUp of every digit: x [ell][N] coefficient form -> y [nd][ell+alpha][N] coefficient form
+__global__ void k_modup(const u64 *x, u64 *y, int ell, int alpha, int L, int NP, int logN, const PrimeDev *pr,
+                        KsTables T) {
+    const int N = 1 << logN;
+    const int nd = (ell + alpha - 1) / alpha;
+    size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= ((size_t)nd << logN)) return;
+    const int j = (int)(e >> logN), n = (int)(e & (N - 1));
+    const int lo = j * alpha, hi = min((j + 1) * alpha, ell);
+    const int nx = ell + alpha;
+    u64 yv[MAX_ALPHA];
+    bool neg[MAX_ALPHA];
+    for (int i = lo; i < hi; i++) {
+        const u64 qi = pr[i].q;
+        u64 v = mul_shoup(x[((size_t)i << logN) + n], T.modup_inv[(size_t)ell * L + i], qi);
+        yv[i - lo] = v;
+        neg[i - lo] = v > (qi - 1) / 2;
+    }
+    u64 *yj = y + (size_t)j * nx * N;
+    for (int r = 0; r < nx; r++) {
+        const int g = r < ell ? r : L + (r - ell);
+        u64 out;
+        if (g >= lo && g < hi) {
+            out = x[((size_t)g << logN) + n];
+        } else {
+            const u64 qg = pr[g].q;
+            out = 0;
+            for (int i = lo; i < hi; i++) {
+                const size_t ti = ((size_t)ell * L + i) * NP + g;
+                u64 v = mul_shoup(yv[i - lo], T.modup_hat[ti], qg);
+                if (neg[i - lo]) v = sub_mod(v, T.modup_qhat[ti], qg);
+                out = add_mod(out, v, qg);
+            }
+        }
+        yj[((size_t)r << logN) + n] = out;
+    }
+}
+
+struct InnerJob {
+    const u64 *ksk;  // [ndig][2][L+alpha][N]
+    u64 *out;        // [2][ell+alpha][N]
+    u64 g;           // Galois element applied to the ModUp output, 1 = none
+};
+
+// (u0, u1)[r][n] = sum_j yhat[j][r][tau_g n] * ksk[j][c][ext_prime(r)][n]
+__global__ void k_ks_inner(const u64 *yhat, const InnerJob *jobs, int ell, int alpha, int L, int logN,
+                           const PrimeDev *pr) {
+    const int N = 1 << logN;
+    const int nx = ell + alpha, nd = (ell + alpha - 1) / alpha;
+    const int NB = L + alpha;
+    size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= ((size_t)nx << logN)) return;
+    const InnerJob J = jobs[blockIdx.y];
+    const int r = (int)(e >> logN);
+    const uint32_t n = (uint32_t)(e & (N - 1));
+    const int g = r < ell ? r : L + (r - ell);
+    const PrimeDev P = pr[g];
+    const uint32_t src = J.g == 1 ? n : galois_src(n, J.g, logN);
+    u64 acc0 = 0, acc1 = 0;
+    for (int j = 0; j < nd; j++) {
+        const u64 y = yhat[(((size_t)j * nx + r) << logN) + src];
+        const u64 *k0 = J.ksk + (((size_t)(2 * j) * NB + g) << logN);
+        const u64 *k1 = J.ksk + (((size_t)(2 * j + 1) * NB + g) << logN);
+        acc0 = add_mod(acc0, mul_mod(y, k0[n], P), P.q);
+        acc1 = add_mod(acc1, mul_mod(y, k1[n], P), P.q);
+    }
+    J.out[e] = acc0;
+    J.out[((size_t)nx << logN) + e] = acc1;
+}
+
+// ModDown conversion: u polys (stride ustride) whose residues ell..ell+alpha-1 are in
+// coefficient form -> W polys [ell][N] (stride wstride) in coefficient form
+__global__ void k_moddown_conv(const u64 *u, size_t ustride, u64 *W, size_t wstride, int npoly, int ell,
+                               int alpha, int L, int logN, const PrimeDev *pr, KsTables T) {
+    const int N = 1 << logN;
+    size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= ((size_t)npoly << logN)) return;
+    const int p = (int)(e >> logN), n = (int)(e & (N - 1));
+    const u64 *up = u + (size_t)p * ustride;
+    u64 yv[MAX_ALPHA];
+    bool neg[MAX_ALPHA];
+    for (int k = 0; k < alpha; k++) {
+        const u64 pk = pr[L + k].q;
+        u64 v = mul_shoup(up[((size_t)(ell + k) << logN) + n], T.md_inv[k], pk);
+        yv[k] = v;
+        neg[k] = v > (pk - 1) / 2;
+    }
+    u64 *wp = W + (size_t)p * wstride;
+    for (int i = 0; i < ell; i++) {
+        const u64 qi = pr[i].q;
+        u64 acc = 0;
+        for (int k = 0; k < alpha; k++) {
+            u64 v = mul_shoup(yv[k], T.md_hat[(size_t)k * L + i], qi);
+            if (neg[k]) v = sub_mod(v, T.md_P[i], qi);
+            acc = add_mod(acc, v, qi);
+        }
+        wp[((size_t)i << logN) + n] = acc;
+    }
+}
+
+// out_c = add_c (+ tau_g on add_0) + (u_c - t W_c) P^-1, c = 0, 1; all NTT domain
+__global__ void k_ks_finish(const u64 *u, const u64 *W, const u64 *add0, const u64 *add1, u64 g, u64 *out,
+                            int ell, int alpha, int logN, const PrimeDev *pr, KsTables T) {
+    const int N = 1 << logN;
+    size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    size_t n_el = (size_t)ell << logN;
+    if (e >= 2 * n_el) return;
+    const int c = e >= n_el;
+    size_t k = e - c * n_el;
+    const int i = (int)(k >> logN);
+    const uint32_t n = (uint32_t)(k & (N - 1));
+    const PrimeDev P = pr[i];
+    const u64 uv = u[(size_t)c * ((size_t)(ell + alpha) << logN) + k];
+    const u64 w = W[e];
+    u64 v = mul_shoup(sub_mod(uv, mul_shoup(w, P.t_mod, P.t_mod_sh, P.q), P.q), T.md_Pinv[i], P.q);
+    const u64 *ad = c ? add1 : add0;
+    if (ad) {
+        const uint32_t src = (c == 0 && g != 1) ? galois_src(n, g, logN) : n;
+        v = add_mod(v, ad[((size_t)i << logN) + src], P.q);
+    }
+    out[e] = v;
+}
+
+// Multiply-accumulate of a chunk of rotations into up to MAX_ACC accumulators:
+//   rot_k = (k has no key switch) ? v : (tau_g v0, 0) + (U_k - t W_k) P^-1
+//   acc_a += pt[a][k] * rot_k
+__global__ void k_matmul_mac(const u64 *U, const u64 *W, const u64 *v, int nrot, const u64 *gl,
+                             const int *has_ks, const u64 *const *pt_tab, u64 *const *acc, int nacc, int ell,
+                             int alpha, int logN, const PrimeDev *pr, KsTables T) {
+    const int N = 1 << logN;
+    size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t n_el = (size_t)ell << logN;
+    if (e >= 2 * n_el) return;
+    const int c = e >= n_el;
+    const size_t k = e - c * n_el;
+    const int i = (int)(k >> logN);
+    const uint32_t n = (uint32_t)(k & (N - 1));
+    const PrimeDev P = pr[i];
+    const Shoup Pinv = T.md_Pinv[i];
+    u64 a[MAX_ACC];
+    for (int x = 0; x < nacc; x++) a[x] = acc[x][e];
+    const size_t ustride = 2 * ((size_t)(ell + alpha) << logN), wstride = 2 * n_el;
+    int ks = 0;
+    for (int r = 0; r < nrot; r++) {
+        u64 rv;
+        if (!has_ks[r]) {
+            rv = v[e];
+        } else {
+            const u64 uv = U[(size_t)ks * ustride + (size_t)c * ((size_t)(ell + alpha) << logN) + k];
+            const u64 wv = W[(size_t)ks * wstride + e];
+            rv = mul_shoup(sub_mod(uv, mul_shoup(wv, P.t_mod, P.t_mod_sh, P.q), P.q), Pinv, P.q);
+            if (c == 0) rv = add_mod(rv, v[((size_t)i << logN) + galois_src(n, gl[r], logN)], P.q);
+            ks++;
+        }
+        for (int x = 0; x < nacc; x++) {
+            const u64 *p = pt_tab[(size_t)x * nrot + r];
+            if (p) a[x] = add_mod(a[x], mul_mod(p[k], rv, P), P.q);
+        }
+    }
+    for (int x = 0; x < nacc; x++) acc[x][e] = a[x];
+}
+
+// modulus switch, conversion step: last [ncomp][N] coefficients of q_{ell-1} ->
+// W [ncomp][ell-1][N] = [last * t^-1]_{q_{ell-1}} (centred) mod q_i
+__global__ void k_ms_conv(const u64 *last, u64 *W, int ncomp, int ell, int L, int logN, const PrimeDev *pr,
+                          KsTables T) {
+    const int N = 1 << logN;
+    size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= ((size_t)ncomp << logN)) return;
+    const int c = (int)(e >> logN), n = (int)(e & (N - 1));
+    const u64 ql = pr[ell - 1].q;
+    const u64 w = mul_shoup(last[e], T.ms_tinv[ell], ql);
+    const bool neg = w > (ql - 1) / 2;
+    for (int i = 0; i < ell - 1; i++) {
+        // |centred w| < q_{ell-1}/2 < q_i: the chain is in decreasing order
+        const u64 qi = pr[i].q;
+        W[(((size_t)c * (ell - 1) + i) << logN) + n] = neg ? qi - (ql - w) : w;
+    }
+}
+
+__global__ void k_ms_finish(const u64 *ct, const u64 *W, u64 *out, int ncomp, int ell, int L, int logN,
+                            const PrimeDev *pr, KsTables T) {
+    size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t per = (size_t)(ell - 1) << logN;
+    if (e >= (size_t)ncomp * per) return;
+    const int c = (int)(e / per);
+    const size_t k = e - c * per;
+    const int i = (int)(k >> logN);
+    const PrimeDev P = pr[i];
+    const u64 x = ct[(size_t)c * ((size_t)ell << logN) + k];
+    const u64 d = mul_shoup(W[e], P.t_mod, P.t_mod_sh, P.q);
+    out[e] = mul_shoup(sub_mod(x, d, P.q), T.ms_qinv[(size_t)ell * L + i], P.q);
+}
+
+// uniform residues: out[r][j] for global prime g0 + r, (hi 2^64 + lo) mod q with
+// hi, lo the words 2 (g N + j) and 2 (g N + j) + 1 of the stream
+__global__ void k_sample_uniform(u64 *out, int nres, int g0, u64 seed, u64 stream, int logN, const PrimeDev *pr) {
+    size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= ((size_t)nres << logN)) return;
+    const int g = g0 + (int)(e >> logN);
+    const u64 j = e & ((1ull << logN) - 1);
+    const PrimeDev P = pr[g];
+    const u64 idx = 2 * (((u64)g << logN) + j);
+    const u64 hi = rng_word(seed, stream, idx), lo = rng_word(seed, stream, idx + 1);
+    const u64 hm = barrett_wide(0, hi, P), lm = barrett_wide(0, lo, P);
+    out[e] = add_mod(mul_shoup(hm, P.r64, P.r64_sh, P.q), lm, P.q);
+}
+
+__device__ __forceinline__ i64 sample_small(u64 seed, u64 stream, u64 j, int kind) {
+    const u64 w = rng_word(seed, stream, j);
+    if (kind == 0) return (i64)(w % 3) - 1;  // ternary
+    return (i64)__popcll(w & 0x1FFFFFull) - (i64)__popcll((w >> 21) & 0x1FFFFFull);  // centred binomial, eta 21
+}
+
+// small samples scaled by `scale`, as residues of global primes 0..nres-1; raw copy optional
+__global__ void k_sample_small(u64 *out, int nres, u64 seed, u64 stream, int kind, i64 scale, i64 *raw, int logN,
+                               const PrimeDev *pr) {
+    size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= ((size_t)nres << logN)) return;
+    const int r = (int)(e >> logN);
+    const u64 j = e & ((1ull << logN) - 1);
+    const i64 v = sample_small(seed, stream, j, kind) * scale;
+    out[e] = from_signed(v, pr[r].q);
+    if (raw && r == 0) raw[j] = v;
+}
+
+// pk0 = t e - a s, pk1 = a  (residues 0..L-1)
+__global__ void k_pk(const u64 *a, const u64 *s, const u64 *te, u64 *pk, int L, int logN, const PrimeDev *pr) {
+    size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t n = (size_t)L << logN;
+    if (e >= n) return;
+    const PrimeDev P = pr[e >> logN];
+    pk[e] = sub_mod(te[e], mul_mod(a[e], s[e], P), P.q);
+    pk[n + e] = a[e];
+}
+
+// ksk_j = (t e - a s + [r in digit] (P mod q_r) s', a) over all L+alpha primes
+__global__ void k_ksk(const u64 *a, const u64 *s, const u64 *te, const u64 *sfrom, u64 *k, int lo, int hi, int L,
+                      int alpha, int logN, const PrimeDev *pr, KsTables T) {
+    size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t n = (size_t)(L + alpha) << logN;
+    if (e >= n) return;
+    const int r = (int)(e >> logN);
+    const PrimeDev P = pr[r];
+    u64 v = sub_mod(te[e], mul_mod(a[e], s[e], P), P.q);
+    if (r >= lo && r < hi) v = add_mod(v, mul_mod(T.md_P[r], sfrom[e], P), P.q);
+    k[e] = v;
+    k[n + e] = a[e];
+}
+
+// slot patterns -> NTT(mod t) order: out[i][slot_index[s]] = pattern_i[s mod period] (0 past len)
+__global__ void k_scatter_pattern(const uint32_t *pat, int npat, int len, int period, int logN,
+                                  const uint32_t *slot_index, u64 *out) {
+    size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= ((size_t)npat << logN)) return;
+    const int i = (int)(e >> logN);
+    const uint32_t s = (uint32_t)(e & ((1u << logN) - 1));
+    const int x = (int)(s % (uint32_t)period);
+    out[((size_t)i << logN) + slot_index[s]] = x < len ? pat[(size_t)i * len + x] : 0;
+}
+
+// coefficients mod t -> centred -> residues mod q_0..q_{level-1}: out [n][level][N]
+__global__ void k_lift(const u64 *in, u64 *out, int npoly, int level, int logN, u64 t, const PrimeDev *pr) {
+    size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t per = (size_t)level << logN;
+    if (e >= (size_t)npoly * per) return;
+    const size_t i = e / per, k = e - i * per;
+    const int r = (int)(k >> logN);
+    const u64 c = in[(i << logN) + (k & ((1ull << logN) - 1))];
+    const i64 m = c > (t - 1) / 2 ? (i64)c - (i64)t : (i64)c;
+    out[e] = from_signed(m, pr[r].q);
+}
+
+// bit-planes of the replicated, block-periodic feature vectors, NTT(mod t) order
+__global__ void k_feature_planes(const uint32_t *feats, int nq, int nf, int K, int q, int pd, int block, int p,
+                                 int logN, const uint32_t *slot_index, u64 *out) {
+    size_t s = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= (1ull << logN)) return;
+    const int j = (int)(s / block), x = (int)(s % block);
+    uint32_t val = 0;
+    if (j < nq && x < pd) val = feats[(size_t)j * nf + (x % q) / K];
+    const uint32_t pos = slot_index[s];
+    for (int i = 0; i < p; i++) out[((size_t)i << logN) + pos] = (val >> i) & 1u;
+}
+
+// encryption randomness of plane i (stream base 0x1000000 + 3 i):
+// u ternary, x0 = t e0 + m, x1 = t e1, as residues mod q_0..q_{L-1}
+__global__ void k_enc_prep(const u64 *mt, int p, u64 seed, int L, int logN, u64 t, const PrimeDev *pr, u64 *U,
+                           u64 *X0, u64 *X1) {
+    size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= ((size_t)p << logN)) return;
+    const int i = (int)(e >> logN);
+    const u64 n = e & ((1ull << logN) - 1);
+    const u64 sb = 0x1000000ull + 3ull * (u64)i;
+    const i64 u = sample_small(seed, sb, n, 0);
+    const i64 e0 = sample_small(seed, sb + 1, n, 1), e1 = sample_small(seed, sb + 2, n, 1);
+    const u64 c = mt[e];
+    const i64 m = c > (t - 1) / 2 ? (i64)c - (i64)t : (i64)c;
+    const i64 x0 = (i64)t * e0 + m, x1 = (i64)t * e1;
+    for (int r = 0; r < L; r++) {
+        const u64 q = pr[r].q;
+        const size_t o = (((size_t)i * L + r) << logN) + n;
+        U[o] = from_signed(u, q);
+        X0[o] = from_signed(x0, q);
+        X1[o] = from_signed(x1, q);
+    }
+}
+
+// ct_i = (pk0 u + x0, pk1 u + x1), out [p][2][L][N]
+__global__ void k_enc_combine(const u64 *pk, const u64 *U, const u64 *X0, const u64 *X1, u64 *out, int p, int L,
+                              int logN, const PrimeDev *pr) {
+    size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t per = (size_t)L << logN;
+    if (e >= (size_t)p * per) return;
+    const size_t i = e / per, k = e - i * per;
+    const PrimeDev P = pr[k >> logN];
+    const u64 u = U[e];
+    out[(2 * i) * per + k] = add_mod(mul_mod(pk[k], u, P), X0[e], P.q);
+    out[(2 * i + 1) * per + k] = add_mod(mul_mod(pk[per + k], u, P), X1[e], P.q);
+}
+
+__global__ void k_dec_dot(const u64 *ct, const u64 *s, u64 *x, int logN, const PrimeDev *pr) {
+    size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (1ull << logN)) return;
+    const PrimeDev P = pr[0];
+    x[e] = add_mod(ct[e], mul_mod(ct[(1ull << logN) + e], s[e], P), P.q);
+}
+
+__global__ void k_dec_to_t(const u64 *x, u64 *out, int logN, u64 t, const PrimeDev *pr) {
+    size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (1ull << logN)) return;
+    const u64 q = pr[0].q, v = x[e];
+    if (v > (q - 1) / 2) {
+        const u64 m = (q - v) % t;  // centred value is -(q - v)
+        out[e] = m ? t - m : 0;
+    } else {
+        out[e] = v % t;
+    }
+}
+
+__global__ void k_gather_slots(const u64 *ntt_t, const uint32_t *slot_index, u64 *slots, int logN) {
+    size_t s = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= (1ull << logN)) return;
+    slots[s] = ntt_t[slot_index[s]];
+}
+
+__global__ void k_extract_bits(const u64 *slots, int nq, int block, int L, uint8_t *bits) {
+    size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (size_t)nq * L) return;
+    const size_t j = e / L, x = e - j * L;
+    const u64 v = slots[j * block + x];
+    bits[e] = v == 0 ? 0 : (v == 1 ? 1 : 2);
+}
+
+// ---------------------------------------------------------------- helpers
+struct Scratch {
+    std::vector<void *> ptrs;
+    cudaStream_t s;
+    explicit Scratch(cudaStream_t st) : s(st) {}
+    ~Scratch() {
+        for (void *p : ptrs) dev_free(p, s);
+    }
+    copse_status get(copse_ctx *c, u64 **p, size_t words) {
+        STATUS_TRY(dev_alloc(c, (void **)p, words * sizeof(u64), s));
+        ptrs.push_back(*p);
+        return COPSE_OK;
+    }
+};
+
+NttBatch batch(u64 *data, size_t stride, int npoly, int r0, int nr, int ell, int fixed = -1) {
+    return NttBatch{data, stride, npoly, r0, nr, ell, fixed};
+}
+
+// ModUp of x (NTT domain [ell][N]) for every digit; result NTT domain [nd][ell+alpha][N]
+copse_status ks_modup(copse_ctx *c, const u64 *x_ntt, int ell, Scratch &sc, u64 **yhat, cudaStream_t s) {
+    const int N = c->N, A = c->alpha, nx = ell + A, nd = (ell + A - 1) / A;
+    u64 *xc = nullptr, *y = nullptr;
+    STATUS_TRY(sc.get(c, &xc, (size_t)ell * N));
+    STATUS_TRY(sc.get(c, &y, (size_t)nd * nx * N));
+    CUDA_TRY(cudaMemcpyAsync(xc, x_ntt, (size_t)ell * N * sizeof(u64), cudaMemcpyDeviceToDevice, s));
+    STATUS_TRY(ntt_inverse(c, batch(xc, (size_t)ell * N, 1, 0, ell, ell), s));
+    k_modup<<<nblk((size_t)nd * N), TPB, 0, s>>>(xc, y, ell, A, c->L, c->NP, c->logN, c->d_prime, c->ks);
+    LAUNCH_CHECK();
+    STATUS_TRY(ntt_forward(c, batch(y, (size_t)nx * N, nd, 0, nx, ell), s));
+    *yhat = y;
+    return COPSE_OK;
+}
+
+// inner products and ModDown conversion for jobs; U [nj][2][ell+alpha][N], W [nj][2][ell][N]
+copse_status ks_apply(copse_ctx *c, const u64 *yhat, int ell, const std::vector<InnerJob> &jobs_h, u64 *U, u64 *W,
+                      Scratch &sc, cudaStream_t s) {
+    const int N = c->N, A = c->alpha, nx = ell + A, nj = (int)jobs_h.size();
+    u64 *jbuf = nullptr;
+    STATUS_TRY(sc.get(c, &jbuf, (nj * sizeof(InnerJob) + 7) / 8));
+    CUDA_TRY(cudaMemcpyAsync(jbuf, jobs_h.data(), nj * sizeof(InnerJob), cudaMemcpyHostToDevice, s));
+    dim3 grid(nblk((size_t)nx * N), nj);
+    k_ks_inner<<<grid, TPB, 0, s>>>(yhat, (const InnerJob *)jbuf, ell, A, c->L, c->logN, c->d_prime);
+    LAUNCH_CHECK();
+    STATUS_TRY(ntt_inverse(c, batch(U, (size_t)nx * N, 2 * nj, ell, A, ell), s));
+    k_moddown_conv<<<nblk((size_t)2 * nj * N), TPB, 0, s>>>(U, (size_t)nx * N, W, (size_t)ell * N, 2 * nj, ell, A,
+                                                            c->L, c->logN, c->d_prime, c->ks);
+    LAUNCH_CHECK();
+    STATUS_TRY(ntt_forward(c, batch(W, (size_t)ell * N, 2 * nj, 0, ell, ell), s));
+    return COPSE_OK;
+}
+
+u64 galois_of_rotation(const copse_ctx *c, uint32_t k) {
+    u64 m = 2ull * c->N, g = 1, b = 3;
+    for (uint32_t e = k % (uint32_t)(c->N / 2); e; e >>= 1, b = b * b % m)
+        if (e & 1) g = g * b % m;
+    return g;
+}
+
+}  // namespace
+
+// the host pinned staging copies in this file are made with the pageable path
+// (cudaMemcpyAsync on host memory the caller owns); callers synchronise.
+
+size_t ksk_words(const copse_ctx *c) { return (size_t)c->ndig * 2 * (c->L + c->alpha) * c->N; }
+
+copse_ctbuf::~copse_ctbuf() {
+    for (auto &ct : cts) ct_free(&ct, 0);
+}
+
+copse_status ct_alloc(copse_ctx *c, DCt *ct, int level, int ncomp, cudaStream_t s) {
+    ct->level = level;
+    ct->ncomp = ncomp;
+    return dev_alloc(c, (void **)&ct->data, (size_t)ncomp * level * c->N * sizeof(u64), s);
+}
+void ct_free(DCt *ct, cudaStream_t s) {
+    dev_free(ct->data, s);
+    ct->data = nullptr;
+}
+copse_status ct_copy(copse_ctx *c, const DCt &in, DCt *out, cudaStream_t s) {
+    STATUS_TRY(ct_alloc(c, out, in.level, in.ncomp, s));
+    CUDA_TRY(cudaMemcpyAsync(out->data, in.data, (size_t)in.ncomp * in.level * c->N * sizeof(u64),
+                             cudaMemcpyDeviceToDevice, s));
+    return COPSE_OK;
+}
+
+copse_status op_modswitch(copse_ctx *c, const DCt &in, DCt *out, cudaStream_t s) {
+    const int ell = in.level, nc = in.ncomp, N = c->N;
+    if (ell < 2) { set_error("modulus switch below one prime"); return COPSE_ELEVEL; }
+    Scratch sc(s);
+    u64 *last = nullptr, *W = nullptr;
+    STATUS_TRY(sc.get(c, &last, (size_t)nc * N));
+    STATUS_TRY(sc.get(c, &W, (size_t)nc * (ell - 1) * N));
+    for (int k = 0; k < nc; k++)
+        CUDA_TRY(cudaMemcpyAsync(last + (size_t)k * N, in.data + ((size_t)k * ell + ell - 1) * N, N * sizeof(u64),
+                                 cudaMemcpyDeviceToDevice, s));
+    STATUS_TRY(ntt_inverse(c, batch(last, N, nc, 0, 1, ell, ell - 1), s));
+    k_ms_conv<<<nblk((size_t)nc * N), TPB, 0, s>>>(last, W, nc, ell, c->L, c->logN, c->d_prime, c->ks);
+    LAUNCH_CHECK();
+    STATUS_TRY(ntt_forward(c, batch(W, (size_t)(ell - 1) * N, nc, 0, ell - 1, ell - 1), s));
+    STATUS_TRY(ct_alloc(c, out, ell - 1, nc, s));
+    k_ms_finish<<<nblk((size_t)nc * (ell - 1) * N), TPB, 0, s>>>(in.data, W, out->data, nc, ell, c->L, c->logN,
+                                                                 c->d_prime, c->ks);
+    LAUNCH_CHECK();
+    return COPSE_OK;
+}
+
+copse_status op_to_level(copse_ctx *c, DCt *ct, int level, cudaStream_t s) {
+    while (ct->level > level) {
+        DCt nx;
+        STATUS_TRY(op_modswitch(c, *ct, &nx, s));
+        ct_free(ct, s);
+        *ct = nx;
+    }
+    return COPSE_OK;
+}
+
+// copies of a and b at a common level (only the higher one is switched)
+static copse_status aligned(copse_ctx *c, const DCt &a, const DCt &b, DCt *ta, DCt *tb, bool *own_a, bool *own_b,
+                            cudaStream_t s) {
+    *ta = a;
+    *tb = b;
+    *own_a = *own_b = false;
+    if (a.level > b.level) {
+        STATUS_TRY(ct_copy(c, a, ta, s));
+        *own_a = true;
+        STATUS_TRY(op_to_level(c, ta, b.level, s));
+    } else if (b.level > a.level) {
+        STATUS_TRY(ct_copy(c, b, tb, s));
+        *own_b = true;
+        STATUS_TRY(op_to_level(c, tb, a.level, s));
+    }
+    return COPSE_OK;
+}
+
+copse_status op_add(copse_ctx *c, const DCt &a, const DCt &b, DCt *out, bool negate_b, cudaStream_t s) {
+    DCt ta, tb;
+    bool oa, ob;
+    STATUS_TRY(aligned(c, a, b, &ta, &tb, &oa, &ob, s));
+    if (ta.ncomp != tb.ncomp) { set_error("component mismatch"); return COPSE_EINVAL; }
+    STATUS_TRY(ct_alloc(c, out, ta.level, ta.ncomp, s));
+    size_t n = (size_t)ta.ncomp * ta.level * c->N;
+    k_add<<<nblk(n), TPB, 0, s>>>(ta.data, tb.data, out->data, ta.ncomp, ta.level, c->logN, negate_b ? 1 : 0,
+                                  c->d_prime);
+    LAUNCH_CHECK();
+    if (oa) ct_free(&ta, s);
+    if (ob) ct_free(&tb, s);
+    return COPSE_OK;
+}
+
+copse_status op_mul(copse_ctx *c, const copse_evk *evk, const DCt &a, const DCt &b, DCt *out, cudaStream_t s) {
+    DCt ta, tb;
+    bool oa, ob;
+    STATUS_TRY(aligned(c, a, b, &ta, &tb, &oa, &ob, s));
+    const int ell = ta.level, N = c->N, A = c->alpha;
+    Scratch sc(s);
+    u64 *d = nullptr, *U = nullptr, *W = nullptr, *yhat = nullptr;
+    STATUS_TRY(sc.get(c, &d, (size_t)3 * ell * N));
+    k_tensor<<<nblk((size_t)ell * N), TPB, 0, s>>>(ta.data, tb.data, d, ell, c->logN, c->d_prime);
+    LAUNCH_CHECK();
+    if (oa) ct_free(&ta, s);
+    if (ob) ct_free(&tb, s);
+    STATUS_TRY(ks_modup(c, d + (size_t)2 * ell * N, ell, sc, &yhat, s));
+    STATUS_TRY(sc.get(c, &U, (size_t)2 * (ell + A) * N));
+    STATUS_TRY(sc.get(c, &W, (size_t)2 * ell * N));
+    std::vector<InnerJob> jobs{InnerJob{evk->rlk, U, 1}};
+    STATUS_TRY(ks_apply(c, yhat, ell, jobs, U, W, sc, s));
+    DCt r;
+    STATUS_TRY(ct_alloc(c, &r, ell, 2, s));
+    k_ks_finish<<<nblk((size_t)2 * ell * N), TPB, 0, s>>>(U, W, d, d + (size_t)ell * N, 1, r.data, ell, A, c->logN,
+                                                          c->d_prime, c->ks);
+    LAUNCH_CHECK();
+    copse_status st = op_modswitch(c, r, out, s);
+    ct_free(&r, s);
+    return st;
+}
+
+copse_status op_affine(copse_ctx *c, const DCt &x, const DPt &mul, const DPt *add, DCt *out, cudaStream_t s) {
+    if (mul.level < x.level || (add && add->level < x.level)) { set_error("plaintext level too low"); return COPSE_EINVAL; }
+    DCt r;
+    STATUS_TRY(ct_alloc(c, &r, x.level, 2, s));
+    k_affine<<<nblk((size_t)2 * x.level * c->N), TPB, 0, s>>>(x.data, mul.data, add ? add->data : nullptr, r.data,
+                                                              x.level, c->logN, c->d_prime);
+    LAUNCH_CHECK();
+    copse_status st = op_modswitch(c, r, out, s);
+    ct_free(&r, s);
+    return st;
+}
+
+copse_status op_rotate(copse_ctx *c, const copse_evk *evk, const DCt &a, uint32_t k, DCt *out, cudaStream_t s) {
+    const int ell = a.level, N = c->N, A = c->alpha;
+    const u64 g = galois_of_rotation(c, k);
+    if (g == 1) return ct_copy(c, a, out, s);
+    const u64 *key = evk->find(g);
+    if (!key) { set_error("no rotation key for amount " + std::to_string(k)); return COPSE_ENOKEY; }
+    Scratch sc(s);
+    u64 *yhat = nullptr, *U = nullptr, *W = nullptr;
+    STATUS_TRY(ks_modup(c, a.data + (size_t)ell * N, ell, sc, &yhat, s));
+    STATUS_TRY(sc.get(c, &U, (size_t)2 * (ell + A) * N));
+    STATUS_TRY(sc.get(c, &W, (size_t)2 * ell * N));
+    std::vector<InnerJob> jobs{InnerJob{key, U, g}};
+    STATUS_TRY(ks_apply(c, yhat, ell, jobs, U, W, sc, s));
+    STATUS_TRY(ct_alloc(c, out, ell, 2, s));
+    k_ks_finish<<<nblk((size_t)2 * ell * N), TPB, 0, s>>>(U, W, a.data, nullptr, g, out->data, ell, A, c->logN,
+                                                          c->d_prime, c->ks);
+    LAUNCH_CHECK();
+    return COPSE_OK;
+}
+
+copse_status op_matmul(copse_ctx *c, const copse_evk *evk, const DCt &v, const std::vector<uint32_t> &rots,
+                       const std::vector<std::vector<const u64 *>> &pt, const std::vector<const u64 *> &add,
+                       std::vector<DCt> &out, cudaStream_t s) {
+    const int ell = v.level, N = c->N, A = c->alpha, nacc = (int)pt.size(), nrot = (int)rots.size();
+    const size_t per = (size_t)2 * ell * N;
+    Scratch sc(s);
+    std::vector<u64 *> acc(nacc);
+    for (int a = 0; a < nacc; a++) {
+        STATUS_TRY(sc.get(c, &acc[a], per));
+        CUDA_TRY(cudaMemsetAsync(acc[a], 0, per * sizeof(u64), s));
+    }
+    // rotations that need a key switch share one ModUp
+    bool any_ks = false;
+    std::vector<u64> gal(nrot);
+    for (int r = 0; r < nrot; r++) {
+        gal[r] = galois_of_rotation(c, rots[r]);
+        if (gal[r] != 1) {
+            any_ks = true;
+            if (!evk->find(gal[r])) { set_error("no rotation key for amount " + std::to_string(rots[r])); return COPSE_ENOKEY; }
+        }
+    }
+    u64 *yhat = nullptr, *U = nullptr, *W = nullptr;
+    if (any_ks) {
+        STATUS_TRY(ks_modup(c, v.data + (size_t)ell * N, ell, sc, &yhat, s));
+        STATUS_TRY(sc.get(c, &U, (size_t)CHUNK_ROT * 2 * (ell + A) * N));
+        STATUS_TRY(sc.get(c, &W, (size_t)CHUNK_ROT * 2 * ell * N));
+    }
+    // per-chunk device tables: galois list, has-keyswitch flags, pt pointers, acc pointers
+    const int tab_words = CHUNK_ROT * (2 + MAX_ACC) + MAX_ACC + 8;
+    for (int r0 = 0; r0 < nrot;) {
+        // chunk: up to CHUNK_ROT rotations with key switches (identity terms ride along)
+        std::vector<int> idx;
+        std::vector<InnerJob> jobs;
+        int r = r0;
+        while (r < nrot && (int)idx.size() < CHUNK_ROT) {
+            if (gal[r] != 1) {
+                jobs.push_back(InnerJob{evk->find(gal[r]), U + (size_t)jobs.size() * 2 * (ell + A) * N, gal[r]});
+            }
+            idx.push_back(r);
+            r++;
+        }
+        if (!jobs.empty()) STATUS_TRY(ks_apply(c, yhat, ell, jobs, U, W, sc, s));
+        const int nr = (int)idx.size();
+        for (int a0 = 0; a0 < nacc; a0 += MAX_ACC) {
+            const int na = std::min(MAX_ACC, nacc - a0);
+            std::vector<u64> tab((size_t)tab_words, 0);
+            u64 *gl = tab.data();
+            int *hk = (int *)(tab.data() + CHUNK_ROT);
+            const u64 **ptab = (const u64 **)(tab.data() + 2 * CHUNK_ROT);
+            u64 **accp = (u64 **)(tab.data() + 2 * CHUNK_ROT + (size_t)CHUNK_ROT * MAX_ACC);
+            for (int x = 0; x < nr; x++) {
+                gl[x] = gal[idx[x]];
+                hk[x] = gal[idx[x]] != 1;
+                for (int a = 0; a < na; a++) ptab[(size_t)a * nr + x] = pt[a0 + a][idx[x]];
+            }
+            for (int a = 0; a < na; a++) accp[a] = acc[a0 + a];
+            u64 *dtab = nullptr;
+            STATUS_TRY(sc.get(c, &dtab, (size_t)tab_words));
+            CUDA_TRY(cudaMemcpyAsync(dtab, tab.data(), tab.size() * sizeof(u64), cudaMemcpyHostToDevice, s));
+            k_matmul_mac<<<nblk(per), TPB, 0, s>>>(U, W, v.data, nr, dtab, (const int *)(dtab + CHUNK_ROT),
+                                                   (const u64 *const *)(dtab + 2 * CHUNK_ROT),
+                                                   (u64 *const *)(dtab + 2 * CHUNK_ROT + (size_t)CHUNK_ROT * MAX_ACC),
+                                                   na, ell, A, c->logN, c->d_prime, c->ks);
+            LAUNCH_CHECK();
+        }
+        r0 = r;
+    }
+    out.assign(nacc, DCt());
+    for (int a = 0; a < nacc; a++) {
+        if (add.size() > (size_t)a && add[a]) {
+            k_add_plain<<<nblk((size_t)ell * N), TPB, 0, s>>>(acc[a], add[a], ell, c->logN, c->d_prime);
+            LAUNCH_CHECK();
+        }
+        DCt tmp;
+        tmp.level = ell;
+        tmp.ncomp = 2;
+        tmp.data = acc[a];
+        STATUS_TRY(op_modswitch(c, tmp, &out[a], s));
+    }
+    return COPSE_OK;
+}
+
+copse_status encode_patterns(copse_ctx *c, const std::vector<uint32_t> &patterns, int n, int len, int period,
+                             int level, u64 *out, cudaStream_t s) {
+    const int N = c->N;
+    if (n <= 0) return COPSE_OK;
+    Scratch sc(s);
+    u64 *pat = nullptr, *mt = nullptr;
+    STATUS_TRY(sc.get(c, &pat, ((size_t)n * len + 1) / 2 + 1));
+    STATUS_TRY(sc.get(c, &mt, (size_t)n * N));
+    CUDA_TRY(cudaMemcpyAsync(pat, patterns.data(), (size_t)n * len * sizeof(uint32_t), cudaMemcpyHostToDevice, s));
+    k_scatter_pattern<<<nblk((size_t)n * N), TPB, 0, s>>>((const uint32_t *)pat, n, len, period, c->logN,
+                                                          c->d_slot_index, mt);
+    LAUNCH_CHECK();
+    STATUS_TRY(ntt_inverse(c, batch(mt, N, n, 0, 1, 0, c->t_index()), s));
+    k_lift<<<nblk((size_t)n * level * N), TPB, 0, s>>>(mt, out, n, level, c->logN, c->t, c->d_prime);
+    LAUNCH_CHECK();
+    STATUS_TRY(ntt_forward(c, batch(out, (size_t)level * N, n, 0, level, level), s));
+    // the pattern staging buffer is read by the device before the caller's vector dies
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return COPSE_OK;
+}
+
+static copse_status make_switch_key(copse_ctx *c, u64 seed, u64 sb, const u64 *s_hat, const u64 *sfrom, u64 *ksk,
+                                    Scratch &sc, cudaStream_t s) {
+    const int N = c->N, NB = c->L + c->alpha;
+    u64 *a = nullptr, *te = nullptr;
+    STATUS_TRY(sc.get(c, &a, (size_t)NB * N));
+    STATUS_TRY(sc.get(c, &te, (size_t)NB * N));
+    for (int j = 0; j < c->ndig; j++) {
+        k_sample_uniform<<<nblk((size_t)NB * N), TPB, 0, s>>>(a, NB, 0, seed, sb + 2 * j, c->logN, c->d_prime);
+        LAUNCH_CHECK();
+        k_sample_small<<<nblk((size_t)NB * N), TPB, 0, s>>>(te, NB, seed, sb + 2 * j + 1, 1, (i64)c->t, nullptr,
+                                                            c->logN, c->d_prime);
+        LAUNCH_CHECK();
+        STATUS_TRY(ntt_forward(c, batch(a, (size_t)NB * N, 1, 0, NB, NB), s));
+        STATUS_TRY(ntt_forward(c, batch(te, (size_t)NB * N, 1, 0, NB, NB), s));
+        const int lo = j * c->alpha, hi = std::min((j + 1) * c->alpha, c->L);
+        k_ksk<<<nblk((size_t)NB * N), TPB, 0, s>>>(a, s_hat, te, sfrom, ksk + (size_t)j * 2 * NB * N, lo, hi, c->L,
+                                                   c->alpha, c->logN, c->d_prime, c->ks);
+        LAUNCH_CHECK();
+    }
+    return COPSE_OK;
+}
+
+copse_status keygen_dev(copse_ctx *c, u64 seed, const std::vector<u64> &galois, copse_keys **keys_out,
+                        copse_evk **evk_out) {
+    cudaStream_t s = 0;
+    const int N = c->N, L = c->L, NB = c->L + c->alpha;
+    copse_keys *K = new copse_keys();
+    copse_evk *E = new copse_evk();
+    K->ctx = E->ctx = c;
+    auto fail = [&](copse_status st) {
+        cudaStreamSynchronize(s);
+        dev_free(K->s_hat, s);
+        dev_free(K->pk, s);
+        dev_free(E->rlk, s);
+        for (u64 *p : E->gk) dev_free(p, s);
+        delete K;
+        delete E;
+        return st;
+    };
+    Scratch sc(s);
+    copse_status st;
+    u64 *raw = nullptr, *a = nullptr, *te = nullptr, *sf = nullptr;
+    if ((st = dev_alloc(c, (void **)&K->s_hat, (size_t)NB * N * 8, s)) || (st = dev_alloc(c, (void **)&K->pk, (size_t)2 * L * N * 8, s)) ||
+        (st = sc.get(c, &raw, N)) || (st = sc.get(c, &a, (size_t)L * N)) || (st = sc.get(c, &te, (size_t)L * N)) ||
+        (st = sc.get(c, &sf, (size_t)NB * N)))
+        return fail(st);
+    // secret: ternary, stream 1
+    k_sample_small<<<nblk((size_t)NB * N), TPB, 0, s>>>(K->s_hat, NB, seed, 1, 0, 1, (i64 *)raw, c->logN, c->d_prime);
+    if ((st = ntt_forward(c, batch(K->s_hat, (size_t)NB * N, 1, 0, NB, NB), s))) return fail(st);
+    // public key: a from stream 2 (primes 0..L-1), e from stream 3
+    k_sample_uniform<<<nblk((size_t)L * N), TPB, 0, s>>>(a, L, 0, seed, 2, c->logN, c->d_prime);
+    k_sample_small<<<nblk((size_t)L * N), TPB, 0, s>>>(te, L, seed, 3, 1, (i64)c->t, nullptr, c->logN, c->d_prime);
+    if ((st = ntt_forward(c, batch(a, (size_t)L * N, 1, 0, L, L), s))) return fail(st);
+    if ((st = ntt_forward(c, batch(te, (size_t)L * N, 1, 0, L, L), s))) return fail(st);
+    k_pk<<<nblk((size_t)L * N), TPB, 0, s>>>(a, K->s_hat, te, K->pk, L, c->logN, c->d_prime);
+    // relinearisation key: s' = s^2, streams 16 + 2j, 17 + 2j
+    if ((st = dev_alloc(c, (void **)&E->rlk, ksk_words(c) * 8, s))) return fail(st);
+    k_mul_elem<<<nblk((size_t)NB * N), TPB, 0, s>>>(K->s_hat, K->s_hat, sf, NB, c->logN, c->d_prime);
+    if ((st = make_switch_key(c, seed, 16, K->s_hat, sf, E->rlk, sc, s))) return fail(st);
+    // rotation keys: s' = tau_g(s), streams 0x10000 + 64 g + (2j, 2j + 1)
+    for (u64 g : galois) {
+        if (g == 1 || E->find(g)) continue;
+        u64 *k = nullptr;
+        if ((st = dev_alloc(c, (void **)&k, ksk_words(c) * 8, s))) return fail(st);
+        E->galois.push_back(g);
+        E->gk.push_back(k);
+        k_permute<<<nblk((size_t)NB * N), TPB, 0, s>>>(K->s_hat, sf, NB, g, c->logN);
+        if ((st = make_switch_key(c, seed, 0x10000ull + 64ull * g, K->s_hat, sf, k, sc, s))) return fail(st);
+    }
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) {
+        set_error("key generation kernels failed");
+        return fail(COPSE_ECUDA);
+    }
+    K->s_host.resize(N);
+    if (cudaMemcpy(K->s_host.data(), raw, N * sizeof(i64), cudaMemcpyDeviceToHost) != cudaSuccess) {
+        set_error("secret key copy failed");
+        return fail(COPSE_ECUDA);
+    }
+    *keys_out = K;
+    *evk_out = E;
+    return COPSE_OK;
+}
+
+copse_status encrypt_planes(copse_ctx *c, const copse_keys *k, const uint32_t *d_feats, int nq, int nf, int K,
+                            int q, int pd, int block, int p, u64 seed, std::vector<DCt> &out, cudaStream_t s) {
+    const int N = c->N, L = c->L;
+    Scratch sc(s);
+    u64 *mt = nullptr, *U = nullptr, *X0 = nullptr, *X1 = nullptr, *cts = nullptr;
+    STATUS_TRY(sc.get(c, &mt, (size_t)p * N));
+    STATUS_TRY(sc.get(c, &U, (size_t)p * L * N));
+    STATUS_TRY(sc.get(c, &X0, (size_t)p * L * N));
+    STATUS_TRY(sc.get(c, &X1, (size_t)p * L * N));
+    k_feature_planes<<<nblk(N), TPB, 0, s>>>(d_feats, nq, nf, K, q, pd, block, p, c->logN, c->d_slot_index, mt);
+    LAUNCH_CHECK();
+    STATUS_TRY(ntt_inverse(c, batch(mt, N, p, 0, 1, 0, c->t_index()), s));
+    k_enc_prep<<<nblk((size_t)p * N), TPB, 0, s>>>(mt, p, seed, L, c->logN, c->t, c->d_prime, U, X0, X1);
+    LAUNCH_CHECK();
+    STATUS_TRY(ntt_forward(c, batch(U, (size_t)L * N, p, 0, L, L), s));
+    STATUS_TRY(ntt_forward(c, batch(X0, (size_t)L * N, p, 0, L, L), s));
+    STATUS_TRY(ntt_forward(c, batch(X1, (size_t)L * N, p, 0, L, L), s));
+    STATUS_TRY(dev_alloc(c, (void **)&cts, (size_t)p * 2 * L * N * 8, s));
+    k_enc_combine<<<nblk((size_t)p * L * N), TPB, 0, s>>>(k->pk, U, X0, X1, cts, p, L, c->logN, c->d_prime);
+    LAUNCH_CHECK();
+    // one allocation, p views; the first ciphertext owns it
+    out.clear();
+    for (int i = 0; i < p; i++) {
+        DCt ct;
+        ct.level = L;
+        ct.ncomp = 2;
+        STATUS_TRY(ct_alloc(c, &ct, L, 2, s));
+        CUDA_TRY(cudaMemcpyAsync(ct.data, cts + (size_t)i * 2 * L * N, (size_t)2 * L * N * 8, cudaMemcpyDeviceToDevice, s));
+        out.push_back(ct);
+    }
+    dev_free(cts, s);
+    return COPSE_OK;
+}
+
+copse_status decrypt_slots_dev(copse_ctx *c, const copse_keys *k, const DCt &ct, u64 *d_slots, cudaStream_t s) {
+    const int N = c->N;
+    DCt cur;
+    STATUS_TRY(ct_copy(c, ct, &cur, s));
+    copse_status st = op_to_level(c, &cur, 1, s);
+    if (st) { ct_free(&cur, s); return st; }
+    Scratch sc(s);
+    u64 *x = nullptr, *xt = nullptr;
+    STATUS_TRY(sc.get(c, &x, N));
+    STATUS_TRY(sc.get(c, &xt, N));
+    k_dec_dot<<<nblk(N), TPB, 0, s>>>(cur.data, k->s_hat, x, c->logN, c->d_prime);
+    LAUNCH_CHECK();
+    ct_free(&cur, s);
+    STATUS_TRY(ntt_inverse(c, batch(x, N, 1, 0, 1, 1), s));
+    k_dec_to_t<<<nblk(N), TPB, 0, s>>>(x, xt, c->logN, c->t, c->d_prime);
+    LAUNCH_CHECK();
+    STATUS_TRY(ntt_forward(c, batch(xt, N, 1, 0, 1, 0, c->t_index()), s));
+    k_gather_slots<<<nblk(N), TPB, 0, s>>>(xt, c->d_slot_index, d_slots, c->logN);
+    LAUNCH_CHECK();
+    return COPSE_OK;
+}
+
+copse_status extract_bits(copse_ctx *c, const u64 *d_slots, int nq, int block, int L, uint8_t *d_bits,
+                          cudaStream_t s) {
+    if (nq * L == 0) return COPSE_OK;
+    k_extract_bits<<<nblk((size_t)nq * L), TPB, 0, s>>>(d_slots, nq, block, L, d_bits);
+    LAUNCH_CHECK();
+    return COPSE_OK;
+}
+
+copse_status ct_to_coeff_host(copse_ctx *c, const DCt &ct, u64 *host, cudaStream_t s) {
+    const size_t words = (size_t)ct.ncomp * ct.level * c->N;
+    Scratch sc(s);
+    u64 *tmp = nullptr;
+    STATUS_TRY(sc.get(c, &tmp, words));
+    CUDA_TRY(cudaMemcpyAsync(tmp, ct.data, words * 8, cudaMemcpyDeviceToDevice, s));
+    STATUS_TRY(ntt_inverse(c, batch(tmp, (size_t)ct.level * c->N, ct.ncomp, 0, ct.level, ct.level), s));
+    CUDA_TRY(cudaMemcpyAsync(host, tmp, words * 8, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return COPSE_OK;
+}
+
+copse_status ct_from_coeff_host(copse_ctx *c, const u64 *host, int level, DCt *out, cudaStream_t s) {
+    const size_t words = (size_t)2 * level * c->N;
+    STATUS_TRY(ct_alloc(c, out, level, 2, s));
+    CUDA_TRY(cudaMemcpyAsync(out->data, host, words * 8, cudaMemcpyHostToDevice, s));
+    STATUS_TRY(ntt_forward(c, batch(out->data, (size_t)level * c->N, 2, 0, level, level), s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return COPSE_OK;
+}
+
+extern "C" copse_status copse_poly_mul(copse_ctx *c, const uint64_t *a, const uint64_t *b, uint64_t *out,
+                                       uint32_t n_res, void *stream) {
+    if (!c || !a || !b || !out || n_res < 1 || (int)n_res > c->L) { set_error("bad argument"); return COPSE_EINVAL; }
+    cudaStream_t s = (cudaStream_t)stream;
+    const int N = c->N, nr = (int)n_res;
+    const size_t words = (size_t)nr * N;
+    Scratch sc(s);
+    u64 *fa = nullptr, *fb = nullptr;
+    STATUS_TRY(sc.get(c, &fa, words));
+    STATUS_TRY(sc.get(c, &fb, words));
+    CUDA_TRY(cudaMemcpyAsync(fa, a, words * 8, cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(fb, b, words * 8, cudaMemcpyDeviceToDevice, s));
+    STATUS_TRY(ntt_forward(c, batch(fa, words, 1, 0, nr, nr), s));
+    STATUS_TRY(ntt_forward(c, batch(fb, words, 1, 0, nr, nr), s));
+    k_mul_elem<<<nblk(words), TPB, 0, s>>>(fa, fb, out, nr, c->logN, c->d_prime);
+    LAUNCH_CHECK();
+    return ntt_inverse(c, batch(out, words, 1, 0, nr, nr), s);
+}

@@ -1,0 +1,82 @@
+"""Host-side checks of the C-ABI library (no GPU needed): it loads, exports
+every function include/copse.h declares, and its forest compiler and
+plaintext classifier agree with the oracle's exactly."""
+import numpy as np
+import pytest
+
+from conftest import read_golden
+from oracle import copse as Cp
+from paper_2104_09583_gb300 import synth
+
+K = pytest.importorskip("paper_2104_09583_gb300.copse", reason="CUDA library not built")
+
+
+def test_exports_every_declared_symbol():
+    names = K.declared_functions()
+    assert len(names) >= 25
+    lib = K.library()
+    assert [n for n in names if not hasattr(lib, n)] == []
+
+
+def _forests():
+    out = [(read_golden("fig1_forest.txt"), 4, 2, 10)]
+    for s in range(8):
+        out.append((synth.random_forest(300 + s, 1 + s % 4, 2 + s % 5, 1 + s % 6, 6, 3, complete=(s % 3 == 0)),
+                    6, 0, 12))
+    out.append(("a b\nb 0 5 l 0 b 0 9 l 1 l 0\nl 1\n", 4, 1, 8))
+    for name in ("toy-n1024", "forest100-n16384", "batch3-n16384"):
+        W = synth.WORKLOADS[name]
+        for k, text in enumerate(W.forest_texts()):
+            out.append((text, W.precision(k), W.n_features(k), W.log_n))
+    return out
+
+
+@pytest.mark.parametrize("case", range(len(_forests())))
+def test_compile_matches_oracle(case):
+    text, p, nf, logN = _forests()[case]
+    om = Cp.compile_forest(text, p, nf)
+    h = K.copse_compile_forest(text, p, nf, logN)
+    try:
+        info = K.copse_model_info_get(h)
+        assert (info["K"], info["q"], info["b"], info["n_leaves"], info["depth"], info["block"]) == \
+            (om.K, om.q, om.b, om.L, om.d, om.block)
+        assert info["n_features"] == om.n_features and info["levels_used"] == Cp.levels_needed(om)
+        ex = K.copse_model_export(h)
+        assert ex["thr_slot"].tolist() == om.thr_slot
+        assert ex["slot_branch"].tolist() == om.slot_branch
+        assert np.array_equal(ex["R"], om.R)
+        assert np.array_equal(ex["lvl"], np.stack(om.lvl))
+        assert np.array_equal(ex["mask"], np.stack(om.mask))
+        assert ex["br_level"].tolist() == om.br_level
+        rs, ls = K.copse_model_rotations(h)
+        ors, ols = Cp.rotation_sets(om)
+        assert rs == ors and ls == ols
+        qs = synth.random_queries(case, 20, om.n_features, p)
+        got = K.copse_classify_plain(h, qs)
+        _, trees = Cp.parse_forest(text)
+        for j in range(len(qs)):
+            assert got[j].tolist() == Cp.classify_plain(trees, qs[j])
+    finally:
+        K.copse_model_destroy(h)
+
+
+@pytest.mark.parametrize("text,p,code", [
+    ("a b\n", 4, "EPARSE"),                           # no tree
+    ("a b\nb 0 3 l 0\n", 4, "EPARSE"),                # branch missing a subtree
+    ("a b\nl 0 l 1\n", 4, "EPARSE"),                  # trailing tokens
+    ("a b\nx 0\n", 4, "EPARSE"),                      # unknown token
+    ("a b\nb 0 16 l 0 l 1\n", 4, "EINVAL"),           # threshold needs 5 bits
+    ("a b\nb 0 3 l 0 l 2\n", 4, "EINVAL"),            # class index out of range
+    ("a b\nl 0\n", 4, "EINVAL"),                      # no branches at all
+])
+def test_compile_errors(text, p, code):
+    with pytest.raises(K.CopseError) as e:
+        K.copse_compile_forest(text, p, 0, 10)
+    assert e.value.name == code
+
+
+def test_block_must_fit_a_row():
+    text = synth.random_forest(5, 4, 5, 8, 8, 4, complete=True)
+    with pytest.raises(K.CopseError) as e:
+        K.copse_compile_forest(text, 8, 8, 8)   # N = 256: a row has 128 slots
+    assert e.value.name == "EFIT"
