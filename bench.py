@@ -1,0 +1,441 @@
+#!/usr/bin/env python3
+"""Secure decision-forest inference benchmark (COPSE, Algorithm 1) on GB300.
+
+A step is one pass of the whole path over one batch of queries: encode and
+encrypt the feature bit-planes, SecComp, reshuffle product, level products
+with masks, product across levels, decrypt the leaf bits.  The default
+workload is the N = 2^14, 10-prime forest (4 random trees, 90..110 branches,
+8 features, 8-bit) with one query per step; the batched line packs the 32
+queries one ciphertext holds.  ``value`` is measured with the queries'
+feature words already in device memory; ``e2e`` goes through the C ABI with
+pinned host buffers (host-to-device copy of the features and device-to-host
+copy of the leaf bits inside every step).  ``--impl reference`` times the
+CPU oracle on the host instead.
+
+Under torchrun (N > 1) every rank runs an independent replica (the method
+has no exchange step); value = all ranks' inferences / the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "secure inferences/s"
+UNIT = "inferences/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["cuda", "reference"], default="cuda")
+    ap.add_argument("--workload", default="forest100-n16384")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-stats", action="store_true", help="skip the per-kernel event timers")
+    ap.add_argument("--profile", action="store_true", help="bracket the timed region with cudaProfilerStart/Stop")
+    ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work for cpu_baseline")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- distributed
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------- clocks
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.path = os.path.join("/tmp", f"copse_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.device), "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in open(self.path):
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- roofline inputs
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def ncu_traffic(family):
+    """Per-launch DRAM bytes from the committed ncu summary of this kernel family, or None when
+    the summary is missing or was taken on a different source file than the one built now."""
+    path = os.path.join(ROOT, "profiles", f"{family}_traffic.md")
+    try:
+        lines = open(path).read().splitlines()
+    except OSError:
+        return None
+    kv = {}
+    for ln in lines:
+        if ln.startswith("- ") and ":" in ln:
+            k, v = ln[2:].split(":", 1)
+            kv[k.strip()] = v.strip()
+    src = os.path.join(ROOT, "paper_2104_09583_gb300", "csrc", kv.get("source", ""))
+    try:
+        if hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] != kv.get("source_sha256_16"):
+            return None
+        return float(kv["dram_bytes_per_launch"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+# ---------------------------------------------------------------- CUDA arm
+def run_cuda(args, ws, rank, local):
+    import torch
+
+    from paper_2104_09583_gb300 import copse as K
+    from paper_2104_09583_gb300 import synth
+
+    W = synth.WORKLOADS[args.workload]
+    text = W.forest_texts()[0]
+    N = 1 << W.log_n
+    ctx = K.copse_ctx_create(W.log_n, W.bits, W.primes, W.dnum, device=local)
+    model = K.copse_compile_forest(text, W.precision(), W.n_features(), W.log_n)
+    info = K.copse_model_info_get(model)
+    keys, evk = K.copse_keygen(ctx, 7 + rank, [model])
+    stream = torch.cuda.current_stream().cuda_stream
+    per_ct = N // info["block"]
+    nf, L = info["n_features"], info["n_leaves"]
+
+    def make_inputs(nq, seed):
+        q = synth.random_queries(seed, nq, nf, W.precision())
+        d_feats = torch.from_numpy(q.astype(np.int32)).cuda()
+        d_bits = torch.zeros(max(nq * L, 1), dtype=torch.uint8, device="cuda")
+        return q, d_feats, d_bits
+
+    def step(nq, d_feats, d_bits, seed):
+        ct = K.copse_encrypt_features(ctx, keys, model, d_feats.data_ptr(), seed, stream=stream, on_device=True,
+                                      n_queries=nq)
+        res = K.copse_infer(ctx, evk, model, ct, stream=stream)
+        K.copse_decrypt_labels(ctx, keys, model, res, nq, stream=stream, out_device_ptr=d_bits.data_ptr())
+        K.copse_ctbuf_destroy(res)
+        K.copse_ctbuf_destroy(ct)
+
+    def timed(nq, steps, warmup, seed0, stats=False, clocks=None, profile=False):
+        q, d_feats, d_bits = make_inputs(nq, seed0 + rank)
+        for w in range(warmup):
+            step(nq, d_feats, d_bits, 1000 + w)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        barrier(ws)
+        torch.cuda.synchronize()
+        if stats:
+            K.copse_stats_reset()
+            K.copse_stats_enable(True)
+        if clocks:
+            clocks.start()
+        if profile:
+            torch.cuda.profiler.start()
+        for i in range(steps):
+            ev[i][0].record()
+            step(nq, d_feats, d_bits, 2000 + i)
+            ev[i][1].record()
+        torch.cuda.synchronize()
+        if profile:
+            torch.cuda.profiler.stop()
+        ck = clocks.stop() if clocks else None
+        if stats:
+            K.copse_stats_enable(False)
+        barrier(ws)
+        per = [ev[i][0].elapsed_time(ev[i][1]) for i in range(steps)]
+        total_ms = ev[0][0].elapsed_time(ev[-1][1])
+        # decrypted bits of the last step against plaintext classification
+        got = d_bits[: nq * L].cpu().numpy().reshape(nq, L)
+        ok = bool(np.array_equal(got, K.copse_classify_plain(model, q)))
+        return total_ms, per, ok, ck
+
+    clocks = Clocks(local)
+    total_ms, per, ok, ck = timed(1, args.steps, args.warmup, 11, stats=not args.no_stats, clocks=clocks,
+                                  profile=args.profile)
+    fam = K.copse_stats_all() if not args.no_stats else {}
+    total_ms = max_over_ranks(total_ms, ws)
+    value = ws * args.steps / (total_ms / 1e3)
+    # batched: every slot block of the ciphertext holds a query
+    b_ms, b_per, b_ok, _ = timed(per_ct, max(3, args.steps // 2), args.warmup, 21)
+    b_ms = max_over_ranks(b_ms, ws)
+    b_steps = max(3, args.steps // 2)
+    batched = {"queries_per_step": per_ct, "value": ws * per_ct * b_steps / (b_ms / 1e3), "unit": UNIT,
+               "ms_per_step": b_ms / b_steps, "p50_ms": float(np.percentile(b_per, 50)),
+               "p99_ms": float(np.percentile(b_per, 99)), "labels_ok": b_ok}
+
+    # end to end through the C ABI with pinned host buffers
+    q = synth.random_queries(31 + rank, 1, nf, W.precision())
+    h_feats = torch.from_numpy(q.copy()).pin_memory()
+    h_bits = torch.zeros(L, dtype=torch.uint8).pin_memory()
+
+    def e2e_step(seed):
+        ct = K.copse_encrypt_features(ctx, keys, model, h_feats.numpy(), seed, stream=stream)
+        res = K.copse_infer(ctx, evk, model, ct, stream=stream)
+        h_bits.numpy()[:] = K.copse_decrypt_labels(ctx, keys, model, res, 1, stream=stream).reshape(-1)
+        K.copse_ctbuf_destroy(res)
+        K.copse_ctbuf_destroy(ct)
+
+    for w in range(args.warmup):
+        e2e_step(3000 + w)
+    barrier(ws)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for i in range(args.steps):
+        e2e_step(4000 + i)
+    e1.record()
+    torch.cuda.synchronize()
+    e_ms = max_over_ranks(e0.elapsed_time(e1), ws)
+    e2e = {"value": ws * args.steps / (e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(q.nbytes),
+           "d2h_bytes_per_step": int(L), "labels_ok": bool(np.array_equal(h_bits.numpy(), K.copse_classify_plain(model, q)[0]))}
+
+    # roofline of the dominant kernel family (largest summed event time)
+    peaks, how = measured_peaks()
+    roof = None
+    launches_total = 0
+    kern = {}
+    if fam:
+        launches_total = int(sum(v["launches"] for v in fam.values()))
+        for k, v in fam.items():
+            if v["launches"]:
+                kern[k] = {"launches_per_step": v["launches"] / args.steps, "ms_per_step": v["ms"] / args.steps,
+                           "share": v["ms"] / max(1e-9, sum(x["ms"] for x in fam.values())),
+                           "gbs": v["bytes"] / (v["ms"] * 1e-3) / 1e9 if v["ms"] else 0.0}
+        top = max(fam, key=lambda k: fam[k]["ms"])
+        v = fam[top]
+        achieved = v["bytes"] / (v["ms"] * 1e-3) / 1e9
+        tr = ncu_traffic(top)
+        roof = {"kernel": top, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": tr,
+                "algorithmic_bytes_per_launch": v["bytes"] / v["launches"],
+                "avg_launch_us": v["ms"] * 1e3 / v["launches"], "peak_source": f"{how} hbm_gbs (copy)"}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = oracle_baseline(W, text, args.cpu_budget)
+
+    for h in (keys,):
+        K.copse_keys_destroy(h)
+    K.copse_evk_destroy(evk)
+    K.copse_model_destroy(model)
+    K.copse_ctx_destroy(ctx)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps, "p50_ms": float(np.percentile(per, 50)),
+        "p99_ms": float(np.percentile(per, 99)), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u64 (RNS residues mod 55-bit primes)", "data": "synthetic (seeded random forest and queries)",
+        "config": {"workload": W.name, "ring_degree": N, "ciphertext_primes": W.primes, "prime_bits": W.bits,
+                   "dnum": W.dnum, "trees": 4, "branches": info["b"], "leaves": L, "depth": info["depth"],
+                   "features": nf, "precision": W.precision(), "queries_per_step": 1, "parallelism": f"replicas{ws}",
+                   "l2": "working set > L2 (rotation keys alone are %.1f GB)" % (
+                       (info["n_rot_reshuffle"] + info["n_rot_level"]) * 3 * 2 * (W.primes + 4) * N * 8 / 1e9)},
+        "labels_ok": ok, "batched": batched, "e2e": e2e, "gpu_launches": launches_total,
+        "roofline": roof, "kernels": kern, "clocks": ck, "cpu_baseline": cpu,
+    }
+    return line
+
+
+# ---------------------------------------------------------------- CPU oracle (baseline / reference arm)
+class OracleBench:
+    """The oracle on the benchmark workload: operation counts of one inference
+    (exact, from the compiled model and the circuit's structure) and timed
+    samples of its operations at the levels where the circuit runs them."""
+
+    def __init__(self, W, text):
+        from oracle import bgv as B
+        from oracle import copse as Cp
+
+        self.B, self.Cp = B, Cp
+        self.m = m = Cp.compile_forest(text, W.precision(), W.n_features())
+        self.P = P = B.Params(logN=W.log_n, L=W.primes, bits=W.bits, dnum=W.dnum)
+        self.bgv = B.Bgv(P)
+        self.rs, self.ls = Cp.rotation_sets(m)
+        self.keys = self.bgv.keygen(7, [B.galois_rot(W.log_n, k) for k in self.rs[:2]])
+        self.qs = W.query_arrays()[0]
+        p = m.precision
+        self.n = {"affine": 2 * p, "mul": max(0, 2 * p - 3) + (m.d - 1), "rot": len(self.rs) + len(self.ls),
+                  "pt": len(Cp.reshuffle_diagonals(m)) + sum(len(Cp.level_diagonals(m, k, P.t))
+                                                             for k in range(1, m.d + 1))}
+        self.Rd = {i: Cp.tile_blocks(m, dg, P.N) for i, dg in Cp.reshuffle_diagonals(m).items()}
+
+    def _clock(self, f, *a):
+        s = time.perf_counter()
+        r = f(*a)
+        return r, time.perf_counter() - s
+
+    def sample_small(self):
+        """One of each operation (encrypt of all planes, affine leaf, multiply, rotation, plaintext
+        product) -> seconds per inference."""
+        Cp, bgv, m = self.Cp, self.bgv, self.m
+        X, t_enc = self._clock(Cp.encrypt_queries, bgv, self.keys, m, self.qs, 99)
+        E = Cp.BgvEngine(bgv, self.keys)
+        Y = E.thresholds(m)
+        lt, t_aff = self._clock(E.affine, X[0], (-Y[0]) % E.t, Y[0])
+        _, t_mul = self._clock(E.mul, lt, lt)
+        lvl_D = self.P.L - 1 - (m.precision - 1).bit_length()
+        v = bgv.to_level(X[0], lvl_D)
+        k = self.rs[0]
+        r, t_rot = self._clock(E.rot, v, k)
+        _, t_pt = self._clock(E.mul_plain, r, self.Rd[k])
+        n = self.n
+        est = t_enc + n["affine"] * t_aff + n["mul"] * t_mul + n["rot"] * t_rot + n["pt"] * t_pt
+        return est, (f"oracle timed on one of each operation of the workload (encrypt of {m.precision} planes, "
+                     f"affine leaf, multiply, rotation at the reshuffle level, plaintext product); one inference "
+                     f"extrapolated with its exact counts ({n['affine']} affine, {n['mul']} multiplies, "
+                     f"{n['rot']} rotations, {n['pt']} plaintext products)")
+
+    def sample_large(self, budget_s):
+        """Encrypt and the whole SecComp, then reshuffle terms while the budget lasts -> s/inference."""
+        Cp, bgv, m = self.Cp, self.bgv, self.m
+        t0 = time.perf_counter()
+        X = Cp.encrypt_queries(bgv, self.keys, m, self.qs, 99)
+        t_enc = time.perf_counter() - t0
+        times = {"mul": []}
+
+        class Timed(Cp.BgvEngine):
+            def mul(s_, a, b):
+                s = time.perf_counter()
+                r = Cp.BgvEngine.mul(s_, a, b)
+                times["mul"].append(time.perf_counter() - s)
+                return r
+
+        E = Timed(bgv, self.keys)
+        t1 = time.perf_counter()
+        D = Cp.seccomp(E, X, E.thresholds(m), m.precision)
+        t_sec = time.perf_counter() - t1
+        t_rot, t_pt = [], []
+        for k in self.rs[:2]:
+            r, tr = self._clock(E.rot, D, k)
+            _, tp = self._clock(E.mul_plain, r, self.Rd[k])
+            t_rot.append(tr)
+            t_pt.append(tp)
+            if time.perf_counter() - t0 > budget_s:
+                break
+        n = self.n
+        est = (t_enc + t_sec + n["rot"] * statistics.mean(t_rot) + n["pt"] * statistics.mean(t_pt)
+               + (m.d - 1) * statistics.mean(times["mul"]))
+        return est, (f"oracle timed on encrypt ({m.precision} planes), the whole SecComp, {len(t_rot)} rotations and "
+                     f"plaintext products of the reshuffle ({time.perf_counter() - t0:.1f} s of CPU work); one "
+                     f"inference extrapolated with its exact counts ({n['rot']} rotations, {n['pt']} plaintext "
+                     f"products, {m.d - 1} more multiplies): {est:.1f} s/inference")
+
+
+def oracle_baseline(W, text, budget_s):
+    est, sample = OracleBench(W, text).sample_large(budget_s)
+    return {"value": 1.0 / est, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+
+
+def run_reference(args, ws, rank):
+    from paper_2104_09583_gb300 import synth
+
+    if rank != 0:
+        return None
+    W = synth.WORKLOADS[args.workload]
+    ob = OracleBench(W, W.forest_texts()[0])
+    for _ in range(args.warmup):
+        ob.sample_small()
+    ests, sample = [], ""
+    for _ in range(args.steps):
+        est, sample = ob.sample_small()
+        ests.append(est)
+    est = statistics.mean(ests)
+    value = 1.0 / est
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": est * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64 (RNS residues mod 55-bit primes)",
+            "data": "synthetic (seeded random forest and queries)", "config": {"workload": W.name},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_setup()
+    if args.impl == "reference":
+        line = run_reference(args, ws, rank)
+    else:
+        line = run_cuda(args, ws, rank, local)
+    if rank == 0 and line is not None:
+        print(json.dumps(line))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

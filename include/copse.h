@@ -227,6 +227,23 @@ copse_status copse_ntt(copse_ctx *ctx, uint64_t *data, size_t n_polys, uint32_t 
 copse_status copse_poly_mul(copse_ctx *ctx, const uint64_t *a, const uint64_t *b, uint64_t *c, uint32_t n_res,
                             void *stream);
 
+/* ---------------------------------------------------------------- kernel timing
+ * Instrumentation, off by default.  When on, the library brackets every
+ * kernel launch with two CUDA events on the launch stream and tags it with
+ * its family ("ntt_fwd", "ntt_inv", "modup", "ks_inner", "moddown_conv",
+ * "ks_finish", "matmul_mac", "tensor", "ms_conv", "ms_finish", "affine",
+ * "add") and its algorithmic bytes (each operand read once, each result
+ * written once).  The paper's own measurement is per-stage wall time
+ * (Section 8.4); this gives the per-kernel view. */
+copse_status copse_stats_enable(int on);
+/* Wait for the device and clear every total. */
+copse_status copse_stats_reset(void);
+/* Wait for the device; totals of family `name` (NULL or "" = all families):
+ * launches, summed event time in milliseconds, algorithmic bytes. */
+copse_status copse_stats_get(const char *name, uint64_t *launches, double *ms, double *bytes);
+/* Newline-separated family names seen so far into buf[cap]. */
+copse_status copse_stats_names(char *buf, size_t cap);
+
 #ifdef __cplusplus
 }
 #endif

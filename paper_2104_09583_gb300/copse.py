@@ -83,6 +83,10 @@ _SIG = {
     "copse_ct_mul_plain": (C.c_int, [vp, vp, C.c_size_t, u64p, vp, pvp, vp]),
     "copse_ntt": (C.c_int, [vp, vp, C.c_size_t, C.c_uint32, C.c_int, vp]),
     "copse_poly_mul": (C.c_int, [vp, vp, vp, vp, C.c_uint32, vp]),
+    "copse_stats_enable": (C.c_int, [C.c_int]),
+    "copse_stats_reset": (C.c_int, []),
+    "copse_stats_get": (C.c_int, [C.c_char_p, C.POINTER(C.c_uint64), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "copse_stats_names": (C.c_int, [C.c_char_p, C.c_size_t]),
 }
 for _n, (_r, _a) in _SIG.items():
     _f = getattr(_lib, _n)
@@ -308,3 +312,28 @@ def copse_ntt(ctx, data_ptr, n_polys, n_res, inverse=False, stream=None):
 def copse_poly_mul(ctx, a_ptr, b_ptr, c_ptr, n_res, stream=None):
     _check(_lib.copse_poly_mul(ctx, C.c_void_p(a_ptr), C.c_void_p(b_ptr), C.c_void_p(c_ptr), n_res,
                                C.c_void_p(stream)))
+
+
+# ---------------------------------------------------------------- kernel timing
+def copse_stats_enable(on=True):
+    _check(_lib.copse_stats_enable(1 if on else 0))
+
+
+def copse_stats_reset():
+    _check(_lib.copse_stats_reset())
+
+
+def copse_stats_get(name=None):
+    n, ms, by = C.c_uint64(), C.c_double(), C.c_double()
+    _check(_lib.copse_stats_get(name.encode() if name else None, C.byref(n), C.byref(ms), C.byref(by)))
+    return {"launches": n.value, "ms": ms.value, "bytes": by.value}
+
+
+def copse_stats_names():
+    buf = C.create_string_buffer(4096)
+    _check(_lib.copse_stats_names(buf, 4096))
+    return [x for x in buf.value.decode().split("\n") if x]
+
+
+def copse_stats_all():
+    return {n: copse_stats_get(n) for n in copse_stats_names()}

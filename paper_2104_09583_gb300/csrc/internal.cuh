@@ -41,6 +41,16 @@ void set_error(const std::string &msg);
 // after a kernel launch
 #define LAUNCH_CHECK() CUDA_TRY(cudaGetLastError())
 
+// kernel timing (stats.cu): brackets a launch with CUDA events when enabled
+int stats_begin(const char *name, double bytes, cudaStream_t s);
+void stats_end(int token, cudaStream_t s);
+#define TIMED(name, bytes, s, ...)                                                               \
+    do {                                                                                         \
+        int tk__ = stats_begin(name, (double)(bytes), s);                                        \
+        __VA_ARGS__;                                                                             \
+        stats_end(tk__, s);                                                                      \
+    } while (0)
+
 // ---------------------------------------------------------------- per-prime constants
 struct PrimeDev {
     u64 q;

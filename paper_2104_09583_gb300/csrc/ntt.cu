@@ -99,10 +99,13 @@ copse_status launch(copse_ctx *ctx, const NttBatch &b, cudaStream_t s, bool inve
         CUDA_TRY(cudaFuncSetAttribute(k_ntt_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         smem_limit.store((int)smem);
     }
+    const double bytes = (double)grid * N * 16.0;  // one read and one write of each residue polynomial
     if (inverse)
-        k_ntt_inv<<<grid, threads, smem, s>>>(b, ctx->d_prime, ctx->d_ipsi, ctx->d_ipsi_sh, ctx->logN, ctx->L);
+        TIMED("ntt_inv", bytes, s,
+              k_ntt_inv<<<grid, threads, smem, s>>>(b, ctx->d_prime, ctx->d_ipsi, ctx->d_ipsi_sh, ctx->logN, ctx->L));
     else
-        k_ntt_fwd<<<grid, threads, smem, s>>>(b, ctx->d_prime, ctx->d_psi, ctx->d_psi_sh, ctx->logN, ctx->L);
+        TIMED("ntt_fwd", bytes, s,
+              k_ntt_fwd<<<grid, threads, smem, s>>>(b, ctx->d_prime, ctx->d_psi, ctx->d_psi_sh, ctx->logN, ctx->L));
     LAUNCH_CHECK();
     return COPSE_OK;
 }

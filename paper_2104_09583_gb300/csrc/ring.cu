@@ -470,7 +470,7 @@ copse_status ks_modup(copse_ctx *c, const u64 *x_ntt, int ell, Scratch &sc, u64 
     STATUS_TRY(sc.get(c, &y, (size_t)nd * nx * N));
     CUDA_TRY(cudaMemcpyAsync(xc, x_ntt, (size_t)ell * N * sizeof(u64), cudaMemcpyDeviceToDevice, s));
     STATUS_TRY(ntt_inverse(c, batch(xc, (size_t)ell * N, 1, 0, ell, ell), s));
-    k_modup<<<nblk((size_t)nd * N), TPB, 0, s>>>(xc, y, ell, A, c->L, c->NP, c->logN, c->d_prime, c->ks);
+    TIMED("modup", 8.0 * N * ((double)ell + (double)nd * nx), s, k_modup<<<nblk((size_t)nd * N), TPB, 0, s>>>(xc, y, ell, A, c->L, c->NP, c->logN, c->d_prime, c->ks));
     LAUNCH_CHECK();
     STATUS_TRY(ntt_forward(c, batch(y, (size_t)nx * N, nd, 0, nx, ell), s));
     *yhat = y;
@@ -485,11 +485,11 @@ copse_status ks_apply(copse_ctx *c, const u64 *yhat, int ell, const std::vector<
     STATUS_TRY(sc.get(c, &jbuf, (nj * sizeof(InnerJob) + 7) / 8));
     CUDA_TRY(cudaMemcpyAsync(jbuf, jobs_h.data(), nj * sizeof(InnerJob), cudaMemcpyHostToDevice, s));
     dim3 grid(nblk((size_t)nx * N), nj);
-    k_ks_inner<<<grid, TPB, 0, s>>>(yhat, (const InnerJob *)jbuf, ell, A, c->L, c->logN, c->d_prime);
+    TIMED("ks_inner", 8.0 * N * ((double)((ell + A - 1) / A) * nx + (double)nj * (2.0 * ((ell + A - 1) / A) * nx + 2.0 * nx)), s, k_ks_inner<<<grid, TPB, 0, s>>>(yhat, (const InnerJob *)jbuf, ell, A, c->L, c->logN, c->d_prime));
     LAUNCH_CHECK();
     STATUS_TRY(ntt_inverse(c, batch(U, (size_t)nx * N, 2 * nj, ell, A, ell), s));
-    k_moddown_conv<<<nblk((size_t)2 * nj * N), TPB, 0, s>>>(U, (size_t)nx * N, W, (size_t)ell * N, 2 * nj, ell, A,
-                                                            c->L, c->logN, c->d_prime, c->ks);
+    TIMED("moddown_conv", 8.0 * N * 2.0 * nj * ((double)A + ell), s, k_moddown_conv<<<nblk((size_t)2 * nj * N), TPB, 0, s>>>(U, (size_t)nx * N, W, (size_t)ell * N, 2 * nj, ell, A,
+                                                            c->L, c->logN, c->d_prime, c->ks));
     LAUNCH_CHECK();
     STATUS_TRY(ntt_forward(c, batch(W, (size_t)ell * N, 2 * nj, 0, ell, ell), s));
     return COPSE_OK;
@@ -540,12 +540,12 @@ copse_status op_modswitch(copse_ctx *c, const DCt &in, DCt *out, cudaStream_t s)
         CUDA_TRY(cudaMemcpyAsync(last + (size_t)k * N, in.data + ((size_t)k * ell + ell - 1) * N, N * sizeof(u64),
                                  cudaMemcpyDeviceToDevice, s));
     STATUS_TRY(ntt_inverse(c, batch(last, N, nc, 0, 1, ell, ell - 1), s));
-    k_ms_conv<<<nblk((size_t)nc * N), TPB, 0, s>>>(last, W, nc, ell, c->L, c->logN, c->d_prime, c->ks);
+    TIMED("ms_conv", 8.0 * N * (double)nc * ell, s, k_ms_conv<<<nblk((size_t)nc * N), TPB, 0, s>>>(last, W, nc, ell, c->L, c->logN, c->d_prime, c->ks));
     LAUNCH_CHECK();
     STATUS_TRY(ntt_forward(c, batch(W, (size_t)(ell - 1) * N, nc, 0, ell - 1, ell - 1), s));
     STATUS_TRY(ct_alloc(c, out, ell - 1, nc, s));
-    k_ms_finish<<<nblk((size_t)nc * (ell - 1) * N), TPB, 0, s>>>(in.data, W, out->data, nc, ell, c->L, c->logN,
-                                                                 c->d_prime, c->ks);
+    TIMED("ms_finish", 8.0 * N * 3.0 * nc * (ell - 1), s, k_ms_finish<<<nblk((size_t)nc * (ell - 1) * N), TPB, 0, s>>>(in.data, W, out->data, nc, ell, c->L, c->logN,
+                                                                 c->d_prime, c->ks));
     LAUNCH_CHECK();
     return COPSE_OK;
 }
@@ -585,8 +585,8 @@ copse_status op_add(copse_ctx *c, const DCt &a, const DCt &b, DCt *out, bool neg
     if (ta.ncomp != tb.ncomp) { set_error("component mismatch"); return COPSE_EINVAL; }
     STATUS_TRY(ct_alloc(c, out, ta.level, ta.ncomp, s));
     size_t n = (size_t)ta.ncomp * ta.level * c->N;
-    k_add<<<nblk(n), TPB, 0, s>>>(ta.data, tb.data, out->data, ta.ncomp, ta.level, c->logN, negate_b ? 1 : 0,
-                                  c->d_prime);
+    TIMED("add", 8.0 * c->N * 3.0 * ta.ncomp * ta.level, s, k_add<<<nblk(n), TPB, 0, s>>>(ta.data, tb.data, out->data, ta.ncomp, ta.level, c->logN, negate_b ? 1 : 0,
+                                  c->d_prime));
     LAUNCH_CHECK();
     if (oa) ct_free(&ta, s);
     if (ob) ct_free(&tb, s);
@@ -601,7 +601,7 @@ copse_status op_mul(copse_ctx *c, const copse_evk *evk, const DCt &a, const DCt 
     Scratch sc(s);
     u64 *d = nullptr, *U = nullptr, *W = nullptr, *yhat = nullptr;
     STATUS_TRY(sc.get(c, &d, (size_t)3 * ell * N));
-    k_tensor<<<nblk((size_t)ell * N), TPB, 0, s>>>(ta.data, tb.data, d, ell, c->logN, c->d_prime);
+    TIMED("tensor", 8.0 * N * 7.0 * ell, s, k_tensor<<<nblk((size_t)ell * N), TPB, 0, s>>>(ta.data, tb.data, d, ell, c->logN, c->d_prime));
     LAUNCH_CHECK();
     if (oa) ct_free(&ta, s);
     if (ob) ct_free(&tb, s);
@@ -612,8 +612,8 @@ copse_status op_mul(copse_ctx *c, const copse_evk *evk, const DCt &a, const DCt 
     STATUS_TRY(ks_apply(c, yhat, ell, jobs, U, W, sc, s));
     DCt r;
     STATUS_TRY(ct_alloc(c, &r, ell, 2, s));
-    k_ks_finish<<<nblk((size_t)2 * ell * N), TPB, 0, s>>>(U, W, d, d + (size_t)ell * N, 1, r.data, ell, A, c->logN,
-                                                          c->d_prime, c->ks);
+    TIMED("ks_finish", 8.0 * N * 7.0 * ell, s, k_ks_finish<<<nblk((size_t)2 * ell * N), TPB, 0, s>>>(U, W, d, d + (size_t)ell * N, 1, r.data, ell, A, c->logN,
+                                                          c->d_prime, c->ks));
     LAUNCH_CHECK();
     copse_status st = op_modswitch(c, r, out, s);
     ct_free(&r, s);
@@ -624,8 +624,8 @@ copse_status op_affine(copse_ctx *c, const DCt &x, const DPt &mul, const DPt *ad
     if (mul.level < x.level || (add && add->level < x.level)) { set_error("plaintext level too low"); return COPSE_EINVAL; }
     DCt r;
     STATUS_TRY(ct_alloc(c, &r, x.level, 2, s));
-    k_affine<<<nblk((size_t)2 * x.level * c->N), TPB, 0, s>>>(x.data, mul.data, add ? add->data : nullptr, r.data,
-                                                              x.level, c->logN, c->d_prime);
+    TIMED("affine", 8.0 * c->N * 6.0 * x.level, s, k_affine<<<nblk((size_t)2 * x.level * c->N), TPB, 0, s>>>(x.data, mul.data, add ? add->data : nullptr, r.data,
+                                                              x.level, c->logN, c->d_prime));
     LAUNCH_CHECK();
     copse_status st = op_modswitch(c, r, out, s);
     ct_free(&r, s);
@@ -646,8 +646,8 @@ copse_status op_rotate(copse_ctx *c, const copse_evk *evk, const DCt &a, uint32_
     std::vector<InnerJob> jobs{InnerJob{key, U, g}};
     STATUS_TRY(ks_apply(c, yhat, ell, jobs, U, W, sc, s));
     STATUS_TRY(ct_alloc(c, out, ell, 2, s));
-    k_ks_finish<<<nblk((size_t)2 * ell * N), TPB, 0, s>>>(U, W, a.data, nullptr, g, out->data, ell, A, c->logN,
-                                                          c->d_prime, c->ks);
+    TIMED("ks_finish", 8.0 * N * 6.0 * ell, s, k_ks_finish<<<nblk((size_t)2 * ell * N), TPB, 0, s>>>(U, W, a.data, nullptr, g, out->data, ell, A, c->logN,
+                                                          c->d_prime, c->ks));
     LAUNCH_CHECK();
     return COPSE_OK;
 }
@@ -708,13 +708,16 @@ copse_status op_matmul(copse_ctx *c, const copse_evk *evk, const DCt &v, const s
                 for (int a = 0; a < na; a++) ptab[(size_t)a * nr + x] = pt[a0 + a][idx[x]];
             }
             for (int a = 0; a < na; a++) accp[a] = acc[a0 + a];
+            int nz_pt = 0;
+            for (int x = 0; x < nr; x++)
+                for (int a = 0; a < na; a++) nz_pt += ptab[(size_t)a * nr + x] != nullptr;
             u64 *dtab = nullptr;
             STATUS_TRY(sc.get(c, &dtab, (size_t)tab_words));
             CUDA_TRY(cudaMemcpyAsync(dtab, tab.data(), tab.size() * sizeof(u64), cudaMemcpyHostToDevice, s));
-            k_matmul_mac<<<nblk(per), TPB, 0, s>>>(U, W, v.data, nr, dtab, (const int *)(dtab + CHUNK_ROT),
+            TIMED("matmul_mac", 8.0 * N * ell * (4.0 * jobs.size() + 2.0 + (double)nz_pt + 4.0 * na), s, k_matmul_mac<<<nblk(per), TPB, 0, s>>>(U, W, v.data, nr, dtab, (const int *)(dtab + CHUNK_ROT),
                                                    (const u64 *const *)(dtab + 2 * CHUNK_ROT),
                                                    (u64 *const *)(dtab + 2 * CHUNK_ROT + (size_t)CHUNK_ROT * MAX_ACC),
-                                                   na, ell, A, c->logN, c->d_prime, c->ks);
+                                                   na, ell, A, c->logN, c->d_prime, c->ks));
             LAUNCH_CHECK();
         }
         r0 = r;
