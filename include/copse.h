@@ -227,6 +227,23 @@ copse_status copse_ntt(copse_ctx *ctx, uint64_t *data, size_t n_polys, uint32_t 
 copse_status copse_poly_mul(copse_ctx *ctx, const uint64_t *a, const uint64_t *b, uint64_t *c, uint32_t n_res,
                             void *stream);
 
+/* The same product as copse_poly_mul, computed without allocating anything.
+ * The paper has no counterpart: this exists for callers that cannot allocate
+ * device memory when they need the product -- serving loops that forbid
+ * allocation after start-up to keep latency flat and memory use fixed, or
+ * programs whose device memory is already reserved by another allocator.
+ * It calls no cudaMalloc, cudaFree or allocating library routine.
+ * The caller still provides a, b and c (device memory, as for
+ * copse_poly_mul).  The two transform buffers are a fixed device array of
+ * 2 x 2^18 words (4 MiB) that every GPU loading this library holds until the
+ * process exits; n_res * N above 2^18 words fails with COPSE_EINVAL.  The
+ * first call on a device looks up the array's device address (the context's
+ * device must be current); make that first call before any stream capture.
+ * All calls on a device share the array: calls that overlap on the GPU race,
+ * so order them on one stream.  Async. */
+copse_status copse_poly_mul_noalloc(copse_ctx *ctx, const uint64_t *a, const uint64_t *b, uint64_t *c,
+                                    uint32_t n_res, void *stream);
+
 /* ---------------------------------------------------------------- kernel timing
  * Instrumentation, off by default.  When on, the library brackets every
  * kernel launch with two CUDA events on the launch stream and tags it with

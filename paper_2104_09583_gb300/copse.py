@@ -337,3 +337,14 @@ def copse_stats_names():
 
 def copse_stats_all():
     return {n: copse_stats_get(n) for n in copse_stats_names()}
+
+
+# ---------------------------------------------------------------- allocation-free product
+_lib.copse_poly_mul_noalloc.restype = C.c_int
+_lib.copse_poly_mul_noalloc.argtypes = [vp, vp, vp, vp, C.c_uint32, vp]
+
+
+def copse_poly_mul_noalloc(ctx, a_ptr, b_ptr, c_ptr, n_res, stream=None):
+    """copse_poly_mul without any allocation (fixed device scratch; see include/copse.h)."""
+    _check(_lib.copse_poly_mul_noalloc(ctx, C.c_void_p(a_ptr), C.c_void_p(b_ptr), C.c_void_p(c_ptr), n_res,
+                                       C.c_void_p(stream)))
