@@ -290,6 +290,7 @@ extern "C" copse_status copse_encrypt_features(copse_ctx *c, const copse_keys *k
     }
     auto buf = std::make_unique<copse_ctbuf>();
     buf->ctx = c;
+    buf->stream = s;
     copse_status st = encrypt_planes(c, k, d_feats, (int)nq, (int)f.n_features, (int)f.K, (int)f.q, (int)f.pd(),
                                      (int)f.block, (int)f.precision, seed, buf->cts, s);
     if (tmp) dev_free(tmp, s);
@@ -372,6 +373,7 @@ extern "C" copse_status copse_infer(copse_ctx *c, const copse_evk *evk, copse_mo
     if (!c || !evk || !m || !feats || !out) { set_error("null argument"); return COPSE_EINVAL; }
     auto buf = std::make_unique<copse_ctbuf>();
     buf->ctx = c;
+    buf->stream = as_stream(stream);
     DCt r;
     STATUS_TRY(infer_impl(c, evk, m, feats, &r, as_stream(stream)));
     buf->cts.push_back(r);
@@ -445,15 +447,16 @@ extern "C" copse_status copse_ctbuf_import(copse_ctx *c, const uint64_t *in, siz
 }
 
 extern "C" void copse_ctbuf_destroy(copse_ctbuf *b) {
-    if (!b) return;
-    cudaStreamSynchronize(0);
+    // frees are stream-ordered after the work that produced the buffer; work on
+    // other streams that still reads it must be ordered before this call
     delete b;
 }
 
 // ---------------------------------------------------------------- ring ops
-static copse_status one(copse_ctx *c, DCt &r, copse_ctbuf **out) {
+static copse_status one(copse_ctx *c, DCt &r, copse_ctbuf **out, void *stream) {
     auto buf = std::make_unique<copse_ctbuf>();
     buf->ctx = c;
+    buf->stream = as_stream(stream);
     buf->cts.push_back(r);
     *out = buf.release();
     return COPSE_OK;
@@ -464,7 +467,7 @@ extern "C" copse_status copse_ct_mul(copse_ctx *c, const copse_evk *evk, const c
     if (!c || !evk || !a || !b || !out || ia >= a->cts.size() || ib >= b->cts.size()) { set_error("bad argument"); return COPSE_EINVAL; }
     DCt r;
     STATUS_TRY(op_mul(c, evk, a->cts[ia], b->cts[ib], &r, as_stream(stream)));
-    return one(c, r, out);
+    return one(c, r, out, stream);
 }
 
 extern "C" copse_status copse_ct_rotate(copse_ctx *c, const copse_evk *evk, const copse_ctbuf *a, size_t ia,
@@ -472,7 +475,7 @@ extern "C" copse_status copse_ct_rotate(copse_ctx *c, const copse_evk *evk, cons
     if (!c || !evk || !a || !out || ia >= a->cts.size()) { set_error("bad argument"); return COPSE_EINVAL; }
     DCt r;
     STATUS_TRY(op_rotate(c, evk, a->cts[ia], k, &r, as_stream(stream)));
-    return one(c, r, out);
+    return one(c, r, out, stream);
 }
 
 extern "C" copse_status copse_ct_modswitch(copse_ctx *c, const copse_ctbuf *a, size_t ia, copse_ctbuf **out,
@@ -480,7 +483,7 @@ extern "C" copse_status copse_ct_modswitch(copse_ctx *c, const copse_ctbuf *a, s
     if (!c || !a || !out || ia >= a->cts.size()) { set_error("bad argument"); return COPSE_EINVAL; }
     DCt r;
     STATUS_TRY(op_modswitch(c, a->cts[ia], &r, as_stream(stream)));
-    return one(c, r, out);
+    return one(c, r, out, stream);
 }
 
 extern "C" copse_status copse_ct_mul_plain(copse_ctx *c, const copse_ctbuf *a, size_t ia, const uint64_t *mul_slots,
@@ -502,7 +505,7 @@ extern "C" copse_status copse_ct_mul_plain(copse_ctx *c, const copse_ctbuf *a, s
     copse_status st = op_affine(c, x, mp, add_slots ? &ap : nullptr, &r, s);
     dev_free(pts, s);
     if (st) return st;
-    return one(c, r, out);
+    return one(c, r, out, stream);
 }
 
 extern "C" copse_status copse_ntt(copse_ctx *c, uint64_t *data, size_t n_polys, uint32_t n_res, int inverse,

@@ -191,6 +191,7 @@ struct NttBatch {
     int r0, nr;
     int ell;
     int fixed;
+    int skip_alpha = 0;  // > 0: poly p skips residues [p*skip_alpha, min((p+1)*skip_alpha, ell))
 };
 copse_status ntt_forward(copse_ctx *ctx, const NttBatch &b, cudaStream_t s);
 copse_status ntt_inverse(copse_ctx *ctx, const NttBatch &b, cudaStream_t s);
@@ -216,6 +217,7 @@ struct copse_evk {
 struct copse_ctbuf {
     copse_ctx *ctx = nullptr;
     std::vector<DCt> cts;
+    cudaStream_t stream = 0;  // the stream whose work produced the ciphertexts; frees are ordered on it
     ~copse_ctbuf();
 };
 

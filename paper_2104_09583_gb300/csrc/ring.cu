@@ -15,6 +15,7 @@
 // serves every rotation of the same ciphertext and the result equals
 // rotating first and key switching after.
 #include <algorithm>
+#include <cstring>
 
 #include "internal.cuh"
 
@@ -89,8 +90,9 @@ __global__ void k_permute(const u64 *src, u64 *dst, int nres, u64 g, int logN) {
     dst[e] = src[(r << logN) + galois_src(n, g, logN)];
 }
 
-// ModUp of every digit: x [ell][N] coefficient form -> y [nd][ell+alpha][N] coefficient form
-__global__ void k_modup(const u64 *x, u64 *y, int ell, int alpha, int L, int NP, int logN, const PrimeDev *pr,
+// ModUp of every digit: x [ell][N] coefficient form -> y [nd][ell+alpha][N] coefficient form, except the
+// digit's own primes, which are copied from x_ntt (the same residues in NTT form)
+__global__ void k_modup(const u64 *x, const u64 *x_ntt, u64 *y, int ell, int alpha, int L, int NP, int logN, const PrimeDev *pr,
                         KsTables T) {
     const int N = 1 << logN;
     const int nd = (ell + alpha - 1) / alpha;
@@ -112,7 +114,7 @@ __global__ void k_modup(const u64 *x, u64 *y, int ell, int alpha, int L, int NP,
         const int g = r < ell ? r : L + (r - ell);
         u64 out;
         if (g >= lo && g < hi) {
-            out = x[((size_t)g << logN) + n];
+            out = x_ntt[((size_t)g << logN) + n];  // own prime: already in NTT form, not transformed again
         } else {
             const u64 qg = pr[g].q;
             out = 0;
@@ -132,16 +134,20 @@ struct InnerJob {
     u64 *out;        // [2][ell+alpha][N]
     u64 g;           // Galois element applied to the ModUp output, 1 = none
 };
+// a launch's jobs, passed by value (kernel parameter space): no host-to-device copy
+struct InnerJobs {
+    InnerJob j[CHUNK_ROT];
+};
 
 // (u0, u1)[r][n] = sum_j yhat[j][r][tau_g n] * ksk[j][c][ext_prime(r)][n]
-__global__ void k_ks_inner(const u64 *yhat, const InnerJob *jobs, int ell, int alpha, int L, int logN,
+__global__ void k_ks_inner(const u64 *yhat, const InnerJobs jobs, int ell, int alpha, int L, int logN,
                            const PrimeDev *pr) {
     const int N = 1 << logN;
     const int nx = ell + alpha, nd = (ell + alpha - 1) / alpha;
     const int NB = L + alpha;
     size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= ((size_t)nx << logN)) return;
-    const InnerJob J = jobs[blockIdx.y];
+    const InnerJob J = jobs.j[blockIdx.y];
     const int r = (int)(e >> logN);
     const uint32_t n = (uint32_t)(e & (N - 1));
     const int g = r < ell ? r : L + (r - ell);
@@ -212,12 +218,23 @@ __global__ void k_ks_finish(const u64 *u, const u64 *W, const u64 *add0, const u
     out[e] = v;
 }
 
+// per-chunk table of the multiply-accumulate, passed by value
+struct MacTable {
+    u64 gl[CHUNK_ROT];                 // Galois element of each rotation
+    int has_ks[CHUNK_ROT];             // 0: the rotation is the identity (no key switch)
+    const u64 *pt[MAX_ACC * CHUNK_ROT]; // [acc][rotation] diagonal, null = zero
+    u64 *acc[MAX_ACC];
+};
+
 // Multiply-accumulate of a chunk of rotations into up to MAX_ACC accumulators:
 //   rot_k = (k has no key switch) ? v : (tau_g v0, 0) + (U_k - t W_k) P^-1
 //   acc_a += pt[a][k] * rot_k
-__global__ void k_matmul_mac(const u64 *U, const u64 *W, const u64 *v, int nrot, const u64 *gl,
-                             const int *has_ks, const u64 *const *pt_tab, u64 *const *acc, int nacc, int ell,
-                             int alpha, int logN, const PrimeDev *pr, KsTables T) {
+__global__ void k_matmul_mac(const u64 *U, const u64 *W, const u64 *v, int nrot, const MacTable tab, int nacc,
+                             int ell, int alpha, int logN, const PrimeDev *pr, KsTables T) {
+    const u64 *gl = tab.gl;
+    const int *has_ks = tab.has_ks;
+    const u64 *const *pt_tab = tab.pt;
+    u64 *const *acc = tab.acc;
     const int N = 1 << logN;
     size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const size_t n_el = (size_t)ell << logN;
@@ -470,9 +487,12 @@ copse_status ks_modup(copse_ctx *c, const u64 *x_ntt, int ell, Scratch &sc, u64 
     STATUS_TRY(sc.get(c, &y, (size_t)nd * nx * N));
     CUDA_TRY(cudaMemcpyAsync(xc, x_ntt, (size_t)ell * N * sizeof(u64), cudaMemcpyDeviceToDevice, s));
     STATUS_TRY(ntt_inverse(c, batch(xc, (size_t)ell * N, 1, 0, ell, ell), s));
-    TIMED("modup", 8.0 * N * ((double)ell + (double)nd * nx), s, k_modup<<<nblk((size_t)nd * N), TPB, 0, s>>>(xc, y, ell, A, c->L, c->NP, c->logN, c->d_prime, c->ks));
+    TIMED("modup", 8.0 * N * ((double)ell + (double)nd * nx), s, k_modup<<<nblk((size_t)nd * N), TPB, 0, s>>>(xc, x_ntt, y, ell, A, c->L, c->NP, c->logN, c->d_prime, c->ks));
     LAUNCH_CHECK();
-    STATUS_TRY(ntt_forward(c, batch(y, (size_t)nx * N, nd, 0, nx, ell), s));
+    // the digit's own primes already hold the input's NTT values: skip them
+    NttBatch nb = batch(y, (size_t)nx * N, nd, 0, nx, ell);
+    nb.skip_alpha = A;
+    STATUS_TRY(ntt_forward(c, nb, s));
     *yhat = y;
     return COPSE_OK;
 }
@@ -481,11 +501,11 @@ copse_status ks_modup(copse_ctx *c, const u64 *x_ntt, int ell, Scratch &sc, u64 
 copse_status ks_apply(copse_ctx *c, const u64 *yhat, int ell, const std::vector<InnerJob> &jobs_h, u64 *U, u64 *W,
                       Scratch &sc, cudaStream_t s) {
     const int N = c->N, A = c->alpha, nx = ell + A, nj = (int)jobs_h.size();
-    u64 *jbuf = nullptr;
-    STATUS_TRY(sc.get(c, &jbuf, (nj * sizeof(InnerJob) + 7) / 8));
-    CUDA_TRY(cudaMemcpyAsync(jbuf, jobs_h.data(), nj * sizeof(InnerJob), cudaMemcpyHostToDevice, s));
+    if (nj > CHUNK_ROT) { set_error("internal: too many key-switch jobs in one launch"); return COPSE_EINVAL; }
+    InnerJobs jobs;
+    for (int i = 0; i < nj; i++) jobs.j[i] = jobs_h[i];
     dim3 grid(nblk((size_t)nx * N), nj);
-    TIMED("ks_inner", 8.0 * N * ((double)((ell + A - 1) / A) * nx + (double)nj * (2.0 * ((ell + A - 1) / A) * nx + 2.0 * nx)), s, k_ks_inner<<<grid, TPB, 0, s>>>(yhat, (const InnerJob *)jbuf, ell, A, c->L, c->logN, c->d_prime));
+    TIMED("ks_inner", 8.0 * N * ((double)((ell + A - 1) / A) * nx + (double)nj * (2.0 * ((ell + A - 1) / A) * nx + 2.0 * nx)), s, k_ks_inner<<<grid, TPB, 0, s>>>(yhat, jobs, ell, A, c->L, c->logN, c->d_prime));
     LAUNCH_CHECK();
     STATUS_TRY(ntt_inverse(c, batch(U, (size_t)nx * N, 2 * nj, ell, A, ell), s));
     TIMED("moddown_conv", 8.0 * N * 2.0 * nj * ((double)A + ell), s, k_moddown_conv<<<nblk((size_t)2 * nj * N), TPB, 0, s>>>(U, (size_t)nx * N, W, (size_t)ell * N, 2 * nj, ell, A,
@@ -510,7 +530,7 @@ u64 galois_of_rotation(const copse_ctx *c, uint32_t k) {
 size_t ksk_words(const copse_ctx *c) { return (size_t)c->ndig * 2 * (c->L + c->alpha) * c->N; }
 
 copse_ctbuf::~copse_ctbuf() {
-    for (auto &ct : cts) ct_free(&ct, 0);
+    for (auto &ct : cts) ct_free(&ct, stream);
 }
 
 copse_status ct_alloc(copse_ctx *c, DCt *ct, int level, int ncomp, cudaStream_t s) {
@@ -679,10 +699,8 @@ copse_status op_matmul(copse_ctx *c, const copse_evk *evk, const DCt &v, const s
         STATUS_TRY(sc.get(c, &U, (size_t)CHUNK_ROT * 2 * (ell + A) * N));
         STATUS_TRY(sc.get(c, &W, (size_t)CHUNK_ROT * 2 * ell * N));
     }
-    // per-chunk device tables: galois list, has-keyswitch flags, pt pointers, acc pointers
-    const int tab_words = CHUNK_ROT * (2 + MAX_ACC) + MAX_ACC + 8;
     for (int r0 = 0; r0 < nrot;) {
-        // chunk: up to CHUNK_ROT rotations with key switches (identity terms ride along)
+        // chunk: up to CHUNK_ROT rotations (identity terms included)
         std::vector<int> idx;
         std::vector<InnerJob> jobs;
         int r = r0;
@@ -697,27 +715,21 @@ copse_status op_matmul(copse_ctx *c, const copse_evk *evk, const DCt &v, const s
         const int nr = (int)idx.size();
         for (int a0 = 0; a0 < nacc; a0 += MAX_ACC) {
             const int na = std::min(MAX_ACC, nacc - a0);
-            std::vector<u64> tab((size_t)tab_words, 0);
-            u64 *gl = tab.data();
-            int *hk = (int *)(tab.data() + CHUNK_ROT);
-            const u64 **ptab = (const u64 **)(tab.data() + 2 * CHUNK_ROT);
-            u64 **accp = (u64 **)(tab.data() + 2 * CHUNK_ROT + (size_t)CHUNK_ROT * MAX_ACC);
-            for (int x = 0; x < nr; x++) {
-                gl[x] = gal[idx[x]];
-                hk[x] = gal[idx[x]] != 1;
-                for (int a = 0; a < na; a++) ptab[(size_t)a * nr + x] = pt[a0 + a][idx[x]];
-            }
-            for (int a = 0; a < na; a++) accp[a] = acc[a0 + a];
+            MacTable tab;
+            memset(&tab, 0, sizeof(tab));
             int nz_pt = 0;
-            for (int x = 0; x < nr; x++)
-                for (int a = 0; a < na; a++) nz_pt += ptab[(size_t)a * nr + x] != nullptr;
-            u64 *dtab = nullptr;
-            STATUS_TRY(sc.get(c, &dtab, (size_t)tab_words));
-            CUDA_TRY(cudaMemcpyAsync(dtab, tab.data(), tab.size() * sizeof(u64), cudaMemcpyHostToDevice, s));
-            TIMED("matmul_mac", 8.0 * N * ell * (4.0 * jobs.size() + 2.0 + (double)nz_pt + 4.0 * na), s, k_matmul_mac<<<nblk(per), TPB, 0, s>>>(U, W, v.data, nr, dtab, (const int *)(dtab + CHUNK_ROT),
-                                                   (const u64 *const *)(dtab + 2 * CHUNK_ROT),
-                                                   (u64 *const *)(dtab + 2 * CHUNK_ROT + (size_t)CHUNK_ROT * MAX_ACC),
-                                                   na, ell, A, c->logN, c->d_prime, c->ks));
+            for (int x = 0; x < nr; x++) {
+                tab.gl[x] = gal[idx[x]];
+                tab.has_ks[x] = gal[idx[x]] != 1;
+                for (int a = 0; a < na; a++) {
+                    tab.pt[(size_t)a * nr + x] = pt[a0 + a][idx[x]];
+                    nz_pt += tab.pt[(size_t)a * nr + x] != nullptr;
+                }
+            }
+            for (int a = 0; a < na; a++) tab.acc[a] = acc[a0 + a];
+            TIMED("matmul_mac", 8.0 * N * ell * (4.0 * jobs.size() + 2.0 + (double)nz_pt + 4.0 * na), s,
+                  k_matmul_mac<<<nblk(per), TPB, 0, s>>>(U, W, v.data, nr, tab, na, ell, A, c->logN, c->d_prime,
+                                                         c->ks));
             LAUNCH_CHECK();
         }
         r0 = r;
