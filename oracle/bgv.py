@@ -88,6 +88,8 @@ def lib():
             "or_mul_plain": (None, [P, u64p, C.c_int, C.c_int, i64p, u64p]),
             "or_add_plain": (None, [P, u64p, C.c_int, i64p]),
             "or_add": (None, [P, u64p, u64p, C.c_int, C.c_int, C.c_int, u64p]),
+            "or_matmul": (None, [P, u64p, C.c_int, C.c_int, u64p, C.POINTER(C.c_void_p), C.c_int, i64p,
+                                 np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS"), u64p]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -369,6 +371,28 @@ class Bgv:
         out = np.zeros((2, ell, self.P.N), dtype=np.uint64)
         self.L.or_rotate(self.P.c, ct, ell, g, gk, out)
         return out
+
+    def matmul(self, ct, galois, gks, pts) -> list:
+        """Sums of plaintext-times-rotation products sharing the rotations of ct, with one
+        modulus-down step per sum (see or_matmul).  galois[k]: Galois element of rotation k
+        (1 = none), gks[k]: its key (None for 1); pts[a][k]: centred plaintext coefficients
+        or None for a zero diagonal.  Returns one 2-component ciphertext per accumulator."""
+        P = self.P
+        ct = np.ascontiguousarray(ct)
+        ell = ct.shape[1]
+        nrot, nacc = len(galois), len(pts)
+        g = np.ascontiguousarray(galois, dtype=np.uint64)
+        keys = (C.c_void_p * max(nrot, 1))(*[None if k is None else k.ctypes.data for k in gks])
+        m = np.zeros((nacc, nrot, P.N), dtype=np.int64)
+        present = np.zeros(nacc * nrot, dtype=np.int32)
+        for a in range(nacc):
+            for k in range(nrot):
+                if pts[a][k] is not None:
+                    m[a, k] = pts[a][k]
+                    present[a * nrot + k] = 1
+        out = np.zeros((nacc, 2, ell, P.N), dtype=np.uint64)
+        self.L.or_matmul(P.c, ct, ell, nrot, g, keys, nacc, m, present, out)
+        return [out[a] for a in range(nacc)]
 
     def mul(self, a, b, rlk) -> np.ndarray:
         """ct x ct: tensor, relinearise, then drop one prime (the canonical policy)."""

@@ -499,15 +499,15 @@ static void moddown(const or_params *P, const u64 *u, int ell, u64 *out)
     }
 }
 
-/* Hybrid key switching of x ([ell][N], coefficient form) with ksk
- * ([ndig][2][L+alpha][N]): sum over the ceil(ell/alpha) active digits of
- * ModUp(digit) * ksk_j over the extended basis, then ModDown.  out: [2][ell][N]. */
-void or_keyswitch(const or_params *P, const u64 *x, int ell, const u64 *ksk, u64 *out)
+/* The key-switching sum before ModDown: over the ceil(ell/alpha) active digits,
+ * acc_c = sum_j ModUp(digit j of x) * ksk_j[c] over the extended basis.
+ * x: [ell][N] coefficient form; ksk: [ndig][2][L+alpha][N]; acc: [2][ell+alpha][N]. */
+static void keyswitch_raw(const or_params *P, const u64 *x, int ell, const u64 *ksk, u64 *acc)
 {
     int N = P->N, nx = ell + P->alpha, nb = P->L + P->alpha;
     int nd = (ell + P->alpha - 1) / P->alpha;
     u64 *y = malloc(sizeof(u64) * nx * N);
-    u64 *acc = calloc((size_t)2 * nx * N, sizeof(u64));
+    memset(acc, 0, sizeof(u64) * 2 * nx * N);
     for (int j = 0; j < nd; j++) {
         modup_digit(P, x, ell, j, y);
         for (int c = 0; c < 2; c++)
@@ -517,10 +517,91 @@ void or_keyswitch(const or_params *P, const u64 *x, int ell, const u64 *ksk, u64
                 poly_mul_acc(y + (size_t)r * N, k, P->logN, P->primes[g], acc + ((size_t)c * nx + r) * N);
             }
     }
+    free(y);
+}
+
+/* Hybrid key switching of x ([ell][N], coefficient form) with ksk
+ * ([ndig][2][L+alpha][N]): the raw sum above, then ModDown.  out: [2][ell][N]. */
+void or_keyswitch(const or_params *P, const u64 *x, int ell, const u64 *ksk, u64 *out)
+{
+    int N = P->N, nx = ell + P->alpha;
+    u64 *acc = malloc(sizeof(u64) * 2 * nx * N);
+    keyswitch_raw(P, x, ell, ksk, acc);
     moddown(P, acc, ell, out);
     moddown(P, acc + (size_t)nx * N, ell, out + (size_t)ell * N);
-    free(y);
     free(acc);
+}
+
+/* Diagonal matrix-vector products sharing the rotations of one ciphertext
+ * (the MatMul of Section 4.1.2: sum over diagonals of d_k * rot(v, k)), with
+ * the modulus-down step of key switching applied once to each sum:
+ *   for a rotation with Galois element g != 1,
+ *     R_g = KSraw(tau_g c1) + (P * tau_g c0, 0)      over q_0..q_{ell-1}, p_0..p_{alpha-1}
+ *   acc_a = sum_{g != 1} pt[a][g] * R_g,   out_a = ModDown(acc_a) + pt[a][1] * (c0, c1).
+ * R_g is P times the rotated ciphertext (up to key-switching noise), so the
+ * result decrypts to the sum of products, with one rounding error per sum.
+ * ct: [2][ell][N]; galois[k], gks[k] ([ndig][2][L+alpha][N]) for k < nrot;
+ * pts: [nacc][nrot][N] centred plaintext coefficients, present[a*nrot+k] = 0
+ * for a zero diagonal; out: [nacc][2][ell][N].  No modulus switch here. */
+void or_matmul(const or_params *P, const u64 *ct, int ell, int nrot, const u64 *galois, const u64 *const *gks,
+               int nacc, const i64 *pts, const int *present, u64 *out)
+{
+    int N = P->N, nx = ell + P->alpha;
+    u64 Pmod[OR_MAXP];
+    for (int i = 0; i < ell; i++) {
+        Pmod[i] = 1;
+        for (int k = 0; k < P->alpha; k++) Pmod[i] = mulmod(Pmod[i], P->primes[P->L + k] % P->primes[i], P->primes[i]);
+    }
+    u64 *acc = calloc((size_t)nacc * 2 * nx * N, sizeof(u64));
+    u64 *tc = malloc(sizeof(u64) * 2 * ell * N), *R = malloc(sizeof(u64) * 2 * nx * N);
+    u64 *pr = malloc(sizeof(u64) * N), *tmp = malloc(sizeof(u64) * N);
+    for (int k = 0; k < nrot; k++) {
+        u64 g = galois[k];
+        if (g == 1) continue;
+        int used = 0;
+        for (int a = 0; a < nacc; a++) used |= present[a * nrot + k];
+        if (!used) continue;
+        for (int c = 0; c < 2; c++)
+            for (int r = 0; r < ell; r++)
+                or_automorphism(ct + ((size_t)c * ell + r) * N, P->logN, P->primes[r], g, tc + ((size_t)c * ell + r) * N);
+        keyswitch_raw(P, tc + (size_t)ell * N, ell, gks[k], R);
+        for (int r = 0; r < ell; r++) {
+            u64 q = P->primes[r];
+            for (int j = 0; j < N; j++)
+                R[(size_t)r * N + j] = addmod(R[(size_t)r * N + j], mulmod(Pmod[r], tc[(size_t)r * N + j], q), q);
+        }
+        for (int a = 0; a < nacc; a++) {
+            if (!present[a * nrot + k]) continue;
+            const i64 *m = pts + ((size_t)a * nrot + k) * N;
+            for (int c = 0; c < 2; c++)
+                for (int r = 0; r < nx; r++) {
+                    int gi = ext_prime(P, ell, r);
+                    u64 q = P->primes[gi];
+                    for (int j = 0; j < N; j++) pr[j] = from_signed(m[j], q);
+                    poly_mul_acc(R + ((size_t)c * nx + r) * N, pr, P->logN, q, acc + (((size_t)a * 2 + c) * nx + r) * N);
+                }
+        }
+    }
+    for (int a = 0; a < nacc; a++) {
+        u64 *o = out + (size_t)a * 2 * ell * N;
+        u64 *ac = acc + (size_t)a * 2 * nx * N;
+        moddown(P, ac, ell, o);
+        moddown(P, ac + (size_t)nx * N, ell, o + (size_t)ell * N);
+        for (int k = 0; k < nrot; k++) {
+            if (galois[k] != 1 || !present[a * nrot + k]) continue;
+            const i64 *m = pts + ((size_t)a * nrot + k) * N;
+            for (int r = 0; r < ell; r++) {
+                u64 q = P->primes[r];
+                for (int j = 0; j < N; j++) pr[j] = from_signed(m[j], q);
+                for (int c = 0; c < 2; c++) {
+                    or_negacyclic_mul(ct + ((size_t)c * ell + r) * N, pr, P->logN, q, tmp);
+                    u64 *d = o + ((size_t)c * ell + r) * N;
+                    for (int j = 0; j < N; j++) d[j] = addmod(d[j], tmp[j], q);
+                }
+            }
+        }
+    }
+    free(acc); free(tc); free(R); free(pr); free(tmp);
 }
 
 /* (c0,c1) x (d0,d1) -> (c0d0, c0d1 + c1d0, c1d1), out [3][ell][N] */

@@ -323,17 +323,18 @@ def seccomp(E, X, Y_planes, p):
     return pairwise(leaves, combine)[0]
 
 
-def matmul(E, v, diags, add_vec=None):
-    """Diagonal method (Section 4.1.2, Matrix Multiplication): sum over the
-    nonzero diagonals of d_i * rot(v, i), plus an optional plaintext, then one
-    modulus switch."""
-    acc = None
-    for i in sorted(diags):
-        term = E.mul_plain(E.rot(v, i), diags[i])
-        acc = term if acc is None else E.add(acc, term)
-    if add_vec is not None:
-        acc = E.add_plain(acc, add_vec)
-    return E.rescale(acc)
+def matmul(E, v, diag_sets, add_vecs):
+    """Diagonal method (Section 4.1.2, Matrix Multiplication) for several matrices
+    applied to the same vector: for each matrix a, the sum over its nonzero
+    diagonals of d_i * rot(v, i), plus an optional plaintext, then one modulus
+    switch.  Rotations of v by the same amount serve every matrix."""
+    sums = E.diag_sums(v, diag_sets)
+    out = []
+    for acc, add in zip(sums, add_vecs):
+        if add is not None:
+            acc = E.add_plain(acc, add)
+        out.append(E.rescale(acc))
+    return out
 
 
 def infer(E, m: Model, X, N: int):
@@ -344,13 +345,9 @@ def infer(E, m: Model, X, N: int):
     Y = E.thresholds(m)
     D = seccomp(E, X, Y, m.precision)
     Rd = {i: tile_blocks(m, dg, N) for i, dg in reshuffle_diagonals(m).items()}
-    Br = matmul(E, D, Rd)
-    E.begin_shared_rotations(Br)
-    res = []
-    for k in range(1, m.d + 1):
-        Ld = {i: tile_blocks(m, dg, N) for i, dg in level_diagonals(m, k, t).items()}
-        res.append(matmul(E, Br, Ld, tile_blocks(m, m.mask[k - 1], N)))
-    E.end_shared_rotations()
+    Br = matmul(E, D, [Rd], [None])[0]
+    Ld = [{i: tile_blocks(m, dg, N) for i, dg in level_diagonals(m, k, t).items()} for k in range(1, m.d + 1)]
+    res = matmul(E, Br, Ld, [tile_blocks(m, m.mask[k - 1], N) for k in range(1, m.d + 1)])
     return pairwise(res, lambda a, b, root: E.mul(a, b))
 
 
@@ -391,19 +388,24 @@ class SlotEngine:
     def rescale(self, a):
         return a
 
-    def begin_shared_rotations(self, v):
-        pass
-
-    def end_shared_rotations(self):
-        pass
+    def diag_sums(self, v, diag_sets):
+        out = []
+        for diags in diag_sets:
+            acc = np.zeros(self.N, dtype=np.int64)
+            for i in sorted(diags):
+                acc = (acc + diags[i] * self.rot(v, i)) % self.t
+            out.append(acc)
+        return out
 
 
 class BgvEngine:
     """The same circuit on BGV ciphertexts with the canonical policy: after every
     multiplication (ct x ct after relinearisation; after each affine plaintext
     step and after each matrix product) drop one prime; before a binary
-    operation bring the operand at the higher level down.  Rotations of one
-    ciphertext by the same amount are computed once and reused."""
+    operation bring the operand at the higher level down.  The products of one
+    vector with several matrices share its rotations, and each sum of
+    diagonal products takes the modulus-down step of key switching once
+    (Bgv.matmul)."""
 
     def __init__(self, bgv: B.Bgv, keys: B.Keys, encrypted_model=False, enc_model=None):
         self.b, self.k = bgv, keys
@@ -411,8 +413,6 @@ class BgvEngine:
         self.N, self.t = self.P.N, self.P.t
         self.encrypted_model = encrypted_model
         self.enc_model = enc_model
-        self._memo_src = None
-        self._memo = {}
         self.counts = {"rot": 0, "mul": 0, "mul_plain": 0, "modswitch_ops": 0}
 
     def thresholds(self, m):
@@ -421,22 +421,20 @@ class BgvEngine:
         return threshold_planes(m, self.N)
 
     def rot(self, v, i):
+        """One rotation with its own modulus-down step (used to time single operations)."""
         if i == 0:
             return v
-        if self._memo_src is v and i in self._memo:
-            return self._memo[i]
         g = B.galois_rot(self.P.logN, i)
-        r = self.b.rotate(v, g, self.k.gk[g])
-        self.counts["rot"] += 1
-        if self._memo_src is v:
-            self._memo[i] = r
-        return r
+        return self.b.rotate(v, g, self.k.gk[g])
 
-    def begin_shared_rotations(self, v):
-        self._memo_src, self._memo = v, {}
-
-    def end_shared_rotations(self):
-        self._memo_src, self._memo = None, {}
+    def diag_sums(self, v, diag_sets):
+        rots = sorted(set(i for d in diag_sets for i in d))
+        galois = [B.galois_rot(self.P.logN, i) if i else 1 for i in rots]
+        gks = [self.k.gk[g] if g != 1 else None for g in galois]
+        pts = [[B.encode(self.P, d[i]) if i in d else None for i in rots] for d in diag_sets]
+        self.counts["rot"] += sum(1 for i in rots if i)
+        self.counts["mul_plain"] += sum(len(d) for d in diag_sets)
+        return self.b.matmul(v, galois, gks, pts)
 
     def mul(self, a, b):
         self.counts["mul"] += 1

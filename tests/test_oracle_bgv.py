@@ -162,3 +162,41 @@ def test_noise_budget_consumption():
         assert bgv.noise_bits(keys.sk, cur) < fresh + 8
     assert bgv.budget_bits(keys.sk, cur) > 10
     assert np.array_equal(bgv.decrypt_slots(keys.sk, cur).astype(np.int64), a)
+
+
+@pytest.mark.parametrize("k", [1, 5])
+def test_matmul_with_unit_diagonal_is_rotation(k):
+    """ModDown(U + P x) = ModDown(U) + x exactly, so a one-rotation product with the
+    constant plaintext 1 must equal the rotation operation bit for bit."""
+    logN = 6
+    g = B.galois_rot(logN, k)
+    P, bgv, keys = _setup(logN, 5, 50, 2, galois=[g])
+    rng = np.random.default_rng(k)
+    ct = bgv.encrypt_slots(keys.pk, rng.integers(0, T, size=P.N), 3, 0)
+    one = B.encode(P, np.ones(P.N, dtype=np.int64))
+    (got,) = bgv.matmul(ct, [g], [keys.gk[g]], [[one]])
+    assert np.array_equal(got, bgv.rotate(ct, g, keys.gk[g]))
+    # the identity term alone is the plaintext product
+    (ident,) = bgv.matmul(ct, [1], [None], [[one]])
+    assert np.array_equal(ident, ct)
+
+
+def test_matmul_slot_semantics():
+    """Two accumulators over shared rotations decrypt to sum_i d_i * rot(v, i)."""
+    logN = 6
+    ks = [0, 1, 3, 10]
+    gal = [B.galois_rot(logN, k) if k else 1 for k in ks]
+    P, bgv, keys = _setup(logN, 5, 50, 2, galois=[g for g in gal if g != 1])
+    rng = np.random.default_rng(2)
+    v = rng.integers(0, 2, size=P.N)
+    ct = bgv.encrypt_slots(keys.pk, v, 3, 0)
+    diags = [[rng.integers(0, 3, size=P.N) for _ in ks], [rng.integers(0, 2, size=P.N) if j != 2 else None
+                                                           for j in range(len(ks))]]
+    pts = [[None if d is None else B.encode(P, d) for d in row] for row in diags]
+    outs = bgv.matmul(ct, gal, [keys.gk[g] if g != 1 else None for g in gal], pts)
+    for row, out in zip(diags, outs):
+        want = np.zeros(P.N, dtype=np.int64)
+        for k, d in zip(ks, row):
+            if d is not None:
+                want = (want + d * _rot(v, k, P.N)) % T
+        assert np.array_equal(bgv.decrypt_slots(keys.sk, out).astype(np.int64), want)
