@@ -183,6 +183,28 @@ copse_status copse_decrypt_labels(copse_ctx *ctx, const copse_keys *keys, const 
 copse_status copse_decrypt_slots(copse_ctx *ctx, const copse_keys *keys, const copse_ctbuf *buf, size_t index,
                                  uint64_t *out_slots);
 
+/* ---------------------------------------------------------------- sessions
+ * A session fixes the context, keys, model and number of queries and records
+ * one whole secure inference -- feature encryption (Section 3.3, Step 0),
+ * Algorithm 1 (Section 4.3) and decryption of the leaf bits -- as a CUDA
+ * graph, replayed by every run.  The same per-model operation sequence is
+ * reused for every batch of queries; results equal copse_encrypt_features +
+ * copse_infer + copse_decrypt_labels with the same seed. */
+typedef struct copse_session copse_session;
+
+/* Record the graph (uploads the model's plaintexts first; synchronous).
+ * n_queries <= N / block.  keys, evk and model must outlive the session. */
+copse_status copse_session_create(copse_ctx *ctx, const copse_keys *keys, const copse_evk *evk,
+                                  copse_model *model, size_t n_queries, copse_session **out);
+/* One step: feats[n_queries * n_features] (host if feats_on_device = 0, else
+ * device), fresh encryption randomness from `seed`, leaf bits into
+ * out_bits[n_queries * n_leaves] (host if out_on_device = 0: the call then
+ * synchronises; else device: async).  Runs on `stream`; runs of one session
+ * must not overlap (they share the session's buffers). */
+copse_status copse_session_run(copse_session *session, const uint32_t *feats, int feats_on_device, uint64_t seed,
+                               uint8_t *out_bits, int out_on_device, void *stream);
+void copse_session_destroy(copse_session *session);
+
 /* ---------------------------------------------------------------- buffers */
 
 size_t copse_ctbuf_count(const copse_ctbuf *buf);

@@ -348,3 +348,37 @@ def copse_poly_mul_noalloc(ctx, a_ptr, b_ptr, c_ptr, n_res, stream=None):
     """copse_poly_mul without any allocation (fixed device scratch; see include/copse.h)."""
     _check(_lib.copse_poly_mul_noalloc(ctx, C.c_void_p(a_ptr), C.c_void_p(b_ptr), C.c_void_p(c_ptr), n_res,
                                        C.c_void_p(stream)))
+
+
+# ---------------------------------------------------------------- sessions (CUDA graphs)
+_lib.copse_session_create.restype = C.c_int
+_lib.copse_session_create.argtypes = [vp, vp, vp, vp, C.c_size_t, pvp]
+_lib.copse_session_run.restype = C.c_int
+_lib.copse_session_run.argtypes = [vp, vp, C.c_int, C.c_uint64, vp, C.c_int, vp]
+_lib.copse_session_destroy.restype = None
+_lib.copse_session_destroy.argtypes = [vp]
+
+
+def copse_session_create(ctx, keys, evk, model, n_queries):
+    h = C.c_void_p()
+    _check(_lib.copse_session_create(ctx, keys, evk, model, n_queries, C.byref(h)))
+    return h
+
+
+def copse_session_run(session, feats, seed, out=None, stream=None, feats_ptr=None, out_ptr=None):
+    """feats: host numpy [n, n_features] or feats_ptr (device); result into `out` (host numpy
+    uint8 [n, n_leaves], returned) or out_ptr (device, async)."""
+    if feats_ptr is not None:
+        fp, fd = C.c_void_p(feats_ptr), 1
+    else:
+        f = np.ascontiguousarray(feats, dtype=np.uint32)
+        fp, fd = _ptr(f), 0
+    if out_ptr is not None:
+        _check(_lib.copse_session_run(session, fp, fd, seed, C.c_void_p(out_ptr), 1, C.c_void_p(stream)))
+        return None
+    _check(_lib.copse_session_run(session, fp, fd, seed, _ptr(out), 0, C.c_void_p(stream)))
+    return out
+
+
+def copse_session_destroy(session):
+    _lib.copse_session_destroy(session)

@@ -54,7 +54,7 @@ static copse_status upload_model(copse_ctx *c, copse_model *m, cudaStream_t s) {
     }
     auto D = std::make_unique<DeviceModel>();
     D->ctx = c;
-    const int N = c->N, L = c->L, p = (int)f.precision, B = (int)f.block;
+    const int N = c->N, L = c->L, A = c->alpha, p = (int)f.precision, B = (int)f.block;
     D->lvl_D = L - 1 - (int)clog2u(f.precision);
     D->lvl_B = D->lvl_D - 1;
     const u64 t = c->t;
@@ -74,7 +74,7 @@ static copse_status upload_model(copse_ctx *c, copse_model *m, cudaStream_t s) {
             lvl_nz[k - 1][r] = nz;
             nlvl += nz;
         }
-    const size_t words = (nleaf * L + D->rot_R.size() * D->lvl_D + (nlvl + f.d) * D->lvl_B) * (size_t)N;
+    const size_t words = (nleaf * L + D->rot_R.size() * (D->lvl_D + A) + nlvl * (D->lvl_B + A) + f.d * D->lvl_B) * (size_t)N;
     CUDA_TRY(cudaMalloc(&D->store, std::max<size_t>(words, 1) * sizeof(u64)));
     u64 *cur = D->store;
     // SecComp leaf plaintexts over whole blocks (threshold bit 0 past the decisions)
@@ -89,7 +89,7 @@ static copse_status upload_model(copse_ctx *c, copse_model *m, cudaStream_t s) {
                 pat[(3 * p + i) * (size_t)B + x] = y ? 0u : 1u;
             }
         }
-        STATUS_TRY(encode_patterns(c, pat, (int)nleaf, B, B, L, cur, s));
+        STATUS_TRY(encode_patterns(c, pat, (int)nleaf, B, B, L, 0, cur, s));
         for (int i = 0; i < p; i++) {
             D->lt_mul.push_back(cur + ((size_t)(0 * p + i) * L) * N);
             D->lt_add.push_back(cur + ((size_t)(1 * p + i) * L) * N);
@@ -106,15 +106,18 @@ static copse_status upload_model(copse_ctx *c, copse_model *m, cudaStream_t s) {
             f.reshuffle_diagonal(D->rot_R[r], dg8);
             for (int x = 0; x < m1; x++) pat[r * m1 + x] = dg8[x];
         }
-        STATUS_TRY(encode_patterns(c, pat, (int)D->rot_R.size(), m1, B, D->lvl_D, cur, s));
+        // extended basis: the products are summed before the key switch's ModDown
+        const size_t w = (size_t)(D->lvl_D + A) * N;
+        STATUS_TRY(encode_patterns(c, pat, (int)D->rot_R.size(), m1, B, D->lvl_D, A, cur, s));
         D->pt_R.assign(1, std::vector<const u64 *>());
-        for (size_t r = 0; r < D->rot_R.size(); r++) D->pt_R[0].push_back(cur + r * D->lvl_D * (size_t)N);
-        cur += D->rot_R.size() * D->lvl_D * (size_t)N;
+        for (size_t r = 0; r < D->rot_R.size(); r++) D->pt_R[0].push_back(cur + r * w);
+        cur += D->rot_R.size() * w;
     }
-    // level diagonals (signed, mask folded in) and masks at the level of Branches
+    // level diagonals (signed, mask folded in; extended basis) and masks at the level of Branches
     {
         const int Lf = (int)f.L;
-        std::vector<uint32_t> pat((nlvl + f.d) * (size_t)Lf);
+        const size_t w = (size_t)(D->lvl_B + A) * N;
+        std::vector<uint32_t> pat(nlvl * (size_t)Lf);
         size_t at = 0;
         D->pt_B.assign(f.d, std::vector<const u64 *>(D->rot_B.size(), nullptr));
         for (uint32_t k = 1; k <= f.d; k++)
@@ -122,15 +125,17 @@ static copse_status upload_model(copse_ctx *c, copse_model *m, cudaStream_t s) {
                 if (!lvl_nz[k - 1][r]) continue;
                 f.level_diagonal(k, D->rot_B[r], t, dg64);
                 for (int x = 0; x < Lf; x++) pat[at * Lf + x] = (uint32_t)dg64[x];
-                D->pt_B[k - 1][r] = cur + at * D->lvl_B * (size_t)N;
+                D->pt_B[k - 1][r] = cur + at * w;
                 at++;
             }
+        STATUS_TRY(encode_patterns(c, pat, (int)at, Lf, B, D->lvl_B, A, cur, s));
+        cur += at * w;
+        std::vector<uint32_t> mpat((size_t)f.d * Lf);
         for (uint32_t k = 1; k <= f.d; k++) {
-            for (int x = 0; x < Lf; x++) pat[at * Lf + x] = f.mask[(size_t)(k - 1) * Lf + x];
-            D->mask.push_back(cur + at * D->lvl_B * (size_t)N);
-            at++;
+            for (int x = 0; x < Lf; x++) mpat[(size_t)(k - 1) * Lf + x] = f.mask[(size_t)(k - 1) * Lf + x];
+            D->mask.push_back(cur + (size_t)(k - 1) * D->lvl_B * N);
         }
-        STATUS_TRY(encode_patterns(c, pat, (int)at, Lf, B, D->lvl_B, cur, s));
+        STATUS_TRY(encode_patterns(c, mpat, (int)f.d, Lf, B, D->lvl_B, 0, cur, s));
     }
     CUDA_TRY(cudaStreamSynchronize(s));
     m->dev = std::move(D);
@@ -309,33 +314,42 @@ static copse_status infer_impl(copse_ctx *c, const copse_evk *evk, copse_model *
     for (const DCt &x : feats->cts)
         if (x.level != c->L) { set_error("feature ciphertexts must be fresh"); return COPSE_EINVAL; }
     struct Node { DCt lt, eq; };
+    // Independent operations of one step run on forked side streams and are
+    // joined back onto s; every free happens on s after the join.
     // SecComp leaves, most significant plane first: lt = (1 - x) y, eq = [x == y]
-    std::vector<Node> nodes;
-    for (int i = p - 1; i >= 0; i--) {
-        Node nd;
+    std::vector<Node> nodes(p);
+    STATUS_TRY(fork_begin(c, s, 2 * p));
+    for (int k = 0; k < p; k++) {
+        const int i = p - 1 - k;
         DPt lm{c->L, (u64 *)D.lt_mul[i]}, la{c->L, (u64 *)D.lt_add[i]};
         DPt em{c->L, (u64 *)D.eq_mul[i]}, ea{c->L, (u64 *)D.eq_add[i]};
-        STATUS_TRY(op_affine(c, feats->cts[i], lm, &la, &nd.lt, s));
-        STATUS_TRY(op_affine(c, feats->cts[i], em, &ea, &nd.eq, s));
-        nodes.push_back(nd);
+        STATUS_TRY(op_affine(c, feats->cts[i], lm, &la, &nodes[k].lt, fork_stream(c, 2 * k)));
+        STATUS_TRY(op_affine(c, feats->cts[i], em, &ea, &nodes[k].eq, fork_stream(c, 2 * k + 1)));
     }
+    STATUS_TRY(fork_join(c, s, 2 * p));
     // balanced combine (lt_h + eq_h lt_l, eq_h eq_l); no eq at the root
     while (nodes.size() > 1) {
-        std::vector<Node> nx;
         const bool root = nodes.size() == 2;
-        for (size_t k = 0; k + 1 < nodes.size(); k += 2) {
-            Node &hi = nodes[k], &lo = nodes[k + 1];
-            Node r;
-            DCt prod;
-            STATUS_TRY(op_mul(c, evk, hi.eq, lo.lt, &prod, s));
-            STATUS_TRY(op_add(c, hi.lt, prod, &r.lt, false, s));
-            ct_free(&prod, s);
-            if (!root) STATUS_TRY(op_mul(c, evk, hi.eq, lo.eq, &r.eq, s));
-            ct_free(&hi.lt, s);
-            ct_free(&hi.eq, s);
-            ct_free(&lo.lt, s);
-            ct_free(&lo.eq, s);
-            nx.push_back(r);
+        const int npair = (int)(nodes.size() / 2);
+        std::vector<Node> nx(npair);
+        std::vector<DCt> prod(npair);
+        STATUS_TRY(fork_begin(c, s, 2 * npair));
+        for (int k = 0; k < npair; k++) {
+            Node &hi = nodes[2 * k], &lo = nodes[2 * k + 1];
+            STATUS_TRY(op_mul(c, evk, hi.eq, lo.lt, &prod[k], fork_stream(c, 2 * k)));
+            if (!root) STATUS_TRY(op_mul(c, evk, hi.eq, lo.eq, &nx[k].eq, fork_stream(c, 2 * k + 1)));
+        }
+        STATUS_TRY(fork_join(c, s, 2 * npair));
+        STATUS_TRY(fork_begin(c, s, npair));
+        for (int k = 0; k < npair; k++)
+            STATUS_TRY(op_add(c, nodes[2 * k].lt, prod[k], &nx[k].lt, false, fork_stream(c, k)));
+        STATUS_TRY(fork_join(c, s, npair));
+        for (int k = 0; k < npair; k++) {
+            ct_free(&prod[k], s);
+            for (Node *n : {&nodes[2 * k], &nodes[2 * k + 1]}) {
+                ct_free(&n->lt, s);
+                ct_free(&n->eq, s);
+            }
         }
         if (nodes.size() % 2) nx.push_back(nodes.back());
         nodes.swap(nx);
@@ -353,14 +367,13 @@ static copse_status infer_impl(copse_ctx *c, const copse_evk *evk, copse_model *
     ct_free(&br[0], s);
     // product across levels, balanced
     while (lv.size() > 1) {
-        std::vector<DCt> nx;
-        for (size_t k = 0; k + 1 < lv.size(); k += 2) {
-            DCt r;
-            STATUS_TRY(op_mul(c, evk, lv[k], lv[k + 1], &r, s));
-            ct_free(&lv[k], s);
-            ct_free(&lv[k + 1], s);
-            nx.push_back(r);
-        }
+        const int npair = (int)(lv.size() / 2);
+        std::vector<DCt> nx(npair);
+        STATUS_TRY(fork_begin(c, s, npair));
+        for (int k = 0; k < npair; k++)
+            STATUS_TRY(op_mul(c, evk, lv[2 * k], lv[2 * k + 1], &nx[k], fork_stream(c, k)));
+        STATUS_TRY(fork_join(c, s, npair));
+        for (int k = 0; k < 2 * npair; k++) ct_free(&lv[k], s);
         if (lv.size() % 2) nx.push_back(lv.back());
         lv.swap(nx);
     }
@@ -499,7 +512,7 @@ extern "C" copse_status copse_ct_mul_plain(copse_ctx *c, const copse_ctbuf *a, s
     }
     u64 *pts = nullptr;
     STATUS_TRY(dev_alloc(c, (void **)&pts, (size_t)2 * x.level * N * 8, s));
-    STATUS_TRY(encode_patterns(c, pat, 2, N, N, x.level, pts, s));
+    STATUS_TRY(encode_patterns(c, pat, 2, N, N, x.level, 0, pts, s));
     DPt mp{x.level, pts}, ap{x.level, pts + (size_t)x.level * N};
     DCt r;
     copse_status st = op_affine(c, x, mp, add_slots ? &ap : nullptr, &r, s);
@@ -513,4 +526,128 @@ extern "C" copse_status copse_ntt(copse_ctx *c, uint64_t *data, size_t n_polys, 
     if (!c || !data || n_res < 1 || (int)n_res > c->L) { set_error("bad argument"); return COPSE_EINVAL; }
     NttBatch b{data, (size_t)n_res * c->N, (int)n_polys, 0, (int)n_res, (int)n_res, -1};
     return inverse ? ntt_inverse(c, b, as_stream(stream)) : ntt_forward(c, b, as_stream(stream));
+}
+
+// ---------------------------------------------------------------- sessions (CUDA graphs)
+// A session fixes (context, keys, model, number of queries) and captures the
+// whole step -- feature encryption, Algorithm 1, decryption of the leaf bits --
+// once as a CUDA graph.  Every run copies the features and a fresh seed into
+// the session's device buffers and launches the graph: no host-side kernel
+// launches, allocations or synchronisation inside the step.  Intermediates are
+// graph memory nodes allocated and freed inside the graph.
+struct copse_session {
+    copse_ctx *c = nullptr;
+    const copse_keys *keys = nullptr;
+    const copse_evk *evk = nullptr;
+    copse_model *m = nullptr;
+    size_t nq = 0;
+    uint32_t *d_feats = nullptr;  // [nq][n_features]
+    uint8_t *d_bits = nullptr;    // [nq][n_leaves]
+    u64 *d_seed = nullptr;        // encryption seed of the next run
+    cudaStream_t cap = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    ~copse_session() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        if (cap) cudaStreamDestroy(cap);
+        cudaFree(d_feats);
+        cudaFree(d_bits);
+        cudaFree(d_seed);
+    }
+};
+
+// the captured body: everything it allocates it also frees
+static copse_status session_body(copse_session *S, cudaStream_t s) {
+    copse_ctx *c = S->c;
+    const CompiledForest &f = S->m->f;
+    copse_ctbuf feats;
+    feats.ctx = c;
+    feats.stream = s;
+    STATUS_TRY(encrypt_planes(c, S->keys, S->d_feats, (int)S->nq, (int)f.n_features, (int)f.K, (int)f.q, (int)f.pd(),
+                              (int)f.block, (int)f.precision, 0, feats.cts, s, S->d_seed));
+    DCt res;
+    STATUS_TRY(infer_impl(c, S->evk, S->m, &feats, &res, s));
+    u64 *slots = nullptr;
+    STATUS_TRY(dev_alloc(c, (void **)&slots, (size_t)c->N * 8, s));
+    STATUS_TRY(decrypt_slots_dev(c, S->keys, res, slots, s));
+    STATUS_TRY(extract_bits(c, slots, (int)S->nq, (int)f.block, (int)f.L, S->d_bits, s));
+    dev_free(slots, s);
+    ct_free(&res, s);
+    return COPSE_OK;  // feats frees its ciphertexts on s when it goes out of scope
+}
+
+extern "C" copse_status copse_session_create(copse_ctx *c, const copse_keys *keys, const copse_evk *evk,
+                                             copse_model *m, size_t n_queries, copse_session **out) {
+    if (!c || !keys || !evk || !m || !out) { set_error("null argument"); return COPSE_EINVAL; }
+    const CompiledForest &f = m->f;
+    if ((int)f.log_n != c->logN) { set_error("model compiled for another ring degree"); return COPSE_EINVAL; }
+    if (n_queries > (size_t)(c->N / f.block)) { set_error("more queries than slot blocks"); return COPSE_EINVAL; }
+    auto S = std::make_unique<copse_session>();
+    S->c = c;
+    S->keys = keys;
+    S->evk = evk;
+    S->m = m;
+    S->nq = n_queries;
+    CUDA_TRY(cudaSetDevice(c->device));
+    CUDA_TRY(cudaMalloc(&S->d_feats, std::max<size_t>(n_queries * f.n_features, 1) * 4));
+    CUDA_TRY(cudaMalloc(&S->d_bits, std::max<size_t>(n_queries * f.L, 1)));
+    CUDA_TRY(cudaMalloc(&S->d_seed, 8));
+    CUDA_TRY(cudaMemset(S->d_feats, 0, std::max<size_t>(n_queries * f.n_features, 1) * 4));
+    CUDA_TRY(cudaMemset(S->d_seed, 0, 8));
+    CUDA_TRY(cudaStreamCreateWithFlags(&S->cap, cudaStreamNonBlocking));
+    // everything that synchronises or allocates outside the stream happens before capture
+    STATUS_TRY(upload_model(c, m, S->cap));
+    STATUS_TRY(fork_begin(c, S->cap, 0));
+    CUDA_TRY(cudaStreamSynchronize(S->cap));
+    stats_suspend(true);
+    c->capturing = true;
+    cudaError_t e = cudaStreamBeginCapture(S->cap, cudaStreamCaptureModeThreadLocal);
+    copse_status st = e == cudaSuccess ? session_body(S.get(), S->cap) : COPSE_ECUDA;
+    if (e != cudaSuccess) set_error(std::string("cudaStreamBeginCapture: ") + cudaGetErrorString(e));
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(S->cap, &g);
+    c->capturing = false;
+    stats_suspend(false);
+    if (st != COPSE_OK) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return st;
+    }
+    if (e2 != cudaSuccess || !g) {
+        set_error(std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e2));
+        return COPSE_ECUDA;
+    }
+    S->graph = g;
+    CUDA_TRY(cudaGraphInstantiate(&S->exec, g, 0));
+    *out = S.release();
+    return COPSE_OK;
+}
+
+extern "C" copse_status copse_session_run(copse_session *S, const uint32_t *feats, int feats_on_device,
+                                          uint64_t seed, uint8_t *out_bits, int out_on_device, void *stream) {
+    if (!S || (S->nq && (!feats || !out_bits))) { set_error("null argument"); return COPSE_EINVAL; }
+    cudaStream_t s = as_stream(stream);
+    const CompiledForest &f = S->m->f;
+    const size_t nfe = S->nq * f.n_features, nb = S->nq * f.L;
+    if (!feats_on_device)
+        for (size_t i = 0; i < nfe; i++)
+            if (f.precision < 32 && feats[i] >= (1u << f.precision)) { set_error("feature value needs more bits than the precision"); return COPSE_EINVAL; }
+    if (nfe)
+        CUDA_TRY(cudaMemcpyAsync(S->d_feats, feats, nfe * 4,
+                                 feats_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    // pageable source: the copy is staged before this call returns, so `seed` may go out of scope
+    CUDA_TRY(cudaMemcpyAsync(S->d_seed, &seed, 8, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaGraphLaunch(S->exec, s));
+    if (nb)
+        CUDA_TRY(cudaMemcpyAsync(out_bits, S->d_bits, nb, out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                 s));
+    if (!out_on_device) CUDA_TRY(cudaStreamSynchronize(s));
+    return COPSE_OK;
+}
+
+extern "C" void copse_session_destroy(copse_session *S) {
+    if (!S) return;
+    cudaDeviceSynchronize();
+    delete S;
 }

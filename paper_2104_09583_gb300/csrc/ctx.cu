@@ -66,7 +66,9 @@ static uint32_t h_brev(uint32_t x, int bits) {
 // ---------------------------------------------------------------- memory
 copse_status dev_alloc(copse_ctx *ctx, void **p, size_t bytes, cudaStream_t s) {
     if (bytes == 0) bytes = 256;
-    cudaError_t e = cudaMallocFromPoolAsync(p, bytes, ctx->pool, s);
+    // inside a stream capture the allocation becomes a graph memory node, whose
+    // memory the graph owns between launches
+    cudaError_t e = ctx->capturing ? cudaMallocAsync(p, bytes, s) : cudaMallocFromPoolAsync(p, bytes, ctx->pool, s);
     if (e != cudaSuccess) {
         set_error(std::string("device allocation of ") + std::to_string(bytes) + " bytes: " + cudaGetErrorString(e));
         cudaGetLastError();
@@ -76,6 +78,38 @@ copse_status dev_alloc(copse_ctx *ctx, void **p, size_t bytes, cudaStream_t s) {
 }
 void dev_free(void *p, cudaStream_t s) {
     if (p) cudaFreeAsync(p, s);
+}
+
+// ---------------------------------------------------------------- fork / join
+static copse_status ensure_side(copse_ctx *c) {
+    if (!c->side.empty()) return COPSE_OK;
+    CUDA_TRY(cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming));
+    for (int i = 0; i < COPSE_SIDE_STREAMS; i++) {
+        cudaStream_t st;
+        cudaEvent_t ev;
+        CUDA_TRY(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+        CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        c->side.push_back(st);
+        c->side_done.push_back(ev);
+    }
+    return COPSE_OK;
+}
+
+copse_status fork_begin(copse_ctx *c, cudaStream_t s, int n) {
+    STATUS_TRY(ensure_side(c));
+    CUDA_TRY(cudaEventRecord(c->fork_ev, s));
+    for (int i = 0; i < n && i < COPSE_SIDE_STREAMS; i++) CUDA_TRY(cudaStreamWaitEvent(c->side[i], c->fork_ev, 0));
+    return COPSE_OK;
+}
+
+cudaStream_t fork_stream(copse_ctx *c, int i) { return c->side[i % COPSE_SIDE_STREAMS]; }
+
+copse_status fork_join(copse_ctx *c, cudaStream_t s, int n) {
+    for (int i = 0; i < n && i < COPSE_SIDE_STREAMS; i++) {
+        CUDA_TRY(cudaEventRecord(c->side_done[i], c->side[i]));
+        CUDA_TRY(cudaStreamWaitEvent(s, c->side_done[i], 0));
+    }
+    return COPSE_OK;
 }
 
 template <class T>
@@ -262,6 +296,9 @@ extern "C" void copse_ctx_destroy(copse_ctx *c) {
     if (!c) return;
     cudaSetDevice(c->device);
     cudaDeviceSynchronize();
+    for (cudaStream_t st : c->side) cudaStreamDestroy(st);
+    for (cudaEvent_t ev : c->side_done) cudaEventDestroy(ev);
+    if (c->fork_ev) cudaEventDestroy(c->fork_ev);
     for (void *p : c->owned) cudaFree(p);
     if (c->pool) cudaMemPoolDestroy(c->pool);
     delete c;

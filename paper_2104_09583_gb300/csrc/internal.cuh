@@ -44,6 +44,7 @@ void set_error(const std::string &msg);
 // kernel timing (stats.cu): brackets a launch with CUDA events when enabled
 int stats_begin(const char *name, double bytes, cudaStream_t s);
 void stats_end(int token, cudaStream_t s);
+void stats_suspend(bool on);
 #define TIMED(name, bytes, s, ...)                                                               \
     do {                                                                                         \
         int tk__ = stats_begin(name, (double)(bytes), s);                                        \
@@ -157,10 +158,23 @@ struct copse_ctx {
     KsTables ks{};
     std::vector<void *> owned;        // device allocations freed with the context
     cudaMemPool_t pool = nullptr;
+    // side streams for independent operations of one inference (fork/join with events)
+    std::vector<cudaStream_t> side;
+    std::vector<cudaEvent_t> side_done;
+    cudaEvent_t fork_ev = nullptr;
+    // set while a graph is being captured: allocations become graph memory nodes
+    bool capturing = false;
 
     int ext_prime(int ell, int r) const { return r < ell ? r : L + (r - ell); }
     int t_index() const { return L + alpha; }
 };
+
+// Fork n independent branches off stream s: branch i runs on fork_stream(c, i)
+// after everything already queued on s; fork_join makes s wait for all n.
+copse_status fork_begin(copse_ctx *c, cudaStream_t s, int n);
+cudaStream_t fork_stream(copse_ctx *c, int i);
+copse_status fork_join(copse_ctx *c, cudaStream_t s, int n);
+#define COPSE_SIDE_STREAMS 16
 
 // device memory from the context's stream-ordered pool
 copse_status dev_alloc(copse_ctx *ctx, void **p, size_t bytes, cudaStream_t s);
@@ -233,21 +247,27 @@ copse_status op_add(copse_ctx *c, const DCt &a, const DCt &b, DCt *out, bool neg
 copse_status op_mul(copse_ctx *c, const copse_evk *evk, const DCt &a, const DCt &b, DCt *out, cudaStream_t s);
 copse_status op_affine(copse_ctx *c, const DCt &x, const DPt &mul, const DPt *add, DCt *out, cudaStream_t s);
 copse_status op_rotate(copse_ctx *c, const copse_evk *evk, const DCt &a, uint32_t k, DCt *out, cudaStream_t s);
-// Hoisted diagonal products: for each accumulator a, out[a] = modswitch(
-//   sum_k pt[a][k] * rot(v, rots[k]) + add[a]); pt[a][k] may be null (zero diagonal),
-// rots[k] = 0 means v itself.  pt pointers are NTT-domain [v.level][N].
+// Diagonal products sharing the rotations of v: for each accumulator a,
+//   out[a] = modswitch(ModDown(sum_{k: rots[k] != 0} pt[a][k] * R_k) + pt[a][k0] * v + add[a])
+// with R_k the rotation by rots[k] before its ModDown (one ModUp of v serves all k)
+// and k0 the zero rotation if present.  pt[a][k] may be null (zero diagonal);
+// pt pointers are NTT-domain [v.level + alpha][N] (extended basis), add[a] [v.level][N].
 copse_status op_matmul(copse_ctx *c, const copse_evk *evk, const DCt &v, const std::vector<uint32_t> &rots,
                        const std::vector<std::vector<const u64 *>> &pt, const std::vector<const u64 *> &add,
                        std::vector<DCt> &out, cudaStream_t s);
 // encode host slot patterns: n patterns of `len` values mod t, repeated every
-// `period` slots (period divides N; len <= period), into NTT-domain plaintexts at `level`
+// `period` slots (period divides N; len <= period), into NTT-domain plaintexts
+// [n][level + ext_alpha][N] over q_0..q_{level-1} and, when ext_alpha > 0, the
+// first ext_alpha special primes
 copse_status encode_patterns(copse_ctx *c, const std::vector<uint32_t> &patterns, int n, int len, int period,
-                             int level, u64 *out, cudaStream_t s);
+                             int level, int ext_alpha, u64 *out, cudaStream_t s);
 copse_status keygen_dev(copse_ctx *c, u64 seed, const std::vector<u64> &galois, copse_keys **keys, copse_evk **evk);
 // p planes for n queries: feats [n][nf] (device), layout of the model given by
 // K, q, pd, block
+// (d_seed: when set, the seed is read from that device word instead of `seed`)
 copse_status encrypt_planes(copse_ctx *c, const copse_keys *k, const uint32_t *d_feats, int nq, int nf, int K,
-                            int q, int pd, int block, int p, u64 seed, std::vector<DCt> &out, cudaStream_t s);
+                            int q, int pd, int block, int p, u64 seed, std::vector<DCt> &out, cudaStream_t s,
+                            const u64 *d_seed = nullptr);
 // decrypt to N slot values (device output, NTT(mod t) order remapped to slot order)
 copse_status decrypt_slots_dev(copse_ctx *c, const copse_keys *k, const DCt &ct, u64 *d_slots, cudaStream_t s);
 copse_status extract_bits(copse_ctx *c, const u64 *d_slots, int nq, int block, int L, uint8_t *d_bits,

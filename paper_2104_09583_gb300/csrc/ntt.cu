@@ -13,10 +13,12 @@
 // rows of N2 contiguous coefficients.  The first log2(N1) forward stages pair
 // coefficients of the same column; the last log2(N2) pair coefficients of the
 // same row.  Each pass stages a 16 KB tile (columns x all rows, or rows x all
-// columns) in shared memory, so one polynomial spreads over N / 2048 CTAs per
-// pass and a launch fills the GPU even for a few dozen polynomials; the
-// intermediate round trip stays in L2.  Small rings use one CTA per
-// polynomial.
+// columns) in shared memory together with every twiddle the tile needs (one
+// coalesced load up front instead of a dependent global load per stage), and
+// runs two stages per barrier as radix-4 butterflies in registers.  One
+// polynomial spreads over N / 2048 CTAs per pass, so a launch fills the GPU
+// even for a few dozen polynomials; the intermediate round trip stays in L2.
+// Small rings use one CTA per polynomial.
 #include "internal.cuh"
 
 namespace {
@@ -33,23 +35,26 @@ __device__ __forceinline__ bool ntt_skipped(const NttBatch &b, int p, int r) {
     return b.skip_alpha > 0 && r >= p * b.skip_alpha && r < min((p + 1) * b.skip_alpha, b.ell);
 }
 
-// forward butterfly on shared memory, values in [0, 4q)
-__device__ __forceinline__ void bf_fwd(u64 *x, u64 *y, u64 w, u64 wp, u64 q, u64 q2) {
-    u64 U = *x;
+// forward butterfly, values in [0, 4q)
+__device__ __forceinline__ void bfv_fwd(u64 &x, u64 &y, u64 w, u64 wp, u64 q, u64 q2) {
+    u64 U = x;
     if (U >= q2) U -= q2;
-    const u64 V = mul_shoup_lazy(*y, w, wp, q);
-    *x = U + V;
-    *y = U - V + q2;
+    const u64 V = mul_shoup_lazy(y, w, wp, q);
+    x = U + V;
+    y = U - V + q2;
 }
 
-// inverse butterfly on shared memory, values in [0, 2q)
-__device__ __forceinline__ void bf_inv(u64 *x, u64 *y, u64 w, u64 wp, u64 q, u64 q2) {
-    const u64 U = *x, V = *y;
+// inverse butterfly, values in [0, 2q)
+__device__ __forceinline__ void bfv_inv(u64 &x, u64 &y, u64 w, u64 wp, u64 q, u64 q2) {
+    const u64 U = x, V = y;
     u64 s = U + V;
     if (s >= q2) s -= q2;
-    *x = s;
-    *y = mul_shoup_lazy(U - V + q2, w, wp, q);
+    x = s;
+    y = mul_shoup_lazy(U - V + q2, w, wp, q);
 }
+
+__device__ __forceinline__ void bf_fwd(u64 *x, u64 *y, u64 w, u64 wp, u64 q, u64 q2) { bfv_fwd(*x, *y, w, wp, q, q2); }
+__device__ __forceinline__ void bf_inv(u64 *x, u64 *y, u64 w, u64 wp, u64 q, u64 q2) { bfv_inv(*x, *y, w, wp, q, q2); }
 
 // ---------------------------------------------------------------- one CTA per polynomial
 __global__ void __launch_bounds__(512) k_ntt_fwd(NttBatch b, const PrimeDev *__restrict__ primes,
@@ -109,140 +114,227 @@ __global__ void __launch_bounds__(512) k_ntt_inv(NttBatch b, const PrimeDev *__r
 }
 
 // ---------------------------------------------------------------- two passes (N = N1 x N2)
+// A tile holds TILE / S independent sequences of length S = 2^ls (columns of a
+// column tile, rows of a row tile); element i of sequence g sits at sm[IX(g, i)].
+// TW(u, g, il) is the shared-memory index of the twiddle of local stage u and
+// local group il of sequence g.
+
+// forward stages 0 .. ls-1 of every sequence: radix-4 pairs of stages, then a radix-2 stage if ls is odd
+// work item x -> (sequence g, index j within the sequence's 2^nb items); when the
+// sequences are columns of a row-major tile, consecutive threads take consecutive
+// columns so that a warp touches consecutive words (no bank conflicts)
+template <bool SEQ_FAST>
+__device__ __forceinline__ void split_item(int x, int ls, int nb, int &g, int &j) {
+    if (SEQ_FAST) {
+        const int lg = 11 - ls;  // log2 of the number of sequences in the tile
+        g = x & ((1 << lg) - 1);
+        j = x >> lg;
+    } else {
+        g = x >> nb;
+        j = x & ((1 << nb) - 1);
+    }
+}
+
+template <bool SEQ_FAST, class IX, class TWI>
+__device__ __forceinline__ void tile_fwd(u64 *sm, const u64 *tw, const u64 *twp, int ls, u64 q, u64 q2, IX ix,
+                                         TWI twi) {
+    int u = 0;
+    for (; u + 1 < ls; u += 2) {
+        const int lt = ls - 1 - u, tt = 1 << lt, h2 = tt >> 1;
+        for (int x = threadIdx.x; x < TILE / 4; x += NT2) {
+            int g, jq;
+            split_item<SEQ_FAST>(x, ls, ls - 2, g, jq);
+            const int il = jq >> (lt - 1), jj = jq & (h2 - 1);
+            const int i0 = (il << (lt + 1)) + jj;
+            const int a0 = ix(g, i0), a1 = ix(g, i0 + h2), a2 = ix(g, i0 + tt), a3 = ix(g, i0 + tt + h2);
+            u64 v0 = sm[a0], v1 = sm[a1], v2 = sm[a2], v3 = sm[a3];
+            const int t0 = twi(u, g, il);
+            bfv_fwd(v0, v2, tw[t0], twp[t0], q, q2);
+            bfv_fwd(v1, v3, tw[t0], twp[t0], q, q2);
+            const int ta = twi(u + 1, g, 2 * il), tb = twi(u + 1, g, 2 * il + 1);
+            bfv_fwd(v0, v1, tw[ta], twp[ta], q, q2);
+            bfv_fwd(v2, v3, tw[tb], twp[tb], q, q2);
+            sm[a0] = v0;
+            sm[a1] = v1;
+            sm[a2] = v2;
+            sm[a3] = v3;
+        }
+        __syncthreads();
+    }
+    if (u < ls) {  // last stage, distance 1
+        for (int x = threadIdx.x; x < TILE / 2; x += NT2) {
+            int g, il;
+            split_item<SEQ_FAST>(x, ls, ls - 1, g, il);
+            const int a0 = ix(g, 2 * il), a1 = ix(g, 2 * il + 1);
+            const int t0 = twi(u, g, il);
+            bf_fwd(&sm[a0], &sm[a1], tw[t0], twp[t0], q, q2);
+        }
+        __syncthreads();
+    }
+}
+
+// inverse stages (distances 1, 2, .., S/2) of every sequence, radix-4 pairs then radix-2
+template <bool SEQ_FAST, class IX, class TWI>
+__device__ __forceinline__ void tile_inv(u64 *sm, const u64 *tw, const u64 *twp, int ls, u64 q, u64 q2, IX ix,
+                                         TWI twi) {
+    int u = 0;
+    for (; u + 1 < ls; u += 2) {
+        const int tt = 1 << u;
+        for (int x = threadIdx.x; x < TILE / 4; x += NT2) {
+            int g, jq;
+            split_item<SEQ_FAST>(x, ls, ls - 2, g, jq);
+            const int il1 = jq >> u, jj = jq & (tt - 1);
+            const int i0 = (il1 << (u + 2)) + jj;
+            const int a0 = ix(g, i0), a1 = ix(g, i0 + tt), a2 = ix(g, i0 + 2 * tt), a3 = ix(g, i0 + 3 * tt);
+            u64 v0 = sm[a0], v1 = sm[a1], v2 = sm[a2], v3 = sm[a3];
+            const int ta = twi(u, g, 2 * il1), tb = twi(u, g, 2 * il1 + 1);
+            bfv_inv(v0, v1, tw[ta], twp[ta], q, q2);
+            bfv_inv(v2, v3, tw[tb], twp[tb], q, q2);
+            const int t1 = twi(u + 1, g, il1);
+            bfv_inv(v0, v2, tw[t1], twp[t1], q, q2);
+            bfv_inv(v1, v3, tw[t1], twp[t1], q, q2);
+            sm[a0] = v0;
+            sm[a1] = v1;
+            sm[a2] = v2;
+            sm[a3] = v3;
+        }
+        __syncthreads();
+    }
+    if (u < ls) {  // last stage, distance S/2, one group
+        const int tt = 1 << u;
+        for (int x = threadIdx.x; x < TILE / 2; x += NT2) {
+            int g, j;
+            split_item<SEQ_FAST>(x, ls, ls - 1, g, j);
+            const int a0 = ix(g, j), a1 = ix(g, j + tt);
+            const int t0 = twi(u, g, 0);
+            bf_inv(&sm[a0], &sm[a1], tw[t0], twp[t0], q, q2);
+        }
+        __syncthreads();
+    }
+}
+
+struct TileCtx {
+    int p, r, g, tile;
+    u64 q, q2;
+};
+
+__device__ __forceinline__ bool tile_ctx(const NttBatch &b, const PrimeDev *primes, int L, int tiles, TileCtx &t) {
+    const int pr = blockIdx.x / tiles;
+    t.tile = blockIdx.x % tiles;
+    t.p = pr / b.nr;
+    t.r = b.r0 + pr % b.nr;
+    if (ntt_skipped(b, t.p, t.r)) return false;
+    t.g = ntt_prime(b, t.r, L);
+    t.q = primes[t.g].q;
+    t.q2 = 2 * t.q;
+    return true;
+}
+
 // Column pass: tile = C consecutive columns x all N1 rows, stored row-major [row][C].
-// Forward: stages 0 .. a-1 (pairs of rows within a column, distance N1/2 .. 1).
 __global__ void __launch_bounds__(NT2) k_ntt_fwd_cols(NttBatch b, const PrimeDev *__restrict__ primes,
                                                       const u64 *__restrict__ tw, const u64 *__restrict__ tw_sh,
                                                       int logN, int L, int a) {
-    __shared__ u64 sm[TILE];
-    const int N = 1 << logN, lb = logN - a, N2 = 1 << lb;
-    const int lc = __ffs(TILE) - 1 - a, C = 1 << lc;  // columns per tile
-    const int tiles = N2 >> lc;
-    const int pr = blockIdx.x / tiles, tile = blockIdx.x % tiles;
-    const int p = pr / b.nr, r = b.r0 + pr % b.nr;
-    if (ntt_skipped(b, p, r)) return;
-    const int g = ntt_prime(b, r, L);
-    const u64 q = primes[g].q, q2 = 2 * q;
-    u64 *data = b.data + (size_t)p * b.stride + (size_t)r * N + (tile << lc);
-    const u64 *W = tw + (size_t)g * N, *Wp = tw_sh + (size_t)g * N;
+    __shared__ u64 sm[TILE], stw[TILE], stwp[TILE];
+    const int N = 1 << logN, lb = logN - a, lc = 11 - a, C = 1 << lc;
+    TileCtx t;
+    if (!tile_ctx(b, primes, L, (1 << lb) >> lc, t)) return;
+    u64 *data = b.data + (size_t)t.p * b.stride + (size_t)t.r * N + (t.tile << lc);
+    const u64 *W = tw + (size_t)t.g * N, *Wp = tw_sh + (size_t)t.g * N;
     for (int e = threadIdx.x; e < TILE; e += NT2) sm[e] = data[((size_t)(e >> lc) << lb) + (e & (C - 1))];
-    __syncthreads();
-    for (int s = 0; s < a; s++) {
-        const int lt = a - 1 - s, tt = 1 << lt, m = 1 << s;
-        for (int x = threadIdx.x; x < TILE / 2; x += NT2) {
-            const int col = x & (C - 1), j = x >> lc;
-            const int i = j >> lt, jj = j & (tt - 1);
-            const int row = (i << (lt + 1)) + jj;
-            bf_fwd(&sm[(row << lc) + col], &sm[((row + tt) << lc) + col], W[m + i], Wp[m + i], q, q2);
-        }
-        __syncthreads();
+    for (int k = threadIdx.x; k < (1 << a); k += NT2) {
+        stw[k] = W[k];
+        stwp[k] = Wp[k];
     }
+    __syncthreads();
+    tile_fwd<true>(sm, stw, stwp, a, t.q, t.q2, [&](int g, int i) { return (i << lc) + g; },
+             [&](int u, int, int il) { return (1 << u) + il; });
     for (int e = threadIdx.x; e < TILE; e += NT2) data[((size_t)(e >> lc) << lb) + (e & (C - 1))] = sm[e];
 }
 
-// Row pass: tile = R consecutive rows of N2 contiguous coefficients.
-// Forward: stages a .. logN-1; the group of a butterfly is row * 2^s' + local group.
+// Row pass: tile = R consecutive rows of N2 contiguous coefficients; the twiddle
+// of row g, stage u, group il is W[2^(a+u) + ((row0 + g) << u) + il].
 __global__ void __launch_bounds__(NT2) k_ntt_fwd_rows(NttBatch b, const PrimeDev *__restrict__ primes,
                                                       const u64 *__restrict__ tw, const u64 *__restrict__ tw_sh,
                                                       int logN, int L, int a) {
-    __shared__ u64 sm[TILE];
-    const int N = 1 << logN, lb = logN - a;
-    const int lr = __ffs(TILE) - 1 - lb;  // rows per tile = 2^lr
-    const int tiles = 1 << (a - lr);
-    const int pr = blockIdx.x / tiles, tile = blockIdx.x % tiles;
-    const int p = pr / b.nr, r = b.r0 + pr % b.nr;
-    if (ntt_skipped(b, p, r)) return;
-    const int g = ntt_prime(b, r, L);
-    const u64 q = primes[g].q, q2 = 2 * q;
-    const int row0 = tile << lr;
-    u64 *data = b.data + (size_t)p * b.stride + (size_t)r * N + ((size_t)row0 << lb);
-    const u64 *W = tw + (size_t)g * N, *Wp = tw_sh + (size_t)g * N;
+    __shared__ u64 sm[TILE], stw[TILE], stwp[TILE];
+    const int N = 1 << logN, lb = logN - a, lr = 11 - lb;
+    TileCtx t;
+    if (!tile_ctx(b, primes, L, 1 << (a - lr), t)) return;
+    const int row0 = t.tile << lr;
+    u64 *data = b.data + (size_t)t.p * b.stride + (size_t)t.r * N + ((size_t)row0 << lb);
+    const u64 *W = tw + (size_t)t.g * N, *Wp = tw_sh + (size_t)t.g * N;
     for (int e = threadIdx.x; e < TILE; e += NT2) sm[e] = data[e];
-    __syncthreads();
-    const int lh = lb - 1;  // log2 of butterflies per row
-    for (int s = 0; s < lb; s++) {
-        const int lt = lb - 1 - s, tt = 1 << lt, m = 1 << (a + s);
-        for (int x = threadIdx.x; x < TILE / 2; x += NT2) {
-            const int rl = x >> lh, j = x & ((1 << lh) - 1);
-            const int il = j >> lt, jj = j & (tt - 1);
-            const int idx = (rl << lb) + (il << (lt + 1)) + jj;
-            const int gi = m + (((row0 + rl) << s) + il);
-            bf_fwd(&sm[idx], &sm[idx + tt], W[gi], Wp[gi], q, q2);
+    // stage u needs R << u consecutive twiddles from 2^(a+u) + (row0 << u); stored at R (2^u - 1)
+    for (int u = 0; u < lb; u++) {
+        const int cnt = 1 << (lr + u), off = (1 << lr) * ((1 << u) - 1), src = (1 << (a + u)) + (row0 << u);
+        for (int k = threadIdx.x; k < cnt; k += NT2) {
+            stw[off + k] = W[src + k];
+            stwp[off + k] = Wp[src + k];
         }
-        __syncthreads();
     }
+    __syncthreads();
+    tile_fwd<false>(sm, stw, stwp, lb, t.q, t.q2, [&](int g, int i) { return (g << lb) + i; },
+             [&](int u, int g, int il) { return ((1 << lr) * ((1 << u) - 1)) + (g << u) + il; });
     for (int e = threadIdx.x; e < TILE; e += NT2) {
         u64 v = sm[e];
-        if (v >= q2) v -= q2;
-        if (v >= q) v -= q;
+        if (v >= t.q2) v -= t.q2;
+        if (v >= t.q) v -= t.q;
         data[e] = v;
     }
 }
 
-// Inverse, row pass first: distances 1 .. N2/2; group = row * 2^(lb-1-u) + local group.
+// Inverse row pass (first): twiddle of row g, stage u, group il is
+// W[2^(logN-1-u) + ((row0 + g) << (lb-1-u)) + il].
 __global__ void __launch_bounds__(NT2) k_ntt_inv_rows(NttBatch b, const PrimeDev *__restrict__ primes,
                                                       const u64 *__restrict__ tw, const u64 *__restrict__ tw_sh,
                                                       int logN, int L, int a) {
-    __shared__ u64 sm[TILE];
-    const int N = 1 << logN, lb = logN - a;
-    const int lr = __ffs(TILE) - 1 - lb;
-    const int tiles = 1 << (a - lr);
-    const int pr = blockIdx.x / tiles, tile = blockIdx.x % tiles;
-    const int p = pr / b.nr, r = b.r0 + pr % b.nr;
-    if (ntt_skipped(b, p, r)) return;
-    const int g = ntt_prime(b, r, L);
-    const u64 q = primes[g].q, q2 = 2 * q;
-    const int row0 = tile << lr;
-    u64 *data = b.data + (size_t)p * b.stride + (size_t)r * N + ((size_t)row0 << lb);
-    const u64 *W = tw + (size_t)g * N, *Wp = tw_sh + (size_t)g * N;
+    __shared__ u64 sm[TILE], stw[TILE], stwp[TILE];
+    const int N = 1 << logN, lb = logN - a, lr = 11 - lb;
+    TileCtx t;
+    if (!tile_ctx(b, primes, L, 1 << (a - lr), t)) return;
+    const int row0 = t.tile << lr;
+    u64 *data = b.data + (size_t)t.p * b.stride + (size_t)t.r * N + ((size_t)row0 << lb);
+    const u64 *W = tw + (size_t)t.g * N, *Wp = tw_sh + (size_t)t.g * N;
     for (int e = threadIdx.x; e < TILE; e += NT2) sm[e] = data[e];
-    __syncthreads();
-    const int lh = lb - 1;
-    for (int u = 0; u < lb; u++) {
-        const int tt = 1 << u;
-        const int h = 1 << (logN - 1 - u);  // N / (2 tt)
-        for (int x = threadIdx.x; x < TILE / 2; x += NT2) {
-            const int rl = x >> lh, j = x & ((1 << lh) - 1);
-            const int il = j >> u, jj = j & (tt - 1);
-            const int idx = (rl << lb) + (il << (u + 1)) + jj;
-            const int gi = h + (((row0 + rl) << (lb - 1 - u)) + il);
-            bf_inv(&sm[idx], &sm[idx + tt], W[gi], Wp[gi], q, q2);
+    // stage u needs R << (lb-1-u) twiddles; stored after those of the earlier stages
+    for (int u = 0, off = 0; u < lb; u++) {
+        const int su = lb - 1 - u, cnt = 1 << (lr + su), src = (1 << (logN - 1 - u)) + (row0 << su);
+        for (int k = threadIdx.x; k < cnt; k += NT2) {
+            stw[off + k] = W[src + k];
+            stwp[off + k] = Wp[src + k];
         }
-        __syncthreads();
+        off += cnt;
     }
+    __syncthreads();
+    // offset of stage u: sum_{v<u} R 2^(lb-1-v) = R (2^lb - 2^(lb-u))
+    tile_inv<false>(sm, stw, stwp, lb, t.q, t.q2, [&](int g, int i) { return (g << lb) + i; },
+             [&](int u, int g, int il) {
+                 return (1 << lr) * ((1 << lb) - (1 << (lb - u))) + (g << (lb - 1 - u)) + il;
+             });
     for (int e = threadIdx.x; e < TILE; e += NT2) data[e] = sm[e];
 }
 
-// Inverse, column pass: row distances 1 .. N1/2, then the N^-1 scaling.
+// Inverse column pass: twiddle of stage u, group il is W[2^(a-1-u) + il]; then N^-1.
 __global__ void __launch_bounds__(NT2) k_ntt_inv_cols(NttBatch b, const PrimeDev *__restrict__ primes,
                                                       const u64 *__restrict__ tw, const u64 *__restrict__ tw_sh,
                                                       int logN, int L, int a) {
-    __shared__ u64 sm[TILE];
-    const int N = 1 << logN, lb = logN - a, N2 = 1 << lb;
-    const int lc = __ffs(TILE) - 1 - a, C = 1 << lc;
-    const int tiles = N2 >> lc;
-    const int pr = blockIdx.x / tiles, tile = blockIdx.x % tiles;
-    const int p = pr / b.nr, r = b.r0 + pr % b.nr;
-    if (ntt_skipped(b, p, r)) return;
-    const int g = ntt_prime(b, r, L);
-    const PrimeDev P = primes[g];
-    const u64 q = P.q, q2 = 2 * q;
-    u64 *data = b.data + (size_t)p * b.stride + (size_t)r * N + (tile << lc);
-    const u64 *W = tw + (size_t)g * N, *Wp = tw_sh + (size_t)g * N;
+    __shared__ u64 sm[TILE], stw[TILE], stwp[TILE];
+    const int N = 1 << logN, lb = logN - a, lc = 11 - a, C = 1 << lc;
+    TileCtx t;
+    if (!tile_ctx(b, primes, L, (1 << lb) >> lc, t)) return;
+    const PrimeDev P = primes[t.g];
+    u64 *data = b.data + (size_t)t.p * b.stride + (size_t)t.r * N + (t.tile << lc);
+    const u64 *W = tw + (size_t)t.g * N, *Wp = tw_sh + (size_t)t.g * N;
     for (int e = threadIdx.x; e < TILE; e += NT2) sm[e] = data[((size_t)(e >> lc) << lb) + (e & (C - 1))];
-    __syncthreads();
-    for (int v = 0; v < a; v++) {
-        const int tt = 1 << v, h = 1 << (a - 1 - v);
-        for (int x = threadIdx.x; x < TILE / 2; x += NT2) {
-            const int col = x & (C - 1), j = x >> lc;
-            const int i = j >> v, jj = j & (tt - 1);
-            const int row = (i << (v + 1)) + jj;
-            bf_inv(&sm[(row << lc) + col], &sm[((row + tt) << lc) + col], W[h + i], Wp[h + i], q, q2);
-        }
-        __syncthreads();
+    for (int k = threadIdx.x; k < (1 << a); k += NT2) {
+        stw[k] = W[k];
+        stwp[k] = Wp[k];
     }
+    __syncthreads();
+    tile_inv<true>(sm, stw, stwp, a, t.q, t.q2, [&](int g, int i) { return (i << lc) + g; },
+             [&](int u, int, int il) { return (1 << (a - 1 - u)) + il; });
     for (int e = threadIdx.x; e < TILE; e += NT2)
-        data[((size_t)(e >> lc) << lb) + (e & (C - 1))] = mul_shoup(sm[e], P.ninv, P.ninv_sh, q);
+        data[((size_t)(e >> lc) << lb) + (e & (C - 1))] = mul_shoup(sm[e], P.ninv, P.ninv_sh, t.q);
 }
 
 copse_status launch(copse_ctx *ctx, const NttBatch &b, cudaStream_t s, bool inverse) {

@@ -218,54 +218,89 @@ __global__ void k_ks_finish(const u64 *u, const u64 *W, const u64 *add0, const u
     out[e] = v;
 }
 
-// per-chunk table of the multiply-accumulate, passed by value
-struct MacTable {
-    u64 gl[CHUNK_ROT];                 // Galois element of each rotation
-    int has_ks[CHUNK_ROT];             // 0: the rotation is the identity (no key switch)
-    const u64 *pt[MAX_ACC * CHUNK_ROT]; // [acc][rotation] diagonal, null = zero
-    u64 *acc[MAX_ACC];
+// Diagonal products over shared rotations with one ModDown per sum (double
+// hoisting).  For every element (r, n) of the extended basis and each rotation k
+// of the chunk:
+//   R_k = sum_j tau_k(yhat_j) * ksk_k[j]  (+ P * tau_k(c0) on component 0 at q-primes)
+//   acc_a += pt[a][k] * R_k
+// The key-switched ciphertexts are never written: each key, each diagonal and
+// each accumulator is read once per chunk.
+struct MmJob {
+    const u64 *ksk;  // [ndig][2][L+alpha][N] NTT domain
+    u64 g;           // Galois element
+};
+struct MmTable {
+    MmJob job[CHUNK_ROT];
+    const u64 *pt[MAX_ACC * CHUNK_ROT];  // [acc][rotation], [ell+alpha][N], null = zero diagonal
+    u64 *acc[MAX_ACC];                   // [2][ell+alpha][N]
 };
 
-// Multiply-accumulate of a chunk of rotations into up to MAX_ACC accumulators:
-//   rot_k = (k has no key switch) ? v : (tau_g v0, 0) + (U_k - t W_k) P^-1
-//   acc_a += pt[a][k] * rot_k
-__global__ void k_matmul_mac(const u64 *U, const u64 *W, const u64 *v, int nrot, const MacTable tab, int nacc,
-                             int ell, int alpha, int logN, const PrimeDev *pr, KsTables T) {
-    const u64 *gl = tab.gl;
-    const int *has_ks = tab.has_ks;
-    const u64 *const *pt_tab = tab.pt;
-    u64 *const *acc = tab.acc;
+__global__ void __launch_bounds__(256) k_mm_fused(const u64 *yhat, const u64 *c0, int nrot, const MmTable tab,
+                                                  int nacc, int ell, int alpha, int L, int logN, const PrimeDev *pr,
+                                                  KsTables T) {
     const int N = 1 << logN;
-    size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const size_t n_el = (size_t)ell << logN;
-    if (e >= 2 * n_el) return;
-    const int c = e >= n_el;
-    const size_t k = e - c * n_el;
-    const int i = (int)(k >> logN);
-    const uint32_t n = (uint32_t)(k & (N - 1));
-    const PrimeDev P = pr[i];
-    const Shoup Pinv = T.md_Pinv[i];
-    u64 a[MAX_ACC];
-    for (int x = 0; x < nacc; x++) a[x] = acc[x][e];
-    const size_t ustride = 2 * ((size_t)(ell + alpha) << logN), wstride = 2 * n_el;
-    int ks = 0;
-    for (int r = 0; r < nrot; r++) {
-        u64 rv;
-        if (!has_ks[r]) {
-            rv = v[e];
-        } else {
-            const u64 uv = U[(size_t)ks * ustride + (size_t)c * ((size_t)(ell + alpha) << logN) + k];
-            const u64 wv = W[(size_t)ks * wstride + e];
-            rv = mul_shoup(sub_mod(uv, mul_shoup(wv, P.t_mod, P.t_mod_sh, P.q), P.q), Pinv, P.q);
-            if (c == 0) rv = add_mod(rv, v[((size_t)i << logN) + galois_src(n, gl[r], logN)], P.q);
-            ks++;
+    const int nx = ell + alpha, nd = (ell + alpha - 1) / alpha, NB = L + alpha;
+    const size_t n_el = (size_t)nx << logN;
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n_el) return;
+    const int r = (int)(e >> logN);
+    const uint32_t n = (uint32_t)(e & (N - 1));
+    const int g = r < ell ? r : L + (r - ell);
+    const PrimeDev P = pr[g];
+    const u64 Pm = r < ell ? T.md_P[r] : 0;
+    u64 a0[MAX_ACC], a1[MAX_ACC];
+    for (int x = 0; x < nacc; x++) {
+        a0[x] = tab.acc[x][e];
+        a1[x] = tab.acc[x][n_el + e];
+    }
+    for (int k = 0; k < nrot; k++) {
+        const MmJob J = tab.job[k];
+        const uint32_t src = galois_src(n, J.g, logN);
+        u64 u0 = 0, u1 = 0;
+        for (int j = 0; j < nd; j++) {
+            const u64 y = yhat[(((size_t)j * nx + r) << logN) + src];
+            const u64 *k0 = J.ksk + (((size_t)(2 * j) * NB + g) << logN);
+            const u64 *k1 = J.ksk + (((size_t)(2 * j + 1) * NB + g) << logN);
+            u0 = add_mod(u0, mul_mod(y, k0[n], P), P.q);
+            u1 = add_mod(u1, mul_mod(y, k1[n], P), P.q);
         }
+        if (r < ell) u0 = add_mod(u0, mul_mod(Pm, c0[((size_t)r << logN) + src], P), P.q);
         for (int x = 0; x < nacc; x++) {
-            const u64 *p = pt_tab[(size_t)x * nrot + r];
-            if (p) a[x] = add_mod(a[x], mul_mod(p[k], rv, P), P.q);
+            const u64 *p = tab.pt[x * nrot + k];
+            if (!p) continue;
+            const u64 pv = p[e];
+            a0[x] = add_mod(a0[x], mul_mod(pv, u0, P), P.q);
+            a1[x] = add_mod(a1[x], mul_mod(pv, u1, P), P.q);
         }
     }
-    for (int x = 0; x < nacc; x++) acc[x][e] = a[x];
+    for (int x = 0; x < nacc; x++) {
+        tab.acc[x][e] = a0[x];
+        tab.acc[x][n_el + e] = a1[x];
+    }
+}
+
+// ModDown finish over npoly polys: out = (u - t W) * P^-1, u with stride ustride (its first
+// ell residues in NTT domain), W and out [npoly][ell][N]
+__global__ void k_md_finish(const u64 *u, size_t ustride, const u64 *W, u64 *out, int npoly, int ell, int logN,
+                            const PrimeDev *pr, KsTables T) {
+    const size_t per = (size_t)ell << logN;
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (size_t)npoly * per) return;
+    const size_t p = e / per, k = e - p * per;
+    const int i = (int)(k >> logN);
+    const PrimeDev P = pr[i];
+    const u64 uv = u[p * ustride + k];
+    out[e] = mul_shoup(sub_mod(uv, mul_shoup(W[e], P.t_mod, P.t_mod_sh, P.q), P.q), T.md_Pinv[i], P.q);
+}
+
+// out[c] += pt * v[c] for both components (pt: first ell residues of an extended-basis plaintext)
+__global__ void k_ident_mac(u64 *out, const u64 *v, const u64 *pt, int ell, int logN, const PrimeDev *pr) {
+    const size_t n = (size_t)ell << logN;
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= 2 * n) return;
+    const size_t k = e < n ? e : e - n;
+    const PrimeDev P = pr[k >> logN];
+    out[e] = add_mod(out[e], mul_mod(pt[k], v[e], P), P.q);
 }
 
 // modulus switch, conversion step: last [ncomp][N] coefficients of q_{ell-1} ->
@@ -367,13 +402,16 @@ __global__ void k_scatter_pattern(const uint32_t *pat, int npat, int len, int pe
     out[((size_t)i << logN) + slot_index[s]] = x < len ? pat[(size_t)i * len + x] : 0;
 }
 
-// coefficients mod t -> centred -> residues mod q_0..q_{level-1}: out [n][level][N]
-__global__ void k_lift(const u64 *in, u64 *out, int npoly, int level, int logN, u64 t, const PrimeDev *pr) {
+// coefficients mod t -> centred -> residues over q_0..q_{level-1} then (nres > level)
+// p_0..p_{nres-level-1}: out [n][nres][N]
+__global__ void k_lift(const u64 *in, u64 *out, int npoly, int level, int nres, int L, int logN, u64 t,
+                       const PrimeDev *pr) {
     size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const size_t per = (size_t)level << logN;
+    const size_t per = (size_t)nres << logN;
     if (e >= (size_t)npoly * per) return;
     const size_t i = e / per, k = e - i * per;
-    const int r = (int)(k >> logN);
+    const int rr = (int)(k >> logN);
+    const int r = rr < level ? rr : L + (rr - level);
     const u64 c = in[(i << logN) + (k & ((1ull << logN) - 1))];
     const i64 m = c > (t - 1) / 2 ? (i64)c - (i64)t : (i64)c;
     out[e] = from_signed(m, pr[r].q);
@@ -392,11 +430,13 @@ __global__ void k_feature_planes(const uint32_t *feats, int nq, int nf, int K, i
 }
 
 // encryption randomness of plane i (stream base 0x1000000 + 3 i):
-// u ternary, x0 = t e0 + m, x1 = t e1, as residues mod q_0..q_{L-1}
-__global__ void k_enc_prep(const u64 *mt, int p, u64 seed, int L, int logN, u64 t, const PrimeDev *pr, u64 *U,
-                           u64 *X0, u64 *X1) {
+// u ternary, x0 = t e0 + m, x1 = t e1, as residues mod q_0..q_{L-1}; the seed is
+// read from device memory when seed_ptr is set (replayed graphs)
+__global__ void k_enc_prep(const u64 *mt, int p, u64 seed_val, const u64 *seed_ptr, int L, int logN, u64 t,
+                           const PrimeDev *pr, u64 *U, u64 *X0, u64 *X1) {
     size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= ((size_t)p << logN)) return;
+    const u64 seed = seed_ptr ? *seed_ptr : seed_val;
     const int i = (int)(e >> logN);
     const u64 n = e & ((1ull << logN) - 1);
     const u64 sb = 0x1000000ull + 3ull * (u64)i;
@@ -675,83 +715,94 @@ copse_status op_rotate(copse_ctx *c, const copse_evk *evk, const DCt &a, uint32_
 copse_status op_matmul(copse_ctx *c, const copse_evk *evk, const DCt &v, const std::vector<uint32_t> &rots,
                        const std::vector<std::vector<const u64 *>> &pt, const std::vector<const u64 *> &add,
                        std::vector<DCt> &out, cudaStream_t s) {
-    const int ell = v.level, N = c->N, A = c->alpha, nacc = (int)pt.size(), nrot = (int)rots.size();
-    const size_t per = (size_t)2 * ell * N;
+    const int ell = v.level, N = c->N, A = c->alpha, nx = ell + A, nacc = (int)pt.size(), nrot = (int)rots.size();
+    const size_t ext = (size_t)2 * nx * N, per = (size_t)2 * ell * N;
     Scratch sc(s);
-    std::vector<u64 *> acc(nacc);
-    for (int a = 0; a < nacc; a++) {
-        STATUS_TRY(sc.get(c, &acc[a], per));
-        CUDA_TRY(cudaMemsetAsync(acc[a], 0, per * sizeof(u64), s));
-    }
-    // rotations that need a key switch share one ModUp
-    bool any_ks = false;
     std::vector<u64> gal(nrot);
+    std::vector<int> ks_idx;  // rotations that need a key switch
     for (int r = 0; r < nrot; r++) {
         gal[r] = galois_of_rotation(c, rots[r]);
-        if (gal[r] != 1) {
-            any_ks = true;
-            if (!evk->find(gal[r])) { set_error("no rotation key for amount " + std::to_string(rots[r])); return COPSE_ENOKEY; }
-        }
+        if (gal[r] == 1) continue;
+        if (!evk->find(gal[r])) { set_error("no rotation key for amount " + std::to_string(rots[r])); return COPSE_ENOKEY; }
+        bool used = false;
+        for (int a = 0; a < nacc; a++) used |= pt[a][r] != nullptr;
+        if (used) ks_idx.push_back(r);
     }
-    u64 *yhat = nullptr, *U = nullptr, *W = nullptr;
-    if (any_ks) {
+    // extended-basis accumulators [nacc][2][ell+alpha][N] and the Q-basis results [nacc][2][ell][N]
+    u64 *acc = nullptr, *res = nullptr, *W = nullptr;
+    STATUS_TRY(sc.get(c, &res, (size_t)nacc * per));
+    CUDA_TRY(cudaMemsetAsync(res, 0, (size_t)nacc * per * sizeof(u64), s));
+    if (!ks_idx.empty()) {
+        STATUS_TRY(sc.get(c, &acc, (size_t)nacc * ext));
+        STATUS_TRY(sc.get(c, &W, (size_t)nacc * per));
+        CUDA_TRY(cudaMemsetAsync(acc, 0, (size_t)nacc * ext * sizeof(u64), s));
+        u64 *yhat = nullptr;
         STATUS_TRY(ks_modup(c, v.data + (size_t)ell * N, ell, sc, &yhat, s));
-        STATUS_TRY(sc.get(c, &U, (size_t)CHUNK_ROT * 2 * (ell + A) * N));
-        STATUS_TRY(sc.get(c, &W, (size_t)CHUNK_ROT * 2 * ell * N));
-    }
-    for (int r0 = 0; r0 < nrot;) {
-        // chunk: up to CHUNK_ROT rotations (identity terms included)
-        std::vector<int> idx;
-        std::vector<InnerJob> jobs;
-        int r = r0;
-        while (r < nrot && (int)idx.size() < CHUNK_ROT) {
-            if (gal[r] != 1) {
-                jobs.push_back(InnerJob{evk->find(gal[r]), U + (size_t)jobs.size() * 2 * (ell + A) * N, gal[r]});
-            }
-            idx.push_back(r);
-            r++;
-        }
-        if (!jobs.empty()) STATUS_TRY(ks_apply(c, yhat, ell, jobs, U, W, sc, s));
-        const int nr = (int)idx.size();
-        for (int a0 = 0; a0 < nacc; a0 += MAX_ACC) {
-            const int na = std::min(MAX_ACC, nacc - a0);
-            MacTable tab;
-            memset(&tab, 0, sizeof(tab));
-            int nz_pt = 0;
-            for (int x = 0; x < nr; x++) {
-                tab.gl[x] = gal[idx[x]];
-                tab.has_ks[x] = gal[idx[x]] != 1;
-                for (int a = 0; a < na; a++) {
-                    tab.pt[(size_t)a * nr + x] = pt[a0 + a][idx[x]];
-                    nz_pt += tab.pt[(size_t)a * nr + x] != nullptr;
+        const int nd = (ell + A - 1) / A;
+        for (size_t k0 = 0; k0 < ks_idx.size(); k0 += CHUNK_ROT) {
+            const int nr = (int)std::min<size_t>(CHUNK_ROT, ks_idx.size() - k0);
+            for (int a0 = 0; a0 < nacc; a0 += MAX_ACC) {
+                const int na = std::min(MAX_ACC, nacc - a0);
+                MmTable tab;
+                memset(&tab, 0, sizeof(tab));
+                int nz_pt = 0;
+                for (int x = 0; x < nr; x++) {
+                    const int r = ks_idx[k0 + x];
+                    tab.job[x] = MmJob{evk->find(gal[r]), gal[r]};
+                    for (int a = 0; a < na; a++) {
+                        tab.pt[a * nr + x] = pt[a0 + a][r];
+                        nz_pt += pt[a0 + a][r] != nullptr;
+                    }
                 }
+                for (int a = 0; a < na; a++) tab.acc[a] = acc + (size_t)(a0 + a) * ext;
+                // algorithmic bytes: keys, diagonals, accumulators in and out, the rotated
+                // digits and c0 once
+                const double bytes = 8.0 * N * ((double)nr * 2 * nd * nx + nz_pt * (double)nx + 4.0 * na * nx +
+                                                (double)nd * nx + ell);
+                TIMED("mm_fused", bytes, s,
+                      k_mm_fused<<<nblk((size_t)nx * N), TPB, 0, s>>>(yhat, v.data, nr, tab, na, ell, A, c->L,
+                                                                      c->logN, c->d_prime, c->ks));
+                LAUNCH_CHECK();
             }
-            for (int a = 0; a < na; a++) tab.acc[a] = acc[a0 + a];
-            TIMED("matmul_mac", 8.0 * N * ell * (4.0 * jobs.size() + 2.0 + (double)nz_pt + 4.0 * na), s,
-                  k_matmul_mac<<<nblk(per), TPB, 0, s>>>(U, W, v.data, nr, tab, na, ell, A, c->logN, c->d_prime,
-                                                         c->ks));
-            LAUNCH_CHECK();
         }
-        r0 = r;
+        // one ModDown per accumulator (both components)
+        STATUS_TRY(ntt_inverse(c, batch(acc, (size_t)nx * N, 2 * nacc, ell, A, ell), s));
+        TIMED("moddown_conv", 8.0 * N * 2.0 * nacc * ((double)A + ell), s,
+              k_moddown_conv<<<nblk((size_t)2 * nacc * N), TPB, 0, s>>>(acc, (size_t)nx * N, W, (size_t)ell * N,
+                                                                        2 * nacc, ell, A, c->L, c->logN, c->d_prime,
+                                                                        c->ks));
+        LAUNCH_CHECK();
+        STATUS_TRY(ntt_forward(c, batch(W, (size_t)ell * N, 2 * nacc, 0, ell, ell), s));
+        TIMED("md_finish", 8.0 * N * 3.0 * 2 * nacc * ell, s,
+              k_md_finish<<<nblk((size_t)nacc * per), TPB, 0, s>>>(acc, (size_t)nx * N, W, res, 2 * nacc, ell,
+                                                                   c->logN, c->d_prime, c->ks));
+        LAUNCH_CHECK();
     }
     out.assign(nacc, DCt());
     for (int a = 0; a < nacc; a++) {
+        u64 *ra = res + (size_t)a * per;
+        for (int r = 0; r < nrot; r++) {
+            if (gal[r] != 1 || !pt[a][r]) continue;
+            TIMED("ident_mac", 8.0 * N * 4.0 * ell, s,
+                  k_ident_mac<<<nblk(per), TPB, 0, s>>>(ra, v.data, pt[a][r], ell, c->logN, c->d_prime));
+            LAUNCH_CHECK();
+        }
         if (add.size() > (size_t)a && add[a]) {
-            k_add_plain<<<nblk((size_t)ell * N), TPB, 0, s>>>(acc[a], add[a], ell, c->logN, c->d_prime);
+            k_add_plain<<<nblk((size_t)ell * N), TPB, 0, s>>>(ra, add[a], ell, c->logN, c->d_prime);
             LAUNCH_CHECK();
         }
         DCt tmp;
         tmp.level = ell;
         tmp.ncomp = 2;
-        tmp.data = acc[a];
+        tmp.data = ra;
         STATUS_TRY(op_modswitch(c, tmp, &out[a], s));
     }
     return COPSE_OK;
 }
 
 copse_status encode_patterns(copse_ctx *c, const std::vector<uint32_t> &patterns, int n, int len, int period,
-                             int level, u64 *out, cudaStream_t s) {
-    const int N = c->N;
+                             int level, int ext_alpha, u64 *out, cudaStream_t s) {
+    const int N = c->N, nres = level + ext_alpha;
     if (n <= 0) return COPSE_OK;
     Scratch sc(s);
     u64 *pat = nullptr, *mt = nullptr;
@@ -762,9 +813,9 @@ copse_status encode_patterns(copse_ctx *c, const std::vector<uint32_t> &patterns
                                                           c->d_slot_index, mt);
     LAUNCH_CHECK();
     STATUS_TRY(ntt_inverse(c, batch(mt, N, n, 0, 1, 0, c->t_index()), s));
-    k_lift<<<nblk((size_t)n * level * N), TPB, 0, s>>>(mt, out, n, level, c->logN, c->t, c->d_prime);
+    k_lift<<<nblk((size_t)n * nres * N), TPB, 0, s>>>(mt, out, n, level, nres, c->L, c->logN, c->t, c->d_prime);
     LAUNCH_CHECK();
-    STATUS_TRY(ntt_forward(c, batch(out, (size_t)level * N, n, 0, level, level), s));
+    STATUS_TRY(ntt_forward(c, batch(out, (size_t)nres * N, n, 0, nres, level), s));
     // the pattern staging buffer is read by the device before the caller's vector dies
     CUDA_TRY(cudaStreamSynchronize(s));
     return COPSE_OK;
@@ -854,7 +905,8 @@ copse_status keygen_dev(copse_ctx *c, u64 seed, const std::vector<u64> &galois, 
 }
 
 copse_status encrypt_planes(copse_ctx *c, const copse_keys *k, const uint32_t *d_feats, int nq, int nf, int K,
-                            int q, int pd, int block, int p, u64 seed, std::vector<DCt> &out, cudaStream_t s) {
+                            int q, int pd, int block, int p, u64 seed, std::vector<DCt> &out, cudaStream_t s,
+                            const u64 *d_seed) {
     const int N = c->N, L = c->L;
     Scratch sc(s);
     u64 *mt = nullptr, *U = nullptr, *X0 = nullptr, *X1 = nullptr, *cts = nullptr;
@@ -865,7 +917,7 @@ copse_status encrypt_planes(copse_ctx *c, const copse_keys *k, const uint32_t *d
     k_feature_planes<<<nblk(N), TPB, 0, s>>>(d_feats, nq, nf, K, q, pd, block, p, c->logN, c->d_slot_index, mt);
     LAUNCH_CHECK();
     STATUS_TRY(ntt_inverse(c, batch(mt, N, p, 0, 1, 0, c->t_index()), s));
-    k_enc_prep<<<nblk((size_t)p * N), TPB, 0, s>>>(mt, p, seed, L, c->logN, c->t, c->d_prime, U, X0, X1);
+    k_enc_prep<<<nblk((size_t)p * N), TPB, 0, s>>>(mt, p, seed, d_seed, L, c->logN, c->t, c->d_prime, U, X0, X1);
     LAUNCH_CHECK();
     STATUS_TRY(ntt_forward(c, batch(U, (size_t)L * N, p, 0, L, L), s));
     STATUS_TRY(ntt_forward(c, batch(X0, (size_t)L * N, p, 0, L, L), s));

@@ -47,8 +47,12 @@ void drain() {
 
 }  // namespace
 
+// graph capture records no timing events
+static thread_local bool suspended = false;
+void stats_suspend(bool on) { suspended = on; }
+
 int stats_begin(const char *name, double bytes, cudaStream_t s) {
-    if (!enabled) return -1;
+    if (!enabled || suspended) return -1;
     std::lock_guard<std::mutex> g(mu);
     if (used == pool.size()) {
         cudaEvent_t a, b;
