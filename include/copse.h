@@ -196,6 +196,15 @@ typedef struct copse_session copse_session;
  * n_queries <= N / block.  keys, evk and model must outlive the session. */
 copse_status copse_session_create(copse_ctx *ctx, const copse_keys *keys, const copse_evk *evk,
                                   copse_model *model, size_t n_queries, copse_session **out);
+/* A session over n_items work items (models[i], n_queries[i]): one graph
+ * launch evaluates every item, each on its own lane of streams, so queries of
+ * several forests of uneven size run in one launch.  Runs take the items'
+ * features concatenated in item order and return their leaf bits
+ * concatenated in item order; item i encrypts with seed + i.  A model may
+ * appear in several items (each item holds up to N / block queries). */
+copse_status copse_session_create_batch(copse_ctx *ctx, const copse_keys *keys, const copse_evk *evk,
+                                        size_t n_items, copse_model *const *models, const size_t *n_queries,
+                                        copse_session **out);
 /* One step: feats[n_queries * n_features] (host if feats_on_device = 0, else
  * device), fresh encryption randomness from `seed`, leaf bits into
  * out_bits[n_queries * n_leaves] (host if out_on_device = 0: the call then

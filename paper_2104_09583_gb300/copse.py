@@ -382,3 +382,18 @@ def copse_session_run(session, feats, seed, out=None, stream=None, feats_ptr=Non
 
 def copse_session_destroy(session):
     _lib.copse_session_destroy(session)
+
+
+_lib.copse_session_create_batch.restype = C.c_int
+_lib.copse_session_create_batch.argtypes = [vp, vp, vp, C.c_size_t, C.POINTER(C.c_void_p),
+                                            C.POINTER(C.c_size_t), pvp]
+
+
+def copse_session_create_batch(ctx, keys, evk, models, n_queries):
+    """One graph over several (model, n_queries) items; see include/copse.h."""
+    n = len(models)
+    ms = (C.c_void_p * n)(*[m.value for m in models])
+    qs = (C.c_size_t * n)(*n_queries)
+    h = C.c_void_p()
+    _check(_lib.copse_session_create_batch(ctx, keys, evk, n, ms, qs, C.byref(h)))
+    return h

@@ -305,7 +305,7 @@ extern "C" copse_status copse_encrypt_features(copse_ctx *c, const copse_keys *k
 }
 
 static copse_status infer_impl(copse_ctx *c, const copse_evk *evk, copse_model *m, const copse_ctbuf *feats,
-                               DCt *result, cudaStream_t s) {
+                               DCt *result, cudaStream_t s, int lane = 0) {
     STATUS_TRY(upload_model(c, m, s));
     const DeviceModel &D = *m->dev;
     const CompiledForest &f = m->f;
@@ -318,32 +318,32 @@ static copse_status infer_impl(copse_ctx *c, const copse_evk *evk, copse_model *
     // joined back onto s; every free happens on s after the join.
     // SecComp leaves, most significant plane first: lt = (1 - x) y, eq = [x == y]
     std::vector<Node> nodes(p);
-    STATUS_TRY(fork_begin(c, s, 2 * p));
+    STATUS_TRY(fork_begin(c, s, 2 * p, lane));
     for (int k = 0; k < p; k++) {
         const int i = p - 1 - k;
         DPt lm{c->L, (u64 *)D.lt_mul[i]}, la{c->L, (u64 *)D.lt_add[i]};
         DPt em{c->L, (u64 *)D.eq_mul[i]}, ea{c->L, (u64 *)D.eq_add[i]};
-        STATUS_TRY(op_affine(c, feats->cts[i], lm, &la, &nodes[k].lt, fork_stream(c, 2 * k)));
-        STATUS_TRY(op_affine(c, feats->cts[i], em, &ea, &nodes[k].eq, fork_stream(c, 2 * k + 1)));
+        STATUS_TRY(op_affine(c, feats->cts[i], lm, &la, &nodes[k].lt, fork_stream(c, 2 * k, lane)));
+        STATUS_TRY(op_affine(c, feats->cts[i], em, &ea, &nodes[k].eq, fork_stream(c, 2 * k + 1, lane)));
     }
-    STATUS_TRY(fork_join(c, s, 2 * p));
+    STATUS_TRY(fork_join(c, s, 2 * p, lane));
     // balanced combine (lt_h + eq_h lt_l, eq_h eq_l); no eq at the root
     while (nodes.size() > 1) {
         const bool root = nodes.size() == 2;
         const int npair = (int)(nodes.size() / 2);
         std::vector<Node> nx(npair);
         std::vector<DCt> prod(npair);
-        STATUS_TRY(fork_begin(c, s, 2 * npair));
+        STATUS_TRY(fork_begin(c, s, 2 * npair, lane));
         for (int k = 0; k < npair; k++) {
             Node &hi = nodes[2 * k], &lo = nodes[2 * k + 1];
-            STATUS_TRY(op_mul(c, evk, hi.eq, lo.lt, &prod[k], fork_stream(c, 2 * k)));
-            if (!root) STATUS_TRY(op_mul(c, evk, hi.eq, lo.eq, &nx[k].eq, fork_stream(c, 2 * k + 1)));
+            STATUS_TRY(op_mul(c, evk, hi.eq, lo.lt, &prod[k], fork_stream(c, 2 * k, lane)));
+            if (!root) STATUS_TRY(op_mul(c, evk, hi.eq, lo.eq, &nx[k].eq, fork_stream(c, 2 * k + 1, lane)));
         }
-        STATUS_TRY(fork_join(c, s, 2 * npair));
-        STATUS_TRY(fork_begin(c, s, npair));
+        STATUS_TRY(fork_join(c, s, 2 * npair, lane));
+        STATUS_TRY(fork_begin(c, s, npair, lane));
         for (int k = 0; k < npair; k++)
-            STATUS_TRY(op_add(c, nodes[2 * k].lt, prod[k], &nx[k].lt, false, fork_stream(c, k)));
-        STATUS_TRY(fork_join(c, s, npair));
+            STATUS_TRY(op_add(c, nodes[2 * k].lt, prod[k], &nx[k].lt, false, fork_stream(c, k, lane)));
+        STATUS_TRY(fork_join(c, s, npair, lane));
         for (int k = 0; k < npair; k++) {
             ct_free(&prod[k], s);
             for (Node *n : {&nodes[2 * k], &nodes[2 * k + 1]}) {
@@ -369,10 +369,10 @@ static copse_status infer_impl(copse_ctx *c, const copse_evk *evk, copse_model *
     while (lv.size() > 1) {
         const int npair = (int)(lv.size() / 2);
         std::vector<DCt> nx(npair);
-        STATUS_TRY(fork_begin(c, s, npair));
+        STATUS_TRY(fork_begin(c, s, npair, lane));
         for (int k = 0; k < npair; k++)
-            STATUS_TRY(op_mul(c, evk, lv[2 * k], lv[2 * k + 1], &nx[k], fork_stream(c, k)));
-        STATUS_TRY(fork_join(c, s, npair));
+            STATUS_TRY(op_mul(c, evk, lv[2 * k], lv[2 * k + 1], &nx[k], fork_stream(c, k, lane)));
+        STATUS_TRY(fork_join(c, s, npair, lane));
         for (int k = 0; k < 2 * npair; k++) ct_free(&lv[k], s);
         if (lv.size() % 2) nx.push_back(lv.back());
         lv.swap(nx);
@@ -529,27 +529,37 @@ extern "C" copse_status copse_ntt(copse_ctx *c, uint64_t *data, size_t n_polys, 
 }
 
 // ---------------------------------------------------------------- sessions (CUDA graphs)
-// A session fixes (context, keys, model, number of queries) and captures the
-// whole step -- feature encryption, Algorithm 1, decryption of the leaf bits --
-// once as a CUDA graph.  Every run copies the features and a fresh seed into
-// the session's device buffers and launches the graph: no host-side kernel
-// launches, allocations or synchronisation inside the step.  Intermediates are
-// graph memory nodes allocated and freed inside the graph.
+// A session fixes the context, keys and a list of work items (model, number of
+// queries) and records one step -- feature encryption, Algorithm 1 and
+// decryption of the leaf bits for every item -- once as a CUDA graph.  Items
+// run on separate lanes of streams inside the graph, so many queries of many
+// forests of uneven size are evaluated by one graph launch.  Every run copies
+// the features and a fresh seed into the session's device buffers and
+// launches the graph: no host-side kernel launches, allocations or
+// synchronisation inside the step.  Intermediates are graph memory nodes
+// allocated and freed inside the graph.
+struct SessItem {
+    copse_model *m = nullptr;
+    size_t nq = 0, feat_off = 0, bit_off = 0;
+};
+
 struct copse_session {
     copse_ctx *c = nullptr;
     const copse_keys *keys = nullptr;
     const copse_evk *evk = nullptr;
-    copse_model *m = nullptr;
-    size_t nq = 0;
-    uint32_t *d_feats = nullptr;  // [nq][n_features]
-    uint8_t *d_bits = nullptr;    // [nq][n_leaves]
-    u64 *d_seed = nullptr;        // encryption seed of the next run
+    std::vector<SessItem> items;
+    size_t n_feats = 0, n_bits = 0;
+    uint32_t *d_feats = nullptr;  // items' features, concatenated
+    uint8_t *d_bits = nullptr;    // items' leaf bits, concatenated
+    u64 *d_seed = nullptr;        // encryption seed of the next run (item i encrypts with seed + i)
     cudaStream_t cap = nullptr;
+    cudaEvent_t ev = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     ~copse_session() {
         if (exec) cudaGraphExecDestroy(exec);
         if (graph) cudaGraphDestroy(graph);
+        if (ev) cudaEventDestroy(ev);
         if (cap) cudaStreamDestroy(cap);
         cudaFree(d_feats);
         cudaFree(d_bits);
@@ -557,48 +567,77 @@ struct copse_session {
     }
 };
 
-// the captured body: everything it allocates it also frees
-static copse_status session_body(copse_session *S, cudaStream_t s) {
+// one item's step on stream s and lane `lane`; everything it allocates it also frees
+static copse_status item_body(copse_session *S, size_t i, cudaStream_t s, int lane) {
     copse_ctx *c = S->c;
-    const CompiledForest &f = S->m->f;
+    const SessItem &it = S->items[i];
+    const CompiledForest &f = it.m->f;
     copse_ctbuf feats;
     feats.ctx = c;
     feats.stream = s;
-    STATUS_TRY(encrypt_planes(c, S->keys, S->d_feats, (int)S->nq, (int)f.n_features, (int)f.K, (int)f.q, (int)f.pd(),
-                              (int)f.block, (int)f.precision, 0, feats.cts, s, S->d_seed));
+    STATUS_TRY(encrypt_planes(c, S->keys, S->d_feats + it.feat_off, (int)it.nq, (int)f.n_features, (int)f.K,
+                              (int)f.q, (int)f.pd(), (int)f.block, (int)f.precision, (u64)i, feats.cts, s,
+                              S->d_seed));
     DCt res;
-    STATUS_TRY(infer_impl(c, S->evk, S->m, &feats, &res, s));
+    STATUS_TRY(infer_impl(c, S->evk, it.m, &feats, &res, s, lane));
     u64 *slots = nullptr;
     STATUS_TRY(dev_alloc(c, (void **)&slots, (size_t)c->N * 8, s));
     STATUS_TRY(decrypt_slots_dev(c, S->keys, res, slots, s));
-    STATUS_TRY(extract_bits(c, slots, (int)S->nq, (int)f.block, (int)f.L, S->d_bits, s));
+    STATUS_TRY(extract_bits(c, slots, (int)it.nq, (int)f.block, (int)f.L, S->d_bits + it.bit_off, s));
     dev_free(slots, s);
     ct_free(&res, s);
     return COPSE_OK;  // feats frees its ciphertexts on s when it goes out of scope
 }
 
-extern "C" copse_status copse_session_create(copse_ctx *c, const copse_keys *keys, const copse_evk *evk,
-                                             copse_model *m, size_t n_queries, copse_session **out) {
-    if (!c || !keys || !evk || !m || !out) { set_error("null argument"); return COPSE_EINVAL; }
-    const CompiledForest &f = m->f;
-    if ((int)f.log_n != c->logN) { set_error("model compiled for another ring degree"); return COPSE_EINVAL; }
-    if (n_queries > (size_t)(c->N / f.block)) { set_error("more queries than slot blocks"); return COPSE_EINVAL; }
+static copse_status session_body(copse_session *S, cudaStream_t cap) {
+    copse_ctx *c = S->c;
+    const size_t n = S->items.size();
+    if (n == 1) return item_body(S, 0, cap, 0);
+    const int lanes = (int)std::min<size_t>(n, COPSE_MAX_LANES);
+    CUDA_TRY(cudaEventRecord(S->ev, cap));
+    for (int l = 0; l < lanes; l++) CUDA_TRY(cudaStreamWaitEvent(lane_stream(c, l), S->ev, 0));
+    for (size_t i = 0; i < n; i++) STATUS_TRY(item_body(S, i, lane_stream(c, (int)(i % lanes)), (int)(i % lanes)));
+    for (int l = 0; l < lanes; l++) {
+        CUDA_TRY(cudaEventRecord(lane_event(c, l), lane_stream(c, l)));
+        CUDA_TRY(cudaStreamWaitEvent(cap, lane_event(c, l), 0));
+    }
+    return COPSE_OK;
+}
+
+extern "C" copse_status copse_session_create_batch(copse_ctx *c, const copse_keys *keys, const copse_evk *evk,
+                                                   size_t n_items, copse_model *const *models,
+                                                   const size_t *n_queries, copse_session **out) {
+    if (!c || !keys || !evk || !out || !n_items || !models || !n_queries) { set_error("bad argument"); return COPSE_EINVAL; }
     auto S = std::make_unique<copse_session>();
     S->c = c;
     S->keys = keys;
     S->evk = evk;
-    S->m = m;
-    S->nq = n_queries;
+    for (size_t i = 0; i < n_items; i++) {
+        copse_model *m = models[i];
+        if (!m) { set_error("null model"); return COPSE_EINVAL; }
+        const CompiledForest &f = m->f;
+        if ((int)f.log_n != c->logN) { set_error("model compiled for another ring degree"); return COPSE_EINVAL; }
+        if (n_queries[i] > (size_t)(c->N / f.block)) { set_error("more queries than slot blocks"); return COPSE_EINVAL; }
+        SessItem it;
+        it.m = m;
+        it.nq = n_queries[i];
+        it.feat_off = S->n_feats;
+        it.bit_off = S->n_bits;
+        S->n_feats += it.nq * f.n_features;
+        S->n_bits += it.nq * f.L;
+        S->items.push_back(it);
+    }
     CUDA_TRY(cudaSetDevice(c->device));
-    CUDA_TRY(cudaMalloc(&S->d_feats, std::max<size_t>(n_queries * f.n_features, 1) * 4));
-    CUDA_TRY(cudaMalloc(&S->d_bits, std::max<size_t>(n_queries * f.L, 1)));
+    CUDA_TRY(cudaMalloc(&S->d_feats, std::max<size_t>(S->n_feats, 1) * 4));
+    CUDA_TRY(cudaMalloc(&S->d_bits, std::max<size_t>(S->n_bits, 1)));
     CUDA_TRY(cudaMalloc(&S->d_seed, 8));
-    CUDA_TRY(cudaMemset(S->d_feats, 0, std::max<size_t>(n_queries * f.n_features, 1) * 4));
+    CUDA_TRY(cudaMemset(S->d_feats, 0, std::max<size_t>(S->n_feats, 1) * 4));
     CUDA_TRY(cudaMemset(S->d_seed, 0, 8));
     CUDA_TRY(cudaStreamCreateWithFlags(&S->cap, cudaStreamNonBlocking));
-    // everything that synchronises or allocates outside the stream happens before capture
-    STATUS_TRY(upload_model(c, m, S->cap));
-    STATUS_TRY(fork_begin(c, S->cap, 0));
+    CUDA_TRY(cudaEventCreateWithFlags(&S->ev, cudaEventDisableTiming));
+    // everything that synchronises or creates resources happens before capture
+    for (const SessItem &it : S->items) STATUS_TRY(upload_model(c, it.m, S->cap));
+    STATUS_TRY(ensure_lanes(c, (int)std::min<size_t>(n_items, COPSE_MAX_LANES)));
     CUDA_TRY(cudaStreamSynchronize(S->cap));
     stats_suspend(true);
     c->capturing = true;
@@ -624,24 +663,30 @@ extern "C" copse_status copse_session_create(copse_ctx *c, const copse_keys *key
     return COPSE_OK;
 }
 
+extern "C" copse_status copse_session_create(copse_ctx *c, const copse_keys *keys, const copse_evk *evk,
+                                             copse_model *m, size_t n_queries, copse_session **out) {
+    return copse_session_create_batch(c, keys, evk, 1, &m, &n_queries, out);
+}
+
 extern "C" copse_status copse_session_run(copse_session *S, const uint32_t *feats, int feats_on_device,
                                           uint64_t seed, uint8_t *out_bits, int out_on_device, void *stream) {
-    if (!S || (S->nq && (!feats || !out_bits))) { set_error("null argument"); return COPSE_EINVAL; }
+    if (!S || (S->n_feats && !feats) || (S->n_bits && !out_bits)) { set_error("null argument"); return COPSE_EINVAL; }
     cudaStream_t s = as_stream(stream);
-    const CompiledForest &f = S->m->f;
-    const size_t nfe = S->nq * f.n_features, nb = S->nq * f.L;
     if (!feats_on_device)
-        for (size_t i = 0; i < nfe; i++)
-            if (f.precision < 32 && feats[i] >= (1u << f.precision)) { set_error("feature value needs more bits than the precision"); return COPSE_EINVAL; }
-    if (nfe)
-        CUDA_TRY(cudaMemcpyAsync(S->d_feats, feats, nfe * 4,
+        for (const SessItem &it : S->items) {
+            const uint32_t p = it.m->f.precision;
+            for (size_t k = it.feat_off; k < it.feat_off + it.nq * it.m->f.n_features; k++)
+                if (p < 32 && feats[k] >= (1u << p)) { set_error("feature value needs more bits than the precision"); return COPSE_EINVAL; }
+        }
+    if (S->n_feats)
+        CUDA_TRY(cudaMemcpyAsync(S->d_feats, feats, S->n_feats * 4,
                                  feats_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
     // pageable source: the copy is staged before this call returns, so `seed` may go out of scope
     CUDA_TRY(cudaMemcpyAsync(S->d_seed, &seed, 8, cudaMemcpyHostToDevice, s));
     CUDA_TRY(cudaGraphLaunch(S->exec, s));
-    if (nb)
-        CUDA_TRY(cudaMemcpyAsync(out_bits, S->d_bits, nb, out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
-                                 s));
+    if (S->n_bits)
+        CUDA_TRY(cudaMemcpyAsync(out_bits, S->d_bits, S->n_bits,
+                                 out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
     if (!out_on_device) CUDA_TRY(cudaStreamSynchronize(s));
     return COPSE_OK;
 }

@@ -81,36 +81,50 @@ void dev_free(void *p, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------- fork / join
-static copse_status ensure_side(copse_ctx *c) {
-    if (!c->side.empty()) return COPSE_OK;
-    CUDA_TRY(cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming));
-    for (int i = 0; i < COPSE_SIDE_STREAMS; i++) {
-        cudaStream_t st;
-        cudaEvent_t ev;
-        CUDA_TRY(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
-        CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
-        c->side.push_back(st);
-        c->side_done.push_back(ev);
+// A lane is COPSE_SIDE_STREAMS fork streams plus one lane stream (index
+// COPSE_SIDE_STREAMS) with an event each, and one fork event.  Independent
+// inferences use different lanes so their forks never share a stream.
+static constexpr int LANE_W = COPSE_SIDE_STREAMS + 1;
+
+copse_status ensure_lanes(copse_ctx *c, int lanes) {
+    if (lanes > COPSE_MAX_LANES) { set_error("too many lanes"); return COPSE_EINVAL; }
+    while ((int)c->fork_ev.size() < lanes) {
+        cudaEvent_t fe;
+        CUDA_TRY(cudaEventCreateWithFlags(&fe, cudaEventDisableTiming));
+        c->fork_ev.push_back(fe);
+        for (int i = 0; i < LANE_W; i++) {
+            cudaStream_t st;
+            cudaEvent_t ev;
+            CUDA_TRY(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+            CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+            c->side.push_back(st);
+            c->side_done.push_back(ev);
+        }
     }
     return COPSE_OK;
 }
 
-copse_status fork_begin(copse_ctx *c, cudaStream_t s, int n) {
-    STATUS_TRY(ensure_side(c));
-    CUDA_TRY(cudaEventRecord(c->fork_ev, s));
-    for (int i = 0; i < n && i < COPSE_SIDE_STREAMS; i++) CUDA_TRY(cudaStreamWaitEvent(c->side[i], c->fork_ev, 0));
+copse_status fork_begin(copse_ctx *c, cudaStream_t s, int n, int lane) {
+    STATUS_TRY(ensure_lanes(c, lane + 1));
+    CUDA_TRY(cudaEventRecord(c->fork_ev[lane], s));
+    for (int i = 0; i < n && i < COPSE_SIDE_STREAMS; i++)
+        CUDA_TRY(cudaStreamWaitEvent(c->side[lane * LANE_W + i], c->fork_ev[lane], 0));
     return COPSE_OK;
 }
 
-cudaStream_t fork_stream(copse_ctx *c, int i) { return c->side[i % COPSE_SIDE_STREAMS]; }
+cudaStream_t fork_stream(copse_ctx *c, int i, int lane) { return c->side[lane * LANE_W + i % COPSE_SIDE_STREAMS]; }
 
-copse_status fork_join(copse_ctx *c, cudaStream_t s, int n) {
+copse_status fork_join(copse_ctx *c, cudaStream_t s, int n, int lane) {
     for (int i = 0; i < n && i < COPSE_SIDE_STREAMS; i++) {
-        CUDA_TRY(cudaEventRecord(c->side_done[i], c->side[i]));
-        CUDA_TRY(cudaStreamWaitEvent(s, c->side_done[i], 0));
+        const int k = lane * LANE_W + i;
+        CUDA_TRY(cudaEventRecord(c->side_done[k], c->side[k]));
+        CUDA_TRY(cudaStreamWaitEvent(s, c->side_done[k], 0));
     }
     return COPSE_OK;
 }
+
+cudaStream_t lane_stream(copse_ctx *c, int lane) { return c->side[lane * LANE_W + COPSE_SIDE_STREAMS]; }
+cudaEvent_t lane_event(copse_ctx *c, int lane) { return c->side_done[lane * LANE_W + COPSE_SIDE_STREAMS]; }
 
 template <class T>
 static copse_status upload(copse_ctx *ctx, T **dst, const std::vector<T> &src) {
@@ -298,7 +312,7 @@ extern "C" void copse_ctx_destroy(copse_ctx *c) {
     cudaDeviceSynchronize();
     for (cudaStream_t st : c->side) cudaStreamDestroy(st);
     for (cudaEvent_t ev : c->side_done) cudaEventDestroy(ev);
-    if (c->fork_ev) cudaEventDestroy(c->fork_ev);
+    for (cudaEvent_t ev : c->fork_ev) cudaEventDestroy(ev);
     for (void *p : c->owned) cudaFree(p);
     if (c->pool) cudaMemPoolDestroy(c->pool);
     delete c;

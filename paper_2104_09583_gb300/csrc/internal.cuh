@@ -161,7 +161,7 @@ struct copse_ctx {
     // side streams for independent operations of one inference (fork/join with events)
     std::vector<cudaStream_t> side;
     std::vector<cudaEvent_t> side_done;
-    cudaEvent_t fork_ev = nullptr;
+    std::vector<cudaEvent_t> fork_ev;  // one per lane
     // set while a graph is being captured: allocations become graph memory nodes
     bool capturing = false;
 
@@ -171,10 +171,15 @@ struct copse_ctx {
 
 // Fork n independent branches off stream s: branch i runs on fork_stream(c, i)
 // after everything already queued on s; fork_join makes s wait for all n.
-copse_status fork_begin(copse_ctx *c, cudaStream_t s, int n);
-cudaStream_t fork_stream(copse_ctx *c, int i);
-copse_status fork_join(copse_ctx *c, cudaStream_t s, int n);
+// `lane` selects an independent set of fork streams (one per concurrent inference).
 #define COPSE_SIDE_STREAMS 16
+#define COPSE_MAX_LANES 32
+copse_status ensure_lanes(copse_ctx *c, int lanes);
+copse_status fork_begin(copse_ctx *c, cudaStream_t s, int n, int lane = 0);
+cudaStream_t fork_stream(copse_ctx *c, int i, int lane = 0);
+copse_status fork_join(copse_ctx *c, cudaStream_t s, int n, int lane = 0);
+cudaStream_t lane_stream(copse_ctx *c, int lane);  // the lane's own stream
+cudaEvent_t lane_event(copse_ctx *c, int lane);
 
 // device memory from the context's stream-ordered pool
 copse_status dev_alloc(copse_ctx *ctx, void **p, size_t bytes, cudaStream_t s);

@@ -25,6 +25,7 @@ constexpr int TPB = 256;
 constexpr int MAX_ALPHA = 40;
 constexpr int MAX_ACC = 8;
 constexpr int CHUNK_ROT = 64;
+constexpr int MM_PARTS = 8;  // rotation ranges with their own partial sums in k_mm_fused
 
 inline unsigned nblk(size_t n) { return (unsigned)((n + TPB - 1) / TPB); }
 
@@ -235,14 +236,20 @@ struct MmTable {
     u64 *acc[MAX_ACC];                   // [2][ell+alpha][N]
 };
 
+// grid.y splits the chunk's rotations into gridDim.y contiguous ranges; range y
+// accumulates into its own partial sums at acc + y * part_stride (summed later).
 __global__ void __launch_bounds__(256) k_mm_fused(const u64 *yhat, const u64 *c0, int nrot, const MmTable tab,
-                                                  int nacc, int ell, int alpha, int L, int logN, const PrimeDev *pr,
-                                                  KsTables T) {
+                                                  int nacc, size_t part_stride, int ell, int alpha, int L, int logN,
+                                                  const PrimeDev *pr, KsTables T) {
     const int N = 1 << logN;
     const int nx = ell + alpha, nd = (ell + alpha - 1) / alpha, NB = L + alpha;
     const size_t n_el = (size_t)nx << logN;
     const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n_el) return;
+    const int per = (nrot + (int)gridDim.y - 1) / (int)gridDim.y;
+    const int k0 = (int)blockIdx.y * per, k1 = min(nrot, k0 + per);
+    if (k0 >= k1) return;
+    const size_t poff = (size_t)blockIdx.y * part_stride;
     const int r = (int)(e >> logN);
     const uint32_t n = (uint32_t)(e & (N - 1));
     const int g = r < ell ? r : L + (r - ell);
@@ -250,10 +257,10 @@ __global__ void __launch_bounds__(256) k_mm_fused(const u64 *yhat, const u64 *c0
     const u64 Pm = r < ell ? T.md_P[r] : 0;
     u64 a0[MAX_ACC], a1[MAX_ACC];
     for (int x = 0; x < nacc; x++) {
-        a0[x] = tab.acc[x][e];
-        a1[x] = tab.acc[x][n_el + e];
+        a0[x] = tab.acc[x][poff + e];
+        a1[x] = tab.acc[x][poff + n_el + e];
     }
-    for (int k = 0; k < nrot; k++) {
+    for (int k = k0; k < k1; k++) {
         const MmJob J = tab.job[k];
         const uint32_t src = galois_src(n, J.g, logN);
         u64 u0 = 0, u1 = 0;
@@ -274,9 +281,22 @@ __global__ void __launch_bounds__(256) k_mm_fused(const u64 *yhat, const u64 *c0
         }
     }
     for (int x = 0; x < nacc; x++) {
-        tab.acc[x][e] = a0[x];
-        tab.acc[x][n_el + e] = a1[x];
+        tab.acc[x][poff + e] = a0[x];
+        tab.acc[x][poff + n_el + e] = a1[x];
     }
+}
+
+// out[i] = sum_y part[y * stride + i] over nparts partial sums of extended-basis
+// polynomials ([npoly][ell+alpha][N] each)
+__global__ void k_sum_parts(const u64 *part, size_t stride, int nparts, u64 *out, size_t words, int ell, int alpha,
+                            int L, int logN, const PrimeDev *pr) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= words) return;
+    const int r = (int)((i >> logN) % (size_t)(ell + alpha));
+    const u64 q = pr[r < ell ? r : L + (r - ell)].q;
+    u64 s = part[i];
+    for (int y = 1; y < nparts; y++) s = add_mod(s, part[(size_t)y * stride + i], q);
+    out[i] = s;
 }
 
 // ModDown finish over npoly polys: out = (u - t W) * P^-1, u with stride ustride (its first
@@ -436,7 +456,8 @@ __global__ void k_enc_prep(const u64 *mt, int p, u64 seed_val, const u64 *seed_p
                            const PrimeDev *pr, u64 *U, u64 *X0, u64 *X1) {
     size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= ((size_t)p << logN)) return;
-    const u64 seed = seed_ptr ? *seed_ptr : seed_val;
+    // replayed graphs: the run's seed from device memory plus the item's offset
+    const u64 seed = seed_ptr ? *seed_ptr + seed_val : seed_val;
     const int i = (int)(e >> logN);
     const u64 n = e & ((1ull << logN) - 1);
     const u64 sb = 0x1000000ull + 3ull * (u64)i;
@@ -733,9 +754,15 @@ copse_status op_matmul(copse_ctx *c, const copse_evk *evk, const DCt &v, const s
     STATUS_TRY(sc.get(c, &res, (size_t)nacc * per));
     CUDA_TRY(cudaMemsetAsync(res, 0, (size_t)nacc * per * sizeof(u64), s));
     if (!ks_idx.empty()) {
+        // rotations of a chunk are split into `parts` ranges with their own partial sums
+        // (more independent threads to hide the gathers' latency), summed before ModDown
+        const int parts = (int)std::min<size_t>(MM_PARTS, (ks_idx.size() + 7) / 8);
+        const size_t part_stride = (size_t)nacc * ext;
+        u64 *part = nullptr;
         STATUS_TRY(sc.get(c, &acc, (size_t)nacc * ext));
+        STATUS_TRY(sc.get(c, &part, (size_t)parts * part_stride));
         STATUS_TRY(sc.get(c, &W, (size_t)nacc * per));
-        CUDA_TRY(cudaMemsetAsync(acc, 0, (size_t)nacc * ext * sizeof(u64), s));
+        CUDA_TRY(cudaMemsetAsync(part, 0, (size_t)parts * part_stride * sizeof(u64), s));
         u64 *yhat = nullptr;
         STATUS_TRY(ks_modup(c, v.data + (size_t)ell * N, ell, sc, &yhat, s));
         const int nd = (ell + A - 1) / A;
@@ -754,17 +781,21 @@ copse_status op_matmul(copse_ctx *c, const copse_evk *evk, const DCt &v, const s
                         nz_pt += pt[a0 + a][r] != nullptr;
                     }
                 }
-                for (int a = 0; a < na; a++) tab.acc[a] = acc + (size_t)(a0 + a) * ext;
+                for (int a = 0; a < na; a++) tab.acc[a] = part + (size_t)(a0 + a) * ext;
                 // algorithmic bytes: keys, diagonals, accumulators in and out, the rotated
                 // digits and c0 once
-                const double bytes = 8.0 * N * ((double)nr * 2 * nd * nx + nz_pt * (double)nx + 4.0 * na * nx +
-                                                (double)nd * nx + ell);
+                const double bytes = 8.0 * N * ((double)nr * 2 * nd * nx + nz_pt * (double)nx +
+                                                4.0 * na * nx * parts + (double)nd * nx + ell);
                 TIMED("mm_fused", bytes, s,
-                      k_mm_fused<<<nblk((size_t)nx * N), TPB, 0, s>>>(yhat, v.data, nr, tab, na, ell, A, c->L,
-                                                                      c->logN, c->d_prime, c->ks));
+                      k_mm_fused<<<dim3(nblk((size_t)nx * N), parts), TPB, 0, s>>>(
+                          yhat, v.data, nr, tab, na, part_stride, ell, A, c->L, c->logN, c->d_prime, c->ks));
                 LAUNCH_CHECK();
             }
         }
+        TIMED("sum_parts", 8.0 * (double)(parts + 1) * part_stride, s,
+              k_sum_parts<<<nblk(part_stride), TPB, 0, s>>>(part, part_stride, parts, acc, part_stride, ell, A,
+                                                            c->L, c->logN, c->d_prime));
+        LAUNCH_CHECK();
         // one ModDown per accumulator (both components)
         STATUS_TRY(ntt_inverse(c, batch(acc, (size_t)nx * N, 2 * nacc, ell, A, ell), s));
         TIMED("moddown_conv", 8.0 * N * 2.0 * nacc * ((double)A + ell), s,

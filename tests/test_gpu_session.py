@@ -76,3 +76,38 @@ def test_session_rejects_too_many_queries():
         assert e.value.name == "EINVAL"
     finally:
         _close(ctx, model, keys, evk)
+
+
+def test_batch_session_three_forests_in_one_launch():
+    """Items of three forests with different query blocks (32, 3 x 32 and 4 queries) in one graph."""
+    W = synth.WORKLOADS["batch3-n16384"]
+    ctx = K.copse_ctx_create(W.log_n, W.bits, W.primes, W.dnum)
+    texts = W.forest_texts()
+    models = [K.copse_compile_forest(t, W.precision(k), W.n_features(k), W.log_n) for k, t in enumerate(texts)]
+    keys, evk = K.copse_keygen(ctx, 9, models)
+    infos = [K.copse_model_info_get(m) for m in models]
+    per_ct = [(1 << W.log_n) // i["block"] for i in infos]
+    items = [(0, per_ct[0]), (1, per_ct[1]), (1, per_ct[1]), (1, 5), (2, per_ct[2])]
+    sess = K.copse_session_create_batch(ctx, keys, evk, [models[k] for k, _ in items], [n for _, n in items])
+    trees = [Cp.parse_forest(t)[1] for t in texts]
+    try:
+        for run in range(2):
+            qs = [synth.random_queries(31 * run + i, n, infos[k]["n_features"], W.precision(k))
+                  for i, (k, n) in enumerate(items)]
+            feats = np.concatenate([q.reshape(-1) for q in qs])
+            out = np.zeros(sum(n * infos[k]["n_leaves"] for k, n in items), dtype=np.uint8)
+            K.copse_session_run(sess, feats, 77 + run, out)
+            off = 0
+            for (k, n), q in zip(items, qs):
+                L = infos[k]["n_leaves"]
+                got = out[off: off + n * L].reshape(n, L)
+                off += n * L
+                for j in range(n):
+                    assert got[j].tolist() == Cp.classify_plain(trees[k], q[j]), f"run {run} forest {k} query {j}"
+    finally:
+        K.copse_session_destroy(sess)
+        K.copse_keys_destroy(keys)
+        K.copse_evk_destroy(evk)
+        for m in models:
+            K.copse_model_destroy(m)
+        K.copse_ctx_destroy(ctx)
