@@ -46,19 +46,23 @@ def parse():
     ap.add_argument("--no-stats", action="store_true", help="skip the per-kernel event timers")
     ap.add_argument("--profile", action="store_true", help="bracket the timed region with cudaProfilerStart/Stop")
     ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work for cpu_baseline")
+    ap.add_argument("--no-serving", action="store_true", help="skip the Poisson-arrival serving leg")
     return ap.parse_args()
 
 
 # ---------------------------------------------------------------- distributed
 def dist_setup():
+    """One process per GPU (replicas: queries are independent, nothing is exchanged on the
+    data path).  NCCL with CUDA, gloo without (host-side tests)."""
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if ws > 1:
         import torch
         import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     return ws, rank, local
 
 
@@ -69,13 +73,20 @@ def barrier(ws):
 
 
 def max_over_ranks(x, ws):
+    """The slowest rank's time (the job's wall time for weak scaling)."""
     if ws == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_throughput(units_per_rank, total_ms, ws):
+    """Whole-job value: the units all ranks processed / the slowest rank's time."""
+    return ws * units_per_rank / (max_over_ranks(total_ms, ws) / 1e3)
 
 
 # ---------------------------------------------------------------- clocks
@@ -325,6 +336,9 @@ def run_cuda(args, ws, rank, local):
                 "avg_launch_us": v["ms"] * 1e3 / v["launches"], "peak_source": f"{how} hbm_gbs (copy)",
                 "measured_on": "instrumented host-launched replay of the timed step (CUDA events per launch)"}
 
+    serving = None if args.no_serving else run_serving(local)
+    batch3 = None if args.no_serving else run_batch3(local)
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = oracle_baseline(W, text, args.cpu_budget)
@@ -346,10 +360,140 @@ def run_cuda(args, ws, rank, local):
                    "l2": "working set > L2 (rotation keys alone are %.1f GB)" % (
                        (info["n_rot_reshuffle"] + info["n_rot_level"]) * 3 * 2 * (W.primes + 4) * N * 8 / 1e9)},
         "labels_ok": ok, "path": "graph session", "batched": batched, "plain_ops": plain_ops, "e2e": e2e,
-        "gpu_launches": launches_total,
+        "serving": serving, "batch3": batch3, "gpu_launches": launches_total,
         "roofline": roof, "kernels": kern, "clocks": ck, "cpu_baseline": cpu,
     }
     return line
+
+
+# ---------------------------------------------------------------- serving
+def run_serving(local, rate=200.0, n_req=1000, warm=100, seed=5):
+    """Poisson arrivals (mean `rate` per second) of single queries against four resident models
+    (the N = 2^14 bench forest and the three batching forests), each model chosen uniformly; the
+    server batches them continuously into graph launches.  Latency is submit -> completion as the
+    server measures it; throughput is completed requests over the wall time of the run."""
+    import queue
+    import threading
+
+    from paper_2104_09583_gb300 import copse as K
+    from paper_2104_09583_gb300 import synth
+
+    Wf, Wb = synth.WORKLOADS["forest100-n16384"], synth.WORKLOADS["batch3-n16384"]
+    specs = [(Wf.forest_texts()[0], Wf.precision(), Wf.n_features())] + \
+            [(t, Wb.precision(k), Wb.n_features(k)) for k, t in enumerate(Wb.forest_texts())]
+    ctx = K.copse_ctx_create(Wf.log_n, Wf.bits, Wf.primes, Wf.dnum, device=local)
+    models = [K.copse_compile_forest(t, p, nf, Wf.log_n) for t, p, nf in specs]
+    keys, evk = K.copse_keygen(ctx, 13, models)
+    infos = [K.copse_model_info_get(m) for m in models]
+    srv = K.copse_server_create(ctx, keys, evk, models)
+    rng = np.random.default_rng(seed)
+    total = warm + n_req
+    choice = rng.integers(len(models), size=total)
+    gaps = rng.exponential(1.0 / rate, size=total)
+    qs = [synth.random_queries(10000 + i, 1, infos[k]["n_features"], specs[k][1])[0] for i, k in enumerate(choice)]
+    tickets = queue.Queue()
+    refused = [0]
+
+    def submitter():
+        t_next = time.perf_counter()
+        for i in range(total):
+            t_next += gaps[i]
+            d = t_next - time.perf_counter()
+            if d > 0:
+                time.sleep(d)
+            try:
+                tickets.put((i, int(choice[i]), K.copse_server_submit(srv, int(choice[i]), qs[i])))
+            except K.CopseError:
+                refused[0] += 1
+                tickets.put((i, int(choice[i]), None))
+
+    th = threading.Thread(target=submitter)
+    t0 = time.perf_counter()
+    th.start()
+    lat, ok, t_first, t_last = [], True, None, None
+    for _ in range(total):
+        i, k, t = tickets.get()
+        if t is None:
+            continue
+        bits, ms = K.copse_server_poll(srv, t, infos[k]["n_leaves"], 60000)
+        ok &= bool(np.array_equal(bits, K.copse_classify_plain(models[k], qs[i][None, :])[0]))
+        if i >= warm:
+            lat.append(ms)
+            now = time.perf_counter()
+            t_first = t_first if t_first is not None else now
+            t_last = now
+    th.join()
+    wall = time.perf_counter() - t0
+    K.copse_server_destroy(srv)
+    K.copse_keys_destroy(keys)
+    K.copse_evk_destroy(evk)
+    for m in models:
+        K.copse_model_destroy(m)
+    K.copse_ctx_destroy(ctx)
+    measured_s = sum(gaps[warm:])
+    return {"value": len(lat) / measured_s, "unit": UNIT, "offered_rate": rate, "requests": n_req,
+            "warmup_requests": warm, "refused": refused[0], "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(np.mean(lat)), "labels_ok": ok,
+            "models": [f"{i['n_trees']} trees, {i['b']} branches, block {i['block']}" for i in infos],
+            "wall_s": wall}
+
+
+def run_batch3(local, steps=3, warmup=1):
+    """256 queries over three forests (1 x depth 3, 4 x depth 5, 16 x depth 6; 8/16/32 features, 8-bit)
+    evaluated by one graph launch: one work item per ciphertext (32 + 3 x 32 + 32 x 4 queries)."""
+    import torch
+
+    from paper_2104_09583_gb300 import copse as K
+    from paper_2104_09583_gb300 import synth
+
+    W = synth.WORKLOADS["batch3-n16384"]
+    ctx = K.copse_ctx_create(W.log_n, W.bits, W.primes, W.dnum, device=local)
+    texts = W.forest_texts()
+    models = [K.copse_compile_forest(t, W.precision(k), W.n_features(k), W.log_n) for k, t in enumerate(texts)]
+    keys, evk = K.copse_keygen(ctx, 17, models)
+    infos = [K.copse_model_info_get(m) for m in models]
+    per = [(1 << W.log_n) // i["block"] for i in infos]
+    items = []
+    for k, nq in enumerate(W.queries):
+        while nq > 0:
+            items.append((k, min(per[k], nq)))
+            nq -= per[k]
+    qa = W.query_arrays()
+    feats, used = [], [0] * len(models)
+    for k, n in items:
+        feats.append(qa[k][used[k]: used[k] + n].reshape(-1))
+        used[k] += n
+    feats = np.concatenate(feats)
+    out = np.zeros(sum(n * infos[k]["n_leaves"] for k, n in items), dtype=np.uint8)
+    sess = K.copse_session_create_batch(ctx, keys, evk, [models[k] for k, _ in items], [n for _, n in items])
+    stream = torch.cuda.current_stream().cuda_stream
+    for w in range(warmup):
+        K.copse_session_run(sess, feats, 70 + w, out, stream=stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for i in range(steps):
+        K.copse_session_run(sess, feats, 80 + i, out, stream=stream)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    ok, off, used = True, 0, [0] * len(models)
+    for k, n in items:
+        Lk = infos[k]["n_leaves"]
+        want = K.copse_classify_plain(models[k], qa[k][used[k]: used[k] + n])
+        ok &= bool(np.array_equal(out[off: off + n * Lk].reshape(n, Lk), want))
+        off += n * Lk
+        used[k] += n
+    K.copse_session_destroy(sess)
+    K.copse_keys_destroy(keys)
+    K.copse_evk_destroy(evk)
+    for m in models:
+        K.copse_model_destroy(m)
+    K.copse_ctx_destroy(ctx)
+    return {"value": 256 / (ms / 1e3), "unit": UNIT, "ms_per_launch": ms, "queries_per_launch": 256,
+            "items": len(items), "labels_ok": ok,
+            "forests": [f"{i['n_trees']} trees, {i['b']} branches, {i['n_rot_reshuffle']}+{i['n_rot_level']} "
+                        f"rotations, {p} queries/ciphertext" for i, p in zip(infos, per)]}
 
 
 # ---------------------------------------------------------------- CPU oracle (baseline / reference arm)

@@ -47,6 +47,8 @@ typedef int copse_status;
 #define COPSE_ENOKEY (-5)   /* a rotation key the model needs is missing        */
 #define COPSE_ELEVEL (-6)   /* the prime chain is too short for the circuit    */
 #define COPSE_EFIT (-7)     /* the model's slot block does not fit a slot row   */
+#define COPSE_EADMIT (-8)   /* the server's request queue is full (admission)  */
+#define COPSE_ETIMEOUT (-9) /* a wait ran out before the result was ready      */
 
 /* Ring and RNS parameters.  All primes are = 1 mod 2*N*t and below
  * 2^prime_bits, chosen in decreasing order: n_primes ciphertext primes, then
@@ -213,6 +215,36 @@ copse_status copse_session_create_batch(copse_ctx *ctx, const copse_keys *keys, 
 copse_status copse_session_run(copse_session *session, const uint32_t *feats, int feats_on_device, uint64_t seed,
                                uint8_t *out_bits, int out_on_device, void *stream);
 void copse_session_destroy(copse_session *session);
+
+/* ---------------------------------------------------------------- serving
+ * The evaluator of the paper's workflow (Section 3.2: the server accepts
+ * inference queries against resident models) as a request loop.  Each request
+ * is one query for one model.  A worker thread packs a model's pending
+ * requests into the slot blocks of that model's next launch (continuous
+ * batching: requests that arrive while a launch is on the GPU join the next
+ * one) and keeps up to two launches per model in flight.  Keys, model
+ * plaintexts and the launches' device memory stay resident; device memory is
+ * reserved at creation, and a request is admitted only while the pending
+ * queue holds fewer than max_pending requests (0 = four times the slot
+ * capacity of all in-flight launches).  The server is internally locked. */
+typedef struct copse_server copse_server;
+
+copse_status copse_server_create(copse_ctx *ctx, const copse_keys *keys, const copse_evk *evk,
+                                 copse_model *const *models, size_t n_models, size_t max_pending,
+                                 copse_server **out);
+/* Queue one query (feats[n_features], host) for models[model_id].  Returns a
+ * ticket, or COPSE_EADMIT when the queue is full (nothing queued). */
+copse_status copse_server_submit(copse_server *server, uint32_t model_id, const uint32_t *feats, uint64_t *ticket);
+/* Wait up to timeout_ms for a ticket: its leaf bits into out_bits[n_leaves]
+ * (host) and, if latency_ms is not NULL, the time from submit to completion.
+ * COPSE_ETIMEOUT if not ready (the ticket stays valid); a ticket is released
+ * by the successful poll. */
+copse_status copse_server_poll(copse_server *server, uint64_t ticket, uint8_t *out_bits, int timeout_ms,
+                               double *latency_ms);
+/* Requests waiting for a launch, and requests in launches on the GPU. */
+copse_status copse_server_pending(copse_server *server, size_t *queued, size_t *in_flight);
+/* Stops the worker after the launches in flight and frees everything. */
+void copse_server_destroy(copse_server *server);
 
 /* ---------------------------------------------------------------- buffers */
 

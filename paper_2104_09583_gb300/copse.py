@@ -397,3 +397,48 @@ def copse_session_create_batch(ctx, keys, evk, models, n_queries):
     h = C.c_void_p()
     _check(_lib.copse_session_create_batch(ctx, keys, evk, n, ms, qs, C.byref(h)))
     return h
+
+
+# ---------------------------------------------------------------- serving
+STATUS.update({-8: "EADMIT", -9: "ETIMEOUT"})
+_lib.copse_server_create.restype = C.c_int
+_lib.copse_server_create.argtypes = [vp, vp, vp, C.POINTER(C.c_void_p), C.c_size_t, C.c_size_t, pvp]
+_lib.copse_server_submit.restype = C.c_int
+_lib.copse_server_submit.argtypes = [vp, C.c_uint32, u32p, C.POINTER(C.c_uint64)]
+_lib.copse_server_poll.restype = C.c_int
+_lib.copse_server_poll.argtypes = [vp, C.c_uint64, u8p, C.c_int, C.POINTER(C.c_double)]
+_lib.copse_server_pending.restype = C.c_int
+_lib.copse_server_pending.argtypes = [vp, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)]
+_lib.copse_server_destroy.restype = None
+_lib.copse_server_destroy.argtypes = [vp]
+
+
+def copse_server_create(ctx, keys, evk, models, max_pending=0):
+    arr = (C.c_void_p * len(models))(*[m.value for m in models])
+    h = C.c_void_p()
+    _check(_lib.copse_server_create(ctx, keys, evk, arr, len(models), max_pending, C.byref(h)))
+    return h
+
+
+def copse_server_submit(server, model_id, feats):
+    t = C.c_uint64()
+    _check(_lib.copse_server_submit(server, model_id, np.ascontiguousarray(feats, dtype=np.uint32), C.byref(t)))
+    return t.value
+
+
+def copse_server_poll(server, ticket, n_leaves, timeout_ms=10000):
+    """(bits, latency_ms) or raises CopseError(ETIMEOUT)."""
+    out = np.zeros(n_leaves, dtype=np.uint8)
+    lat = C.c_double()
+    _check(_lib.copse_server_poll(server, ticket, out, timeout_ms, C.byref(lat)))
+    return out, lat.value
+
+
+def copse_server_pending(server):
+    a, b = C.c_size_t(), C.c_size_t()
+    _check(_lib.copse_server_pending(server, C.byref(a), C.byref(b)))
+    return a.value, b.value
+
+
+def copse_server_destroy(server):
+    _lib.copse_server_destroy(server)

@@ -157,6 +157,12 @@ extern "C" copse_status copse_compile_forest(const char *text, size_t len, uint3
 
 extern "C" void copse_model_destroy(copse_model *m) { delete m; }
 
+uint32_t model_block(const copse_model *m) { return m->f.block; }
+uint32_t model_features(const copse_model *m) { return m->f.n_features; }
+uint32_t model_leaves(const copse_model *m) { return m->f.L; }
+uint32_t model_precision(const copse_model *m) { return m->f.precision; }
+int model_log_n(const copse_model *m) { return (int)m->f.log_n; }
+
 extern "C" copse_status copse_model_info_get(const copse_model *m, copse_model_info *info) {
     if (!m || !info) { set_error("null argument"); return COPSE_EINVAL; }
     const CompiledForest &f = m->f;
@@ -690,6 +696,20 @@ extern "C" copse_status copse_session_run(copse_session *S, const uint32_t *feat
     if (!out_on_device) CUDA_TRY(cudaStreamSynchronize(s));
     return COPSE_OK;
 }
+
+// Asynchronous launch for the server: features and bits may be pinned host or device
+// memory (copies by unified addressing), values already validated, nothing synchronised.
+copse_status session_launch(copse_session *S, const uint32_t *feats, uint64_t seed, uint8_t *bits, cudaStream_t s,
+                            uint64_t *seed_slot) {
+    if (S->n_feats) CUDA_TRY(cudaMemcpyAsync(S->d_feats, feats, S->n_feats * 4, cudaMemcpyDefault, s));
+    *seed_slot = seed;  // pinned, owned by the caller and not reused before this launch completes
+    CUDA_TRY(cudaMemcpyAsync(S->d_seed, seed_slot, 8, cudaMemcpyDefault, s));
+    CUDA_TRY(cudaGraphLaunch(S->exec, s));
+    if (S->n_bits) CUDA_TRY(cudaMemcpyAsync(bits, S->d_bits, S->n_bits, cudaMemcpyDefault, s));
+    return COPSE_OK;
+}
+
+size_t session_queries(const copse_session *S) { return S->items.empty() ? 0 : S->items[0].nq; }
 
 extern "C" void copse_session_destroy(copse_session *S) {
     if (!S) return;

@@ -277,6 +277,18 @@ copse_status encrypt_planes(copse_ctx *c, const copse_keys *k, const uint32_t *d
 copse_status decrypt_slots_dev(copse_ctx *c, const copse_keys *k, const DCt &ct, u64 *d_slots, cudaStream_t s);
 copse_status extract_bits(copse_ctx *c, const u64 *d_slots, int nq, int block, int L, uint8_t *d_bits,
                           cudaStream_t s);
+// sessions (copse.cu): asynchronous launch with feature/bit buffers in pinned host or
+// device memory; seed_slot is pinned host memory holding the run's seed until it completes
+copse_status session_launch(copse_session *S, const uint32_t *feats, uint64_t seed, uint8_t *bits, cudaStream_t s,
+                            uint64_t *seed_slot);
+size_t session_queries(const copse_session *S);
+// model accessors for the server (copse.cu)
+uint32_t model_block(const copse_model *m);
+uint32_t model_features(const copse_model *m);
+uint32_t model_leaves(const copse_model *m);
+uint32_t model_precision(const copse_model *m);
+int model_log_n(const copse_model *m);
+
 // coefficient-form export/import of one ciphertext (device scratch, host buffer)
 copse_status ct_to_coeff_host(copse_ctx *c, const DCt &ct, u64 *host, cudaStream_t s);
 copse_status ct_from_coeff_host(copse_ctx *c, const u64 *host, int level, DCt *out, cudaStream_t s);

@@ -1,0 +1,268 @@
+// Serving loop: requests (one query each) against several device-resident
+// models arrive at any time; a worker thread packs the pending requests of a
+// model into the slot blocks of that model's next graph launch (continuous
+// batching: requests that arrive while a launch is on the GPU go into the
+// next one), runs up to two launches per model concurrently on their own
+// streams, and completes tickets as launches finish.  Evaluation keys,
+// model plaintexts and the graphs' memory stay on the device.  Admission:
+// the graphs' device memory is reserved when the server is created (each
+// model's two launches are replayed once), and while running a request is
+// admitted only if the pending queue -- host memory -- has room, else
+// COPSE_EADMIT.
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+
+#include "internal.cuh"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Request {
+    uint64_t ticket;
+    std::vector<uint32_t> feats;
+};
+
+struct Ticket {
+    int model;
+    int state;  // 0 queued, 1 running, 2 done
+    std::vector<uint8_t> bits;
+    Clock::time_point t_submit, t_done;
+};
+
+struct Buffer {
+    copse_session *sess = nullptr;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+    uint32_t *h_feats = nullptr;  // pinned [per_ct][nf]
+    uint8_t *h_bits = nullptr;    // pinned [per_ct][L]
+    uint64_t *h_seed = nullptr;   // pinned
+    bool busy = false;
+    std::vector<uint64_t> tickets;
+};
+
+struct ModelSlot {
+    copse_model *m = nullptr;
+    size_t per_ct = 0, nf = 0, L = 0;
+    uint32_t precision = 0;
+    Buffer buf[2];
+    std::deque<Request> pending;
+};
+
+}  // namespace
+
+struct copse_server {
+    copse_ctx *c = nullptr;
+    std::vector<ModelSlot> models;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::unordered_map<uint64_t, Ticket> tickets;
+    std::thread worker;
+    bool stop = false;
+    size_t max_pending = 0, n_pending = 0;
+    uint64_t next_ticket = 1, seed = 0;
+    copse_status worker_error = COPSE_OK;
+    std::string worker_msg;
+
+    void loop();
+};
+
+void copse_server::loop() {
+    cudaSetDevice(c->device);
+    std::unique_lock<std::mutex> lk(mu);
+    while (!stop) {
+        bool progressed = false;
+        // complete finished launches
+        for (ModelSlot &ms : models)
+            for (Buffer &b : ms.buf) {
+                if (!b.busy || cudaEventQuery(b.done) != cudaSuccess) continue;
+                const Clock::time_point now = Clock::now();
+                for (size_t j = 0; j < b.tickets.size(); j++) {
+                    auto it = tickets.find(b.tickets[j]);
+                    if (it == tickets.end()) continue;
+                    it->second.bits.assign(b.h_bits + j * ms.L, b.h_bits + (j + 1) * ms.L);
+                    it->second.state = 2;
+                    it->second.t_done = now;
+                }
+                b.tickets.clear();
+                b.busy = false;
+                progressed = true;
+                cv_done.notify_all();
+            }
+        // start launches for models with pending requests and a free buffer
+        for (ModelSlot &ms : models)
+            for (Buffer &b : ms.buf) {
+                if (b.busy || ms.pending.empty()) continue;
+                const size_t n = std::min(ms.per_ct, ms.pending.size());
+                memset(b.h_feats, 0, ms.per_ct * ms.nf * 4);
+                for (size_t j = 0; j < n; j++) {
+                    Request &r = ms.pending.front();
+                    memcpy(b.h_feats + j * ms.nf, r.feats.data(), ms.nf * 4);
+                    b.tickets.push_back(r.ticket);
+                    tickets[r.ticket].state = 1;
+                    ms.pending.pop_front();
+                }
+                n_pending -= n;
+                copse_status st = session_launch(b.sess, b.h_feats, ++seed * 0x9E3779B97F4A7C15ULL, b.h_bits,
+                                                 b.stream, b.h_seed);
+                if (st == COPSE_OK && cudaEventRecord(b.done, b.stream) != cudaSuccess) st = COPSE_ECUDA;
+                if (st != COPSE_OK) {
+                    worker_error = st;
+                    worker_msg = copse_last_error();
+                    stop = true;
+                    cv_done.notify_all();
+                    return;
+                }
+                b.busy = true;
+                progressed = true;
+            }
+        if (!progressed) {
+            bool any_busy = false;
+            for (ModelSlot &ms : models) any_busy |= ms.buf[0].busy || ms.buf[1].busy;
+            // poll the GPU briefly while launches are in flight; otherwise sleep until a submit
+            if (any_busy)
+                cv_work.wait_for(lk, std::chrono::microseconds(50));
+            else
+                cv_work.wait(lk, [&] { return stop || n_pending > 0; });
+        }
+    }
+}
+
+extern "C" copse_status copse_server_create(copse_ctx *c, const copse_keys *keys, const copse_evk *evk,
+                                            copse_model *const *models, size_t n_models, size_t max_pending,
+                                            copse_server **out) {
+    if (!c || !keys || !evk || !models || !n_models || !out) { set_error("bad argument"); return COPSE_EINVAL; }
+    auto S = std::make_unique<copse_server>();
+    S->c = c;
+    S->models.resize(n_models);
+    size_t total_slots = 0;
+    for (size_t i = 0; i < n_models; i++) {
+        ModelSlot &ms = S->models[i];
+        ms.m = models[i];
+        if (model_log_n(ms.m) != c->logN) { set_error("model compiled for another ring degree"); return COPSE_EINVAL; }
+        ms.per_ct = (size_t)c->N / model_block(ms.m);
+        ms.nf = model_features(ms.m);
+        ms.L = model_leaves(ms.m);
+        ms.precision = model_precision(ms.m);
+        total_slots += 2 * ms.per_ct;
+    }
+    S->max_pending = max_pending ? max_pending : 4 * total_slots;
+    auto cleanup = [&](copse_status st) {
+        for (ModelSlot &ms : S->models)
+            for (Buffer &b : ms.buf) {
+                if (b.sess) copse_session_destroy(b.sess);
+                if (b.stream) cudaStreamDestroy(b.stream);
+                if (b.done) cudaEventDestroy(b.done);
+                cudaFreeHost(b.h_feats);
+                cudaFreeHost(b.h_bits);
+                cudaFreeHost(b.h_seed);
+            }
+        return st;
+    };
+    CUDA_TRY(cudaSetDevice(c->device));
+    for (ModelSlot &ms : S->models)
+        for (Buffer &b : ms.buf) {
+            copse_status st = copse_session_create(c, keys, evk, ms.m, ms.per_ct, &b.sess);
+            if (st) return cleanup(st);
+            if (cudaStreamCreateWithFlags(&b.stream, cudaStreamNonBlocking) != cudaSuccess ||
+                cudaEventCreateWithFlags(&b.done, cudaEventDisableTiming) != cudaSuccess ||
+                cudaMallocHost(&b.h_feats, std::max<size_t>(ms.per_ct * ms.nf, 1) * 4) != cudaSuccess ||
+                cudaMallocHost(&b.h_bits, std::max<size_t>(ms.per_ct * ms.L, 1)) != cudaSuccess ||
+                cudaMallocHost(&b.h_seed, 8) != cudaSuccess) {
+                set_error("server resources could not be created");
+                cudaGetLastError();
+                return cleanup(COPSE_ENOMEM);
+            }
+            memset(b.h_feats, 0, ms.per_ct * ms.nf * 4);
+            // reserve the graph's device memory now: admission afterwards only concerns the queue
+            st = session_launch(b.sess, b.h_feats, 1, b.h_bits, b.stream, b.h_seed);
+            if (st || cudaStreamSynchronize(b.stream) != cudaSuccess) {
+                if (!st) set_error("server warm-up launch failed");
+                return cleanup(st ? st : COPSE_ECUDA);
+            }
+        }
+    copse_server *raw = S.release();
+    raw->worker = std::thread([raw] { raw->loop(); });
+    *out = raw;
+    return COPSE_OK;
+}
+
+extern "C" copse_status copse_server_submit(copse_server *S, uint32_t model_id, const uint32_t *feats,
+                                            uint64_t *ticket) {
+    if (!S || !feats || !ticket) { set_error("bad argument"); return COPSE_EINVAL; }
+    if (model_id >= S->models.size()) { set_error("unknown model id"); return COPSE_EINVAL; }
+    ModelSlot &ms = S->models[model_id];
+    for (size_t k = 0; k < ms.nf; k++)
+        if (ms.precision < 32 && feats[k] >= (1u << ms.precision)) { set_error("feature value needs more bits than the precision"); return COPSE_EINVAL; }
+    std::lock_guard<std::mutex> g(S->mu);
+    if (S->worker_error) { set_error("server stopped: " + S->worker_msg); return S->worker_error; }
+    if (S->n_pending >= S->max_pending) { set_error("request queue is full"); return COPSE_EADMIT; }
+    const uint64_t t = S->next_ticket++;
+    Ticket tk;
+    tk.model = (int)model_id;
+    tk.state = 0;
+    tk.t_submit = Clock::now();
+    S->tickets.emplace(t, std::move(tk));
+    ms.pending.push_back(Request{t, std::vector<uint32_t>(feats, feats + ms.nf)});
+    S->n_pending++;
+    S->cv_work.notify_one();
+    *ticket = t;
+    return COPSE_OK;
+}
+
+extern "C" copse_status copse_server_poll(copse_server *S, uint64_t ticket, uint8_t *out_bits, int timeout_ms,
+                                          double *latency_ms) {
+    if (!S || !out_bits) { set_error("bad argument"); return COPSE_EINVAL; }
+    std::unique_lock<std::mutex> lk(S->mu);
+    auto it = S->tickets.find(ticket);
+    if (it == S->tickets.end()) { set_error("unknown ticket"); return COPSE_EINVAL; }
+    auto done = [&] { return S->worker_error != COPSE_OK || S->tickets[ticket].state == 2; };
+    if (!S->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms < 0 ? 0 : timeout_ms), done)) {
+        set_error("result not ready");
+        return COPSE_ETIMEOUT;
+    }
+    if (S->worker_error) { set_error("server stopped: " + S->worker_msg); return S->worker_error; }
+    Ticket &tk = S->tickets[ticket];
+    memcpy(out_bits, tk.bits.data(), tk.bits.size());
+    if (latency_ms) latency_ms[0] = std::chrono::duration<double, std::milli>(tk.t_done - tk.t_submit).count();
+    S->tickets.erase(ticket);
+    return COPSE_OK;
+}
+
+extern "C" copse_status copse_server_pending(copse_server *S, size_t *queued, size_t *in_flight) {
+    if (!S) { set_error("bad argument"); return COPSE_EINVAL; }
+    std::lock_guard<std::mutex> g(S->mu);
+    size_t fl = 0;
+    for (ModelSlot &ms : S->models)
+        for (Buffer &b : ms.buf) fl += b.tickets.size();
+    if (queued) *queued = S->n_pending;
+    if (in_flight) *in_flight = fl;
+    return COPSE_OK;
+}
+
+extern "C" void copse_server_destroy(copse_server *S) {
+    if (!S) return;
+    {
+        std::lock_guard<std::mutex> g(S->mu);
+        S->stop = true;
+    }
+    S->cv_work.notify_all();
+    if (S->worker.joinable()) S->worker.join();
+    cudaSetDevice(S->c->device);
+    for (ModelSlot &ms : S->models)
+        for (Buffer &b : ms.buf) {
+            if (b.stream) cudaStreamSynchronize(b.stream);
+            if (b.sess) copse_session_destroy(b.sess);
+            if (b.stream) cudaStreamDestroy(b.stream);
+            if (b.done) cudaEventDestroy(b.done);
+            cudaFreeHost(b.h_feats);
+            cudaFreeHost(b.h_bits);
+            cudaFreeHost(b.h_seed);
+        }
+    delete S;
+}
