@@ -147,9 +147,10 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def ncu_traffic(family):
-    """Per-launch DRAM bytes from the committed ncu summary of this kernel family, or None when
-    the summary is missing or was taken on a different source file than the one built now."""
+def ncu_traffic(family, alg_bytes_per_launch):
+    """Per-launch DRAM bytes from the committed ncu summary of this kernel family, scaled from its
+    per-unit figure to a launch of `alg_bytes_per_launch` algorithmic bytes; None when the
+    summary is missing or was taken on a different source file than the one built now."""
     path = os.path.join(ROOT, "profiles", f"{family}_traffic.md")
     try:
         lines = open(path).read().splitlines()
@@ -164,7 +165,8 @@ def ncu_traffic(family):
     try:
         if hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] != kv.get("source_sha256_16"):
             return None
-        return float(kv["dram_bytes_per_launch"])
+        units = alg_bytes_per_launch / float(kv["unit_algorithmic_bytes"])
+        return float(kv["dram_bytes_per_unit"]) * units
     except (OSError, KeyError, ValueError):
         return None
 
@@ -329,7 +331,7 @@ def run_cuda(args, ws, rank, local):
         top = max(fam, key=lambda k: fam[k]["ms"])
         v = fam[top]
         achieved = v["bytes"] / (v["ms"] * 1e-3) / 1e9
-        tr = ncu_traffic(top)
+        tr = ncu_traffic(top, v["bytes"] / v["launches"])
         roof = {"kernel": top, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "traffic": tr,
                 "algorithmic_bytes_per_launch": v["bytes"] / v["launches"],

@@ -263,6 +263,8 @@ extern "C" copse_status copse_ctx_create(const copse_params *pp, int device, cop
     c->ndig = (c->L + c->alpha - 1) / c->alpha;
     c->bits = (int)pp->prime_bits;
     c->NP = c->L + c->alpha + 1;
+    const char *nc = getenv("COPSE_NTT_CLUSTERS");
+    c->ntt_clusters = !(nc && nc[0] == '0');
     // primes k*2N*t + 1 below 2^bits, k scanned downward: ciphertext primes first
     u64 M = (2ull << c->logN) * c->t;
     u64 k = ((1ull << c->bits) - 2) / M;

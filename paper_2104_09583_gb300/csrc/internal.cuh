@@ -164,6 +164,9 @@ struct copse_ctx {
     std::vector<cudaEvent_t> fork_ev;  // one per lane
     // set while a graph is being captured: allocations become graph memory nodes
     bool capturing = false;
+    // one-launch cluster NTT for 2^12 <= N <= 2^14 (environment COPSE_NTT_CLUSTERS=0 selects the
+    // two-launch form)
+    bool ntt_clusters = true;
 
     int ext_prime(int ell, int r) const { return r < ell ? r : L + (r - ell); }
     int t_index() const { return L + alpha; }

@@ -19,7 +19,11 @@
 // polynomial spreads over N / 2048 CTAs per pass, so a launch fills the GPU
 // even for a few dozen polynomials; the intermediate round trip stays in L2.
 // Small rings use one CTA per polynomial.
+#include <cooperative_groups.h>
+
 #include "internal.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace {
 
@@ -337,10 +341,153 @@ __global__ void __launch_bounds__(NT2) k_ntt_inv_cols(NttBatch b, const PrimeDev
         data[((size_t)(e >> lc) << lb) + (e & (C - 1))] = mul_shoup(sm[e], P.ninv, P.ninv_sh, t.q);
 }
 
+// ---------------------------------------------------------------- one launch per transform (clusters)
+// For 2^12 <= N <= 2^14 a thread-block cluster of CL = N / 2048 CTAs owns one
+// residue polynomial.  Each CTA runs the column stages on its column tile;
+// after a cluster barrier it gathers its row tile from the other CTAs' shared
+// memory (distributed shared memory), a second barrier keeps every tile alive
+// until all gathers are done, and it runs the row stages.  One launch and no
+// round trip through L2 between the two halves of the transform.
+struct ClusterSmem {
+    u64 colt[TILE], rowt[TILE];  // column tile [row][C], row tile [row][N2]
+    u64 stw[TILE], stwp[TILE];   // row-stage twiddles of this CTA's rows
+    u64 ctw[256], ctwp[256];     // column-stage twiddles (the first N1 entries)
+};
+
+template <int CL>
+__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT2)
+    k_ntt_fwd_cluster(NttBatch b, const PrimeDev *__restrict__ primes, const u64 *__restrict__ tw,
+                      const u64 *__restrict__ tw_sh, int logN, int L, int a) {
+    extern __shared__ __align__(16) u64 dyn_smem[];
+    ClusterSmem &S = *reinterpret_cast<ClusterSmem *>(dyn_smem);
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const int N = 1 << logN, lb = logN - a, N2 = 1 << lb, lc = 11 - a, C = 1 << lc, lr = 11 - lb;
+    const int pr = blockIdx.x / CL;
+    const int p = pr / b.nr, r = b.r0 + pr % b.nr;
+    if (ntt_skipped(b, p, r)) return;  // the same for every CTA of the cluster
+    const int g = ntt_prime(b, r, L);
+    const u64 q = primes[g].q, q2 = 2 * q;
+    u64 *poly = b.data + (size_t)p * b.stride + (size_t)r * N;
+    const u64 *W = tw + (size_t)g * N, *Wp = tw_sh + (size_t)g * N;
+    const u64 *cdata = poly + (rank << lc);
+    for (int e = threadIdx.x; e < TILE; e += NT2) S.colt[e] = cdata[((size_t)(e >> lc) << lb) + (e & (C - 1))];
+    for (int k = threadIdx.x; k < (1 << a); k += NT2) {
+        S.ctw[k] = W[k];
+        S.ctwp[k] = Wp[k];
+    }
+    const int row0 = rank << lr;
+    for (int u = 0; u < lb; u++) {
+        const int cnt = 1 << (lr + u), off = (1 << lr) * ((1 << u) - 1), src = (1 << (a + u)) + (row0 << u);
+        for (int k = threadIdx.x; k < cnt; k += NT2) {
+            S.stw[off + k] = W[src + k];
+            S.stwp[off + k] = Wp[src + k];
+        }
+    }
+    __syncthreads();
+    tile_fwd<true>(S.colt, S.ctw, S.ctwp, a, q, q2, [&](int gg, int i) { return (i << lc) + gg; },
+                   [&](int u, int, int il) { return (1 << u) + il; });
+    cl.sync();
+    for (int e = threadIdx.x; e < TILE; e += NT2) {
+        const int row = row0 + (e >> lb), col = e & (N2 - 1);
+        const u64 *rc = cl.map_shared_rank(S.colt, col >> lc);
+        S.rowt[e] = rc[(row << lc) + (col & (C - 1))];
+    }
+    cl.sync();
+    tile_fwd<false>(S.rowt, S.stw, S.stwp, lb, q, q2, [&](int gg, int i) { return (gg << lb) + i; },
+                    [&](int u, int gg, int il) { return ((1 << lr) * ((1 << u) - 1)) + (gg << u) + il; });
+    u64 *rdata = poly + ((size_t)row0 << lb);
+    for (int e = threadIdx.x; e < TILE; e += NT2) {
+        u64 v = S.rowt[e];
+        if (v >= q2) v -= q2;
+        if (v >= q) v -= q;
+        rdata[e] = v;
+    }
+}
+
+template <int CL>
+__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT2)
+    k_ntt_inv_cluster(NttBatch b, const PrimeDev *__restrict__ primes, const u64 *__restrict__ tw,
+                      const u64 *__restrict__ tw_sh, int logN, int L, int a) {
+    extern __shared__ __align__(16) u64 dyn_smem[];
+    ClusterSmem &S = *reinterpret_cast<ClusterSmem *>(dyn_smem);
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const int N = 1 << logN, lb = logN - a, lc = 11 - a, C = 1 << lc, lr = 11 - lb, R = 1 << lr;
+    const int pr = blockIdx.x / CL;
+    const int p = pr / b.nr, r = b.r0 + pr % b.nr;
+    if (ntt_skipped(b, p, r)) return;
+    const int g = ntt_prime(b, r, L);
+    const PrimeDev P = primes[g];
+    const u64 q = P.q, q2 = 2 * q;
+    u64 *poly = b.data + (size_t)p * b.stride + (size_t)r * N;
+    const u64 *W = tw + (size_t)g * N, *Wp = tw_sh + (size_t)g * N;
+    const int row0 = rank << lr;
+    const u64 *rdata = poly + ((size_t)row0 << lb);
+    for (int e = threadIdx.x; e < TILE; e += NT2) S.rowt[e] = rdata[e];
+    for (int k = threadIdx.x; k < (1 << a); k += NT2) {
+        S.ctw[k] = W[k];
+        S.ctwp[k] = Wp[k];
+    }
+    for (int u = 0, off = 0; u < lb; u++) {
+        const int su = lb - 1 - u, cnt = 1 << (lr + su), src = (1 << (logN - 1 - u)) + (row0 << su);
+        for (int k = threadIdx.x; k < cnt; k += NT2) {
+            S.stw[off + k] = W[src + k];
+            S.stwp[off + k] = Wp[src + k];
+        }
+        off += cnt;
+    }
+    __syncthreads();
+    tile_inv<false>(S.rowt, S.stw, S.stwp, lb, q, q2, [&](int gg, int i) { return (gg << lb) + i; },
+                    [&](int u, int gg, int il) {
+                        return (1 << lr) * ((1 << lb) - (1 << (lb - u))) + (gg << (lb - 1 - u)) + il;
+                    });
+    cl.sync();
+    for (int e = threadIdx.x; e < TILE; e += NT2) {
+        const int row = e >> lc, col = (rank << lc) + (e & (C - 1));
+        const u64 *rc = cl.map_shared_rank(S.rowt, row >> lr);
+        S.colt[e] = rc[((row & (R - 1)) << lb) + col];
+    }
+    cl.sync();
+    tile_inv<true>(S.colt, S.ctw, S.ctwp, a, q, q2, [&](int gg, int i) { return (i << lc) + gg; },
+                   [&](int u, int, int il) { return (1 << (a - 1 - u)) + il; });
+    u64 *cdata = poly + (rank << lc);
+    for (int e = threadIdx.x; e < TILE; e += NT2)
+        cdata[((size_t)(e >> lc) << lb) + (e & (C - 1))] = mul_shoup(S.colt[e], P.ninv, P.ninv_sh, q);
+}
+
+template <int CL>
+copse_status launch_cluster(copse_ctx *ctx, const NttBatch &b, cudaStream_t s, bool inverse, double bytes) {
+    static bool attr_set = false;  // per instantiation; raising the limit twice is harmless
+    const int smem = (int)sizeof(ClusterSmem);
+    if (!attr_set) {
+        CUDA_TRY(cudaFuncSetAttribute(k_ntt_fwd_cluster<CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        CUDA_TRY(cudaFuncSetAttribute(k_ntt_inv_cluster<CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        attr_set = true;
+    }
+    const unsigned grid = (unsigned)b.npoly * (unsigned)b.nr * CL;
+    const int a = ctx->logN / 2;
+    if (inverse)
+        TIMED("ntt_inv", bytes, s,
+              k_ntt_inv_cluster<CL><<<grid, NT2, smem, s>>>(b, ctx->d_prime, ctx->d_ipsi, ctx->d_ipsi_sh, ctx->logN,
+                                                            ctx->L, a));
+    else
+        TIMED("ntt_fwd", bytes, s,
+              k_ntt_fwd_cluster<CL><<<grid, NT2, smem, s>>>(b, ctx->d_prime, ctx->d_psi, ctx->d_psi_sh, ctx->logN,
+                                                            ctx->L, a));
+    LAUNCH_CHECK();
+    return COPSE_OK;
+}
+
 copse_status launch(copse_ctx *ctx, const NttBatch &b, cudaStream_t s, bool inverse) {
     if (b.npoly <= 0 || b.nr <= 0) return COPSE_OK;
     const int N = ctx->N, logN = ctx->logN;
     const double bytes = (double)b.npoly * b.nr * N * 16.0;  // one read and one write of each residue polynomial
+    if (ctx->ntt_clusters) {
+        if (logN == 12) return launch_cluster<2>(ctx, b, s, inverse, bytes);
+        if (logN == 13) return launch_cluster<4>(ctx, b, s, inverse, bytes);
+        if (logN == 14) return launch_cluster<8>(ctx, b, s, inverse, bytes);
+    }
     if (logN >= 12) {
         const int a = logN / 2;  // column length 2^a, row length 2^(logN - a)
         const unsigned grid = (unsigned)b.npoly * (unsigned)b.nr * (unsigned)(N / TILE);
