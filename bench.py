@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--profile", action="store_true", help="bracket the timed region with cudaProfilerStart/Stop")
     ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--no-serving", action="store_true", help="skip the Poisson-arrival serving leg")
+    ap.add_argument("--no-table6", action="store_true", help="skip the per-stage microbenchmark sweep")
     return ap.parse_args()
 
 
@@ -340,6 +341,7 @@ def run_cuda(args, ws, rank, local):
 
     serving = None if args.no_serving else run_serving(local)
     batch3 = None if args.no_serving else run_batch3(local)
+    table6 = None if args.no_table6 else run_table6(local)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -362,7 +364,7 @@ def run_cuda(args, ws, rank, local):
                    "l2": "working set > L2 (rotation keys alone are %.1f GB)" % (
                        (info["n_rot_reshuffle"] + info["n_rot_level"]) * 3 * 2 * (W.primes + 4) * N * 8 / 1e9)},
         "labels_ok": ok, "path": "graph session", "batched": batched, "plain_ops": plain_ops, "e2e": e2e,
-        "serving": serving, "batch3": batch3, "gpu_launches": launches_total,
+        "serving": serving, "batch3": batch3, "table6": table6, "gpu_launches": launches_total,
         "roofline": roof, "kernels": kern, "clocks": ck, "cpu_baseline": cpu,
     }
     return line
@@ -496,6 +498,50 @@ def run_batch3(local, steps=3, warmup=1):
             "items": len(items), "labels_ok": ok,
             "forests": [f"{i['n_trees']} trees, {i['b']} branches, {i['n_rot_reshuffle']}+{i['n_rot_level']} "
                         f"rotations, {p} queries/ciphertext" for i, p in zip(infos, per)]}
+
+
+# ---------------------------------------------------------------- Table 6 microbenchmarks
+def run_table6(local, reps=7, warmup=2, log_n=14, bits=55, primes=11, dnum=3):
+    """The eight microbenchmark forests of Section 8.4 (Table 6; 2 features, 3 labels),
+    one query each, with the device time of every step of Algorithm 1 (comparison,
+    reshuffling, level processing, aggregation): median over `reps` timed inferences."""
+    from paper_2104_09583_gb300 import copse as K
+    from paper_2104_09583_gb300 import synth
+
+    ctx = K.copse_ctx_create(log_n, bits, primes, dnum, device=local)
+    out = {}
+    try:
+        for name in sorted(synth.TABLE6):
+            depth, p, per_tree = synth.TABLE6[name]
+            text = synth.table6_forest(name)
+            model = K.copse_compile_forest(text, p, synth.TABLE6_FEATURES, log_n)
+            keys, evk = K.copse_keygen(ctx, 23, [model])
+            info = K.copse_model_info_get(model)
+            qs = synth.random_queries(200 + sorted(synth.TABLE6).index(name), 1, synth.TABLE6_FEATURES, p)
+            want = K.copse_classify_plain(model, qs)
+            rows, ok = [], True
+            for r in range(warmup + reps):
+                feats = K.copse_encrypt_features(ctx, keys, model, qs, 300 + r)
+                res, ms = K.copse_infer_timed(ctx, evk, model, feats)
+                bits_ = K.copse_decrypt_labels(ctx, keys, model, res, 1)
+                ok &= bool(np.array_equal(bits_, want))
+                K.copse_ctbuf_destroy(res)
+                K.copse_ctbuf_destroy(feats)
+                if r >= warmup:
+                    rows.append([ms[k] for k in K.STAGES])
+            med = np.median(np.asarray(rows), axis=0)
+            out[name] = {"depth": depth, "precision": p, "trees": len(per_tree), "branches": int(info["b"]),
+                         "rotations": int(info["n_rot_reshuffle"] + info["n_rot_level"]),
+                         **{f"{k}_ms": round(float(v), 4) for k, v in zip(K.STAGES, med)},
+                         "total_ms": round(float(med.sum()), 4), "labels_ok": ok}
+            K.copse_keys_destroy(keys)
+            K.copse_evk_destroy(evk)
+            K.copse_model_destroy(model)
+    finally:
+        K.copse_ctx_destroy(ctx)
+    return {"ring_degree": 1 << log_n, "ciphertext_primes": primes, "prime_bits": bits,
+            "queries_per_inference": 1, "stat": f"median of {reps} (host-launched, per-stage CUDA events)",
+            "models": out}
 
 
 # ---------------------------------------------------------------- CPU oracle (baseline / reference arm)

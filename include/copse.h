@@ -172,6 +172,18 @@ copse_status copse_encrypt_features(copse_ctx *ctx, const copse_keys *keys, cops
 copse_status copse_infer(copse_ctx *ctx, const copse_evk *evk, copse_model *model, const copse_ctbuf *feats,
                          copse_ctbuf **out, void *stream);
 
+/* copse_infer with the per-step breakdown that Section 8.4 reports for the
+ * Table 6 microbenchmarks: CUDA events recorded on `stream` at the step
+ * boundaries give stage_ms[0] comparison (SecComp, Section 4.1.2),
+ * stage_ms[1] reshuffling (R * Decisions), stage_ms[2] level processing
+ * (Lvl_k * Branches XOR Mask_k), stage_ms[3] aggregation (product across
+ * levels).  The result is the same ciphertext copse_infer returns.  Blocks
+ * the calling thread until the stream reaches the end of the inference;
+ * EINVAL while a graph is being recorded on the context, or on null
+ * arguments; stage_ms is host memory owned by the caller. */
+copse_status copse_infer_timed(copse_ctx *ctx, const copse_evk *evk, copse_model *model, const copse_ctbuf *feats,
+                               copse_ctbuf **out, void *stream, float stage_ms[4]);
+
 /* Decrypt an inference result into out_bits[n_queries * n_leaves]: 1 for the
  * leaf each tree selects, 0 elsewhere, 2 for a slot that is not a bit
  * (noise overflow).  out_bits is host memory if out_on_device = 0 (the call

@@ -70,6 +70,7 @@ _SIG = {
     "copse_evk_export": (C.c_int, [vp, C.c_uint64, u64p, C.c_size_t]),
     "copse_encrypt_features": (C.c_int, [vp, vp, vp, vp, C.c_size_t, C.c_int, C.c_uint64, pvp, vp]),
     "copse_infer": (C.c_int, [vp, vp, vp, vp, pvp, vp]),
+    "copse_infer_timed": (C.c_int, [vp, vp, vp, vp, pvp, vp, C.POINTER(C.c_float)]),
     "copse_decrypt_labels": (C.c_int, [vp, vp, vp, vp, vp, C.c_size_t, C.c_int, vp]),
     "copse_decrypt_slots": (C.c_int, [vp, vp, vp, C.c_size_t, u64p]),
     "copse_ctbuf_count": (C.c_size_t, [vp]),
@@ -229,6 +230,18 @@ def copse_infer(ctx, evk, model, feats, stream=None):
     h = C.c_void_p()
     _check(_lib.copse_infer(ctx, evk, model, feats, C.byref(h), C.c_void_p(stream)))
     return h
+
+
+STAGES = ("comparison", "reshuffle", "levels", "aggregation")
+
+
+def copse_infer_timed(ctx, evk, model, feats, stream=None):
+    """copse_infer with device time per stage of Algorithm 1; returns
+    (result buffer, {stage: ms})."""
+    h = C.c_void_p()
+    ms = (C.c_float * 4)()
+    _check(_lib.copse_infer_timed(ctx, evk, model, feats, C.byref(h), C.c_void_p(stream), ms))
+    return h, dict(zip(STAGES, (float(v) for v in ms)))
 
 
 def copse_decrypt_labels(ctx, keys, model, result, n_queries, stream=None, out_device_ptr=None):

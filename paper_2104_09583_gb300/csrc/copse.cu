@@ -311,8 +311,14 @@ extern "C" copse_status copse_encrypt_features(copse_ctx *c, const copse_keys *k
 }
 
 static copse_status infer_impl(copse_ctx *c, const copse_evk *evk, copse_model *m, const copse_ctbuf *feats,
-                               DCt *result, cudaStream_t s, int lane = 0) {
+                               DCt *result, cudaStream_t s, int lane = 0, cudaEvent_t *stage_ev = nullptr) {
     STATUS_TRY(upload_model(c, m, s));
+    // stage boundaries (comparison | reshuffle | levels | aggregation), when timed
+    auto mark = [&](int i) -> copse_status {
+        if (stage_ev) CUDA_TRY(cudaEventRecord(stage_ev[i], s));
+        return COPSE_OK;
+    };
+    STATUS_TRY(mark(0));
     const DeviceModel &D = *m->dev;
     const CompiledForest &f = m->f;
     const int p = (int)f.precision;
@@ -363,14 +369,17 @@ static copse_status infer_impl(copse_ctx *c, const copse_evk *evk, copse_model *
     DCt Dc = nodes[0].lt;
     if (nodes[0].eq.data) ct_free(&nodes[0].eq, s);
     if (Dc.level != D.lvl_D) { set_error("internal: unexpected level of the decision vector"); return COPSE_EINVAL; }
+    STATUS_TRY(mark(1));
     // reshuffle: Branches = R_ext * Decisions
     std::vector<DCt> br;
     STATUS_TRY(op_matmul(c, evk, Dc, D.rot_R, D.pt_R, {nullptr}, br, s));
     ct_free(&Dc, s);
+    STATUS_TRY(mark(2));
     // levels: Lvl_k * Branches XOR Mask_k, rotations of Branches shared by every level
     std::vector<DCt> lv;
     STATUS_TRY(op_matmul(c, evk, br[0], D.rot_B, D.pt_B, D.mask, lv, s));
     ct_free(&br[0], s);
+    STATUS_TRY(mark(3));
     // product across levels, balanced
     while (lv.size() > 1) {
         const int npair = (int)(lv.size() / 2);
@@ -383,6 +392,7 @@ static copse_status infer_impl(copse_ctx *c, const copse_evk *evk, copse_model *
         if (lv.size() % 2) nx.push_back(lv.back());
         lv.swap(nx);
     }
+    STATUS_TRY(mark(4));
     *result = lv[0];
     return COPSE_OK;
 }
@@ -395,6 +405,35 @@ extern "C" copse_status copse_infer(copse_ctx *c, const copse_evk *evk, copse_mo
     buf->stream = as_stream(stream);
     DCt r;
     STATUS_TRY(infer_impl(c, evk, m, feats, &r, as_stream(stream)));
+    buf->cts.push_back(r);
+    *out = buf.release();
+    return COPSE_OK;
+}
+
+extern "C" copse_status copse_infer_timed(copse_ctx *c, const copse_evk *evk, copse_model *m,
+                                          const copse_ctbuf *feats, copse_ctbuf **out, void *stream,
+                                          float stage_ms[4]) {
+    if (!c || !evk || !m || !feats || !out || !stage_ms) { set_error("null argument"); return COPSE_EINVAL; }
+    if (c->capturing) { set_error("copse_infer_timed cannot be recorded into a graph"); return COPSE_EINVAL; }
+    cudaStream_t s = as_stream(stream);
+    cudaEvent_t ev[5] = {};
+    copse_status st = COPSE_OK;
+    for (int i = 0; i < 5 && st == COPSE_OK; i++)
+        if (cudaEventCreate(&ev[i]) != cudaSuccess) { set_error("cudaEventCreate failed"); st = COPSE_ECUDA; }
+    DCt r;
+    if (st == COPSE_OK) st = infer_impl(c, evk, m, feats, &r, s, 0, ev);
+    if (st == COPSE_OK && cudaEventSynchronize(ev[4]) != cudaSuccess) { set_error("stage event failed"); st = COPSE_ECUDA; }
+    for (int i = 0; i < 4 && st == COPSE_OK; i++)
+        if (cudaEventElapsedTime(&stage_ms[i], ev[i], ev[i + 1]) != cudaSuccess) { set_error("stage timing failed"); st = COPSE_ECUDA; }
+    for (cudaEvent_t e : ev)
+        if (e) cudaEventDestroy(e);
+    if (st != COPSE_OK) {
+        if (r.data) ct_free(&r, s);
+        return st;
+    }
+    auto buf = std::make_unique<copse_ctbuf>();
+    buf->ctx = c;
+    buf->stream = s;
     buf->cts.push_back(r);
     *out = buf.release();
     return COPSE_OK;

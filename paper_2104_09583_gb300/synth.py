@@ -53,6 +53,78 @@ def random_forest(seed, n_trees, depth, n_features, precision, n_classes,
             return "\n".join(lines) + "\n"
 
 
+def exact_tree_tokens(rng, n_branches, depth, n_features, precision, n_classes):
+    """One tree with exactly n_branches branches whose longest root-to-leaf
+    path crosses exactly min(depth, n_branches) of them: a random spine of
+    that length, then leaves above the depth limit, drawn uniformly, turned
+    into branches until the count is reached."""
+    depth = min(depth, n_branches)
+    if n_branches > (1 << depth) - 1:
+        raise ValueError("a binary tree of this depth cannot hold that many branches")
+    root = {"d": 0, "kids": None}
+    node = root
+    for _ in range(depth):                       # the spine
+        node["kids"] = [{"d": node["d"] + 1, "kids": None}, {"d": node["d"] + 1, "kids": None}]
+        node = node["kids"][int(rng.integers(2))]
+    count = depth
+
+    def open_leaves(n, out):
+        if n["kids"] is None:
+            if n["d"] < depth:
+                out.append(n)
+        else:
+            for k in n["kids"]:
+                open_leaves(k, out)
+        return out
+
+    while count < n_branches:
+        cand = open_leaves(root, [])
+        leaf = cand[int(rng.integers(len(cand)))]
+        leaf["kids"] = [{"d": leaf["d"] + 1, "kids": None}, {"d": leaf["d"] + 1, "kids": None}]
+        count += 1
+    toks = []
+
+    def emit(n):
+        if n["kids"] is None:
+            toks.extend(["l", str(int(rng.integers(n_classes)))])
+        else:
+            toks.extend(["b", str(int(rng.integers(n_features))), str(int(rng.integers(1 << precision)))])
+            emit(n["kids"][0])
+            emit(n["kids"][1])
+
+    emit(root)
+    return toks
+
+
+# The eight microbenchmark forests of Section 8.4 (Table 6): max depth,
+# precision and branches per tree.  Every forest has 2 features and 3 labels.
+# The printed table gives the total branch count (15, 10 or 20); the names
+# width55 / width78 / width677 give the split over the trees, and the other
+# models split 15 branches as 7 + 8 like width78.
+TABLE6 = {
+    "depth4": (4, 8, (7, 8)),
+    "depth5": (5, 8, (7, 8)),
+    "depth6": (6, 8, (7, 8)),
+    "width55": (5, 8, (5, 5)),
+    "width78": (5, 8, (7, 8)),
+    "width677": (5, 8, (6, 7, 7)),
+    "prec8": (5, 8, (7, 8)),
+    "prec16": (5, 16, (7, 8)),
+}
+TABLE6_FEATURES = 2
+TABLE6_CLASSES = 3
+
+
+def table6_forest(name, seed=6000):
+    """A Table 6 microbenchmark forest as text, redrawn from its own seed."""
+    depth, precision, per_tree = TABLE6[name]
+    rng = np.random.default_rng(seed + sorted(TABLE6).index(name))
+    lines = [" ".join(f"c{i}" for i in range(TABLE6_CLASSES))]
+    for nb in per_tree:
+        lines.append(" ".join(exact_tree_tokens(rng, nb, depth, TABLE6_FEATURES, precision, TABLE6_CLASSES)))
+    return "\n".join(lines) + "\n"
+
+
 def random_queries(seed, n, n_features, precision):
     rng = np.random.default_rng(seed)
     return rng.integers(0, 1 << precision, size=(n, n_features), dtype=np.int64).astype(np.uint32)
