@@ -90,6 +90,7 @@ def lib():
             "or_add": (None, [P, u64p, u64p, C.c_int, C.c_int, C.c_int, u64p]),
             "or_matmul": (None, [P, u64p, C.c_int, C.c_int, u64p, C.POINTER(C.c_void_p), C.c_int, i64p,
                                  np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS"), u64p]),
+            "or_rotsum": (None, [P, C.POINTER(C.c_void_p), C.c_int, C.c_int, u64p, C.POINTER(C.c_void_p), u64p]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -393,6 +394,21 @@ class Bgv:
         out = np.zeros((nacc, 2, ell, P.N), dtype=np.uint64)
         self.L.or_matmul(P.c, ct, ell, nrot, g, keys, nacc, m, present, out)
         return [out[a] for a in range(nacc)]
+
+    def rotsum(self, cts, galois, gks) -> np.ndarray:
+        """sum_k rot_{galois[k]}(cts[k]) with one modulus-down step for the sum (see
+        or_rotsum); galois[k] = 1 adds cts[k] unrotated (gks[k] then None)."""
+        P = self.P
+        cts = [np.ascontiguousarray(c) for c in cts]
+        ell = cts[0].shape[1]
+        assert all(c.shape == (2, ell, P.N) for c in cts)
+        n = len(cts)
+        g = np.ascontiguousarray(galois, dtype=np.uint64)
+        ptrs = (C.c_void_p * n)(*[c.ctypes.data for c in cts])
+        keys = (C.c_void_p * n)(*[None if k is None else k.ctypes.data for k in gks])
+        out = np.zeros((2, ell, P.N), dtype=np.uint64)
+        self.L.or_rotsum(P.c, ptrs, ell, n, g, keys, out)
+        return out
 
     def mul(self, a, b, rlk) -> np.ndarray:
         """ct x ct: tensor, relinearise, then drop one prime (the canonical policy)."""

@@ -604,6 +604,61 @@ void or_matmul(const or_params *P, const u64 *ct, int ell, int nrot, const u64 *
     free(acc); free(tc); free(R); free(pr); free(tmp);
 }
 
+/* Sum of rotations of several ciphertexts (the giant steps of a baby-step /
+ * giant-step matrix product), with the modulus-down step taken once:
+ *   acc = sum_{k: g_k != 1} KSraw(tau_{g_k} c_k1) + (P * tau_{g_k} c_k0, 0)   over q and p
+ *   out = ModDown(acc) + sum_{k: g_k = 1} c_k.
+ * Each rotated term is P times the rotation of c_k up to key-switching noise,
+ * so out decrypts to sum_k rot(c_k) with one rounding error for the sum.
+ * cts: n ciphertexts [2][ell][N] (pointers); galois[k], gks[k] as in or_matmul;
+ * out: [2][ell][N].  No modulus switch here. */
+void or_rotsum(const or_params *P, const u64 *const *cts, int ell, int n, const u64 *galois, const u64 *const *gks,
+               u64 *out)
+{
+    int N = P->N, nx = ell + P->alpha;
+    u64 Pmod[OR_MAXP];
+    for (int i = 0; i < ell; i++) {
+        Pmod[i] = 1;
+        for (int k = 0; k < P->alpha; k++) Pmod[i] = mulmod(Pmod[i], P->primes[P->L + k] % P->primes[i], P->primes[i]);
+    }
+    u64 *acc = calloc((size_t)2 * nx * N, sizeof(u64));
+    u64 *tc = malloc(sizeof(u64) * 2 * ell * N), *R = malloc(sizeof(u64) * 2 * nx * N);
+    for (int k = 0; k < n; k++) {
+        u64 g = galois[k];
+        if (g == 1) continue;
+        const u64 *ct = cts[k];
+        for (int c = 0; c < 2; c++)
+            for (int r = 0; r < ell; r++)
+                or_automorphism(ct + ((size_t)c * ell + r) * N, P->logN, P->primes[r], g, tc + ((size_t)c * ell + r) * N);
+        keyswitch_raw(P, tc + (size_t)ell * N, ell, gks[k], R);
+        for (int r = 0; r < ell; r++) {
+            u64 q = P->primes[r];
+            for (int j = 0; j < N; j++)
+                R[(size_t)r * N + j] = addmod(R[(size_t)r * N + j], mulmod(Pmod[r], tc[(size_t)r * N + j], q), q);
+        }
+        for (int c = 0; c < 2; c++)
+            for (int r = 0; r < nx; r++) {
+                u64 q = P->primes[ext_prime(P, ell, r)];
+                u64 *a = acc + ((size_t)c * nx + r) * N;
+                const u64 *b = R + ((size_t)c * nx + r) * N;
+                for (int j = 0; j < N; j++) a[j] = addmod(a[j], b[j], q);
+            }
+    }
+    moddown(P, acc, ell, out);
+    moddown(P, acc + (size_t)nx * N, ell, out + (size_t)ell * N);
+    for (int k = 0; k < n; k++) {
+        if (galois[k] != 1) continue;
+        for (int c = 0; c < 2; c++)
+            for (int r = 0; r < ell; r++) {
+                u64 q = P->primes[r];
+                u64 *d = out + ((size_t)c * ell + r) * N;
+                const u64 *b = cts[k] + ((size_t)c * ell + r) * N;
+                for (int j = 0; j < N; j++) d[j] = addmod(d[j], b[j], q);
+            }
+    }
+    free(acc); free(tc); free(R);
+}
+
 /* (c0,c1) x (d0,d1) -> (c0d0, c0d1 + c1d0, c1d1), out [3][ell][N] */
 void or_tensor(const or_params *P, const u64 *a, const u64 *b, int ell, u64 *out)
 {

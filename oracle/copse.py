@@ -271,13 +271,43 @@ def level_diagonals(m: Model, k: int, t: int):
     return out
 
 
-def rotation_sets(m: Model):
-    """Rotation amounts used by the reshuffle and by the level products (0 excluded)."""
-    rs = sorted(i for i in reshuffle_diagonals(m) if i)
-    ls = set()
-    for k in range(1, m.d + 1):
-        ls |= set(i for i in level_diagonals(m, k, 65537) if i)
-    return rs, sorted(ls)
+def bsgs_split(diags: dict, g: int, block: int):
+    """Baby-step / giant-step grouping of the diagonal method (Halevi and Shoup's
+    BSGS form of the MatMul of Section 4.1.2): diagonal i = k g + j, 0 <= j < g,
+    joins giant step k g with baby step j, its block-local slot vector shifted
+    by k g,  d'_{k,j}[s] = d_i[s - k g],  so that
+        M v = sum_k rot( sum_j d'_{k,j} * rot(v, j), k g ).
+    The shift stays inside the query's block (k g + rows <= block), so no
+    product reaches another block.  Returns {k g: {j: d'}}."""
+    out = {}
+    for i in sorted(diags):
+        k, j = divmod(i, g)
+        d = np.asarray(diags[i])
+        assert k * g + len(d) <= block, "shifted diagonal leaves the block"
+        sh = np.zeros(k * g + len(d), dtype=np.int64)
+        sh[k * g:] = d
+        out.setdefault(k * g, {})[j] = sh
+    return out
+
+
+def _rots(diag_sets, g, block):
+    if not g:
+        return set(i for d in diag_sets for i in d if i)
+    r = set()
+    for d in diag_sets:
+        for kg, babies in bsgs_split(d, g, block).items():
+            r |= set(j for j in babies if j)
+            if kg:
+                r.add(kg)
+    return r
+
+
+def rotation_sets(m: Model, g=(0, 0)):
+    """Rotation amounts used by the reshuffle and by the level products (0 excluded);
+    g = (baby-step size of the reshuffle, of the levels), 0 = the plain diagonal method."""
+    rs = _rots([reshuffle_diagonals(m)], g[0], m.block)
+    ls = _rots([level_diagonals(m, k, 65537) for k in range(1, m.d + 1)], g[1], m.block)
+    return sorted(rs), sorted(ls)
 
 
 # ---------------------------------------------------------------------------
@@ -323,12 +353,22 @@ def seccomp(E, X, Y_planes, p):
     return pairwise(leaves, combine)[0]
 
 
-def matmul(E, v, diag_sets, add_vecs):
+def matmul(E, v, diag_sets, add_vecs, m: Model, N: int, g: int = 0):
     """Diagonal method (Section 4.1.2, Matrix Multiplication) for several matrices
     applied to the same vector: for each matrix a, the sum over its nonzero
     diagonals of d_i * rot(v, i), plus an optional plaintext, then one modulus
-    switch.  Rotations of v by the same amount serve every matrix."""
-    sums = E.diag_sums(v, diag_sets)
+    switch.  Rotations of v by the same amount serve every matrix.  diag_sets
+    hold block-local diagonals.  With g > 0 the sum is taken in baby-step /
+    giant-step form (bsgs_split): the baby-step sums of every (matrix, giant
+    step) share the rotations of v, and each matrix's giant steps are rotated
+    and summed (E.rot_sum)."""
+    if not g:
+        sums = E.diag_sums(v, [{i: tile_blocks(m, d, N) for i, d in ds.items()} for ds in diag_sets])
+    else:
+        groups = [bsgs_split(ds, g, m.block) for ds in diag_sets]
+        inner_sets = [{j: tile_blocks(m, d, N) for j, d in grp[kg].items()} for grp in groups for kg in sorted(grp)]
+        inner = iter(E.diag_sums(v, inner_sets))
+        sums = [E.rot_sum([(kg, next(inner)) for kg in sorted(grp)]) for grp in groups]
     out = []
     for acc, add in zip(sums, add_vecs):
         if add is not None:
@@ -337,17 +377,17 @@ def matmul(E, v, diag_sets, add_vecs):
     return out
 
 
-def infer(E, m: Model, X, N: int):
+def infer(E, m: Model, X, N: int, g=(0, 0)):
     """Algorithm 1: SecComp, reshuffle, per-level product XOR mask, MultAll.
     Reading: the level products use Branches (the reshuffled vector, as the
-    text of Section 4.3 says), not Decisions as the listing prints."""
+    text of Section 4.3 says), not Decisions as the listing prints.
+    g = (baby-step size of the reshuffle, of the levels); 0 = plain diagonal method."""
     t = E.t
     Y = E.thresholds(m)
     D = seccomp(E, X, Y, m.precision)
-    Rd = {i: tile_blocks(m, dg, N) for i, dg in reshuffle_diagonals(m).items()}
-    Br = matmul(E, D, [Rd], [None])[0]
-    Ld = [{i: tile_blocks(m, dg, N) for i, dg in level_diagonals(m, k, t).items()} for k in range(1, m.d + 1)]
-    res = matmul(E, Br, Ld, [tile_blocks(m, m.mask[k - 1], N) for k in range(1, m.d + 1)])
+    Br = matmul(E, D, [reshuffle_diagonals(m)], [None], m, N, g[0])[0]
+    Ld = [level_diagonals(m, k, t) for k in range(1, m.d + 1)]
+    res = matmul(E, Br, Ld, [tile_blocks(m, m.mask[k - 1], N) for k in range(1, m.d + 1)], m, N, g[1])
     return pairwise(res, lambda a, b, root: E.mul(a, b))
 
 
@@ -387,6 +427,12 @@ class SlotEngine:
 
     def rescale(self, a):
         return a
+
+    def rot_sum(self, terms):
+        acc = np.zeros(self.N, dtype=np.int64)
+        for k, c in terms:
+            acc = (acc + self.rot(c, k)) % self.t
+        return acc
 
     def diag_sums(self, v, diag_sets):
         out = []
@@ -436,6 +482,14 @@ class BgvEngine:
         self.counts["mul_plain"] += sum(len(d) for d in diag_sets)
         return self.b.matmul(v, galois, gks, pts)
 
+    def rot_sum(self, terms):
+        """Giant steps: sum_k rot(c_k, k) with one modulus-down step (Bgv.rotsum)."""
+        if all(k == 0 for k, _ in terms) and len(terms) == 1:
+            return terms[0][1]
+        galois = [B.galois_rot(self.P.logN, k) if k else 1 for k, _ in terms]
+        self.counts["rot"] += sum(1 for k, _ in terms if k)
+        return self.b.rotsum([c for _, c in terms], galois, [self.k.gk[g] if g != 1 else None for g in galois])
+
     def mul(self, a, b):
         self.counts["mul"] += 1
         return self.b.mul(a, b, self.k.rlk)
@@ -464,8 +518,8 @@ class BgvEngine:
         return self.b.modswitch(a)
 
 
-def galois_elements(m: Model, logN: int):
-    rs, ls = rotation_sets(m)
+def galois_elements(m: Model, logN: int, g=(0, 0)):
+    rs, ls = rotation_sets(m, g)
     return sorted(set(B.galois_rot(logN, i) for i in rs + ls))
 
 
