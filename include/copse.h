@@ -124,8 +124,22 @@ copse_status copse_model_info_get(const copse_model *model, copse_model_info *in
 copse_status copse_model_export(const copse_model *model, uint32_t *thr_slot, int32_t *slot_branch, uint8_t *R,
                                 uint8_t *lvl, uint8_t *mask, uint32_t *br_level);
 
-/* Nonzero rotation amounts: reshuffle then level products, ascending in each. */
+/* Nonzero rotation amounts: reshuffle then level products, ascending in each
+ * (baby and giant steps when a baby-step size is set). */
 copse_status copse_model_rotations(const copse_model *model, uint32_t *reshuffle, uint32_t *level);
+
+/* Baby-step / giant-step matrix products (the diagonal method of Section 4.1.2
+ * in Halevi and Shoup's BSGS form): diagonal i = k g + j is multiplied, shifted
+ * by k g inside the query block, with rot(v, j); the sums per giant step k g are
+ * rotated by k g and added, with one ModDown for all giant steps of a matrix.
+ * g_reshuffle, g_level: baby-step sizes for the reshuffle and for the level
+ * products; 0 keeps the plain method (one rotation per nonzero diagonal).
+ * About 2 sqrt(width) rotation keys instead of one per diagonal.  Set before
+ * copse_keygen (the key set follows the setting); drops the model's device
+ * copy if the setting changes.  EINVAL if a shifted diagonal would leave the
+ * query block. */
+copse_status copse_model_set_bsgs(copse_model *model, uint32_t g_reshuffle, uint32_t g_level);
+copse_status copse_model_get_bsgs(const copse_model *model, uint32_t *g_reshuffle, uint32_t *g_level);
 
 /* Plaintext classification (Section 2.1): one bit per leaf per query,
  * out_bits[n_queries * n_leaves]; feats[n_queries * n_features] on the host. */

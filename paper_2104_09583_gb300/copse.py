@@ -62,6 +62,8 @@ _SIG = {
     "copse_model_info_get": (C.c_int, [vp, C.POINTER(copse_model_info)]),
     "copse_model_export": (C.c_int, [vp, vp, vp, vp, vp, vp, vp]),
     "copse_model_rotations": (C.c_int, [vp, vp, vp]),
+    "copse_model_set_bsgs": (C.c_int, [vp, C.c_uint32, C.c_uint32]),
+    "copse_model_get_bsgs": (C.c_int, [vp, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)]),
     "copse_classify_plain": (C.c_int, [vp, u32p, C.c_size_t, u8p]),
     "copse_keygen": (C.c_int, [vp, C.c_uint64, C.POINTER(C.c_void_p), C.c_size_t, pvp, pvp]),
     "copse_keys_destroy": (None, [vp]),
@@ -173,6 +175,16 @@ def copse_model_rotations(m):
     b = np.zeros(max(i["n_rot_level"], 1), np.uint32)
     _check(_lib.copse_model_rotations(m, _ptr(a), _ptr(b)))
     return a[: i["n_rot_reshuffle"]].tolist(), b[: i["n_rot_level"]].tolist()
+
+
+def copse_model_set_bsgs(m, g_reshuffle, g_level):
+    _check(_lib.copse_model_set_bsgs(m, g_reshuffle, g_level))
+
+
+def copse_model_get_bsgs(m):
+    a, b = C.c_uint32(), C.c_uint32()
+    _check(_lib.copse_model_get_bsgs(m, C.byref(a), C.byref(b)))
+    return a.value, b.value
 
 
 def copse_classify_plain(m, feats):

@@ -3,6 +3,7 @@
 // device, decryption, buffers and single ring operations.
 #include <algorithm>
 #include <cstring>
+#include <functional>
 #include <memory>
 
 #include "forest.h"
@@ -27,10 +28,15 @@ struct DeviceModel {
     u64 *store = nullptr;              // one allocation for every plaintext
     // SecComp leaves, plane i: lt = x * lt_mul + lt_add, eq = x * eq_mul + eq_add (level L)
     std::vector<const u64 *> lt_mul, lt_add, eq_mul, eq_add;
-    std::vector<uint32_t> rot_R;                    // reshuffle rotation amounts
-    std::vector<std::vector<const u64 *>> pt_R;     // [1][rot]
-    std::vector<uint32_t> rot_B;                    // level rotation amounts
-    std::vector<std::vector<const u64 *>> pt_B;     // [d][rot] (null = zero diagonal)
+    // matrix products: baby-step amounts, per accumulator (matrix, giant step) the
+    // diagonal plaintexts per baby step (null = zero), extended basis
+    struct Group {
+        BsgsGroup plan;
+        std::vector<std::vector<const u64 *>> pt;  // [acc][baby]
+        std::vector<int> acc_mat;
+        std::vector<uint32_t> acc_giant;
+    };
+    Group R, Lv;                                    // reshuffle; levels (d matrices)
     std::vector<const u64 *> mask;                  // [d]
     ~DeviceModel() {
         if (store) cudaFree(store);
@@ -58,23 +64,17 @@ static copse_status upload_model(copse_ctx *c, copse_model *m, cudaStream_t s) {
     D->lvl_D = L - 1 - (int)clog2u(f.precision);
     D->lvl_B = D->lvl_D - 1;
     const u64 t = c->t;
-    // count plaintexts
     const size_t nleaf = 4 * (size_t)p;
-    D->rot_R = f.rot_reshuffle;
-    D->rot_B = f.rot_level;
-    std::vector<uint8_t> dg8;
-    std::vector<uint64_t> dg64;
-    // level diagonal presence per (k, rot)
-    std::vector<std::vector<char>> lvl_nz(f.d, std::vector<char>(D->rot_B.size(), 0));
-    size_t nlvl = 0;
-    for (uint32_t k = 1; k <= f.d; k++)
-        for (size_t r = 0; r < D->rot_B.size(); r++) {
-            f.level_diagonal(k, D->rot_B[r], t, dg64);
-            bool nz = std::any_of(dg64.begin(), dg64.end(), [](uint64_t v) { return v != 0; });
-            lvl_nz[k - 1][r] = nz;
-            nlvl += nz;
-        }
-    const size_t words = (nleaf * L + D->rot_R.size() * (D->lvl_D + A) + nlvl * (D->lvl_B + A) + f.d * D->lvl_B) * (size_t)N;
+    D->R.plan = f.group_reshuffle();
+    D->Lv.plan = f.group_level();
+    auto count_pt = [](const BsgsGroup &G) {
+        size_t n = 0;
+        for (const auto &a : G.acc)
+            for (int32_t i : a.diag) n += i >= 0;
+        return n;
+    };
+    const size_t nR = count_pt(D->R.plan), nLv = count_pt(D->Lv.plan);
+    const size_t words = (nleaf * L + nR * (D->lvl_D + A) + nLv * (D->lvl_B + A) + f.d * D->lvl_B) * (size_t)N;
     CUDA_TRY(cudaMalloc(&D->store, std::max<size_t>(words, 1) * sizeof(u64)));
     u64 *cur = D->store;
     // SecComp leaf plaintexts over whole blocks (threshold bit 0 past the decisions)
@@ -98,38 +98,60 @@ static copse_status upload_model(copse_ctx *c, copse_model *m, cudaStream_t s) {
         }
         cur += nleaf * L * (size_t)N;
     }
+    // Diagonal plaintexts of a group, in the extended basis (the products are summed
+    // before the key switch's ModDown): diagonal giant + baby of matrix a, shifted by
+    // the giant step inside the block; encoded in chunks to bound the staging memory.
+    auto encode_group = [&](DeviceModel::Group &G, int level, int rows,
+                            const std::function<void(uint32_t, uint32_t, std::vector<uint32_t> &)> &diag) {
+        const size_t w = (size_t)(level + A) * N;
+        const size_t nacc = G.plan.acc.size(), nb = G.plan.baby.size();
+        G.pt.assign(nacc, std::vector<const u64 *>(nb, nullptr));
+        G.acc_mat.resize(nacc);
+        G.acc_giant.resize(nacc);
+        std::vector<std::pair<size_t, size_t>> items;  // (acc, baby) with a nonzero diagonal
+        for (size_t a = 0; a < nacc; a++) {
+            G.acc_mat[a] = (int)G.plan.acc[a].mat;
+            G.acc_giant[a] = G.plan.acc[a].giant;
+            for (size_t j = 0; j < nb; j++)
+                if (G.plan.acc[a].diag[j] >= 0) items.push_back({a, j});
+        }
+        const size_t CH = 256;
+        std::vector<uint32_t> pat, dg;
+        for (size_t i0 = 0; i0 < items.size(); i0 += CH) {
+            const size_t n = std::min(CH, items.size() - i0);
+            pat.assign(n * (size_t)B, 0u);
+            for (size_t x = 0; x < n; x++) {
+                const auto &A_ = G.plan.acc[items[i0 + x].first];
+                const uint32_t giant = A_.giant, i = (uint32_t)A_.diag[items[i0 + x].second];
+                diag(A_.mat, i, dg);
+                for (int r = 0; r < rows; r++) pat[x * B + giant + r] = dg[r];
+                G.pt[items[i0 + x].first][items[i0 + x].second] = cur + (i0 + x) * w;
+            }
+            STATUS_TRY(encode_patterns(c, pat, (int)n, B, B, level, A, cur + i0 * w, s));
+        }
+        cur += items.size() * w;
+        return COPSE_OK;
+    };
+    for (const auto &a : D->R.plan.acc)
+        if (a.giant + f.m1() > (uint32_t)B) { set_error("internal: shifted reshuffle diagonal leaves the block"); return COPSE_EINVAL; }
+    for (const auto &a : D->Lv.plan.acc)
+        if (a.giant + f.L > (uint32_t)B) { set_error("internal: shifted level diagonal leaves the block"); return COPSE_EINVAL; }
     // reshuffle diagonals at the level of Decisions
     {
-        const int m1 = (int)f.m1();
-        std::vector<uint32_t> pat(D->rot_R.size() * (size_t)m1);
-        for (size_t r = 0; r < D->rot_R.size(); r++) {
-            f.reshuffle_diagonal(D->rot_R[r], dg8);
-            for (int x = 0; x < m1; x++) pat[r * m1 + x] = dg8[x];
-        }
-        // extended basis: the products are summed before the key switch's ModDown
-        const size_t w = (size_t)(D->lvl_D + A) * N;
-        STATUS_TRY(encode_patterns(c, pat, (int)D->rot_R.size(), m1, B, D->lvl_D, A, cur, s));
-        D->pt_R.assign(1, std::vector<const u64 *>());
-        for (size_t r = 0; r < D->rot_R.size(); r++) D->pt_R[0].push_back(cur + r * w);
-        cur += D->rot_R.size() * w;
+        std::vector<uint8_t> dg8;
+        STATUS_TRY(encode_group(D->R, D->lvl_D, (int)f.m1(), [&](uint32_t, uint32_t i, std::vector<uint32_t> &out) {
+            f.reshuffle_diagonal(i, dg8);
+            out.assign(dg8.begin(), dg8.end());
+        }));
     }
-    // level diagonals (signed, mask folded in; extended basis) and masks at the level of Branches
+    // level diagonals (signed, mask folded in) and masks at the level of Branches
     {
+        std::vector<uint64_t> dg64;
+        STATUS_TRY(encode_group(D->Lv, D->lvl_B, (int)f.L, [&](uint32_t k, uint32_t i, std::vector<uint32_t> &out) {
+            f.level_diagonal(k + 1, i, t, dg64);
+            out.assign(dg64.begin(), dg64.end());
+        }));
         const int Lf = (int)f.L;
-        const size_t w = (size_t)(D->lvl_B + A) * N;
-        std::vector<uint32_t> pat(nlvl * (size_t)Lf);
-        size_t at = 0;
-        D->pt_B.assign(f.d, std::vector<const u64 *>(D->rot_B.size(), nullptr));
-        for (uint32_t k = 1; k <= f.d; k++)
-            for (size_t r = 0; r < D->rot_B.size(); r++) {
-                if (!lvl_nz[k - 1][r]) continue;
-                f.level_diagonal(k, D->rot_B[r], t, dg64);
-                for (int x = 0; x < Lf; x++) pat[at * Lf + x] = (uint32_t)dg64[x];
-                D->pt_B[k - 1][r] = cur + at * w;
-                at++;
-            }
-        STATUS_TRY(encode_patterns(c, pat, (int)at, Lf, B, D->lvl_B, A, cur, s));
-        cur += at * w;
         std::vector<uint32_t> mpat((size_t)f.d * Lf);
         for (uint32_t k = 1; k <= f.d; k++) {
             for (int x = 0; x < Lf; x++) mpat[(size_t)(k - 1) * Lf + x] = f.mask[(size_t)(k - 1) * Lf + x];
@@ -176,11 +198,11 @@ extern "C" copse_status copse_model_info_get(const copse_model *m, copse_model_i
     info->n_trees = (uint32_t)f.roots.size();
     info->n_classes = (uint32_t)f.classes.size();
     info->block = f.block;
-    uint32_t nr = 0, nl = 0;
-    for (uint32_t r : f.rot_reshuffle) nr += r != 0;
-    for (uint32_t r : f.rot_level) nl += r != 0;
-    info->n_rot_reshuffle = nr;
-    info->n_rot_level = nl;
+    std::vector<uint32_t> rs, ls;
+    f.group_reshuffle().rotations(rs);
+    f.group_level().rotations(ls);
+    info->n_rot_reshuffle = (uint32_t)rs.size();
+    info->n_rot_level = (uint32_t)ls.size();
     info->levels_used = f.levels_used();
     return COPSE_OK;
 }
@@ -201,11 +223,42 @@ extern "C" copse_status copse_model_export(const copse_model *m, uint32_t *thr_s
 
 extern "C" copse_status copse_model_rotations(const copse_model *m, uint32_t *reshuffle, uint32_t *level) {
     if (!m) { set_error("null model"); return COPSE_EINVAL; }
-    size_t a = 0, b = 0;
-    for (uint32_t r : m->f.rot_reshuffle)
-        if (r && reshuffle) reshuffle[a++] = r;
-    for (uint32_t r : m->f.rot_level)
-        if (r && level) level[b++] = r;
+    std::vector<uint32_t> rs, ls;
+    m->f.group_reshuffle().rotations(rs);
+    m->f.group_level().rotations(ls);
+    if (reshuffle) std::copy(rs.begin(), rs.end(), reshuffle);
+    if (level) std::copy(ls.begin(), ls.end(), level);
+    return COPSE_OK;
+}
+
+extern "C" copse_status copse_model_set_bsgs(copse_model *m, uint32_t g_reshuffle, uint32_t g_level) {
+    if (!m) { set_error("null model"); return COPSE_EINVAL; }
+    CompiledForest &f = m->f;
+    // a giant step k g must keep the shifted diagonal inside the query block
+    auto fits = [&](const BsgsGroup &G, uint32_t rows) {
+        for (const auto &a : G.acc)
+            if (a.giant + rows > f.block) return false;
+        return true;
+    };
+    if (!fits(bsgs_group({f.rot_reshuffle}, g_reshuffle), f.m1()) || !fits(bsgs_group(f.lvl_nonzero, g_level), f.L)) {
+        set_error("baby-step size moves a diagonal out of the query block");
+        return COPSE_EINVAL;
+    }
+    if (f.g_reshuffle != g_reshuffle || f.g_level != g_level) {
+        f.g_reshuffle = g_reshuffle;
+        f.g_level = g_level;
+        if (m->dev) {
+            cudaDeviceSynchronize();
+            m->dev.reset();
+        }
+    }
+    return COPSE_OK;
+}
+
+extern "C" copse_status copse_model_get_bsgs(const copse_model *m, uint32_t *g_reshuffle, uint32_t *g_level) {
+    if (!m || !g_reshuffle || !g_level) { set_error("null argument"); return COPSE_EINVAL; }
+    *g_reshuffle = m->f.g_reshuffle;
+    *g_level = m->f.g_level;
     return COPSE_OK;
 }
 
@@ -225,8 +278,10 @@ extern "C" copse_status copse_keygen(copse_ctx *c, uint64_t seed, const copse_mo
     for (size_t i = 0; i < n_models; i++) {
         const CompiledForest &f = models[i]->f;
         if ((int)f.log_n != c->logN) { set_error("model compiled for another ring degree"); return COPSE_EINVAL; }
-        std::vector<uint32_t> rs = f.rot_reshuffle;
-        rs.insert(rs.end(), f.rot_level.begin(), f.rot_level.end());
+        std::vector<uint32_t> rs, ls;
+        f.group_reshuffle().rotations(rs);
+        f.group_level().rotations(ls);
+        rs.insert(rs.end(), ls.begin(), ls.end());
         for (uint32_t r : rs) {
             if (!r) continue;
             u64 g = 1, b = 3;
@@ -310,6 +365,14 @@ extern "C" copse_status copse_encrypt_features(copse_ctx *c, const copse_keys *k
     return COPSE_OK;
 }
 
+// The products of one vector with a group of matrices: the plain diagonal method,
+// or its baby-step / giant-step form.
+static copse_status group_matmul(copse_ctx *c, const copse_evk *evk, const DCt &v, const DeviceModel::Group &G,
+                                 const std::vector<const u64 *> &add, std::vector<DCt> &out, cudaStream_t s) {
+    if (G.plan.plain()) return op_matmul(c, evk, v, G.plan.baby, G.pt, add, out, s);
+    return op_matmul_bsgs(c, evk, v, G.plan.baby, G.pt, G.acc_mat, G.acc_giant, (int)G.plan.n_mat, add, out, s);
+}
+
 static copse_status infer_impl(copse_ctx *c, const copse_evk *evk, copse_model *m, const copse_ctbuf *feats,
                                DCt *result, cudaStream_t s, int lane = 0, cudaEvent_t *stage_ev = nullptr) {
     STATUS_TRY(upload_model(c, m, s));
@@ -372,12 +435,12 @@ static copse_status infer_impl(copse_ctx *c, const copse_evk *evk, copse_model *
     STATUS_TRY(mark(1));
     // reshuffle: Branches = R_ext * Decisions
     std::vector<DCt> br;
-    STATUS_TRY(op_matmul(c, evk, Dc, D.rot_R, D.pt_R, {nullptr}, br, s));
+    STATUS_TRY(group_matmul(c, evk, Dc, D.R, {nullptr}, br, s));
     ct_free(&Dc, s);
     STATUS_TRY(mark(2));
     // levels: Lvl_k * Branches XOR Mask_k, rotations of Branches shared by every level
     std::vector<DCt> lv;
-    STATUS_TRY(op_matmul(c, evk, br[0], D.rot_B, D.pt_B, D.mask, lv, s));
+    STATUS_TRY(group_matmul(c, evk, br[0], D.Lv, D.mask, lv, s));
     ct_free(&br[0], s);
     STATUS_TRY(mark(3));
     // product across levels, balanced

@@ -222,14 +222,73 @@ int compile_forest(const char *text, size_t len, uint32_t precision, uint32_t n_
         f.reshuffle_diagonal(i, dg);
         if (std::any_of(dg.begin(), dg.end(), [](uint8_t v) { return v != 0; })) f.rot_reshuffle.push_back(i);
     }
+    f.lvl_nonzero.assign(f.d, {});
     for (uint32_t i = 0; i < f.b; i++) {
-        bool nz = false;
-        for (uint32_t k = 0; k < f.d && !nz; k++)
-            for (uint32_t x = 0; x < f.L && !nz; x++)
-                nz = f.lvl[((size_t)k * f.L + x) * f.b + (x + i) % f.b] != 0;
-        if (nz) f.rot_level.push_back(i);
+        bool any = false;
+        for (uint32_t k = 0; k < f.d; k++) {
+            bool nz = false;
+            for (uint32_t x = 0; x < f.L && !nz; x++) nz = f.lvl[((size_t)k * f.L + x) * f.b + (x + i) % f.b] != 0;
+            if (nz) f.lvl_nonzero[k].push_back(i);
+            any |= nz;
+        }
+        if (any) f.rot_level.push_back(i);
     }
     return 0;
+}
+
+bool BsgsGroup::plain() const {
+    if (acc.size() != n_mat) return false;
+    for (const Acc &a : acc)
+        if (a.giant != 0) return false;
+    return true;
+}
+
+void BsgsGroup::rotations(std::vector<uint32_t> &out) const {
+    std::vector<uint32_t> r;
+    for (uint32_t b : baby)
+        if (b) r.push_back(b);
+    for (const Acc &a : acc)
+        if (a.giant) r.push_back(a.giant);
+    std::sort(r.begin(), r.end());
+    r.erase(std::unique(r.begin(), r.end()), r.end());
+    out = r;
+}
+
+BsgsGroup bsgs_group(const std::vector<std::vector<uint32_t>> &nonzero, uint32_t g) {
+    BsgsGroup G;
+    G.n_mat = (uint32_t)nonzero.size();
+    std::vector<uint32_t> babies;
+    for (const auto &nz : nonzero)
+        for (uint32_t i : nz) babies.push_back(g ? i % g : i);
+    std::sort(babies.begin(), babies.end());
+    babies.erase(std::unique(babies.begin(), babies.end()), babies.end());
+    G.baby = babies;
+    auto baby_pos = [&](uint32_t j) {
+        return (int)(std::lower_bound(G.baby.begin(), G.baby.end(), j) - G.baby.begin());
+    };
+    for (uint32_t a = 0; a < G.n_mat; a++) {
+        // giant steps of this matrix, ascending (the nonzero lists are ascending)
+        std::vector<BsgsGroup::Acc> accs;
+        for (uint32_t i : nonzero[a]) {
+            const uint32_t giant = g ? i - i % g : 0, j = g ? i % g : i;
+            if (accs.empty() || accs.back().giant != giant) {
+                BsgsGroup::Acc x;
+                x.mat = a;
+                x.giant = giant;
+                x.diag.assign(G.baby.size(), -1);
+                accs.push_back(std::move(x));
+            }
+            accs.back().diag[baby_pos(j)] = (int32_t)i;
+        }
+        if (accs.empty()) {  // a zero matrix still yields its (zero) product
+            BsgsGroup::Acc x;
+            x.mat = a;
+            x.diag.assign(G.baby.size(), -1);
+            accs.push_back(std::move(x));
+        }
+        for (auto &x : accs) G.acc.push_back(std::move(x));
+    }
+    return G;
 }
 
 void classify_plain(const CompiledForest &m, const uint32_t *x, uint8_t *bits) {

@@ -17,6 +17,25 @@ struct ForestNode {
     int left = -1, right = -1;  // node indices
 };
 
+// Baby-step / giant-step split of the diagonal method for a group of matrices
+// applied to one vector: diagonal i = k g + j of matrix a is multiplied, shifted
+// by k g inside the query block, with rot(v, j) into accumulator (a, k g); each
+// matrix's accumulators are then rotated by their giant step and summed.  g = 0
+// keeps the plain method: all nonzero diagonals are baby steps, one
+// accumulator per matrix with giant step 0.
+struct BsgsGroup {
+    struct Acc {
+        uint32_t mat = 0, giant = 0;
+        std::vector<int32_t> diag;  // per baby step: diagonal index giant + baby, or -1 (zero)
+    };
+    std::vector<uint32_t> baby;     // ascending, may include 0
+    std::vector<Acc> acc;           // matrices in order, giant steps ascending within a matrix
+    uint32_t n_mat = 0;
+    bool plain() const;             // one accumulator per matrix, every giant step 0
+    void rotations(std::vector<uint32_t> &out) const;  // nonzero baby and giant amounts, ascending
+};
+BsgsGroup bsgs_group(const std::vector<std::vector<uint32_t>> &nonzero, uint32_t g);
+
 struct CompiledForest {
     // forest
     std::vector<std::string> classes;
@@ -40,6 +59,11 @@ struct CompiledForest {
     // nonzero diagonal indices
     std::vector<uint32_t> rot_reshuffle;  // ascending, may include 0
     std::vector<uint32_t> rot_level;      // union over levels, ascending, may include 0
+    std::vector<std::vector<uint32_t>> lvl_nonzero;  // per level: nonzero diagonal indices
+    // baby-step sizes of the reshuffle and of the level products (0 = plain method)
+    uint32_t g_reshuffle = 0, g_level = 0;
+    BsgsGroup group_reshuffle() const { return bsgs_group({rot_reshuffle}, g_reshuffle); }
+    BsgsGroup group_level() const { return bsgs_group(lvl_nonzero, g_level); }
 
     uint32_t m1() const { return L + b - 1; }       // rows of the extended reshuffle
     uint32_t pd() const { return m1() + q - 1; }    // slots carrying the periodic decisions

@@ -260,9 +260,22 @@ copse_status op_rotate(copse_ctx *c, const copse_evk *evk, const DCt &a, uint32_
 // with R_k the rotation by rots[k] before its ModDown (one ModUp of v serves all k)
 // and k0 the zero rotation if present.  pt[a][k] may be null (zero diagonal);
 // pt pointers are NTT-domain [v.level + alpha][N] (extended basis), add[a] [v.level][N].
+// raw = true: out[a] = ModDown(...) + pt[a][k0] * v only (no add, no modswitch).
 copse_status op_matmul(copse_ctx *c, const copse_evk *evk, const DCt &v, const std::vector<uint32_t> &rots,
                        const std::vector<std::vector<const u64 *>> &pt, const std::vector<const u64 *> &add,
-                       std::vector<DCt> &out, cudaStream_t s);
+                       std::vector<DCt> &out, cudaStream_t s, bool raw = false);
+// Baby-step / giant-step products: the baby-step sums of every accumulator
+// (matrix acc_mat[x], giant step acc_giant[x]) share the rotations of v by the
+// baby amounts (op_matmul, raw); then for each matrix a
+//   out[a] = modswitch(rotsum_k(inner[a, k], k) + add[a]).
+copse_status op_matmul_bsgs(copse_ctx *c, const copse_evk *evk, const DCt &v, const std::vector<uint32_t> &baby,
+                            const std::vector<std::vector<const u64 *>> &pt, const std::vector<int> &acc_mat,
+                            const std::vector<uint32_t> &acc_giant, int n_mat, const std::vector<const u64 *> &add,
+                            std::vector<DCt> &out, cudaStream_t s);
+// sum_k rot(terms[k], amounts[k]) with one ModDown for all rotated terms (amount 0:
+// added as is), plus add (a [level][N] plaintext or null), then one modulus switch.
+copse_status op_rotsum(copse_ctx *c, const copse_evk *evk, const std::vector<DCt> &terms,
+                       const std::vector<uint32_t> &amounts, const u64 *add, DCt *out, cudaStream_t s);
 // encode host slot patterns: n patterns of `len` values mod t, repeated every
 // `period` slots (period divides N; len <= period), into NTT-domain plaintexts
 // [n][level + ext_alpha][N] over q_0..q_{level-1} and, when ext_alpha > 0, the

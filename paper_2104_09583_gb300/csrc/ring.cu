@@ -26,6 +26,7 @@ constexpr int MAX_ALPHA = 40;
 constexpr int MAX_ACC = 8;
 constexpr int CHUNK_ROT = 64;
 constexpr int MM_PARTS = 8;  // rotation ranges with their own partial sums in k_mm_fused
+constexpr int RS_CHUNK = 32; // giant-step terms per k_rotsum launch
 
 inline unsigned nblk(size_t n) { return (unsigned)((n + TPB - 1) / TPB); }
 
@@ -284,6 +285,49 @@ __global__ void __launch_bounds__(256) k_mm_fused(const u64 *yhat, const u64 *c0
         tab.acc[x][poff + e] = a0[x];
         tab.acc[x][poff + n_el + e] = a1[x];
     }
+}
+
+// Giant steps of a baby-step / giant-step product: for every element (r, n) of
+// the extended basis, over the terms t of the chunk (ciphertext c_t, rotation g_t)
+//   acc += sum_j tau_t(yhat_t[j]) * ksk_t[j]   (+ P * tau_t(c_t0) on component 0 at q-primes)
+// i.e. the key-switched rotation of each term before its ModDown, summed.
+struct RsTerm {
+    const u64 *yhat;  // ModUp digits of c_t1, [ndig][ell+alpha][N]
+    const u64 *c0;    // c_t0, [ell][N]
+    const u64 *ksk;   // [ndig][2][L+alpha][N]
+    u64 g;            // Galois element
+};
+struct RsTable {
+    RsTerm t[RS_CHUNK];
+};
+
+__global__ void __launch_bounds__(256) k_rotsum(const RsTable tab, int nterm, u64 *acc, int ell, int alpha, int L,
+                                                int logN, const PrimeDev *pr, KsTables T) {
+    const int N = 1 << logN;
+    const int nx = ell + alpha, nd = (ell + alpha - 1) / alpha, NB = L + alpha;
+    const size_t n_el = (size_t)nx << logN;
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n_el) return;
+    const int r = (int)(e >> logN);
+    const uint32_t n = (uint32_t)(e & (N - 1));
+    const int g = r < ell ? r : L + (r - ell);
+    const PrimeDev P = pr[g];
+    const u64 Pm = r < ell ? T.md_P[r] : 0;
+    u64 a0 = acc[e], a1 = acc[n_el + e];
+    for (int k = 0; k < nterm; k++) {
+        const RsTerm J = tab.t[k];
+        const uint32_t src = galois_src(n, J.g, logN);
+        for (int j = 0; j < nd; j++) {
+            const u64 y = J.yhat[(((size_t)j * nx + r) << logN) + src];
+            const u64 *k0 = J.ksk + (((size_t)(2 * j) * NB + g) << logN);
+            const u64 *k1 = J.ksk + (((size_t)(2 * j + 1) * NB + g) << logN);
+            a0 = add_mod(a0, mul_mod(y, k0[n], P), P.q);
+            a1 = add_mod(a1, mul_mod(y, k1[n], P), P.q);
+        }
+        if (r < ell) a0 = add_mod(a0, mul_mod(Pm, J.c0[((size_t)r << logN) + src], P), P.q);
+    }
+    acc[e] = a0;
+    acc[n_el + e] = a1;
 }
 
 // out[i] = sum_y part[y * stride + i] over nparts partial sums of extended-basis
@@ -735,7 +779,7 @@ copse_status op_rotate(copse_ctx *c, const copse_evk *evk, const DCt &a, uint32_
 
 copse_status op_matmul(copse_ctx *c, const copse_evk *evk, const DCt &v, const std::vector<uint32_t> &rots,
                        const std::vector<std::vector<const u64 *>> &pt, const std::vector<const u64 *> &add,
-                       std::vector<DCt> &out, cudaStream_t s) {
+                       std::vector<DCt> &out, cudaStream_t s, bool raw) {
     const int ell = v.level, N = c->N, A = c->alpha, nx = ell + A, nacc = (int)pt.size(), nrot = (int)rots.size();
     const size_t ext = (size_t)2 * nx * N, per = (size_t)2 * ell * N;
     Scratch sc(s);
@@ -756,7 +800,8 @@ copse_status op_matmul(copse_ctx *c, const copse_evk *evk, const DCt &v, const s
     if (!ks_idx.empty()) {
         // rotations of a chunk are split into `parts` ranges with their own partial sums
         // (more independent threads to hide the gathers' latency), summed before ModDown
-        const int parts = (int)std::min<size_t>(MM_PARTS, (ks_idx.size() + 7) / 8);
+        // (with many accumulators the launches over accumulator chunks already fill the GPU)
+        const int parts = nacc > MAX_ACC ? 1 : (int)std::min<size_t>(MM_PARTS, (ks_idx.size() + 7) / 8);
         const size_t part_stride = (size_t)nacc * ext;
         u64 *part = nullptr;
         STATUS_TRY(sc.get(c, &acc, (size_t)nacc * ext));
@@ -818,6 +863,13 @@ copse_status op_matmul(copse_ctx *c, const copse_evk *evk, const DCt &v, const s
                   k_ident_mac<<<nblk(per), TPB, 0, s>>>(ra, v.data, pt[a][r], ell, c->logN, c->d_prime));
             LAUNCH_CHECK();
         }
+        if (raw) {
+            DCt tmp;
+            tmp.level = ell;
+            tmp.data = ra;
+            STATUS_TRY(ct_copy(c, tmp, &out[a], s));
+            continue;
+        }
         if (add.size() > (size_t)a && add[a]) {
             k_add_plain<<<nblk((size_t)ell * N), TPB, 0, s>>>(ra, add[a], ell, c->logN, c->d_prime);
             LAUNCH_CHECK();
@@ -829,6 +881,96 @@ copse_status op_matmul(copse_ctx *c, const copse_evk *evk, const DCt &v, const s
         STATUS_TRY(op_modswitch(c, tmp, &out[a], s));
     }
     return COPSE_OK;
+}
+
+copse_status op_rotsum(copse_ctx *c, const copse_evk *evk, const std::vector<DCt> &terms,
+                       const std::vector<uint32_t> &amounts, const u64 *add, DCt *out, cudaStream_t s) {
+    if (terms.empty() || terms.size() != amounts.size()) { set_error("internal: bad rotation sum"); return COPSE_EINVAL; }
+    const int ell = terms[0].level, N = c->N, A = c->alpha, nx = ell + A;
+    const size_t per = (size_t)2 * ell * N, ext = (size_t)2 * nx * N;
+    std::vector<int> rot;
+    std::vector<u64> gal(terms.size());
+    for (size_t k = 0; k < terms.size(); k++) {
+        if (terms[k].level != ell) { set_error("internal: rotation sum over mixed levels"); return COPSE_EINVAL; }
+        gal[k] = galois_of_rotation(c, amounts[k]);
+        if (gal[k] == 1) continue;
+        if (!evk->find(gal[k])) { set_error("no rotation key for amount " + std::to_string(amounts[k])); return COPSE_ENOKEY; }
+        rot.push_back((int)k);
+    }
+    Scratch sc(s);
+    u64 *res = nullptr;
+    STATUS_TRY(sc.get(c, &res, per));
+    if (rot.empty()) {
+        CUDA_TRY(cudaMemsetAsync(res, 0, per * sizeof(u64), s));
+    } else {
+        u64 *acc = nullptr, *W = nullptr;
+        STATUS_TRY(sc.get(c, &acc, ext));
+        STATUS_TRY(sc.get(c, &W, per));
+        CUDA_TRY(cudaMemsetAsync(acc, 0, ext * sizeof(u64), s));
+        const int nd = (ell + A - 1) / A;
+        for (size_t k0 = 0; k0 < rot.size(); k0 += RS_CHUNK) {
+            const int nt = (int)std::min<size_t>(RS_CHUNK, rot.size() - k0);
+            Scratch sk(s);  // the chunk's ModUp digits, freed (stream-ordered) after its launch
+            RsTable tab;
+            memset(&tab, 0, sizeof(tab));
+            for (int x = 0; x < nt; x++) {
+                const DCt &ct = terms[rot[k0 + x]];
+                u64 *yhat = nullptr;
+                STATUS_TRY(ks_modup(c, ct.data + (size_t)ell * N, ell, sk, &yhat, s));
+                tab.t[x] = RsTerm{yhat, ct.data, evk->find(gal[rot[k0 + x]]), gal[rot[k0 + x]]};
+            }
+            const double bytes = 8.0 * N * ((double)nt * (2.0 * nd * nx + (double)nd * nx + ell) + 4.0 * nx);
+            TIMED("rotsum", bytes, s,
+                  k_rotsum<<<nblk((size_t)nx * N), TPB, 0, s>>>(tab, nt, acc, ell, A, c->L, c->logN, c->d_prime,
+                                                                c->ks));
+            LAUNCH_CHECK();
+        }
+        STATUS_TRY(ntt_inverse(c, batch(acc, (size_t)nx * N, 2, ell, A, ell), s));
+        TIMED("moddown_conv", 8.0 * N * 2.0 * ((double)A + ell), s,
+              k_moddown_conv<<<nblk((size_t)2 * N), TPB, 0, s>>>(acc, (size_t)nx * N, W, (size_t)ell * N, 2, ell, A,
+                                                                 c->L, c->logN, c->d_prime, c->ks));
+        LAUNCH_CHECK();
+        STATUS_TRY(ntt_forward(c, batch(W, (size_t)ell * N, 2, 0, ell, ell), s));
+        TIMED("md_finish", 8.0 * N * 3.0 * 2 * ell, s,
+              k_md_finish<<<nblk(per), TPB, 0, s>>>(acc, (size_t)nx * N, W, res, 2, ell, c->logN, c->d_prime, c->ks));
+        LAUNCH_CHECK();
+    }
+    for (size_t k = 0; k < terms.size(); k++) {
+        if (gal[k] != 1) continue;
+        k_add<<<nblk(per), TPB, 0, s>>>(res, terms[k].data, res, 2, ell, c->logN, 0, c->d_prime);
+        LAUNCH_CHECK();
+    }
+    if (add) {
+        k_add_plain<<<nblk((size_t)ell * N), TPB, 0, s>>>(res, add, ell, c->logN, c->d_prime);
+        LAUNCH_CHECK();
+    }
+    DCt tmp;
+    tmp.level = ell;
+    tmp.data = res;
+    return op_modswitch(c, tmp, out, s);
+}
+
+copse_status op_matmul_bsgs(copse_ctx *c, const copse_evk *evk, const DCt &v, const std::vector<uint32_t> &baby,
+                            const std::vector<std::vector<const u64 *>> &pt, const std::vector<int> &acc_mat,
+                            const std::vector<uint32_t> &acc_giant, int n_mat, const std::vector<const u64 *> &add,
+                            std::vector<DCt> &out, cudaStream_t s) {
+    std::vector<DCt> inner;
+    STATUS_TRY(op_matmul(c, evk, v, baby, pt, {}, inner, s, true));
+    out.assign(n_mat, DCt());
+    copse_status st = COPSE_OK;
+    for (int a = 0; a < n_mat && st == COPSE_OK; a++) {
+        std::vector<DCt> terms;
+        std::vector<uint32_t> amounts;
+        for (size_t x = 0; x < inner.size(); x++)
+            if (acc_mat[x] == a) {
+                terms.push_back(inner[x]);
+                amounts.push_back(acc_giant[x]);
+            }
+        const u64 *ad = add.size() > (size_t)a ? add[a] : nullptr;
+        st = op_rotsum(c, evk, terms, amounts, ad, &out[a], s);
+    }
+    for (DCt &x : inner) ct_free(&x, s);
+    return st;
 }
 
 copse_status encode_patterns(copse_ctx *c, const std::vector<uint32_t> &patterns, int n, int len, int period,

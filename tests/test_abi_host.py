@@ -51,6 +51,12 @@ def test_compile_matches_oracle(case):
         rs, ls = K.copse_model_rotations(h)
         ors, ols = Cp.rotation_sets(om)
         assert rs == ors and ls == ols
+        # baby-step / giant-step plans: the same key sets as the oracle's
+        for g in [(1, 1), (2, 3), (5, 4), (om.q, om.b)]:
+            K.copse_model_set_bsgs(h, *g)
+            assert K.copse_model_get_bsgs(h) == g
+            assert K.copse_model_rotations(h) == Cp.rotation_sets(om, g), g
+        K.copse_model_set_bsgs(h, 0, 0)
         qs = synth.random_queries(case, 20, om.n_features, p)
         got = K.copse_classify_plain(h, qs)
         _, trees = Cp.parse_forest(text)
