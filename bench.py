@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--no-serving", action="store_true", help="skip the Poisson-arrival serving leg")
     ap.add_argument("--no-table6", action="store_true", help="skip the per-stage microbenchmark sweep")
+    ap.add_argument("--no-tune", action="store_true", help="fixed schedule (dnum 3, plain products, cluster NTT)")
     return ap.parse_args()
 
 
@@ -182,8 +183,14 @@ def run_cuda(args, ws, rank, local):
     W = synth.WORKLOADS[args.workload]
     text = W.forest_texts()[0]
     N = 1 << W.log_n
-    ctx = K.copse_ctx_create(W.log_n, W.bits, W.primes, W.dnum, device=local)
     model = K.copse_compile_forest(text, W.precision(), W.n_features(), W.log_n)
+    dnum, tuning = W.dnum, None
+    if not args.no_tune:
+        dnum, dn_ms = K.copse_tune_dnum(W.log_n, W.bits, W.primes, model, [1, 2, 3, 4], 1, 3, device=local)
+        tuning = {"dnum_ms_per_inference": dn_ms}
+    ctx = K.copse_ctx_create(W.log_n, W.bits, W.primes, dnum, device=local)
+    if not args.no_tune:
+        tuning.update(autotune(K, ctx, [model]))
     info = K.copse_model_info_get(model)
     keys, evk = K.copse_keygen(ctx, 7 + rank, [model])
     stream = torch.cuda.current_stream().cuda_stream
@@ -339,8 +346,8 @@ def run_cuda(args, ws, rank, local):
                 "avg_launch_us": v["ms"] * 1e3 / v["launches"], "peak_source": f"{how} hbm_gbs (copy)",
                 "measured_on": "instrumented host-launched replay of the timed step (CUDA events per launch)"}
 
-    serving = None if args.no_serving else run_serving(local)
-    batch3 = None if args.no_serving else run_batch3(local)
+    serving = None if args.no_serving else run_serving(local, tune=not args.no_tune)
+    batch3 = None if args.no_serving else run_batch3(local, tune=not args.no_tune)
     table6 = None if args.no_table6 else run_table6(local)
 
     cpu = None
@@ -359,7 +366,7 @@ def run_cuda(args, ws, rank, local):
         "p99_ms": float(np.percentile(per, 99)), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "u64 (RNS residues mod 55-bit primes)", "data": "synthetic (seeded random forest and queries)",
         "config": {"workload": W.name, "ring_degree": N, "ciphertext_primes": W.primes, "prime_bits": W.bits,
-                   "dnum": W.dnum, "trees": 4, "branches": info["b"], "leaves": L, "depth": info["depth"],
+                   "dnum": dnum, "tuning": tuning, "trees": 4, "branches": info["b"], "leaves": L, "depth": info["depth"],
                    "features": nf, "precision": W.precision(), "queries_per_step": 1, "parallelism": f"replicas{ws}",
                    "l2": "working set > L2 (rotation keys alone are %.1f GB)" % (
                        (info["n_rot_reshuffle"] + info["n_rot_level"]) * 3 * 2 * (W.primes + 4) * N * 8 / 1e9)},
@@ -370,26 +377,56 @@ def run_cuda(args, ws, rank, local):
     return line
 
 
+def autotune(K, ctx, models, g_r=(0, 16, 32, 64), g_l=(0, 4, 8), nq=1):
+    """NTT kernel crossover for the context, then baby-step sizes per model (fastest stage times)."""
+    lim, _ = K.copse_tune_ntt(ctx)
+    plans = []
+    for m in models:
+        K.copse_tune_bsgs(ctx, m, list(g_r), list(g_l), nq, 3)
+        plans.append(list(K.copse_model_get_bsgs(m)))
+    return {"ntt_cluster_max_polys": lim, "bsgs_plans": plans}
+
+
 # ---------------------------------------------------------------- serving
-def run_serving(local, rate=200.0, n_req=1000, warm=100, seed=5):
-    """Poisson arrivals (mean `rate` per second) of single queries against four resident models
-    (the N = 2^14 bench forest and the three batching forests), each model chosen uniformly; the
-    server batches them continuously into graph launches.  Latency is submit -> completion as the
-    server measures it; throughput is completed requests over the wall time of the run."""
+def run_serving(local, rate=200.0, n_req=1000, warm=100, seed=5, tune=True):
+    """Poisson arrivals (mean `rate` per second) of single queries against four resident models,
+    each chosen uniformly: the shapes of the three smaller workloads (1 tree of depth 3; 4 random
+    trees, ~100 branches; 16 trees of depth 6) on an N = 2^14 server and a 64-tree depth-6 8-bit
+    forest, whose query block needs N = 2^15, on a second server.  Each server batches its
+    requests continuously into graph launches.  Latency is submit -> completion as the server
+    measures it; throughput is completed requests over the offered time of the measured part."""
     import queue
     import threading
 
     from paper_2104_09583_gb300 import copse as K
     from paper_2104_09583_gb300 import synth
 
-    Wf, Wb = synth.WORKLOADS["forest100-n16384"], synth.WORKLOADS["batch3-n16384"]
-    specs = [(Wf.forest_texts()[0], Wf.precision(), Wf.n_features())] + \
-            [(t, Wb.precision(k), Wb.n_features(k)) for k, t in enumerate(Wb.forest_texts())]
-    ctx = K.copse_ctx_create(Wf.log_n, Wf.bits, Wf.primes, Wf.dnum, device=local)
-    models = [K.copse_compile_forest(t, p, nf, Wf.log_n) for t, p, nf in specs]
-    keys, evk = K.copse_keygen(ctx, 13, models)
+    Wt, Wf, Wb = (synth.WORKLOADS[n] for n in ("toy-n1024", "forest100-n16384", "batch3-n16384"))
+    # (text, precision, features, ring) per model
+    specs = [(Wt.forest_texts()[0], Wt.precision(), Wt.n_features(), 14),
+             (Wf.forest_texts()[0], Wf.precision(), Wf.n_features(), 14),
+             (Wb.forest_texts()[2], Wb.precision(2), Wb.n_features(2), 14),
+             (synth.random_forest(5004, 64, 6, 16, 8, 4, complete=True), 8, 16, 15)]
+    rings = {}
+    for log_n in (14, 15):
+        ids = [k for k, sp in enumerate(specs) if sp[3] == log_n]
+        ctx = K.copse_ctx_create(log_n, Wf.bits, Wf.primes, 2, device=local)
+        ms = [K.copse_compile_forest(specs[k][0], specs[k][1], specs[k][2], log_n) for k in ids]
+        if tune:
+            # the 64-tree reshuffle has ~3700 diagonals: its plain key set is not an option
+            autotune(K, ctx, ms, g_r=(32, 64, 128) if log_n == 15 else (0, 16, 32, 64), g_l=(0, 8, 16))
+        elif log_n == 15:
+            K.copse_model_set_bsgs(ms[0], 64, 0)
+        keys, evk = K.copse_keygen(ctx, 13, ms)
+        srv = K.copse_server_create(ctx, keys, evk, ms)
+        rings[log_n] = (ctx, ms, keys, evk, srv, ids)
+    route = {}
+    models = [None] * len(specs)
+    for log_n, (ctx, ms, keys, evk, srv, ids) in rings.items():
+        for local_id, k in enumerate(ids):
+            route[k] = (srv, local_id)
+            models[k] = ms[local_id]
     infos = [K.copse_model_info_get(m) for m in models]
-    srv = K.copse_server_create(ctx, keys, evk, models)
     rng = np.random.default_rng(seed)
     total = warm + n_req
     choice = rng.integers(len(models), size=total)
@@ -405,8 +442,9 @@ def run_serving(local, rate=200.0, n_req=1000, warm=100, seed=5):
             d = t_next - time.perf_counter()
             if d > 0:
                 time.sleep(d)
+            srv_k, mid = route[int(choice[i])]
             try:
-                tickets.put((i, int(choice[i]), K.copse_server_submit(srv, int(choice[i]), qs[i])))
+                tickets.put((i, int(choice[i]), K.copse_server_submit(srv_k, mid, qs[i])))
             except K.CopseError:
                 refused[0] += 1
                 tickets.put((i, int(choice[i]), None))
@@ -419,7 +457,7 @@ def run_serving(local, rate=200.0, n_req=1000, warm=100, seed=5):
         i, k, t = tickets.get()
         if t is None:
             continue
-        bits, ms = K.copse_server_poll(srv, t, infos[k]["n_leaves"], 60000)
+        bits, ms = K.copse_server_poll(route[k][0], t, infos[k]["n_leaves"], 60000)
         ok &= bool(np.array_equal(bits, K.copse_classify_plain(models[k], qs[i][None, :])[0]))
         if i >= warm:
             lat.append(ms)
@@ -428,21 +466,23 @@ def run_serving(local, rate=200.0, n_req=1000, warm=100, seed=5):
             t_last = now
     th.join()
     wall = time.perf_counter() - t0
-    K.copse_server_destroy(srv)
-    K.copse_keys_destroy(keys)
-    K.copse_evk_destroy(evk)
-    for m in models:
-        K.copse_model_destroy(m)
-    K.copse_ctx_destroy(ctx)
+    for ctx, ms, keys, evk, srv, ids in rings.values():
+        K.copse_server_destroy(srv)
+        K.copse_keys_destroy(keys)
+        K.copse_evk_destroy(evk)
+        for m in ms:
+            K.copse_model_destroy(m)
+        K.copse_ctx_destroy(ctx)
     measured_s = sum(gaps[warm:])
     return {"value": len(lat) / measured_s, "unit": UNIT, "offered_rate": rate, "requests": n_req,
             "warmup_requests": warm, "refused": refused[0], "p50_ms": float(np.percentile(lat, 50)),
             "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(np.mean(lat)), "labels_ok": ok,
-            "models": [f"{i['n_trees']} trees, {i['b']} branches, block {i['block']}" for i in infos],
+            "models": [f"{i['n_trees']} trees, {i['b']} branches, block {i['block']}, N = 2^{sp[3]}"
+                       for i, sp in zip(infos, specs)],
             "wall_s": wall}
 
 
-def run_batch3(local, steps=3, warmup=1):
+def run_batch3(local, steps=3, warmup=1, tune=True):
     """256 queries over three forests (1 x depth 3, 4 x depth 5, 16 x depth 6; 8/16/32 features, 8-bit)
     evaluated by one graph launch: one work item per ciphertext (32 + 3 x 32 + 32 x 4 queries)."""
     import torch
@@ -451,9 +491,16 @@ def run_batch3(local, steps=3, warmup=1):
     from paper_2104_09583_gb300 import synth
 
     W = synth.WORKLOADS["batch3-n16384"]
-    ctx = K.copse_ctx_create(W.log_n, W.bits, W.primes, W.dnum, device=local)
     texts = W.forest_texts()
     models = [K.copse_compile_forest(t, W.precision(k), W.n_features(k), W.log_n) for k, t in enumerate(texts)]
+    dnum, tuning = W.dnum, None
+    if tune:
+        # digit count on the largest forest, then the NTT crossover and every forest's plan
+        dnum, dn_ms = K.copse_tune_dnum(W.log_n, W.bits, W.primes, models[2], [2, 3, 4], 1, 2, device=local)
+        tuning = {"dnum": dnum, "dnum_ms_per_inference": dn_ms}
+    ctx = K.copse_ctx_create(W.log_n, W.bits, W.primes, dnum, device=local)
+    if tune:
+        tuning.update(autotune(K, ctx, models, g_r=(0, 16, 32, 64), g_l=(0, 8, 16)))
     keys, evk = K.copse_keygen(ctx, 17, models)
     infos = [K.copse_model_info_get(m) for m in models]
     per = [(1 << W.log_n) // i["block"] for i in infos]
@@ -495,7 +542,7 @@ def run_batch3(local, steps=3, warmup=1):
         K.copse_model_destroy(m)
     K.copse_ctx_destroy(ctx)
     return {"value": 256 / (ms / 1e3), "unit": UNIT, "ms_per_launch": ms, "queries_per_launch": 256,
-            "items": len(items), "labels_ok": ok,
+            "items": len(items), "labels_ok": ok, "tuning": tuning,
             "forests": [f"{i['n_trees']} trees, {i['b']} branches, {i['n_rot_reshuffle']}+{i['n_rot_level']} "
                         f"rotations, {p} queries/ciphertext" for i, p in zip(infos, per)]}
 

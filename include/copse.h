@@ -333,6 +333,38 @@ copse_status copse_poly_mul(copse_ctx *ctx, const uint64_t *a, const uint64_t *b
 copse_status copse_poly_mul_noalloc(copse_ctx *ctx, const uint64_t *a, const uint64_t *b, uint64_t *c,
                                     uint32_t n_res, void *stream);
 
+/* ---------------------------------------------------------------- autotuning
+ * The paper fixes its HElib parameters by hand (Section 8.1); these calls pick
+ * schedule choices by running every candidate on the device and timing it
+ * with CUDA events (median of `reps` timed runs after one warm-up).  None
+ * changes a result: any choice gives a correct inference, the ciphertexts
+ * differ only in rounding.  All block the calling thread. */
+
+/* NTT kernel family by batch size: one thread-block-cluster launch per
+ * transform against two tiled launches, forward + inverse of sizes[i]
+ * residue polynomials each (ms_cluster[i], ms_tiled[i]).  The context then
+ * takes the cluster form for batches up to *max_cluster residue polynomials
+ * (the largest timed size at which it is not slower; 0 = never, 2^30 =
+ * always, when that is the largest size timed) and the tiled form above. */
+copse_status copse_tune_ntt(copse_ctx *ctx, const uint32_t *sizes, size_t n, int reps, float *ms_cluster,
+                            float *ms_tiled, uint32_t *max_cluster);
+
+/* Baby-step sizes (copse_model_set_bsgs): the reshuffle candidates g_r[] are
+ * timed by the reshuffle stage with the level plan held, then the level
+ * candidates g_l[] by the level stage with the chosen reshuffle plan, each
+ * with fresh keys for its plan and n_queries random queries.  ms_r[i], ms_l[i]:
+ * stage medians, -1 for a candidate the query block cannot hold.  Leaves the
+ * best plan set on the model; keys must then be made for it. */
+copse_status copse_tune_bsgs(copse_ctx *ctx, copse_model *model, const uint32_t *g_r, size_t n_r,
+                             const uint32_t *g_l, size_t n_l, size_t n_queries, int reps, float *ms_r,
+                             float *ms_l);
+
+/* Key-switching digit count: one context per candidate dnums[i] (base's other
+ * parameters), one whole inference timed on each; ms[i] its median (-1 for a
+ * parameter set out of range), *best the fastest dnum. */
+copse_status copse_tune_dnum(const copse_params *base, int device, copse_model *model, const uint32_t *dnums,
+                             size_t n, size_t n_queries, int reps, float *ms, uint32_t *best);
+
 /* ---------------------------------------------------------------- kernel timing
  * Instrumentation, off by default.  When on, the library brackets every
  * kernel launch with two CUDA events on the launch stream and tags it with

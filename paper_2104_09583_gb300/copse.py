@@ -63,6 +63,12 @@ _SIG = {
     "copse_model_export": (C.c_int, [vp, vp, vp, vp, vp, vp, vp]),
     "copse_model_rotations": (C.c_int, [vp, vp, vp]),
     "copse_model_set_bsgs": (C.c_int, [vp, C.c_uint32, C.c_uint32]),
+    "copse_tune_ntt": (C.c_int, [vp, u32p, C.c_size_t, C.c_int, C.POINTER(C.c_float), C.POINTER(C.c_float),
+                                 C.POINTER(C.c_uint32)]),
+    "copse_tune_bsgs": (C.c_int, [vp, vp, u32p, C.c_size_t, u32p, C.c_size_t, C.c_size_t, C.c_int,
+                                  C.POINTER(C.c_float), C.POINTER(C.c_float)]),
+    "copse_tune_dnum": (C.c_int, [vp, C.c_int, vp, u32p, C.c_size_t, C.c_size_t, C.c_int,
+                                  C.POINTER(C.c_float), C.POINTER(C.c_uint32)]),
     "copse_model_get_bsgs": (C.c_int, [vp, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)]),
     "copse_classify_plain": (C.c_int, [vp, u32p, C.c_size_t, u8p]),
     "copse_keygen": (C.c_int, [vp, C.c_uint64, C.POINTER(C.c_void_p), C.c_size_t, pvp, pvp]),
@@ -185,6 +191,37 @@ def copse_model_get_bsgs(m):
     a, b = C.c_uint32(), C.c_uint32()
     _check(_lib.copse_model_get_bsgs(m, C.byref(a), C.byref(b)))
     return a.value, b.value
+
+
+def copse_tune_ntt(ctx, sizes=(4, 8, 16, 32, 64, 128, 256), reps=5):
+    """-> (max_cluster, {size: (cluster ms, tiled ms)}); the context takes the cluster
+    NTT for batches up to max_cluster residue polynomials."""
+    sz = np.ascontiguousarray(sizes, dtype=np.uint32)
+    mc = (C.c_float * len(sizes))()
+    mt = (C.c_float * len(sizes))()
+    lim = C.c_uint32()
+    _check(_lib.copse_tune_ntt(ctx, sz, len(sizes), reps, mc, mt, C.byref(lim)))
+    return lim.value, {int(x): (float(mc[i]), float(mt[i])) for i, x in enumerate(sizes)}
+
+
+def copse_tune_bsgs(ctx, model, g_r, g_l, n_queries=1, reps=3):
+    """-> ({g_r: reshuffle ms}, {g_l: level ms}); the best plan is left set on the model."""
+    a = np.ascontiguousarray(g_r, dtype=np.uint32) if len(g_r) else np.zeros(1, np.uint32)
+    b = np.ascontiguousarray(g_l, dtype=np.uint32) if len(g_l) else np.zeros(1, np.uint32)
+    ma = (C.c_float * max(len(g_r), 1))()
+    mb = (C.c_float * max(len(g_l), 1))()
+    _check(_lib.copse_tune_bsgs(ctx, model, a, len(g_r), b, len(g_l), n_queries, reps, ma, mb))
+    return ({int(g): float(ma[i]) for i, g in enumerate(g_r)}, {int(g): float(mb[i]) for i, g in enumerate(g_l)})
+
+
+def copse_tune_dnum(log_n, prime_bits, n_primes, model, dnums, n_queries=1, reps=3, device=0):
+    """-> (best dnum, {dnum: ms per inference})."""
+    p = copse_params(log_n, prime_bits, n_primes, 1)
+    d = np.ascontiguousarray(dnums, dtype=np.uint32)
+    ms = (C.c_float * len(dnums))()
+    best = C.c_uint32()
+    _check(_lib.copse_tune_dnum(C.byref(p), device, model, d, len(dnums), n_queries, reps, ms, C.byref(best)))
+    return best.value, {int(x): float(ms[i]) for i, x in enumerate(dnums)}
 
 
 def copse_classify_plain(m, feats):

@@ -24,6 +24,7 @@ cudaStream_t as_stream(void *s) { return (cudaStream_t)s; }
 // Plaintext structures of one model encoded for one context (NTT domain, device).
 struct DeviceModel {
     copse_ctx *ctx = nullptr;
+    uint64_t ctx_serial = 0;           // the context it was encoded for (addresses can be reused)
     int lvl_D = 0, lvl_B = 0;          // levels of Decisions and of Branches
     u64 *store = nullptr;              // one allocation for every plaintext
     // SecComp leaves, plane i: lt = x * lt_mul + lt_add, eq = x * eq_mul + eq_add (level L)
@@ -50,7 +51,7 @@ struct copse_model {
 
 // ---------------------------------------------------------------- model upload
 static copse_status upload_model(copse_ctx *c, copse_model *m, cudaStream_t s) {
-    if (m->dev && m->dev->ctx == c) return COPSE_OK;
+    if (m->dev && m->dev->ctx_serial == c->serial) return COPSE_OK;
     const CompiledForest &f = m->f;
     if ((int)f.log_n != c->logN) { set_error("model compiled for another ring degree"); return COPSE_EINVAL; }
     if ((uint32_t)c->L <= f.levels_used()) {
@@ -60,6 +61,7 @@ static copse_status upload_model(copse_ctx *c, copse_model *m, cudaStream_t s) {
     }
     auto D = std::make_unique<DeviceModel>();
     D->ctx = c;
+    D->ctx_serial = c->serial;
     const int N = c->N, L = c->L, A = c->alpha, p = (int)f.precision, B = (int)f.block;
     D->lvl_D = L - 1 - (int)clog2u(f.precision);
     D->lvl_B = D->lvl_D - 1;

@@ -1,5 +1,6 @@
 // Context: prime chain, NTT twiddle tables, slot index table, base-conversion
 // constants, error reporting and the device memory pool.
+#include <atomic>
 #include <algorithm>
 #include <cstring>
 
@@ -254,6 +255,8 @@ extern "C" copse_status copse_ctx_create(const copse_params *pp, int device, cop
         return COPSE_EINVAL;
     }
     copse_ctx *c = new copse_ctx();
+    static std::atomic<uint64_t> next_serial{1};
+    c->serial = next_serial++;
     c->device = device;
     c->logN = (int)pp->log_n;
     c->N = 1 << c->logN;

@@ -142,6 +142,7 @@ struct KsTables {
 };
 
 struct copse_ctx {
+    uint64_t serial = 0;              // unique per context made in this process
     int device = 0;
     int logN = 0, N = 0;
     u64 t = COPSE_T;
@@ -167,6 +168,8 @@ struct copse_ctx {
     // one-launch cluster NTT for 2^12 <= N <= 2^14 (environment COPSE_NTT_CLUSTERS=0 selects the
     // two-launch form)
     bool ntt_clusters = true;
+    // batches of more residue polynomials than this take the two-launch form (autotuned)
+    long ntt_cluster_max = 1L << 30;
 
     int ext_prime(int ell, int r) const { return r < ell ? r : L + (r - ell); }
     int t_index() const { return L + alpha; }
@@ -213,7 +216,8 @@ struct NttBatch {
     int r0, nr;
     int ell;
     int fixed;
-    int skip_alpha = 0;  // > 0: poly p skips residues [p*skip_alpha, min((p+1)*skip_alpha, ell))
+    int skip_alpha = 0;  // > 0: poly p skips residues [j*skip_alpha, min((j+1)*skip_alpha, ell)),
+    int skip_period = 0; //      j = p (skip_period = 0) or p mod skip_period (digits of several inputs)
 };
 copse_status ntt_forward(copse_ctx *ctx, const NttBatch &b, cudaStream_t s);
 copse_status ntt_inverse(copse_ctx *ctx, const NttBatch &b, cudaStream_t s);
@@ -260,22 +264,22 @@ copse_status op_rotate(copse_ctx *c, const copse_evk *evk, const DCt &a, uint32_
 // with R_k the rotation by rots[k] before its ModDown (one ModUp of v serves all k)
 // and k0 the zero rotation if present.  pt[a][k] may be null (zero diagonal);
 // pt pointers are NTT-domain [v.level + alpha][N] (extended basis), add[a] [v.level][N].
-// raw = true: out[a] = ModDown(...) + pt[a][k0] * v only (no add, no modswitch).
+// raw_out set: the sums ModDown(...) + pt[a][k0] * v go to raw_out [nacc][2][v.level][N]
+// (no add, no modswitch) and `out` stays empty.
 copse_status op_matmul(copse_ctx *c, const copse_evk *evk, const DCt &v, const std::vector<uint32_t> &rots,
                        const std::vector<std::vector<const u64 *>> &pt, const std::vector<const u64 *> &add,
-                       std::vector<DCt> &out, cudaStream_t s, bool raw = false);
+                       std::vector<DCt> &out, cudaStream_t s, u64 *raw_out = nullptr);
 // Baby-step / giant-step products: the baby-step sums of every accumulator
 // (matrix acc_mat[x], giant step acc_giant[x]) share the rotations of v by the
 // baby amounts (op_matmul, raw); then for each matrix a
-//   out[a] = modswitch(rotsum_k(inner[a, k], k) + add[a]).
+//   out[a] = modswitch(ModDown(sum_{k != 0} R_k(inner[a, k])) + inner[a, 0] + add[a]),
+// R_k the rotation by k before its ModDown; accumulators of one matrix are
+// contiguous with giant steps ascending.
 copse_status op_matmul_bsgs(copse_ctx *c, const copse_evk *evk, const DCt &v, const std::vector<uint32_t> &baby,
                             const std::vector<std::vector<const u64 *>> &pt, const std::vector<int> &acc_mat,
                             const std::vector<uint32_t> &acc_giant, int n_mat, const std::vector<const u64 *> &add,
                             std::vector<DCt> &out, cudaStream_t s);
-// sum_k rot(terms[k], amounts[k]) with one ModDown for all rotated terms (amount 0:
-// added as is), plus add (a [level][N] plaintext or null), then one modulus switch.
-copse_status op_rotsum(copse_ctx *c, const copse_evk *evk, const std::vector<DCt> &terms,
-                       const std::vector<uint32_t> &amounts, const u64 *add, DCt *out, cudaStream_t s);
+
 // encode host slot patterns: n patterns of `len` values mod t, repeated every
 // `period` slots (period divides N; len <= period), into NTT-domain plaintexts
 // [n][level + ext_alpha][N] over q_0..q_{level-1} and, when ext_alpha > 0, the

@@ -36,7 +36,8 @@ __device__ __forceinline__ int ntt_prime(const NttBatch &b, int r, int L) {
 
 // residue r of poly p is excluded from this batch (a ModUp digit's own primes)
 __device__ __forceinline__ bool ntt_skipped(const NttBatch &b, int p, int r) {
-    return b.skip_alpha > 0 && r >= p * b.skip_alpha && r < min((p + 1) * b.skip_alpha, b.ell);
+    const int j = b.skip_period > 0 ? p % b.skip_period : p;
+    return b.skip_alpha > 0 && r >= j * b.skip_alpha && r < min((j + 1) * b.skip_alpha, b.ell);
 }
 
 // forward butterfly, values in [0, 4q)
@@ -483,7 +484,7 @@ copse_status launch(copse_ctx *ctx, const NttBatch &b, cudaStream_t s, bool inve
     if (b.npoly <= 0 || b.nr <= 0) return COPSE_OK;
     const int N = ctx->N, logN = ctx->logN;
     const double bytes = (double)b.npoly * b.nr * N * 16.0;  // one read and one write of each residue polynomial
-    if (ctx->ntt_clusters) {
+    if (ctx->ntt_clusters && (long)b.npoly * b.nr <= ctx->ntt_cluster_max) {
         if (logN == 12) return launch_cluster<2>(ctx, b, s, inverse, bytes);
         if (logN == 13) return launch_cluster<4>(ctx, b, s, inverse, bytes);
         if (logN == 14) return launch_cluster<8>(ctx, b, s, inverse, bytes);

@@ -94,8 +94,9 @@ __global__ void k_permute(const u64 *src, u64 *dst, int nres, u64 g, int logN) {
 
 // ModUp of every digit: x [ell][N] coefficient form -> y [nd][ell+alpha][N] coefficient form, except the
 // digit's own primes, which are copied from x_ntt (the same residues in NTT form)
-__global__ void k_modup(const u64 *x, const u64 *x_ntt, u64 *y, int ell, int alpha, int L, int NP, int logN, const PrimeDev *pr,
-                        KsTables T) {
+// blockIdx.y = input item: x [item][ell][N] contiguous, x_ntt at item * xs, y [item][nd][nx][N]
+__global__ void k_modup(const u64 *x, const u64 *x_ntt, size_t xs, u64 *y, int ell, int alpha, int L, int NP,
+                        int logN, const PrimeDev *pr, KsTables T) {
     const int N = 1 << logN;
     const int nd = (ell + alpha - 1) / alpha;
     size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -103,6 +104,9 @@ __global__ void k_modup(const u64 *x, const u64 *x_ntt, u64 *y, int ell, int alp
     const int j = (int)(e >> logN), n = (int)(e & (N - 1));
     const int lo = j * alpha, hi = min((j + 1) * alpha, ell);
     const int nx = ell + alpha;
+    x += (size_t)blockIdx.y * ((size_t)ell << logN);
+    x_ntt += (size_t)blockIdx.y * xs;
+    y += (size_t)blockIdx.y * nd * ((size_t)nx << logN);
     u64 yv[MAX_ALPHA];
     bool neg[MAX_ALPHA];
     for (int i = lo; i < hi; i++) {
@@ -592,11 +596,34 @@ copse_status ks_modup(copse_ctx *c, const u64 *x_ntt, int ell, Scratch &sc, u64 
     STATUS_TRY(sc.get(c, &y, (size_t)nd * nx * N));
     CUDA_TRY(cudaMemcpyAsync(xc, x_ntt, (size_t)ell * N * sizeof(u64), cudaMemcpyDeviceToDevice, s));
     STATUS_TRY(ntt_inverse(c, batch(xc, (size_t)ell * N, 1, 0, ell, ell), s));
-    TIMED("modup", 8.0 * N * ((double)ell + (double)nd * nx), s, k_modup<<<nblk((size_t)nd * N), TPB, 0, s>>>(xc, x_ntt, y, ell, A, c->L, c->NP, c->logN, c->d_prime, c->ks));
+    TIMED("modup", 8.0 * N * ((double)ell + (double)nd * nx), s, k_modup<<<nblk((size_t)nd * N), TPB, 0, s>>>(xc, x_ntt, 0, y, ell, A, c->L, c->NP, c->logN, c->d_prime, c->ks));
     LAUNCH_CHECK();
     // the digit's own primes already hold the input's NTT values: skip them
     NttBatch nb = batch(y, (size_t)nx * N, nd, 0, nx, ell);
     nb.skip_alpha = A;
+    STATUS_TRY(ntt_forward(c, nb, s));
+    *yhat = y;
+    return COPSE_OK;
+}
+
+// ModUp of n inputs x_ntt + i * xs (NTT domain [ell][N] each) in one pass of
+// launches; result NTT domain [n][nd][ell+alpha][N]
+copse_status ks_modup_batch(copse_ctx *c, const u64 *x_ntt, size_t xs, int n, int ell, Scratch &sc, u64 **yhat,
+                            cudaStream_t s) {
+    const int N = c->N, A = c->alpha, nx = ell + A, nd = (ell + A - 1) / A;
+    u64 *xc = nullptr, *y = nullptr;
+    STATUS_TRY(sc.get(c, &xc, (size_t)n * ell * N));
+    STATUS_TRY(sc.get(c, &y, (size_t)n * nd * nx * N));
+    CUDA_TRY(cudaMemcpy2DAsync(xc, (size_t)ell * N * sizeof(u64), x_ntt, xs * sizeof(u64), (size_t)ell * N * sizeof(u64),
+                               n, cudaMemcpyDeviceToDevice, s));
+    STATUS_TRY(ntt_inverse(c, batch(xc, (size_t)ell * N, n, 0, ell, ell), s));
+    TIMED("modup", 8.0 * N * n * ((double)ell + (double)nd * nx), s,
+          k_modup<<<dim3(nblk((size_t)nd * N), n), TPB, 0, s>>>(xc, x_ntt, xs, y, ell, A, c->L, c->NP, c->logN,
+                                                                 c->d_prime, c->ks));
+    LAUNCH_CHECK();
+    NttBatch nb = batch(y, (size_t)nx * N, n * nd, 0, nx, ell);
+    nb.skip_alpha = A;
+    nb.skip_period = nd;
     STATUS_TRY(ntt_forward(c, nb, s));
     *yhat = y;
     return COPSE_OK;
@@ -777,9 +804,28 @@ copse_status op_rotate(copse_ctx *c, const copse_evk *evk, const DCt &a, uint32_
     return COPSE_OK;
 }
 
+// ModDown of n extended-basis ciphertexts acc [n][2][ell+alpha][N] (NTT domain; the
+// special-prime residues are transformed in place) into res [n][2][ell][N]; W scratch
+// of res's size.
+static copse_status moddown_batch(copse_ctx *c, u64 *acc, int n, int ell, u64 *W, u64 *res, cudaStream_t s) {
+    const int N = c->N, A = c->alpha, nx = ell + A;
+    const size_t per = (size_t)2 * ell * N;
+    STATUS_TRY(ntt_inverse(c, batch(acc, (size_t)nx * N, 2 * n, ell, A, ell), s));
+    TIMED("moddown_conv", 8.0 * N * 2.0 * n * ((double)A + ell), s,
+          k_moddown_conv<<<nblk((size_t)2 * n * N), TPB, 0, s>>>(acc, (size_t)nx * N, W, (size_t)ell * N, 2 * n, ell,
+                                                                 A, c->L, c->logN, c->d_prime, c->ks));
+    LAUNCH_CHECK();
+    STATUS_TRY(ntt_forward(c, batch(W, (size_t)ell * N, 2 * n, 0, ell, ell), s));
+    TIMED("md_finish", 8.0 * N * 3.0 * 2 * n * ell, s,
+          k_md_finish<<<nblk((size_t)n * per), TPB, 0, s>>>(acc, (size_t)nx * N, W, res, 2 * n, ell, c->logN,
+                                                            c->d_prime, c->ks));
+    LAUNCH_CHECK();
+    return COPSE_OK;
+}
+
 copse_status op_matmul(copse_ctx *c, const copse_evk *evk, const DCt &v, const std::vector<uint32_t> &rots,
                        const std::vector<std::vector<const u64 *>> &pt, const std::vector<const u64 *> &add,
-                       std::vector<DCt> &out, cudaStream_t s, bool raw) {
+                       std::vector<DCt> &out, cudaStream_t s, u64 *raw_out) {
     const int ell = v.level, N = c->N, A = c->alpha, nx = ell + A, nacc = (int)pt.size(), nrot = (int)rots.size();
     const size_t ext = (size_t)2 * nx * N, per = (size_t)2 * ell * N;
     Scratch sc(s);
@@ -794,8 +840,8 @@ copse_status op_matmul(copse_ctx *c, const copse_evk *evk, const DCt &v, const s
         if (used) ks_idx.push_back(r);
     }
     // extended-basis accumulators [nacc][2][ell+alpha][N] and the Q-basis results [nacc][2][ell][N]
-    u64 *acc = nullptr, *res = nullptr, *W = nullptr;
-    STATUS_TRY(sc.get(c, &res, (size_t)nacc * per));
+    u64 *acc = nullptr, *res = raw_out, *W = nullptr;
+    if (!res) STATUS_TRY(sc.get(c, &res, (size_t)nacc * per));
     CUDA_TRY(cudaMemsetAsync(res, 0, (size_t)nacc * per * sizeof(u64), s));
     if (!ks_idx.empty()) {
         // rotations of a chunk are split into `parts` ranges with their own partial sums
@@ -842,19 +888,9 @@ copse_status op_matmul(copse_ctx *c, const copse_evk *evk, const DCt &v, const s
                                                             c->L, c->logN, c->d_prime));
         LAUNCH_CHECK();
         // one ModDown per accumulator (both components)
-        STATUS_TRY(ntt_inverse(c, batch(acc, (size_t)nx * N, 2 * nacc, ell, A, ell), s));
-        TIMED("moddown_conv", 8.0 * N * 2.0 * nacc * ((double)A + ell), s,
-              k_moddown_conv<<<nblk((size_t)2 * nacc * N), TPB, 0, s>>>(acc, (size_t)nx * N, W, (size_t)ell * N,
-                                                                        2 * nacc, ell, A, c->L, c->logN, c->d_prime,
-                                                                        c->ks));
-        LAUNCH_CHECK();
-        STATUS_TRY(ntt_forward(c, batch(W, (size_t)ell * N, 2 * nacc, 0, ell, ell), s));
-        TIMED("md_finish", 8.0 * N * 3.0 * 2 * nacc * ell, s,
-              k_md_finish<<<nblk((size_t)nacc * per), TPB, 0, s>>>(acc, (size_t)nx * N, W, res, 2 * nacc, ell,
-                                                                   c->logN, c->d_prime, c->ks));
-        LAUNCH_CHECK();
+        STATUS_TRY(moddown_batch(c, acc, nacc, ell, W, res, s));
     }
-    out.assign(nacc, DCt());
+    out.assign(raw_out ? 0 : nacc, DCt());
     for (int a = 0; a < nacc; a++) {
         u64 *ra = res + (size_t)a * per;
         for (int r = 0; r < nrot; r++) {
@@ -863,13 +899,7 @@ copse_status op_matmul(copse_ctx *c, const copse_evk *evk, const DCt &v, const s
                   k_ident_mac<<<nblk(per), TPB, 0, s>>>(ra, v.data, pt[a][r], ell, c->logN, c->d_prime));
             LAUNCH_CHECK();
         }
-        if (raw) {
-            DCt tmp;
-            tmp.level = ell;
-            tmp.data = ra;
-            STATUS_TRY(ct_copy(c, tmp, &out[a], s));
-            continue;
-        }
+        if (raw_out) continue;
         if (add.size() > (size_t)a && add[a]) {
             k_add_plain<<<nblk((size_t)ell * N), TPB, 0, s>>>(ra, add[a], ell, c->logN, c->d_prime);
             LAUNCH_CHECK();
@@ -883,94 +913,80 @@ copse_status op_matmul(copse_ctx *c, const copse_evk *evk, const DCt &v, const s
     return COPSE_OK;
 }
 
-copse_status op_rotsum(copse_ctx *c, const copse_evk *evk, const std::vector<DCt> &terms,
-                       const std::vector<uint32_t> &amounts, const u64 *add, DCt *out, cudaStream_t s) {
-    if (terms.empty() || terms.size() != amounts.size()) { set_error("internal: bad rotation sum"); return COPSE_EINVAL; }
-    const int ell = terms[0].level, N = c->N, A = c->alpha, nx = ell + A;
-    const size_t per = (size_t)2 * ell * N, ext = (size_t)2 * nx * N;
-    std::vector<int> rot;
-    std::vector<u64> gal(terms.size());
-    for (size_t k = 0; k < terms.size(); k++) {
-        if (terms[k].level != ell) { set_error("internal: rotation sum over mixed levels"); return COPSE_EINVAL; }
-        gal[k] = galois_of_rotation(c, amounts[k]);
-        if (gal[k] == 1) continue;
-        if (!evk->find(gal[k])) { set_error("no rotation key for amount " + std::to_string(amounts[k])); return COPSE_ENOKEY; }
-        rot.push_back((int)k);
-    }
-    Scratch sc(s);
-    u64 *res = nullptr;
-    STATUS_TRY(sc.get(c, &res, per));
-    if (rot.empty()) {
-        CUDA_TRY(cudaMemsetAsync(res, 0, per * sizeof(u64), s));
-    } else {
-        u64 *acc = nullptr, *W = nullptr;
-        STATUS_TRY(sc.get(c, &acc, ext));
-        STATUS_TRY(sc.get(c, &W, per));
-        CUDA_TRY(cudaMemsetAsync(acc, 0, ext * sizeof(u64), s));
-        const int nd = (ell + A - 1) / A;
-        for (size_t k0 = 0; k0 < rot.size(); k0 += RS_CHUNK) {
-            const int nt = (int)std::min<size_t>(RS_CHUNK, rot.size() - k0);
-            Scratch sk(s);  // the chunk's ModUp digits, freed (stream-ordered) after its launch
-            RsTable tab;
-            memset(&tab, 0, sizeof(tab));
-            for (int x = 0; x < nt; x++) {
-                const DCt &ct = terms[rot[k0 + x]];
-                u64 *yhat = nullptr;
-                STATUS_TRY(ks_modup(c, ct.data + (size_t)ell * N, ell, sk, &yhat, s));
-                tab.t[x] = RsTerm{yhat, ct.data, evk->find(gal[rot[k0 + x]]), gal[rot[k0 + x]]};
-            }
-            const double bytes = 8.0 * N * ((double)nt * (2.0 * nd * nx + (double)nd * nx + ell) + 4.0 * nx);
-            TIMED("rotsum", bytes, s,
-                  k_rotsum<<<nblk((size_t)nx * N), TPB, 0, s>>>(tab, nt, acc, ell, A, c->L, c->logN, c->d_prime,
-                                                                c->ks));
-            LAUNCH_CHECK();
-        }
-        STATUS_TRY(ntt_inverse(c, batch(acc, (size_t)nx * N, 2, ell, A, ell), s));
-        TIMED("moddown_conv", 8.0 * N * 2.0 * ((double)A + ell), s,
-              k_moddown_conv<<<nblk((size_t)2 * N), TPB, 0, s>>>(acc, (size_t)nx * N, W, (size_t)ell * N, 2, ell, A,
-                                                                 c->L, c->logN, c->d_prime, c->ks));
-        LAUNCH_CHECK();
-        STATUS_TRY(ntt_forward(c, batch(W, (size_t)ell * N, 2, 0, ell, ell), s));
-        TIMED("md_finish", 8.0 * N * 3.0 * 2 * ell, s,
-              k_md_finish<<<nblk(per), TPB, 0, s>>>(acc, (size_t)nx * N, W, res, 2, ell, c->logN, c->d_prime, c->ks));
-        LAUNCH_CHECK();
-    }
-    for (size_t k = 0; k < terms.size(); k++) {
-        if (gal[k] != 1) continue;
-        k_add<<<nblk(per), TPB, 0, s>>>(res, terms[k].data, res, 2, ell, c->logN, 0, c->d_prime);
-        LAUNCH_CHECK();
-    }
-    if (add) {
-        k_add_plain<<<nblk((size_t)ell * N), TPB, 0, s>>>(res, add, ell, c->logN, c->d_prime);
-        LAUNCH_CHECK();
-    }
-    DCt tmp;
-    tmp.level = ell;
-    tmp.data = res;
-    return op_modswitch(c, tmp, out, s);
-}
-
 copse_status op_matmul_bsgs(copse_ctx *c, const copse_evk *evk, const DCt &v, const std::vector<uint32_t> &baby,
                             const std::vector<std::vector<const u64 *>> &pt, const std::vector<int> &acc_mat,
                             const std::vector<uint32_t> &acc_giant, int n_mat, const std::vector<const u64 *> &add,
                             std::vector<DCt> &out, cudaStream_t s) {
-    std::vector<DCt> inner;
-    STATUS_TRY(op_matmul(c, evk, v, baby, pt, {}, inner, s, true));
-    out.assign(n_mat, DCt());
-    copse_status st = COPSE_OK;
-    for (int a = 0; a < n_mat && st == COPSE_OK; a++) {
-        std::vector<DCt> terms;
-        std::vector<uint32_t> amounts;
-        for (size_t x = 0; x < inner.size(); x++)
-            if (acc_mat[x] == a) {
-                terms.push_back(inner[x]);
-                amounts.push_back(acc_giant[x]);
-            }
-        const u64 *ad = add.size() > (size_t)a ? add[a] : nullptr;
-        st = op_rotsum(c, evk, terms, amounts, ad, &out[a], s);
+    const int ell = v.level, N = c->N, A = c->alpha, nx = ell + A, nd = (ell + A - 1) / A;
+    const int nacc = (int)pt.size();
+    const size_t per = (size_t)2 * ell * N, ext = (size_t)2 * nx * N;
+    std::vector<u64> gal(nacc);
+    for (int x = 0; x < nacc; x++) {
+        gal[x] = galois_of_rotation(c, acc_giant[x]);
+        if (gal[x] != 1 && !evk->find(gal[x])) {
+            set_error("no rotation key for amount " + std::to_string(acc_giant[x]));
+            return COPSE_ENOKEY;
+        }
     }
-    for (DCt &x : inner) ct_free(&x, s);
-    return st;
+    Scratch sc(s);
+    // baby steps: inner[x] = sum_j d'_{x,j} * rot(v, j), one ModDown each
+    u64 *inner = nullptr, *acc = nullptr, *W = nullptr, *res = nullptr;
+    STATUS_TRY(sc.get(c, &inner, (size_t)nacc * per));
+    std::vector<DCt> none;
+    STATUS_TRY(op_matmul(c, evk, v, baby, pt, {}, none, s, inner));
+    // giant steps: per matrix, the rotated accumulators key-switched into one
+    // extended-basis sum (the ModUps of a matrix's terms batched), one ModDown for all
+    STATUS_TRY(sc.get(c, &acc, (size_t)n_mat * ext));
+    STATUS_TRY(sc.get(c, &W, (size_t)n_mat * per));
+    STATUS_TRY(sc.get(c, &res, (size_t)n_mat * per));
+    CUDA_TRY(cudaMemsetAsync(acc, 0, (size_t)n_mat * ext * sizeof(u64), s));
+    for (int a = 0; a < n_mat; a++) {
+        int x0 = 0;
+        while (x0 < nacc && (acc_mat[x0] != a || gal[x0] == 1)) x0++;
+        int x1 = x0;
+        while (x1 < nacc && acc_mat[x1] == a && gal[x1] != 1) x1++;
+        if (x0 == x1) continue;
+        for (int x = x1; x < nacc; x++)
+            if (acc_mat[x] == a && gal[x] != 1) { set_error("internal: giant steps of a matrix not contiguous"); return COPSE_EINVAL; }
+        Scratch sk(s);  // this matrix's ModUp digits, freed (stream-ordered) after its launches
+        u64 *yhat = nullptr;
+        STATUS_TRY(ks_modup_batch(c, inner + (size_t)x0 * per + (size_t)ell * N, per, x1 - x0, ell, sk, &yhat, s));
+        for (int k0 = x0; k0 < x1; k0 += RS_CHUNK) {
+            const int nt = std::min(RS_CHUNK, x1 - k0);
+            RsTable tab;
+            memset(&tab, 0, sizeof(tab));
+            for (int i = 0; i < nt; i++) {
+                const int x = k0 + i;
+                tab.t[i] = RsTerm{yhat + (size_t)(x - x0) * nd * nx * N, inner + (size_t)x * per, evk->find(gal[x]),
+                                  gal[x]};
+            }
+            const double bytes = 8.0 * N * ((double)nt * (2.0 * nd * nx + (double)nd * nx + ell) + 4.0 * nx);
+            TIMED("rotsum", bytes, s,
+                  k_rotsum<<<nblk((size_t)nx * N), TPB, 0, s>>>(tab, nt, acc + (size_t)a * ext, ell, A, c->L,
+                                                                c->logN, c->d_prime, c->ks));
+            LAUNCH_CHECK();
+        }
+    }
+    STATUS_TRY(moddown_batch(c, acc, n_mat, ell, W, res, s));
+    // + the giant-step-0 sums, + add, then one modulus switch per matrix
+    out.assign(n_mat, DCt());
+    for (int a = 0; a < n_mat; a++) {
+        u64 *ra = res + (size_t)a * per;
+        for (int x = 0; x < nacc; x++)
+            if (acc_mat[x] == a && gal[x] == 1) {
+                k_add<<<nblk(per), TPB, 0, s>>>(ra, inner + (size_t)x * per, ra, 2, ell, c->logN, 0, c->d_prime);
+                LAUNCH_CHECK();
+            }
+        if (add.size() > (size_t)a && add[a]) {
+            k_add_plain<<<nblk((size_t)ell * N), TPB, 0, s>>>(ra, add[a], ell, c->logN, c->d_prime);
+            LAUNCH_CHECK();
+        }
+        DCt tmp;
+        tmp.level = ell;
+        tmp.data = ra;
+        STATUS_TRY(op_modswitch(c, tmp, &out[a], s));
+    }
+    return COPSE_OK;
 }
 
 copse_status encode_patterns(copse_ctx *c, const std::vector<uint32_t> &patterns, int n, int len, int period,

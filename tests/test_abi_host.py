@@ -86,3 +86,13 @@ def test_block_must_fit_a_row():
     with pytest.raises(K.CopseError) as e:
         K.copse_compile_forest(text, 8, 8, 8)   # N = 256: a row has 128 slots
     assert e.value.name == "EFIT"
+
+
+def test_tuning_calls_marshal_and_reject_null_handles():
+    """The autotuning entry points check their handles before any device work."""
+    for call in (lambda: K.copse_tune_ntt(None),
+                 lambda: K.copse_tune_bsgs(None, None, [0, 8], [0, 4]),
+                 lambda: K.copse_tune_dnum(10, 50, 4, None, [1, 2])):
+        with pytest.raises(K.CopseError) as e:
+            call()
+        assert e.value.name == "EINVAL"
