@@ -91,6 +91,7 @@ def lib():
             "or_matmul": (None, [P, u64p, C.c_int, C.c_int, u64p, C.POINTER(C.c_void_p), C.c_int, i64p,
                                  np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS"), u64p]),
             "or_rotsum": (None, [P, C.POINTER(C.c_void_p), C.c_int, C.c_int, u64p, C.POINTER(C.c_void_p), u64p]),
+            "or_encrypt_sk": (None, [P, i64p, i64p, C.c_uint64, C.c_uint64, C.c_int, u64p]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -117,6 +118,11 @@ def stream_galois(g: int) -> int:
 def stream_encrypt(index: int) -> int:
     """Stream base (u, e0, e1) of the index-th encryption under one seed."""
     return 0x1000000 + 3 * index
+
+
+def stream_model(index: int) -> int:
+    """Stream base (a, e) of the index-th secret-key encryption of an encrypted model."""
+    return 0x40000000 + 2 * index
 
 
 # ---------------------------------------------------------------------------
@@ -254,6 +260,14 @@ class Bgv:
         ct = np.zeros((2, P.L, P.N), dtype=np.uint64)
         self.L.or_encrypt(P.c, pk, np.ascontiguousarray(m_centred, dtype=np.int64), seed,
                           stream_encrypt(index), ct)
+        return ct
+
+    def encrypt_sk(self, sk, m_centred, seed: int, index: int, ell: int) -> np.ndarray:
+        """Secret-key encryption at level ell with a seeded mask (see or_encrypt_sk)."""
+        P = self.P
+        ct = np.zeros((2, ell, P.N), dtype=np.uint64)
+        self.L.or_encrypt_sk(P.c, np.ascontiguousarray(sk, dtype=np.int64),
+                             np.ascontiguousarray(m_centred, dtype=np.int64), seed, stream_model(index), ell, ct)
         return ct
 
     def encrypt_slots(self, pk, slots, seed: int, index: int) -> np.ndarray:

@@ -407,6 +407,33 @@ void or_encrypt(const or_params *P, const u64 *pk, const i64 *m, u64 seed, u64 s
     free(u); free(e0); free(e1); free(ur); free(p0u); free(p1u);
 }
 
+/* Secret-key encryption at level ell (the model owner holds the secret key
+ * when the model is encrypted, Section 8.3 "Maurice = Diane"), with a seeded
+ * mask: the evaluations of a at psi_r^(2j+1), j = 0..N-1 in natural order,
+ * are uniform residues from stream sb (so a can be regenerated from the seed
+ * in evaluation form); e centred binomial from stream sb+1;
+ *   c1 = a,  c0 = -a*s + t*e + m.   ct layout [2][ell][N], coefficient form. */
+void or_encrypt_sk(const or_params *P, const i64 *s, const i64 *m, u64 seed, u64 sb, int ell, u64 *ct)
+{
+    int N = P->N;
+    i64 *e = malloc(sizeof(i64) * N);
+    u64 *a = malloc(sizeof(u64) * N), *sr = malloc(sizeof(u64) * N), *as = malloc(sizeof(u64) * N);
+    or_sample_cbd(seed, sb + 1, N, e);
+    for (int r = 0; r < ell; r++) {
+        u64 q = P->primes[r], tq = P->t % q;
+        for (int j = 0; j < N; j++) a[j] = uniform_residue(seed, sb, N, r, j, q);
+        or_ntt_inv(a, P->logN, q, or_root_2n(q, P->logN));
+        for (int j = 0; j < N; j++) sr[j] = from_signed(s[j], q);
+        or_negacyclic_mul(a, sr, P->logN, q, as);
+        for (int j = 0; j < N; j++) {
+            u64 v = addmod(mulmod(tq, from_signed(e[j], q), q), from_signed(m[j], q), q);
+            ct[(size_t)r * N + j] = submod(v, as[j], q);
+            ct[(size_t)(ell + r) * N + j] = a[j];
+        }
+    }
+    free(e); free(a); free(sr); free(as);
+}
+
 /* [c0 + c1*s] mod q_r for r < ell (no reduction mod t): used for noise measurement */
 void or_decrypt_raw(const or_params *P, const i64 *s, const u64 *ct, int ell, u64 *x)
 {

@@ -385,10 +385,93 @@ def infer(E, m: Model, X, N: int, g=(0, 0)):
     t = E.t
     Y = E.thresholds(m)
     D = seccomp(E, X, Y, m.precision)
+    if E.encrypted_model:
+        em = E.enc_model
+        Br = matmul_enc(E, D, [em["R"]], [None], em["g"][0])[0]
+        res = matmul_enc(E, Br, em["levels"], em["masks"], em["g"][1])
+        return pairwise(res, lambda a, b, root: E.mul(a, b))
     Br = matmul(E, D, [reshuffle_diagonals(m)], [None], m, N, g[0])[0]
     Ld = [level_diagonals(m, k, t) for k in range(1, m.d + 1)]
     res = matmul(E, Br, Ld, [tile_blocks(m, m.mask[k - 1], N) for k in range(1, m.d + 1)], m, N, g[1])
     return pairwise(res, lambda a, b, root: E.mul(a, b))
+
+
+# ---------------------------------------------------------------------------
+# Encrypted model (Section 3.1 with Maurice = Diane; Section 8.3): the model
+# owner encrypts the threshold planes, every diagonal of the reshuffle and
+# level matrices (zero ones included, so their number p + q + d(b+1) of
+# Table 1d reveals only the sizes) and the masks, and the products become
+# ciphertext x ciphertext.
+# ---------------------------------------------------------------------------
+def model_ct_index(m: Model, kind: str, k: int = 0, i: int = 0) -> int:
+    """Canonical numbering of the encrypted model's ciphertexts: threshold planes,
+    reshuffle diagonals, level k diagonals (k = 1..d), masks."""
+    if kind == "thr":
+        return i
+    if kind == "R":
+        return m.precision + i
+    if kind == "lvl":
+        return m.precision + m.q + (k - 1) * m.b + i
+    return m.precision + m.q + m.d * m.b + (k - 1)
+
+
+def _clog2(x):
+    return (x - 1).bit_length() if x > 1 else 0
+
+
+def encrypt_model(bgv: B.Bgv, sk, m: Model, N: int, seed: int, g=(0, 0)):
+    """Every ciphertext of the encrypted model, under the secret key with seeded
+    masks (Bgv.encrypt_sk), each at the level where the circuit uses it:
+    thresholds at L, reshuffle diagonals at the level of Decisions, level
+    diagonals and masks at the level of Branches.  With a baby-step size g the
+    diagonal i is stored shifted by its giant step (bsgs_split)."""
+    P = bgv.P
+    lvl_D = P.L - 1 - _clog2(m.precision)
+    lvl_B = lvl_D - 1
+
+    def enc(vec, idx, ell):
+        return bgv.encrypt_sk(sk, B.encode(P, vec % P.t), seed, idx, ell)
+
+    def shifted(d, i, gg):
+        kg = i - i % gg if gg else 0
+        v = np.zeros(kg + len(d), dtype=np.int64)
+        v[kg:] = d
+        return v
+
+    thr = [enc(y, model_ct_index(m, "thr", i=i), P.L) for i, y in enumerate(threshold_planes(m, N))]
+    R = {i: enc(tile_blocks(m, shifted(generalized_diagonal(m.R, i, m.m1), i, g[0]), N),
+                model_ct_index(m, "R", i=i), lvl_D) for i in range(m.q)}
+    levels, masks = [], []
+    for k in range(1, m.d + 1):
+        sgn = 1 - 2 * m.mask[k - 1]
+        levels.append({i: enc(tile_blocks(m, shifted((sgn * generalized_diagonal(m.lvl[k - 1], i, m.L)) % P.t,
+                                                     i, g[1]), N), model_ct_index(m, "lvl", k, i), lvl_B)
+                       for i in range(m.b)})
+        masks.append(enc(tile_blocks(m, m.mask[k - 1], N), model_ct_index(m, "mask", k), lvl_B))
+    return {"thresholds": thr, "R": R, "levels": levels, "masks": masks, "g": tuple(g)}
+
+
+def encrypted_rotation_sets(m: Model, g=(0, 0)):
+    """Rotation amounts of the encrypted-model products: every diagonal index is present."""
+    def amounts(n, gg):
+        if not gg:
+            return set(range(1, n))
+        return set(i % gg for i in range(n)) - {0} | set(i - i % gg for i in range(n)) - {0}
+    return sorted(amounts(m.q, g[0])), sorted(amounts(m.b, g[1]))
+
+
+def matmul_enc(E, v, enc_sets, add_cts, g: int = 0):
+    """MatMul with encrypted diagonals: for each matrix, per giant step k g the sum
+    over baby steps j of Enc(d'_{k,j}) x rot(v, j) as 3-component tensors,
+    relinearised once (lazy relinearisation); the giant steps rotated and summed
+    (E.rot_sum); plus the encrypted mask; then one modulus switch."""
+    sums = E.enc_diag_sums(v, enc_sets, g)
+    out = []
+    for acc, add in zip(sums, add_cts):
+        if add is not None:
+            acc = E.add(acc, add)
+        out.append(E.rescale(acc))
+    return out
 
 
 class SlotEngine:
@@ -467,7 +550,7 @@ class BgvEngine:
         return threshold_planes(m, self.N)
 
     def rot(self, v, i):
-        """One rotation with its own modulus-down step (used to time single operations)."""
+        """One rotation with its own modulus-down step (equal, bit for bit, to a hoisted one)."""
         if i == 0:
             return v
         g = B.galois_rot(self.P.logN, i)
@@ -481,6 +564,29 @@ class BgvEngine:
         self.counts["rot"] += sum(1 for i in rots if i)
         self.counts["mul_plain"] += sum(len(d) for d in diag_sets)
         return self.b.matmul(v, galois, gks, pts)
+
+    def enc_diag_sums(self, v, enc_sets, g):
+        """Per matrix {diagonal index: ciphertext}: baby rotations of v shared by every
+        matrix (each with its own key switch, identical to hoisting), per giant step
+        the tensor products summed and relinearised once, then the giant-step sum."""
+        babies = sorted(set((i % g if g else i) for es in enc_sets for i in es))
+        R = {j: self.rot(v, j) for j in babies}
+        self.counts["rot"] += sum(1 for j in babies if j)
+        out = []
+        for es in enc_sets:
+            groups = {}
+            for i in sorted(es):
+                groups.setdefault(i - i % g if g else 0, []).append((i % g if g else i, es[i]))
+            terms = []
+            for kg in sorted(groups):
+                acc = None
+                for j, d in groups[kg]:
+                    t3 = self.b.tensor(d, R[j])
+                    acc = t3 if acc is None else self.b.add(acc, t3)
+                self.counts["mul"] += len(groups[kg])
+                terms.append((kg, self.b.relin(acc, self.k.rlk)))
+            out.append(self.rot_sum(terms))
+        return out
 
     def rot_sum(self, terms):
         """Giant steps: sum_k rot(c_k, k) with one modulus-down step (Bgv.rotsum)."""
