@@ -102,7 +102,12 @@ def lib():
 
 
 # ---------------------------------------------------------------------------
-# Randomness streams (the counter-based SplitMix64 layout both sides follow)
+# Randomness streams (the counter-based SplitMix64 layout both sides follow).
+# word(seed, stream, idx) is output number stream * 2^40 + idx + 1, so every
+# stream id stays below 2^24 (the product never wraps past 2^64 and no two
+# streams share words): secret 1, public key 2-3, relinearisation key from 16,
+# rotation keys from 0x10000 (64 per odd Galois element, < 0x410000),
+# encryptions from 0x500000, encrypted-model ciphertexts from 0x800000.
 # ---------------------------------------------------------------------------
 STREAM_SECRET = 1
 STREAM_PK_A = 2
@@ -117,12 +122,14 @@ def stream_galois(g: int) -> int:
 
 def stream_encrypt(index: int) -> int:
     """Stream base (u, e0, e1) of the index-th encryption under one seed."""
-    return 0x1000000 + 3 * index
+    assert 0 <= index < 0x100000
+    return 0x500000 + 3 * index
 
 
 def stream_model(index: int) -> int:
     """Stream base (a, e) of the index-th secret-key encryption of an encrypted model."""
-    return 0x40000000 + 2 * index
+    assert 0 <= index < 0x400000
+    return 0x800000 + 2 * index
 
 
 # ---------------------------------------------------------------------------

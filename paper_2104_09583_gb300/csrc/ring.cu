@@ -508,7 +508,7 @@ __global__ void k_enc_prep(const u64 *mt, int p, u64 seed_val, const u64 *seed_p
     const u64 seed = seed_ptr ? *seed_ptr + seed_val : seed_val;
     const int i = (int)(e >> logN);
     const u64 n = e & ((1ull << logN) - 1);
-    const u64 sb = 0x1000000ull + 3ull * (u64)i;
+    const u64 sb = 0x500000ull + 3ull * (u64)i;  // every stream id stays below 2^24: stream * 2^40 + idx never wraps
     const i64 u = sample_small(seed, sb, n, 0);
     const i64 e0 = sample_small(seed, sb + 1, n, 1), e1 = sample_small(seed, sb + 2, n, 1);
     const u64 c = mt[e];

@@ -185,3 +185,17 @@ def test_samplers_distributions():
     # distinct streams and seeds give distinct words
     L = B.lib()
     assert L.or_word(1, 2, 3) != L.or_word(1, 3, 3) != L.or_word(2, 2, 3)
+
+
+def test_stream_layout_never_wraps():
+    """word(seed, stream, idx) = SplitMix64 output stream * 2^40 + idx + 1: every stream
+    the layout uses is below 2^24, so distinct (stream, idx) pairs never share an output."""
+    from oracle import bgv as B
+    used = [B.STREAM_SECRET, B.STREAM_PK_A, B.STREAM_PK_E, B.STREAM_RELIN + 79,
+            B.stream_galois(65535) + 79, B.stream_encrypt(0), B.stream_encrypt(0xFFFFF) + 2,
+            B.stream_model(0), B.stream_model(0x3FFFFF) + 1]
+    assert all(0 < s < (1 << 24) for s in used)
+    assert B.stream_galois(65535) + 79 < B.stream_encrypt(0)
+    assert B.stream_encrypt(0xFFFFF) + 2 < B.stream_model(0)
+    # the two families that collided under a wrapping layout now differ
+    assert B.lib().or_word(5, B.stream_encrypt(0) + 1, 0) != B.lib().or_word(5, B.STREAM_SECRET, 0)
