@@ -141,6 +141,30 @@ copse_status copse_model_rotations(const copse_model *model, uint32_t *reshuffle
 copse_status copse_model_set_bsgs(copse_model *model, uint32_t g_reshuffle, uint32_t g_level);
 copse_status copse_model_get_bsgs(const copse_model *model, uint32_t *g_reshuffle, uint32_t *g_level);
 
+/* Encrypted-model mode (Section 3.1's model owner Maurice is the data owner
+ * Diane, Section 8.3): the threshold planes, every diagonal of the reshuffle
+ * and level matrices, zero ones included, and the level masks are encrypted,
+ * p + q + d(b+1) ciphertexts (Table 1d), and the products of Algorithm 1
+ * become ciphertext x ciphertext (relinearised once per baby-step sum).
+ * copse_model_set_encrypted selects the mode before copse_keygen (the mode
+ * needs a rotation for every diagonal: use a baby-step plan for large models).
+ * copse_encrypt_model then encrypts the model under `keys`' secret key on ctx:
+ * secret-key encryptions at the levels of use whose masks c1 are drawn from
+ * `seed` in evaluation form, so only c0 is stored on the device (words:
+ * p L + q lvl_D + d (b+1) lvl_B times N) and c1 is regenerated where the
+ * products consume it.  copse_infer on the model then runs the encrypted
+ * circuit; EINVAL if the model has no encryption for that context or was
+ * encrypted for another baby-step plan.  Changing the mode or the plan drops
+ * the encryption. */
+copse_status copse_model_set_encrypted(copse_model *model, int on);
+copse_status copse_encrypt_model(copse_ctx *ctx, const copse_keys *keys, copse_model *model, uint64_t seed);
+
+/* Model ciphertext `index` (threshold planes, reshuffle diagonals, level
+ * diagonals level by level, masks) in coefficient form [2][level][N] into
+ * out[0..words), host memory, c1 regenerated.  For parity tests. */
+copse_status copse_encmodel_export(copse_ctx *ctx, const copse_model *model, size_t index, uint64_t *out,
+                                   size_t words);
+
 /* Plaintext classification (Section 2.1): one bit per leaf per query,
  * out_bits[n_queries * n_leaves]; feats[n_queries * n_features] on the host. */
 copse_status copse_classify_plain(const copse_model *model, const uint32_t *feats, size_t n_queries,

@@ -63,6 +63,9 @@ _SIG = {
     "copse_model_export": (C.c_int, [vp, vp, vp, vp, vp, vp, vp]),
     "copse_model_rotations": (C.c_int, [vp, vp, vp]),
     "copse_model_set_bsgs": (C.c_int, [vp, C.c_uint32, C.c_uint32]),
+    "copse_model_set_encrypted": (C.c_int, [vp, C.c_int]),
+    "copse_encrypt_model": (C.c_int, [vp, vp, vp, C.c_uint64]),
+    "copse_encmodel_export": (C.c_int, [vp, vp, C.c_size_t, u64p, C.c_size_t]),
     "copse_tune_ntt": (C.c_int, [vp, u32p, C.c_size_t, C.c_int, C.POINTER(C.c_float), C.POINTER(C.c_float),
                                  C.POINTER(C.c_uint32)]),
     "copse_tune_bsgs": (C.c_int, [vp, vp, u32p, C.c_size_t, u32p, C.c_size_t, C.c_size_t, C.c_int,
@@ -185,6 +188,21 @@ def copse_model_rotations(m):
 
 def copse_model_set_bsgs(m, g_reshuffle, g_level):
     _check(_lib.copse_model_set_bsgs(m, g_reshuffle, g_level))
+
+
+def copse_model_set_encrypted(m, on=True):
+    _check(_lib.copse_model_set_encrypted(m, 1 if on else 0))
+
+
+def copse_encrypt_model(ctx, keys, m, seed):
+    _check(_lib.copse_encrypt_model(ctx, keys, m, seed))
+
+
+def copse_encmodel_export(ctx, m, index, level, N):
+    """model ciphertext `index` in coefficient form, [2][level][N]"""
+    out = np.zeros(2 * level * N, dtype=np.uint64)
+    _check(_lib.copse_encmodel_export(ctx, m, index, out, out.size))
+    return out.reshape(2, level, N)
 
 
 def copse_model_get_bsgs(m):

@@ -47,6 +47,7 @@ struct DeviceModel {
 struct copse_model {
     CompiledForest f;
     std::unique_ptr<DeviceModel> dev;
+    std::unique_ptr<EncModel> enc;  // set by copse_encrypt_model
 };
 
 // ---------------------------------------------------------------- model upload
@@ -249,12 +250,58 @@ extern "C" copse_status copse_model_set_bsgs(copse_model *m, uint32_t g_reshuffl
     if (f.g_reshuffle != g_reshuffle || f.g_level != g_level) {
         f.g_reshuffle = g_reshuffle;
         f.g_level = g_level;
-        if (m->dev) {
+        if (m->dev || m->enc) {
             cudaDeviceSynchronize();
             m->dev.reset();
+            m->enc.reset();
         }
     }
     return COPSE_OK;
+}
+
+extern "C" copse_status copse_model_set_encrypted(copse_model *m, int on) {
+    if (!m) { set_error("null model"); return COPSE_EINVAL; }
+    if (m->f.encrypted != (on != 0)) {
+        m->f.encrypted = on != 0;
+        if (m->dev || m->enc) {
+            cudaDeviceSynchronize();
+            m->dev.reset();
+            m->enc.reset();
+        }
+    }
+    return COPSE_OK;
+}
+
+extern "C" copse_status copse_encrypt_model(copse_ctx *c, const copse_keys *k, copse_model *m, uint64_t seed) {
+    if (!c || !k || !m) { set_error("null argument"); return COPSE_EINVAL; }
+    const CompiledForest &f = m->f;
+    if (!f.encrypted) { set_error("model is not in encrypted mode (copse_model_set_encrypted)"); return COPSE_EINVAL; }
+    if ((int)f.log_n != c->logN) { set_error("model compiled for another ring degree"); return COPSE_EINVAL; }
+    if ((uint32_t)c->L <= f.levels_used()) {
+        set_error("prime chain of " + std::to_string(c->L) + " is too short: the circuit drops " +
+                  std::to_string(f.levels_used()) + " primes");
+        return COPSE_ELEVEL;
+    }
+    CUDA_TRY(cudaSetDevice(c->device));
+    auto E = std::make_unique<EncModel>();
+    STATUS_TRY(enc_model_build(c, k, f, seed, *E, 0));
+    m->enc = std::move(E);
+    return COPSE_OK;
+}
+
+extern "C" copse_status copse_encmodel_export(copse_ctx *c, const copse_model *m, size_t index, uint64_t *out,
+                                             size_t words) {
+    if (!c || !m || !out) { set_error("null argument"); return COPSE_EINVAL; }
+    if (!m->enc || m->enc->ctx_serial != c->serial) { set_error("model not encrypted on this context"); return COPSE_EINVAL; }
+    const EncModel &E = *m->enc;
+    if (index >= E.level.size()) { set_error("model ciphertext index out of range"); return COPSE_EINVAL; }
+    if (words < (size_t)2 * E.level[index] * c->N) { set_error("output buffer too small"); return COPSE_EINVAL; }
+    DCt ct;
+    STATUS_TRY(enc_materialize(c, E, (int)index, &ct, 0));
+    copse_status st = ct_to_coeff_host(c, ct, out, 0);
+    ct_free(&ct, 0);
+    CUDA_TRY(cudaStreamSynchronize(0));
+    return st;
 }
 
 extern "C" copse_status copse_model_get_bsgs(const copse_model *m, uint32_t *g_reshuffle, uint32_t *g_level) {
@@ -377,14 +424,26 @@ static copse_status group_matmul(copse_ctx *c, const copse_evk *evk, const DCt &
 
 static copse_status infer_impl(copse_ctx *c, const copse_evk *evk, copse_model *m, const copse_ctbuf *feats,
                                DCt *result, cudaStream_t s, int lane = 0, cudaEvent_t *stage_ev = nullptr) {
-    STATUS_TRY(upload_model(c, m, s));
+    const bool enc = m->f.encrypted;
+    if (enc) {
+        if (!m->enc || m->enc->ctx_serial != c->serial) {
+            set_error("encrypted-mode model has no encryption on this context (copse_encrypt_model)");
+            return COPSE_EINVAL;
+        }
+        if (m->enc->g_r != m->f.g_reshuffle || m->enc->g_l != m->f.g_level) {
+            set_error("model was encrypted for another baby-step plan");
+            return COPSE_EINVAL;
+        }
+    } else {
+        STATUS_TRY(upload_model(c, m, s));
+    }
     // stage boundaries (comparison | reshuffle | levels | aggregation), when timed
     auto mark = [&](int i) -> copse_status {
         if (stage_ev) CUDA_TRY(cudaEventRecord(stage_ev[i], s));
         return COPSE_OK;
     };
     STATUS_TRY(mark(0));
-    const DeviceModel &D = *m->dev;
+    const DeviceModel *D = m->dev.get();
     const CompiledForest &f = m->f;
     const int p = (int)f.precision;
     if ((int)feats->cts.size() != p) { set_error("feature buffer does not hold one ciphertext per bit-plane"); return COPSE_EINVAL; }
@@ -395,15 +454,37 @@ static copse_status infer_impl(copse_ctx *c, const copse_evk *evk, copse_model *
     // joined back onto s; every free happens on s after the join.
     // SecComp leaves, most significant plane first: lt = (1 - x) y, eq = [x == y]
     std::vector<Node> nodes(p);
-    STATUS_TRY(fork_begin(c, s, 2 * p, lane));
-    for (int k = 0; k < p; k++) {
-        const int i = p - 1 - k;
-        DPt lm{c->L, (u64 *)D.lt_mul[i]}, la{c->L, (u64 *)D.lt_add[i]};
-        DPt em{c->L, (u64 *)D.eq_mul[i]}, ea{c->L, (u64 *)D.eq_add[i]};
-        STATUS_TRY(op_affine(c, feats->cts[i], lm, &la, &nodes[k].lt, fork_stream(c, 2 * k, lane)));
-        STATUS_TRY(op_affine(c, feats->cts[i], em, &ea, &nodes[k].eq, fork_stream(c, 2 * k + 1, lane)));
+    if (!enc) {
+        // plaintext thresholds: both leaves are affine in x
+        STATUS_TRY(fork_begin(c, s, 2 * p, lane));
+        for (int k = 0; k < p; k++) {
+            const int i = p - 1 - k;
+            DPt lm{c->L, (u64 *)D->lt_mul[i]}, la{c->L, (u64 *)D->lt_add[i]};
+            DPt em{c->L, (u64 *)D->eq_mul[i]}, ea{c->L, (u64 *)D->eq_add[i]};
+            STATUS_TRY(op_affine(c, feats->cts[i], lm, &la, &nodes[k].lt, fork_stream(c, 2 * k, lane)));
+            STATUS_TRY(op_affine(c, feats->cts[i], em, &ea, &nodes[k].eq, fork_stream(c, 2 * k + 1, lane)));
+        }
+        STATUS_TRY(fork_join(c, s, 2 * p, lane));
+    } else {
+        // encrypted thresholds y: xy = x * y, lt = y - xy, eq = 2 xy - (x + y) + 1
+        std::vector<DCt> tmp(4 * (size_t)p);
+        STATUS_TRY(fork_begin(c, s, p, lane));
+        for (int k = 0; k < p; k++) {
+            const int i = p - 1 - k;
+            const cudaStream_t fs = fork_stream(c, k, lane);
+            DCt &Y = tmp[4 * k], &xy = tmp[4 * k + 1], &two = tmp[4 * k + 2], &sum = tmp[4 * k + 3];
+            STATUS_TRY(enc_materialize(c, *m->enc, m->enc->idx_thr(i), &Y, fs));
+            STATUS_TRY(op_mul(c, evk, feats->cts[i], Y, &xy, fs));
+            STATUS_TRY(op_add(c, Y, xy, &nodes[k].lt, true, fs));
+            STATUS_TRY(op_add(c, xy, xy, &two, false, fs));
+            STATUS_TRY(op_add(c, feats->cts[i], Y, &sum, false, fs));
+            STATUS_TRY(op_add(c, two, sum, &nodes[k].eq, true, fs));
+            STATUS_TRY(op_add_one(c, nodes[k].eq, fs));
+        }
+        STATUS_TRY(fork_join(c, s, p, lane));
+        for (DCt &x : tmp)
+            if (x.data) ct_free(&x, s);
     }
-    STATUS_TRY(fork_join(c, s, 2 * p, lane));
     // balanced combine (lt_h + eq_h lt_l, eq_h eq_l); no eq at the root
     while (nodes.size() > 1) {
         const bool root = nodes.size() == 2;
@@ -433,16 +514,25 @@ static copse_status infer_impl(copse_ctx *c, const copse_evk *evk, copse_model *
     }
     DCt Dc = nodes[0].lt;
     if (nodes[0].eq.data) ct_free(&nodes[0].eq, s);
-    if (Dc.level != D.lvl_D) { set_error("internal: unexpected level of the decision vector"); return COPSE_EINVAL; }
+    if (Dc.level != (enc ? m->enc->lvl_D : D->lvl_D)) {
+        set_error("internal: unexpected level of the decision vector");
+        return COPSE_EINVAL;
+    }
     STATUS_TRY(mark(1));
     // reshuffle: Branches = R_ext * Decisions
     std::vector<DCt> br;
-    STATUS_TRY(group_matmul(c, evk, Dc, D.R, {nullptr}, br, s));
+    if (enc)
+        STATUS_TRY(enc_matmul(c, evk, *m->enc, Dc, 0, br, s));
+    else
+        STATUS_TRY(group_matmul(c, evk, Dc, D->R, {nullptr}, br, s));
     ct_free(&Dc, s);
     STATUS_TRY(mark(2));
     // levels: Lvl_k * Branches XOR Mask_k, rotations of Branches shared by every level
     std::vector<DCt> lv;
-    STATUS_TRY(group_matmul(c, evk, br[0], D.Lv, D.mask, lv, s));
+    if (enc)
+        STATUS_TRY(enc_matmul(c, evk, *m->enc, br[0], 1, lv, s));
+    else
+        STATUS_TRY(group_matmul(c, evk, br[0], D->Lv, D->mask, lv, s));
     ct_free(&br[0], s);
     STATUS_TRY(mark(3));
     // product across levels, balanced
@@ -746,7 +836,8 @@ extern "C" copse_status copse_session_create_batch(copse_ctx *c, const copse_key
     CUDA_TRY(cudaStreamCreateWithFlags(&S->cap, cudaStreamNonBlocking));
     CUDA_TRY(cudaEventCreateWithFlags(&S->ev, cudaEventDisableTiming));
     // everything that synchronises or creates resources happens before capture
-    for (const SessItem &it : S->items) STATUS_TRY(upload_model(c, it.m, S->cap));
+    for (const SessItem &it : S->items)
+        if (!it.m->f.encrypted) STATUS_TRY(upload_model(c, it.m, S->cap));
     STATUS_TRY(ensure_lanes(c, (int)std::min<size_t>(n_items, COPSE_MAX_LANES)));
     CUDA_TRY(cudaStreamSynchronize(S->cap));
     stats_suspend(true);

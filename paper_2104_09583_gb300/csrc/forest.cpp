@@ -236,6 +236,20 @@ int compile_forest(const char *text, size_t len, uint32_t precision, uint32_t n_
     return 0;
 }
 
+BsgsGroup CompiledForest::group_reshuffle() const {
+    if (!encrypted) return bsgs_group({rot_reshuffle}, g_reshuffle);
+    std::vector<uint32_t> all(q);
+    for (uint32_t i = 0; i < q; i++) all[i] = i;
+    return bsgs_group({all}, g_reshuffle);
+}
+
+BsgsGroup CompiledForest::group_level() const {
+    if (!encrypted) return bsgs_group(lvl_nonzero, g_level);
+    std::vector<uint32_t> all(b);
+    for (uint32_t i = 0; i < b; i++) all[i] = i;
+    return bsgs_group(std::vector<std::vector<uint32_t>>(d, all), g_level);
+}
+
 bool BsgsGroup::plain() const {
     if (acc.size() != n_mat) return false;
     for (const Acc &a : acc)

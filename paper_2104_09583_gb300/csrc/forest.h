@@ -62,8 +62,11 @@ struct CompiledForest {
     std::vector<std::vector<uint32_t>> lvl_nonzero;  // per level: nonzero diagonal indices
     // baby-step sizes of the reshuffle and of the level products (0 = plain method)
     uint32_t g_reshuffle = 0, g_level = 0;
-    BsgsGroup group_reshuffle() const { return bsgs_group({rot_reshuffle}, g_reshuffle); }
-    BsgsGroup group_level() const { return bsgs_group(lvl_nonzero, g_level); }
+    // encrypted model (every diagonal is a ciphertext, zero ones included, so the
+    // products run over all q reshuffle and all b level diagonals)
+    bool encrypted = false;
+    BsgsGroup group_reshuffle() const;
+    BsgsGroup group_level() const;
 
     uint32_t m1() const { return L + b - 1; }       // rows of the extended reshuffle
     uint32_t pd() const { return m1() + q - 1; }    // slots carrying the periodic decisions

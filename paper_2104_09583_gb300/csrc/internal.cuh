@@ -15,6 +15,8 @@
 #include <string>
 #include <vector>
 
+#include "forest.h"
+
 #include "../../include/copse.h"
 
 typedef uint64_t u64;
@@ -191,6 +193,21 @@ cudaEvent_t lane_event(copse_ctx *c, int lane);
 copse_status dev_alloc(copse_ctx *ctx, void **p, size_t bytes, cudaStream_t s);
 void dev_free(void *p, cudaStream_t s);
 
+// stream-ordered scratch allocations freed (on the same stream) when it goes out of scope
+struct Scratch {
+    std::vector<void *> ptrs;
+    cudaStream_t s;
+    explicit Scratch(cudaStream_t st) : s(st) {}
+    ~Scratch() {
+        for (void *p : ptrs) dev_free(p, s);
+    }
+    copse_status get(copse_ctx *c, u64 **p, size_t words) {
+        STATUS_TRY(dev_alloc(c, (void **)p, words * sizeof(u64), s));
+        ptrs.push_back(*p);
+        return COPSE_OK;
+    }
+};
+
 // ---------------------------------------------------------------- ciphertexts
 // A ciphertext at level ell with ncomp components, each [ell][N] residues
 // (residue r modulo q_r), stored in the bit-reversed NTT (evaluation) domain.
@@ -275,6 +292,48 @@ copse_status op_matmul(copse_ctx *c, const copse_evk *evk, const DCt &v, const s
 //   out[a] = modswitch(ModDown(sum_{k != 0} R_k(inner[a, k])) + inner[a, 0] + add[a]),
 // R_k the rotation by k before its ModDown; accumulators of one matrix are
 // contiguous with giant steps ascending.
+// ---------------------------------------------------------------- encrypted models
+// The model's ciphertexts in canonical order (threshold planes, reshuffle diagonals,
+// level-k diagonals for k = 1..d, masks), each a secret-key encryption at its level
+// of use with only c0 stored; c1 is regenerated from (seed, stream of the index).
+struct EncModel {
+    uint64_t ctx_serial = 0;
+    u64 seed = 0;
+    uint32_t g_r = 0, g_l = 0;       // baby-step plan the diagonals were shifted for
+    int lvl_D = 0, lvl_B = 0;
+    int p = 0, q = 0, b = 0, d = 0;
+    u64 *store = nullptr;
+    std::vector<size_t> off;         // word offset of each ciphertext's c0
+    std::vector<int> level;
+    BsgsGroup grpR, grpL;            // dense plans (every diagonal present)
+    int idx_thr(int i) const { return i; }
+    int idx_R(int i) const { return p + i; }
+    int idx_lvl(int k, int i) const { return p + q + (k - 1) * b + i; }
+    int idx_mask(int k) const { return p + q + d * b + (k - 1); }
+    const u64 *c0(int idx) const { return store + off[idx]; }
+    ~EncModel();
+};
+copse_status enc_model_build(copse_ctx *c, const copse_keys *keys, const CompiledForest &f, u64 seed, EncModel &E,
+                             cudaStream_t s);
+// the full ciphertext idx [2][level][N] (c1 regenerated) into a new buffer
+copse_status enc_materialize(copse_ctx *c, const EncModel &E, int idx, DCt *out, cudaStream_t s);
+// products of v with the encrypted reshuffle (kind 0) or level matrices and masks (kind 1)
+copse_status enc_matmul(copse_ctx *c, const copse_evk *evk, const EncModel &E, const DCt &v, int kind,
+                        std::vector<DCt> &out, cudaStream_t s);
+
+// Giant steps over per-accumulator ciphertexts inner [nacc][2][ell][N] (accumulators of
+// one matrix contiguous, giant steps ascending): per matrix a
+//   out[a] = modswitch(ModDown(sum_{k != 0} R_k(inner_k)) + inner_0 + add_pt[a] + add_ct[a]).
+copse_status giant_phase(copse_ctx *c, const copse_evk *evk, const u64 *inner, int ell, const std::vector<int> &acc_mat,
+                         const std::vector<uint32_t> &acc_giant, int n_mat, const std::vector<const u64 *> &add_pt,
+                         const std::vector<const u64 *> &add_ct, std::vector<DCt> &out, cudaStream_t s);
+// rotations of v by each amount (one ModUp shared by all), out [n][2][v.level][N]
+copse_status op_rotations(copse_ctx *c, const copse_evk *evk, const DCt &v, const std::vector<uint32_t> &amounts,
+                          u64 *out, cudaStream_t s);
+// relinearisation of n 3-component ciphertexts d3 [n][3][ell][N] into out [n][2][ell][N]
+copse_status relin_batch(copse_ctx *c, const copse_evk *evk, const u64 *d3, int n, int ell, u64 *out, cudaStream_t s);
+// c0 += 1 in place
+copse_status op_add_one(copse_ctx *c, DCt &x, cudaStream_t s);
 copse_status op_matmul_bsgs(copse_ctx *c, const copse_evk *evk, const DCt &v, const std::vector<uint32_t> &baby,
                             const std::vector<std::vector<const u64 *>> &pt, const std::vector<int> &acc_mat,
                             const std::vector<uint32_t> &acc_giant, int n_mat, const std::vector<const u64 *> &add,

@@ -136,9 +136,10 @@ __global__ void k_modup(const u64 *x, const u64 *x_ntt, size_t xs, u64 *y, int e
 }
 
 struct InnerJob {
-    const u64 *ksk;  // [ndig][2][L+alpha][N]
-    u64 *out;        // [2][ell+alpha][N]
-    u64 g;           // Galois element applied to the ModUp output, 1 = none
+    const u64 *ksk;          // [ndig][2][L+alpha][N]
+    u64 *out;                // [2][ell+alpha][N]
+    u64 g;                   // Galois element applied to the ModUp output, 1 = none
+    const u64 *y = nullptr;  // this job's own ModUp digits (null = the launch's shared ones)
 };
 // a launch's jobs, passed by value (kernel parameter space): no host-to-device copy
 struct InnerJobs {
@@ -159,9 +160,10 @@ __global__ void k_ks_inner(const u64 *yhat, const InnerJobs jobs, int ell, int a
     const int g = r < ell ? r : L + (r - ell);
     const PrimeDev P = pr[g];
     const uint32_t src = J.g == 1 ? n : galois_src(n, J.g, logN);
+    const u64 *yh = J.y ? J.y : yhat;
     u64 acc0 = 0, acc1 = 0;
     for (int j = 0; j < nd; j++) {
-        const u64 y = yhat[(((size_t)j * nx + r) << logN) + src];
+        const u64 y = yh[(((size_t)j * nx + r) << logN) + src];
         const u64 *k0 = J.ksk + (((size_t)(2 * j) * NB + g) << logN);
         const u64 *k1 = J.ksk + (((size_t)(2 * j + 1) * NB + g) << logN);
         acc0 = add_mod(acc0, mul_mod(y, k0[n], P), P.q);
@@ -569,21 +571,36 @@ __global__ void k_extract_bits(const u64 *slots, int nq, int block, int L, uint8
     bits[e] = v == 0 ? 0 : (v == 1 ? 1 : 2);
 }
 
-// ---------------------------------------------------------------- helpers
-struct Scratch {
-    std::vector<void *> ptrs;
-    cudaStream_t s;
-    explicit Scratch(cudaStream_t st) : s(st) {}
-    ~Scratch() {
-        for (void *p : ptrs) dev_free(p, s);
-    }
-    copse_status get(copse_ctx *c, u64 **p, size_t words) {
-        STATUS_TRY(dev_alloc(c, (void **)p, words * sizeof(u64), s));
-        ptrs.push_back(*p);
-        return COPSE_OK;
-    }
-};
+// Relinearisation finish for a batch (blockIdx.y = item): out = (d0, d1) + (U - t W) P^-1,
+// U [n][2][ell+alpha][N], W [n][2][ell][N], d3 [n][3][ell][N], out [n][2][ell][N]
+__global__ void k_relin_finish(const u64 *U, const u64 *W, const u64 *d3, u64 *out, int ell, int alpha, int logN,
+                               const PrimeDev *pr, KsTables T) {
+    const size_t n_el = (size_t)ell << logN;
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= 2 * n_el) return;
+    const size_t it = blockIdx.y;
+    U += it * 2 * ((size_t)(ell + alpha) << logN);
+    W += it * 2 * n_el;
+    d3 += it * 3 * n_el;
+    out += it * 2 * n_el;
+    const int c = e >= n_el;
+    const size_t k = e - c * n_el;
+    const int i = (int)(k >> logN);
+    const PrimeDev P = pr[i];
+    const u64 uv = U[(size_t)c * ((size_t)(ell + alpha) << logN) + k];
+    const u64 v = mul_shoup(sub_mod(uv, mul_shoup(W[e], P.t_mod, P.t_mod_sh, P.q), P.q), T.md_Pinv[i], P.q);
+    out[e] = add_mod(v, d3[e], P.q);
+}
 
+// c0 += 1 (the constant polynomial 1 is 1 at every evaluation point)
+__global__ void k_add_one(u64 *c0, int ell, int logN, const PrimeDev *pr) {
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= ((size_t)ell << logN)) return;
+    const u64 q = pr[e >> logN].q;
+    c0[e] = add_mod(c0[e], 1, q);
+}
+
+// ---------------------------------------------------------------- helpers
 NttBatch batch(u64 *data, size_t stride, int npoly, int r0, int nr, int ell, int fixed = -1) {
     return NttBatch{data, stride, npoly, r0, nr, ell, fixed};
 }
@@ -913,62 +930,67 @@ copse_status op_matmul(copse_ctx *c, const copse_evk *evk, const DCt &v, const s
     return COPSE_OK;
 }
 
-copse_status op_matmul_bsgs(copse_ctx *c, const copse_evk *evk, const DCt &v, const std::vector<uint32_t> &baby,
-                            const std::vector<std::vector<const u64 *>> &pt, const std::vector<int> &acc_mat,
-                            const std::vector<uint32_t> &acc_giant, int n_mat, const std::vector<const u64 *> &add,
-                            std::vector<DCt> &out, cudaStream_t s) {
-    const int ell = v.level, N = c->N, A = c->alpha, nx = ell + A, nd = (ell + A - 1) / A;
-    const int nacc = (int)pt.size();
+copse_status giant_phase(copse_ctx *c, const copse_evk *evk, const u64 *inner, int ell, const std::vector<int> &acc_mat,
+                         const std::vector<uint32_t> &acc_giant, int n_mat, const std::vector<const u64 *> &add_pt,
+                         const std::vector<const u64 *> &add_ct, std::vector<DCt> &out, cudaStream_t s) {
+    const int N = c->N, A = c->alpha, nx = ell + A, nd = (ell + A - 1) / A;
+    const int nacc = (int)acc_mat.size();
     const size_t per = (size_t)2 * ell * N, ext = (size_t)2 * nx * N;
     std::vector<u64> gal(nacc);
+    bool any_rot = false;
     for (int x = 0; x < nacc; x++) {
         gal[x] = galois_of_rotation(c, acc_giant[x]);
-        if (gal[x] != 1 && !evk->find(gal[x])) {
+        if (gal[x] == 1) continue;
+        any_rot = true;
+        if (!evk->find(gal[x])) {
             set_error("no rotation key for amount " + std::to_string(acc_giant[x]));
             return COPSE_ENOKEY;
         }
     }
     Scratch sc(s);
-    // baby steps: inner[x] = sum_j d'_{x,j} * rot(v, j), one ModDown each
-    u64 *inner = nullptr, *acc = nullptr, *W = nullptr, *res = nullptr;
-    STATUS_TRY(sc.get(c, &inner, (size_t)nacc * per));
-    std::vector<DCt> none;
-    STATUS_TRY(op_matmul(c, evk, v, baby, pt, {}, none, s, inner));
-    // giant steps: per matrix, the rotated accumulators key-switched into one
-    // extended-basis sum (the ModUps of a matrix's terms batched), one ModDown for all
-    STATUS_TRY(sc.get(c, &acc, (size_t)n_mat * ext));
-    STATUS_TRY(sc.get(c, &W, (size_t)n_mat * per));
+    u64 *acc = nullptr, *W = nullptr, *res = nullptr;
     STATUS_TRY(sc.get(c, &res, (size_t)n_mat * per));
-    CUDA_TRY(cudaMemsetAsync(acc, 0, (size_t)n_mat * ext * sizeof(u64), s));
-    for (int a = 0; a < n_mat; a++) {
-        int x0 = 0;
-        while (x0 < nacc && (acc_mat[x0] != a || gal[x0] == 1)) x0++;
-        int x1 = x0;
-        while (x1 < nacc && acc_mat[x1] == a && gal[x1] != 1) x1++;
-        if (x0 == x1) continue;
-        for (int x = x1; x < nacc; x++)
-            if (acc_mat[x] == a && gal[x] != 1) { set_error("internal: giant steps of a matrix not contiguous"); return COPSE_EINVAL; }
-        Scratch sk(s);  // this matrix's ModUp digits, freed (stream-ordered) after its launches
-        u64 *yhat = nullptr;
-        STATUS_TRY(ks_modup_batch(c, inner + (size_t)x0 * per + (size_t)ell * N, per, x1 - x0, ell, sk, &yhat, s));
-        for (int k0 = x0; k0 < x1; k0 += RS_CHUNK) {
-            const int nt = std::min(RS_CHUNK, x1 - k0);
-            RsTable tab;
-            memset(&tab, 0, sizeof(tab));
-            for (int i = 0; i < nt; i++) {
-                const int x = k0 + i;
-                tab.t[i] = RsTerm{yhat + (size_t)(x - x0) * nd * nx * N, inner + (size_t)x * per, evk->find(gal[x]),
-                                  gal[x]};
+    if (!any_rot) {
+        CUDA_TRY(cudaMemsetAsync(res, 0, (size_t)n_mat * per * sizeof(u64), s));
+    } else {
+        // per matrix, the rotated accumulators key-switched into one extended-basis sum
+        // (the ModUps of a matrix's terms batched), one ModDown for all matrices
+        STATUS_TRY(sc.get(c, &acc, (size_t)n_mat * ext));
+        STATUS_TRY(sc.get(c, &W, (size_t)n_mat * per));
+        CUDA_TRY(cudaMemsetAsync(acc, 0, (size_t)n_mat * ext * sizeof(u64), s));
+        for (int a = 0; a < n_mat; a++) {
+            int x0 = 0;
+            while (x0 < nacc && (acc_mat[x0] != a || gal[x0] == 1)) x0++;
+            int x1 = x0;
+            while (x1 < nacc && acc_mat[x1] == a && gal[x1] != 1) x1++;
+            if (x0 == x1) continue;
+            for (int x = x1; x < nacc; x++)
+                if (acc_mat[x] == a && gal[x] != 1) {
+                    set_error("internal: giant steps of a matrix not contiguous");
+                    return COPSE_EINVAL;
+                }
+            Scratch sk(s);  // this matrix's ModUp digits, freed (stream-ordered) after its launches
+            u64 *yhat = nullptr;
+            STATUS_TRY(ks_modup_batch(c, inner + (size_t)x0 * per + (size_t)ell * N, per, x1 - x0, ell, sk, &yhat, s));
+            for (int k0 = x0; k0 < x1; k0 += RS_CHUNK) {
+                const int nt = std::min(RS_CHUNK, x1 - k0);
+                RsTable tab;
+                memset(&tab, 0, sizeof(tab));
+                for (int i = 0; i < nt; i++) {
+                    const int x = k0 + i;
+                    tab.t[i] = RsTerm{yhat + (size_t)(x - x0) * nd * nx * N, inner + (size_t)x * per,
+                                      evk->find(gal[x]), gal[x]};
+                }
+                const double bytes = 8.0 * N * ((double)nt * (2.0 * nd * nx + (double)nd * nx + ell) + 4.0 * nx);
+                TIMED("rotsum", bytes, s,
+                      k_rotsum<<<nblk((size_t)nx * N), TPB, 0, s>>>(tab, nt, acc + (size_t)a * ext, ell, A, c->L,
+                                                                    c->logN, c->d_prime, c->ks));
+                LAUNCH_CHECK();
             }
-            const double bytes = 8.0 * N * ((double)nt * (2.0 * nd * nx + (double)nd * nx + ell) + 4.0 * nx);
-            TIMED("rotsum", bytes, s,
-                  k_rotsum<<<nblk((size_t)nx * N), TPB, 0, s>>>(tab, nt, acc + (size_t)a * ext, ell, A, c->L,
-                                                                c->logN, c->d_prime, c->ks));
-            LAUNCH_CHECK();
         }
+        STATUS_TRY(moddown_batch(c, acc, n_mat, ell, W, res, s));
     }
-    STATUS_TRY(moddown_batch(c, acc, n_mat, ell, W, res, s));
-    // + the giant-step-0 sums, + add, then one modulus switch per matrix
+    // + the giant-step-0 sums, + the plaintext or ciphertext addend, then one modulus switch per matrix
     out.assign(n_mat, DCt());
     for (int a = 0; a < n_mat; a++) {
         u64 *ra = res + (size_t)a * per;
@@ -977,8 +999,12 @@ copse_status op_matmul_bsgs(copse_ctx *c, const copse_evk *evk, const DCt &v, co
                 k_add<<<nblk(per), TPB, 0, s>>>(ra, inner + (size_t)x * per, ra, 2, ell, c->logN, 0, c->d_prime);
                 LAUNCH_CHECK();
             }
-        if (add.size() > (size_t)a && add[a]) {
-            k_add_plain<<<nblk((size_t)ell * N), TPB, 0, s>>>(ra, add[a], ell, c->logN, c->d_prime);
+        if (add_pt.size() > (size_t)a && add_pt[a]) {
+            k_add_plain<<<nblk((size_t)ell * N), TPB, 0, s>>>(ra, add_pt[a], ell, c->logN, c->d_prime);
+            LAUNCH_CHECK();
+        }
+        if (add_ct.size() > (size_t)a && add_ct[a]) {
+            k_add<<<nblk(per), TPB, 0, s>>>(ra, add_ct[a], ra, 2, ell, c->logN, 0, c->d_prime);
             LAUNCH_CHECK();
         }
         DCt tmp;
@@ -986,6 +1012,91 @@ copse_status op_matmul_bsgs(copse_ctx *c, const copse_evk *evk, const DCt &v, co
         tmp.data = ra;
         STATUS_TRY(op_modswitch(c, tmp, &out[a], s));
     }
+    return COPSE_OK;
+}
+
+copse_status op_matmul_bsgs(copse_ctx *c, const copse_evk *evk, const DCt &v, const std::vector<uint32_t> &baby,
+                            const std::vector<std::vector<const u64 *>> &pt, const std::vector<int> &acc_mat,
+                            const std::vector<uint32_t> &acc_giant, int n_mat, const std::vector<const u64 *> &add,
+                            std::vector<DCt> &out, cudaStream_t s) {
+    const int ell = v.level, nacc = (int)pt.size();
+    Scratch sc(s);
+    // baby steps: inner[x] = sum_j d'_{x,j} * rot(v, j), one ModDown each
+    u64 *inner = nullptr;
+    STATUS_TRY(sc.get(c, &inner, (size_t)nacc * 2 * ell * c->N));
+    std::vector<DCt> none;
+    STATUS_TRY(op_matmul(c, evk, v, baby, pt, {}, none, s, inner));
+    return giant_phase(c, evk, inner, ell, acc_mat, acc_giant, n_mat, add, {}, out, s);
+}
+
+copse_status op_rotations(copse_ctx *c, const copse_evk *evk, const DCt &v, const std::vector<uint32_t> &amounts,
+                          u64 *out, cudaStream_t s) {
+    const int ell = v.level, N = c->N, A = c->alpha, nx = ell + A;
+    const size_t per = (size_t)2 * ell * N;
+    std::vector<int> ks;
+    std::vector<u64> gal(amounts.size());
+    for (size_t x = 0; x < amounts.size(); x++) {
+        gal[x] = galois_of_rotation(c, amounts[x]);
+        if (gal[x] == 1) {
+            CUDA_TRY(cudaMemcpyAsync(out + x * per, v.data, per * sizeof(u64), cudaMemcpyDeviceToDevice, s));
+            continue;
+        }
+        if (!evk->find(gal[x])) { set_error("no rotation key for amount " + std::to_string(amounts[x])); return COPSE_ENOKEY; }
+        ks.push_back((int)x);
+    }
+    if (ks.empty()) return COPSE_OK;
+    Scratch sc(s);
+    u64 *yhat = nullptr;
+    STATUS_TRY(ks_modup(c, v.data + (size_t)ell * N, ell, sc, &yhat, s));
+    for (size_t k0 = 0; k0 < ks.size(); k0 += CHUNK_ROT) {
+        const int nj = (int)std::min<size_t>(CHUNK_ROT, ks.size() - k0);
+        Scratch sk(s);
+        u64 *U = nullptr, *W = nullptr;
+        STATUS_TRY(sk.get(c, &U, (size_t)nj * 2 * nx * N));
+        STATUS_TRY(sk.get(c, &W, (size_t)nj * per));
+        std::vector<InnerJob> jobs;
+        for (int i = 0; i < nj; i++) {
+            const int x = ks[k0 + i];
+            jobs.push_back(InnerJob{evk->find(gal[x]), U + (size_t)i * 2 * nx * N, gal[x]});
+        }
+        STATUS_TRY(ks_apply(c, yhat, ell, jobs, U, W, sk, s));
+        for (int i = 0; i < nj; i++) {
+            const int x = ks[k0 + i];
+            TIMED("ks_finish", 8.0 * N * 6.0 * ell, s,
+                  k_ks_finish<<<nblk(per), TPB, 0, s>>>(U + (size_t)i * 2 * nx * N, W + (size_t)i * per, v.data,
+                                                        nullptr, gal[x], out + (size_t)x * per, ell, A, c->logN,
+                                                        c->d_prime, c->ks));
+            LAUNCH_CHECK();
+        }
+    }
+    return COPSE_OK;
+}
+
+copse_status relin_batch(copse_ctx *c, const copse_evk *evk, const u64 *d3, int n, int ell, u64 *out, cudaStream_t s) {
+    const int N = c->N, A = c->alpha, nx = ell + A, nd = (ell + A - 1) / A;
+    const size_t per3 = (size_t)3 * ell * N, per = (size_t)2 * ell * N;
+    for (int x0 = 0; x0 < n; x0 += CHUNK_ROT) {
+        const int nj = std::min(CHUNK_ROT, n - x0);
+        Scratch sk(s);
+        u64 *yhat = nullptr, *U = nullptr, *W = nullptr;
+        STATUS_TRY(ks_modup_batch(c, d3 + (size_t)x0 * per3 + (size_t)2 * ell * N, per3, nj, ell, sk, &yhat, s));
+        STATUS_TRY(sk.get(c, &U, (size_t)nj * 2 * nx * N));
+        STATUS_TRY(sk.get(c, &W, (size_t)nj * per));
+        std::vector<InnerJob> jobs;
+        for (int i = 0; i < nj; i++)
+            jobs.push_back(InnerJob{evk->rlk, U + (size_t)i * 2 * nx * N, 1, yhat + (size_t)i * nd * nx * N});
+        STATUS_TRY(ks_apply(c, yhat, ell, jobs, U, W, sk, s));
+        TIMED("ks_finish", 8.0 * N * 7.0 * ell * nj, s,
+              k_relin_finish<<<dim3(nblk(per), nj), TPB, 0, s>>>(U, W, d3 + (size_t)x0 * per3, out + (size_t)x0 * per,
+                                                                 ell, A, c->logN, c->d_prime, c->ks));
+        LAUNCH_CHECK();
+    }
+    return COPSE_OK;
+}
+
+copse_status op_add_one(copse_ctx *c, DCt &x, cudaStream_t s) {
+    k_add_one<<<nblk((size_t)x.level * c->N), TPB, 0, s>>>(x.data, x.level, c->logN, c->d_prime);
+    LAUNCH_CHECK();
     return COPSE_OK;
 }
 

@@ -96,3 +96,21 @@ def test_tuning_calls_marshal_and_reject_null_handles():
         with pytest.raises(K.CopseError) as e:
             call()
         assert e.value.name == "EINVAL"
+
+
+def test_encrypted_mode_key_sets_match_oracle():
+    """Encrypted-model mode runs the products over every diagonal: its rotation sets
+    (plain and baby-step / giant-step) equal the oracle's."""
+    text = synth.random_forest(77, 3, 4, 3, 5, 3, complete=False)
+    om = Cp.compile_forest(text, 5, 3)
+    h = K.copse_compile_forest(text, 5, 3, 10)
+    try:
+        K.copse_model_set_encrypted(h, True)
+        for g in [(0, 0), (4, 3), (8, 8)]:
+            K.copse_model_set_bsgs(h, *g)
+            assert K.copse_model_rotations(h) == Cp.encrypted_rotation_sets(om, g), g
+        K.copse_model_set_encrypted(h, False)
+        K.copse_model_set_bsgs(h, 0, 0)
+        assert K.copse_model_rotations(h) == Cp.rotation_sets(om)
+    finally:
+        K.copse_model_destroy(h)
