@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--no-serving", action="store_true", help="skip the Poisson-arrival serving leg")
     ap.add_argument("--no-table6", action="store_true", help="skip the per-stage microbenchmark sweep")
     ap.add_argument("--no-tune", action="store_true", help="fixed schedule (dnum 3, plain products, cluster NTT)")
+    ap.add_argument("--no-encmodel", action="store_true", help="skip the encrypted-model leg")
     return ap.parse_args()
 
 
@@ -349,6 +350,7 @@ def run_cuda(args, ws, rank, local):
     serving = None if args.no_serving else run_serving(local, tune=not args.no_tune)
     batch3 = None if args.no_serving else run_batch3(local, tune=not args.no_tune)
     table6 = None if args.no_table6 else run_table6(local)
+    encmodel = None if args.no_encmodel else run_encmodel(local)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -371,7 +373,7 @@ def run_cuda(args, ws, rank, local):
                    "l2": "working set > L2 (rotation keys alone are %.1f GB)" % (
                        (info["n_rot_reshuffle"] + info["n_rot_level"]) * 3 * 2 * (W.primes + 4) * N * 8 / 1e9)},
         "labels_ok": ok, "path": "graph session", "batched": batched, "plain_ops": plain_ops, "e2e": e2e,
-        "serving": serving, "batch3": batch3, "table6": table6, "gpu_launches": launches_total,
+        "serving": serving, "batch3": batch3, "table6": table6, "encmodel": encmodel, "gpu_launches": launches_total,
         "roofline": roof, "kernels": kern, "clocks": ck, "cpu_baseline": cpu,
     }
     return line
@@ -545,6 +547,93 @@ def run_batch3(local, steps=3, warmup=1, tune=True):
             "items": len(items), "labels_ok": ok, "tuning": tuning,
             "forests": [f"{i['n_trees']} trees, {i['b']} branches, {i['n_rot_reshuffle']}+{i['n_rot_level']} "
                         f"rotations, {p} queries/ciphertext" for i, p in zip(infos, per)]}
+
+
+# ---------------------------------------------------------------- encrypted model
+def run_encmodel(local, steps=1, warmup=1, g=(128, 256)):
+    """The encrypted-model workload (Maurice = Diane): 32 random trees of depth <= 8, 32 features,
+    16-bit, 10 classes, N = 2^15 with 16 primes; every model ciphertext (thresholds, all reshuffle
+    and level diagonals, masks) encrypted once; one step = the 64 queries (2 per ciphertext, 32
+    ciphertexts) encrypted, inferred together and decrypted on one stream.  Baby-step sizes from
+    a tuner sweep of this model (copse_tune_bsgs: 128 / 256 fastest)."""
+    import torch
+
+    from paper_2104_09583_gb300 import copse as K
+    from paper_2104_09583_gb300 import synth
+
+    W = synth.WORKLOADS["encmodel32-n32768"]
+    text = W.forest_texts()[0]
+    N = 1 << W.log_n
+    ctx = K.copse_ctx_create(W.log_n, W.bits, W.primes, W.dnum, device=local)
+    model = K.copse_compile_forest(text, W.precision(), W.n_features(), W.log_n)
+    K.copse_model_set_encrypted(model, True)
+    K.copse_model_set_bsgs(model, *g)
+    info = K.copse_model_info_get(model)
+    per_ct = N // info["block"]
+    t0 = time.perf_counter()
+    keys, evk = K.copse_keygen(ctx, 29, [model])
+    torch.cuda.synchronize()
+    t_keys = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    K.copse_encrypt_model(ctx, keys, model, 2024)
+    t_enc = time.perf_counter() - t0
+    nq = W.queries[0]
+    qs = W.query_arrays()[0]
+    want = K.copse_classify_plain(model, qs)
+    L = info["n_leaves"]
+    stream = torch.cuda.current_stream().cuda_stream
+    d_q = torch.from_numpy(qs.astype(np.int32)).cuda()
+    d_bits = torch.zeros(nq * L, dtype=torch.uint8, device="cuda")
+
+    def step(seed):
+        # all query ciphertexts in one buffer: the products read each encrypted diagonal
+        # (and regenerate its mask) once per group of query ciphertexts
+        ct = K.copse_encrypt_features(ctx, keys, model, d_q.data_ptr(), seed, stream=stream, on_device=True,
+                                      n_queries=nq)
+        res = K.copse_infer(ctx, evk, model, ct, stream=stream)
+        K.copse_decrypt_labels(ctx, keys, model, res, nq, stream=stream, out_device_ptr=d_bits.data_ptr())
+        K.copse_ctbuf_destroy(res)
+        K.copse_ctbuf_destroy(ct)
+
+    for w in range(warmup):
+        step(500 + 100 * w)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for i in range(steps):
+        step(900 + 100 * i)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    ok = bool(np.array_equal(d_bits.cpu().numpy().reshape(nq, L), want))
+    # per-stage breakdown of one ciphertext's inference, then its kernels by family
+    ct = K.copse_encrypt_features(ctx, keys, model, qs[:per_ct], 77)
+    res, stages = K.copse_infer_timed(ctx, evk, model, ct)
+    K.copse_ctbuf_destroy(res)
+    K.copse_stats_reset()
+    K.copse_stats_enable(True)
+    res = K.copse_infer(ctx, evk, model, ct)
+    torch.cuda.synchronize()
+    K.copse_stats_enable(False)
+    fam = {k: {"launches": v["launches"], "ms": round(v["ms"], 3)} for k, v in K.copse_stats_all().items()
+           if v["launches"]}
+    fam = dict(sorted(fam.items(), key=lambda kv: -kv[1]["ms"])[:8])
+    K.copse_ctbuf_destroy(res)
+    K.copse_ctbuf_destroy(ct)
+    n_ct = info["precision"] + info["q"] + info["depth"] * (info["b"] + 1)
+    lvl_D = W.primes - 1 - (info["precision"] - 1).bit_length()
+    words = (info["precision"] * W.primes + info["q"] * lvl_D + info["depth"] * (info["b"] + 1) * (lvl_D - 1)) * N
+    K.copse_keys_destroy(keys)
+    K.copse_evk_destroy(evk)
+    K.copse_model_destroy(model)
+    K.copse_ctx_destroy(ctx)
+    return {"value": nq / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "queries_per_step": nq,
+            "ciphertexts_per_step": (nq + per_ct - 1) // per_ct, "labels_ok": ok,
+            "stage_ms_one_ciphertext": stages, "kernels_one_ciphertext": fam, "model_ciphertexts": n_ct,
+            "model_gb_on_device": round(words * 8 / 1e9, 1), "model_encryption_s": round(t_enc, 2),
+            "keygen_s": round(t_keys, 2), "bsgs": list(g), "rotation_keys": info["n_rot_reshuffle"] + info["n_rot_level"],
+            "model": f"{info['n_trees']} trees, {info['b']} branches, depth {info['depth']}, q {info['q']}, "
+                     f"{info['precision']}-bit, N = 2^{W.log_n}, {W.primes} primes"}
 
 
 # ---------------------------------------------------------------- Table 6 microbenchmarks

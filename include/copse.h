@@ -157,6 +157,7 @@ copse_status copse_model_get_bsgs(const copse_model *model, uint32_t *g_reshuffl
  * encrypted for another baby-step plan.  Changing the mode or the plan drops
  * the encryption. */
 copse_status copse_model_set_encrypted(copse_model *model, int on);
+int copse_model_is_encrypted(const copse_model *model);  /* 1 in encrypted-model mode, else 0 */
 copse_status copse_encrypt_model(copse_ctx *ctx, const copse_keys *keys, copse_model *model, uint64_t seed);
 
 /* Model ciphertext `index` (threshold planes, reshuffle diagonals, level

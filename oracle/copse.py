@@ -629,9 +629,11 @@ def galois_elements(m: Model, logN: int, g=(0, 0)):
     return sorted(set(B.galois_rot(logN, i) for i in rs + ls))
 
 
-def encrypt_queries(bgv: B.Bgv, keys: B.Keys, m: Model, queries, seed: int):
+def encrypt_queries(bgv: B.Bgv, keys: B.Keys, m: Model, queries, seed: int, index0: int = 0):
+    """The p feature planes of one query ciphertext, plane i as encryption index0 + i
+    (query ciphertext c of a larger batch uses index0 = c p)."""
     planes = feature_planes(m, queries, bgv.P.N)
-    return [bgv.encrypt_slots(keys.pk, planes[i], seed, i) for i in range(m.precision)]
+    return [bgv.encrypt_slots(keys.pk, planes[i], seed, index0 + i) for i in range(m.precision)]
 
 
 def decode_labels(m: Model, slots, n_queries: int):

@@ -64,6 +64,7 @@ _SIG = {
     "copse_model_rotations": (C.c_int, [vp, vp, vp]),
     "copse_model_set_bsgs": (C.c_int, [vp, C.c_uint32, C.c_uint32]),
     "copse_model_set_encrypted": (C.c_int, [vp, C.c_int]),
+    "copse_model_is_encrypted": (C.c_int, [vp]),
     "copse_encrypt_model": (C.c_int, [vp, vp, vp, C.c_uint64]),
     "copse_encmodel_export": (C.c_int, [vp, vp, C.c_size_t, u64p, C.c_size_t]),
     "copse_tune_ntt": (C.c_int, [vp, u32p, C.c_size_t, C.c_int, C.POINTER(C.c_float), C.POINTER(C.c_float),

@@ -272,6 +272,8 @@ extern "C" copse_status copse_model_set_encrypted(copse_model *m, int on) {
     return COPSE_OK;
 }
 
+extern "C" int copse_model_is_encrypted(const copse_model *m) { return m && m->f.encrypted ? 1 : 0; }
+
 extern "C" copse_status copse_encrypt_model(copse_ctx *c, const copse_keys *k, copse_model *m, uint64_t seed) {
     if (!c || !k || !m) { set_error("null argument"); return COPSE_EINVAL; }
     const CompiledForest &f = m->f;
@@ -391,7 +393,8 @@ extern "C" copse_status copse_encrypt_features(copse_ctx *c, const copse_keys *k
     if (!c || !k || !m || !out || (nq && !feats)) { set_error("null argument"); return COPSE_EINVAL; }
     const CompiledForest &f = m->f;
     if ((int)f.log_n != c->logN) { set_error("model compiled for another ring degree"); return COPSE_EINVAL; }
-    if (nq > (size_t)(c->N / f.block)) { set_error("more queries than slot blocks"); return COPSE_EINVAL; }
+    const size_t per_ct = (size_t)(c->N / f.block);
+    if (nq > per_ct * 64) { set_error("more than 64 ciphertexts of queries"); return COPSE_EINVAL; }
     cudaStream_t s = as_stream(stream);
     const uint32_t *d_feats = feats;
     uint32_t *tmp = nullptr;
@@ -406,8 +409,15 @@ extern "C" copse_status copse_encrypt_features(copse_ctx *c, const copse_keys *k
     auto buf = std::make_unique<copse_ctbuf>();
     buf->ctx = c;
     buf->stream = s;
-    copse_status st = encrypt_planes(c, k, d_feats, (int)nq, (int)f.n_features, (int)f.K, (int)f.q, (int)f.pd(),
-                                     (int)f.block, (int)f.precision, seed, buf->cts, s);
+    // query ciphertext q holds queries [q per_ct, (q + 1) per_ct); its plane i is encryption q p + i
+    copse_status st = COPSE_OK;
+    for (size_t j0 = 0, q = 0; st == COPSE_OK && (j0 < nq || (nq == 0 && q == 0)); j0 += per_ct, q++) {
+        const size_t n = std::min(per_ct, nq - j0);
+        st = encrypt_planes(c, k, d_feats + j0 * f.n_features, (int)n, (int)f.n_features, (int)f.K, (int)f.q,
+                            (int)f.pd(), (int)f.block, (int)f.precision, seed, buf->cts, s, nullptr,
+                            (int)(q * f.precision));
+        if (nq == 0) break;
+    }
     if (tmp) dev_free(tmp, s);
     if (st) return st;
     *out = buf.release();
@@ -422,33 +432,13 @@ static copse_status group_matmul(copse_ctx *c, const copse_evk *evk, const DCt &
     return op_matmul_bsgs(c, evk, v, G.plan.baby, G.pt, G.acc_mat, G.acc_giant, (int)G.plan.n_mat, add, out, s);
 }
 
-static copse_status infer_impl(copse_ctx *c, const copse_evk *evk, copse_model *m, const copse_ctbuf *feats,
-                               DCt *result, cudaStream_t s, int lane = 0, cudaEvent_t *stage_ev = nullptr) {
+// SecComp of one query ciphertext's p feature planes x[0..p) (Section 4.1.2):
+// the decision vector D = [x < thresholds] at level lvl_D.
+static copse_status seccomp_one(copse_ctx *c, const copse_evk *evk, copse_model *m, const DCt *x, DCt *Dc,
+                                cudaStream_t s, int lane) {
     const bool enc = m->f.encrypted;
-    if (enc) {
-        if (!m->enc || m->enc->ctx_serial != c->serial) {
-            set_error("encrypted-mode model has no encryption on this context (copse_encrypt_model)");
-            return COPSE_EINVAL;
-        }
-        if (m->enc->g_r != m->f.g_reshuffle || m->enc->g_l != m->f.g_level) {
-            set_error("model was encrypted for another baby-step plan");
-            return COPSE_EINVAL;
-        }
-    } else {
-        STATUS_TRY(upload_model(c, m, s));
-    }
-    // stage boundaries (comparison | reshuffle | levels | aggregation), when timed
-    auto mark = [&](int i) -> copse_status {
-        if (stage_ev) CUDA_TRY(cudaEventRecord(stage_ev[i], s));
-        return COPSE_OK;
-    };
-    STATUS_TRY(mark(0));
     const DeviceModel *D = m->dev.get();
-    const CompiledForest &f = m->f;
-    const int p = (int)f.precision;
-    if ((int)feats->cts.size() != p) { set_error("feature buffer does not hold one ciphertext per bit-plane"); return COPSE_EINVAL; }
-    for (const DCt &x : feats->cts)
-        if (x.level != c->L) { set_error("feature ciphertexts must be fresh"); return COPSE_EINVAL; }
+    const int p = (int)m->f.precision;
     struct Node { DCt lt, eq; };
     // Independent operations of one step run on forked side streams and are
     // joined back onto s; every free happens on s after the join.
@@ -461,8 +451,8 @@ static copse_status infer_impl(copse_ctx *c, const copse_evk *evk, copse_model *
             const int i = p - 1 - k;
             DPt lm{c->L, (u64 *)D->lt_mul[i]}, la{c->L, (u64 *)D->lt_add[i]};
             DPt em{c->L, (u64 *)D->eq_mul[i]}, ea{c->L, (u64 *)D->eq_add[i]};
-            STATUS_TRY(op_affine(c, feats->cts[i], lm, &la, &nodes[k].lt, fork_stream(c, 2 * k, lane)));
-            STATUS_TRY(op_affine(c, feats->cts[i], em, &ea, &nodes[k].eq, fork_stream(c, 2 * k + 1, lane)));
+            STATUS_TRY(op_affine(c, x[i], lm, &la, &nodes[k].lt, fork_stream(c, 2 * k, lane)));
+            STATUS_TRY(op_affine(c, x[i], em, &ea, &nodes[k].eq, fork_stream(c, 2 * k + 1, lane)));
         }
         STATUS_TRY(fork_join(c, s, 2 * p, lane));
     } else {
@@ -474,16 +464,16 @@ static copse_status infer_impl(copse_ctx *c, const copse_evk *evk, copse_model *
             const cudaStream_t fs = fork_stream(c, k, lane);
             DCt &Y = tmp[4 * k], &xy = tmp[4 * k + 1], &two = tmp[4 * k + 2], &sum = tmp[4 * k + 3];
             STATUS_TRY(enc_materialize(c, *m->enc, m->enc->idx_thr(i), &Y, fs));
-            STATUS_TRY(op_mul(c, evk, feats->cts[i], Y, &xy, fs));
+            STATUS_TRY(op_mul(c, evk, x[i], Y, &xy, fs));
             STATUS_TRY(op_add(c, Y, xy, &nodes[k].lt, true, fs));
             STATUS_TRY(op_add(c, xy, xy, &two, false, fs));
-            STATUS_TRY(op_add(c, feats->cts[i], Y, &sum, false, fs));
+            STATUS_TRY(op_add(c, x[i], Y, &sum, false, fs));
             STATUS_TRY(op_add(c, two, sum, &nodes[k].eq, true, fs));
             STATUS_TRY(op_add_one(c, nodes[k].eq, fs));
         }
         STATUS_TRY(fork_join(c, s, p, lane));
-        for (DCt &x : tmp)
-            if (x.data) ct_free(&x, s);
+        for (DCt &t : tmp)
+            if (t.data) ct_free(&t, s);
     }
     // balanced combine (lt_h + eq_h lt_l, eq_h eq_l); no eq at the root
     while (nodes.size() > 1) {
@@ -512,43 +502,99 @@ static copse_status infer_impl(copse_ctx *c, const copse_evk *evk, copse_model *
         if (nodes.size() % 2) nx.push_back(nodes.back());
         nodes.swap(nx);
     }
-    DCt Dc = nodes[0].lt;
+    *Dc = nodes[0].lt;
     if (nodes[0].eq.data) ct_free(&nodes[0].eq, s);
-    if (Dc.level != (enc ? m->enc->lvl_D : D->lvl_D)) {
+    if (Dc->level != (enc ? m->enc->lvl_D : D->lvl_D)) {
         set_error("internal: unexpected level of the decision vector");
         return COPSE_EINVAL;
     }
+    return COPSE_OK;
+}
+
+// Algorithm 1 for every query ciphertext of `feats` (p feature planes each, one
+// ciphertext after another): one result ciphertext per query ciphertext.  With an
+// encrypted model the matrix products of all query ciphertexts run together, so
+// each encrypted diagonal is read and its mask regenerated once for all of them.
+static copse_status infer_multi(copse_ctx *c, const copse_evk *evk, copse_model *m, const copse_ctbuf *feats,
+                                std::vector<DCt> &results, cudaStream_t s, int lane = 0,
+                                cudaEvent_t *stage_ev = nullptr) {
+    const bool enc = m->f.encrypted;
+    if (enc) {
+        if (!m->enc || m->enc->ctx_serial != c->serial) {
+            set_error("encrypted-mode model has no encryption on this context (copse_encrypt_model)");
+            return COPSE_EINVAL;
+        }
+        if (m->enc->g_r != m->f.g_reshuffle || m->enc->g_l != m->f.g_level) {
+            set_error("model was encrypted for another baby-step plan");
+            return COPSE_EINVAL;
+        }
+    } else {
+        STATUS_TRY(upload_model(c, m, s));
+    }
+    const DeviceModel *D = m->dev.get();
+    const int p = (int)m->f.precision;
+    const size_t n_in = feats->cts.size();
+    if (n_in == 0 || n_in % (size_t)p) { set_error("feature buffer does not hold p ciphertexts per query ciphertext"); return COPSE_EINVAL; }
+    for (const DCt &x : feats->cts)
+        if (x.level != c->L) { set_error("feature ciphertexts must be fresh"); return COPSE_EINVAL; }
+    const int nct = (int)(n_in / p);
+    // stage boundaries (comparison | reshuffle | levels | aggregation), when timed
+    auto mark = [&](int i) -> copse_status {
+        if (stage_ev) CUDA_TRY(cudaEventRecord(stage_ev[i], s));
+        return COPSE_OK;
+    };
+    STATUS_TRY(mark(0));
+    std::vector<DCt> Dc(nct);
+    for (int q = 0; q < nct; q++) STATUS_TRY(seccomp_one(c, evk, m, &feats->cts[(size_t)q * p], &Dc[q], s, lane));
     STATUS_TRY(mark(1));
     // reshuffle: Branches = R_ext * Decisions
-    std::vector<DCt> br;
-    if (enc)
+    std::vector<std::vector<DCt>> br(nct);
+    if (enc) {
         STATUS_TRY(enc_matmul(c, evk, *m->enc, Dc, 0, br, s));
-    else
-        STATUS_TRY(group_matmul(c, evk, Dc, D->R, {nullptr}, br, s));
-    ct_free(&Dc, s);
+    } else {
+        for (int q = 0; q < nct; q++) STATUS_TRY(group_matmul(c, evk, Dc[q], D->R, {nullptr}, br[q], s));
+    }
+    for (DCt &x : Dc) ct_free(&x, s);
     STATUS_TRY(mark(2));
     // levels: Lvl_k * Branches XOR Mask_k, rotations of Branches shared by every level
-    std::vector<DCt> lv;
-    if (enc)
-        STATUS_TRY(enc_matmul(c, evk, *m->enc, br[0], 1, lv, s));
-    else
-        STATUS_TRY(group_matmul(c, evk, br[0], D->Lv, D->mask, lv, s));
-    ct_free(&br[0], s);
+    std::vector<std::vector<DCt>> lvs(nct);
+    std::vector<DCt> B(nct);
+    for (int q = 0; q < nct; q++) B[q] = br[q][0];
+    if (enc) {
+        STATUS_TRY(enc_matmul(c, evk, *m->enc, B, 1, lvs, s));
+    } else {
+        for (int q = 0; q < nct; q++) STATUS_TRY(group_matmul(c, evk, B[q], D->Lv, D->mask, lvs[q], s));
+    }
+    for (DCt &x : B) ct_free(&x, s);
     STATUS_TRY(mark(3));
     // product across levels, balanced
-    while (lv.size() > 1) {
-        const int npair = (int)(lv.size() / 2);
-        std::vector<DCt> nx(npair);
-        STATUS_TRY(fork_begin(c, s, npair, lane));
-        for (int k = 0; k < npair; k++)
-            STATUS_TRY(op_mul(c, evk, lv[2 * k], lv[2 * k + 1], &nx[k], fork_stream(c, k, lane)));
-        STATUS_TRY(fork_join(c, s, npair, lane));
-        for (int k = 0; k < 2 * npair; k++) ct_free(&lv[k], s);
-        if (lv.size() % 2) nx.push_back(lv.back());
-        lv.swap(nx);
+    results.assign(nct, DCt());
+    for (int q = 0; q < nct; q++) {
+        std::vector<DCt> &lv = lvs[q];
+        while (lv.size() > 1) {
+            const int npair = (int)(lv.size() / 2);
+            std::vector<DCt> nx(npair);
+            STATUS_TRY(fork_begin(c, s, npair, lane));
+            for (int k = 0; k < npair; k++)
+                STATUS_TRY(op_mul(c, evk, lv[2 * k], lv[2 * k + 1], &nx[k], fork_stream(c, k, lane)));
+            STATUS_TRY(fork_join(c, s, npair, lane));
+            for (int k = 0; k < 2 * npair; k++) ct_free(&lv[k], s);
+            if (lv.size() % 2) nx.push_back(lv.back());
+            lv.swap(nx);
+        }
+        results[q] = lv[0];
     }
     STATUS_TRY(mark(4));
-    *result = lv[0];
+    return COPSE_OK;
+}
+
+// one query ciphertext (graph-recorded session items)
+static copse_status infer_impl(copse_ctx *c, const copse_evk *evk, copse_model *m, const copse_ctbuf *feats,
+                               DCt *result, cudaStream_t s, int lane = 0) {
+    if (feats->cts.size() != m->f.precision) { set_error("feature buffer does not hold one ciphertext per bit-plane"); return COPSE_EINVAL; }
+    std::vector<DCt> r;
+    STATUS_TRY(infer_multi(c, evk, m, feats, r, s, lane));
+    *result = r[0];
     return COPSE_OK;
 }
 
@@ -558,9 +604,7 @@ extern "C" copse_status copse_infer(copse_ctx *c, const copse_evk *evk, copse_mo
     auto buf = std::make_unique<copse_ctbuf>();
     buf->ctx = c;
     buf->stream = as_stream(stream);
-    DCt r;
-    STATUS_TRY(infer_impl(c, evk, m, feats, &r, as_stream(stream)));
-    buf->cts.push_back(r);
+    STATUS_TRY(infer_multi(c, evk, m, feats, buf->cts, as_stream(stream)));
     *out = buf.release();
     return COPSE_OK;
 }
@@ -575,21 +619,22 @@ extern "C" copse_status copse_infer_timed(copse_ctx *c, const copse_evk *evk, co
     copse_status st = COPSE_OK;
     for (int i = 0; i < 5 && st == COPSE_OK; i++)
         if (cudaEventCreate(&ev[i]) != cudaSuccess) { set_error("cudaEventCreate failed"); st = COPSE_ECUDA; }
-    DCt r;
-    if (st == COPSE_OK) st = infer_impl(c, evk, m, feats, &r, s, 0, ev);
+    std::vector<DCt> r;
+    if (st == COPSE_OK) st = infer_multi(c, evk, m, feats, r, s, 0, ev);
     if (st == COPSE_OK && cudaEventSynchronize(ev[4]) != cudaSuccess) { set_error("stage event failed"); st = COPSE_ECUDA; }
     for (int i = 0; i < 4 && st == COPSE_OK; i++)
         if (cudaEventElapsedTime(&stage_ms[i], ev[i], ev[i + 1]) != cudaSuccess) { set_error("stage timing failed"); st = COPSE_ECUDA; }
     for (cudaEvent_t e : ev)
         if (e) cudaEventDestroy(e);
     if (st != COPSE_OK) {
-        if (r.data) ct_free(&r, s);
+        for (DCt &x : r)
+            if (x.data) ct_free(&x, s);
         return st;
     }
     auto buf = std::make_unique<copse_ctbuf>();
     buf->ctx = c;
     buf->stream = s;
-    buf->cts.push_back(r);
+    buf->cts = r;
     *out = buf.release();
     return COPSE_OK;
 }
@@ -599,14 +644,20 @@ extern "C" copse_status copse_decrypt_labels(copse_ctx *c, const copse_keys *k, 
                                              void *stream) {
     if (!c || !k || !m || !res || res->cts.empty() || (nq && !out_bits)) { set_error("null argument"); return COPSE_EINVAL; }
     const CompiledForest &f = m->f;
-    if (nq > (size_t)(c->N / f.block)) { set_error("more queries than slot blocks"); return COPSE_EINVAL; }
+    const size_t per_ct = (size_t)(c->N / f.block);
+    if (nq > per_ct * res->cts.size()) { set_error("more queries than slot blocks"); return COPSE_EINVAL; }
     cudaStream_t s = as_stream(stream);
     u64 *slots = nullptr;
     uint8_t *bits = on_device ? out_bits : nullptr;
     STATUS_TRY(dev_alloc(c, (void **)&slots, (size_t)c->N * 8, s));
     if (!on_device) STATUS_TRY(dev_alloc(c, (void **)&bits, std::max<size_t>(nq * f.L, 1), s));
-    STATUS_TRY(decrypt_slots_dev(c, k, res->cts[0], slots, s));
-    STATUS_TRY(extract_bits(c, slots, (int)nq, (int)f.block, (int)f.L, bits, s));
+    // query j is block j mod per_ct of result ciphertext j / per_ct
+    for (size_t j0 = 0, q = 0; j0 < nq || (nq == 0 && q == 0); j0 += per_ct, q++) {
+        const size_t n = std::min(per_ct, nq - j0);
+        STATUS_TRY(decrypt_slots_dev(c, k, res->cts[q], slots, s));
+        STATUS_TRY(extract_bits(c, slots, (int)n, (int)f.block, (int)f.L, bits + j0 * f.L, s));
+        if (nq == 0) break;
+    }
     if (!on_device) {
         CUDA_TRY(cudaMemcpyAsync(out_bits, bits, nq * f.L, cudaMemcpyDeviceToHost, s));
         dev_free(bits, s);

@@ -19,8 +19,9 @@
 namespace {
 
 constexpr int TPB = 256;
-constexpr int EM_ACC = 8;      // accumulators per MAC launch
+constexpr int EM_ACC = 8;      // accumulators per MAC launch (the table's capacity)
 constexpr int EM_BABY = 16;    // baby steps per MAC launch
+constexpr int EM_GROUP = 8;    // query ciphertexts whose rotations are held at once
 constexpr int EM_CHUNK = 256;  // model ciphertexts encrypted per batch
 constexpr u64 MODEL_STREAM = 0x800000ull;
 
@@ -80,47 +81,129 @@ __global__ void k_materialize(const u64 *c0, u64 *out, int ell, u64 seed, u64 st
 }
 
 // Ciphertext x ciphertext products summed per accumulator, before relinearisation:
-// for each element (r, k) and every (accumulator x, baby step j) of the launch,
-//   (acc0, acc1, acc2) += (d0 R0, d0 R1 + d1 R0, d1 R1),
-// d = the encrypted diagonal (c0 read, c1 regenerated), R = rot(v, j).
+// for each element (r, k), every accumulator x and query ciphertext b of the
+// thread's tile and every baby step j of the launch,
+//   (acc0, acc1, acc2)[b][x] += (d0 R0, d0 R1 + d1 R0, d1 R1),
+// d = the encrypted diagonal of (x, j) (c0 read, c1 regenerated once for all
+// query ciphertexts), R = rot(v_b, j) (read once for all accumulators).
 struct EncMacTable {
     const u64 *c0[EM_ACC * EM_BABY];  // [acc][baby], null = no such diagonal
     u64 stream[EM_ACC * EM_BABY];
-    const u64 *R[EM_BABY];            // [2][ell][N]
-    u64 *acc[EM_ACC];                 // [3][ell][N]
 };
 
-__global__ void __launch_bounds__(256) k_enc_mac(const EncMacTable tab, int na, int nb, int ell, int logN, u64 seed,
+// 128-bit accumulator: the products of one launch (each < 4 q^2 < 2^122, at most
+// EM_BABY of them per accumulator, < 2^126) are summed exactly and reduced once.
+struct Acc128 {
+    u64 lo, hi;
+};
+__device__ __forceinline__ void mac128(Acc128 &a, u64 x, u64 y) {
+    const u64 plo = x * y, phi = __umul64hi(x, y);
+    a.lo += plo;
+    a.hi += phi + (a.lo < plo);
+}
+__device__ __forceinline__ u64 reduce128(const Acc128 &a, const PrimeDev &P) {
+    return add_mod(mul_shoup(barrett_wide(0, a.hi, P), P.r64, P.r64_sh, P.q), barrett_wide(0, a.lo, P), P.q);
+}
+
+// R: rotations [query ct][baby][2][ell][N] from the launch's first baby (r_ct words per
+// query ciphertext); acc: [query ct][acc][3][ell][N] from the launch's first accumulator
+// (a_ct words per query ciphertext).  A thread holds a register tile of TA
+// accumulators x TQ query ciphertexts for one element; blockIdx.y = group of TQ
+// query ciphertexts, blockIdx.z = group of TA accumulators.  The next baby step's
+// rotations and diagonal words are loaded while the current one is multiplied.
+template <int TA, int TQ>
+__global__ void __launch_bounds__(128) k_enc_mac(const EncMacTable tab, int na, int nb, int nq, const u64 *R,
+                                                 size_t r_ct, u64 *acc, size_t a_ct, int ell, int logN, u64 seed,
                                                  const PrimeDev *pr) {
     const size_t n_el = (size_t)ell << logN;
     const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n_el) return;
+    const int q0 = (int)blockIdx.y * TQ, nc = min(TQ, nq - q0);
+    const int x0 = (int)blockIdx.z * TA, nx = min(TA, na - x0);
     const int r = (int)(e >> logN);
     const uint32_t k = (uint32_t)(e & ((1ull << logN) - 1));
     const PrimeDev P = pr[r];
-    u64 a0[EM_ACC], a1[EM_ACC], a2[EM_ACC];
-    for (int x = 0; x < na; x++) {
-        a0[x] = tab.acc[x][e];
-        a1[x] = tab.acc[x][n_el + e];
-        a2[x] = tab.acc[x][2 * n_el + e];
-    }
+    // Karatsuba: P0 = sum d0 R0, P2 = sum d1 R1, S = sum (d0 + d1)(R0 + R1), and the
+    // middle component is S - P0 - P2 (sums < 2q, products < 2^122, at most EM_BABY terms)
+    Acc128 a[TQ][TA][3];
+#pragma unroll
+    for (int b = 0; b < TQ; b++)
+#pragma unroll
+        for (int x = 0; x < TA; x++)
+#pragma unroll
+            for (int c = 0; c < 3; c++) a[b][x][c] = Acc128{0, 0};
+    u64 R0[TQ], R1[TQ], D0[TA];
+    auto load = [&](int j, u64 *r0, u64 *r1, u64 *d0) {
+#pragma unroll
+        for (int b = 0; b < TQ; b++) {
+            const u64 *Rb = R + (size_t)(q0 + b) * r_ct + (size_t)j * 2 * n_el;
+            r0[b] = b < nc ? Rb[e] : 0;
+            r1[b] = b < nc ? Rb[n_el + e] : 0;
+        }
+#pragma unroll
+        for (int x = 0; x < TA; x++) {
+            const u64 *p = x < nx ? tab.c0[(x0 + x) * nb + j] : nullptr;
+            d0[x] = p ? p[e] : 0;
+        }
+    };
+    load(0, R0, R1, D0);
     for (int j = 0; j < nb; j++) {
-        const u64 R0 = tab.R[j][e], R1 = tab.R[j][n_el + e];
-        for (int x = 0; x < na; x++) {
-            const u64 *p = tab.c0[x * nb + j];
-            if (!p) continue;
-            const u64 d0 = p[e];
-            const u64 d1 = seeded_mask(seed, tab.stream[x * nb + j], r, k, logN, P);
-            a0[x] = add_mod(a0[x], mul_mod(d0, R0, P), P.q);
-            a1[x] = add_mod(a1[x], add_mod(mul_mod(d0, R1, P), mul_mod(d1, R0, P), P.q), P.q);
-            a2[x] = add_mod(a2[x], mul_mod(d1, R1, P), P.q);
+        u64 N0[TQ], N1[TQ], ND[TA];
+        if (j + 1 < nb) load(j + 1, N0, N1, ND);
+        u64 RS[TQ];
+#pragma unroll
+        for (int b = 0; b < TQ; b++) RS[b] = R0[b] + R1[b];
+#pragma unroll
+        for (int x = 0; x < TA; x++) {
+            if (x >= nx || !tab.c0[(x0 + x) * nb + j]) continue;
+            const u64 d0 = D0[x];
+            const u64 d1 = seeded_mask(seed, tab.stream[(x0 + x) * nb + j], r, k, logN, P);
+            const u64 ds = d0 + d1;
+#pragma unroll
+            for (int b = 0; b < TQ; b++) {
+                mac128(a[b][x][0], d0, R0[b]);
+                mac128(a[b][x][1], ds, RS[b]);
+                mac128(a[b][x][2], d1, R1[b]);
+            }
+        }
+        if (j + 1 < nb) {
+#pragma unroll
+            for (int b = 0; b < TQ; b++) {
+                R0[b] = N0[b];
+                R1[b] = N1[b];
+            }
+#pragma unroll
+            for (int x = 0; x < TA; x++) D0[x] = ND[x];
         }
     }
-    for (int x = 0; x < na; x++) {
-        tab.acc[x][e] = a0[x];
-        tab.acc[x][n_el + e] = a1[x];
-        tab.acc[x][2 * n_el + e] = a2[x];
-    }
+#pragma unroll
+    for (int b = 0; b < TQ; b++)
+#pragma unroll
+        for (int x = 0; x < TA; x++)
+            if (b < nc && x < nx) {
+                u64 *o = acc + (size_t)(q0 + b) * a_ct + (size_t)(x0 + x) * 3 * n_el + e;
+                const u64 p0 = reduce128(a[b][x][0], P), p2 = reduce128(a[b][x][2], P);
+                const u64 mid = sub_mod(sub_mod(reduce128(a[b][x][1], P), p0, P.q), p2, P.q);
+                o[0] = add_mod(o[0], p0, P.q);
+                o[n_el] = add_mod(o[n_el], mid, P.q);
+                o[2 * n_el] = add_mod(o[2 * n_el], p2, P.q);
+            }
+}
+
+// register tile by the number of query ciphertexts multiplied together
+template <int TA, int TQ>
+void launch_mac(const EncMacTable &tab, int na, int nb, int nq, const u64 *R, size_t r_ct, u64 *acc, size_t a_ct,
+                int ell, int logN, u64 seed, const PrimeDev *pr, cudaStream_t s) {
+    const size_t n_el = (size_t)ell << logN;
+    const dim3 grid((unsigned)((n_el + 127) / 128), (unsigned)((nq + TQ - 1) / TQ), (unsigned)((na + TA - 1) / TA));
+    k_enc_mac<TA, TQ><<<grid, 128, 0, s>>>(tab, na, nb, nq, R, r_ct, acc, a_ct, ell, logN, seed, pr);
+}
+
+void enc_mac(const EncMacTable &tab, int na, int nb, int nq, const u64 *R, size_t r_ct, u64 *acc, size_t a_ct,
+             int ell, int logN, u64 seed, const PrimeDev *pr, cudaStream_t s) {
+    if (nq == 1) launch_mac<4, 1>(tab, na, nb, nq, R, r_ct, acc, a_ct, ell, logN, seed, pr, s);
+    else if (nq == 2) launch_mac<2, 2>(tab, na, nb, nq, R, r_ct, acc, a_ct, ell, logN, seed, pr, s);
+    else launch_mac<1, 4>(tab, na, nb, nq, R, r_ct, acc, a_ct, ell, logN, seed, pr, s);
 }
 
 }  // namespace
@@ -215,67 +298,86 @@ copse_status enc_materialize(copse_ctx *c, const EncModel &E, int idx, DCt *out,
     return COPSE_OK;
 }
 
-copse_status enc_matmul(copse_ctx *c, const copse_evk *evk, const EncModel &E, const DCt &v, int kind,
-                        std::vector<DCt> &out, cudaStream_t s) {
+copse_status enc_matmul(copse_ctx *c, const copse_evk *evk, const EncModel &E, const std::vector<DCt> &v, int kind,
+                        std::vector<std::vector<DCt>> &out, cudaStream_t s) {
     const BsgsGroup &G = kind == 0 ? E.grpR : E.grpL;
-    const int ell = v.level, N = c->N;
-    if (ell != (kind == 0 ? E.lvl_D : E.lvl_B)) { set_error("internal: vector at an unexpected level"); return COPSE_EINVAL; }
-    const int nb = (int)G.baby.size(), nacc = (int)G.acc.size();
-    const size_t per = (size_t)2 * ell * N, per3 = (size_t)3 * ell * N;
-    Scratch sc(s);
-    // baby steps: rotations of v (one ModUp shared by all)
-    u64 *Rb = nullptr, *acc3 = nullptr, *inner = nullptr;
-    STATUS_TRY(sc.get(c, &Rb, (size_t)nb * per));
-    STATUS_TRY(op_rotations(c, evk, v, G.baby, Rb, s));
-    // per (matrix, giant step): sum_j Enc(d'_{k, j}) x rot(v, j), three components
-    STATUS_TRY(sc.get(c, &acc3, (size_t)nacc * per3));
-    CUDA_TRY(cudaMemsetAsync(acc3, 0, (size_t)nacc * per3 * sizeof(u64), s));
-    for (int a0 = 0; a0 < nacc; a0 += EM_ACC) {
-        const int na = std::min(EM_ACC, nacc - a0);
-        for (int x0 = 0; x0 < nb; x0 += EM_BABY) {
-            const int nbb = std::min(EM_BABY, nb - x0);
-            EncMacTable tab;
-            memset(&tab, 0, sizeof(tab));
-            int present = 0;
-            for (int x = 0; x < nbb; x++) tab.R[x] = Rb + (size_t)(x0 + x) * per;
-            for (int a = 0; a < na; a++) {
-                const BsgsGroup::Acc &A = G.acc[a0 + a];
-                tab.acc[a] = acc3 + (size_t)(a0 + a) * per3;
-                for (int x = 0; x < nbb; x++) {
-                    const int i = A.diag[x0 + x];
-                    if (i < 0) continue;
-                    const int idx = kind == 0 ? E.idx_R(i) : E.idx_lvl((int)A.mat + 1, i);
-                    tab.c0[a * nbb + x] = E.c0(idx);
-                    tab.stream[a * nbb + x] = MODEL_STREAM + 2ull * (u64)idx;
-                    present++;
-                }
-            }
-            if (!present) continue;
-            TIMED("enc_mac", 8.0 * N * ell * ((double)present + 2.0 * nbb + 6.0 * na), s,
-                  k_enc_mac<<<nblk((size_t)ell * N), TPB, 0, s>>>(tab, na, nbb, ell, c->logN, E.seed, c->d_prime));
-            LAUNCH_CHECK();
-        }
-    }
-    // one relinearisation per accumulator, then the giant steps (+ the encrypted masks)
-    STATUS_TRY(sc.get(c, &inner, (size_t)nacc * per));
-    STATUS_TRY(relin_batch(c, evk, acc3, nacc, ell, inner, s));
+    const int N = c->N, nv = (int)v.size();
+    if (nv == 0) return COPSE_OK;
+    const int ell = v[0].level;
+    for (const DCt &x : v)
+        if (x.level != (kind == 0 ? E.lvl_D : E.lvl_B)) { set_error("internal: vector at an unexpected level"); return COPSE_EINVAL; }
+    const int nb = (int)G.baby.size(), nacc = (int)G.acc.size(), n_mat = (int)G.n_mat;
+    const size_t n_el = (size_t)ell * N, per = 2 * n_el, per3 = 3 * n_el;
+    out.assign(nv, std::vector<DCt>(n_mat));
+    // encrypted masks of the level products
     std::vector<DCt> masks;
-    std::vector<const u64 *> add_ct;
     copse_status st = COPSE_OK;
     if (kind == 1) {
         masks.assign(E.d, DCt());
-        for (int k = 1; k <= E.d && st == COPSE_OK; k++) {
-            st = enc_materialize(c, E, E.idx_mask(k), &masks[k - 1], s);
-            add_ct.push_back(masks[k - 1].data);
+        for (int k = 1; k <= E.d && st == COPSE_OK; k++) st = enc_materialize(c, E, E.idx_mask(k), &masks[k - 1], s);
+    }
+    for (int g0 = 0; g0 < nv && st == COPSE_OK; g0 += EM_GROUP) {
+        const int ng = std::min(EM_GROUP, nv - g0);
+        Scratch sc(s);
+        // baby steps: rotations of every query ciphertext of the group (one ModUp each)
+        u64 *Rb = nullptr;
+        if ((st = sc.get(c, &Rb, (size_t)ng * nb * per))) break;
+        for (int q = 0; q < ng && st == COPSE_OK; q++) st = op_rotations(c, evk, v[g0 + q], G.baby, Rb + (size_t)q * nb * per, s);
+        // matrix by matrix: products, relinearisation, giant steps (+ mask)
+        for (int a = 0; a < n_mat && st == COPSE_OK; a++) {
+            int x0 = 0;
+            while (x0 < nacc && (int)G.acc[x0].mat != a) x0++;
+            int x1 = x0;
+            while (x1 < nacc && (int)G.acc[x1].mat == a) x1++;
+            const int nm = x1 - x0;
+            Scratch sm(s);
+            u64 *acc3 = nullptr, *inner = nullptr;
+            if ((st = sm.get(c, &acc3, (size_t)ng * nm * per3))) break;
+            if ((st = sm.get(c, &inner, (size_t)ng * nm * per))) break;
+            if (cudaMemsetAsync(acc3, 0, (size_t)ng * nm * per3 * sizeof(u64), s) != cudaSuccess) {
+                set_error("cudaMemsetAsync failed");
+                st = COPSE_ECUDA;
+                break;
+            }
+            for (int y0 = 0; y0 < nm; y0 += EM_ACC) {
+                const int na = std::min(EM_ACC, nm - y0);
+                for (int j0 = 0; j0 < nb; j0 += EM_BABY) {
+                    const int nbb = std::min(EM_BABY, nb - j0);
+                    EncMacTable tab;
+                    memset(&tab, 0, sizeof(tab));
+                    int present = 0;
+                    for (int y = 0; y < na; y++) {
+                        const BsgsGroup::Acc &A = G.acc[x0 + y0 + y];
+                        for (int j = 0; j < nbb; j++) {
+                            const int i = A.diag[j0 + j];
+                            if (i < 0) continue;
+                            const int idx = kind == 0 ? E.idx_R(i) : E.idx_lvl((int)A.mat + 1, i);
+                            tab.c0[y * nbb + j] = E.c0(idx);
+                            tab.stream[y * nbb + j] = MODEL_STREAM + 2ull * (u64)idx;
+                            present++;
+                        }
+                    }
+                    if (!present) continue;
+                    TIMED("enc_mac", 8.0 * (double)n_el * ((double)present + 2.0 * nbb * ng + 6.0 * na * ng), s,
+                          enc_mac(tab, na, nbb, ng, Rb + (size_t)j0 * per, (size_t)nb * per, acc3 + (size_t)y0 * per3,
+                                  (size_t)nm * per3, ell, c->logN, E.seed, c->d_prime, s));
+                    LAUNCH_CHECK();
+                }
+            }
+            // one relinearisation per (query ciphertext, accumulator), then the giant steps
+            if ((st = relin_batch(c, evk, acc3, ng * nm, ell, inner, s))) break;
+            std::vector<int> acc_mat(nm, 0);
+            std::vector<uint32_t> acc_giant(nm);
+            for (int y = 0; y < nm; y++) acc_giant[y] = G.acc[x0 + y].giant;
+            std::vector<const u64 *> add_ct;
+            if (kind == 1) add_ct.push_back(masks[a].data);
+            for (int q = 0; q < ng && st == COPSE_OK; q++) {
+                std::vector<DCt> o;
+                st = giant_phase(c, evk, inner + (size_t)q * nm * per, ell, acc_mat, acc_giant, 1, {}, add_ct, o, s);
+                if (st == COPSE_OK) out[g0 + q][a] = o[0];
+            }
         }
     }
-    std::vector<int> acc_mat(nacc);
-    std::vector<uint32_t> acc_giant(nacc);
-    for (int x = 0; x < nacc; x++) {
-        acc_mat[x] = (int)G.acc[x].mat;
-        acc_giant[x] = G.acc[x].giant;
-    }
-    if (st == COPSE_OK) st = giant_phase(c, evk, inner, ell, acc_mat, acc_giant, (int)G.n_mat, {}, add_ct, out, s);
     for (DCt &m : masks)
         if (m.data) ct_free(&m, s);
     return st;

@@ -317,9 +317,10 @@ copse_status enc_model_build(copse_ctx *c, const copse_keys *keys, const Compile
                              cudaStream_t s);
 // the full ciphertext idx [2][level][N] (c1 regenerated) into a new buffer
 copse_status enc_materialize(copse_ctx *c, const EncModel &E, int idx, DCt *out, cudaStream_t s);
-// products of v with the encrypted reshuffle (kind 0) or level matrices and masks (kind 1)
-copse_status enc_matmul(copse_ctx *c, const copse_evk *evk, const EncModel &E, const DCt &v, int kind,
-                        std::vector<DCt> &out, cudaStream_t s);
+// products of each v[i] with the encrypted reshuffle (kind 0) or level matrices and masks
+// (kind 1): out[i][matrix]; the query ciphertexts share every diagonal read
+copse_status enc_matmul(copse_ctx *c, const copse_evk *evk, const EncModel &E, const std::vector<DCt> &v, int kind,
+                        std::vector<std::vector<DCt>> &out, cudaStream_t s);
 
 // Giant steps over per-accumulator ciphertexts inner [nacc][2][ell][N] (accumulators of
 // one matrix contiguous, giant steps ascending): per matrix a
@@ -351,7 +352,7 @@ copse_status keygen_dev(copse_ctx *c, u64 seed, const std::vector<u64> &galois, 
 // (d_seed: when set, the seed is read from that device word instead of `seed`)
 copse_status encrypt_planes(copse_ctx *c, const copse_keys *k, const uint32_t *d_feats, int nq, int nf, int K,
                             int q, int pd, int block, int p, u64 seed, std::vector<DCt> &out, cudaStream_t s,
-                            const u64 *d_seed = nullptr);
+                            const u64 *d_seed = nullptr, int index0 = 0);
 // decrypt to N slot values (device output, NTT(mod t) order remapped to slot order)
 copse_status decrypt_slots_dev(copse_ctx *c, const copse_keys *k, const DCt &ct, u64 *d_slots, cudaStream_t s);
 copse_status extract_bits(copse_ctx *c, const u64 *d_slots, int nq, int block, int L, uint8_t *d_bits,

@@ -502,7 +502,7 @@ __global__ void k_feature_planes(const uint32_t *feats, int nq, int nf, int K, i
 // encryption randomness of plane i (stream base 0x1000000 + 3 i):
 // u ternary, x0 = t e0 + m, x1 = t e1, as residues mod q_0..q_{L-1}; the seed is
 // read from device memory when seed_ptr is set (replayed graphs)
-__global__ void k_enc_prep(const u64 *mt, int p, u64 seed_val, const u64 *seed_ptr, int L, int logN, u64 t,
+__global__ void k_enc_prep(const u64 *mt, int p, int index0, u64 seed_val, const u64 *seed_ptr, int L, int logN, u64 t,
                            const PrimeDev *pr, u64 *U, u64 *X0, u64 *X1) {
     size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= ((size_t)p << logN)) return;
@@ -510,7 +510,8 @@ __global__ void k_enc_prep(const u64 *mt, int p, u64 seed_val, const u64 *seed_p
     const u64 seed = seed_ptr ? *seed_ptr + seed_val : seed_val;
     const int i = (int)(e >> logN);
     const u64 n = e & ((1ull << logN) - 1);
-    const u64 sb = 0x500000ull + 3ull * (u64)i;  // every stream id stays below 2^24: stream * 2^40 + idx never wraps
+    // encryption index index0 + i; every stream id stays below 2^24: stream * 2^40 + idx never wraps
+    const u64 sb = 0x500000ull + 3ull * (u64)(index0 + i);
     const i64 u = sample_small(seed, sb, n, 0);
     const i64 e0 = sample_small(seed, sb + 1, n, 1), e1 = sample_small(seed, sb + 2, n, 1);
     const u64 c = mt[e];
@@ -1206,7 +1207,7 @@ copse_status keygen_dev(copse_ctx *c, u64 seed, const std::vector<u64> &galois, 
 
 copse_status encrypt_planes(copse_ctx *c, const copse_keys *k, const uint32_t *d_feats, int nq, int nf, int K,
                             int q, int pd, int block, int p, u64 seed, std::vector<DCt> &out, cudaStream_t s,
-                            const u64 *d_seed) {
+                            const u64 *d_seed, int index0) {
     const int N = c->N, L = c->L;
     Scratch sc(s);
     u64 *mt = nullptr, *U = nullptr, *X0 = nullptr, *X1 = nullptr, *cts = nullptr;
@@ -1217,7 +1218,8 @@ copse_status encrypt_planes(copse_ctx *c, const copse_keys *k, const uint32_t *d
     k_feature_planes<<<nblk(N), TPB, 0, s>>>(d_feats, nq, nf, K, q, pd, block, p, c->logN, c->d_slot_index, mt);
     LAUNCH_CHECK();
     STATUS_TRY(ntt_inverse(c, batch(mt, N, p, 0, 1, 0, c->t_index()), s));
-    k_enc_prep<<<nblk((size_t)p * N), TPB, 0, s>>>(mt, p, seed, d_seed, L, c->logN, c->t, c->d_prime, U, X0, X1);
+    if (index0 < 0 || index0 + p > 0x100000) { set_error("encryption index out of range"); return COPSE_EINVAL; }
+    k_enc_prep<<<nblk((size_t)p * N), TPB, 0, s>>>(mt, p, index0, seed, d_seed, L, c->logN, c->t, c->d_prime, U, X0, X1);
     LAUNCH_CHECK();
     STATUS_TRY(ntt_forward(c, batch(U, (size_t)L * N, p, 0, L, L), s));
     STATUS_TRY(ntt_forward(c, batch(X0, (size_t)L * N, p, 0, L, L), s));
@@ -1225,8 +1227,7 @@ copse_status encrypt_planes(copse_ctx *c, const copse_keys *k, const uint32_t *d
     STATUS_TRY(dev_alloc(c, (void **)&cts, (size_t)p * 2 * L * N * 8, s));
     k_enc_combine<<<nblk((size_t)p * L * N), TPB, 0, s>>>(k->pk, U, X0, X1, cts, p, L, c->logN, c->d_prime);
     LAUNCH_CHECK();
-    // one allocation, p views; the first ciphertext owns it
-    out.clear();
+    // appended to `out`
     for (int i = 0; i < p; i++) {
         DCt ct;
         ct.level = L;

@@ -53,6 +53,7 @@ copse_status time_model(copse_ctx *c, copse_model *m, size_t nq, int reps, float
     Handles h;
     const copse_model *ms[1] = {m};
     STATUS_TRY(copse_keygen(c, 0x5eed, ms, 1, &h.k, &h.e));
+    if (copse_model_is_encrypted(m)) STATUS_TRY(copse_encrypt_model(c, h.k, m, 0xe7c));
     const std::vector<uint32_t> feats = timing_features(info, nq);
     STATUS_TRY(copse_encrypt_features(c, h.k, m, feats.data(), nq, 0, 0x7a11, &h.f, nullptr));
     std::vector<float> per[4], tot;

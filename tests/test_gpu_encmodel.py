@@ -116,3 +116,53 @@ def test_encrypted_model_n16384_labels_and_session():
         K.copse_model_destroy(model)
     finally:
         K.copse_ctx_destroy(ctx)
+
+
+@pytest.mark.parametrize("encrypted", [True, False])
+def test_several_query_ciphertexts_match_oracle(encrypted):
+    """More queries than one ciphertext holds: query ciphertext c is encrypted with
+    indices c p + i and inferred with the others (sharing every encrypted diagonal
+    read); each result equals the oracle's for that ciphertext."""
+    text, p, nf, g = CASES[0]
+    logN, bits = 10, 50
+    om = Cp.compile_forest(text, p, nf)
+    L = Cp.levels_needed(om) + 1
+    P = B.Params(logN=logN, L=L, bits=bits, dnum=3)
+    per_ct = P.N // om.block
+    nq = 5 * per_ct + 3                       # six ciphertexts, the last one partly filled
+    qs = synth.random_queries(808, nq, nf, p)
+    ctx = K.copse_ctx_create(logN, bits, L, 3)
+    try:
+        model = K.copse_compile_forest(text, p, nf, logN)
+        K.copse_model_set_encrypted(model, encrypted)
+        K.copse_model_set_bsgs(model, *g)
+        keys, evk = K.copse_keygen(ctx, 31, [model])
+        if encrypted:
+            K.copse_encrypt_model(ctx, keys, model, 4040)
+        feats = K.copse_encrypt_features(ctx, keys, model, qs, 12)
+        assert K.copse_ctbuf_count(feats) == 6 * p
+        res = K.copse_infer(ctx, evk, model, feats)
+        assert K.copse_ctbuf_count(res) == 6
+        got = [K.copse_ctbuf_export(ctx, res, cq, P.N) for cq in range(6)]
+        labels = K.copse_decrypt_labels(ctx, keys, model, res, nq)
+        K.copse_ctbuf_destroy(res)
+        K.copse_ctbuf_destroy(feats)
+        K.copse_keys_destroy(keys)
+        K.copse_evk_destroy(evk)
+        K.copse_model_destroy(model)
+    finally:
+        K.copse_ctx_destroy(ctx)
+    _, trees = Cp.parse_forest(text)
+    for j in range(nq):
+        assert labels[j].tolist() == Cp.classify_plain(trees, qs[j]), f"query {j}"
+    bgv = B.Bgv(P)
+    if encrypted:
+        rs, ls = Cp.encrypted_rotation_sets(om, g)
+        okeys = bgv.keygen(31, sorted(set(B.galois_rot(logN, k) for k in rs + ls)))
+        E = Cp.BgvEngine(bgv, okeys, encrypted_model=True, enc_model=Cp.encrypt_model(bgv, okeys.sk, om, P.N, 4040, g))
+    else:
+        okeys = bgv.keygen(31, Cp.galois_elements(om, logN))
+        E = Cp.BgvEngine(bgv, okeys)
+    for cq in (0, 5):                          # the first and the partly filled last ciphertext
+        X = Cp.encrypt_queries(bgv, okeys, om, qs[cq * per_ct:(cq + 1) * per_ct], 12, cq * p)
+        assert_same(got[cq], Cp.infer(E, om, X, P.N), f"query ciphertext {cq}")
