@@ -38,7 +38,7 @@ UNIT = "inferences/s"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["cuda", "reference"], default="cuda")
     ap.add_argument("--workload", default="forest100-n16384")
@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--no-serving", action="store_true", help="skip the Poisson-arrival serving leg")
     ap.add_argument("--no-table6", action="store_true", help="skip the per-stage microbenchmark sweep")
     ap.add_argument("--no-tune", action="store_true", help="fixed schedule (dnum 3, plain products, cluster NTT)")
+    ap.add_argument("--schedule", default=None,
+                    help="dnum,g_reshuffle,g_level,ntt_cluster_max for the headline workload instead of tuning "
+                         "(e.g. the values a tuned run printed, to profile that schedule)")
     ap.add_argument("--no-encmodel", action="store_true", help="skip the encrypted-model leg")
     return ap.parse_args()
 
@@ -107,8 +110,9 @@ class Clocks:
         try:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                                          "-i", str(self.device), "-lms", "200"], stdout=self.f,
+                                          "-i", str(self.device), "-lms", "50"], stdout=self.f,
                                          stderr=subprocess.DEVNULL)
+            time.sleep(0.5)  # the sampler is running before the timed region starts
         except OSError:
             self.proc = None
 
@@ -150,10 +154,11 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def ncu_traffic(family, alg_bytes_per_launch):
-    """Per-launch DRAM bytes from the committed ncu summary of this kernel family, scaled from its
-    per-unit figure to a launch of `alg_bytes_per_launch` algorithmic bytes; None when the
-    summary is missing or was taken on a different source file than the one built now."""
+def ncu_traffic(family, alg_bytes_per_launch, key="dram_bytes_per_unit"):
+    """Per-launch DRAM bytes (or another per-unit counter, `key`) from the committed ncu summary
+    of this kernel family, scaled from its per-unit figure to a launch of `alg_bytes_per_launch`
+    algorithmic bytes; None when the summary is missing or was taken on a different source file
+    than the one built now."""
     path = os.path.join(ROOT, "profiles", f"{family}_traffic.md")
     try:
         lines = open(path).read().splitlines()
@@ -169,7 +174,7 @@ def ncu_traffic(family, alg_bytes_per_launch):
         if hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] != kv.get("source_sha256_16"):
             return None
         units = alg_bytes_per_launch / float(kv["unit_algorithmic_bytes"])
-        return float(kv["dram_bytes_per_unit"]) * units
+        return float(kv[key]) * units
     except (OSError, KeyError, ValueError):
         return None
 
@@ -186,11 +191,18 @@ def run_cuda(args, ws, rank, local):
     N = 1 << W.log_n
     model = K.copse_compile_forest(text, W.precision(), W.n_features(), W.log_n)
     dnum, tuning = W.dnum, None
-    if not args.no_tune:
+    sched = [int(x) for x in args.schedule.split(",")] if args.schedule else None
+    if sched:
+        dnum = sched[0]
+        K.copse_model_set_bsgs(model, sched[1], sched[2])
+        tuning = {"fixed_schedule": sched}
+    elif not args.no_tune:
         dnum, dn_ms = K.copse_tune_dnum(W.log_n, W.bits, W.primes, model, [1, 2, 3, 4], 1, 3, device=local)
         tuning = {"dnum_ms_per_inference": dn_ms}
     ctx = K.copse_ctx_create(W.log_n, W.bits, W.primes, dnum, device=local)
-    if not args.no_tune:
+    if sched:
+        K.copse_ctx_set_ntt_cluster_max(ctx, sched[3])
+    elif not args.no_tune:
         tuning.update(autotune(K, ctx, [model]))
     info = K.copse_model_info_get(model)
     keys, evk = K.copse_keygen(ctx, 7 + rank, [model])
@@ -341,11 +353,24 @@ def run_cuda(args, ws, rank, local):
         v = fam[top]
         achieved = v["bytes"] / (v["ms"] * 1e-3) / 1e9
         tr = ncu_traffic(top, v["bytes"] / v["launches"])
-        roof = {"kernel": top, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": tr,
-                "algorithmic_bytes_per_launch": v["bytes"] / v["launches"],
-                "avg_launch_us": v["ms"] * 1e3 / v["launches"], "peak_source": f"{how} hbm_gbs (copy)",
-                "measured_on": "instrumented host-launched replay of the timed step (CUDA events per launch)"}
+        hbm = {"achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+               "peak_source": f"{how} hbm_gbs (copy)"}
+        wi = ncu_traffic(top, v["bytes"] / v["launches"], key="warp_instructions_per_unit")
+        if wi is not None:
+            # integer issue roof: 152 SMs x 4 schedulers x 1 warp instruction per clock at the
+            # maximum SM clock; achieved = the ncu instruction count per unit scaled to the
+            # average launch, over its CUDA-event duration
+            peak_wi = 152 * 4 * 2.07e9 / 1e9
+            ach_wi = wi / (v["ms"] * 1e-3 / v["launches"]) / 1e9
+            roof = {"kernel": top, "bound": "alu", "achieved": ach_wi, "peak": peak_wi,
+                    "unit": "G warp-instructions/s", "frac": ach_wi / peak_wi, "traffic": tr, "hbm": hbm,
+                    "peak_source": "152 SMs x 4 schedulers x 1 warp instruction/clock x 2.07 GHz"}
+        else:
+            roof = {"kernel": top, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "frac": achieved / peaks["hbm_gbs"], "traffic": tr, "peak_source": f"{how} hbm_gbs (copy)"}
+        roof.update({"algorithmic_bytes_per_launch": v["bytes"] / v["launches"],
+                     "avg_launch_us": v["ms"] * 1e3 / v["launches"],
+                     "measured_on": "instrumented host-launched replay of the timed step (CUDA events per launch)"})
 
     serving = None if args.no_serving else run_serving(local, tune=not args.no_tune)
     batch3 = None if args.no_serving else run_batch3(local, tune=not args.no_tune)
@@ -708,26 +733,46 @@ class OracleBench:
         r = f(*a)
         return r, time.perf_counter() - s
 
-    def sample_small(self):
-        """One of each operation (encrypt of all planes, affine leaf, multiply, rotation, plaintext
-        product) -> seconds per inference."""
+    def _op(self, kind):
+        """Run and time one operation of the workload's inference (seconds)."""
         Cp, bgv, m = self.Cp, self.bgv, self.m
-        X, t_enc = self._clock(Cp.encrypt_queries, bgv, self.keys, m, self.qs, 99)
-        E = Cp.BgvEngine(bgv, self.keys)
-        Y = E.thresholds(m)
-        lt, t_aff = self._clock(E.affine, X[0], (-Y[0]) % E.t, Y[0])
-        _, t_mul = self._clock(E.mul, lt, lt)
-        lvl_D = self.P.L - 1 - (m.precision - 1).bit_length()
-        v = bgv.to_level(X[0], lvl_D)
+        if not hasattr(self, "_X"):
+            self._X = Cp.encrypt_queries(bgv, self.keys, m, self.qs, 99)
+            self._E = Cp.BgvEngine(bgv, self.keys)
+            self._Y = self._E.thresholds(m)
+            lvl_D = self.P.L - 1 - (m.precision - 1).bit_length()
+            self._v = bgv.to_level(self._X[0], lvl_D)
+        E, X, Y = self._E, self._X, self._Y
+        if kind == "enc":
+            return self._clock(Cp.encrypt_queries, bgv, self.keys, m, self.qs, 99)[1]
+        if kind == "affine":
+            return self._clock(E.affine, X[0], (-Y[0]) % E.t, Y[0])[1]
+        if kind == "mul":
+            return self._clock(E.mul, X[0], X[1 % len(X)])[1]
         k = self.rs[0]
-        r, t_rot = self._clock(E.rot, v, k)
-        _, t_pt = self._clock(E.mul_plain, r, self.Rd[k])
-        n = self.n
-        est = t_enc + n["affine"] * t_aff + n["mul"] * t_mul + n["rot"] * t_rot + n["pt"] * t_pt
-        return est, (f"oracle timed on one of each operation of the workload (encrypt of {m.precision} planes, "
-                     f"affine leaf, multiply, rotation at the reshuffle level, plaintext product); one inference "
-                     f"extrapolated with its exact counts ({n['affine']} affine, {n['mul']} multiplies, "
-                     f"{n['rot']} rotations, {n['pt']} plaintext products)")
+        if kind == "rot":
+            return self._clock(E.rot, self._v, k)[1]
+        return self._clock(E.mul_plain, self._v, self.Rd[k])[1]
+
+    def sample_small(self):
+        """One step of the reference arm: one operation of the workload timed (round robin over
+        encrypt of all planes, affine leaf, multiply, rotation, plaintext product; every one
+        timed once first), the inference time extrapolated from the latest time of each with
+        the inference's exact counts -> seconds per inference."""
+        kinds = ("enc", "affine", "mul", "rot", "pt")
+        if not hasattr(self, "_t"):
+            self._t = {kd: self._op(kd) for kd in kinds}
+            self._next = 0
+        else:
+            kd = kinds[self._next % len(kinds)]
+            self._t[kd] = self._op(kd)
+            self._next += 1
+        t, n, m = self._t, self.n, self.m
+        est = t["enc"] + n["affine"] * t["affine"] + n["mul"] * t["mul"] + n["rot"] * t["rot"] + n["pt"] * t["pt"]
+        return est, (f"oracle, one operation of the workload timed per step (round robin over encrypt of "
+                     f"{m.precision} planes, affine leaf, multiply, rotation at the reshuffle level, plaintext "
+                     f"product); one inference extrapolated with its exact counts ({n['affine']} affine, "
+                     f"{n['mul']} multiplies, {n['rot']} rotations, {n['pt']} plaintext products)")
 
     def sample_large(self, budget_s):
         """Encrypt and the whole SecComp, then reshuffle terms while the budget lasts -> s/inference."""

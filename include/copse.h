@@ -373,6 +373,8 @@ copse_status copse_poly_mul_noalloc(copse_ctx *ctx, const uint64_t *a, const uin
  * always, when that is the largest size timed) and the tiled form above. */
 copse_status copse_tune_ntt(copse_ctx *ctx, const uint32_t *sizes, size_t n, int reps, float *ms_cluster,
                             float *ms_tiled, uint32_t *max_cluster);
+/* Set the crossover copse_tune_ntt would choose (to replay a tuned schedule). */
+copse_status copse_ctx_set_ntt_cluster_max(copse_ctx *ctx, uint32_t max_cluster);
 
 /* Baby-step sizes (copse_model_set_bsgs): the reshuffle candidates g_r[] are
  * timed by the reshuffle stage with the level plan held, then the level

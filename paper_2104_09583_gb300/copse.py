@@ -63,6 +63,7 @@ _SIG = {
     "copse_model_export": (C.c_int, [vp, vp, vp, vp, vp, vp, vp]),
     "copse_model_rotations": (C.c_int, [vp, vp, vp]),
     "copse_model_set_bsgs": (C.c_int, [vp, C.c_uint32, C.c_uint32]),
+    "copse_ctx_set_ntt_cluster_max": (C.c_int, [vp, C.c_uint32]),
     "copse_model_set_encrypted": (C.c_int, [vp, C.c_int]),
     "copse_model_is_encrypted": (C.c_int, [vp]),
     "copse_encrypt_model": (C.c_int, [vp, vp, vp, C.c_uint64]),
@@ -221,6 +222,10 @@ def copse_tune_ntt(ctx, sizes=(4, 8, 16, 32, 64, 128, 256), reps=5):
     lim = C.c_uint32()
     _check(_lib.copse_tune_ntt(ctx, sz, len(sizes), reps, mc, mt, C.byref(lim)))
     return lim.value, {int(x): (float(mc[i]), float(mt[i])) for i, x in enumerate(sizes)}
+
+
+def copse_ctx_set_ntt_cluster_max(ctx, max_cluster):
+    _check(_lib.copse_ctx_set_ntt_cluster_max(ctx, max_cluster))
 
 
 def copse_tune_bsgs(ctx, model, g_r, g_l, n_queries=1, reps=3):

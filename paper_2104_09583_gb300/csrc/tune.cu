@@ -216,3 +216,9 @@ extern "C" copse_status copse_tune_dnum(const copse_params *base, int device, co
     }
     return COPSE_OK;
 }
+
+extern "C" copse_status copse_ctx_set_ntt_cluster_max(copse_ctx *c, uint32_t max_cluster) {
+    if (!c) { set_error("null context"); return COPSE_EINVAL; }
+    c->ntt_cluster_max = max_cluster >= (1u << 30) ? (1L << 30) : (long)max_cluster;
+    return COPSE_OK;
+}
