@@ -79,7 +79,8 @@ typedef struct copse_model_info {
     uint32_t block;       /* slots per query block (power of two >= L+b+q-2)          */
     uint32_t n_rot_reshuffle; /* nonzero rotation amounts of the reshuffle product   */
     uint32_t n_rot_level;     /* nonzero rotation amounts shared by the level products */
-    uint32_t levels_used; /* primes the circuit drops: 3 + ceil(log2 p) + ceil(log2 d) */
+    uint32_t levels_used; /* primes the circuit drops: 3 + ceil(log2 p) + ceil(log2 d) (+1 shuffled) */
+    uint32_t n_out;       /* result slots per query: n_leaves, or the shuffled and padded length */
 } copse_model_info;
 
 /* Message for the last failed call on this thread (never NULL). */
@@ -159,6 +160,21 @@ copse_status copse_model_get_bsgs(const copse_model *model, uint32_t *g_reshuffl
 copse_status copse_model_set_encrypted(copse_model *model, int on);
 int copse_model_is_encrypted(const copse_model *model);  /* 1 in encrypted-model mode, else 0 */
 copse_status copse_encrypt_model(copse_ctx *ctx, const copse_keys *keys, copse_model *model, uint64_t seed);
+
+/* Label shuffle with padding (Section 7.2, "Returning classification
+ * bitvectors"; the paper describes it and leaves it unimplemented): the server
+ * permutes the result bitvector by one more plaintext matrix product (diagonal
+ * method over signed shifts) and hands out the codebook permuted alike, padded
+ * with extra labels whose bits are always 0.  src[j] = the leaf output slot j
+ * carries (-1 = padding), codebook[j] = its class; every leaf exactly once,
+ * n_leaves <= n_out <= block; n_out = 0 turns the shuffle off.  Costs one more
+ * prime (levels_used + 1) and one rotation key per distinct shift; results,
+ * copse_decrypt_labels and sessions then give n_out bits per query (info.n_out).
+ * Host only; set before copse_keygen.  EINVAL on a malformed plan. */
+copse_status copse_model_set_shuffle(copse_model *model, const int32_t *src, size_t n_out, const uint32_t *codebook);
+/* The class of each result slot, classes[0..n_out): the codebook (leaf classes
+ * in preorder when not shuffled). */
+copse_status copse_model_codebook(const copse_model *model, uint32_t *classes);
 
 /* Model ciphertext `index` (threshold planes, reshuffle diagonals, level
  * diagonals level by level, masks) in coefficient form [2][level][N] into

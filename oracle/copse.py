@@ -377,11 +377,12 @@ def matmul(E, v, diag_sets, add_vecs, m: Model, N: int, g: int = 0):
     return out
 
 
-def infer(E, m: Model, X, N: int, g=(0, 0)):
+def infer(E, m: Model, X, N: int, g=(0, 0), shuffle=None):
     """Algorithm 1: SecComp, reshuffle, per-level product XOR mask, MultAll.
     Reading: the level products use Branches (the reshuffled vector, as the
     text of Section 4.3 says), not Decisions as the listing prints.
-    g = (baby-step size of the reshuffle, of the levels); 0 = plain diagonal method."""
+    g = (baby-step size of the reshuffle, of the levels); 0 = plain diagonal method.
+    shuffle = src of a label shuffle (shuffle_diagonals), applied to the result."""
     t = E.t
     Y = E.thresholds(m)
     D = seccomp(E, X, Y, m.precision)
@@ -389,11 +390,36 @@ def infer(E, m: Model, X, N: int, g=(0, 0)):
         em = E.enc_model
         Br = matmul_enc(E, D, [em["R"]], [None], em["g"][0])[0]
         res = matmul_enc(E, Br, em["levels"], em["masks"], em["g"][1])
-        return pairwise(res, lambda a, b, root: E.mul(a, b))
-    Br = matmul(E, D, [reshuffle_diagonals(m)], [None], m, N, g[0])[0]
-    Ld = [level_diagonals(m, k, t) for k in range(1, m.d + 1)]
-    res = matmul(E, Br, Ld, [tile_blocks(m, m.mask[k - 1], N) for k in range(1, m.d + 1)], m, N, g[1])
-    return pairwise(res, lambda a, b, root: E.mul(a, b))
+    else:
+        Br = matmul(E, D, [reshuffle_diagonals(m)], [None], m, N, g[0])[0]
+        Ld = [level_diagonals(m, k, t) for k in range(1, m.d + 1)]
+        res = matmul(E, Br, Ld, [tile_blocks(m, m.mask[k - 1], N) for k in range(1, m.d + 1)], m, N, g[1])
+    out = pairwise(res, lambda a, b, root: E.mul(a, b))
+    if shuffle is not None:
+        out = matmul(E, out, [shuffle_diagonals(m, shuffle, N)], [None], m, N)[0]
+    return out
+
+
+def shuffle_diagonals(m: Model, src, N: int):
+    """A server-side label shuffle with padding (Section 7.2, "Returning classification
+    bitvectors": a permutation of the result bitvector by a plaintext matrix product, the
+    codebook permuted alike, padded with extra labels).  Output slot j of a block takes leaf
+    src[j] (-1: a padding slot, always 0).  Diagonal method over signed shifts: the term with
+    shift k = src[j] - j is the rotation by k mod N/2 (a negative shift reads backwards inside
+    the block, since src[j] >= 0).  Returns {rotation amount: block-local diagonal}."""
+    assert len(src) <= m.block
+    h = N // 2
+    out = {}
+    for j, i in enumerate(src):
+        if i < 0:
+            continue
+        a = (int(i) - j) % h
+        out.setdefault(a, np.zeros(len(src), dtype=np.int64))[j] = 1
+    return out
+
+
+def shuffle_galois(m: Model, src, logN: int):
+    return sorted(set(B.galois_rot(logN, a) for a in shuffle_diagonals(m, src, 1 << logN) if a))
 
 
 # ---------------------------------------------------------------------------
@@ -636,18 +662,20 @@ def encrypt_queries(bgv: B.Bgv, keys: B.Keys, m: Model, queries, seed: int, inde
     return [bgv.encrypt_slots(keys.pk, planes[i], seed, index0 + i) for i in range(m.precision)]
 
 
-def decode_labels(m: Model, slots, n_queries: int):
-    """Result slots -> per query, one bit per leaf (Section 4.1.2, Classification Result)."""
+def decode_labels(m: Model, slots, n_queries: int, n_out: int = 0):
+    """Result slots -> per query, one bit per leaf (Section 4.1.2, Classification Result);
+    n_out output slots per query when the result was shuffled and padded."""
+    n_out = n_out or m.L
     out = []
     for j in range(n_queries):
-        v = np.asarray(slots[j * m.block: j * m.block + m.L], dtype=np.int64)
+        v = np.asarray(slots[j * m.block: j * m.block + n_out], dtype=np.int64)
         out.append(v.tolist())
     return out
 
 
-def levels_needed(m: Model, encrypted_model=False) -> int:
+def levels_needed(m: Model, encrypted_model=False, shuffle=False) -> int:
     """Primes dropped by the circuit under the canonical policy (plaintext model):
     1 (SecComp leaves) + ceil(log2 p) + 1 (reshuffle) + 1 (levels) + ceil(log2 d)."""
     def clog2(x):
         return (x - 1).bit_length() if x > 1 else 0
-    return (1 if not encrypted_model else 1) + clog2(m.precision) + 2 + clog2(m.d)
+    return (1 if not encrypted_model else 1) + clog2(m.precision) + 2 + clog2(m.d) + (1 if shuffle else 0)

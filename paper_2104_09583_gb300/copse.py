@@ -41,7 +41,7 @@ class copse_params(C.Structure):
 class copse_model_info(C.Structure):
     _fields_ = [(n, C.c_uint32) for n in (
         "n_features", "precision", "K", "q", "b", "n_leaves", "depth", "n_trees", "n_classes", "block",
-        "n_rot_reshuffle", "n_rot_level", "levels_used")]
+        "n_rot_reshuffle", "n_rot_level", "levels_used", "n_out")]
 
 
 vp = C.c_void_p
@@ -65,6 +65,8 @@ _SIG = {
     "copse_model_set_bsgs": (C.c_int, [vp, C.c_uint32, C.c_uint32]),
     "copse_ctx_set_ntt_cluster_max": (C.c_int, [vp, C.c_uint32]),
     "copse_model_set_encrypted": (C.c_int, [vp, C.c_int]),
+    "copse_model_set_shuffle": (C.c_int, [vp, vp, C.c_size_t, vp]),
+    "copse_model_codebook": (C.c_int, [vp, u32p]),
     "copse_model_is_encrypted": (C.c_int, [vp]),
     "copse_encrypt_model": (C.c_int, [vp, vp, vp, C.c_uint64]),
     "copse_encmodel_export": (C.c_int, [vp, vp, C.c_size_t, u64p, C.c_size_t]),
@@ -190,6 +192,23 @@ def copse_model_rotations(m):
 
 def copse_model_set_bsgs(m, g_reshuffle, g_level):
     _check(_lib.copse_model_set_bsgs(m, g_reshuffle, g_level))
+
+
+def copse_model_set_shuffle(m, src=None, codebook=None):
+    """src[j]: leaf of output slot j (-1 = padding); codebook[j]: its class; None turns it off."""
+    if src is None:
+        _check(_lib.copse_model_set_shuffle(m, None, 0, None))
+        return
+    a = np.ascontiguousarray(src, dtype=np.int32)
+    b = np.ascontiguousarray(codebook, dtype=np.uint32)
+    _check(_lib.copse_model_set_shuffle(m, a.ctypes.data_as(C.c_void_p), a.size, b.ctypes.data_as(C.c_void_p)))
+
+
+def copse_model_codebook(m):
+    i = copse_model_info_get(m)
+    out = np.zeros(max(i["n_out"], 1), np.uint32)
+    _check(_lib.copse_model_codebook(m, out))
+    return out[: i["n_out"]]
 
 
 def copse_model_set_encrypted(m, on=True):
@@ -322,7 +341,7 @@ def copse_decrypt_labels(ctx, keys, model, result, n_queries, stream=None, out_d
         _check(_lib.copse_decrypt_labels(ctx, keys, model, result, C.c_void_p(out_device_ptr), n_queries, 1,
                                          C.c_void_p(stream)))
         return None
-    L = copse_model_info_get(model)["n_leaves"]
+    L = copse_model_info_get(model)["n_out"]
     out = np.zeros(max(n_queries * L, 1), np.uint8)
     _check(_lib.copse_decrypt_labels(ctx, keys, model, result, _ptr(out), n_queries, 0, C.c_void_p(stream)))
     return out[: n_queries * L].reshape(n_queries, L)

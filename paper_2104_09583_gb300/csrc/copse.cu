@@ -44,11 +44,51 @@ struct DeviceModel {
     }
 };
 
+// The label shuffle's diagonal plaintexts (extended basis, at the level of the result)
+struct ShuffleDev {
+    uint64_t ctx_serial = 0;
+    std::vector<uint32_t> rots;
+    std::vector<std::vector<const u64 *>> pt;  // [1][rot]
+    u64 *store = nullptr;
+    ~ShuffleDev() {
+        if (store) cudaFree(store);
+    }
+};
+
 struct copse_model {
     CompiledForest f;
     std::unique_ptr<DeviceModel> dev;
-    std::unique_ptr<EncModel> enc;  // set by copse_encrypt_model
+    std::unique_ptr<EncModel> enc;       // set by copse_encrypt_model
+    std::unique_ptr<ShuffleDev> shuf;    // set on first use of a shuffled model
 };
+
+// level of Algorithm 1's result before the shuffle: Branches at lvl_D - 1, the level
+// products drop one more prime, MultAll ceil(log2 d)
+static int result_level(const copse_ctx *c, const CompiledForest &f) {
+    return c->L - 1 - (int)clog2u(f.precision) - 2 - (int)clog2u(f.d);
+}
+
+static copse_status upload_shuffle(copse_ctx *c, copse_model *m, cudaStream_t s) {
+    if (m->shuf && m->shuf->ctx_serial == c->serial) return COPSE_OK;
+    const CompiledForest &f = m->f;
+    auto S = std::make_unique<ShuffleDev>();
+    S->ctx_serial = c->serial;
+    f.shuffle_rotations(S->rots);
+    const int ell = result_level(c, f), A = c->alpha, N = c->N;
+    const size_t w = (size_t)(ell + A) * N, nr = S->rots.size();
+    CUDA_TRY(cudaMalloc(&S->store, std::max<size_t>(nr * w, 1) * sizeof(u64)));
+    const uint32_t n_out = f.n_out();
+    std::vector<uint32_t> pat(nr * (size_t)n_out), dg;
+    S->pt.assign(1, std::vector<const u64 *>());
+    for (size_t r = 0; r < nr; r++) {
+        f.shuffle_diagonal(S->rots[r], dg);
+        std::copy(dg.begin(), dg.end(), pat.begin() + r * n_out);
+        S->pt[0].push_back(S->store + r * w);
+    }
+    STATUS_TRY(encode_patterns(c, pat, (int)nr, (int)n_out, (int)f.block, ell, A, S->store, s));
+    m->shuf = std::move(S);
+    return COPSE_OK;
+}
 
 // ---------------------------------------------------------------- model upload
 static copse_status upload_model(copse_ctx *c, copse_model *m, cudaStream_t s) {
@@ -184,7 +224,7 @@ extern "C" void copse_model_destroy(copse_model *m) { delete m; }
 
 uint32_t model_block(const copse_model *m) { return m->f.block; }
 uint32_t model_features(const copse_model *m) { return m->f.n_features; }
-uint32_t model_leaves(const copse_model *m) { return m->f.L; }
+uint32_t model_leaves(const copse_model *m) { return m->f.n_out(); }
 uint32_t model_precision(const copse_model *m) { return m->f.precision; }
 int model_log_n(const copse_model *m) { return (int)m->f.log_n; }
 
@@ -207,6 +247,7 @@ extern "C" copse_status copse_model_info_get(const copse_model *m, copse_model_i
     info->n_rot_reshuffle = (uint32_t)rs.size();
     info->n_rot_level = (uint32_t)ls.size();
     info->levels_used = f.levels_used();
+    info->n_out = f.n_out();
     return COPSE_OK;
 }
 
@@ -274,6 +315,44 @@ extern "C" copse_status copse_model_set_encrypted(copse_model *m, int on) {
 
 extern "C" int copse_model_is_encrypted(const copse_model *m) { return m && m->f.encrypted ? 1 : 0; }
 
+extern "C" copse_status copse_model_set_shuffle(copse_model *m, const int32_t *src, size_t n_out,
+                                                const uint32_t *codebook) {
+    if (!m || (n_out && (!src || !codebook))) { set_error("null argument"); return COPSE_EINVAL; }
+    CompiledForest &f = m->f;
+    if (n_out) {
+        if (n_out < f.L || n_out > f.block) { set_error("shuffle output must hold every leaf and fit the query block"); return COPSE_EINVAL; }
+        std::vector<char> seen(f.L, 0);
+        for (size_t j = 0; j < n_out; j++) {
+            if (src[j] < -1 || src[j] >= (int32_t)f.L || (src[j] >= 0 && seen[src[j]]++)) {
+                set_error("shuffle source is not a padded permutation of the leaves");
+                return COPSE_EINVAL;
+            }
+            if (codebook[j] >= f.classes.size()) { set_error("codebook class out of range"); return COPSE_EINVAL; }
+            if (src[j] >= 0 && (int)codebook[j] != f.leaf_class[src[j]]) {
+                set_error("codebook does not carry each leaf's class");
+                return COPSE_EINVAL;
+            }
+        }
+        for (char x : seen)
+            if (!x) { set_error("shuffle source misses a leaf"); return COPSE_EINVAL; }
+    }
+    cudaDeviceSynchronize();
+    f.shuffle_src.assign(src, src + n_out);
+    f.codebook.assign(codebook, codebook + n_out);
+    m->shuf.reset();
+    return COPSE_OK;
+}
+
+extern "C" copse_status copse_model_codebook(const copse_model *m, uint32_t *classes) {
+    if (!m || !classes) { set_error("null argument"); return COPSE_EINVAL; }
+    const CompiledForest &f = m->f;
+    if (f.shuffle_src.empty())
+        for (uint32_t j = 0; j < f.L; j++) classes[j] = (uint32_t)f.leaf_class[j];
+    else
+        std::copy(f.codebook.begin(), f.codebook.end(), classes);
+    return COPSE_OK;
+}
+
 extern "C" copse_status copse_encrypt_model(copse_ctx *c, const copse_keys *k, copse_model *m, uint64_t seed) {
     if (!c || !k || !m) { set_error("null argument"); return COPSE_EINVAL; }
     const CompiledForest &f = m->f;
@@ -330,9 +409,12 @@ extern "C" copse_status copse_keygen(copse_ctx *c, uint64_t seed, const copse_mo
         const CompiledForest &f = models[i]->f;
         if ((int)f.log_n != c->logN) { set_error("model compiled for another ring degree"); return COPSE_EINVAL; }
         std::vector<uint32_t> rs, ls;
+        std::vector<uint32_t> sr;
         f.group_reshuffle().rotations(rs);
         f.group_level().rotations(ls);
+        f.shuffle_rotations(sr);
         rs.insert(rs.end(), ls.begin(), ls.end());
+        rs.insert(rs.end(), sr.begin(), sr.end());
         for (uint32_t r : rs) {
             if (!r) continue;
             u64 g = 1, b = 3;
@@ -584,6 +666,16 @@ static copse_status infer_multi(copse_ctx *c, const copse_evk *evk, copse_model 
         }
         results[q] = lv[0];
     }
+    // label shuffle with padding (Section 7.2): one more plaintext matrix product
+    if (!m->f.shuffle_src.empty()) {
+        STATUS_TRY(upload_shuffle(c, m, s));
+        for (int q = 0; q < nct; q++) {
+            std::vector<DCt> o;
+            STATUS_TRY(op_matmul(c, evk, results[q], m->shuf->rots, m->shuf->pt, {nullptr}, o, s));
+            ct_free(&results[q], s);
+            results[q] = o[0];
+        }
+    }
     STATUS_TRY(mark(4));
     return COPSE_OK;
 }
@@ -650,16 +742,17 @@ extern "C" copse_status copse_decrypt_labels(copse_ctx *c, const copse_keys *k, 
     u64 *slots = nullptr;
     uint8_t *bits = on_device ? out_bits : nullptr;
     STATUS_TRY(dev_alloc(c, (void **)&slots, (size_t)c->N * 8, s));
-    if (!on_device) STATUS_TRY(dev_alloc(c, (void **)&bits, std::max<size_t>(nq * f.L, 1), s));
+    const size_t n_out = f.n_out();
+    if (!on_device) STATUS_TRY(dev_alloc(c, (void **)&bits, std::max<size_t>(nq * n_out, 1), s));
     // query j is block j mod per_ct of result ciphertext j / per_ct
     for (size_t j0 = 0, q = 0; j0 < nq || (nq == 0 && q == 0); j0 += per_ct, q++) {
         const size_t n = std::min(per_ct, nq - j0);
         STATUS_TRY(decrypt_slots_dev(c, k, res->cts[q], slots, s));
-        STATUS_TRY(extract_bits(c, slots, (int)n, (int)f.block, (int)f.L, bits + j0 * f.L, s));
+        STATUS_TRY(extract_bits(c, slots, (int)n, (int)f.block, (int)n_out, bits + j0 * n_out, s));
         if (nq == 0) break;
     }
     if (!on_device) {
-        CUDA_TRY(cudaMemcpyAsync(out_bits, bits, nq * f.L, cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(cudaMemcpyAsync(out_bits, bits, nq * n_out, cudaMemcpyDeviceToHost, s));
         dev_free(bits, s);
     }
     dev_free(slots, s);
@@ -834,7 +927,7 @@ static copse_status item_body(copse_session *S, size_t i, cudaStream_t s, int la
     u64 *slots = nullptr;
     STATUS_TRY(dev_alloc(c, (void **)&slots, (size_t)c->N * 8, s));
     STATUS_TRY(decrypt_slots_dev(c, S->keys, res, slots, s));
-    STATUS_TRY(extract_bits(c, slots, (int)it.nq, (int)f.block, (int)f.L, S->d_bits + it.bit_off, s));
+    STATUS_TRY(extract_bits(c, slots, (int)it.nq, (int)f.block, (int)f.n_out(), S->d_bits + it.bit_off, s));
     dev_free(slots, s);
     ct_free(&res, s);
     return COPSE_OK;  // feats frees its ciphertexts on s when it goes out of scope
@@ -875,7 +968,7 @@ extern "C" copse_status copse_session_create_batch(copse_ctx *c, const copse_key
         it.feat_off = S->n_feats;
         it.bit_off = S->n_bits;
         S->n_feats += it.nq * f.n_features;
-        S->n_bits += it.nq * f.L;
+        S->n_bits += it.nq * f.n_out();
         S->items.push_back(it);
     }
     CUDA_TRY(cudaSetDevice(c->device));
@@ -887,8 +980,10 @@ extern "C" copse_status copse_session_create_batch(copse_ctx *c, const copse_key
     CUDA_TRY(cudaStreamCreateWithFlags(&S->cap, cudaStreamNonBlocking));
     CUDA_TRY(cudaEventCreateWithFlags(&S->ev, cudaEventDisableTiming));
     // everything that synchronises or creates resources happens before capture
-    for (const SessItem &it : S->items)
+    for (const SessItem &it : S->items) {
         if (!it.m->f.encrypted) STATUS_TRY(upload_model(c, it.m, S->cap));
+        if (!it.m->f.shuffle_src.empty()) STATUS_TRY(upload_shuffle(c, it.m, S->cap));
+    }
     STATUS_TRY(ensure_lanes(c, (int)std::min<size_t>(n_items, COPSE_MAX_LANES)));
     CUDA_TRY(cudaStreamSynchronize(S->cap));
     stats_suspend(true);

@@ -64,7 +64,9 @@ uint32_t clog2(uint32_t x) {
 
 }  // namespace
 
-uint32_t CompiledForest::levels_used() const { return 1 + clog2(precision) + 2 + clog2(d); }
+uint32_t CompiledForest::levels_used() const {
+    return 1 + clog2(precision) + 2 + clog2(d) + (shuffle_src.empty() ? 0 : 1);
+}
 
 void CompiledForest::reshuffle_diagonal(uint32_t i, std::vector<uint8_t> &out) const {
     // extended reshuffle: row x is R[x mod b]; diagonal entry x is R_ext[x][(x+i) mod q]
@@ -234,6 +236,23 @@ int compile_forest(const char *text, size_t len, uint32_t precision, uint32_t n_
         if (any) f.rot_level.push_back(i);
     }
     return 0;
+}
+
+void CompiledForest::shuffle_rotations(std::vector<uint32_t> &out) const {
+    const int64_t h = (int64_t)1 << (log_n - 1);
+    out.clear();
+    for (size_t j = 0; j < shuffle_src.size(); j++)
+        if (shuffle_src[j] >= 0) out.push_back((uint32_t)((((int64_t)shuffle_src[j] - (int64_t)j) % h + h) % h));
+    std::sort(out.begin(), out.end());
+    out.erase(std::unique(out.begin(), out.end()), out.end());
+}
+
+void CompiledForest::shuffle_diagonal(uint32_t amount, std::vector<uint32_t> &out) const {
+    const int64_t h = (int64_t)1 << (log_n - 1);
+    out.assign(shuffle_src.size(), 0u);
+    for (size_t j = 0; j < shuffle_src.size(); j++)
+        if (shuffle_src[j] >= 0 && (uint32_t)((((int64_t)shuffle_src[j] - (int64_t)j) % h + h) % h) == amount)
+            out[j] = 1u;
 }
 
 BsgsGroup CompiledForest::group_reshuffle() const {

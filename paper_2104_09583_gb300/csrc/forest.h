@@ -68,6 +68,16 @@ struct CompiledForest {
     BsgsGroup group_reshuffle() const;
     BsgsGroup group_level() const;
 
+    // label shuffle with padding (Section 7.2): output slot j takes leaf shuffle_src[j]
+    // (-1 = padding, always 0); codebook[j] is its class.  Empty = no shuffle.
+    std::vector<int32_t> shuffle_src;
+    std::vector<uint32_t> codebook;
+    uint32_t n_out() const { return shuffle_src.empty() ? L : (uint32_t)shuffle_src.size(); }
+    // rotation amounts of the shuffle product (signed shifts src[j] - j taken mod N/2), ascending
+    void shuffle_rotations(std::vector<uint32_t> &out) const;
+    // its diagonal for one rotation amount, block-local over n_out() slots
+    void shuffle_diagonal(uint32_t amount, std::vector<uint32_t> &out) const;
+
     uint32_t m1() const { return L + b - 1; }       // rows of the extended reshuffle
     uint32_t pd() const { return m1() + q - 1; }    // slots carrying the periodic decisions
     uint32_t levels_used() const;

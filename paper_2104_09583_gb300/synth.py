@@ -125,6 +125,19 @@ def table6_forest(name, seed=6000):
     return "\n".join(lines) + "\n"
 
 
+def shuffle_plan(seed, leaf_classes, n_pad, n_classes):
+    """A server-side label shuffle with padding (the option of Section 7.2, "Returning
+    classification bitvectors"): a uniform permutation of the L leaves and n_pad padding slots.
+    Returns (src, codebook): output slot j carries leaf src[j] (-1 = a padding slot, whose bit
+    is always 0), codebook[j] its class (padding slots get uniform random classes)."""
+    rng = np.random.default_rng(seed)
+    L = len(leaf_classes)
+    src = np.concatenate([np.arange(L), -np.ones(n_pad, dtype=np.int64)])
+    rng.shuffle(src)
+    code = np.array([leaf_classes[i] if i >= 0 else int(rng.integers(n_classes)) for i in src], dtype=np.uint32)
+    return src.astype(np.int32), code
+
+
 def random_queries(seed, n, n_features, precision):
     rng = np.random.default_rng(seed)
     return rng.integers(0, 1 << precision, size=(n, n_features), dtype=np.int64).astype(np.uint32)

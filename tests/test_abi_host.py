@@ -114,3 +114,33 @@ def test_encrypted_mode_key_sets_match_oracle():
         assert K.copse_model_rotations(h) == Cp.rotation_sets(om)
     finally:
         K.copse_model_destroy(h)
+
+
+def test_shuffle_plan_validation_and_codebook():
+    """copse_model_set_shuffle accepts a padded permutation whose codebook carries each
+    leaf's class, rejects anything else, and adds one prime and the shift rotations."""
+    text = synth.random_forest(77, 3, 4, 3, 5, 3, complete=False)
+    om = Cp.compile_forest(text, 5, 3)
+    h = K.copse_compile_forest(text, 5, 3, 10)
+    try:
+        base = K.copse_model_info_get(h)
+        assert base["n_out"] == om.L
+        assert K.copse_model_codebook(h).tolist() == om.labels_per_leaf
+        src, code = synth.shuffle_plan(3, om.labels_per_leaf, 11, 3)
+        K.copse_model_set_shuffle(h, src, code)
+        info = K.copse_model_info_get(h)
+        assert info["n_out"] == om.L + 11 and info["levels_used"] == base["levels_used"] + 1
+        assert K.copse_model_codebook(h).tolist() == code.tolist()
+        want = sorted(set(Cp.shuffle_diagonals(om, src, 1024)) - {0})
+        rs, ls = K.copse_model_rotations(h)           # the reshuffle and level sets are unchanged
+        assert (rs, ls) == Cp.rotation_sets(om) and want
+        bad = src.copy()
+        bad[bad == 0] = 1                              # leaf 1 twice, leaf 0 missing
+        for s_, c_ in [(bad, code), (src, (code + 1) % 3), (src[: om.L - 1], code[: om.L - 1])]:
+            with pytest.raises(K.CopseError) as e:
+                K.copse_model_set_shuffle(h, s_, c_)
+            assert e.value.name == "EINVAL"
+        K.copse_model_set_shuffle(h)
+        assert K.copse_model_info_get(h)["n_out"] == om.L
+    finally:
+        K.copse_model_destroy(h)
