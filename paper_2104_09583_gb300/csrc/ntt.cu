@@ -28,7 +28,7 @@ namespace cg = cooperative_groups;
 namespace {
 
 constexpr int TILE = 2048;  // coefficients per CTA in the two-pass kernels
-constexpr int NT2 = 256;    // threads per CTA in the two-pass kernels
+constexpr int NT2 = 512;    // threads per CTA in the two-pass and cluster kernels
 
 __device__ __forceinline__ int ntt_prime(const NttBatch &b, int r, int L) {
     return b.fixed >= 0 ? b.fixed : (r < b.ell ? r : L + (r - b.ell));
