@@ -107,6 +107,13 @@ __device__ __forceinline__ u64 mul_mod(u64 a, u64 b, const PrimeDev &p) {
 // a signed small integer (|v| < q) as a residue
 __device__ __forceinline__ u64 from_signed(i64 v, u64 q) { return v < 0 ? q - (u64)(-v) : (u64)v; }
 __device__ __forceinline__ uint32_t bit_reverse(uint32_t x, int logN) { return __brev(x) >> (32 - logN); }
+// NTT position whose value lands on position n under X -> X^g (bit-reversed layout:
+// position n holds the evaluation at psi^(2 brev(n) + 1))
+__device__ __forceinline__ uint32_t galois_src(uint32_t n, u64 g, int logN) {
+    uint32_t e = 2u * bit_reverse(n, logN) + 1u;
+    uint32_t e2 = (uint32_t)(((u64)e * g) & ((2ull << logN) - 1));
+    return bit_reverse((e2 - 1u) >> 1, logN);
+}
 
 // SplitMix64 (Steele, Lea, Flood, OOPSLA 2014) in counter form: output number
 // (stream * 2^40 + idx + 1) of the sequence whose state starts at `seed`.
@@ -238,6 +245,43 @@ struct NttBatch {
 };
 copse_status ntt_forward(copse_ctx *ctx, const NttBatch &b, cudaStream_t s);
 copse_status ntt_inverse(copse_ctx *ctx, const NttBatch &b, cudaStream_t s);
+
+// ---- forward transforms fused with the base conversions around them
+// Modulus switch dropping q_{ell-1} (nc components): the transform's input is the
+// centred conversion of last ([nc][N], coefficient form, [c_{ell-1} t^-1]) to
+// q_0..q_{ell-2}, its output goes straight into
+//   out[c][i] = (x[c][i] - t * NTT(conv)) * q_{ell-1}^-1.
+struct MsFuse {
+    const u64 *last;  // [nc][N] coefficient form
+    const u64 *x;     // [nc][ell][N] NTT domain
+    u64 *out;         // [nc][ell-1][N]
+    int ell;
+};
+// ModDown finish of key-switching sums (job j = polys 2j, 2j+1): U (stride ustride
+// per poly) holds the extended-basis sum with its alpha special residues in
+// coefficient form; the transform's input is their conversion to q_0..q_{ell-1} and
+//   out_j[c][i] = (U[c][i] - t * NTT(conv)) * P^-1  + add_j[c] (tau_{gal_j} on c = 0; none
+//   when add_comps = 0; component 0 only when add_comps = 1).
+#define MD_JOBS 64
+struct MdFuse {
+    const u64 *U;
+    size_t ustride;
+    int ell;
+    u64 *out[MD_JOBS];        // [2][ell][N] each (components ocomp words apart)
+    size_t ocomp;
+    const u64 *add[MD_JOBS];  // [2][ell][N] each (components acomp words apart)
+    size_t acomp;
+    int add_comps;
+    u64 gal[MD_JOBS];         // 1 = no permutation
+};
+// The fused forms run on the cluster transform (2^12 <= N <= 2^14); *done = false
+// (nothing launched) otherwise, and the caller takes the unfused sequence.
+copse_status ntt_forward_modswitch(copse_ctx *ctx, const MsFuse &f, int nc, cudaStream_t s, bool *done);
+copse_status ntt_forward_moddown(copse_ctx *ctx, const MdFuse &f, int njobs, cudaStream_t s, bool *done);
+// the same finishing arithmetic without a transform (W: the converted sums already in
+// NTT form, [2 njobs][ell][N]; last: unused for MdFuse)
+copse_status moddown_finish(copse_ctx *ctx, const MdFuse &f, const u64 *W, int njobs, cudaStream_t s);
+copse_status modswitch_finish(copse_ctx *ctx, const MsFuse &f, const u64 *W, int nc, cudaStream_t s);
 
 // ---------------------------------------------------------------- keys
 struct copse_keys {

@@ -355,24 +355,103 @@ struct ClusterSmem {
     u64 ctw[256], ctwp[256];     // column-stage twiddles (the first N1 entries)
 };
 
-template <int CL>
+// finishing arithmetic of a modulus switch for value v = NTT(conversion) at (p, r, k)
+__device__ __forceinline__ void ms_store(const MsFuse &f, const PrimeDev *pr, const KsTables &T, int L, int logN,
+                                         int p, int r, size_t k, u64 v) {
+    const PrimeDev P = pr[r];
+    const u64 xv = f.x[(((size_t)p * f.ell + r) << logN) + k];
+    const u64 d = mul_shoup(v, P.t_mod, P.t_mod_sh, P.q);
+    f.out[(((size_t)p * (f.ell - 1) + r) << logN) + k] =
+        mul_shoup(sub_mod(xv, d, P.q), T.ms_qinv[(size_t)f.ell * L + r], P.q);
+}
+
+// finishing arithmetic of a ModDown for value v = NTT(conversion) at (p = 2 job + c, r, k)
+__device__ __forceinline__ void md_store(const MdFuse &f, const PrimeDev *pr, const KsTables &T, int logN, int p,
+                                         int r, size_t k, u64 v) {
+    const int job = p >> 1, c = p & 1;
+    const PrimeDev P = pr[r];
+    const u64 uv = f.U[(size_t)p * f.ustride + ((size_t)r << logN) + k];
+    u64 res = mul_shoup(sub_mod(uv, mul_shoup(v, P.t_mod, P.t_mod_sh, P.q), P.q), T.md_Pinv[r], P.q);
+    if (c < f.add_comps && f.add[job]) {
+        const size_t src = (c == 0 && f.gal[job] != 1) ? galois_src((uint32_t)k, f.gal[job], logN) : k;
+        res = add_mod(res, f.add[job][(size_t)c * f.acomp + ((size_t)r << logN) + src], P.q);
+    }
+    f.out[job][(size_t)c * f.ocomp + ((size_t)r << logN) + k] = res;
+}
+
+// Load / store of the forward cluster transform: coefficient n of residue r (global
+// prime g) of batch polynomial p in; NTT-domain value v (in [0, q)) at position k out.
+struct PlainIO {
+    u64 *data;
+    size_t stride;
+    int logN;
+    __device__ __forceinline__ u64 load(int p, int r, int, size_t n) const {
+        return data[(size_t)p * stride + ((size_t)r << logN) + n];
+    }
+    __device__ __forceinline__ void store(int p, int r, int, size_t k, u64 v) const {
+        data[(size_t)p * stride + ((size_t)r << logN) + k] = v;
+    }
+};
+
+// modulus switch: load the centred conversion of the last prime's residue, store the finish
+struct MsIO {
+    MsFuse f;
+    const PrimeDev *pr;
+    KsTables T;
+    int L, logN;
+    __device__ __forceinline__ u64 load(int p, int r, int, size_t n) const {
+        const u64 ql = pr[f.ell - 1].q;
+        const u64 w = mul_shoup(f.last[((size_t)p << logN) + n], T.ms_tinv[f.ell], ql);
+        // |centred w| < q_{ell-1}/2 < q_r: the chain is in decreasing order
+        return w > (ql - 1) / 2 ? pr[r].q - (ql - w) : w;
+    }
+    __device__ __forceinline__ void store(int p, int r, int, size_t k, u64 v) const {
+        ms_store(f, pr, T, L, logN, p, r, k, v);
+    }
+};
+
+// ModDown: load the conversion of the alpha special residues, store the finish
+struct MdIO {
+    MdFuse f;
+    const PrimeDev *pr;
+    KsTables T;
+    int L, alpha, logN;
+    __device__ __forceinline__ u64 load(int p, int r, int, size_t n) const {
+        const u64 *up = f.U + (size_t)p * f.ustride;
+        const u64 qi = pr[r].q;
+        u64 acc = 0;
+        for (int k = 0; k < alpha; k++) {
+            const u64 pk = pr[L + k].q;
+            const u64 y = mul_shoup(up[((size_t)(f.ell + k) << logN) + n], T.md_inv[k], pk);
+            u64 v = mul_shoup(y, T.md_hat[(size_t)k * L + r], qi);
+            if (y > (pk - 1) / 2) v = sub_mod(v, T.md_P[r], qi);
+            acc = add_mod(acc, v, qi);
+        }
+        return acc;
+    }
+    __device__ __forceinline__ void store(int p, int r, int, size_t k, u64 v) const {
+        md_store(f, pr, T, logN, p, r, k, v);
+    }
+};
+
+template <int CL, class IO>
 __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT2)
     k_ntt_fwd_cluster(NttBatch b, const PrimeDev *__restrict__ primes, const u64 *__restrict__ tw,
-                      const u64 *__restrict__ tw_sh, int logN, int L, int a) {
+                      const u64 *__restrict__ tw_sh, int logN, int L, int a, IO io) {
     extern __shared__ __align__(16) u64 dyn_smem[];
     ClusterSmem &S = *reinterpret_cast<ClusterSmem *>(dyn_smem);
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
-    const int N = 1 << logN, lb = logN - a, N2 = 1 << lb, lc = 11 - a, C = 1 << lc, lr = 11 - lb;
+    const int lb = logN - a, N2 = 1 << lb, lc = 11 - a, C = 1 << lc, lr = 11 - lb;
     const int pr = blockIdx.x / CL;
     const int p = pr / b.nr, r = b.r0 + pr % b.nr;
     if (ntt_skipped(b, p, r)) return;  // the same for every CTA of the cluster
     const int g = ntt_prime(b, r, L);
     const u64 q = primes[g].q, q2 = 2 * q;
-    u64 *poly = b.data + (size_t)p * b.stride + (size_t)r * N;
+    const size_t N = (size_t)1 << logN;
     const u64 *W = tw + (size_t)g * N, *Wp = tw_sh + (size_t)g * N;
-    const u64 *cdata = poly + (rank << lc);
-    for (int e = threadIdx.x; e < TILE; e += NT2) S.colt[e] = cdata[((size_t)(e >> lc) << lb) + (e & (C - 1))];
+    for (int e = threadIdx.x; e < TILE; e += NT2)
+        S.colt[e] = io.load(p, r, g, (size_t)(rank << lc) + ((size_t)(e >> lc) << lb) + (e & (C - 1)));
     for (int k = threadIdx.x; k < (1 << a); k += NT2) {
         S.ctw[k] = W[k];
         S.ctwp[k] = Wp[k];
@@ -397,12 +476,11 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT2)
     cl.sync();
     tile_fwd<false>(S.rowt, S.stw, S.stwp, lb, q, q2, [&](int gg, int i) { return (gg << lb) + i; },
                     [&](int u, int gg, int il) { return ((1 << lr) * ((1 << u) - 1)) + (gg << u) + il; });
-    u64 *rdata = poly + ((size_t)row0 << lb);
     for (int e = threadIdx.x; e < TILE; e += NT2) {
         u64 v = S.rowt[e];
         if (v >= q2) v -= q2;
         if (v >= q) v -= q;
-        rdata[e] = v;
+        io.store(p, r, g, ((size_t)row0 << lb) + e, v);
     }
 }
 
@@ -462,7 +540,7 @@ copse_status launch_cluster(copse_ctx *ctx, const NttBatch &b, cudaStream_t s, b
     static bool attr_set = false;  // per instantiation; raising the limit twice is harmless
     const int smem = (int)sizeof(ClusterSmem);
     if (!attr_set) {
-        CUDA_TRY(cudaFuncSetAttribute(k_ntt_fwd_cluster<CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        CUDA_TRY(cudaFuncSetAttribute(k_ntt_fwd_cluster<CL, PlainIO>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
         CUDA_TRY(cudaFuncSetAttribute(k_ntt_inv_cluster<CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
         attr_set = true;
     }
@@ -474,8 +552,9 @@ copse_status launch_cluster(copse_ctx *ctx, const NttBatch &b, cudaStream_t s, b
                                                             ctx->L, a));
     else
         TIMED("ntt_fwd", bytes, s,
-              k_ntt_fwd_cluster<CL><<<grid, NT2, smem, s>>>(b, ctx->d_prime, ctx->d_psi, ctx->d_psi_sh, ctx->logN,
-                                                            ctx->L, a));
+              k_ntt_fwd_cluster<CL, PlainIO><<<grid, NT2, smem, s>>>(b, ctx->d_prime, ctx->d_psi, ctx->d_psi_sh,
+                                                                     ctx->logN, ctx->L, a,
+                                                                     PlainIO{b.data, b.stride, ctx->logN}));
     LAUNCH_CHECK();
     return COPSE_OK;
 }
@@ -519,7 +598,84 @@ copse_status launch(copse_ctx *ctx, const NttBatch &b, cudaStream_t s, bool inve
     return COPSE_OK;
 }
 
+template <int CL, class IO>
+copse_status launch_cluster_io(copse_ctx *ctx, const NttBatch &b, const IO &io, cudaStream_t s) {
+    static bool attr_set = false;
+    const int smem = (int)sizeof(ClusterSmem);
+    if (!attr_set) {
+        CUDA_TRY(cudaFuncSetAttribute(k_ntt_fwd_cluster<CL, IO>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        attr_set = true;
+    }
+    const unsigned grid = (unsigned)b.npoly * (unsigned)b.nr * CL;
+    TIMED("ntt_fwd", (double)b.npoly * b.nr * ctx->N * 16.0, s,
+          k_ntt_fwd_cluster<CL, IO><<<grid, NT2, smem, s>>>(b, ctx->d_prime, ctx->d_psi, ctx->d_psi_sh, ctx->logN,
+                                                            ctx->L, ctx->logN / 2, io));
+    LAUNCH_CHECK();
+    return COPSE_OK;
+}
+
+template <class IO>
+copse_status launch_fused(copse_ctx *ctx, const NttBatch &b, const IO &io, cudaStream_t s, bool *done) {
+    *done = false;
+    if (b.npoly <= 0 || b.nr <= 0) { *done = true; return COPSE_OK; }
+    if (!ctx->ntt_clusters || (long)b.npoly * b.nr > ctx->ntt_cluster_max) return COPSE_OK;
+    if (ctx->logN == 12) STATUS_TRY((launch_cluster_io<2, IO>(ctx, b, io, s)));
+    else if (ctx->logN == 13) STATUS_TRY((launch_cluster_io<4, IO>(ctx, b, io, s)));
+    else if (ctx->logN == 14) STATUS_TRY((launch_cluster_io<8, IO>(ctx, b, io, s)));
+    else return COPSE_OK;
+    *done = true;
+    return COPSE_OK;
+}
+
+__global__ void k_ms_finish_io(const MsFuse f, const u64 *W, int nc, const PrimeDev *pr, KsTables T, int L,
+                               int logN) {
+    const size_t per = (size_t)(f.ell - 1) << logN;
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (size_t)nc * per) return;
+    const int p = (int)(e / per);
+    const size_t rem = e - p * per;
+    ms_store(f, pr, T, L, logN, p, (int)(rem >> logN), rem & ((1ull << logN) - 1), W[e]);
+}
+
+__global__ void k_md_finish_io(const MdFuse f, const u64 *W, int njobs, const PrimeDev *pr, KsTables T, int logN) {
+    const size_t per = (size_t)f.ell << logN;
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (size_t)2 * njobs * per) return;
+    const int p = (int)(e / per);
+    const size_t rem = e - p * per;
+    md_store(f, pr, T, logN, p, (int)(rem >> logN), rem & ((1ull << logN) - 1), W[e]);
+}
+
 }  // namespace
+
+copse_status ntt_forward_modswitch(copse_ctx *ctx, const MsFuse &f, int nc, cudaStream_t s, bool *done) {
+    NttBatch b{nullptr, 0, nc, 0, f.ell - 1, f.ell - 1, -1};
+    return launch_fused(ctx, b, MsIO{f, ctx->d_prime, ctx->ks, ctx->L, ctx->logN}, s, done);
+}
+
+copse_status ntt_forward_moddown(copse_ctx *ctx, const MdFuse &f, int njobs, cudaStream_t s, bool *done) {
+    if (njobs > MD_JOBS) { set_error("internal: too many ModDown jobs"); return COPSE_EINVAL; }
+    NttBatch b{nullptr, 0, 2 * njobs, 0, f.ell, f.ell, -1};
+    return launch_fused(ctx, b, MdIO{f, ctx->d_prime, ctx->ks, ctx->L, ctx->alpha, ctx->logN}, s, done);
+}
+
+copse_status modswitch_finish(copse_ctx *ctx, const MsFuse &f, const u64 *W, int nc, cudaStream_t s) {
+    const size_t n = (size_t)nc * (f.ell - 1) * ctx->N;
+    TIMED("ms_finish", 8.0 * 3.0 * (double)n, s,
+          k_ms_finish_io<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(f, W, nc, ctx->d_prime, ctx->ks, ctx->L,
+                                                                      ctx->logN));
+    LAUNCH_CHECK();
+    return COPSE_OK;
+}
+
+copse_status moddown_finish(copse_ctx *ctx, const MdFuse &f, const u64 *W, int njobs, cudaStream_t s) {
+    if (njobs > MD_JOBS) { set_error("internal: too many ModDown jobs"); return COPSE_EINVAL; }
+    const size_t n = (size_t)2 * njobs * f.ell * ctx->N;
+    TIMED("ks_finish", 8.0 * 4.0 * (double)n, s,
+          k_md_finish_io<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(f, W, njobs, ctx->d_prime, ctx->ks, ctx->logN));
+    LAUNCH_CHECK();
+    return COPSE_OK;
+}
 
 copse_status ntt_forward(copse_ctx *ctx, const NttBatch &b, cudaStream_t s) { return launch(ctx, b, s, false); }
 copse_status ntt_inverse(copse_ctx *ctx, const NttBatch &b, cudaStream_t s) { return launch(ctx, b, s, true); }

@@ -32,11 +32,7 @@ inline unsigned nblk(size_t n) { return (unsigned)((n + TPB - 1) / TPB); }
 
 // Position n of the bit-reversed NTT holds the evaluation at psi^(2 brev(n) + 1);
 // tau_g(a) there equals a at psi^((2 brev(n) + 1) g).
-__device__ __forceinline__ uint32_t galois_src(uint32_t n, u64 g, int logN) {
-    uint32_t e = 2u * bit_reverse(n, logN) + 1u;
-    uint32_t e2 = (uint32_t)(((u64)e * g) & ((2ull << logN) - 1));
-    return bit_reverse((e2 - 1u) >> 1, logN);
-}
+
 
 __global__ void k_add(const u64 *a, const u64 *b, u64 *out, int ncomp, int level, int logN, int neg,
                       const PrimeDev *pr) {
@@ -203,29 +199,6 @@ __global__ void k_moddown_conv(const u64 *u, size_t ustride, u64 *W, size_t wstr
     }
 }
 
-// out_c = add_c (+ tau_g on add_0) + (u_c - t W_c) P^-1, c = 0, 1; all NTT domain
-__global__ void k_ks_finish(const u64 *u, const u64 *W, const u64 *add0, const u64 *add1, u64 g, u64 *out,
-                            int ell, int alpha, int logN, const PrimeDev *pr, KsTables T) {
-    const int N = 1 << logN;
-    size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    size_t n_el = (size_t)ell << logN;
-    if (e >= 2 * n_el) return;
-    const int c = e >= n_el;
-    size_t k = e - c * n_el;
-    const int i = (int)(k >> logN);
-    const uint32_t n = (uint32_t)(k & (N - 1));
-    const PrimeDev P = pr[i];
-    const u64 uv = u[(size_t)c * ((size_t)(ell + alpha) << logN) + k];
-    const u64 w = W[e];
-    u64 v = mul_shoup(sub_mod(uv, mul_shoup(w, P.t_mod, P.t_mod_sh, P.q), P.q), T.md_Pinv[i], P.q);
-    const u64 *ad = c ? add1 : add0;
-    if (ad) {
-        const uint32_t src = (c == 0 && g != 1) ? galois_src(n, g, logN) : n;
-        v = add_mod(v, ad[((size_t)i << logN) + src], P.q);
-    }
-    out[e] = v;
-}
-
 // Diagonal products over shared rotations with one ModDown per sum (double
 // hoisting).  For every element (r, n) of the extended basis and each rotation k
 // of the chunk:
@@ -349,20 +322,6 @@ __global__ void k_sum_parts(const u64 *part, size_t stride, int nparts, u64 *out
     out[i] = s;
 }
 
-// ModDown finish over npoly polys: out = (u - t W) * P^-1, u with stride ustride (its first
-// ell residues in NTT domain), W and out [npoly][ell][N]
-__global__ void k_md_finish(const u64 *u, size_t ustride, const u64 *W, u64 *out, int npoly, int ell, int logN,
-                            const PrimeDev *pr, KsTables T) {
-    const size_t per = (size_t)ell << logN;
-    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= (size_t)npoly * per) return;
-    const size_t p = e / per, k = e - p * per;
-    const int i = (int)(k >> logN);
-    const PrimeDev P = pr[i];
-    const u64 uv = u[p * ustride + k];
-    out[e] = mul_shoup(sub_mod(uv, mul_shoup(W[e], P.t_mod, P.t_mod_sh, P.q), P.q), T.md_Pinv[i], P.q);
-}
-
 // out[c] += pt * v[c] for both components (pt: first ell residues of an extended-basis plaintext)
 __global__ void k_ident_mac(u64 *out, const u64 *v, const u64 *pt, int ell, int logN, const PrimeDev *pr) {
     const size_t n = (size_t)ell << logN;
@@ -389,20 +348,6 @@ __global__ void k_ms_conv(const u64 *last, u64 *W, int ncomp, int ell, int L, in
         const u64 qi = pr[i].q;
         W[(((size_t)c * (ell - 1) + i) << logN) + n] = neg ? qi - (ql - w) : w;
     }
-}
-
-__global__ void k_ms_finish(const u64 *ct, const u64 *W, u64 *out, int ncomp, int ell, int L, int logN,
-                            const PrimeDev *pr, KsTables T) {
-    size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const size_t per = (size_t)(ell - 1) << logN;
-    if (e >= (size_t)ncomp * per) return;
-    const int c = (int)(e / per);
-    const size_t k = e - c * per;
-    const int i = (int)(k >> logN);
-    const PrimeDev P = pr[i];
-    const u64 x = ct[(size_t)c * ((size_t)ell << logN) + k];
-    const u64 d = mul_shoup(W[e], P.t_mod, P.t_mod_sh, P.q);
-    out[e] = mul_shoup(sub_mod(x, d, P.q), T.ms_qinv[(size_t)ell * L + i], P.q);
 }
 
 // uniform residues: out[r][j] for global prime g0 + r, (hi 2^64 + lo) mod q with
@@ -572,27 +517,6 @@ __global__ void k_extract_bits(const u64 *slots, int nq, int block, int L, uint8
     bits[e] = v == 0 ? 0 : (v == 1 ? 1 : 2);
 }
 
-// Relinearisation finish for a batch (blockIdx.y = item): out = (d0, d1) + (U - t W) P^-1,
-// U [n][2][ell+alpha][N], W [n][2][ell][N], d3 [n][3][ell][N], out [n][2][ell][N]
-__global__ void k_relin_finish(const u64 *U, const u64 *W, const u64 *d3, u64 *out, int ell, int alpha, int logN,
-                               const PrimeDev *pr, KsTables T) {
-    const size_t n_el = (size_t)ell << logN;
-    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= 2 * n_el) return;
-    const size_t it = blockIdx.y;
-    U += it * 2 * ((size_t)(ell + alpha) << logN);
-    W += it * 2 * n_el;
-    d3 += it * 3 * n_el;
-    out += it * 2 * n_el;
-    const int c = e >= n_el;
-    const size_t k = e - c * n_el;
-    const int i = (int)(k >> logN);
-    const PrimeDev P = pr[i];
-    const u64 uv = U[(size_t)c * ((size_t)(ell + alpha) << logN) + k];
-    const u64 v = mul_shoup(sub_mod(uv, mul_shoup(W[e], P.t_mod, P.t_mod_sh, P.q), P.q), T.md_Pinv[i], P.q);
-    out[e] = add_mod(v, d3[e], P.q);
-}
-
 // c0 += 1 (the constant polynomial 1 is 1 at every evaluation point)
 __global__ void k_add_one(u64 *c0, int ell, int logN, const PrimeDev *pr) {
     const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -647,22 +571,46 @@ copse_status ks_modup_batch(copse_ctx *c, const u64 *x_ntt, size_t xs, int n, in
     return COPSE_OK;
 }
 
-// inner products and ModDown conversion for jobs; U [nj][2][ell+alpha][N], W [nj][2][ell][N]
-copse_status ks_apply(copse_ctx *c, const u64 *yhat, int ell, const std::vector<InnerJob> &jobs_h, u64 *U, u64 *W,
+// ModDown of nj extended-basis sums U [nj][2][ell+alpha][N] (NTT domain) finished as f
+// says (f.U, f.ustride, f.ell filled here): special residues to coefficients, then the
+// fused conversion + transform + finish, or conversion, transform and finish
+copse_status moddown_apply(copse_ctx *c, u64 *U, int ell, int nj, MdFuse &f, Scratch &sc, cudaStream_t s) {
+    const int N = c->N, A = c->alpha, nx = ell + A;
+    f.U = U;
+    f.ustride = (size_t)nx * N;
+    f.ell = ell;
+    STATUS_TRY(ntt_inverse(c, batch(U, (size_t)nx * N, 2 * nj, ell, A, ell), s));
+    bool done = false;
+    STATUS_TRY(ntt_forward_moddown(c, f, nj, s, &done));
+    if (done) return COPSE_OK;
+    u64 *W = nullptr;
+    STATUS_TRY(sc.get(c, &W, (size_t)nj * 2 * ell * N));
+    TIMED("moddown_conv", 8.0 * N * 2.0 * nj * ((double)A + ell), s,
+          k_moddown_conv<<<nblk((size_t)2 * nj * N), TPB, 0, s>>>(U, (size_t)nx * N, W, (size_t)ell * N, 2 * nj, ell, A,
+                                                                  c->L, c->logN, c->d_prime, c->ks));
+    LAUNCH_CHECK();
+    STATUS_TRY(ntt_forward(c, batch(W, (size_t)ell * N, 2 * nj, 0, ell, ell), s));
+    return moddown_finish(c, f, W, nj, s);
+}
+
+// key-switching inner products for jobs (U [nj][2][ell+alpha][N]), then ModDown finished as f
+copse_status ks_apply(copse_ctx *c, const u64 *yhat, int ell, const std::vector<InnerJob> &jobs_h, u64 *U, MdFuse &f,
                       Scratch &sc, cudaStream_t s) {
     const int N = c->N, A = c->alpha, nx = ell + A, nj = (int)jobs_h.size();
-    if (nj > CHUNK_ROT) { set_error("internal: too many key-switch jobs in one launch"); return COPSE_EINVAL; }
+    if (nj > CHUNK_ROT || nj > MD_JOBS) { set_error("internal: too many key-switch jobs in one launch"); return COPSE_EINVAL; }
     InnerJobs jobs;
     for (int i = 0; i < nj; i++) jobs.j[i] = jobs_h[i];
     dim3 grid(nblk((size_t)nx * N), nj);
     TIMED("ks_inner", 8.0 * N * ((double)((ell + A - 1) / A) * nx + (double)nj * (2.0 * ((ell + A - 1) / A) * nx + 2.0 * nx)), s, k_ks_inner<<<grid, TPB, 0, s>>>(yhat, jobs, ell, A, c->L, c->logN, c->d_prime));
     LAUNCH_CHECK();
-    STATUS_TRY(ntt_inverse(c, batch(U, (size_t)nx * N, 2 * nj, ell, A, ell), s));
-    TIMED("moddown_conv", 8.0 * N * 2.0 * nj * ((double)A + ell), s, k_moddown_conv<<<nblk((size_t)2 * nj * N), TPB, 0, s>>>(U, (size_t)nx * N, W, (size_t)ell * N, 2 * nj, ell, A,
-                                                            c->L, c->logN, c->d_prime, c->ks));
-    LAUNCH_CHECK();
-    STATUS_TRY(ntt_forward(c, batch(W, (size_t)ell * N, 2 * nj, 0, ell, ell), s));
-    return COPSE_OK;
+    return moddown_apply(c, U, ell, nj, f, sc, s);
+}
+
+MdFuse md_fuse() {
+    MdFuse f;
+    memset(&f, 0, sizeof(f));
+    for (int i = 0; i < MD_JOBS; i++) f.gal[i] = 1;
+    return f;
 }
 
 u64 galois_of_rotation(const copse_ctx *c, uint32_t k) {
@@ -703,20 +651,26 @@ copse_status op_modswitch(copse_ctx *c, const DCt &in, DCt *out, cudaStream_t s)
     const int ell = in.level, nc = in.ncomp, N = c->N;
     if (ell < 2) { set_error("modulus switch below one prime"); return COPSE_ELEVEL; }
     Scratch sc(s);
-    u64 *last = nullptr, *W = nullptr;
+    u64 *last = nullptr;
     STATUS_TRY(sc.get(c, &last, (size_t)nc * N));
-    STATUS_TRY(sc.get(c, &W, (size_t)nc * (ell - 1) * N));
-    for (int k = 0; k < nc; k++)
-        CUDA_TRY(cudaMemcpyAsync(last + (size_t)k * N, in.data + ((size_t)k * ell + ell - 1) * N, N * sizeof(u64),
-                                 cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(cudaMemcpy2DAsync(last, (size_t)N * sizeof(u64), in.data + (size_t)(ell - 1) * N,
+                               (size_t)ell * N * sizeof(u64), (size_t)N * sizeof(u64), nc, cudaMemcpyDeviceToDevice, s));
     STATUS_TRY(ntt_inverse(c, batch(last, N, nc, 0, 1, ell, ell - 1), s));
-    TIMED("ms_conv", 8.0 * N * (double)nc * ell, s, k_ms_conv<<<nblk((size_t)nc * N), TPB, 0, s>>>(last, W, nc, ell, c->L, c->logN, c->d_prime, c->ks));
-    LAUNCH_CHECK();
-    STATUS_TRY(ntt_forward(c, batch(W, (size_t)(ell - 1) * N, nc, 0, ell - 1, ell - 1), s));
     STATUS_TRY(ct_alloc(c, out, ell - 1, nc, s));
-    TIMED("ms_finish", 8.0 * N * 3.0 * nc * (ell - 1), s, k_ms_finish<<<nblk((size_t)nc * (ell - 1) * N), TPB, 0, s>>>(in.data, W, out->data, nc, ell, c->L, c->logN,
-                                                                 c->d_prime, c->ks));
-    LAUNCH_CHECK();
+    // conversion of the dropped prime's residue to the others, transform and finish in one
+    // launch where the cluster transform applies; else conversion, transform, finish
+    const MsFuse f{last, in.data, out->data, ell};
+    bool done = false;
+    STATUS_TRY(ntt_forward_modswitch(c, f, nc, s, &done));
+    if (!done) {
+        u64 *W = nullptr;
+        STATUS_TRY(sc.get(c, &W, (size_t)nc * (ell - 1) * N));
+        TIMED("ms_conv", 8.0 * N * (double)nc * ell, s,
+              k_ms_conv<<<nblk((size_t)nc * N), TPB, 0, s>>>(last, W, nc, ell, c->L, c->logN, c->d_prime, c->ks));
+        LAUNCH_CHECK();
+        STATUS_TRY(ntt_forward(c, batch(W, (size_t)(ell - 1) * N, nc, 0, ell - 1, ell - 1), s));
+        STATUS_TRY(modswitch_finish(c, f, W, nc, s));
+    }
     return COPSE_OK;
 }
 
@@ -769,7 +723,7 @@ copse_status op_mul(copse_ctx *c, const copse_evk *evk, const DCt &a, const DCt 
     STATUS_TRY(aligned(c, a, b, &ta, &tb, &oa, &ob, s));
     const int ell = ta.level, N = c->N, A = c->alpha;
     Scratch sc(s);
-    u64 *d = nullptr, *U = nullptr, *W = nullptr, *yhat = nullptr;
+    u64 *d = nullptr, *U = nullptr, *yhat = nullptr;
     STATUS_TRY(sc.get(c, &d, (size_t)3 * ell * N));
     TIMED("tensor", 8.0 * N * 7.0 * ell, s, k_tensor<<<nblk((size_t)ell * N), TPB, 0, s>>>(ta.data, tb.data, d, ell, c->logN, c->d_prime));
     LAUNCH_CHECK();
@@ -777,14 +731,17 @@ copse_status op_mul(copse_ctx *c, const copse_evk *evk, const DCt &a, const DCt 
     if (ob) ct_free(&tb, s);
     STATUS_TRY(ks_modup(c, d + (size_t)2 * ell * N, ell, sc, &yhat, s));
     STATUS_TRY(sc.get(c, &U, (size_t)2 * (ell + A) * N));
-    STATUS_TRY(sc.get(c, &W, (size_t)2 * ell * N));
-    std::vector<InnerJob> jobs{InnerJob{evk->rlk, U, 1}};
-    STATUS_TRY(ks_apply(c, yhat, ell, jobs, U, W, sc, s));
     DCt r;
     STATUS_TRY(ct_alloc(c, &r, ell, 2, s));
-    TIMED("ks_finish", 8.0 * N * 7.0 * ell, s, k_ks_finish<<<nblk((size_t)2 * ell * N), TPB, 0, s>>>(U, W, d, d + (size_t)ell * N, 1, r.data, ell, A, c->logN,
-                                                          c->d_prime, c->ks));
-    LAUNCH_CHECK();
+    // relinearised: (d0, d1) + ModDown(KSraw(d2))
+    std::vector<InnerJob> jobs{InnerJob{evk->rlk, U, 1}};
+    MdFuse f = md_fuse();
+    f.out[0] = r.data;
+    f.ocomp = (size_t)ell * N;
+    f.add[0] = d;
+    f.acomp = (size_t)ell * N;
+    f.add_comps = 2;
+    STATUS_TRY(ks_apply(c, yhat, ell, jobs, U, f, sc, s));
     copse_status st = op_modswitch(c, r, out, s);
     ct_free(&r, s);
     return st;
@@ -809,35 +766,34 @@ copse_status op_rotate(copse_ctx *c, const copse_evk *evk, const DCt &a, uint32_
     const u64 *key = evk->find(g);
     if (!key) { set_error("no rotation key for amount " + std::to_string(k)); return COPSE_ENOKEY; }
     Scratch sc(s);
-    u64 *yhat = nullptr, *U = nullptr, *W = nullptr;
+    u64 *yhat = nullptr, *U = nullptr;
     STATUS_TRY(ks_modup(c, a.data + (size_t)ell * N, ell, sc, &yhat, s));
     STATUS_TRY(sc.get(c, &U, (size_t)2 * (ell + A) * N));
-    STATUS_TRY(sc.get(c, &W, (size_t)2 * ell * N));
-    std::vector<InnerJob> jobs{InnerJob{key, U, g}};
-    STATUS_TRY(ks_apply(c, yhat, ell, jobs, U, W, sc, s));
     STATUS_TRY(ct_alloc(c, out, ell, 2, s));
-    TIMED("ks_finish", 8.0 * N * 6.0 * ell, s, k_ks_finish<<<nblk((size_t)2 * ell * N), TPB, 0, s>>>(U, W, a.data, nullptr, g, out->data, ell, A, c->logN,
-                                                          c->d_prime, c->ks));
-    LAUNCH_CHECK();
-    return COPSE_OK;
+    // (tau_g c0, 0) + ModDown(KSraw(tau_g c1))
+    std::vector<InnerJob> jobs{InnerJob{key, U, g}};
+    MdFuse f = md_fuse();
+    f.out[0] = out->data;
+    f.ocomp = (size_t)ell * N;
+    f.add[0] = a.data;
+    f.add_comps = 1;
+    f.gal[0] = g;
+    return ks_apply(c, yhat, ell, jobs, U, f, sc, s);
 }
 
 // ModDown of n extended-basis ciphertexts acc [n][2][ell+alpha][N] (NTT domain; the
-// special-prime residues are transformed in place) into res [n][2][ell][N]; W scratch
-// of res's size.
-static copse_status moddown_batch(copse_ctx *c, u64 *acc, int n, int ell, u64 *W, u64 *res, cudaStream_t s) {
-    const int N = c->N, A = c->alpha, nx = ell + A;
-    const size_t per = (size_t)2 * ell * N;
-    STATUS_TRY(ntt_inverse(c, batch(acc, (size_t)nx * N, 2 * n, ell, A, ell), s));
-    TIMED("moddown_conv", 8.0 * N * 2.0 * n * ((double)A + ell), s,
-          k_moddown_conv<<<nblk((size_t)2 * n * N), TPB, 0, s>>>(acc, (size_t)nx * N, W, (size_t)ell * N, 2 * n, ell,
-                                                                 A, c->L, c->logN, c->d_prime, c->ks));
-    LAUNCH_CHECK();
-    STATUS_TRY(ntt_forward(c, batch(W, (size_t)ell * N, 2 * n, 0, ell, ell), s));
-    TIMED("md_finish", 8.0 * N * 3.0 * 2 * n * ell, s,
-          k_md_finish<<<nblk((size_t)n * per), TPB, 0, s>>>(acc, (size_t)nx * N, W, res, 2 * n, ell, c->logN,
-                                                            c->d_prime, c->ks));
-    LAUNCH_CHECK();
+// special-prime residues are transformed in place) into res [n][2][ell][N].
+static copse_status moddown_batch(copse_ctx *c, u64 *acc, int n, int ell, u64 *res, cudaStream_t s) {
+    const int N = c->N, nx = ell + c->alpha;
+    const size_t per = (size_t)2 * ell * N, ext = (size_t)2 * nx * N;
+    for (int j0 = 0; j0 < n; j0 += MD_JOBS) {
+        const int nj = std::min(MD_JOBS, n - j0);
+        Scratch sc(s);
+        MdFuse f = md_fuse();
+        for (int i = 0; i < nj; i++) f.out[i] = res + (size_t)(j0 + i) * per;
+        f.ocomp = (size_t)ell * N;
+        STATUS_TRY(moddown_apply(c, acc + (size_t)j0 * ext, ell, nj, f, sc, s));
+    }
     return COPSE_OK;
 }
 
@@ -858,7 +814,7 @@ copse_status op_matmul(copse_ctx *c, const copse_evk *evk, const DCt &v, const s
         if (used) ks_idx.push_back(r);
     }
     // extended-basis accumulators [nacc][2][ell+alpha][N] and the Q-basis results [nacc][2][ell][N]
-    u64 *acc = nullptr, *res = raw_out, *W = nullptr;
+    u64 *acc = nullptr, *res = raw_out;
     if (!res) STATUS_TRY(sc.get(c, &res, (size_t)nacc * per));
     CUDA_TRY(cudaMemsetAsync(res, 0, (size_t)nacc * per * sizeof(u64), s));
     if (!ks_idx.empty()) {
@@ -870,7 +826,6 @@ copse_status op_matmul(copse_ctx *c, const copse_evk *evk, const DCt &v, const s
         u64 *part = nullptr;
         STATUS_TRY(sc.get(c, &acc, (size_t)nacc * ext));
         STATUS_TRY(sc.get(c, &part, (size_t)parts * part_stride));
-        STATUS_TRY(sc.get(c, &W, (size_t)nacc * per));
         CUDA_TRY(cudaMemsetAsync(part, 0, (size_t)parts * part_stride * sizeof(u64), s));
         u64 *yhat = nullptr;
         STATUS_TRY(ks_modup(c, v.data + (size_t)ell * N, ell, sc, &yhat, s));
@@ -906,7 +861,7 @@ copse_status op_matmul(copse_ctx *c, const copse_evk *evk, const DCt &v, const s
                                                             c->L, c->logN, c->d_prime));
         LAUNCH_CHECK();
         // one ModDown per accumulator (both components)
-        STATUS_TRY(moddown_batch(c, acc, nacc, ell, W, res, s));
+        STATUS_TRY(moddown_batch(c, acc, nacc, ell, res, s));
     }
     out.assign(raw_out ? 0 : nacc, DCt());
     for (int a = 0; a < nacc; a++) {
@@ -949,7 +904,7 @@ copse_status giant_phase(copse_ctx *c, const copse_evk *evk, const u64 *inner, i
         }
     }
     Scratch sc(s);
-    u64 *acc = nullptr, *W = nullptr, *res = nullptr;
+    u64 *acc = nullptr, *res = nullptr;
     STATUS_TRY(sc.get(c, &res, (size_t)n_mat * per));
     if (!any_rot) {
         CUDA_TRY(cudaMemsetAsync(res, 0, (size_t)n_mat * per * sizeof(u64), s));
@@ -957,7 +912,6 @@ copse_status giant_phase(copse_ctx *c, const copse_evk *evk, const u64 *inner, i
         // per matrix, the rotated accumulators key-switched into one extended-basis sum
         // (the ModUps of a matrix's terms batched), one ModDown for all matrices
         STATUS_TRY(sc.get(c, &acc, (size_t)n_mat * ext));
-        STATUS_TRY(sc.get(c, &W, (size_t)n_mat * per));
         CUDA_TRY(cudaMemsetAsync(acc, 0, (size_t)n_mat * ext * sizeof(u64), s));
         for (int a = 0; a < n_mat; a++) {
             int x0 = 0;
@@ -989,7 +943,7 @@ copse_status giant_phase(copse_ctx *c, const copse_evk *evk, const u64 *inner, i
                 LAUNCH_CHECK();
             }
         }
-        STATUS_TRY(moddown_batch(c, acc, n_mat, ell, W, res, s));
+        STATUS_TRY(moddown_batch(c, acc, n_mat, ell, res, s));
     }
     // + the giant-step-0 sums, + the plaintext or ciphertext addend, then one modulus switch per matrix
     out.assign(n_mat, DCt());
@@ -1052,23 +1006,20 @@ copse_status op_rotations(copse_ctx *c, const copse_evk *evk, const DCt &v, cons
     for (size_t k0 = 0; k0 < ks.size(); k0 += CHUNK_ROT) {
         const int nj = (int)std::min<size_t>(CHUNK_ROT, ks.size() - k0);
         Scratch sk(s);
-        u64 *U = nullptr, *W = nullptr;
+        u64 *U = nullptr;
         STATUS_TRY(sk.get(c, &U, (size_t)nj * 2 * nx * N));
-        STATUS_TRY(sk.get(c, &W, (size_t)nj * per));
         std::vector<InnerJob> jobs;
+        MdFuse f = md_fuse();
+        f.ocomp = (size_t)ell * N;
+        f.add_comps = 1;
         for (int i = 0; i < nj; i++) {
             const int x = ks[k0 + i];
             jobs.push_back(InnerJob{evk->find(gal[x]), U + (size_t)i * 2 * nx * N, gal[x]});
+            f.out[i] = out + (size_t)x * per;
+            f.add[i] = v.data;
+            f.gal[i] = gal[x];
         }
-        STATUS_TRY(ks_apply(c, yhat, ell, jobs, U, W, sk, s));
-        for (int i = 0; i < nj; i++) {
-            const int x = ks[k0 + i];
-            TIMED("ks_finish", 8.0 * N * 6.0 * ell, s,
-                  k_ks_finish<<<nblk(per), TPB, 0, s>>>(U + (size_t)i * 2 * nx * N, W + (size_t)i * per, v.data,
-                                                        nullptr, gal[x], out + (size_t)x * per, ell, A, c->logN,
-                                                        c->d_prime, c->ks));
-            LAUNCH_CHECK();
-        }
+        STATUS_TRY(ks_apply(c, yhat, ell, jobs, U, f, sk, s));
     }
     return COPSE_OK;
 }
@@ -1079,18 +1030,20 @@ copse_status relin_batch(copse_ctx *c, const copse_evk *evk, const u64 *d3, int 
     for (int x0 = 0; x0 < n; x0 += CHUNK_ROT) {
         const int nj = std::min(CHUNK_ROT, n - x0);
         Scratch sk(s);
-        u64 *yhat = nullptr, *U = nullptr, *W = nullptr;
+        u64 *yhat = nullptr, *U = nullptr;
         STATUS_TRY(ks_modup_batch(c, d3 + (size_t)x0 * per3 + (size_t)2 * ell * N, per3, nj, ell, sk, &yhat, s));
         STATUS_TRY(sk.get(c, &U, (size_t)nj * 2 * nx * N));
-        STATUS_TRY(sk.get(c, &W, (size_t)nj * per));
         std::vector<InnerJob> jobs;
-        for (int i = 0; i < nj; i++)
+        MdFuse f = md_fuse();
+        f.ocomp = (size_t)ell * N;
+        f.acomp = (size_t)ell * N;
+        f.add_comps = 2;
+        for (int i = 0; i < nj; i++) {
             jobs.push_back(InnerJob{evk->rlk, U + (size_t)i * 2 * nx * N, 1, yhat + (size_t)i * nd * nx * N});
-        STATUS_TRY(ks_apply(c, yhat, ell, jobs, U, W, sk, s));
-        TIMED("ks_finish", 8.0 * N * 7.0 * ell * nj, s,
-              k_relin_finish<<<dim3(nblk(per), nj), TPB, 0, s>>>(U, W, d3 + (size_t)x0 * per3, out + (size_t)x0 * per,
-                                                                 ell, A, c->logN, c->d_prime, c->ks));
-        LAUNCH_CHECK();
+            f.out[i] = out + (size_t)(x0 + i) * per;
+            f.add[i] = d3 + (size_t)(x0 + i) * per3;
+        }
+        STATUS_TRY(ks_apply(c, yhat, ell, jobs, U, f, sk, s));
     }
     return COPSE_OK;
 }
