@@ -278,6 +278,15 @@ struct MdFuse {
 // (nothing launched) otherwise, and the caller takes the unfused sequence.
 copse_status ntt_forward_modswitch(copse_ctx *ctx, const MsFuse &f, int nc, cudaStream_t s, bool *done);
 copse_status ntt_forward_moddown(copse_ctx *ctx, const MdFuse &f, int njobs, cudaStream_t s, bool *done);
+// out-of-place inverse transform of residues [0, nr) (prime `fixed` when >= 0) of npoly
+// polynomials src + p sstride into dst + p dstride
+copse_status ntt_inverse_copy(copse_ctx *ctx, const u64 *src, size_t sstride, u64 *dst, size_t dstride, int npoly,
+                              int nr, int fixed, cudaStream_t s, bool *done);
+// ModUp of n_items inputs: the transform of every digit's conversion (xc: the inputs in
+// coefficient form, [item][ell][N]) into y [item][nd][ell+alpha][N], each digit's own
+// residues copied from x_ntt + item * xs
+copse_status ntt_forward_modup(copse_ctx *ctx, const u64 *xc, const u64 *x_ntt, size_t xs, u64 *y, int n_items,
+                               int ell, cudaStream_t s, bool *done);
 // the same finishing arithmetic without a transform (W: the converted sums already in
 // NTT form, [2 njobs][ell][N]; last: unused for MdFuse)
 copse_status moddown_finish(copse_ctx *ctx, const MdFuse &f, const u64 *W, int njobs, cudaStream_t s);

@@ -391,6 +391,63 @@ struct PlainIO {
     __device__ __forceinline__ void store(int p, int r, int, size_t k, u64 v) const {
         data[(size_t)p * stride + ((size_t)r << logN) + k] = v;
     }
+    __device__ __forceinline__ void skip(int, int, int, int) const {}
+};
+
+// out-of-place transform: residue r of polynomial p from src into dst
+struct CopyIO {
+    const u64 *src;
+    size_t sstride;
+    u64 *dst;
+    size_t dstride;
+    int logN;
+    __device__ __forceinline__ u64 load(int p, int r, int, size_t n) const {
+        return src[(size_t)p * sstride + ((size_t)r << logN) + n];
+    }
+    __device__ __forceinline__ void store(int p, int r, int, size_t k, u64 v) const {
+        dst[(size_t)p * dstride + ((size_t)r << logN) + k] = v;
+    }
+    __device__ __forceinline__ void skip(int, int, int, int) const {}
+};
+
+// ModUp (polynomial p = item nd + digit j, residue r of the extended basis): load the
+// centred conversion of the digit's coefficient-form residues, store into
+// y [item][nd][ell+alpha][N]; a digit's own residues (skipped by the transform) are
+// copied from the input, which already holds them in NTT form
+struct MuIO {
+    const u64 *xc;     // [item][ell][N] coefficient form
+    const u64 *x_ntt;  // item i at x_ntt + i * xs, [ell][N] NTT domain
+    size_t xs;
+    u64 *y;
+    int ell, alpha, nd, L, NP, logN;
+    const PrimeDev *pr;
+    KsTables T;
+    __device__ __forceinline__ u64 load(int p, int, int g, size_t n) const {
+        const int item = p / nd, j = p - item * nd;
+        const int lo = j * alpha, hi = min(lo + alpha, ell);
+        const u64 qg = pr[g].q;
+        const u64 *x = xc + (size_t)item * ell * ((size_t)1 << logN);
+        u64 acc = 0;
+        for (int i = lo; i < hi; i++) {
+            const u64 qi = pr[i].q;
+            const u64 v = mul_shoup(x[((size_t)i << logN) + n], T.modup_inv[(size_t)ell * L + i], qi);
+            const size_t ti = ((size_t)ell * L + i) * NP + g;
+            u64 w = mul_shoup(v, T.modup_hat[ti], qg);
+            if (v > (qi - 1) / 2) w = sub_mod(w, T.modup_qhat[ti], qg);
+            acc = add_mod(acc, w, qg);
+        }
+        return acc;
+    }
+    __device__ __forceinline__ void store(int p, int r, int, size_t k, u64 v) const {
+        y[(((size_t)p * (ell + alpha) + r) << logN) + k] = v;
+    }
+    __device__ __forceinline__ void skip(int p, int r, int rank, int cl) const {
+        const int item = p / nd;
+        const size_t n = (size_t)1 << logN, part = n / cl, k0 = (size_t)rank * part;
+        const u64 *src = x_ntt + (size_t)item * xs + ((size_t)r << logN) + k0;
+        u64 *dst = y + (((size_t)p * (ell + alpha) + r) << logN) + k0;
+        for (size_t k = threadIdx.x; k < part; k += blockDim.x) dst[k] = src[k];
+    }
 };
 
 // modulus switch: load the centred conversion of the last prime's residue, store the finish
@@ -408,6 +465,7 @@ struct MsIO {
     __device__ __forceinline__ void store(int p, int r, int, size_t k, u64 v) const {
         ms_store(f, pr, T, L, logN, p, r, k, v);
     }
+    __device__ __forceinline__ void skip(int, int, int, int) const {}
 };
 
 // ModDown: load the conversion of the alpha special residues, store the finish
@@ -432,6 +490,7 @@ struct MdIO {
     __device__ __forceinline__ void store(int p, int r, int, size_t k, u64 v) const {
         md_store(f, pr, T, logN, p, r, k, v);
     }
+    __device__ __forceinline__ void skip(int, int, int, int) const {}
 };
 
 template <int CL, class IO>
@@ -445,7 +504,10 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT2)
     const int lb = logN - a, N2 = 1 << lb, lc = 11 - a, C = 1 << lc, lr = 11 - lb;
     const int pr = blockIdx.x / CL;
     const int p = pr / b.nr, r = b.r0 + pr % b.nr;
-    if (ntt_skipped(b, p, r)) return;  // the same for every CTA of the cluster
+    if (ntt_skipped(b, p, r)) {  // the same for every CTA of the cluster
+        io.skip(p, r, rank, CL);
+        return;
+    }
     const int g = ntt_prime(b, r, L);
     const u64 q = primes[g].q, q2 = 2 * q;
     const size_t N = (size_t)1 << logN;
@@ -484,26 +546,25 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT2)
     }
 }
 
-template <int CL>
+template <int CL, class IO>
 __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT2)
     k_ntt_inv_cluster(NttBatch b, const PrimeDev *__restrict__ primes, const u64 *__restrict__ tw,
-                      const u64 *__restrict__ tw_sh, int logN, int L, int a) {
+                      const u64 *__restrict__ tw_sh, int logN, int L, int a, IO io) {
     extern __shared__ __align__(16) u64 dyn_smem[];
     ClusterSmem &S = *reinterpret_cast<ClusterSmem *>(dyn_smem);
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
-    const int N = 1 << logN, lb = logN - a, lc = 11 - a, C = 1 << lc, lr = 11 - lb, R = 1 << lr;
+    const int lb = logN - a, lc = 11 - a, C = 1 << lc, lr = 11 - lb, R = 1 << lr;
     const int pr = blockIdx.x / CL;
     const int p = pr / b.nr, r = b.r0 + pr % b.nr;
     if (ntt_skipped(b, p, r)) return;
     const int g = ntt_prime(b, r, L);
     const PrimeDev P = primes[g];
     const u64 q = P.q, q2 = 2 * q;
-    u64 *poly = b.data + (size_t)p * b.stride + (size_t)r * N;
+    const size_t N = (size_t)1 << logN;
     const u64 *W = tw + (size_t)g * N, *Wp = tw_sh + (size_t)g * N;
     const int row0 = rank << lr;
-    const u64 *rdata = poly + ((size_t)row0 << lb);
-    for (int e = threadIdx.x; e < TILE; e += NT2) S.rowt[e] = rdata[e];
+    for (int e = threadIdx.x; e < TILE; e += NT2) S.rowt[e] = io.load(p, r, g, ((size_t)row0 << lb) + e);
     for (int k = threadIdx.x; k < (1 << a); k += NT2) {
         S.ctw[k] = W[k];
         S.ctwp[k] = Wp[k];
@@ -530,9 +591,9 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT2)
     cl.sync();
     tile_inv<true>(S.colt, S.ctw, S.ctwp, a, q, q2, [&](int gg, int i) { return (i << lc) + gg; },
                    [&](int u, int, int il) { return (1 << (a - 1 - u)) + il; });
-    u64 *cdata = poly + (rank << lc);
     for (int e = threadIdx.x; e < TILE; e += NT2)
-        cdata[((size_t)(e >> lc) << lb) + (e & (C - 1))] = mul_shoup(S.colt[e], P.ninv, P.ninv_sh, q);
+        io.store(p, r, g, (size_t)(rank << lc) + ((size_t)(e >> lc) << lb) + (e & (C - 1)),
+                 mul_shoup(S.colt[e], P.ninv, P.ninv_sh, q));
 }
 
 template <int CL>
@@ -541,15 +602,16 @@ copse_status launch_cluster(copse_ctx *ctx, const NttBatch &b, cudaStream_t s, b
     const int smem = (int)sizeof(ClusterSmem);
     if (!attr_set) {
         CUDA_TRY(cudaFuncSetAttribute(k_ntt_fwd_cluster<CL, PlainIO>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        CUDA_TRY(cudaFuncSetAttribute(k_ntt_inv_cluster<CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        CUDA_TRY(cudaFuncSetAttribute(k_ntt_inv_cluster<CL, PlainIO>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
         attr_set = true;
     }
     const unsigned grid = (unsigned)b.npoly * (unsigned)b.nr * CL;
     const int a = ctx->logN / 2;
     if (inverse)
         TIMED("ntt_inv", bytes, s,
-              k_ntt_inv_cluster<CL><<<grid, NT2, smem, s>>>(b, ctx->d_prime, ctx->d_ipsi, ctx->d_ipsi_sh, ctx->logN,
-                                                            ctx->L, a));
+              k_ntt_inv_cluster<CL, PlainIO><<<grid, NT2, smem, s>>>(b, ctx->d_prime, ctx->d_ipsi, ctx->d_ipsi_sh,
+                                                                     ctx->logN, ctx->L, a,
+                                                                     PlainIO{b.data, b.stride, ctx->logN}));
     else
         TIMED("ntt_fwd", bytes, s,
               k_ntt_fwd_cluster<CL, PlainIO><<<grid, NT2, smem, s>>>(b, ctx->d_prime, ctx->d_psi, ctx->d_psi_sh,
@@ -598,30 +660,39 @@ copse_status launch(copse_ctx *ctx, const NttBatch &b, cudaStream_t s, bool inve
     return COPSE_OK;
 }
 
-template <int CL, class IO>
+template <int CL, bool INV, class IO>
 copse_status launch_cluster_io(copse_ctx *ctx, const NttBatch &b, const IO &io, cudaStream_t s) {
     static bool attr_set = false;
     const int smem = (int)sizeof(ClusterSmem);
     if (!attr_set) {
-        CUDA_TRY(cudaFuncSetAttribute(k_ntt_fwd_cluster<CL, IO>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        if (INV)
+            CUDA_TRY(cudaFuncSetAttribute(k_ntt_inv_cluster<CL, IO>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        else
+            CUDA_TRY(cudaFuncSetAttribute(k_ntt_fwd_cluster<CL, IO>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
         attr_set = true;
     }
     const unsigned grid = (unsigned)b.npoly * (unsigned)b.nr * CL;
-    TIMED("ntt_fwd", (double)b.npoly * b.nr * ctx->N * 16.0, s,
-          k_ntt_fwd_cluster<CL, IO><<<grid, NT2, smem, s>>>(b, ctx->d_prime, ctx->d_psi, ctx->d_psi_sh, ctx->logN,
-                                                            ctx->L, ctx->logN / 2, io));
+    const double bytes = (double)b.npoly * b.nr * ctx->N * 16.0;
+    if (INV)
+        TIMED("ntt_inv", bytes, s,
+              k_ntt_inv_cluster<CL, IO><<<grid, NT2, smem, s>>>(b, ctx->d_prime, ctx->d_ipsi, ctx->d_ipsi_sh,
+                                                                ctx->logN, ctx->L, ctx->logN / 2, io));
+    else
+        TIMED("ntt_fwd", bytes, s,
+              k_ntt_fwd_cluster<CL, IO><<<grid, NT2, smem, s>>>(b, ctx->d_prime, ctx->d_psi, ctx->d_psi_sh, ctx->logN,
+                                                                ctx->L, ctx->logN / 2, io));
     LAUNCH_CHECK();
     return COPSE_OK;
 }
 
-template <class IO>
+template <bool INV = false, class IO>
 copse_status launch_fused(copse_ctx *ctx, const NttBatch &b, const IO &io, cudaStream_t s, bool *done) {
     *done = false;
     if (b.npoly <= 0 || b.nr <= 0) { *done = true; return COPSE_OK; }
     if (!ctx->ntt_clusters || (long)b.npoly * b.nr > ctx->ntt_cluster_max) return COPSE_OK;
-    if (ctx->logN == 12) STATUS_TRY((launch_cluster_io<2, IO>(ctx, b, io, s)));
-    else if (ctx->logN == 13) STATUS_TRY((launch_cluster_io<4, IO>(ctx, b, io, s)));
-    else if (ctx->logN == 14) STATUS_TRY((launch_cluster_io<8, IO>(ctx, b, io, s)));
+    if (ctx->logN == 12) STATUS_TRY((launch_cluster_io<2, INV, IO>(ctx, b, io, s)));
+    else if (ctx->logN == 13) STATUS_TRY((launch_cluster_io<4, INV, IO>(ctx, b, io, s)));
+    else if (ctx->logN == 14) STATUS_TRY((launch_cluster_io<8, INV, IO>(ctx, b, io, s)));
     else return COPSE_OK;
     *done = true;
     return COPSE_OK;
@@ -657,6 +728,22 @@ copse_status ntt_forward_moddown(copse_ctx *ctx, const MdFuse &f, int njobs, cud
     if (njobs > MD_JOBS) { set_error("internal: too many ModDown jobs"); return COPSE_EINVAL; }
     NttBatch b{nullptr, 0, 2 * njobs, 0, f.ell, f.ell, -1};
     return launch_fused(ctx, b, MdIO{f, ctx->d_prime, ctx->ks, ctx->L, ctx->alpha, ctx->logN}, s, done);
+}
+
+copse_status ntt_inverse_copy(copse_ctx *ctx, const u64 *src, size_t sstride, u64 *dst, size_t dstride, int npoly,
+                              int nr, int fixed, cudaStream_t s, bool *done) {
+    NttBatch b{nullptr, 0, npoly, 0, nr, nr, fixed};
+    return launch_fused<true>(ctx, b, CopyIO{src, sstride, dst, dstride, ctx->logN}, s, done);
+}
+
+copse_status ntt_forward_modup(copse_ctx *ctx, const u64 *xc, const u64 *x_ntt, size_t xs, u64 *y, int n_items,
+                               int ell, cudaStream_t s, bool *done) {
+    const int A = ctx->alpha, nd = (ell + A - 1) / A;
+    NttBatch b{nullptr, 0, n_items * nd, 0, ell + A, ell, -1};
+    b.skip_alpha = A;
+    b.skip_period = nd;
+    return launch_fused(ctx, b, MuIO{xc, x_ntt, xs, y, ell, A, nd, ctx->L, ctx->NP, ctx->logN, ctx->d_prime, ctx->ks},
+                        s, done);
 }
 
 copse_status modswitch_finish(copse_ctx *ctx, const MsFuse &f, const u64 *W, int nc, cudaStream_t s) {

@@ -531,44 +531,46 @@ NttBatch batch(u64 *data, size_t stride, int npoly, int r0, int nr, int ell, int
 }
 
 // ModUp of x (NTT domain [ell][N]) for every digit; result NTT domain [nd][ell+alpha][N]
-copse_status ks_modup(copse_ctx *c, const u64 *x_ntt, int ell, Scratch &sc, u64 **yhat, cudaStream_t s) {
-    const int N = c->N, A = c->alpha, nx = ell + A, nd = (ell + A - 1) / A;
-    u64 *xc = nullptr, *y = nullptr;
-    STATUS_TRY(sc.get(c, &xc, (size_t)ell * N));
-    STATUS_TRY(sc.get(c, &y, (size_t)nd * nx * N));
-    CUDA_TRY(cudaMemcpyAsync(xc, x_ntt, (size_t)ell * N * sizeof(u64), cudaMemcpyDeviceToDevice, s));
-    STATUS_TRY(ntt_inverse(c, batch(xc, (size_t)ell * N, 1, 0, ell, ell), s));
-    TIMED("modup", 8.0 * N * ((double)ell + (double)nd * nx), s, k_modup<<<nblk((size_t)nd * N), TPB, 0, s>>>(xc, x_ntt, 0, y, ell, A, c->L, c->NP, c->logN, c->d_prime, c->ks));
-    LAUNCH_CHECK();
-    // the digit's own primes already hold the input's NTT values: skip them
-    NttBatch nb = batch(y, (size_t)nx * N, nd, 0, nx, ell);
-    nb.skip_alpha = A;
-    STATUS_TRY(ntt_forward(c, nb, s));
-    *yhat = y;
-    return COPSE_OK;
-}
-
-// ModUp of n inputs x_ntt + i * xs (NTT domain [ell][N] each) in one pass of
-// launches; result NTT domain [n][nd][ell+alpha][N]
+// ModUp of n inputs x_ntt + i * xs (NTT domain [ell][N] each); result NTT domain
+// [n][nd][ell+alpha][N].  Where the cluster transform applies: an out-of-place inverse
+// transform, then one forward transform whose load does the digits' base conversion
+// (and whose skipped blocks copy the digits' own residues); else a copy, an in-place
+// inverse transform, the conversion kernel and a forward transform.
 copse_status ks_modup_batch(copse_ctx *c, const u64 *x_ntt, size_t xs, int n, int ell, Scratch &sc, u64 **yhat,
                             cudaStream_t s) {
     const int N = c->N, A = c->alpha, nx = ell + A, nd = (ell + A - 1) / A;
     u64 *xc = nullptr, *y = nullptr;
     STATUS_TRY(sc.get(c, &xc, (size_t)n * ell * N));
     STATUS_TRY(sc.get(c, &y, (size_t)n * nd * nx * N));
-    CUDA_TRY(cudaMemcpy2DAsync(xc, (size_t)ell * N * sizeof(u64), x_ntt, xs * sizeof(u64), (size_t)ell * N * sizeof(u64),
-                               n, cudaMemcpyDeviceToDevice, s));
-    STATUS_TRY(ntt_inverse(c, batch(xc, (size_t)ell * N, n, 0, ell, ell), s));
-    TIMED("modup", 8.0 * N * n * ((double)ell + (double)nd * nx), s,
-          k_modup<<<dim3(nblk((size_t)nd * N), n), TPB, 0, s>>>(xc, x_ntt, xs, y, ell, A, c->L, c->NP, c->logN,
-                                                                 c->d_prime, c->ks));
-    LAUNCH_CHECK();
-    NttBatch nb = batch(y, (size_t)nx * N, n * nd, 0, nx, ell);
-    nb.skip_alpha = A;
-    nb.skip_period = nd;
-    STATUS_TRY(ntt_forward(c, nb, s));
+    bool done = false;
+    STATUS_TRY(ntt_inverse_copy(c, x_ntt, xs, xc, (size_t)ell * N, n, ell, -1, s, &done));
+    if (!done) {
+        if (n == 1)
+            CUDA_TRY(cudaMemcpyAsync(xc, x_ntt, (size_t)ell * N * sizeof(u64), cudaMemcpyDeviceToDevice, s));
+        else
+            CUDA_TRY(cudaMemcpy2DAsync(xc, (size_t)ell * N * sizeof(u64), x_ntt, xs * sizeof(u64),
+                                       (size_t)ell * N * sizeof(u64), n, cudaMemcpyDeviceToDevice, s));
+        STATUS_TRY(ntt_inverse(c, batch(xc, (size_t)ell * N, n, 0, ell, ell), s));
+    }
+    STATUS_TRY(ntt_forward_modup(c, xc, x_ntt, xs, y, n, ell, s, &done));
+    if (!done) {
+        TIMED("modup", 8.0 * N * n * ((double)ell + (double)nd * nx), s,
+              k_modup<<<dim3(nblk((size_t)nd * N), n), TPB, 0, s>>>(xc, x_ntt, xs, y, ell, A, c->L, c->NP, c->logN,
+                                                                     c->d_prime, c->ks));
+        LAUNCH_CHECK();
+        // the digit's own primes already hold the input's NTT values: skip them
+        NttBatch nb = batch(y, (size_t)nx * N, n * nd, 0, nx, ell);
+        nb.skip_alpha = A;
+        nb.skip_period = nd;
+        STATUS_TRY(ntt_forward(c, nb, s));
+    }
     *yhat = y;
     return COPSE_OK;
+}
+
+// ModUp of x (NTT domain [ell][N]) for every digit; result NTT domain [nd][ell+alpha][N]
+copse_status ks_modup(copse_ctx *c, const u64 *x_ntt, int ell, Scratch &sc, u64 **yhat, cudaStream_t s) {
+    return ks_modup_batch(c, x_ntt, 0, 1, ell, sc, yhat, s);
 }
 
 // ModDown of nj extended-basis sums U [nj][2][ell+alpha][N] (NTT domain) finished as f
@@ -653,9 +655,17 @@ copse_status op_modswitch(copse_ctx *c, const DCt &in, DCt *out, cudaStream_t s)
     Scratch sc(s);
     u64 *last = nullptr;
     STATUS_TRY(sc.get(c, &last, (size_t)nc * N));
-    CUDA_TRY(cudaMemcpy2DAsync(last, (size_t)N * sizeof(u64), in.data + (size_t)(ell - 1) * N,
-                               (size_t)ell * N * sizeof(u64), (size_t)N * sizeof(u64), nc, cudaMemcpyDeviceToDevice, s));
-    STATUS_TRY(ntt_inverse(c, batch(last, N, nc, 0, 1, ell, ell - 1), s));
+    // the dropped prime's residues in coefficient form: out of place where the cluster
+    // transform applies, else a copy and an in-place inverse transform
+    bool inv_done = false;
+    STATUS_TRY(ntt_inverse_copy(c, in.data + (size_t)(ell - 1) * N, (size_t)ell * N, last, N, nc, 1, ell - 1, s,
+                                &inv_done));
+    if (!inv_done) {
+        CUDA_TRY(cudaMemcpy2DAsync(last, (size_t)N * sizeof(u64), in.data + (size_t)(ell - 1) * N,
+                                   (size_t)ell * N * sizeof(u64), (size_t)N * sizeof(u64), nc, cudaMemcpyDeviceToDevice,
+                                   s));
+        STATUS_TRY(ntt_inverse(c, batch(last, N, nc, 0, 1, ell, ell - 1), s));
+    }
     STATUS_TRY(ct_alloc(c, out, ell - 1, nc, s));
     // conversion of the dropped prime's residue to the others, transform and finish in one
     // launch where the cluster transform applies; else conversion, transform, finish
