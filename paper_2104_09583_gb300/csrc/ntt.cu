@@ -660,6 +660,13 @@ copse_status launch(copse_ctx *ctx, const NttBatch &b, cudaStream_t s, bool inve
     return COPSE_OK;
 }
 
+// kernel-timer family of each transform variant
+template <class IO> constexpr const char *io_family(bool inv) { return inv ? "ntt_inv" : "ntt_fwd"; }
+template <> constexpr const char *io_family<CopyIO>(bool) { return "ntt_inv_copy"; }
+template <> constexpr const char *io_family<MsIO>(bool) { return "ntt_fwd_ms"; }
+template <> constexpr const char *io_family<MdIO>(bool) { return "ntt_fwd_md"; }
+template <> constexpr const char *io_family<MuIO>(bool) { return "ntt_fwd_mu"; }
+
 template <int CL, bool INV, class IO>
 copse_status launch_cluster_io(copse_ctx *ctx, const NttBatch &b, const IO &io, cudaStream_t s) {
     static bool attr_set = false;
@@ -674,11 +681,11 @@ copse_status launch_cluster_io(copse_ctx *ctx, const NttBatch &b, const IO &io, 
     const unsigned grid = (unsigned)b.npoly * (unsigned)b.nr * CL;
     const double bytes = (double)b.npoly * b.nr * ctx->N * 16.0;
     if (INV)
-        TIMED("ntt_inv", bytes, s,
+        TIMED(io_family<IO>(true), bytes, s,
               k_ntt_inv_cluster<CL, IO><<<grid, NT2, smem, s>>>(b, ctx->d_prime, ctx->d_ipsi, ctx->d_ipsi_sh,
                                                                 ctx->logN, ctx->L, ctx->logN / 2, io));
     else
-        TIMED("ntt_fwd", bytes, s,
+        TIMED(io_family<IO>(false), bytes, s,
               k_ntt_fwd_cluster<CL, IO><<<grid, NT2, smem, s>>>(b, ctx->d_prime, ctx->d_psi, ctx->d_psi_sh, ctx->logN,
                                                                 ctx->L, ctx->logN / 2, io));
     LAUNCH_CHECK();
