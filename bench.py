@@ -480,6 +480,7 @@ def run_serving(local, rate=200.0, n_req=1000, warm=100, seed=5, tune=True):
     t0 = time.perf_counter()
     th.start()
     lat, ok, t_first, t_last = [], True, None, None
+    lat_by = {k: [] for k in range(len(specs))}
     for _ in range(total):
         i, k, t = tickets.get()
         if t is None:
@@ -488,6 +489,7 @@ def run_serving(local, rate=200.0, n_req=1000, warm=100, seed=5, tune=True):
         ok &= bool(np.array_equal(bits, K.copse_classify_plain(models[k], qs[i][None, :])[0]))
         if i >= warm:
             lat.append(ms)
+            lat_by[k].append(ms)
             now = time.perf_counter()
             t_first = t_first if t_first is not None else now
             t_last = now
@@ -506,6 +508,8 @@ def run_serving(local, rate=200.0, n_req=1000, warm=100, seed=5, tune=True):
             "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(np.mean(lat)), "labels_ok": ok,
             "models": [f"{i['n_trees']} trees, {i['b']} branches, block {i['block']}, N = 2^{sp[3]}"
                        for i, sp in zip(infos, specs)],
+            "per_model": [{"requests": len(v), "p50_ms": float(np.percentile(v, 50)) if v else None,
+                           "p99_ms": float(np.percentile(v, 99)) if v else None} for v in lat_by.values()],
             "wall_s": wall}
 
 

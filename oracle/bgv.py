@@ -92,6 +92,7 @@ def lib():
                                  np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS"), u64p]),
             "or_rotsum": (None, [P, C.POINTER(C.c_void_p), C.c_int, C.c_int, u64p, C.POINTER(C.c_void_p), u64p]),
             "or_encrypt_sk": (None, [P, i64p, i64p, C.c_uint64, C.c_uint64, C.c_int, u64p]),
+            "or_relin_drop": (None, [P, u64p, C.c_int, u64p, u64p]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -431,6 +432,14 @@ class Bgv:
         self.L.or_rotsum(P.c, ptrs, ell, n, g, keys, out)
         return out
 
+    def relin_drop(self, ct3, rlk) -> np.ndarray:
+        """Relinearise and drop one prime in one ModDown over P q_{ell-1} (see or_relin_drop)."""
+        ell = ct3.shape[1]
+        out = np.zeros((2, ell - 1, self.P.N), dtype=np.uint64)
+        self.L.or_relin_drop(self.P.c, np.ascontiguousarray(ct3), ell, rlk, out)
+        return out
+
     def mul(self, a, b, rlk) -> np.ndarray:
-        """ct x ct: tensor, relinearise, then drop one prime (the canonical policy)."""
-        return self.modswitch(self.relin(self.tensor(a, b), rlk))
+        """ct x ct: tensor, then relinearise and drop one prime (the canonical policy) in one
+        ModDown over P q_{ell-1}."""
+        return self.relin_drop(self.tensor(a, b), rlk)

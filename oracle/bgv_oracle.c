@@ -719,6 +719,65 @@ void or_relin(const or_params *P, const u64 *ct3, int ell, const u64 *rlk, u64 *
     free(ks);
 }
 
+/* ModDown over P and the ciphertext prime q_{ell-1} together: u over
+ * {q_0..q_{ell-1}, p_0..p_{alpha-1}} -> out over q_0..q_{ell-2}, dividing by
+ * B = q_{ell-1} P with the t-multiple correction (fast base conversion with
+ * centred digits over the basis b_0 = q_{ell-1}, b_k = p_{k-1}):
+ *   y_k = [u_{b_k} t^-1 (B/b_k)^-1]_{b_k} centred,  W = sum_k y_k (B/b_k),
+ *   out_i = (u_i - t W) B^-1 mod q_i   (i < ell - 1). */
+static void moddown_drop(const or_params *P, const u64 *u, int ell, u64 *out)
+{
+    int N = P->N, A = P->alpha, L = P->L, nb = A + 1;
+    u64 bp[OR_MAXP];
+    int bres[OR_MAXP];
+    bp[0] = P->primes[ell - 1];
+    bres[0] = ell - 1;
+    for (int k = 1; k < nb; k++) { bp[k] = P->primes[L + k - 1]; bres[k] = ell + k - 1; }
+    for (int n = 0; n < N; n++) {
+        i64 yc[OR_MAXP];
+        for (int k = 0; k < nb; k++) {
+            u64 bk = bp[k], bhat = 1;
+            for (int m = 0; m < nb; m++) if (m != k) bhat = mulmod(bhat, bp[m] % bk, bk);
+            u64 v = mulmod(u[(size_t)bres[k] * N + n], invmod(P->t % bk, bk), bk);
+            yc[k] = centred(mulmod(v, invmod(bhat, bk), bk), bk);
+        }
+        for (int i = 0; i < ell - 1; i++) {
+            u64 q = P->primes[i], W = 0, B = 1;
+            for (int k = 0; k < nb; k++) {
+                u64 bhat = 1;
+                for (int m = 0; m < nb; m++) if (m != k) bhat = mulmod(bhat, bp[m] % q, q);
+                W = addmod(W, mulmod(from_signed(yc[k], q), bhat, q), q);
+                B = mulmod(B, bp[k] % q, q);
+            }
+            u64 v = submod(u[(size_t)i * N + n], mulmod(P->t % q, W, q), q);
+            out[(size_t)i * N + n] = mulmod(v, invmod(B, q), q);
+        }
+    }
+}
+
+/* Relinearise a 3-component ciphertext and drop one prime in one ModDown:
+ * acc = KSraw(d2) + (P d0, P d1) over q_0..q_{ell-1}, p_0..p_{alpha-1} (P times
+ * the relinearised ciphertext up to key-switching noise), then
+ * out = ModDown over P q_{ell-1} (moddown_drop): the relinearised product at level
+ * ell - 1 with one rounding.  out: [2][ell-1][N]. */
+void or_relin_drop(const or_params *P, const u64 *ct3, int ell, const u64 *rlk, u64 *out)
+{
+    int N = P->N, nx = ell + P->alpha;
+    u64 *acc = malloc(sizeof(u64) * 2 * nx * N);
+    keyswitch_raw(P, ct3 + (size_t)2 * ell * N, ell, rlk, acc);
+    for (int c = 0; c < 2; c++)
+        for (int r = 0; r < ell; r++) {
+            u64 q = P->primes[r], Pm = 1;
+            for (int k = 0; k < P->alpha; k++) Pm = mulmod(Pm, P->primes[P->L + k] % q, q);
+            u64 *a = acc + ((size_t)c * nx + r) * N;
+            const u64 *d = ct3 + ((size_t)c * ell + r) * N;
+            for (int j = 0; j < N; j++) a[j] = addmod(a[j], mulmod(Pm, d[j], q), q);
+        }
+    moddown_drop(P, acc, ell, out);
+    moddown_drop(P, acc + (size_t)nx * N, ell, out + (size_t)(ell - 1) * N);
+    free(acc);
+}
+
 /* rotation by Galois element g: (tau_g c0 + ks0, ks1) with (ks0, ks1) = KS(tau_g c1, gk) */
 void or_rotate(const or_params *P, const u64 *ct, int ell, u64 g, const u64 *gk, u64 *out)
 {

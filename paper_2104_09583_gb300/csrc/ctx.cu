@@ -234,6 +234,41 @@ static copse_status build_tables(copse_ctx *c) {
         ms_tinv[ell] = mk_shoup(h_inv(c->t % ql, ql), ql);
         for (int i = 0; i < ell - 1; i++) ms_qinv[(size_t)ell * L + i] = mk_shoup(h_inv(ql % c->primes[i], c->primes[i]), c->primes[i]);
     }
+    // ModDown over P q_{ell-1} (a relinearisation that also drops a prime): basis
+    // b_0 = q_{ell-1}, b_k = p_{k-1}, B = their product
+    const int nb = A + 1;
+    std::vector<Shoup> mdd_inv((size_t)(L + 1) * nb), mdd_hat((size_t)(L + 1) * nb * L), mdd_Binv((size_t)(L + 1) * L);
+    std::vector<u64> mdd_B((size_t)(L + 1) * L);
+    for (int ell = 2; ell <= L; ell++) {
+        std::vector<u64> bp(nb);
+        bp[0] = c->primes[ell - 1];
+        for (int k = 1; k < nb; k++) bp[k] = c->primes[L + k - 1];
+        for (int k = 0; k < nb; k++) {
+            const u64 bk = bp[k];
+            u64 bh = 1;
+            for (int m = 0; m < nb; m++)
+                if (m != k) bh = h_mul(bh, bp[m] % bk, bk);
+            mdd_inv[(size_t)ell * nb + k] = mk_shoup(h_mul(h_inv(c->t % bk, bk), h_inv(bh, bk), bk), bk);
+            for (int i = 0; i < ell - 1; i++) {
+                const u64 qi = c->primes[i];
+                u64 bhi = 1;
+                for (int m = 0; m < nb; m++)
+                    if (m != k) bhi = h_mul(bhi, bp[m] % qi, qi);
+                mdd_hat[((size_t)ell * nb + k) * L + i] = mk_shoup(bhi, qi);
+            }
+        }
+        for (int i = 0; i < ell - 1; i++) {
+            const u64 qi = c->primes[i];
+            u64 B = 1;
+            for (int k = 0; k < nb; k++) B = h_mul(B, bp[k] % qi, qi);
+            mdd_B[(size_t)ell * L + i] = B;
+            mdd_Binv[(size_t)ell * L + i] = mk_shoup(h_inv(B, qi), qi);
+        }
+    }
+    STATUS_TRY(upload(c, &c->ks.mdd_inv, mdd_inv));
+    STATUS_TRY(upload(c, &c->ks.mdd_hat, mdd_hat));
+    STATUS_TRY(upload(c, &c->ks.mdd_B, mdd_B));
+    STATUS_TRY(upload(c, &c->ks.mdd_Binv, mdd_Binv));
     STATUS_TRY(upload(c, &c->ks.modup_inv, modup_inv));
     STATUS_TRY(upload(c, &c->ks.modup_hat, modup_hat));
     STATUS_TRY(upload(c, &c->ks.modup_qhat, modup_qhat));

@@ -147,6 +147,13 @@ struct KsTables {
     // ms_qinv[ell][i] = q_{ell-1}^-1 mod q_i
     Shoup *ms_tinv;     // [L+1]
     Shoup *ms_qinv;     // [(L+1) * L]
+    // ModDown over B = q_{ell-1} P (relinearise and drop a prime), basis b_0 = q_{ell-1},
+    // b_k = p_{k-1}: mdd_inv[ell][k] = t^-1 (B/b_k)^-1 mod b_k; mdd_hat[ell][k][i] = B/b_k mod q_i;
+    // mdd_B[ell][i] = B mod q_i; mdd_Binv[ell][i] = B^-1 mod q_i  (i < ell - 1)
+    Shoup *mdd_inv;     // [(L+1) * (alpha+1)]
+    Shoup *mdd_hat;     // [(L+1) * (alpha+1) * L]
+    u64 *mdd_B;         // [(L+1) * L]
+    Shoup *mdd_Binv;    // [(L+1) * L]
     // gadget factor of key-switching keys: P mod q_i (i < L)
 };
 
@@ -274,6 +281,18 @@ struct MdFuse {
     int add_comps;
     u64 gal[MD_JOBS];         // 1 = no permutation
 };
+// ModDown over B = q_{ell-1} P of npoly polynomials U (stride ustride) whose residues
+// ell-1 .. ell+alpha-1 are in coefficient form: the transform's input is their centred
+// conversion to q_0..q_{ell-2}, its output goes straight into
+//   out[p][i] = (U[p][i] - t * NTT(conv)) * B^-1   (i < ell - 1).
+struct MddFuse {
+    const u64 *U;
+    size_t ustride;
+    int ell;
+    u64 *out;         // [npoly][ell-1][N]
+};
+copse_status ntt_forward_moddown_drop(copse_ctx *ctx, const MddFuse &f, int npoly, cudaStream_t s, bool *done);
+copse_status moddown_drop_unfused(copse_ctx *ctx, const MddFuse &f, int npoly, cudaStream_t s);
 // The fused forms run on the cluster transform (2^12 <= N <= 2^14); *done = false
 // (nothing launched) otherwise, and the caller takes the unfused sequence.
 copse_status ntt_forward_modswitch(copse_ctx *ctx, const MsFuse &f, int nc, cudaStream_t s, bool *done);

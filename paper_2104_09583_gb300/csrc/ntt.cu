@@ -379,6 +379,31 @@ __device__ __forceinline__ void md_store(const MdFuse &f, const PrimeDev *pr, co
     f.out[job][(size_t)c * f.ocomp + ((size_t)r << logN) + k] = res;
 }
 
+// conversion of polynomial p's residues ell-1 .. ell+alpha-1 (basis of q_{ell-1} P) to q_r
+__device__ __forceinline__ u64 mdd_load(const MddFuse &f, const PrimeDev *pr, const KsTables &T, int L, int alpha,
+                                        int logN, int p, int r, size_t n) {
+    const int nb = alpha + 1, ell = f.ell;
+    const u64 *up = f.U + (size_t)p * f.ustride;
+    const u64 qi = pr[r].q;
+    u64 acc = 0;
+    for (int k = 0; k < nb; k++) {
+        const u64 bk = k == 0 ? pr[ell - 1].q : pr[L + k - 1].q;
+        const u64 y = mul_shoup(up[((size_t)(ell - 1 + k) << logN) + n], T.mdd_inv[(size_t)ell * nb + k], bk);
+        u64 v = mul_shoup(y, T.mdd_hat[((size_t)ell * nb + k) * L + r], qi);
+        if (y > (bk - 1) / 2) v = sub_mod(v, T.mdd_B[(size_t)ell * L + r], qi);
+        acc = add_mod(acc, v, qi);
+    }
+    return acc;
+}
+
+__device__ __forceinline__ void mdd_store(const MddFuse &f, const PrimeDev *pr, const KsTables &T, int L, int logN,
+                                          int p, int r, size_t k, u64 v) {
+    const PrimeDev P = pr[r];
+    const u64 uv = f.U[(size_t)p * f.ustride + ((size_t)r << logN) + k];
+    f.out[(((size_t)p * (f.ell - 1) + r) << logN) + k] =
+        mul_shoup(sub_mod(uv, mul_shoup(v, P.t_mod, P.t_mod_sh, P.q), P.q), T.mdd_Binv[(size_t)f.ell * L + r], P.q);
+}
+
 // Load / store of the forward cluster transform: coefficient n of residue r (global
 // prime g) of batch polynomial p in; NTT-domain value v (in [0, q)) at position k out.
 struct PlainIO {
@@ -489,6 +514,21 @@ struct MdIO {
     }
     __device__ __forceinline__ void store(int p, int r, int, size_t k, u64 v) const {
         md_store(f, pr, T, logN, p, r, k, v);
+    }
+    __device__ __forceinline__ void skip(int, int, int, int) const {}
+};
+
+// relinearise-and-drop ModDown: load the conversion from the q_{ell-1} P basis, store the finish
+struct MddIO {
+    MddFuse f;
+    const PrimeDev *pr;
+    KsTables T;
+    int L, alpha, logN;
+    __device__ __forceinline__ u64 load(int p, int r, int, size_t n) const {
+        return mdd_load(f, pr, T, L, alpha, logN, p, r, n);
+    }
+    __device__ __forceinline__ void store(int p, int r, int, size_t k, u64 v) const {
+        mdd_store(f, pr, T, L, logN, p, r, k, v);
     }
     __device__ __forceinline__ void skip(int, int, int, int) const {}
 };
@@ -666,6 +706,7 @@ template <> constexpr const char *io_family<CopyIO>(bool) { return "ntt_inv_copy
 template <> constexpr const char *io_family<MsIO>(bool) { return "ntt_fwd_ms"; }
 template <> constexpr const char *io_family<MdIO>(bool) { return "ntt_fwd_md"; }
 template <> constexpr const char *io_family<MuIO>(bool) { return "ntt_fwd_mu"; }
+template <> constexpr const char *io_family<MddIO>(bool) { return "ntt_fwd_mdd"; }
 
 template <int CL, bool INV, class IO>
 copse_status launch_cluster_io(copse_ctx *ctx, const NttBatch &b, const IO &io, cudaStream_t s) {
@@ -715,6 +756,26 @@ __global__ void k_ms_finish_io(const MsFuse f, const u64 *W, int nc, const Prime
     ms_store(f, pr, T, L, logN, p, (int)(rem >> logN), rem & ((1ull << logN) - 1), W[e]);
 }
 
+__global__ void k_mdd_conv(const MddFuse f, u64 *W, int npoly, const PrimeDev *pr, KsTables T, int L, int alpha,
+                           int logN) {
+    const size_t per = (size_t)(f.ell - 1) << logN;
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (size_t)npoly * per) return;
+    const int p = (int)(e / per);
+    const size_t rem = e - p * per;
+    W[e] = mdd_load(f, pr, T, L, alpha, logN, p, (int)(rem >> logN), rem & ((1ull << logN) - 1));
+}
+
+__global__ void k_mdd_finish(const MddFuse f, const u64 *W, int npoly, const PrimeDev *pr, KsTables T, int L,
+                             int logN) {
+    const size_t per = (size_t)(f.ell - 1) << logN;
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (size_t)npoly * per) return;
+    const int p = (int)(e / per);
+    const size_t rem = e - p * per;
+    mdd_store(f, pr, T, L, logN, p, (int)(rem >> logN), rem & ((1ull << logN) - 1), W[e]);
+}
+
 __global__ void k_md_finish_io(const MdFuse f, const u64 *W, int njobs, const PrimeDev *pr, KsTables T, int logN) {
     const size_t per = (size_t)f.ell << logN;
     const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -751,6 +812,32 @@ copse_status ntt_forward_modup(copse_ctx *ctx, const u64 *xc, const u64 *x_ntt, 
     b.skip_period = nd;
     return launch_fused(ctx, b, MuIO{xc, x_ntt, xs, y, ell, A, nd, ctx->L, ctx->NP, ctx->logN, ctx->d_prime, ctx->ks},
                         s, done);
+}
+
+copse_status ntt_forward_moddown_drop(copse_ctx *ctx, const MddFuse &f, int npoly, cudaStream_t s, bool *done) {
+    NttBatch b{nullptr, 0, npoly, 0, f.ell - 1, f.ell - 1, -1};
+    return launch_fused(ctx, b, MddIO{f, ctx->d_prime, ctx->ks, ctx->L, ctx->alpha, ctx->logN}, s, done);
+}
+
+copse_status moddown_drop_unfused(copse_ctx *ctx, const MddFuse &f, int npoly, cudaStream_t s) {
+    const size_t n = (size_t)npoly * (f.ell - 1) * ctx->N;
+    u64 *W = nullptr;
+    STATUS_TRY(dev_alloc(ctx, (void **)&W, n * sizeof(u64), s));
+    const unsigned g = (unsigned)((n + 255) / 256);
+    TIMED("moddown_conv", 8.0 * (double)n * (ctx->alpha + 2), s,
+          k_mdd_conv<<<g, 256, 0, s>>>(f, W, npoly, ctx->d_prime, ctx->ks, ctx->L, ctx->alpha, ctx->logN));
+    copse_status st = cudaGetLastError() == cudaSuccess ? COPSE_OK : COPSE_ECUDA;
+    if (st == COPSE_OK) st = launch(ctx, NttBatch{W, (size_t)(f.ell - 1) * ctx->N, npoly, 0, f.ell - 1, f.ell - 1, -1},
+                                    s, false);
+    if (st == COPSE_OK) {
+        TIMED("ks_finish", 8.0 * 3.0 * (double)n, s,
+              k_mdd_finish<<<g, 256, 0, s>>>(f, W, npoly, ctx->d_prime, ctx->ks, ctx->L, ctx->logN));
+        if (cudaGetLastError() != cudaSuccess) st = COPSE_ECUDA;
+    }
+    dev_free(W, s);
+    if (st != COPSE_OK && st != COPSE_ECUDA) return st;
+    if (st == COPSE_ECUDA) set_error("moddown-drop kernels failed to launch");
+    return st;
 }
 
 copse_status modswitch_finish(copse_ctx *ctx, const MsFuse &f, const u64 *W, int nc, cudaStream_t s) {

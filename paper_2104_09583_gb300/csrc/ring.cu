@@ -136,6 +136,7 @@ struct InnerJob {
     u64 *out;                // [2][ell+alpha][N]
     u64 g;                   // Galois element applied to the ModUp output, 1 = none
     const u64 *y = nullptr;  // this job's own ModUp digits (null = the launch's shared ones)
+    const u64 *pd = nullptr; // adds P * (pd[0], pd[1]) ([2][ell][N]) to the sum's q-residues
 };
 // a launch's jobs, passed by value (kernel parameter space): no host-to-device copy
 struct InnerJobs {
@@ -144,7 +145,7 @@ struct InnerJobs {
 
 // (u0, u1)[r][n] = sum_j yhat[j][r][tau_g n] * ksk[j][c][ext_prime(r)][n]
 __global__ void k_ks_inner(const u64 *yhat, const InnerJobs jobs, int ell, int alpha, int L, int logN,
-                           const PrimeDev *pr) {
+                           const PrimeDev *pr, const u64 *mdP) {
     const int N = 1 << logN;
     const int nx = ell + alpha, nd = (ell + alpha - 1) / alpha;
     const int NB = L + alpha;
@@ -164,6 +165,11 @@ __global__ void k_ks_inner(const u64 *yhat, const InnerJobs jobs, int ell, int a
         const u64 *k1 = J.ksk + (((size_t)(2 * j + 1) * NB + g) << logN);
         acc0 = add_mod(acc0, mul_mod(y, k0[n], P), P.q);
         acc1 = add_mod(acc1, mul_mod(y, k1[n], P), P.q);
+    }
+    if (J.pd && r < ell) {
+        const u64 Pm = mdP[r];
+        acc0 = add_mod(acc0, mul_mod(Pm, J.pd[((size_t)r << logN) + n], P), P.q);
+        acc1 = add_mod(acc1, mul_mod(Pm, J.pd[((size_t)(ell + r) << logN) + n], P), P.q);
     }
     J.out[e] = acc0;
     J.out[((size_t)nx << logN) + e] = acc1;
@@ -603,9 +609,34 @@ copse_status ks_apply(copse_ctx *c, const u64 *yhat, int ell, const std::vector<
     InnerJobs jobs;
     for (int i = 0; i < nj; i++) jobs.j[i] = jobs_h[i];
     dim3 grid(nblk((size_t)nx * N), nj);
-    TIMED("ks_inner", 8.0 * N * ((double)((ell + A - 1) / A) * nx + (double)nj * (2.0 * ((ell + A - 1) / A) * nx + 2.0 * nx)), s, k_ks_inner<<<grid, TPB, 0, s>>>(yhat, jobs, ell, A, c->L, c->logN, c->d_prime));
+    TIMED("ks_inner", 8.0 * N * ((double)((ell + A - 1) / A) * nx + (double)nj * (2.0 * ((ell + A - 1) / A) * nx + 2.0 * nx)), s, k_ks_inner<<<grid, TPB, 0, s>>>(yhat, jobs, ell, A, c->L, c->logN, c->d_prime, c->ks.md_P));
     LAUNCH_CHECK();
     return moddown_apply(c, U, ell, nj, f, sc, s);
+}
+
+// Relinearise a 3-component ciphertext d [3][ell][N] and drop one prime in one ModDown:
+// U = KSraw(d2) + P (d0, d1) over the extended basis, then ModDown over q_{ell-1} P.
+copse_status relin_drop(copse_ctx *c, const copse_evk *evk, const u64 *d, int ell, DCt *out, Scratch &sc,
+                        cudaStream_t s) {
+    const int N = c->N, A = c->alpha, nx = ell + A;
+    u64 *yhat = nullptr, *U = nullptr;
+    STATUS_TRY(ks_modup(c, d + (size_t)2 * ell * N, ell, sc, &yhat, s));
+    STATUS_TRY(sc.get(c, &U, (size_t)2 * nx * N));
+    InnerJobs jobs;
+    jobs.j[0] = InnerJob{evk->rlk, U, 1, nullptr, d};
+    TIMED("ks_inner", 8.0 * N * ((double)((ell + A - 1) / A) * nx + 2.0 * ((ell + A - 1) / A) * nx + 2.0 * nx + 2.0 * ell), s,
+          k_ks_inner<<<dim3(nblk((size_t)nx * N), 1), TPB, 0, s>>>(yhat, jobs, ell, A, c->L, c->logN, c->d_prime,
+                                                                    c->ks.md_P));
+    LAUNCH_CHECK();
+    // the dropped prime's and the special residues to coefficients, then the fused
+    // conversion + transform + finish (or conversion, transform, finish)
+    STATUS_TRY(ntt_inverse(c, batch(U, (size_t)nx * N, 2, ell - 1, A + 1, ell), s));
+    STATUS_TRY(ct_alloc(c, out, ell - 1, 2, s));
+    const MddFuse f{U, (size_t)nx * N, ell, out->data};
+    bool done = false;
+    STATUS_TRY(ntt_forward_moddown_drop(c, f, 2, s, &done));
+    if (!done) STATUS_TRY(moddown_drop_unfused(c, f, 2, s));
+    return COPSE_OK;
 }
 
 MdFuse md_fuse() {
@@ -733,28 +764,15 @@ copse_status op_mul(copse_ctx *c, const copse_evk *evk, const DCt &a, const DCt 
     STATUS_TRY(aligned(c, a, b, &ta, &tb, &oa, &ob, s));
     const int ell = ta.level, N = c->N, A = c->alpha;
     Scratch sc(s);
-    u64 *d = nullptr, *U = nullptr, *yhat = nullptr;
+    u64 *d = nullptr;
     STATUS_TRY(sc.get(c, &d, (size_t)3 * ell * N));
     TIMED("tensor", 8.0 * N * 7.0 * ell, s, k_tensor<<<nblk((size_t)ell * N), TPB, 0, s>>>(ta.data, tb.data, d, ell, c->logN, c->d_prime));
     LAUNCH_CHECK();
     if (oa) ct_free(&ta, s);
     if (ob) ct_free(&tb, s);
-    STATUS_TRY(ks_modup(c, d + (size_t)2 * ell * N, ell, sc, &yhat, s));
-    STATUS_TRY(sc.get(c, &U, (size_t)2 * (ell + A) * N));
-    DCt r;
-    STATUS_TRY(ct_alloc(c, &r, ell, 2, s));
-    // relinearised: (d0, d1) + ModDown(KSraw(d2))
-    std::vector<InnerJob> jobs{InnerJob{evk->rlk, U, 1}};
-    MdFuse f = md_fuse();
-    f.out[0] = r.data;
-    f.ocomp = (size_t)ell * N;
-    f.add[0] = d;
-    f.acomp = (size_t)ell * N;
-    f.add_comps = 2;
-    STATUS_TRY(ks_apply(c, yhat, ell, jobs, U, f, sc, s));
-    copse_status st = op_modswitch(c, r, out, s);
-    ct_free(&r, s);
-    return st;
+    if (ell < 2) { set_error("multiplication at one prime: no prime left to drop"); return COPSE_ELEVEL; }
+    // relinearised and one prime dropped (the canonical policy), in one ModDown
+    return relin_drop(c, evk, d, ell, out, sc, s);
 }
 
 copse_status op_affine(copse_ctx *c, const DCt &x, const DPt &mul, const DPt *add, DCt *out, cudaStream_t s) {

@@ -200,3 +200,31 @@ def test_matmul_slot_semantics():
             if d is not None:
                 want = (want + d * _rot(v, k, P.N)) % T
         assert np.array_equal(bgv.decrypt_slots(keys.sk, out).astype(np.int64), want)
+
+
+def test_relin_drop_without_third_component_is_modswitch():
+    """With d2 = 0 the key-switching sum vanishes and the ModDown over P q_{ell-1} of
+    P (d0, d1) is exactly the modulus switch of (d0, d1): an identity between two
+    independently written routines."""
+    P, bgv, keys = _setup(6, 5, 50, 2)
+    rng = np.random.default_rng(8)
+    ct = bgv.encrypt_slots(keys.pk, rng.integers(0, T, size=P.N), 3, 0)
+    ct3 = np.concatenate([ct, np.zeros((1,) + ct.shape[1:], dtype=np.uint64)])
+    assert np.array_equal(bgv.relin_drop(ct3, keys.rlk), bgv.modswitch(ct))
+
+
+@pytest.mark.parametrize("logN,L,dnum", [(6, 5, 2), (10, 6, 3)])
+def test_relin_drop_decrypts_like_two_step_path(logN, L, dnum):
+    P, bgv, keys = _setup(logN, L, 50, dnum)
+    rng = np.random.default_rng(logN + L)
+    a, b = rng.integers(0, T, size=P.N), rng.integers(0, T, size=P.N)
+    ca, cb = bgv.encrypt_slots(keys.pk, a, 5, 0), bgv.encrypt_slots(keys.pk, b, 5, 1)
+    t3 = bgv.tensor(ca, cb)
+    one = bgv.relin_drop(t3, keys.rlk)
+    two = bgv.modswitch(bgv.relin(t3, keys.rlk))
+    assert one.shape == two.shape == (2, L - 1, P.N)
+    want = (a * b) % T
+    assert np.array_equal(bgv.decrypt_slots(keys.sk, one).astype(np.int64), want)
+    assert np.array_equal(bgv.decrypt_slots(keys.sk, two).astype(np.int64), want)
+    # one rounding instead of two: no more noise than the two-step path (within a bit)
+    assert bgv.noise_bits(keys.sk, one) <= bgv.noise_bits(keys.sk, two) + 1
