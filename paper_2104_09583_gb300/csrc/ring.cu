@@ -137,6 +137,7 @@ struct InnerJob {
     u64 g;                   // Galois element applied to the ModUp output, 1 = none
     const u64 *y = nullptr;  // this job's own ModUp digits (null = the launch's shared ones)
     const u64 *pd = nullptr; // adds P * (pd[0], pd[1]) ([2][ell][N]) to the sum's q-residues
+    const u64 *pc0 = nullptr;// adds P * tau_g(pc0) ([ell][N]) to component 0's q-residues
 };
 // a launch's jobs, passed by value (kernel parameter space): no host-to-device copy
 struct InnerJobs {
@@ -171,6 +172,7 @@ __global__ void k_ks_inner(const u64 *yhat, const InnerJobs jobs, int ell, int a
         acc0 = add_mod(acc0, mul_mod(Pm, J.pd[((size_t)r << logN) + n], P), P.q);
         acc1 = add_mod(acc1, mul_mod(Pm, J.pd[((size_t)(ell + r) << logN) + n], P), P.q);
     }
+    if (J.pc0 && r < ell) acc0 = add_mod(acc0, mul_mod(mdP[r], J.pc0[((size_t)r << logN) + src], P), P.q);
     J.out[e] = acc0;
     J.out[((size_t)nx << logN) + e] = acc1;
 }
@@ -215,6 +217,7 @@ __global__ void k_moddown_conv(const u64 *u, size_t ustride, u64 *W, size_t wstr
 struct MmJob {
     const u64 *ksk;  // [ndig][2][L+alpha][N] NTT domain
     u64 g;           // Galois element
+    const u64 *R;    // when set: R_k already computed, [2][ell+alpha][N]
 };
 struct MmTable {
     MmJob job[CHUNK_ROT];
@@ -248,16 +251,21 @@ __global__ void __launch_bounds__(256) k_mm_fused(const u64 *yhat, const u64 *c0
     }
     for (int k = k0; k < k1; k++) {
         const MmJob J = tab.job[k];
-        const uint32_t src = galois_src(n, J.g, logN);
         u64 u0 = 0, u1 = 0;
-        for (int j = 0; j < nd; j++) {
-            const u64 y = yhat[(((size_t)j * nx + r) << logN) + src];
-            const u64 *k0 = J.ksk + (((size_t)(2 * j) * NB + g) << logN);
-            const u64 *k1 = J.ksk + (((size_t)(2 * j + 1) * NB + g) << logN);
-            u0 = add_mod(u0, mul_mod(y, k0[n], P), P.q);
-            u1 = add_mod(u1, mul_mod(y, k1[n], P), P.q);
+        if (J.R) {
+            u0 = J.R[e];
+            u1 = J.R[n_el + e];
+        } else {
+            const uint32_t src = galois_src(n, J.g, logN);
+            for (int j = 0; j < nd; j++) {
+                const u64 y = yhat[(((size_t)j * nx + r) << logN) + src];
+                const u64 *k0 = J.ksk + (((size_t)(2 * j) * NB + g) << logN);
+                const u64 *k1 = J.ksk + (((size_t)(2 * j + 1) * NB + g) << logN);
+                u0 = add_mod(u0, mul_mod(y, k0[n], P), P.q);
+                u1 = add_mod(u1, mul_mod(y, k1[n], P), P.q);
+            }
+            if (r < ell) u0 = add_mod(u0, mul_mod(Pm, c0[((size_t)r << logN) + src], P), P.q);
         }
-        if (r < ell) u0 = add_mod(u0, mul_mod(Pm, c0[((size_t)r << logN) + src], P), P.q);
         for (int x = 0; x < nacc; x++) {
             const u64 *p = tab.pt[x * nrot + k];
             if (!p) continue;
@@ -858,6 +866,24 @@ copse_status op_matmul(copse_ctx *c, const copse_evk *evk, const DCt &v, const s
         u64 *yhat = nullptr;
         STATUS_TRY(ks_modup(c, v.data + (size_t)ell * N, ell, sc, &yhat, s));
         const int nd = (ell + A - 1) / A;
+        // more accumulators than one launch holds: compute every rotation's key-switched
+        // R_k = KSraw(tau_k c1) + (P tau_k c0, 0) once, instead of once per accumulator chunk
+        u64 *Rall = nullptr;
+        if (nacc > MAX_ACC) {
+            STATUS_TRY(sc.get(c, &Rall, ks_idx.size() * ext));
+            for (size_t k0 = 0; k0 < ks_idx.size(); k0 += CHUNK_ROT) {
+                const int nj = (int)std::min<size_t>(CHUNK_ROT, ks_idx.size() - k0);
+                InnerJobs jobs;
+                for (int i = 0; i < nj; i++) {
+                    const int r = ks_idx[k0 + i];
+                    jobs.j[i] = InnerJob{evk->find(gal[r]), Rall + (k0 + i) * ext, gal[r], nullptr, nullptr, v.data};
+                }
+                TIMED("ks_inner", 8.0 * N * nj * (2.0 * nd * nx + 2.0 * nx + ell), s,
+                      k_ks_inner<<<dim3(nblk((size_t)nx * N), nj), TPB, 0, s>>>(yhat, jobs, ell, A, c->L, c->logN,
+                                                                                 c->d_prime, c->ks.md_P));
+                LAUNCH_CHECK();
+            }
+        }
         for (size_t k0 = 0; k0 < ks_idx.size(); k0 += CHUNK_ROT) {
             const int nr = (int)std::min<size_t>(CHUNK_ROT, ks_idx.size() - k0);
             for (int a0 = 0; a0 < nacc; a0 += MAX_ACC) {
@@ -867,7 +893,7 @@ copse_status op_matmul(copse_ctx *c, const copse_evk *evk, const DCt &v, const s
                 int nz_pt = 0;
                 for (int x = 0; x < nr; x++) {
                     const int r = ks_idx[k0 + x];
-                    tab.job[x] = MmJob{evk->find(gal[r]), gal[r]};
+                    tab.job[x] = MmJob{evk->find(gal[r]), gal[r], Rall ? Rall + (k0 + x) * ext : nullptr};
                     for (int a = 0; a < na; a++) {
                         tab.pt[a * nr + x] = pt[a0 + a][r];
                         nz_pt += pt[a0 + a][r] != nullptr;
