@@ -258,11 +258,13 @@ copse_status ntt_inverse(copse_ctx *ctx, const NttBatch &b, cudaStream_t s);
 // centred conversion of last ([nc][N], coefficient form, [c_{ell-1} t^-1]) to
 // q_0..q_{ell-2}, its output goes straight into
 //   out[c][i] = (x[c][i] - t * NTT(conv)) * q_{ell-1}^-1.
+#define MS_POLYS 128
 struct MsFuse {
     const u64 *last;  // [nc][N] coefficient form
     const u64 *x;     // [nc][ell][N] NTT domain
-    u64 *out;         // [nc][ell-1][N]
+    u64 *out;         // [nc][ell-1][N], or per polynomial:
     int ell;
+    u64 *outp[MS_POLYS];  // when outp[0] is set: polynomial p's result [ell-1][N] at outp[p]
 };
 // ModDown finish of key-switching sums (job j = polys 2j, 2j+1): U (stride ustride
 // per poly) holds the extended-basis sum with its alpha special residues in

@@ -361,8 +361,8 @@ __device__ __forceinline__ void ms_store(const MsFuse &f, const PrimeDev *pr, co
     const PrimeDev P = pr[r];
     const u64 xv = f.x[(((size_t)p * f.ell + r) << logN) + k];
     const u64 d = mul_shoup(v, P.t_mod, P.t_mod_sh, P.q);
-    f.out[(((size_t)p * (f.ell - 1) + r) << logN) + k] =
-        mul_shoup(sub_mod(xv, d, P.q), T.ms_qinv[(size_t)f.ell * L + r], P.q);
+    u64 *o = f.outp[0] ? f.outp[p] + ((size_t)r << logN) + k : f.out + (((size_t)p * (f.ell - 1) + r) << logN) + k;
+    *o = mul_shoup(sub_mod(xv, d, P.q), T.ms_qinv[(size_t)f.ell * L + r], P.q);
 }
 
 // finishing arithmetic of a ModDown for value v = NTT(conversion) at (p = 2 job + c, r, k)

@@ -346,6 +346,32 @@ __global__ void k_ident_mac(u64 *out, const u64 *v, const u64 *pt, int ell, int 
     out[e] = add_mod(out[e], mul_mod(pt[k], v[e], P), P.q);
 }
 
+// The last step of matrix products for a batch of outputs (blockIdx.y = output a):
+// res_a += pt_mul_a * v + ct_add_a + ct_add2_a (+ pt_add_a on component 0), each term optional
+#define FIN_MAX 64
+struct FinTable {
+    u64 *res[FIN_MAX];             // [2][ell][N]
+    const u64 *pt_mul[FIN_MAX];    // first ell residues used
+    const u64 *ct_add[FIN_MAX];    // [2][ell][N]
+    const u64 *ct_add2[FIN_MAX];   // [2][ell][N]
+    const u64 *pt_add[FIN_MAX];    // [ell][N]
+};
+
+__global__ void k_finish(const FinTable tab, const u64 *v, int ell, int logN, const PrimeDev *pr) {
+    const size_t n = (size_t)ell << logN;
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= 2 * n) return;
+    const int a = blockIdx.y;
+    const size_t k = e < n ? e : e - n;
+    const PrimeDev P = pr[k >> logN];
+    u64 x = tab.res[a][e];
+    if (tab.pt_mul[a]) x = add_mod(x, mul_mod(tab.pt_mul[a][k], v[e], P), P.q);
+    if (tab.ct_add[a]) x = add_mod(x, tab.ct_add[a][e], P.q);
+    if (tab.ct_add2[a]) x = add_mod(x, tab.ct_add2[a][e], P.q);
+    if (e < n && tab.pt_add[a]) x = add_mod(x, tab.pt_add[a][k], P.q);
+    tab.res[a][e] = x;
+}
+
 // modulus switch, conversion step: last [ncomp][N] coefficients of q_{ell-1} ->
 // W [ncomp][ell-1][N] = [last * t^-1]_{q_{ell-1}} (centred) mod q_i
 __global__ void k_ms_conv(const u64 *last, u64 *W, int ncomp, int ell, int L, int logN, const PrimeDev *pr,
@@ -723,6 +749,43 @@ copse_status op_modswitch(copse_ctx *c, const DCt &in, DCt *out, cudaStream_t s)
     return COPSE_OK;
 }
 
+// modulus switch of n ciphertexts held contiguously in [n][2][ell][N], into new ciphertexts
+copse_status op_modswitch_many(copse_ctx *c, const u64 *in, int n, int ell, std::vector<DCt> &out, cudaStream_t s) {
+    const int N = c->N;
+    const size_t per = (size_t)2 * ell * N;
+    if (ell < 2) { set_error("modulus switch below one prime"); return COPSE_ELEVEL; }
+    out.assign(n, DCt());
+    for (int a = 0; a < n; a++) STATUS_TRY(ct_alloc(c, &out[a], ell - 1, 2, s));
+    for (int a0 = 0; a0 < n; a0 += MS_POLYS / 2) {
+        const int na = std::min(MS_POLYS / 2, n - a0), np = 2 * na;
+        const u64 *x = in + (size_t)a0 * per;
+        Scratch sc(s);
+        u64 *last = nullptr;
+        STATUS_TRY(sc.get(c, &last, (size_t)np * N));
+        bool done = false;
+        STATUS_TRY(ntt_inverse_copy(c, x + (size_t)(ell - 1) * N, (size_t)ell * N, last, N, np, 1, ell - 1, s, &done));
+        if (!done) {
+            CUDA_TRY(cudaMemcpy2DAsync(last, (size_t)N * sizeof(u64), x + (size_t)(ell - 1) * N,
+                                       (size_t)ell * N * sizeof(u64), (size_t)N * sizeof(u64), np,
+                                       cudaMemcpyDeviceToDevice, s));
+            STATUS_TRY(ntt_inverse(c, batch(last, N, np, 0, 1, ell, ell - 1), s));
+        }
+        MsFuse f{last, x, nullptr, ell};
+        for (int p = 0; p < np; p++) f.outp[p] = out[a0 + p / 2].data + (size_t)(p & 1) * (ell - 1) * N;
+        STATUS_TRY(ntt_forward_modswitch(c, f, np, s, &done));
+        if (!done) {
+            u64 *W = nullptr;
+            STATUS_TRY(sc.get(c, &W, (size_t)np * (ell - 1) * N));
+            TIMED("ms_conv", 8.0 * N * (double)np * ell, s,
+                  k_ms_conv<<<nblk((size_t)np * N), TPB, 0, s>>>(last, W, np, ell, c->L, c->logN, c->d_prime, c->ks));
+            LAUNCH_CHECK();
+            STATUS_TRY(ntt_forward(c, batch(W, (size_t)(ell - 1) * N, np, 0, ell - 1, ell - 1), s));
+            STATUS_TRY(modswitch_finish(c, f, W, np, s));
+        }
+    }
+    return COPSE_OK;
+}
+
 copse_status op_to_level(copse_ctx *c, DCt *ct, int level, cudaStream_t s) {
     while (ct->level > level) {
         DCt nx;
@@ -918,26 +981,30 @@ copse_status op_matmul(copse_ctx *c, const copse_evk *evk, const DCt &v, const s
         STATUS_TRY(moddown_batch(c, acc, nacc, ell, res, s));
     }
     out.assign(raw_out ? 0 : nacc, DCt());
-    for (int a = 0; a < nacc; a++) {
-        u64 *ra = res + (size_t)a * per;
-        for (int r = 0; r < nrot; r++) {
-            if (gal[r] != 1 || !pt[a][r]) continue;
-            TIMED("ident_mac", 8.0 * N * 4.0 * ell, s,
-                  k_ident_mac<<<nblk(per), TPB, 0, s>>>(ra, v.data, pt[a][r], ell, c->logN, c->d_prime));
-            LAUNCH_CHECK();
+    // the zero-rotation terms and the addends of every accumulator in one launch, then the
+    // modulus switch of all of them together
+    int r0 = -1;
+    for (int r = 0; r < nrot; r++)
+        if (gal[r] == 1) r0 = r;
+    for (int a0 = 0; a0 < nacc; a0 += FIN_MAX) {
+        const int na = std::min(FIN_MAX, nacc - a0);
+        FinTable tab;
+        memset(&tab, 0, sizeof(tab));
+        bool any = false;
+        for (int i = 0; i < na; i++) {
+            const int a = a0 + i;
+            tab.res[i] = res + (size_t)a * per;
+            tab.pt_mul[i] = r0 >= 0 ? pt[a][r0] : nullptr;
+            tab.pt_add[i] = (!raw_out && add.size() > (size_t)a) ? add[a] : nullptr;
+            any |= tab.pt_mul[i] || tab.pt_add[i];
         }
-        if (raw_out) continue;
-        if (add.size() > (size_t)a && add[a]) {
-            k_add_plain<<<nblk((size_t)ell * N), TPB, 0, s>>>(ra, add[a], ell, c->logN, c->d_prime);
-            LAUNCH_CHECK();
-        }
-        DCt tmp;
-        tmp.level = ell;
-        tmp.ncomp = 2;
-        tmp.data = ra;
-        STATUS_TRY(op_modswitch(c, tmp, &out[a], s));
+        if (!any) continue;
+        TIMED("ident_mac", 8.0 * N * 5.0 * ell * na, s,
+              k_finish<<<dim3(nblk(per), na), TPB, 0, s>>>(tab, v.data, ell, c->logN, c->d_prime));
+        LAUNCH_CHECK();
     }
-    return COPSE_OK;
+    if (raw_out) return COPSE_OK;
+    return op_modswitch_many(c, res, nacc, ell, out, s);
 }
 
 copse_status giant_phase(copse_ctx *c, const copse_evk *evk, const u64 *inner, int ell, const std::vector<int> &acc_mat,
@@ -999,29 +1066,25 @@ copse_status giant_phase(copse_ctx *c, const copse_evk *evk, const u64 *inner, i
         }
         STATUS_TRY(moddown_batch(c, acc, n_mat, ell, res, s));
     }
-    // + the giant-step-0 sums, + the plaintext or ciphertext addend, then one modulus switch per matrix
-    out.assign(n_mat, DCt());
-    for (int a = 0; a < n_mat; a++) {
-        u64 *ra = res + (size_t)a * per;
-        for (int x = 0; x < nacc; x++)
-            if (acc_mat[x] == a && gal[x] == 1) {
-                k_add<<<nblk(per), TPB, 0, s>>>(ra, inner + (size_t)x * per, ra, 2, ell, c->logN, 0, c->d_prime);
-                LAUNCH_CHECK();
-            }
-        if (add_pt.size() > (size_t)a && add_pt[a]) {
-            k_add_plain<<<nblk((size_t)ell * N), TPB, 0, s>>>(ra, add_pt[a], ell, c->logN, c->d_prime);
-            LAUNCH_CHECK();
+    // + the giant-step-0 sums, + the plaintext or ciphertext addend, in one launch for every
+    // matrix, then the modulus switch of all of them together
+    for (int a0 = 0; a0 < n_mat; a0 += FIN_MAX) {
+        const int na = std::min(FIN_MAX, n_mat - a0);
+        FinTable tab;
+        memset(&tab, 0, sizeof(tab));
+        for (int i = 0; i < na; i++) {
+            const int a = a0 + i;
+            tab.res[i] = res + (size_t)a * per;
+            for (int x = 0; x < nacc; x++)
+                if (acc_mat[x] == a && gal[x] == 1) tab.ct_add[i] = inner + (size_t)x * per;
+            tab.pt_add[i] = add_pt.size() > (size_t)a ? add_pt[a] : nullptr;
+            tab.ct_add2[i] = add_ct.size() > (size_t)a ? add_ct[a] : nullptr;
         }
-        if (add_ct.size() > (size_t)a && add_ct[a]) {
-            k_add<<<nblk(per), TPB, 0, s>>>(ra, add_ct[a], ra, 2, ell, c->logN, 0, c->d_prime);
-            LAUNCH_CHECK();
-        }
-        DCt tmp;
-        tmp.level = ell;
-        tmp.data = ra;
-        STATUS_TRY(op_modswitch(c, tmp, &out[a], s));
+        TIMED("add", 8.0 * N * 5.0 * ell * na, s,
+              k_finish<<<dim3(nblk(per), na), TPB, 0, s>>>(tab, nullptr, ell, c->logN, c->d_prime));
+        LAUNCH_CHECK();
     }
-    return COPSE_OK;
+    return op_modswitch_many(c, res, n_mat, ell, out, s);
 }
 
 copse_status op_matmul_bsgs(copse_ctx *c, const copse_evk *evk, const DCt &v, const std::vector<uint32_t> &baby,
