@@ -50,7 +50,7 @@ def parse():
     ap.add_argument("--no-table6", action="store_true", help="skip the per-stage microbenchmark sweep")
     ap.add_argument("--no-tune", action="store_true", help="fixed schedule (dnum 3, plain products, cluster NTT)")
     ap.add_argument("--schedule", default=None,
-                    help="dnum,g_reshuffle,g_level,ntt_cluster_max for the headline workload instead of tuning "
+                    help="dnum,g_reshuffle,g_level,ntt_cluster_max[,ntt_fused_max] for the headline workload instead of tuning "
                          "(e.g. the values a tuned run printed, to profile that schedule)")
     ap.add_argument("--no-encmodel", action="store_true", help="skip the encrypted-model leg")
     return ap.parse_args()
@@ -202,6 +202,8 @@ def run_cuda(args, ws, rank, local):
     ctx = K.copse_ctx_create(W.log_n, W.bits, W.primes, dnum, device=local)
     if sched:
         K.copse_ctx_set_ntt_cluster_max(ctx, sched[3])
+        if len(sched) > 4:
+            K.copse_ctx_set_ntt_fused_max(ctx, sched[4])
     elif not args.no_tune:
         tuning.update(autotune(K, ctx, [model]))
     info = K.copse_model_info_get(model)
@@ -411,7 +413,10 @@ def autotune(K, ctx, models, g_r=(0, 16, 32, 64), g_l=(0, 4, 8), nq=1):
     for m in models:
         K.copse_tune_bsgs(ctx, m, list(g_r), list(g_l), nq, 3)
         plans.append(list(K.copse_model_get_bsgs(m)))
-    return {"ntt_cluster_max_polys": lim, "bsgs_plans": plans}
+    # the fused transforms' crossover, by whole inferences of the largest model
+    fused, fused_ms = K.copse_tune_fused(ctx, models[-1], n_queries=nq)
+    return {"ntt_cluster_max_polys": lim, "ntt_fused_max_polys": fused, "fused_ms_per_inference": fused_ms,
+            "bsgs_plans": plans}
 
 
 # ---------------------------------------------------------------- serving

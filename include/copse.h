@@ -392,6 +392,20 @@ copse_status copse_tune_ntt(copse_ctx *ctx, const uint32_t *sizes, size_t n, int
 /* Set the crossover copse_tune_ntt would choose (to replay a tuned schedule). */
 copse_status copse_ctx_set_ntt_cluster_max(copse_ctx *ctx, uint32_t max_cluster);
 
+/* The crossover of the forward / inverse transforms fused with the base
+ * conversions around them (modulus switch, ModUp, ModDown): a fused launch
+ * replaces a conversion kernel, a transform and a finishing kernel, so its
+ * best crossover differs from the plain one.  Each cands[i] (residue
+ * polynomials per launch; >= 2^30 = always) is set in turn and one whole
+ * inference of the model's current plan timed (ms[i], median of reps); the
+ * fastest stays set and is returned in *best.  Keys are made internally.
+ * Fused transforms exist for 2^12 <= N <= 2^14; at other degrees nothing is
+ * timed (ms[i] = -1) and *best is the current setting. */
+copse_status copse_tune_fused(copse_ctx *ctx, copse_model *model, const uint32_t *cands, size_t n,
+                              size_t n_queries, int reps, float *ms, uint32_t *best);
+/* Set the fused crossover copse_tune_fused would choose (default: always fused). */
+copse_status copse_ctx_set_ntt_fused_max(copse_ctx *ctx, uint32_t max_fused);
+
 /* Baby-step sizes (copse_model_set_bsgs): the reshuffle candidates g_r[] are
  * timed by the reshuffle stage with the level plan held, then the level
  * candidates g_l[] by the level stage with the chosen reshuffle plan, each

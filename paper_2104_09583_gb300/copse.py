@@ -64,6 +64,9 @@ _SIG = {
     "copse_model_rotations": (C.c_int, [vp, vp, vp]),
     "copse_model_set_bsgs": (C.c_int, [vp, C.c_uint32, C.c_uint32]),
     "copse_ctx_set_ntt_cluster_max": (C.c_int, [vp, C.c_uint32]),
+    "copse_ctx_set_ntt_fused_max": (C.c_int, [vp, C.c_uint32]),
+    "copse_tune_fused": (C.c_int, [vp, vp, u32p, C.c_size_t, C.c_size_t, C.c_int, C.POINTER(C.c_float),
+                                   C.POINTER(C.c_uint32)]),
     "copse_model_set_encrypted": (C.c_int, [vp, C.c_int]),
     "copse_model_set_shuffle": (C.c_int, [vp, vp, C.c_size_t, vp]),
     "copse_model_codebook": (C.c_int, [vp, u32p]),
@@ -245,6 +248,19 @@ def copse_tune_ntt(ctx, sizes=(4, 8, 16, 32, 64, 128, 256), reps=5):
 
 def copse_ctx_set_ntt_cluster_max(ctx, max_cluster):
     _check(_lib.copse_ctx_set_ntt_cluster_max(ctx, max_cluster))
+
+
+def copse_ctx_set_ntt_fused_max(ctx, max_fused):
+    _check(_lib.copse_ctx_set_ntt_fused_max(ctx, max_fused))
+
+
+def copse_tune_fused(ctx, model, cands=(64, 128, 256, 512, 1 << 30), n_queries=1, reps=3):
+    """-> (best, {candidate: ms per inference}); the fused-transform crossover is left set."""
+    c = np.ascontiguousarray(cands, dtype=np.uint32)
+    ms = (C.c_float * len(cands))()
+    best = C.c_uint32()
+    _check(_lib.copse_tune_fused(ctx, model, c, len(cands), n_queries, reps, ms, C.byref(best)))
+    return best.value, {int(x): float(ms[i]) for i, x in enumerate(cands)}
 
 
 def copse_tune_bsgs(ctx, model, g_r, g_l, n_queries=1, reps=3):

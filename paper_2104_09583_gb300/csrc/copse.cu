@@ -514,81 +514,105 @@ static copse_status group_matmul(copse_ctx *c, const copse_evk *evk, const DCt &
     return op_matmul_bsgs(c, evk, v, G.plan.baby, G.pt, G.acc_mat, G.acc_giant, (int)G.plan.n_mat, add, out, s);
 }
 
-// SecComp of one query ciphertext's p feature planes x[0..p) (Section 4.1.2):
-// the decision vector D = [x < thresholds] at level lvl_D.
-static copse_status seccomp_one(copse_ctx *c, const copse_evk *evk, copse_model *m, const DCt *x, DCt *Dc,
-                                cudaStream_t s, int lane) {
+// SecComp (Section 4.1.2) of nct query ciphertexts, p feature planes each (x[q p + i]):
+// the decision vectors Dc[q] = [x < thresholds] at level lvl_D.  The leaves of all
+// query ciphertexts, and then each level of their combine trees, run as one batch.
+static copse_status seccomp(copse_ctx *c, const copse_evk *evk, copse_model *m, const DCt *x, int nct,
+                            std::vector<DCt> &Dc, cudaStream_t s, int lane) {
     const bool enc = m->f.encrypted;
     const DeviceModel *D = m->dev.get();
     const int p = (int)m->f.precision;
     struct Node { DCt lt, eq; };
-    // Independent operations of one step run on forked side streams and are
-    // joined back onto s; every free happens on s after the join.
     // SecComp leaves, most significant plane first: lt = (1 - x) y, eq = [x == y]
-    std::vector<Node> nodes(p);
+    std::vector<std::vector<Node>> nodes(nct, std::vector<Node>(p));
     if (!enc) {
         // plaintext thresholds: both leaves are affine in x
-        STATUS_TRY(fork_begin(c, s, 2 * p, lane));
-        for (int k = 0; k < p; k++) {
-            const int i = p - 1 - k;
-            DPt lm{c->L, (u64 *)D->lt_mul[i]}, la{c->L, (u64 *)D->lt_add[i]};
-            DPt em{c->L, (u64 *)D->eq_mul[i]}, ea{c->L, (u64 *)D->eq_add[i]};
-            STATUS_TRY(op_affine(c, x[i], lm, &la, &nodes[k].lt, fork_stream(c, 2 * k, lane)));
-            STATUS_TRY(op_affine(c, x[i], em, &ea, &nodes[k].eq, fork_stream(c, 2 * k + 1, lane)));
-        }
-        STATUS_TRY(fork_join(c, s, 2 * p, lane));
-    } else {
-        // encrypted thresholds y: xy = x * y, lt = y - xy, eq = 2 xy - (x + y) + 1
-        std::vector<DCt> tmp(4 * (size_t)p);
-        STATUS_TRY(fork_begin(c, s, p, lane));
-        for (int k = 0; k < p; k++) {
-            const int i = p - 1 - k;
-            const cudaStream_t fs = fork_stream(c, k, lane);
-            DCt &Y = tmp[4 * k], &xy = tmp[4 * k + 1], &two = tmp[4 * k + 2], &sum = tmp[4 * k + 3];
-            STATUS_TRY(enc_materialize(c, *m->enc, m->enc->idx_thr(i), &Y, fs));
-            STATUS_TRY(op_mul(c, evk, x[i], Y, &xy, fs));
-            STATUS_TRY(op_add(c, Y, xy, &nodes[k].lt, true, fs));
-            STATUS_TRY(op_add(c, xy, xy, &two, false, fs));
-            STATUS_TRY(op_add(c, x[i], Y, &sum, false, fs));
-            STATUS_TRY(op_add(c, two, sum, &nodes[k].eq, true, fs));
-            STATUS_TRY(op_add_one(c, nodes[k].eq, fs));
-        }
-        STATUS_TRY(fork_join(c, s, p, lane));
-        for (DCt &t : tmp)
-            if (t.data) ct_free(&t, s);
-    }
-    // balanced combine (lt_h + eq_h lt_l, eq_h eq_l); no eq at the root
-    while (nodes.size() > 1) {
-        const bool root = nodes.size() == 2;
-        const int npair = (int)(nodes.size() / 2);
-        std::vector<Node> nx(npair);
-        std::vector<DCt> prod(npair);
-        STATUS_TRY(fork_begin(c, s, 2 * npair, lane));
-        for (int k = 0; k < npair; k++) {
-            Node &hi = nodes[2 * k], &lo = nodes[2 * k + 1];
-            STATUS_TRY(op_mul(c, evk, hi.eq, lo.lt, &prod[k], fork_stream(c, 2 * k, lane)));
-            if (!root) STATUS_TRY(op_mul(c, evk, hi.eq, lo.eq, &nx[k].eq, fork_stream(c, 2 * k + 1, lane)));
-        }
-        STATUS_TRY(fork_join(c, s, 2 * npair, lane));
-        STATUS_TRY(fork_begin(c, s, npair, lane));
-        for (int k = 0; k < npair; k++)
-            STATUS_TRY(op_add(c, nodes[2 * k].lt, prod[k], &nx[k].lt, false, fork_stream(c, k, lane)));
-        STATUS_TRY(fork_join(c, s, npair, lane));
-        for (int k = 0; k < npair; k++) {
-            ct_free(&prod[k], s);
-            for (Node *n : {&nodes[2 * k], &nodes[2 * k + 1]}) {
-                ct_free(&n->lt, s);
-                ct_free(&n->eq, s);
+        std::vector<AffineJob> lj;
+        for (int q = 0; q < nct; q++)
+            for (int k = 0; k < p; k++) {
+                const int i = p - 1 - k;
+                const DCt *xi = &x[(size_t)q * p + i];
+                lj.push_back(AffineJob{xi, D->lt_mul[i], D->lt_add[i], &nodes[q][k].lt});
+                lj.push_back(AffineJob{xi, D->eq_mul[i], D->eq_add[i], &nodes[q][k].eq});
             }
+        STATUS_TRY(op_affine_many(c, lj, s));
+    } else {
+        // encrypted thresholds y: xy = x * y (every plane together), lt = y - xy,
+        // eq = 2 xy - (x + y) + 1; the sums of each plane on a forked side stream,
+        // joined back onto s (every free on s after the join)
+        std::vector<DCt> Y(p), XY((size_t)nct * p), tmp(2 * (size_t)nct * p);
+        std::vector<MulJob> mj;
+        for (int k = 0; k < p; k++) STATUS_TRY(enc_materialize(c, *m->enc, m->enc->idx_thr(p - 1 - k), &Y[k], s));
+        for (int q = 0; q < nct; q++)
+            for (int k = 0; k < p; k++)
+                mj.push_back(MulJob{&x[(size_t)q * p + p - 1 - k], &Y[k], &XY[(size_t)q * p + k]});
+        STATUS_TRY(op_mul_many(c, evk, mj, s));
+        for (int q = 0; q < nct; q++) {
+            STATUS_TRY(fork_begin(c, s, p, lane));
+            for (int k = 0; k < p; k++) {
+                const cudaStream_t fs = fork_stream(c, k, lane);
+                const size_t j = (size_t)q * p + k;
+                DCt &two = tmp[2 * j], &sum = tmp[2 * j + 1];
+                STATUS_TRY(op_add(c, Y[k], XY[j], &nodes[q][k].lt, true, fs));
+                STATUS_TRY(op_add(c, XY[j], XY[j], &two, false, fs));
+                STATUS_TRY(op_add(c, x[(size_t)q * p + p - 1 - k], Y[k], &sum, false, fs));
+                STATUS_TRY(op_add(c, two, sum, &nodes[q][k].eq, true, fs));
+                STATUS_TRY(op_add_one(c, nodes[q][k].eq, fs));
+            }
+            STATUS_TRY(fork_join(c, s, p, lane));
         }
-        if (nodes.size() % 2) nx.push_back(nodes.back());
-        nodes.swap(nx);
+        for (auto *v : {&Y, &XY, &tmp})
+            for (DCt &t : *v)
+                if (t.data) ct_free(&t, s);
     }
-    *Dc = nodes[0].lt;
-    if (nodes[0].eq.data) ct_free(&nodes[0].eq, s);
-    if (Dc->level != (enc ? m->enc->lvl_D : D->lvl_D)) {
-        set_error("internal: unexpected level of the decision vector");
-        return COPSE_EINVAL;
+    // balanced combine (lt_h + eq_h lt_l, eq_h eq_l); no eq at the root.  Each tree
+    // level is one batch: the high nodes' lt switched down to the products' level
+    // together, then every product of the level, the lt sums added in the products'
+    // finishing store.
+    while (nodes[0].size() > 1) {
+        const bool root = nodes[0].size() == 2;
+        const int npair = (int)(nodes[0].size() / 2);
+        std::vector<std::vector<Node>> nx(nct, std::vector<Node>(npair));
+        std::vector<const DCt *> hi_lt;
+        for (int q = 0; q < nct; q++)
+            for (int k = 0; k < npair; k++) {
+                const Node &hi = nodes[q][2 * k], &lo = nodes[q][2 * k + 1];
+                // hi.lt and hi.eq share a level; lo (possibly carried up) is never lower
+                if (hi.lt.level != hi.eq.level || lo.lt.level < hi.eq.level || lo.eq.level < hi.eq.level ||
+                    hi.lt.level != nodes[0][0].lt.level) {
+                    set_error("internal: unexpected levels in the comparison tree");
+                    return COPSE_EINVAL;
+                }
+                hi_lt.push_back(&hi.lt);
+            }
+        std::vector<DCt> hms;
+        STATUS_TRY(op_modswitch_cts(c, hi_lt, hms, s));
+        std::vector<MulJob> mj;
+        for (int q = 0; q < nct; q++)
+            for (int k = 0; k < npair; k++) {
+                Node &hi = nodes[q][2 * k], &lo = nodes[q][2 * k + 1];
+                mj.push_back(MulJob{&hi.eq, &lo.lt, &nx[q][k].lt, &hms[(size_t)q * npair + k]});
+                if (!root) mj.push_back(MulJob{&hi.eq, &lo.eq, &nx[q][k].eq});
+            }
+        STATUS_TRY(op_mul_many(c, evk, mj, s));
+        for (DCt &h : hms) ct_free(&h, s);
+        for (int q = 0; q < nct; q++) {
+            for (int k = 0; k < 2 * npair; k++) {
+                ct_free(&nodes[q][k].lt, s);
+                ct_free(&nodes[q][k].eq, s);
+            }
+            if (nodes[q].size() % 2) nx[q].push_back(nodes[q].back());
+            nodes[q].swap(nx[q]);
+        }
+    }
+    Dc.assign(nct, DCt());
+    for (int q = 0; q < nct; q++) {
+        Dc[q] = nodes[q][0].lt;
+        if (nodes[q][0].eq.data) ct_free(&nodes[q][0].eq, s);
+        if (Dc[q].level != (enc ? m->enc->lvl_D : D->lvl_D)) {
+            set_error("internal: unexpected level of the decision vector");
+            return COPSE_EINVAL;
+        }
     }
     return COPSE_OK;
 }
@@ -626,8 +650,8 @@ static copse_status infer_multi(copse_ctx *c, const copse_evk *evk, copse_model 
         return COPSE_OK;
     };
     STATUS_TRY(mark(0));
-    std::vector<DCt> Dc(nct);
-    for (int q = 0; q < nct; q++) STATUS_TRY(seccomp_one(c, evk, m, &feats->cts[(size_t)q * p], &Dc[q], s, lane));
+    std::vector<DCt> Dc;
+    STATUS_TRY(seccomp(c, evk, m, feats->cts.data(), nct, Dc, s, lane));
     STATUS_TRY(mark(1));
     // reshuffle: Branches = R_ext * Decisions
     std::vector<std::vector<DCt>> br(nct);
@@ -649,23 +673,23 @@ static copse_status infer_multi(copse_ctx *c, const copse_evk *evk, copse_model 
     }
     for (DCt &x : B) ct_free(&x, s);
     STATUS_TRY(mark(3));
-    // product across levels, balanced
-    results.assign(nct, DCt());
-    for (int q = 0; q < nct; q++) {
-        std::vector<DCt> &lv = lvs[q];
-        while (lv.size() > 1) {
-            const int npair = (int)(lv.size() / 2);
-            std::vector<DCt> nx(npair);
-            STATUS_TRY(fork_begin(c, s, npair, lane));
-            for (int k = 0; k < npair; k++)
-                STATUS_TRY(op_mul(c, evk, lv[2 * k], lv[2 * k + 1], &nx[k], fork_stream(c, k, lane)));
-            STATUS_TRY(fork_join(c, s, npair, lane));
-            for (int k = 0; k < 2 * npair; k++) ct_free(&lv[k], s);
-            if (lv.size() % 2) nx.push_back(lv.back());
-            lv.swap(nx);
+    // product across levels, balanced; the products of every query ciphertext at one
+    // tree level run together
+    while (lvs[0].size() > 1) {
+        const int npair = (int)(lvs[0].size() / 2);
+        std::vector<std::vector<DCt>> nx(nct, std::vector<DCt>(npair));
+        std::vector<MulJob> mj;
+        for (int q = 0; q < nct; q++)
+            for (int k = 0; k < npair; k++) mj.push_back(MulJob{&lvs[q][2 * k], &lvs[q][2 * k + 1], &nx[q][k]});
+        STATUS_TRY(op_mul_many(c, evk, mj, s));
+        for (int q = 0; q < nct; q++) {
+            for (int k = 0; k < 2 * npair; k++) ct_free(&lvs[q][k], s);
+            if (lvs[q].size() % 2) nx[q].push_back(lvs[q].back());
+            lvs[q].swap(nx[q]);
         }
-        results[q] = lv[0];
     }
+    results.assign(nct, DCt());
+    for (int q = 0; q < nct; q++) results[q] = lvs[q][0];
     // label shuffle with padding (Section 7.2): one more plaintext matrix product
     if (!m->f.shuffle_src.empty()) {
         STATUS_TRY(upload_shuffle(c, m, s));

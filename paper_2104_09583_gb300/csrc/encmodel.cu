@@ -93,18 +93,6 @@ struct EncMacTable {
 
 // 128-bit accumulator: the products of one launch (each < 4 q^2 < 2^122, at most
 // EM_BABY of them per accumulator, < 2^126) are summed exactly and reduced once.
-struct Acc128 {
-    u64 lo, hi;
-};
-__device__ __forceinline__ void mac128(Acc128 &a, u64 x, u64 y) {
-    const u64 plo = x * y, phi = __umul64hi(x, y);
-    a.lo += plo;
-    a.hi += phi + (a.lo < plo);
-}
-__device__ __forceinline__ u64 reduce128(const Acc128 &a, const PrimeDev &P) {
-    return add_mod(mul_shoup(barrett_wide(0, a.hi, P), P.r64, P.r64_sh, P.q), barrett_wide(0, a.lo, P), P.q);
-}
-
 // R: rotations [query ct][baby][2][ell][N] from the launch's first baby (r_ct words per
 // query ciphertext); acc: [query ct][acc][3][ell][N] from the launch's first accumulator
 // (a_ct words per query ciphertext).  A thread holds a register tile of TA

@@ -104,6 +104,20 @@ __device__ __forceinline__ u64 barrett_wide(u64 hi, u64 lo, const PrimeDev &p) {
 __device__ __forceinline__ u64 mul_mod(u64 a, u64 b, const PrimeDev &p) {
     return barrett_wide(__umul64hi(a, b), a * b, p);
 }
+// Lazy sums of products: x * y < 2^120 for residues of primes below 2^60, so a
+// 128-bit accumulator holds 256 such products (2^18 at 55 bits); one reduction at
+// the end gives the same residue as reducing after every step.
+struct Acc128 {
+    u64 lo, hi;
+};
+__device__ __forceinline__ void mac128(Acc128 &a, u64 x, u64 y) {
+    const u64 plo = x * y, phi = __umul64hi(x, y);
+    a.lo += plo;
+    a.hi += phi + (a.lo < plo);
+}
+__device__ __forceinline__ u64 reduce128(const Acc128 &a, const PrimeDev &P) {
+    return add_mod(mul_shoup(barrett_wide(0, a.hi, P), P.r64, P.r64_sh, P.q), barrett_wide(0, a.lo, P), P.q);
+}
 // a signed small integer (|v| < q) as a residue
 __device__ __forceinline__ u64 from_signed(i64 v, u64 q) { return v < 0 ? q - (u64)(-v) : (u64)v; }
 __device__ __forceinline__ uint32_t bit_reverse(uint32_t x, int logN) { return __brev(x) >> (32 - logN); }
@@ -186,6 +200,7 @@ struct copse_ctx {
     bool ntt_clusters = true;
     // batches of more residue polynomials than this take the two-launch form (autotuned)
     long ntt_cluster_max = 1L << 30;
+    long ntt_fused_max = 1L << 30;    // the same crossover for the transforms fused with base conversions
 
     int ext_prime(int ell, int r) const { return r < ell ? r : L + (r - ell); }
     int t_index() const { return L + alpha; }
@@ -265,6 +280,7 @@ struct MsFuse {
     u64 *out;         // [nc][ell-1][N], or per polynomial:
     int ell;
     u64 *outp[MS_POLYS];  // when outp[0] is set: polynomial p's result [ell-1][N] at outp[p]
+    const u64 *xp[MS_POLYS];  // when xp[0] is set: polynomial p's input [ell][N] at xp[p] (x unused)
 };
 // ModDown finish of key-switching sums (job j = polys 2j, 2j+1): U (stride ustride
 // per poly) holds the extended-basis sum with its alpha special residues in
@@ -287,11 +303,16 @@ struct MdFuse {
 // ell-1 .. ell+alpha-1 are in coefficient form: the transform's input is their centred
 // conversion to q_0..q_{ell-2}, its output goes straight into
 //   out[p][i] = (U[p][i] - t * NTT(conv)) * B^-1   (i < ell - 1).
+// Products batched together (polys 2j, 2j+1 = product j) may write ciphertext j to
+// outp[j] ([2][ell-1][N]) and add the ciphertext addp[j] (same layout) to it.
+#define MDD_CTS 32
 struct MddFuse {
     const u64 *U;
     size_t ustride;
     int ell;
-    u64 *out;         // [npoly][ell-1][N]
+    u64 *out;         // [npoly][ell-1][N], or per product when outp[0] is set:
+    u64 *outp[MDD_CTS];
+    const u64 *addp[MDD_CTS];
 };
 copse_status ntt_forward_moddown_drop(copse_ctx *ctx, const MddFuse &f, int npoly, cudaStream_t s, bool *done);
 copse_status moddown_drop_unfused(copse_ctx *ctx, const MddFuse &f, int npoly, cudaStream_t s);
@@ -303,6 +324,13 @@ copse_status ntt_forward_moddown(copse_ctx *ctx, const MdFuse &f, int njobs, cud
 // polynomials src + p sstride into dst + p dstride
 copse_status ntt_inverse_copy(copse_ctx *ctx, const u64 *src, size_t sstride, u64 *dst, size_t dstride, int npoly,
                               int nr, int fixed, cudaStream_t s, bool *done);
+// the same for one residue (prime `fixed`) of npoly <= MS_POLYS polynomials held at
+// separate addresses src[p] ([N] each) into dst + p N
+struct GatherSrc {
+    const u64 *p[MS_POLYS];
+};
+copse_status ntt_inverse_gather(copse_ctx *ctx, const GatherSrc &src, int npoly, u64 *dst, int fixed, cudaStream_t s,
+                                bool *done);
 // ModUp of n_items inputs: the transform of every digit's conversion (xc: the inputs in
 // coefficient form, [item][ell][N]) into y [item][nd][ell+alpha][N], each digit's own
 // residues copied from x_ntt + item * xs
@@ -348,7 +376,26 @@ copse_status op_modswitch(copse_ctx *c, const DCt &in, DCt *out, cudaStream_t s)
 copse_status op_to_level(copse_ctx *c, DCt *ct, int level, cudaStream_t s);  // in place (replaces)
 copse_status op_add(copse_ctx *c, const DCt &a, const DCt &b, DCt *out, bool negate_b, cudaStream_t s);
 copse_status op_mul(copse_ctx *c, const copse_evk *evk, const DCt &a, const DCt &b, DCt *out, cudaStream_t s);
+// Independent products a * b (+ add) run together: one tensor launch, one ModUp, one
+// inner-product launch and one relinearise-and-drop ModDown per group of products at
+// a common level.  Each result equals op_mul(a, b) (then op_add(add, .) when add is
+// set; add must already be at the product's level).
+struct MulJob {
+    const DCt *a, *b;
+    DCt *out;
+    const DCt *add = nullptr;
+};
+copse_status op_mul_many(copse_ctx *c, const copse_evk *evk, const std::vector<MulJob> &jobs, cudaStream_t s);
+// modulus switch of ciphertexts held at separate addresses, all at one level > 1
+copse_status op_modswitch_cts(copse_ctx *c, const std::vector<const DCt *> &in, std::vector<DCt> &out, cudaStream_t s);
 copse_status op_affine(copse_ctx *c, const DCt &x, const DPt &mul, const DPt *add, DCt *out, cudaStream_t s);
+// x_j * mul_j + add_j (add on component 0, may be null) for independent jobs, one launch
+struct AffineJob {
+    const DCt *x;
+    const u64 *mul, *add;  // plaintexts [>= x.level][N] NTT domain
+    DCt *out;
+};
+copse_status op_affine_many(copse_ctx *c, const std::vector<AffineJob> &jobs, cudaStream_t s);
 copse_status op_rotate(copse_ctx *c, const copse_evk *evk, const DCt &a, uint32_t k, DCt *out, cudaStream_t s);
 // Diagonal products sharing the rotations of v: for each accumulator a,
 //   out[a] = modswitch(ModDown(sum_{k: rots[k] != 0} pt[a][k] * R_k) + pt[a][k0] * v + add[a])

@@ -359,7 +359,7 @@ struct ClusterSmem {
 __device__ __forceinline__ void ms_store(const MsFuse &f, const PrimeDev *pr, const KsTables &T, int L, int logN,
                                          int p, int r, size_t k, u64 v) {
     const PrimeDev P = pr[r];
-    const u64 xv = f.x[(((size_t)p * f.ell + r) << logN) + k];
+    const u64 xv = f.xp[0] ? f.xp[p][((size_t)r << logN) + k] : f.x[(((size_t)p * f.ell + r) << logN) + k];
     const u64 d = mul_shoup(v, P.t_mod, P.t_mod_sh, P.q);
     u64 *o = f.outp[0] ? f.outp[p] + ((size_t)r << logN) + k : f.out + (((size_t)p * (f.ell - 1) + r) << logN) + k;
     *o = mul_shoup(sub_mod(xv, d, P.q), T.ms_qinv[(size_t)f.ell * L + r], P.q);
@@ -400,8 +400,14 @@ __device__ __forceinline__ void mdd_store(const MddFuse &f, const PrimeDev *pr, 
                                           int p, int r, size_t k, u64 v) {
     const PrimeDev P = pr[r];
     const u64 uv = f.U[(size_t)p * f.ustride + ((size_t)r << logN) + k];
-    f.out[(((size_t)p * (f.ell - 1) + r) << logN) + k] =
-        mul_shoup(sub_mod(uv, mul_shoup(v, P.t_mod, P.t_mod_sh, P.q), P.q), T.mdd_Binv[(size_t)f.ell * L + r], P.q);
+    u64 res = mul_shoup(sub_mod(uv, mul_shoup(v, P.t_mod, P.t_mod_sh, P.q), P.q), T.mdd_Binv[(size_t)f.ell * L + r], P.q);
+    if (!f.outp[0]) {
+        f.out[(((size_t)p * (f.ell - 1) + r) << logN) + k] = res;
+        return;
+    }
+    const size_t at = (((size_t)(p & 1) * (f.ell - 1) + r) << logN) + k;
+    if (f.addp[p >> 1]) res = add_mod(res, f.addp[p >> 1][at], P.q);
+    f.outp[p >> 1][at] = res;
 }
 
 // Load / store of the forward cluster transform: coefficient n of residue r (global
@@ -431,6 +437,18 @@ struct CopyIO {
     }
     __device__ __forceinline__ void store(int p, int r, int, size_t k, u64 v) const {
         dst[(size_t)p * dstride + ((size_t)r << logN) + k] = v;
+    }
+    __device__ __forceinline__ void skip(int, int, int, int) const {}
+};
+
+// one residue of polynomials at separate addresses in, contiguous residues out
+struct GatherIO {
+    GatherSrc src;
+    u64 *dst;
+    int logN;
+    __device__ __forceinline__ u64 load(int p, int, int, size_t n) const { return src.p[p][n]; }
+    __device__ __forceinline__ void store(int p, int, int, size_t k, u64 v) const {
+        dst[((size_t)p << logN) + k] = v;
     }
     __device__ __forceinline__ void skip(int, int, int, int) const {}
 };
@@ -703,6 +721,7 @@ copse_status launch(copse_ctx *ctx, const NttBatch &b, cudaStream_t s, bool inve
 // kernel-timer family of each transform variant
 template <class IO> constexpr const char *io_family(bool inv) { return inv ? "ntt_inv" : "ntt_fwd"; }
 template <> constexpr const char *io_family<CopyIO>(bool) { return "ntt_inv_copy"; }
+template <> constexpr const char *io_family<GatherIO>(bool) { return "ntt_inv_copy"; }
 template <> constexpr const char *io_family<MsIO>(bool) { return "ntt_fwd_ms"; }
 template <> constexpr const char *io_family<MdIO>(bool) { return "ntt_fwd_md"; }
 template <> constexpr const char *io_family<MuIO>(bool) { return "ntt_fwd_mu"; }
@@ -737,7 +756,7 @@ template <bool INV = false, class IO>
 copse_status launch_fused(copse_ctx *ctx, const NttBatch &b, const IO &io, cudaStream_t s, bool *done) {
     *done = false;
     if (b.npoly <= 0 || b.nr <= 0) { *done = true; return COPSE_OK; }
-    if (!ctx->ntt_clusters || (long)b.npoly * b.nr > ctx->ntt_cluster_max) return COPSE_OK;
+    if (!ctx->ntt_clusters || (long)b.npoly * b.nr > ctx->ntt_fused_max) return COPSE_OK;
     if (ctx->logN == 12) STATUS_TRY((launch_cluster_io<2, INV, IO>(ctx, b, io, s)));
     else if (ctx->logN == 13) STATUS_TRY((launch_cluster_io<4, INV, IO>(ctx, b, io, s)));
     else if (ctx->logN == 14) STATUS_TRY((launch_cluster_io<8, INV, IO>(ctx, b, io, s)));
@@ -754,6 +773,12 @@ __global__ void k_ms_finish_io(const MsFuse f, const u64 *W, int nc, const Prime
     const int p = (int)(e / per);
     const size_t rem = e - p * per;
     ms_store(f, pr, T, L, logN, p, (int)(rem >> logN), rem & ((1ull << logN) - 1), W[e]);
+}
+
+__global__ void k_gather_res(const GatherSrc src, int npoly, u64 *dst, int logN) {
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= ((size_t)npoly << logN)) return;
+    dst[e] = src.p[e >> logN][e & ((1ull << logN) - 1)];
 }
 
 __global__ void k_mdd_conv(const MddFuse f, u64 *W, int npoly, const PrimeDev *pr, KsTables T, int L, int alpha,
@@ -802,6 +827,21 @@ copse_status ntt_inverse_copy(copse_ctx *ctx, const u64 *src, size_t sstride, u6
                               int nr, int fixed, cudaStream_t s, bool *done) {
     NttBatch b{nullptr, 0, npoly, 0, nr, nr, fixed};
     return launch_fused<true>(ctx, b, CopyIO{src, sstride, dst, dstride, ctx->logN}, s, done);
+}
+
+copse_status ntt_inverse_gather(copse_ctx *ctx, const GatherSrc &src, int npoly, u64 *dst, int fixed, cudaStream_t s,
+                                bool *done) {
+    if (npoly > MS_POLYS) { set_error("internal: too many polynomials in one gathered transform"); return COPSE_EINVAL; }
+    NttBatch b{nullptr, 0, npoly, 0, 1, 1, fixed};
+    STATUS_TRY(launch_fused<true>(ctx, b, GatherIO{src, dst, ctx->logN}, s, done));
+    if (*done) return COPSE_OK;
+    // a gather, then the in-place transform
+    const size_t n = (size_t)npoly * ctx->N;
+    k_gather_res<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(src, npoly, dst, ctx->logN);
+    if (cudaGetLastError() != cudaSuccess) { set_error("gather kernel failed to launch"); return COPSE_ECUDA; }
+    STATUS_TRY(launch(ctx, NttBatch{dst, (size_t)ctx->N, npoly, 0, 1, 1, fixed}, s, true));
+    *done = true;
+    return COPSE_OK;
 }
 
 copse_status ntt_forward_modup(copse_ctx *ctx, const u64 *xc, const u64 *x_ntt, size_t xs, u64 *y, int n_items,

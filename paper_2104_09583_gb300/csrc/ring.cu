@@ -24,6 +24,7 @@ namespace {
 constexpr int TPB = 256;
 constexpr int MAX_ALPHA = 40;
 constexpr int MAX_ACC = 8;
+constexpr int MM_PRECOMPUTE_ACC = 4;  // accumulators from which the rotations are key-switched first
 constexpr int CHUNK_ROT = 64;
 constexpr int MM_PARTS = 8;  // rotation ranges with their own partial sums in k_mm_fused
 constexpr int RS_CHUNK = 32; // giant-step terms per k_rotsum launch
@@ -72,6 +73,40 @@ __global__ void k_affine(const u64 *x, const u64 *m, const u64 *addp, u64 *out, 
     u64 v = mul_mod(x[e], m[k], P);
     if (addp && e < n) v = add_mod(v, addp[k], P.q);
     out[e] = v;
+}
+
+// many products / affine maps in one launch: blockIdx.y picks the job
+struct TensorJobs {
+    const u64 *a[MDD_CTS];
+    const u64 *b[MDD_CTS];
+};
+__global__ void k_tensor_many(const TensorJobs J, u64 *out, int level, int logN, const PrimeDev *pr) {
+    size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    size_t n = (size_t)level << logN;
+    if (e >= n) return;
+    const u64 *a = J.a[blockIdx.y], *b = J.b[blockIdx.y];
+    u64 *o = out + (size_t)blockIdx.y * 3 * n;
+    const PrimeDev P = pr[e >> logN];
+    u64 a0 = a[e], a1 = a[n + e], b0 = b[e], b1 = b[n + e];
+    o[e] = mul_mod(a0, b0, P);
+    o[n + e] = add_mod(mul_mod(a0, b1, P), mul_mod(a1, b0, P), P.q);
+    o[2 * n + e] = mul_mod(a1, b1, P);
+}
+
+#define AFF_JOBS 64
+struct AffineJobsDev {
+    const u64 *x[AFF_JOBS], *m[AFF_JOBS], *add[AFF_JOBS];
+};
+__global__ void k_affine_many(const AffineJobsDev J, u64 *out, int level, int logN, const PrimeDev *pr) {
+    size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    size_t n = (size_t)level << logN;
+    if (e >= 2 * n) return;
+    const int j = blockIdx.y;
+    size_t k = e < n ? e : e - n;
+    const PrimeDev P = pr[k >> logN];
+    u64 v = mul_mod(J.x[j][e], J.m[j][k], P);
+    if (J.add[j] && e < n) v = add_mod(v, J.add[j][k], P.q);
+    out[(size_t)j * 2 * n + e] = v;
 }
 
 __global__ void k_mul_elem(const u64 *a, const u64 *b, u64 *out, int nres, int logN, const PrimeDev *pr) {
@@ -227,8 +262,9 @@ struct MmTable {
 
 // grid.y splits the chunk's rotations into gridDim.y contiguous ranges; range y
 // accumulates into its own partial sums at acc + y * part_stride (summed later).
+template <int NA>
 __global__ void __launch_bounds__(256) k_mm_fused(const u64 *yhat, const u64 *c0, int nrot, const MmTable tab,
-                                                  int nacc, size_t part_stride, int ell, int alpha, int L, int logN,
+                                                  size_t part_stride, int ell, int alpha, int L, int logN,
                                                   const PrimeDev *pr, KsTables T) {
     const int N = 1 << logN;
     const int nx = ell + alpha, nd = (ell + alpha - 1) / alpha, NB = L + alpha;
@@ -244,8 +280,11 @@ __global__ void __launch_bounds__(256) k_mm_fused(const u64 *yhat, const u64 *c0
     const int g = r < ell ? r : L + (r - ell);
     const PrimeDev P = pr[g];
     const u64 Pm = r < ell ? T.md_P[r] : 0;
-    u64 a0[MAX_ACC], a1[MAX_ACC];
-    for (int x = 0; x < nacc; x++) {
+    // the accumulators' diagonal products summed lazily (at most CHUNK_ROT terms per
+    // launch on a residue < q), reduced once at the end
+    u64 a0[NA], a1[NA];
+#pragma unroll
+    for (int x = 0; x < NA; x++) {
         a0[x] = tab.acc[x][poff + e];
         a1[x] = tab.acc[x][poff + n_el + e];
     }
@@ -266,7 +305,8 @@ __global__ void __launch_bounds__(256) k_mm_fused(const u64 *yhat, const u64 *c0
             }
             if (r < ell) u0 = add_mod(u0, mul_mod(Pm, c0[((size_t)r << logN) + src], P), P.q);
         }
-        for (int x = 0; x < nacc; x++) {
+#pragma unroll
+        for (int x = 0; x < NA; x++) {
             const u64 *p = tab.pt[x * nrot + k];
             if (!p) continue;
             const u64 pv = p[e];
@@ -274,7 +314,64 @@ __global__ void __launch_bounds__(256) k_mm_fused(const u64 *yhat, const u64 *c0
             a1[x] = add_mod(a1[x], mul_mod(pv, u1, P), P.q);
         }
     }
-    for (int x = 0; x < nacc; x++) {
+#pragma unroll
+    for (int x = 0; x < NA; x++) {
+        tab.acc[x][poff + e] = a0[x];
+        tab.acc[x][poff + n_el + e] = a1[x];
+    }
+}
+
+// The same accumulation with every R_k precomputed: a streaming multiply-accumulate
+// whose loads for rotation k + 1 are issued before the products of rotation k.
+template <int NA>
+__global__ void __launch_bounds__(256) k_mm_mac(int nrot, const MmTable tab, size_t part_stride, int ell, int alpha,
+                                                int L, int logN, const PrimeDev *pr) {
+    const int nx = ell + alpha;
+    const size_t n_el = (size_t)nx << logN;
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n_el) return;
+    const int per = (nrot + (int)gridDim.y - 1) / (int)gridDim.y;
+    const int k0 = (int)blockIdx.y * per, k1 = min(nrot, k0 + per);
+    if (k0 >= k1) return;
+    const size_t poff = (size_t)blockIdx.y * part_stride;
+    const int r = (int)(e >> logN);
+    const PrimeDev P = pr[r < ell ? r : L + (r - ell)];
+    u64 a0[NA], a1[NA];
+#pragma unroll
+    for (int x = 0; x < NA; x++) {
+        a0[x] = tab.acc[x][poff + e];
+        a1[x] = tab.acc[x][poff + n_el + e];
+    }
+    u64 r0, r1, pv[NA];
+    auto load = [&](int k, u64 &x0, u64 &x1, u64 *v) {
+        const u64 *R = tab.job[k].R;
+        x0 = R[e];
+        x1 = R[n_el + e];
+#pragma unroll
+        for (int x = 0; x < NA; x++) {
+            const u64 *p = tab.pt[x * nrot + k];
+            v[x] = p ? p[e] : 0;
+        }
+    };
+    load(k0, r0, r1, pv);
+    for (int k = k0; k < k1; k++) {
+        u64 n0 = 0, n1 = 0, nv[NA];
+#pragma unroll
+        for (int x = 0; x < NA; x++) nv[x] = 0;
+        if (k + 1 < k1) load(k + 1, n0, n1, nv);
+#pragma unroll
+        for (int x = 0; x < NA; x++) {
+            if (!tab.pt[x * nrot + k]) continue;
+            a0[x] = add_mod(a0[x], mul_mod(pv[x], r0, P), P.q);
+            a1[x] = add_mod(a1[x], mul_mod(pv[x], r1, P), P.q);
+        }
+        r0 = n0;
+        r1 = n1;
+#pragma unroll
+        for (int x = 0; x < NA; x++) pv[x] = nv[x];
+    }
+#pragma unroll
+    for (int x = 0; x < NA; x++) {
         tab.acc[x][poff + e] = a0[x];
         tab.acc[x][poff + n_el + e] = a1[x];
     }
@@ -648,31 +745,6 @@ copse_status ks_apply(copse_ctx *c, const u64 *yhat, int ell, const std::vector<
     return moddown_apply(c, U, ell, nj, f, sc, s);
 }
 
-// Relinearise a 3-component ciphertext d [3][ell][N] and drop one prime in one ModDown:
-// U = KSraw(d2) + P (d0, d1) over the extended basis, then ModDown over q_{ell-1} P.
-copse_status relin_drop(copse_ctx *c, const copse_evk *evk, const u64 *d, int ell, DCt *out, Scratch &sc,
-                        cudaStream_t s) {
-    const int N = c->N, A = c->alpha, nx = ell + A;
-    u64 *yhat = nullptr, *U = nullptr;
-    STATUS_TRY(ks_modup(c, d + (size_t)2 * ell * N, ell, sc, &yhat, s));
-    STATUS_TRY(sc.get(c, &U, (size_t)2 * nx * N));
-    InnerJobs jobs;
-    jobs.j[0] = InnerJob{evk->rlk, U, 1, nullptr, d};
-    TIMED("ks_inner", 8.0 * N * ((double)((ell + A - 1) / A) * nx + 2.0 * ((ell + A - 1) / A) * nx + 2.0 * nx + 2.0 * ell), s,
-          k_ks_inner<<<dim3(nblk((size_t)nx * N), 1), TPB, 0, s>>>(yhat, jobs, ell, A, c->L, c->logN, c->d_prime,
-                                                                    c->ks.md_P));
-    LAUNCH_CHECK();
-    // the dropped prime's and the special residues to coefficients, then the fused
-    // conversion + transform + finish (or conversion, transform, finish)
-    STATUS_TRY(ntt_inverse(c, batch(U, (size_t)nx * N, 2, ell - 1, A + 1, ell), s));
-    STATUS_TRY(ct_alloc(c, out, ell - 1, 2, s));
-    const MddFuse f{U, (size_t)nx * N, ell, out->data};
-    bool done = false;
-    STATUS_TRY(ntt_forward_moddown_drop(c, f, 2, s, &done));
-    if (!done) STATUS_TRY(moddown_drop_unfused(c, f, 2, s));
-    return COPSE_OK;
-}
-
 MdFuse md_fuse() {
     MdFuse f;
     memset(&f, 0, sizeof(f));
@@ -830,20 +902,137 @@ copse_status op_add(copse_ctx *c, const DCt &a, const DCt &b, DCt *out, bool neg
 }
 
 copse_status op_mul(copse_ctx *c, const copse_evk *evk, const DCt &a, const DCt &b, DCt *out, cudaStream_t s) {
-    DCt ta, tb;
-    bool oa, ob;
-    STATUS_TRY(aligned(c, a, b, &ta, &tb, &oa, &ob, s));
-    const int ell = ta.level, N = c->N, A = c->alpha;
-    Scratch sc(s);
-    u64 *d = nullptr;
-    STATUS_TRY(sc.get(c, &d, (size_t)3 * ell * N));
-    TIMED("tensor", 8.0 * N * 7.0 * ell, s, k_tensor<<<nblk((size_t)ell * N), TPB, 0, s>>>(ta.data, tb.data, d, ell, c->logN, c->d_prime));
-    LAUNCH_CHECK();
-    if (oa) ct_free(&ta, s);
-    if (ob) ct_free(&tb, s);
+    return op_mul_many(c, evk, {MulJob{&a, &b, out}}, s);
+}
+
+// Products at one level ell, at most MDD_CTS: tensor, then relinearised with one prime
+// dropped (the canonical policy) in one ModDown over q_{ell-1} P:
+// U = KSraw(d2) + P (d0, d1) over the extended basis.
+static copse_status mul_group(copse_ctx *c, const copse_evk *evk, const std::vector<const DCt *> &a,
+                              const std::vector<const DCt *> &b, const std::vector<MulJob> &jobs,
+                              const std::vector<int> &idx, int ell, cudaStream_t s) {
+    const int N = c->N, A = c->alpha, nx = ell + A, nd = (ell + A - 1) / A, nj = (int)idx.size();
+    const size_t per3 = (size_t)3 * ell * N;
     if (ell < 2) { set_error("multiplication at one prime: no prime left to drop"); return COPSE_ELEVEL; }
-    // relinearised and one prime dropped (the canonical policy), in one ModDown
-    return relin_drop(c, evk, d, ell, out, sc, s);
+    for (int i : idx) {
+        const DCt *ad = jobs[i].add;
+        if (ad && (ad->level != ell - 1 || ad->ncomp != 2)) {
+            set_error("internal: addend of a product not at the product's level");
+            return COPSE_EINVAL;
+        }
+    }
+    Scratch sc(s);
+    u64 *d = nullptr, *yhat = nullptr, *U = nullptr;
+    STATUS_TRY(sc.get(c, &d, (size_t)nj * per3));
+    TensorJobs tj;
+    for (int k = 0; k < nj; k++) {
+        tj.a[k] = a[idx[k]]->data;
+        tj.b[k] = b[idx[k]]->data;
+    }
+    TIMED("tensor", 8.0 * N * 7.0 * ell * nj, s,
+          k_tensor_many<<<dim3(nblk((size_t)ell * N), nj), TPB, 0, s>>>(tj, d, ell, c->logN, c->d_prime));
+    LAUNCH_CHECK();
+    STATUS_TRY(ks_modup_batch(c, d + (size_t)2 * ell * N, per3, nj, ell, sc, &yhat, s));
+    STATUS_TRY(sc.get(c, &U, (size_t)nj * 2 * nx * N));
+    InnerJobs ij;
+    for (int k = 0; k < nj; k++)
+        ij.j[k] = InnerJob{evk->rlk, U + (size_t)k * 2 * nx * N, 1, yhat + (size_t)k * nd * nx * N, d + (size_t)k * per3};
+    TIMED("ks_inner", 8.0 * N * nj * (3.0 * nd * nx + 2.0 * nx + 2.0 * ell), s,
+          k_ks_inner<<<dim3(nblk((size_t)nx * N), nj), TPB, 0, s>>>(yhat, ij, ell, A, c->L, c->logN, c->d_prime,
+                                                                     c->ks.md_P));
+    LAUNCH_CHECK();
+    // the dropped prime's and the special residues to coefficients, then the fused
+    // conversion + transform + finish (or conversion, transform, finish)
+    STATUS_TRY(ntt_inverse(c, batch(U, (size_t)nx * N, 2 * nj, ell - 1, A + 1, ell), s));
+    MddFuse f{U, (size_t)nx * N, ell, nullptr};
+    for (int k = 0; k < nj; k++) {
+        const MulJob &J = jobs[idx[k]];
+        STATUS_TRY(ct_alloc(c, J.out, ell - 1, 2, s));
+        f.outp[k] = J.out->data;
+        f.addp[k] = J.add ? J.add->data : nullptr;
+    }
+    bool done = false;
+    STATUS_TRY(ntt_forward_moddown_drop(c, f, 2 * nj, s, &done));
+    if (!done) STATUS_TRY(moddown_drop_unfused(c, f, 2 * nj, s));
+    return COPSE_OK;
+}
+
+copse_status op_mul_many(copse_ctx *c, const copse_evk *evk, const std::vector<MulJob> &jobs, cudaStream_t s) {
+    const size_t n = jobs.size();
+    std::vector<DCt> ta(n), tb(n);
+    std::vector<char> oa(n, 0), ob(n, 0);
+    std::vector<const DCt *> pa(n), pb(n);
+    copse_status st = COPSE_OK;
+    for (size_t i = 0; i < n && st == COPSE_OK; i++) {
+        bool x = false, y = false;
+        st = aligned(c, *jobs[i].a, *jobs[i].b, &ta[i], &tb[i], &x, &y, s);
+        oa[i] = x;
+        ob[i] = y;
+        pa[i] = &ta[i];
+        pb[i] = &tb[i];
+    }
+    // groups of a common level, in the order of first appearance
+    std::vector<int> levels;
+    for (size_t i = 0; i < n && st == COPSE_OK; i++)
+        if (std::find(levels.begin(), levels.end(), ta[i].level) == levels.end()) levels.push_back(ta[i].level);
+    for (int ell : levels) {
+        std::vector<int> idx;
+        for (size_t i = 0; i < n && st == COPSE_OK; i++) {
+            if (ta[i].level != ell) continue;
+            idx.push_back((int)i);
+            if ((int)idx.size() == MDD_CTS) {
+                st = mul_group(c, evk, pa, pb, jobs, idx, ell, s);
+                idx.clear();
+            }
+        }
+        if (st == COPSE_OK && !idx.empty()) st = mul_group(c, evk, pa, pb, jobs, idx, ell, s);
+    }
+    for (size_t i = 0; i < n; i++) {
+        if (oa[i]) ct_free(&ta[i], s);
+        if (ob[i]) ct_free(&tb[i], s);
+    }
+    return st;
+}
+
+copse_status op_modswitch_cts(copse_ctx *c, const std::vector<const DCt *> &in, std::vector<DCt> &out, cudaStream_t s) {
+    const int N = c->N;
+    out.assign(in.size(), DCt());
+    if (in.empty()) return COPSE_OK;
+    const int ell = in[0]->level;
+    if (ell < 2) { set_error("modulus switch below one prime"); return COPSE_ELEVEL; }
+    std::vector<std::pair<int, int>> polys;  // (ciphertext, component)
+    for (size_t a = 0; a < in.size(); a++) {
+        if (in[a]->level != ell) { set_error("internal: ciphertexts of a batched modulus switch at several levels"); return COPSE_EINVAL; }
+        STATUS_TRY(ct_alloc(c, &out[a], ell - 1, in[a]->ncomp, s));
+        for (int k = 0; k < in[a]->ncomp; k++) polys.emplace_back((int)a, k);
+    }
+    for (size_t p0 = 0; p0 < polys.size(); p0 += MS_POLYS) {
+        const int np = (int)std::min<size_t>(MS_POLYS, polys.size() - p0);
+        Scratch sc(s);
+        u64 *last = nullptr;
+        STATUS_TRY(sc.get(c, &last, (size_t)np * N));
+        GatherSrc g{};
+        MsFuse f{last, nullptr, nullptr, ell};
+        for (int p = 0; p < np; p++) {
+            const auto [a, k] = polys[p0 + p];
+            g.p[p] = in[a]->data + ((size_t)k * ell + ell - 1) * N;
+            f.xp[p] = in[a]->data + (size_t)k * ell * N;
+            f.outp[p] = out[a].data + (size_t)k * (ell - 1) * N;
+        }
+        bool done = false;
+        STATUS_TRY(ntt_inverse_gather(c, g, np, last, ell - 1, s, &done));
+        STATUS_TRY(ntt_forward_modswitch(c, f, np, s, &done));
+        if (!done) {
+            u64 *W = nullptr;
+            STATUS_TRY(sc.get(c, &W, (size_t)np * (ell - 1) * N));
+            TIMED("ms_conv", 8.0 * N * (double)np * ell, s,
+                  k_ms_conv<<<nblk((size_t)np * N), TPB, 0, s>>>(last, W, np, ell, c->L, c->logN, c->d_prime, c->ks));
+            LAUNCH_CHECK();
+            STATUS_TRY(ntt_forward(c, batch(W, (size_t)(ell - 1) * N, np, 0, ell - 1, ell - 1), s));
+            STATUS_TRY(modswitch_finish(c, f, W, np, s));
+        }
+    }
+    return COPSE_OK;
 }
 
 copse_status op_affine(copse_ctx *c, const DCt &x, const DPt &mul, const DPt *add, DCt *out, cudaStream_t s) {
@@ -856,6 +1045,32 @@ copse_status op_affine(copse_ctx *c, const DCt &x, const DPt &mul, const DPt *ad
     copse_status st = op_modswitch(c, r, out, s);
     ct_free(&r, s);
     return st;
+}
+
+copse_status op_affine_many(copse_ctx *c, const std::vector<AffineJob> &jobs, cudaStream_t s) {
+    const int N = c->N;
+    for (size_t j0 = 0; j0 < jobs.size(); j0 += AFF_JOBS) {
+        const int nj = (int)std::min<size_t>(AFF_JOBS, jobs.size() - j0);
+        const int ell = jobs[j0].x->level;
+        AffineJobsDev J;
+        for (int k = 0; k < nj; k++) {
+            const AffineJob &a = jobs[j0 + k];
+            if (a.x->level != ell || a.x->ncomp != 2) { set_error("internal: affine jobs at several levels"); return COPSE_EINVAL; }
+            J.x[k] = a.x->data;
+            J.m[k] = a.mul;
+            J.add[k] = a.add;
+        }
+        Scratch sc(s);
+        u64 *r = nullptr;
+        STATUS_TRY(sc.get(c, &r, (size_t)nj * 2 * ell * N));
+        TIMED("affine", 8.0 * N * 6.0 * ell * nj, s,
+              k_affine_many<<<dim3(nblk((size_t)2 * ell * N), nj), TPB, 0, s>>>(J, r, ell, c->logN, c->d_prime));
+        LAUNCH_CHECK();
+        std::vector<DCt> o;
+        STATUS_TRY(op_modswitch_many(c, r, nj, ell, o, s));
+        for (int k = 0; k < nj; k++) *jobs[j0 + k].out = o[k];
+    }
+    return COPSE_OK;
 }
 
 copse_status op_rotate(copse_ctx *c, const copse_evk *evk, const DCt &a, uint32_t k, DCt *out, cudaStream_t s) {
@@ -929,10 +1144,11 @@ copse_status op_matmul(copse_ctx *c, const copse_evk *evk, const DCt &v, const s
         u64 *yhat = nullptr;
         STATUS_TRY(ks_modup(c, v.data + (size_t)ell * N, ell, sc, &yhat, s));
         const int nd = (ell + A - 1) / A;
-        // more accumulators than one launch holds: compute every rotation's key-switched
-        // R_k = KSraw(tau_k c1) + (P tau_k c0, 0) once, instead of once per accumulator chunk
+        // several accumulators: compute every rotation's key-switched
+        // R_k = KSraw(tau_k c1) + (P tau_k c0, 0) once in one wide launch (instead of once
+        // per accumulator chunk, inside the accumulation loop), then stream the products
         u64 *Rall = nullptr;
-        if (nacc > MAX_ACC) {
+        if (nacc >= MM_PRECOMPUTE_ACC) {
             STATUS_TRY(sc.get(c, &Rall, ks_idx.size() * ext));
             for (size_t k0 = 0; k0 < ks_idx.size(); k0 += CHUNK_ROT) {
                 const int nj = (int)std::min<size_t>(CHUNK_ROT, ks_idx.size() - k0);
@@ -965,11 +1181,26 @@ copse_status op_matmul(copse_ctx *c, const copse_evk *evk, const DCt &v, const s
                 for (int a = 0; a < na; a++) tab.acc[a] = part + (size_t)(a0 + a) * ext;
                 // algorithmic bytes: keys, diagonals, accumulators in and out, the rotated
                 // digits and c0 once
-                const double bytes = 8.0 * N * ((double)nr * 2 * nd * nx + nz_pt * (double)nx +
-                                                4.0 * na * nx * parts + (double)nd * nx + ell);
-                TIMED("mm_fused", bytes, s,
-                      k_mm_fused<<<dim3(nblk((size_t)nx * N), parts), TPB, 0, s>>>(
-                          yhat, v.data, nr, tab, na, part_stride, ell, A, c->L, c->logN, c->d_prime, c->ks));
+                // (with R_k precomputed: R_k in place of the keys, digits and c0)
+                const double bytes = 8.0 * N * (nz_pt * (double)nx + 4.0 * na * nx * parts +
+                                                (Rall ? (double)nr * 2 * nx
+                                                      : (double)nr * 2 * nd * nx + (double)nd * nx + ell));
+                const dim3 grid(nblk((size_t)nx * N), parts);
+#define MM_CASE(K)                                                                                        \
+    case K:                                                                                               \
+        if (Rall)                                                                                         \
+            TIMED("mm_fused", bytes, s,                                                                   \
+                  k_mm_mac<K><<<grid, TPB, 0, s>>>(nr, tab, part_stride, ell, A, c->L, c->logN, c->d_prime)); \
+        else                                                                                              \
+            TIMED("mm_fused", bytes, s,                                                                   \
+                  k_mm_fused<K><<<grid, TPB, 0, s>>>(yhat, v.data, nr, tab, part_stride, ell, A, c->L,      \
+                                                      c->logN, c->d_prime, c->ks));                         \
+        break;
+                switch (na) {
+                    MM_CASE(1) MM_CASE(2) MM_CASE(3) MM_CASE(4) MM_CASE(5) MM_CASE(6) MM_CASE(7) MM_CASE(8)
+                    default: set_error("internal: accumulator count"); return COPSE_EINVAL;
+                }
+#undef MM_CASE
                 LAUNCH_CHECK();
             }
         }

@@ -1,6 +1,7 @@
 // Autotuning of the schedule choices that have no single best value across
 // workloads: the NTT kernel family (one cluster launch per transform or two
-// tiled launches), the baby-step sizes of the matrix products, and the number
+// tiled launches, for plain transforms and for those fused with base
+// conversions), the baby-step sizes of the matrix products, and the number
 // of key-switching digits.  Every candidate is run on the device and timed
 // with CUDA events (median of the timed repetitions after a warm-up); the
 // fastest is kept.  Built on the public entry points.
@@ -220,5 +221,46 @@ extern "C" copse_status copse_tune_dnum(const copse_params *base, int device, co
 extern "C" copse_status copse_ctx_set_ntt_cluster_max(copse_ctx *c, uint32_t max_cluster) {
     if (!c) { set_error("null context"); return COPSE_EINVAL; }
     c->ntt_cluster_max = max_cluster >= (1u << 30) ? (1L << 30) : (long)max_cluster;
+    return COPSE_OK;
+}
+
+extern "C" copse_status copse_ctx_set_ntt_fused_max(copse_ctx *c, uint32_t max_fused) {
+    if (!c) { set_error("null context"); return COPSE_EINVAL; }
+    c->ntt_fused_max = max_fused >= (1u << 30) ? (1L << 30) : (long)max_fused;
+    return COPSE_OK;
+}
+
+extern "C" copse_status copse_tune_fused(copse_ctx *c, copse_model *m, const uint32_t *cands, size_t n,
+                                         size_t n_queries, int reps, float *ms, uint32_t *best) {
+    if (!c || !m || !cands || !ms || !best || n < 1 || reps < 1) {
+        set_error("bad argument");
+        return COPSE_EINVAL;
+    }
+    const long before = c->ntt_fused_max;
+    *best = (uint32_t)std::min<long>(before, 0xffffffffL);
+    if (c->logN < 12 || c->logN > 14) {
+        // no fused transform at this ring degree: nothing to choose
+        for (size_t i = 0; i < n; i++) ms[i] = -1.f;
+        return COPSE_OK;
+    }
+    CUDA_TRY(cudaSetDevice(c->device));
+    float bt = std::numeric_limits<float>::infinity();
+    long pick = before;
+    for (size_t i = 0; i < n; i++) {
+        c->ntt_fused_max = cands[i] >= (1u << 30) ? (1L << 30) : (long)cands[i];
+        float st[4], tot = -1.f;
+        const copse_status s = time_model(c, m, n_queries, reps, st, &tot);
+        if (s != COPSE_OK) {
+            c->ntt_fused_max = before;
+            return s;
+        }
+        ms[i] = tot;
+        if (tot < bt) {
+            bt = tot;
+            pick = c->ntt_fused_max;
+        }
+    }
+    c->ntt_fused_max = pick;
+    *best = (uint32_t)std::min<long>(pick, 0xffffffffL);
     return COPSE_OK;
 }

@@ -92,7 +92,9 @@ def test_tuning_calls_marshal_and_reject_null_handles():
     """The autotuning entry points check their handles before any device work."""
     for call in (lambda: K.copse_tune_ntt(None),
                  lambda: K.copse_tune_bsgs(None, None, [0, 8], [0, 4]),
-                 lambda: K.copse_tune_dnum(10, 50, 4, None, [1, 2])):
+                 lambda: K.copse_tune_dnum(10, 50, 4, None, [1, 2]),
+                 lambda: K.copse_tune_fused(None, None),
+                 lambda: K.copse_ctx_set_ntt_fused_max(None, 64)):
         with pytest.raises(K.CopseError) as e:
             call()
         assert e.value.name == "EINVAL"

@@ -230,17 +230,25 @@ def test_chain_too_short_is_an_error(toy):
 
 def test_inference_full_size_matches_oracle():
     """The N = 2^14, 10-prime workload (4 trees, ~100 branches, 8 features, 8-bit), one query,
-    ciphertext for ciphertext against the oracle."""
+    ciphertext for ciphertext against the oracle, under three transform schedules: the
+    cluster transforms (fused with the base conversions) for every batch, the tiled
+    two-pass transforms with separate conversion kernels for every batch, and a mixed
+    crossover at 64 residue polynomials."""
     W = synth.WORKLOADS["forest100-n16384"]
     s = Setup(W.forest_texts()[0], W.precision(), W.n_features(), W.log_n, W.bits, W.primes, W.dnum)
     try:
         qs = W.query_arrays()[0]
-        got, bits, slots = _run_both(s, qs)
+        got = {}
+        for name, cluster_max, fused_max in (("cluster", 1 << 30, 1 << 30), ("tiled", 0, 0), ("mixed", 64, 64)):
+            K.copse_ctx_set_ntt_cluster_max(s.ctx, cluster_max)
+            K.copse_ctx_set_ntt_fused_max(s.ctx, fused_max)
+            got[name], bits, _ = _run_both(s, qs)
+            _, trees = Cp.parse_forest(s.text)
+            assert bits[0].tolist() == Cp.classify_plain(trees, qs[0]), name
         X = Cp.encrypt_queries(s.bgv, s.okeys, s.om, qs, 99)
         want = Cp.infer(Cp.BgvEngine(s.bgv, s.okeys), s.om, X, s.N)
-        assert_same(got, want, "inference result")
-        _, trees = Cp.parse_forest(s.text)
-        assert bits[0].tolist() == Cp.classify_plain(trees, qs[0])
+        for name, g in got.items():
+            assert_same(g, want, f"inference result ({name} transforms)")
     finally:
         s.close()
 

@@ -29,6 +29,8 @@ def test_tuned_schedule_is_correct():
         assert all(v > 0 for v in list(rs.values()) + list(ls.values()))
         g = K.copse_model_get_bsgs(model)
         assert g[0] in (0, 16, 1 << 20) and g[1] in (0, 8)
+        fb, fm = K.copse_tune_fused(ctx, model, (8, 1 << 30), 1, 2)
+        assert fb in (8, 1 << 30) and all(v > 0 for v in fm.values())
         keys, evk = K.copse_keygen(ctx, 4, [model])
         info = K.copse_model_info_get(model)
         nq = (1 << W.log_n) // info["block"]
