@@ -585,8 +585,11 @@ static copse_status seccomp(copse_ctx *c, const copse_evk *evk, copse_model *m, 
                 }
                 hi_lt.push_back(&hi.lt);
             }
+        // the modulus switch on a forked branch, overlapping the products; joined
+        // before their finishing store (the frees below are ordered after the join)
         std::vector<DCt> hms;
-        STATUS_TRY(op_modswitch_cts(c, hi_lt, hms, s));
+        STATUS_TRY(fork_begin(c, s, 1, lane));
+        STATUS_TRY(op_modswitch_cts(c, hi_lt, hms, fork_stream(c, 0, lane)));
         std::vector<MulJob> mj;
         for (int q = 0; q < nct; q++)
             for (int k = 0; k < npair; k++) {
@@ -594,7 +597,7 @@ static copse_status seccomp(copse_ctx *c, const copse_evk *evk, copse_model *m, 
                 mj.push_back(MulJob{&hi.eq, &lo.lt, &nx[q][k].lt, &hms[(size_t)q * npair + k]});
                 if (!root) mj.push_back(MulJob{&hi.eq, &lo.eq, &nx[q][k].eq});
             }
-        STATUS_TRY(op_mul_many(c, evk, mj, s));
+        STATUS_TRY(op_mul_many(c, evk, mj, s, lane));
         for (DCt &h : hms) ct_free(&h, s);
         for (int q = 0; q < nct; q++) {
             for (int k = 0; k < 2 * npair; k++) {

@@ -385,7 +385,10 @@ struct MulJob {
     DCt *out;
     const DCt *add = nullptr;
 };
-copse_status op_mul_many(copse_ctx *c, const copse_evk *evk, const std::vector<MulJob> &jobs, cudaStream_t s);
+// join_lane >= 0: the addends are still being produced on fork branch 0 of that lane
+// (fork_begin); s joins it (fork_join) only before the first finishing store.
+copse_status op_mul_many(copse_ctx *c, const copse_evk *evk, const std::vector<MulJob> &jobs, cudaStream_t s,
+                         int join_lane = -1);
 // modulus switch of ciphertexts held at separate addresses, all at one level > 1
 copse_status op_modswitch_cts(copse_ctx *c, const std::vector<const DCt *> &in, std::vector<DCt> &out, cudaStream_t s);
 copse_status op_affine(copse_ctx *c, const DCt &x, const DPt &mul, const DPt *add, DCt *out, cudaStream_t s);

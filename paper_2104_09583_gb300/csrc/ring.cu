@@ -24,7 +24,7 @@ namespace {
 constexpr int TPB = 256;
 constexpr int MAX_ALPHA = 40;
 constexpr int MAX_ACC = 8;
-constexpr int MM_PRECOMPUTE_ACC = 4;  // accumulators from which the rotations are key-switched first
+constexpr int MM_PRECOMPUTE_ACC = 2;  // accumulators from which the rotations are key-switched first
 constexpr int CHUNK_ROT = 64;
 constexpr int MM_PARTS = 8;  // rotation ranges with their own partial sums in k_mm_fused
 constexpr int RS_CHUNK = 32; // giant-step terms per k_rotsum launch
@@ -910,7 +910,7 @@ copse_status op_mul(copse_ctx *c, const copse_evk *evk, const DCt &a, const DCt 
 // U = KSraw(d2) + P (d0, d1) over the extended basis.
 static copse_status mul_group(copse_ctx *c, const copse_evk *evk, const std::vector<const DCt *> &a,
                               const std::vector<const DCt *> &b, const std::vector<MulJob> &jobs,
-                              const std::vector<int> &idx, int ell, cudaStream_t s) {
+                              const std::vector<int> &idx, int ell, cudaStream_t s, int &join_lane) {
     const int N = c->N, A = c->alpha, nx = ell + A, nd = (ell + A - 1) / A, nj = (int)idx.size();
     const size_t per3 = (size_t)3 * ell * N;
     if (ell < 2) { set_error("multiplication at one prime: no prime left to drop"); return COPSE_ELEVEL; }
@@ -944,6 +944,10 @@ static copse_status mul_group(copse_ctx *c, const copse_evk *evk, const std::vec
     // the dropped prime's and the special residues to coefficients, then the fused
     // conversion + transform + finish (or conversion, transform, finish)
     STATUS_TRY(ntt_inverse(c, batch(U, (size_t)nx * N, 2 * nj, ell - 1, A + 1, ell), s));
+    if (join_lane >= 0) {
+        STATUS_TRY(fork_join(c, s, 1, join_lane));
+        join_lane = -1;
+    }
     MddFuse f{U, (size_t)nx * N, ell, nullptr};
     for (int k = 0; k < nj; k++) {
         const MulJob &J = jobs[idx[k]];
@@ -957,7 +961,8 @@ static copse_status mul_group(copse_ctx *c, const copse_evk *evk, const std::vec
     return COPSE_OK;
 }
 
-copse_status op_mul_many(copse_ctx *c, const copse_evk *evk, const std::vector<MulJob> &jobs, cudaStream_t s) {
+copse_status op_mul_many(copse_ctx *c, const copse_evk *evk, const std::vector<MulJob> &jobs, cudaStream_t s,
+                         int join_lane) {
     const size_t n = jobs.size();
     std::vector<DCt> ta(n), tb(n);
     std::vector<char> oa(n, 0), ob(n, 0);
@@ -981,12 +986,13 @@ copse_status op_mul_many(copse_ctx *c, const copse_evk *evk, const std::vector<M
             if (ta[i].level != ell) continue;
             idx.push_back((int)i);
             if ((int)idx.size() == MDD_CTS) {
-                st = mul_group(c, evk, pa, pb, jobs, idx, ell, s);
+                st = mul_group(c, evk, pa, pb, jobs, idx, ell, s, join_lane);
                 idx.clear();
             }
         }
-        if (st == COPSE_OK && !idx.empty()) st = mul_group(c, evk, pa, pb, jobs, idx, ell, s);
+        if (st == COPSE_OK && !idx.empty()) st = mul_group(c, evk, pa, pb, jobs, idx, ell, s, join_lane);
     }
+    if (st == COPSE_OK && join_lane >= 0) st = fork_join(c, s, 1, join_lane);
     for (size_t i = 0; i < n; i++) {
         if (oa[i]) ct_free(&ta[i], s);
         if (ob[i]) ct_free(&tb[i], s);
