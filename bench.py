@@ -154,12 +154,12 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def ncu_traffic(family, alg_bytes_per_launch, key="dram_bytes_per_unit"):
+def ncu_traffic(family, workload, alg_bytes_per_launch, key="dram_bytes_per_unit"):
     """Per-launch DRAM bytes (or another per-unit counter, `key`) from the committed ncu summary
-    of this kernel family, scaled from its per-unit figure to a launch of `alg_bytes_per_launch`
-    algorithmic bytes; None when the summary is missing or was taken on a different source file
-    than the one built now."""
-    path = os.path.join(ROOT, "profiles", f"{family}_traffic.md")
+    of this kernel family on this workload, scaled from its per-unit figure to a launch of
+    `alg_bytes_per_launch` algorithmic bytes; None when the summary is missing or was taken on a
+    different source file than the one built now."""
+    path = os.path.join(ROOT, "profiles", f"{family}_{workload}.md")
     try:
         lines = open(path).read().splitlines()
     except OSError:
@@ -354,10 +354,10 @@ def run_cuda(args, ws, rank, local):
         top = max(fam, key=lambda k: fam[k]["ms"])
         v = fam[top]
         achieved = v["bytes"] / (v["ms"] * 1e-3) / 1e9
-        tr = ncu_traffic(top, v["bytes"] / v["launches"])
+        tr = ncu_traffic(top, args.workload, v["bytes"] / v["launches"])
         hbm = {"achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
                "peak_source": f"{how} hbm_gbs (copy)"}
-        wi = ncu_traffic(top, v["bytes"] / v["launches"], key="warp_instructions_per_unit")
+        wi = ncu_traffic(top, args.workload, v["bytes"] / v["launches"], key="warp_instructions_per_unit")
         if wi is not None:
             # integer issue roof: 152 SMs x 4 schedulers x 1 warp instruction per clock at the
             # maximum SM clock; achieved = the ncu instruction count per unit scaled to the
