@@ -338,6 +338,7 @@ extern "C" copse_status copse_ctx_create(const copse_params *pp, int device, cop
         return COPSE_ECUDA;
     }
     copse_status st = build_tables(c);
+    if (st == COPSE_OK) st = ntt_stage_tables(c);
     if (st != COPSE_OK) {
         copse_ctx_destroy(c);
         return st;

@@ -185,6 +185,8 @@ struct copse_ctx {
     u64 *d_psi_sh = nullptr;
     u64 *d_ipsi = nullptr;            // [NP][N] psi^-brev(k)
     u64 *d_ipsi_sh = nullptr;
+    u64 *d_stw_f = nullptr;           // N >= 2^12: each cluster CTA's / row tile's row-stage twiddles,
+    u64 *d_stw_i = nullptr;           //   (w, w') pairs in staging order, [NP][N / 2048][2048][2]
     uint32_t *d_slot_index = nullptr; // [N] NTT(mod t) position of slot s
     KsTables ks{};
     std::vector<void *> owned;        // device allocations freed with the context
@@ -265,6 +267,8 @@ struct NttBatch {
     int skip_alpha = 0;  // > 0: poly p skips residues [j*skip_alpha, min((j+1)*skip_alpha, ell)),
     int skip_period = 0; //      j = p (skip_period = 0) or p mod skip_period (digits of several inputs)
 };
+// the staged row twiddles of the cluster transforms (context creation)
+copse_status ntt_stage_tables(copse_ctx *ctx);
 copse_status ntt_forward(copse_ctx *ctx, const NttBatch &b, cudaStream_t s);
 copse_status ntt_inverse(copse_ctx *ctx, const NttBatch &b, cudaStream_t s);
 

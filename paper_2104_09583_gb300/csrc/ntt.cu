@@ -245,10 +245,12 @@ __global__ void __launch_bounds__(NT2) k_ntt_fwd_cols(NttBatch b, const PrimeDev
     if (!tile_ctx(b, primes, L, (1 << lb) >> lc, t)) return;
     u64 *data = b.data + (size_t)t.p * b.stride + (size_t)t.r * N + (t.tile << lc);
     const u64 *W = tw + (size_t)t.g * N, *Wp = tw_sh + (size_t)t.g * N;
-    for (int e = threadIdx.x; e < TILE; e += NT2) sm[e] = data[((size_t)(e >> lc) << lb) + (e & (C - 1))];
-    for (int k = threadIdx.x; k < (1 << a); k += NT2) {
-        stw[k] = W[k];
-        stwp[k] = Wp[k];
+    for (int e = threadIdx.x; e < TILE; e += NT2) {
+        sm[e] = data[((size_t)(e >> lc) << lb) + (e & (C - 1))];
+        if (e < (1 << a)) {
+            stw[e] = W[e];
+            stwp[e] = Wp[e];
+        }
     }
     __syncthreads();
     tile_fwd<true>(sm, stw, stwp, a, t.q, t.q2, [&](int g, int i) { return (i << lc) + g; },
@@ -259,22 +261,23 @@ __global__ void __launch_bounds__(NT2) k_ntt_fwd_cols(NttBatch b, const PrimeDev
 // Row pass: tile = R consecutive rows of N2 contiguous coefficients; the twiddle
 // of row g, stage u, group il is W[2^(a+u) + ((row0 + g) << u) + il].
 __global__ void __launch_bounds__(NT2) k_ntt_fwd_rows(NttBatch b, const PrimeDev *__restrict__ primes,
-                                                      const u64 *__restrict__ tw, const u64 *__restrict__ tw_sh,
-                                                      int logN, int L, int a) {
+                                                      const ulonglong2 *__restrict__ stg, int logN, int L, int a) {
     __shared__ u64 sm[TILE], stw[TILE], stwp[TILE];
     const int N = 1 << logN, lb = logN - a, lr = 11 - lb;
     TileCtx t;
     if (!tile_ctx(b, primes, L, 1 << (a - lr), t)) return;
     const int row0 = t.tile << lr;
     u64 *data = b.data + (size_t)t.p * b.stride + (size_t)t.r * N + ((size_t)row0 << lb);
-    const u64 *W = tw + (size_t)t.g * N, *Wp = tw_sh + (size_t)t.g * N;
-    for (int e = threadIdx.x; e < TILE; e += NT2) sm[e] = data[e];
-    // stage u needs R << u consecutive twiddles from 2^(a+u) + (row0 << u); stored at R (2^u - 1)
-    for (int u = 0; u < lb; u++) {
-        const int cnt = 1 << (lr + u), off = (1 << lr) * ((1 << u) - 1), src = (1 << (a + u)) + (row0 << u);
-        for (int k = threadIdx.x; k < cnt; k += NT2) {
-            stw[off + k] = W[src + k];
-            stwp[off + k] = Wp[src + k];
+    // stage u needs R << u consecutive twiddles from 2^(a+u) + (row0 << u), stored at R (2^u - 1):
+    // pre-staged per tile, loaded together with the data
+    const ulonglong2 *st = stg + ((size_t)t.g * (N / TILE) + t.tile) * TILE;
+    const int nst = TILE - (1 << lr);
+    for (int e = threadIdx.x; e < TILE; e += NT2) {
+        sm[e] = data[e];
+        if (e < nst) {
+            const ulonglong2 v = st[e];
+            stw[e] = v.x;
+            stwp[e] = v.y;
         }
     }
     __syncthreads();
@@ -291,24 +294,24 @@ __global__ void __launch_bounds__(NT2) k_ntt_fwd_rows(NttBatch b, const PrimeDev
 // Inverse row pass (first): twiddle of row g, stage u, group il is
 // W[2^(logN-1-u) + ((row0 + g) << (lb-1-u)) + il].
 __global__ void __launch_bounds__(NT2) k_ntt_inv_rows(NttBatch b, const PrimeDev *__restrict__ primes,
-                                                      const u64 *__restrict__ tw, const u64 *__restrict__ tw_sh,
-                                                      int logN, int L, int a) {
+                                                      const ulonglong2 *__restrict__ stg, int logN, int L, int a) {
     __shared__ u64 sm[TILE], stw[TILE], stwp[TILE];
     const int N = 1 << logN, lb = logN - a, lr = 11 - lb;
     TileCtx t;
     if (!tile_ctx(b, primes, L, 1 << (a - lr), t)) return;
     const int row0 = t.tile << lr;
     u64 *data = b.data + (size_t)t.p * b.stride + (size_t)t.r * N + ((size_t)row0 << lb);
-    const u64 *W = tw + (size_t)t.g * N, *Wp = tw_sh + (size_t)t.g * N;
-    for (int e = threadIdx.x; e < TILE; e += NT2) sm[e] = data[e];
-    // stage u needs R << (lb-1-u) twiddles; stored after those of the earlier stages
-    for (int u = 0, off = 0; u < lb; u++) {
-        const int su = lb - 1 - u, cnt = 1 << (lr + su), src = (1 << (logN - 1 - u)) + (row0 << su);
-        for (int k = threadIdx.x; k < cnt; k += NT2) {
-            stw[off + k] = W[src + k];
-            stwp[off + k] = Wp[src + k];
+    // stage u needs R << (lb-1-u) twiddles from 2^(logN-1-u) + (row0 << (lb-1-u)), stored after
+    // those of the earlier stages: pre-staged per tile, loaded together with the data
+    const ulonglong2 *st = stg + ((size_t)t.g * (N / TILE) + t.tile) * TILE;
+    const int nst = TILE - (1 << lr);
+    for (int e = threadIdx.x; e < TILE; e += NT2) {
+        sm[e] = data[e];
+        if (e < nst) {
+            const ulonglong2 v = st[e];
+            stw[e] = v.x;
+            stwp[e] = v.y;
         }
-        off += cnt;
     }
     __syncthreads();
     // offset of stage u: sum_{v<u} R 2^(lb-1-v) = R (2^lb - 2^(lb-u))
@@ -330,10 +333,12 @@ __global__ void __launch_bounds__(NT2) k_ntt_inv_cols(NttBatch b, const PrimeDev
     const PrimeDev P = primes[t.g];
     u64 *data = b.data + (size_t)t.p * b.stride + (size_t)t.r * N + (t.tile << lc);
     const u64 *W = tw + (size_t)t.g * N, *Wp = tw_sh + (size_t)t.g * N;
-    for (int e = threadIdx.x; e < TILE; e += NT2) sm[e] = data[((size_t)(e >> lc) << lb) + (e & (C - 1))];
-    for (int k = threadIdx.x; k < (1 << a); k += NT2) {
-        stw[k] = W[k];
-        stwp[k] = Wp[k];
+    for (int e = threadIdx.x; e < TILE; e += NT2) {
+        sm[e] = data[((size_t)(e >> lc) << lb) + (e & (C - 1))];
+        if (e < (1 << a)) {
+            stw[e] = W[e];
+            stwp[e] = Wp[e];
+        }
     }
     __syncthreads();
     tile_inv<true>(sm, stw, stwp, a, t.q, t.q2, [&](int g, int i) { return (i << lc) + g; },
@@ -554,7 +559,8 @@ struct MddIO {
 template <int CL, class IO>
 __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT2)
     k_ntt_fwd_cluster(NttBatch b, const PrimeDev *__restrict__ primes, const u64 *__restrict__ tw,
-                      const u64 *__restrict__ tw_sh, int logN, int L, int a, IO io) {
+                      const u64 *__restrict__ tw_sh, const ulonglong2 *__restrict__ stg, int logN, int L, int a,
+                      IO io) {
     extern __shared__ __align__(16) u64 dyn_smem[];
     ClusterSmem &S = *reinterpret_cast<ClusterSmem *>(dyn_smem);
     cg::cluster_group cl = cg::this_cluster();
@@ -570,20 +576,23 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT2)
     const u64 q = primes[g].q, q2 = 2 * q;
     const size_t N = (size_t)1 << logN;
     const u64 *W = tw + (size_t)g * N, *Wp = tw_sh + (size_t)g * N;
-    for (int e = threadIdx.x; e < TILE; e += NT2)
+    // the tile, this CTA's row-stage twiddles (pre-staged, one 16-byte load each) and the
+    // column-stage twiddles, all loads of a thread in flight together
+    const ulonglong2 *st = stg + ((size_t)g * CL + rank) * TILE;
+    const int nst = TILE - (1 << lr);
+    for (int e = threadIdx.x; e < TILE; e += NT2) {
         S.colt[e] = io.load(p, r, g, (size_t)(rank << lc) + ((size_t)(e >> lc) << lb) + (e & (C - 1)));
-    for (int k = threadIdx.x; k < (1 << a); k += NT2) {
-        S.ctw[k] = W[k];
-        S.ctwp[k] = Wp[k];
-    }
-    const int row0 = rank << lr;
-    for (int u = 0; u < lb; u++) {
-        const int cnt = 1 << (lr + u), off = (1 << lr) * ((1 << u) - 1), src = (1 << (a + u)) + (row0 << u);
-        for (int k = threadIdx.x; k < cnt; k += NT2) {
-            S.stw[off + k] = W[src + k];
-            S.stwp[off + k] = Wp[src + k];
+        if (e < nst) {
+            const ulonglong2 v = st[e];
+            S.stw[e] = v.x;
+            S.stwp[e] = v.y;
+        }
+        if (e < (1 << a)) {
+            S.ctw[e] = W[e];
+            S.ctwp[e] = Wp[e];
         }
     }
+    const int row0 = rank << lr;
     __syncthreads();
     tile_fwd<true>(S.colt, S.ctw, S.ctwp, a, q, q2, [&](int gg, int i) { return (i << lc) + gg; },
                    [&](int u, int, int il) { return (1 << u) + il; });
@@ -607,7 +616,8 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT2)
 template <int CL, class IO>
 __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT2)
     k_ntt_inv_cluster(NttBatch b, const PrimeDev *__restrict__ primes, const u64 *__restrict__ tw,
-                      const u64 *__restrict__ tw_sh, int logN, int L, int a, IO io) {
+                      const u64 *__restrict__ tw_sh, const ulonglong2 *__restrict__ stg, int logN, int L, int a,
+                      IO io) {
     extern __shared__ __align__(16) u64 dyn_smem[];
     ClusterSmem &S = *reinterpret_cast<ClusterSmem *>(dyn_smem);
     cg::cluster_group cl = cg::this_cluster();
@@ -622,18 +632,19 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT2)
     const size_t N = (size_t)1 << logN;
     const u64 *W = tw + (size_t)g * N, *Wp = tw_sh + (size_t)g * N;
     const int row0 = rank << lr;
-    for (int e = threadIdx.x; e < TILE; e += NT2) S.rowt[e] = io.load(p, r, g, ((size_t)row0 << lb) + e);
-    for (int k = threadIdx.x; k < (1 << a); k += NT2) {
-        S.ctw[k] = W[k];
-        S.ctwp[k] = Wp[k];
-    }
-    for (int u = 0, off = 0; u < lb; u++) {
-        const int su = lb - 1 - u, cnt = 1 << (lr + su), src = (1 << (logN - 1 - u)) + (row0 << su);
-        for (int k = threadIdx.x; k < cnt; k += NT2) {
-            S.stw[off + k] = W[src + k];
-            S.stwp[off + k] = Wp[src + k];
+    const ulonglong2 *st = stg + ((size_t)g * CL + rank) * TILE;
+    const int nst = TILE - (1 << lr);
+    for (int e = threadIdx.x; e < TILE; e += NT2) {
+        S.rowt[e] = io.load(p, r, g, ((size_t)row0 << lb) + e);
+        if (e < nst) {
+            const ulonglong2 v = st[e];
+            S.stw[e] = v.x;
+            S.stwp[e] = v.y;
         }
-        off += cnt;
+        if (e < (1 << a)) {
+            S.ctw[e] = W[e];
+            S.ctwp[e] = Wp[e];
+        }
     }
     __syncthreads();
     tile_inv<false>(S.rowt, S.stw, S.stwp, lb, q, q2, [&](int gg, int i) { return (gg << lb) + i; },
@@ -668,12 +679,14 @@ copse_status launch_cluster(copse_ctx *ctx, const NttBatch &b, cudaStream_t s, b
     if (inverse)
         TIMED("ntt_inv", bytes, s,
               k_ntt_inv_cluster<CL, PlainIO><<<grid, NT2, smem, s>>>(b, ctx->d_prime, ctx->d_ipsi, ctx->d_ipsi_sh,
-                                                                     ctx->logN, ctx->L, a,
+                                                                     (const ulonglong2 *)ctx->d_stw_i, ctx->logN,
+                                                                     ctx->L, a,
                                                                      PlainIO{b.data, b.stride, ctx->logN}));
     else
         TIMED("ntt_fwd", bytes, s,
               k_ntt_fwd_cluster<CL, PlainIO><<<grid, NT2, smem, s>>>(b, ctx->d_prime, ctx->d_psi, ctx->d_psi_sh,
-                                                                     ctx->logN, ctx->L, a,
+                                                                     (const ulonglong2 *)ctx->d_stw_f, ctx->logN,
+                                                                     ctx->L, a,
                                                                      PlainIO{b.data, b.stride, ctx->logN}));
     LAUNCH_CHECK();
     return COPSE_OK;
@@ -693,13 +706,13 @@ copse_status launch(copse_ctx *ctx, const NttBatch &b, cudaStream_t s, bool inve
         const unsigned grid = (unsigned)b.npoly * (unsigned)b.nr * (unsigned)(N / TILE);
         if (inverse) {
             TIMED("ntt_inv", bytes, s, {
-                k_ntt_inv_rows<<<grid, NT2, 0, s>>>(b, ctx->d_prime, ctx->d_ipsi, ctx->d_ipsi_sh, logN, ctx->L, a);
+                k_ntt_inv_rows<<<grid, NT2, 0, s>>>(b, ctx->d_prime, (const ulonglong2 *)ctx->d_stw_i, logN, ctx->L, a);
                 k_ntt_inv_cols<<<grid, NT2, 0, s>>>(b, ctx->d_prime, ctx->d_ipsi, ctx->d_ipsi_sh, logN, ctx->L, a);
             });
         } else {
             TIMED("ntt_fwd", bytes, s, {
                 k_ntt_fwd_cols<<<grid, NT2, 0, s>>>(b, ctx->d_prime, ctx->d_psi, ctx->d_psi_sh, logN, ctx->L, a);
-                k_ntt_fwd_rows<<<grid, NT2, 0, s>>>(b, ctx->d_prime, ctx->d_psi, ctx->d_psi_sh, logN, ctx->L, a);
+                k_ntt_fwd_rows<<<grid, NT2, 0, s>>>(b, ctx->d_prime, (const ulonglong2 *)ctx->d_stw_f, logN, ctx->L, a);
             });
         }
         LAUNCH_CHECK();
@@ -743,11 +756,13 @@ copse_status launch_cluster_io(copse_ctx *ctx, const NttBatch &b, const IO &io, 
     if (INV)
         TIMED(io_family<IO>(true), bytes, s,
               k_ntt_inv_cluster<CL, IO><<<grid, NT2, smem, s>>>(b, ctx->d_prime, ctx->d_ipsi, ctx->d_ipsi_sh,
-                                                                ctx->logN, ctx->L, ctx->logN / 2, io));
+                                                                (const ulonglong2 *)ctx->d_stw_i, ctx->logN, ctx->L,
+                                                                ctx->logN / 2, io));
     else
         TIMED(io_family<IO>(false), bytes, s,
-              k_ntt_fwd_cluster<CL, IO><<<grid, NT2, smem, s>>>(b, ctx->d_prime, ctx->d_psi, ctx->d_psi_sh, ctx->logN,
-                                                                ctx->L, ctx->logN / 2, io));
+              k_ntt_fwd_cluster<CL, IO><<<grid, NT2, smem, s>>>(b, ctx->d_prime, ctx->d_psi, ctx->d_psi_sh,
+                                                                (const ulonglong2 *)ctx->d_stw_f, ctx->logN, ctx->L,
+                                                                ctx->logN / 2, io));
     LAUNCH_CHECK();
     return COPSE_OK;
 }
@@ -811,6 +826,51 @@ __global__ void k_md_finish_io(const MdFuse f, const u64 *W, int njobs, const Pr
 }
 
 }  // namespace
+
+namespace {
+// Row-stage twiddles of cluster CTA (or row tile) `rank` in the order the cluster and
+// tiled row kernels use them:
+// forward stage u of the row pass takes 2^(lr+u) consecutive entries from
+// W[2^(a+u) + (row0 << u)], the inverse stage u takes 2^(lr+su) (su = lb-1-u) from
+// W[2^(logN-1-u) + (row0 << su)], stages back to back.
+__global__ void k_stage_tw(const u64 *W, const u64 *Wp, u64 *out, int np, int logN, int inverse) {
+    const int CL = 1 << (logN - 11), a = logN / 2, lb = logN - a, lr = 11 - lb;
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (size_t)np * CL * TILE) return;
+    const int j = (int)(e % TILE), rank = (int)((e / TILE) % CL);
+    const size_t g = e / ((size_t)TILE * CL);
+    const int row0 = rank << lr;
+    u64 w = 0, wp = 0;
+    for (int u = 0, off = 0; u < lb; u++) {
+        const int su = inverse ? lb - 1 - u : u, cnt = 1 << (lr + su);
+        if (j < off + cnt) {
+            const int src = (inverse ? (1 << (logN - 1 - u)) : (1 << (a + u))) + (row0 << su) + (j - off);
+            w = W[(g << logN) + src];
+            wp = Wp[(g << logN) + src];
+            break;
+        }
+        off += cnt;
+    }
+    out[2 * e] = w;
+    out[2 * e + 1] = wp;
+}
+}  // namespace
+
+copse_status ntt_stage_tables(copse_ctx *ctx) {
+    if (ctx->logN < 12) return COPSE_OK;   // one CTA per transform below 2^12: nothing staged
+    const size_t n = (size_t)ctx->NP * ctx->N;  // NP x (N / TILE) x TILE entries
+    for (int inv = 0; inv < 2; inv++) {
+        void *p = nullptr;
+        CUDA_TRY(cudaMalloc(&p, n * 2 * sizeof(u64)));
+        ctx->owned.push_back(p);
+        k_stage_tw<<<(unsigned)((n + 255) / 256), 256>>>(inv ? ctx->d_ipsi : ctx->d_psi, inv ? ctx->d_ipsi_sh : ctx->d_psi_sh,
+                                                         (u64 *)p, ctx->NP, ctx->logN, inv);
+        CUDA_TRY(cudaGetLastError());
+        (inv ? ctx->d_stw_i : ctx->d_stw_f) = (u64 *)p;
+    }
+    CUDA_TRY(cudaDeviceSynchronize());
+    return COPSE_OK;
+}
 
 copse_status ntt_forward_modswitch(copse_ctx *ctx, const MsFuse &f, int nc, cudaStream_t s, bool *done) {
     NttBatch b{nullptr, 0, nc, 0, f.ell - 1, f.ell - 1, -1};
