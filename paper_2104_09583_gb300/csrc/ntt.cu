@@ -144,6 +144,7 @@ template <bool SEQ_FAST, class IX, class TWI>
 __device__ __forceinline__ void tile_fwd(u64 *sm, const u64 *tw, const u64 *twp, int ls, u64 q, u64 q2, IX ix,
                                          TWI twi) {
     int u = 0;
+#pragma unroll
     for (; u + 1 < ls; u += 2) {
         const int lt = ls - 1 - u, tt = 1 << lt, h2 = tt >> 1;
         for (int x = threadIdx.x; x < TILE / 4; x += NT2) {
@@ -183,6 +184,7 @@ template <bool SEQ_FAST, class IX, class TWI>
 __device__ __forceinline__ void tile_inv(u64 *sm, const u64 *tw, const u64 *twp, int ls, u64 q, u64 q2, IX ix,
                                          TWI twi) {
     int u = 0;
+#pragma unroll
     for (; u + 1 < ls; u += 2) {
         const int tt = 1 << u;
         for (int x = threadIdx.x; x < TILE / 4; x += NT2) {
@@ -559,13 +561,15 @@ struct MddIO {
 template <int CL, class IO>
 __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT2)
     k_ntt_fwd_cluster(NttBatch b, const PrimeDev *__restrict__ primes, const u64 *__restrict__ tw,
-                      const u64 *__restrict__ tw_sh, const ulonglong2 *__restrict__ stg, int logN, int L, int a,
-                      IO io) {
+                      const u64 *__restrict__ tw_sh, const ulonglong2 *__restrict__ stg, int, int L, int, IO io) {
     extern __shared__ __align__(16) u64 dyn_smem[];
     ClusterSmem &S = *reinterpret_cast<ClusterSmem *>(dyn_smem);
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
-    const int lb = logN - a, N2 = 1 << lb, lc = 11 - a, C = 1 << lc, lr = 11 - lb;
+    // the cluster size fixes the ring degree (CL x 2048 coefficients): every tile shape is a
+    // compile-time constant, so the radix-4 passes and their index arithmetic unroll
+    constexpr int logN = CL == 2 ? 12 : (CL == 4 ? 13 : 14), a = logN / 2;
+    constexpr int lb = logN - a, N2 = 1 << lb, lc = 11 - a, C = 1 << lc, lr = 11 - lb;
     const int pr = blockIdx.x / CL;
     const int p = pr / b.nr, r = b.r0 + pr % b.nr;
     if (ntt_skipped(b, p, r)) {  // the same for every CTA of the cluster
@@ -616,13 +620,13 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT2)
 template <int CL, class IO>
 __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT2)
     k_ntt_inv_cluster(NttBatch b, const PrimeDev *__restrict__ primes, const u64 *__restrict__ tw,
-                      const u64 *__restrict__ tw_sh, const ulonglong2 *__restrict__ stg, int logN, int L, int a,
-                      IO io) {
+                      const u64 *__restrict__ tw_sh, const ulonglong2 *__restrict__ stg, int, int L, int, IO io) {
     extern __shared__ __align__(16) u64 dyn_smem[];
     ClusterSmem &S = *reinterpret_cast<ClusterSmem *>(dyn_smem);
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
-    const int lb = logN - a, lc = 11 - a, C = 1 << lc, lr = 11 - lb, R = 1 << lr;
+    constexpr int logN = CL == 2 ? 12 : (CL == 4 ? 13 : 14), a = logN / 2;
+    constexpr int lb = logN - a, lc = 11 - a, C = 1 << lc, lr = 11 - lb, R = 1 << lr;
     const int pr = blockIdx.x / CL;
     const int p = pr / b.nr, r = b.r0 + pr % b.nr;
     if (ntt_skipped(b, p, r)) return;

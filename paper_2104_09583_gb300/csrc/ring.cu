@@ -181,7 +181,7 @@ struct InnerJobs {
 
 // (u0, u1)[r][n] = sum_j yhat[j][r][tau_g n] * ksk[j][c][ext_prime(r)][n]
 __global__ void k_ks_inner(const u64 *yhat, const InnerJobs jobs, int ell, int alpha, int L, int logN,
-                           const PrimeDev *pr, const u64 *mdP) {
+                           const PrimeDev *pr, const u64 *mdP, size_t kw) {
     const int N = 1 << logN;
     const int nx = ell + alpha, nd = (ell + alpha - 1) / alpha;
     const int NB = L + alpha;
@@ -199,8 +199,8 @@ __global__ void k_ks_inner(const u64 *yhat, const InnerJobs jobs, int ell, int a
         const u64 y = yh[(((size_t)j * nx + r) << logN) + src];
         const u64 *k0 = J.ksk + (((size_t)(2 * j) * NB + g) << logN);
         const u64 *k1 = J.ksk + (((size_t)(2 * j + 1) * NB + g) << logN);
-        acc0 = add_mod(acc0, mul_mod(y, k0[n], P), P.q);
-        acc1 = add_mod(acc1, mul_mod(y, k1[n], P), P.q);
+        acc0 = add_mod(acc0, mul_shoup(y, k0[n], k0[kw + n], P.q), P.q);
+        acc1 = add_mod(acc1, mul_shoup(y, k1[n], k1[kw + n], P.q), P.q);
     }
     if (J.pd && r < ell) {
         const u64 Pm = mdP[r];
@@ -265,7 +265,7 @@ struct MmTable {
 template <int NA>
 __global__ void __launch_bounds__(256) k_mm_fused(const u64 *yhat, const u64 *c0, int nrot, const MmTable tab,
                                                   size_t part_stride, int ell, int alpha, int L, int logN,
-                                                  const PrimeDev *pr, KsTables T) {
+                                                  const PrimeDev *pr, KsTables T, size_t kw) {
     const int N = 1 << logN;
     const int nx = ell + alpha, nd = (ell + alpha - 1) / alpha, NB = L + alpha;
     const size_t n_el = (size_t)nx << logN;
@@ -300,8 +300,8 @@ __global__ void __launch_bounds__(256) k_mm_fused(const u64 *yhat, const u64 *c0
                 const u64 y = yhat[(((size_t)j * nx + r) << logN) + src];
                 const u64 *k0 = J.ksk + (((size_t)(2 * j) * NB + g) << logN);
                 const u64 *k1 = J.ksk + (((size_t)(2 * j + 1) * NB + g) << logN);
-                u0 = add_mod(u0, mul_mod(y, k0[n], P), P.q);
-                u1 = add_mod(u1, mul_mod(y, k1[n], P), P.q);
+                u0 = add_mod(u0, mul_shoup(y, k0[n], k0[kw + n], P.q), P.q);
+                u1 = add_mod(u1, mul_shoup(y, k1[n], k1[kw + n], P.q), P.q);
             }
             if (r < ell) u0 = add_mod(u0, mul_mod(Pm, c0[((size_t)r << logN) + src], P), P.q);
         }
@@ -392,7 +392,7 @@ struct RsTable {
 };
 
 __global__ void __launch_bounds__(256) k_rotsum(const RsTable tab, int nterm, u64 *acc, int ell, int alpha, int L,
-                                                int logN, const PrimeDev *pr, KsTables T) {
+                                                int logN, const PrimeDev *pr, KsTables T, size_t kw) {
     const int N = 1 << logN;
     const int nx = ell + alpha, nd = (ell + alpha - 1) / alpha, NB = L + alpha;
     const size_t n_el = (size_t)nx << logN;
@@ -411,8 +411,8 @@ __global__ void __launch_bounds__(256) k_rotsum(const RsTable tab, int nterm, u6
             const u64 y = J.yhat[(((size_t)j * nx + r) << logN) + src];
             const u64 *k0 = J.ksk + (((size_t)(2 * j) * NB + g) << logN);
             const u64 *k1 = J.ksk + (((size_t)(2 * j + 1) * NB + g) << logN);
-            a0 = add_mod(a0, mul_mod(y, k0[n], P), P.q);
-            a1 = add_mod(a1, mul_mod(y, k1[n], P), P.q);
+            a0 = add_mod(a0, mul_shoup(y, k0[n], k0[kw + n], P.q), P.q);
+            a1 = add_mod(a1, mul_shoup(y, k1[n], k1[kw + n], P.q), P.q);
         }
         if (r < ell) a0 = add_mod(a0, mul_mod(Pm, J.c0[((size_t)r << logN) + src], P), P.q);
     }
@@ -740,7 +740,7 @@ copse_status ks_apply(copse_ctx *c, const u64 *yhat, int ell, const std::vector<
     InnerJobs jobs;
     for (int i = 0; i < nj; i++) jobs.j[i] = jobs_h[i];
     dim3 grid(nblk((size_t)nx * N), nj);
-    TIMED("ks_inner", 8.0 * N * ((double)((ell + A - 1) / A) * nx + (double)nj * (2.0 * ((ell + A - 1) / A) * nx + 2.0 * nx)), s, k_ks_inner<<<grid, TPB, 0, s>>>(yhat, jobs, ell, A, c->L, c->logN, c->d_prime, c->ks.md_P));
+    TIMED("ks_inner", 8.0 * N * ((double)((ell + A - 1) / A) * nx + (double)nj * (2.0 * ((ell + A - 1) / A) * nx + 2.0 * nx)), s, k_ks_inner<<<grid, TPB, 0, s>>>(yhat, jobs, ell, A, c->L, c->logN, c->d_prime, c->ks.md_P, ksk_words(c)));
     LAUNCH_CHECK();
     return moddown_apply(c, U, ell, nj, f, sc, s);
 }
@@ -939,7 +939,7 @@ static copse_status mul_group(copse_ctx *c, const copse_evk *evk, const std::vec
         ij.j[k] = InnerJob{evk->rlk, U + (size_t)k * 2 * nx * N, 1, yhat + (size_t)k * nd * nx * N, d + (size_t)k * per3};
     TIMED("ks_inner", 8.0 * N * nj * (3.0 * nd * nx + 2.0 * nx + 2.0 * ell), s,
           k_ks_inner<<<dim3(nblk((size_t)nx * N), nj), TPB, 0, s>>>(yhat, ij, ell, A, c->L, c->logN, c->d_prime,
-                                                                     c->ks.md_P));
+                                                                     c->ks.md_P, ksk_words(c)));
     LAUNCH_CHECK();
     // the dropped prime's and the special residues to coefficients, then the fused
     // conversion + transform + finish (or conversion, transform, finish)
@@ -1165,7 +1165,7 @@ copse_status op_matmul(copse_ctx *c, const copse_evk *evk, const DCt &v, const s
                 }
                 TIMED("ks_inner", 8.0 * N * nj * (2.0 * nd * nx + 2.0 * nx + ell), s,
                       k_ks_inner<<<dim3(nblk((size_t)nx * N), nj), TPB, 0, s>>>(yhat, jobs, ell, A, c->L, c->logN,
-                                                                                 c->d_prime, c->ks.md_P));
+                                                                                 c->d_prime, c->ks.md_P, ksk_words(c)));
                 LAUNCH_CHECK();
             }
         }
@@ -1200,7 +1200,7 @@ copse_status op_matmul(copse_ctx *c, const copse_evk *evk, const DCt &v, const s
         else                                                                                              \
             TIMED("mm_fused", bytes, s,                                                                   \
                   k_mm_fused<K><<<grid, TPB, 0, s>>>(yhat, v.data, nr, tab, part_stride, ell, A, c->L,      \
-                                                      c->logN, c->d_prime, c->ks));                         \
+                                                      c->logN, c->d_prime, c->ks, ksk_words(c)));           \
         break;
                 switch (na) {
                     MM_CASE(1) MM_CASE(2) MM_CASE(3) MM_CASE(4) MM_CASE(5) MM_CASE(6) MM_CASE(7) MM_CASE(8)
@@ -1297,7 +1297,7 @@ copse_status giant_phase(copse_ctx *c, const copse_evk *evk, const u64 *inner, i
                 const double bytes = 8.0 * N * ((double)nt * (2.0 * nd * nx + (double)nd * nx + ell) + 4.0 * nx);
                 TIMED("rotsum", bytes, s,
                       k_rotsum<<<nblk((size_t)nx * N), TPB, 0, s>>>(tab, nt, acc + (size_t)a * ext, ell, A, c->L,
-                                                                    c->logN, c->d_prime, c->ks));
+                                                                    c->logN, c->d_prime, c->ks, ksk_words(c)));
                 LAUNCH_CHECK();
             }
         }
@@ -1429,6 +1429,24 @@ copse_status encode_patterns(copse_ctx *c, const std::vector<uint32_t> &patterns
     return COPSE_OK;
 }
 
+// Shoup companion floor(k 2^64 / q) of every key word (prime = the word's residue index
+// mod L + alpha), by restoring long division (k < q < 2^61: the remainder never overflows)
+__global__ void k_shoup_companions(const u64 *key, u64 *comp, size_t words, int NB, int logN, const PrimeDev *pr) {
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= words) return;
+    const u64 q = pr[(e >> logN) % NB].q;
+    u64 r = key[e], quo = 0;
+    for (int i = 0; i < 64; i++) {
+        r <<= 1;
+        quo <<= 1;
+        if (r >= q) {
+            r -= q;
+            quo |= 1;
+        }
+    }
+    comp[e] = quo;
+}
+
 static copse_status make_switch_key(copse_ctx *c, u64 seed, u64 sb, const u64 *s_hat, const u64 *sfrom, u64 *ksk,
                                     Scratch &sc, cudaStream_t s) {
     const int N = c->N, NB = c->L + c->alpha;
@@ -1485,18 +1503,26 @@ copse_status keygen_dev(copse_ctx *c, u64 seed, const std::vector<u64> &galois, 
     if ((st = ntt_forward(c, batch(te, (size_t)L * N, 1, 0, L, L), s))) return fail(st);
     k_pk<<<nblk((size_t)L * N), TPB, 0, s>>>(a, K->s_hat, te, K->pk, L, c->logN, c->d_prime);
     // relinearisation key: s' = s^2, streams 16 + 2j, 17 + 2j
-    if ((st = dev_alloc(c, (void **)&E->rlk, ksk_words(c) * 8, s))) return fail(st);
+    // every key is followed by its Shoup companions (ksk_words words later): the key-switch
+    // inner products multiply by the fixed key words with Shoup products
+    const size_t kw = ksk_words(c);
+    auto companions = [&](u64 *k) {
+        k_shoup_companions<<<nblk(kw), TPB, 0, s>>>(k, k + kw, kw, NB, c->logN, c->d_prime);
+    };
+    if ((st = dev_alloc(c, (void **)&E->rlk, kw * 2 * 8, s))) return fail(st);
     k_mul_elem<<<nblk((size_t)NB * N), TPB, 0, s>>>(K->s_hat, K->s_hat, sf, NB, c->logN, c->d_prime);
     if ((st = make_switch_key(c, seed, 16, K->s_hat, sf, E->rlk, sc, s))) return fail(st);
+    companions(E->rlk);
     // rotation keys: s' = tau_g(s), streams 0x10000 + 64 g + (2j, 2j + 1)
     for (u64 g : galois) {
         if (g == 1 || E->find(g)) continue;
         u64 *k = nullptr;
-        if ((st = dev_alloc(c, (void **)&k, ksk_words(c) * 8, s))) return fail(st);
+        if ((st = dev_alloc(c, (void **)&k, kw * 2 * 8, s))) return fail(st);
         E->galois.push_back(g);
         E->gk.push_back(k);
         k_permute<<<nblk((size_t)NB * N), TPB, 0, s>>>(K->s_hat, sf, NB, g, c->logN);
         if ((st = make_switch_key(c, seed, 0x10000ull + 64ull * g, K->s_hat, sf, k, sc, s))) return fail(st);
+        companions(k);
     }
     if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) {
         set_error("key generation kernels failed");
