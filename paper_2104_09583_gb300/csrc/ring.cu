@@ -740,7 +740,7 @@ copse_status ks_apply(copse_ctx *c, const u64 *yhat, int ell, const std::vector<
     InnerJobs jobs;
     for (int i = 0; i < nj; i++) jobs.j[i] = jobs_h[i];
     dim3 grid(nblk((size_t)nx * N), nj);
-    TIMED("ks_inner", 8.0 * N * ((double)((ell + A - 1) / A) * nx + (double)nj * (2.0 * ((ell + A - 1) / A) * nx + 2.0 * nx)), s, k_ks_inner<<<grid, TPB, 0, s>>>(yhat, jobs, ell, A, c->L, c->logN, c->d_prime, c->ks.md_P, ksk_words(c)));
+    TIMED("ks_inner", 8.0 * N * ((double)((ell + A - 1) / A) * nx + (double)nj * (4.0 * ((ell + A - 1) / A) * nx + 2.0 * nx)), s, k_ks_inner<<<grid, TPB, 0, s>>>(yhat, jobs, ell, A, c->L, c->logN, c->d_prime, c->ks.md_P, ksk_words(c)));
     LAUNCH_CHECK();
     return moddown_apply(c, U, ell, nj, f, sc, s);
 }
@@ -937,7 +937,7 @@ static copse_status mul_group(copse_ctx *c, const copse_evk *evk, const std::vec
     InnerJobs ij;
     for (int k = 0; k < nj; k++)
         ij.j[k] = InnerJob{evk->rlk, U + (size_t)k * 2 * nx * N, 1, yhat + (size_t)k * nd * nx * N, d + (size_t)k * per3};
-    TIMED("ks_inner", 8.0 * N * nj * (3.0 * nd * nx + 2.0 * nx + 2.0 * ell), s,
+    TIMED("ks_inner", 8.0 * N * nj * (5.0 * nd * nx + 2.0 * nx + 2.0 * ell), s,
           k_ks_inner<<<dim3(nblk((size_t)nx * N), nj), TPB, 0, s>>>(yhat, ij, ell, A, c->L, c->logN, c->d_prime,
                                                                      c->ks.md_P, ksk_words(c)));
     LAUNCH_CHECK();
@@ -1163,7 +1163,7 @@ copse_status op_matmul(copse_ctx *c, const copse_evk *evk, const DCt &v, const s
                     const int r = ks_idx[k0 + i];
                     jobs.j[i] = InnerJob{evk->find(gal[r]), Rall + (k0 + i) * ext, gal[r], nullptr, nullptr, v.data};
                 }
-                TIMED("ks_inner", 8.0 * N * nj * (2.0 * nd * nx + 2.0 * nx + ell), s,
+                TIMED("ks_inner", 8.0 * N * nj * (4.0 * nd * nx + 2.0 * nx + ell), s,
                       k_ks_inner<<<dim3(nblk((size_t)nx * N), nj), TPB, 0, s>>>(yhat, jobs, ell, A, c->L, c->logN,
                                                                                  c->d_prime, c->ks.md_P, ksk_words(c)));
                 LAUNCH_CHECK();
@@ -1185,12 +1185,12 @@ copse_status op_matmul(copse_ctx *c, const copse_evk *evk, const DCt &v, const s
                     }
                 }
                 for (int a = 0; a < na; a++) tab.acc[a] = part + (size_t)(a0 + a) * ext;
-                // algorithmic bytes: keys, diagonals, accumulators in and out, the rotated
-                // digits and c0 once
+                // algorithmic bytes: keys with their Shoup companions, diagonals, accumulators
+                // in and out, the rotated digits and c0 once
                 // (with R_k precomputed: R_k in place of the keys, digits and c0)
                 const double bytes = 8.0 * N * (nz_pt * (double)nx + 4.0 * na * nx * parts +
                                                 (Rall ? (double)nr * 2 * nx
-                                                      : (double)nr * 2 * nd * nx + (double)nd * nx + ell));
+                                                      : (double)nr * 4 * nd * nx + (double)nd * nx + ell));
                 const dim3 grid(nblk((size_t)nx * N), parts);
 #define MM_CASE(K)                                                                                        \
     case K:                                                                                               \
@@ -1294,7 +1294,7 @@ copse_status giant_phase(copse_ctx *c, const copse_evk *evk, const u64 *inner, i
                     tab.t[i] = RsTerm{yhat + (size_t)(x - x0) * nd * nx * N, inner + (size_t)x * per,
                                       evk->find(gal[x]), gal[x]};
                 }
-                const double bytes = 8.0 * N * ((double)nt * (2.0 * nd * nx + (double)nd * nx + ell) + 4.0 * nx);
+                const double bytes = 8.0 * N * ((double)nt * (4.0 * nd * nx + (double)nd * nx + ell) + 4.0 * nx);
                 TIMED("rotsum", bytes, s,
                       k_rotsum<<<nblk((size_t)nx * N), TPB, 0, s>>>(tab, nt, acc + (size_t)a * ext, ell, A, c->L,
                                                                     c->logN, c->d_prime, c->ks, ksk_words(c)));
