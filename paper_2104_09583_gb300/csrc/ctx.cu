@@ -265,6 +265,21 @@ static copse_status build_tables(copse_ctx *c) {
             mdd_Binv[(size_t)ell * L + i] = mk_shoup(h_inv(B, qi), qi);
         }
     }
+    // first-step factors times N^-1: the scales of the inverse transforms feeding the conversions
+    auto scaled = [&](const Shoup &f, int g) { return mk_shoup(h_mul(f.w, c->hprime[g].ninv, c->primes[g]), c->primes[g]); };
+    std::vector<Shoup> mu_scale(modup_inv.size()), md_scale(A), ms_scale(L + 1), mdd_scale(mdd_inv.size());
+    for (int ell = 1; ell <= L; ell++)
+        for (int i = 0; i < ell; i++) mu_scale[(size_t)ell * L + i] = scaled(modup_inv[(size_t)ell * L + i], i);
+    for (int k = 0; k < A; k++) md_scale[k] = scaled(md_inv[k], L + k);
+    for (int ell = 2; ell <= L; ell++) {
+        ms_scale[ell] = scaled(ms_tinv[ell], ell - 1);
+        for (int k = 0; k < nb; k++)
+            mdd_scale[(size_t)ell * nb + k] = scaled(mdd_inv[(size_t)ell * nb + k], k == 0 ? ell - 1 : L + k - 1);
+    }
+    STATUS_TRY(upload(c, &c->ks.mu_scale, mu_scale));
+    STATUS_TRY(upload(c, &c->ks.md_scale, md_scale));
+    STATUS_TRY(upload(c, &c->ks.ms_scale, ms_scale));
+    STATUS_TRY(upload(c, &c->ks.mdd_scale, mdd_scale));
     STATUS_TRY(upload(c, &c->ks.mdd_inv, mdd_inv));
     STATUS_TRY(upload(c, &c->ks.mdd_hat, mdd_hat));
     STATUS_TRY(upload(c, &c->ks.mdd_B, mdd_B));

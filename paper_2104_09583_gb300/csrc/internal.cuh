@@ -165,6 +165,10 @@ struct KsTables {
     // b_k = p_{k-1}: mdd_inv[ell][k] = t^-1 (B/b_k)^-1 mod b_k; mdd_hat[ell][k][i] = B/b_k mod q_i;
     // mdd_B[ell][i] = B mod q_i; mdd_Binv[ell][i] = B^-1 mod q_i  (i < ell - 1)
     Shoup *mdd_inv;     // [(L+1) * (alpha+1)]
+    // the same first-step factors times N^-1 mod their prime: the scale of the inverse
+    // transform whose output the conversion reads (mu_scale [(L+1) * L], md_scale [alpha],
+    // ms_scale [L+1], mdd_scale [(L+1) * (alpha+1)], indexed like the factors above)
+    Shoup *mu_scale, *md_scale, *ms_scale, *mdd_scale;
     Shoup *mdd_hat;     // [(L+1) * (alpha+1) * L]
     u64 *mdd_B;         // [(L+1) * L]
     Shoup *mdd_Binv;    // [(L+1) * L]
@@ -266,6 +270,9 @@ struct NttBatch {
     int fixed;
     int skip_alpha = 0;  // > 0: poly p skips residues [j*skip_alpha, min((j+1)*skip_alpha, ell)),
     int skip_period = 0; //      j = p (skip_period = 0) or p mod skip_period (digits of several inputs)
+    // inverse transforms: when set, residue r's result is scaled by scale[r - r0] instead of
+    // N^-1 (the first step of the base conversion that reads it folded in: N^-1 * c mod q)
+    const Shoup *scale = nullptr;
 };
 // the staged row twiddles of the cluster transforms (context creation)
 copse_status ntt_stage_tables(copse_ctx *ctx);
@@ -327,14 +334,14 @@ copse_status ntt_forward_moddown(copse_ctx *ctx, const MdFuse &f, int njobs, cud
 // out-of-place inverse transform of residues [0, nr) (prime `fixed` when >= 0) of npoly
 // polynomials src + p sstride into dst + p dstride
 copse_status ntt_inverse_copy(copse_ctx *ctx, const u64 *src, size_t sstride, u64 *dst, size_t dstride, int npoly,
-                              int nr, int fixed, cudaStream_t s, bool *done);
+                              int nr, int fixed, cudaStream_t s, bool *done, const Shoup *scale = nullptr);
 // the same for one residue (prime `fixed`) of npoly <= MS_POLYS polynomials held at
 // separate addresses src[p] ([N] each) into dst + p N
 struct GatherSrc {
     const u64 *p[MS_POLYS];
 };
 copse_status ntt_inverse_gather(copse_ctx *ctx, const GatherSrc &src, int npoly, u64 *dst, int fixed, cudaStream_t s,
-                                bool *done);
+                                bool *done, const Shoup *scale = nullptr);
 // ModUp of n_items inputs: the transform of every digit's conversion (xc: the inputs in
 // coefficient form, [item][ell][N]) into y [item][nd][ell+alpha][N], each digit's own
 // residues copied from x_ntt + item * xs

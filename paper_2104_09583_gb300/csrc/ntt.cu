@@ -115,7 +115,8 @@ __global__ void __launch_bounds__(512) k_ntt_inv(NttBatch b, const PrimeDev *__r
         }
         __syncthreads();
     }
-    for (int i = threadIdx.x; i < N; i += blockDim.x) data[i] = mul_shoup(sm[i], P.ninv, P.ninv_sh, q);
+    const Shoup sc = b.scale ? b.scale[r - b.r0] : Shoup{P.ninv, P.ninv_sh};
+    for (int i = threadIdx.x; i < N; i += blockDim.x) data[i] = mul_shoup(sm[i], sc, q);
 }
 
 // ---------------------------------------------------------------- two passes (N = N1 x N2)
@@ -345,8 +346,9 @@ __global__ void __launch_bounds__(NT2) k_ntt_inv_cols(NttBatch b, const PrimeDev
     __syncthreads();
     tile_inv<true>(sm, stw, stwp, a, t.q, t.q2, [&](int g, int i) { return (i << lc) + g; },
              [&](int u, int, int il) { return (1 << (a - 1 - u)) + il; });
+    const Shoup sc = b.scale ? b.scale[t.r - b.r0] : Shoup{P.ninv, P.ninv_sh};
     for (int e = threadIdx.x; e < TILE; e += NT2)
-        data[((size_t)(e >> lc) << lb) + (e & (C - 1))] = mul_shoup(sm[e], P.ninv, P.ninv_sh, t.q);
+        data[((size_t)(e >> lc) << lb) + (e & (C - 1))] = mul_shoup(sm[e], sc, t.q);
 }
 
 // ---------------------------------------------------------------- one launch per transform (clusters)
@@ -395,7 +397,7 @@ __device__ __forceinline__ u64 mdd_load(const MddFuse &f, const PrimeDev *pr, co
     u64 acc = 0;
     for (int k = 0; k < nb; k++) {
         const u64 bk = k == 0 ? pr[ell - 1].q : pr[L + k - 1].q;
-        const u64 y = mul_shoup(up[((size_t)(ell - 1 + k) << logN) + n], T.mdd_inv[(size_t)ell * nb + k], bk);
+        const u64 y = up[((size_t)(ell - 1 + k) << logN) + n];  // [U_k (B/b_k)^-1 / t]_{b_k}: scaled by the inverse transform
         u64 v = mul_shoup(y, T.mdd_hat[((size_t)ell * nb + k) * L + r], qi);
         if (y > (bk - 1) / 2) v = sub_mod(v, T.mdd_B[(size_t)ell * L + r], qi);
         acc = add_mod(acc, v, qi);
@@ -480,7 +482,7 @@ struct MuIO {
         u64 acc = 0;
         for (int i = lo; i < hi; i++) {
             const u64 qi = pr[i].q;
-            const u64 v = mul_shoup(x[((size_t)i << logN) + n], T.modup_inv[(size_t)ell * L + i], qi);
+            const u64 v = x[((size_t)i << logN) + n];  // already times modup_inv (inverse transform's scale)
             const size_t ti = ((size_t)ell * L + i) * NP + g;
             u64 w = mul_shoup(v, T.modup_hat[ti], qg);
             if (v > (qi - 1) / 2) w = sub_mod(w, T.modup_qhat[ti], qg);
@@ -508,7 +510,7 @@ struct MsIO {
     int L, logN;
     __device__ __forceinline__ u64 load(int p, int r, int, size_t n) const {
         const u64 ql = pr[f.ell - 1].q;
-        const u64 w = mul_shoup(f.last[((size_t)p << logN) + n], T.ms_tinv[f.ell], ql);
+        const u64 w = f.last[((size_t)p << logN) + n];  // already times t^-1 (inverse transform's scale)
         // |centred w| < q_{ell-1}/2 < q_r: the chain is in decreasing order
         return w > (ql - 1) / 2 ? pr[r].q - (ql - w) : w;
     }
@@ -530,7 +532,7 @@ struct MdIO {
         u64 acc = 0;
         for (int k = 0; k < alpha; k++) {
             const u64 pk = pr[L + k].q;
-            const u64 y = mul_shoup(up[((size_t)(f.ell + k) << logN) + n], T.md_inv[k], pk);
+            const u64 y = up[((size_t)(f.ell + k) << logN) + n];  // already times md_inv[k] (inverse transform's scale)
             u64 v = mul_shoup(y, T.md_hat[(size_t)k * L + r], qi);
             if (y > (pk - 1) / 2) v = sub_mod(v, T.md_P[r], qi);
             acc = add_mod(acc, v, qi);
@@ -664,9 +666,10 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT2)
     cl.sync();
     tile_inv<true>(S.colt, S.ctw, S.ctwp, a, q, q2, [&](int gg, int i) { return (i << lc) + gg; },
                    [&](int u, int, int il) { return (1 << (a - 1 - u)) + il; });
+    const Shoup sc = b.scale ? b.scale[r - b.r0] : Shoup{P.ninv, P.ninv_sh};
     for (int e = threadIdx.x; e < TILE; e += NT2)
         io.store(p, r, g, (size_t)(rank << lc) + ((size_t)(e >> lc) << lb) + (e & (C - 1)),
-                 mul_shoup(S.colt[e], P.ninv, P.ninv_sh, q));
+                 mul_shoup(S.colt[e], sc, q));
 }
 
 template <int CL>
@@ -888,22 +891,26 @@ copse_status ntt_forward_moddown(copse_ctx *ctx, const MdFuse &f, int njobs, cud
 }
 
 copse_status ntt_inverse_copy(copse_ctx *ctx, const u64 *src, size_t sstride, u64 *dst, size_t dstride, int npoly,
-                              int nr, int fixed, cudaStream_t s, bool *done) {
+                              int nr, int fixed, cudaStream_t s, bool *done, const Shoup *scale) {
     NttBatch b{nullptr, 0, npoly, 0, nr, nr, fixed};
+    b.scale = scale;
     return launch_fused<true>(ctx, b, CopyIO{src, sstride, dst, dstride, ctx->logN}, s, done);
 }
 
 copse_status ntt_inverse_gather(copse_ctx *ctx, const GatherSrc &src, int npoly, u64 *dst, int fixed, cudaStream_t s,
-                                bool *done) {
+                                bool *done, const Shoup *scale) {
     if (npoly > MS_POLYS) { set_error("internal: too many polynomials in one gathered transform"); return COPSE_EINVAL; }
     NttBatch b{nullptr, 0, npoly, 0, 1, 1, fixed};
+    b.scale = scale;
     STATUS_TRY(launch_fused<true>(ctx, b, GatherIO{src, dst, ctx->logN}, s, done));
     if (*done) return COPSE_OK;
     // a gather, then the in-place transform
     const size_t n = (size_t)npoly * ctx->N;
     k_gather_res<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(src, npoly, dst, ctx->logN);
     if (cudaGetLastError() != cudaSuccess) { set_error("gather kernel failed to launch"); return COPSE_ECUDA; }
-    STATUS_TRY(launch(ctx, NttBatch{dst, (size_t)ctx->N, npoly, 0, 1, 1, fixed}, s, true));
+    NttBatch bi{dst, (size_t)ctx->N, npoly, 0, 1, 1, fixed};
+    bi.scale = scale;
+    STATUS_TRY(launch(ctx, bi, s, true));
     *done = true;
     return COPSE_OK;
 }

@@ -142,7 +142,7 @@ __global__ void k_modup(const u64 *x, const u64 *x_ntt, size_t xs, u64 *y, int e
     bool neg[MAX_ALPHA];
     for (int i = lo; i < hi; i++) {
         const u64 qi = pr[i].q;
-        u64 v = mul_shoup(x[((size_t)i << logN) + n], T.modup_inv[(size_t)ell * L + i], qi);
+        u64 v = x[((size_t)i << logN) + n];  // already times modup_inv (inverse transform's scale)
         yv[i - lo] = v;
         neg[i - lo] = v > (qi - 1) / 2;
     }
@@ -225,7 +225,7 @@ __global__ void k_moddown_conv(const u64 *u, size_t ustride, u64 *W, size_t wstr
     bool neg[MAX_ALPHA];
     for (int k = 0; k < alpha; k++) {
         const u64 pk = pr[L + k].q;
-        u64 v = mul_shoup(up[((size_t)(ell + k) << logN) + n], T.md_inv[k], pk);
+        u64 v = up[((size_t)(ell + k) << logN) + n];  // already times md_inv[k] (inverse transform's scale)
         yv[k] = v;
         neg[k] = v > (pk - 1) / 2;
     }
@@ -478,7 +478,7 @@ __global__ void k_ms_conv(const u64 *last, u64 *W, int ncomp, int ell, int L, in
     if (e >= ((size_t)ncomp << logN)) return;
     const int c = (int)(e >> logN), n = (int)(e & (N - 1));
     const u64 ql = pr[ell - 1].q;
-    const u64 w = mul_shoup(last[e], T.ms_tinv[ell], ql);
+    const u64 w = last[e];  // already times t^-1 (inverse transform's scale)
     const bool neg = w > (ql - 1) / 2;
     for (int i = 0; i < ell - 1; i++) {
         // |centred w| < q_{ell-1}/2 < q_i: the chain is in decreasing order
@@ -680,14 +680,18 @@ copse_status ks_modup_batch(copse_ctx *c, const u64 *x_ntt, size_t xs, int n, in
     STATUS_TRY(sc.get(c, &xc, (size_t)n * ell * N));
     STATUS_TRY(sc.get(c, &y, (size_t)n * nd * nx * N));
     bool done = false;
-    STATUS_TRY(ntt_inverse_copy(c, x_ntt, xs, xc, (size_t)ell * N, n, ell, -1, s, &done));
+    // the inverse transform's output is scaled by modup_inv (the conversion's first step)
+    const Shoup *mu = c->ks.mu_scale + (size_t)ell * c->L;
+    STATUS_TRY(ntt_inverse_copy(c, x_ntt, xs, xc, (size_t)ell * N, n, ell, -1, s, &done, mu));
     if (!done) {
         if (n == 1)
             CUDA_TRY(cudaMemcpyAsync(xc, x_ntt, (size_t)ell * N * sizeof(u64), cudaMemcpyDeviceToDevice, s));
         else
             CUDA_TRY(cudaMemcpy2DAsync(xc, (size_t)ell * N * sizeof(u64), x_ntt, xs * sizeof(u64),
                                        (size_t)ell * N * sizeof(u64), n, cudaMemcpyDeviceToDevice, s));
-        STATUS_TRY(ntt_inverse(c, batch(xc, (size_t)ell * N, n, 0, ell, ell), s));
+        NttBatch ib = batch(xc, (size_t)ell * N, n, 0, ell, ell);
+        ib.scale = mu;
+        STATUS_TRY(ntt_inverse(c, ib, s));
     }
     STATUS_TRY(ntt_forward_modup(c, xc, x_ntt, xs, y, n, ell, s, &done));
     if (!done) {
@@ -718,7 +722,9 @@ copse_status moddown_apply(copse_ctx *c, u64 *U, int ell, int nj, MdFuse &f, Scr
     f.U = U;
     f.ustride = (size_t)nx * N;
     f.ell = ell;
-    STATUS_TRY(ntt_inverse(c, batch(U, (size_t)nx * N, 2 * nj, ell, A, ell), s));
+    NttBatch ib = batch(U, (size_t)nx * N, 2 * nj, ell, A, ell);
+    ib.scale = c->ks.md_scale;  // the conversion's first step (md_inv) folded in
+    STATUS_TRY(ntt_inverse(c, ib, s));
     bool done = false;
     STATUS_TRY(ntt_forward_moddown(c, f, nj, s, &done));
     if (done) return COPSE_OK;
@@ -796,12 +802,14 @@ copse_status op_modswitch(copse_ctx *c, const DCt &in, DCt *out, cudaStream_t s)
     // transform applies, else a copy and an in-place inverse transform
     bool inv_done = false;
     STATUS_TRY(ntt_inverse_copy(c, in.data + (size_t)(ell - 1) * N, (size_t)ell * N, last, N, nc, 1, ell - 1, s,
-                                &inv_done));
+                                &inv_done, c->ks.ms_scale + ell));
     if (!inv_done) {
         CUDA_TRY(cudaMemcpy2DAsync(last, (size_t)N * sizeof(u64), in.data + (size_t)(ell - 1) * N,
                                    (size_t)ell * N * sizeof(u64), (size_t)N * sizeof(u64), nc, cudaMemcpyDeviceToDevice,
                                    s));
-        STATUS_TRY(ntt_inverse(c, batch(last, N, nc, 0, 1, ell, ell - 1), s));
+        NttBatch ib = batch(last, N, nc, 0, 1, ell, ell - 1);
+        ib.scale = c->ks.ms_scale + ell;
+        STATUS_TRY(ntt_inverse(c, ib, s));
     }
     STATUS_TRY(ct_alloc(c, out, ell - 1, nc, s));
     // conversion of the dropped prime's residue to the others, transform and finish in one
@@ -835,12 +843,15 @@ copse_status op_modswitch_many(copse_ctx *c, const u64 *in, int n, int ell, std:
         u64 *last = nullptr;
         STATUS_TRY(sc.get(c, &last, (size_t)np * N));
         bool done = false;
-        STATUS_TRY(ntt_inverse_copy(c, x + (size_t)(ell - 1) * N, (size_t)ell * N, last, N, np, 1, ell - 1, s, &done));
+        STATUS_TRY(ntt_inverse_copy(c, x + (size_t)(ell - 1) * N, (size_t)ell * N, last, N, np, 1, ell - 1, s, &done,
+                                    c->ks.ms_scale + ell));
         if (!done) {
             CUDA_TRY(cudaMemcpy2DAsync(last, (size_t)N * sizeof(u64), x + (size_t)(ell - 1) * N,
                                        (size_t)ell * N * sizeof(u64), (size_t)N * sizeof(u64), np,
                                        cudaMemcpyDeviceToDevice, s));
-            STATUS_TRY(ntt_inverse(c, batch(last, N, np, 0, 1, ell, ell - 1), s));
+            NttBatch ib = batch(last, N, np, 0, 1, ell, ell - 1);
+            ib.scale = c->ks.ms_scale + ell;
+            STATUS_TRY(ntt_inverse(c, ib, s));
         }
         MsFuse f{last, x, nullptr, ell};
         for (int p = 0; p < np; p++) f.outp[p] = out[a0 + p / 2].data + (size_t)(p & 1) * (ell - 1) * N;
@@ -943,7 +954,9 @@ static copse_status mul_group(copse_ctx *c, const copse_evk *evk, const std::vec
     LAUNCH_CHECK();
     // the dropped prime's and the special residues to coefficients, then the fused
     // conversion + transform + finish (or conversion, transform, finish)
-    STATUS_TRY(ntt_inverse(c, batch(U, (size_t)nx * N, 2 * nj, ell - 1, A + 1, ell), s));
+    NttBatch ib = batch(U, (size_t)nx * N, 2 * nj, ell - 1, A + 1, ell);
+    ib.scale = c->ks.mdd_scale + (size_t)ell * (A + 1);  // the conversion's first step (mdd_inv) folded in
+    STATUS_TRY(ntt_inverse(c, ib, s));
     if (join_lane >= 0) {
         STATUS_TRY(fork_join(c, s, 1, join_lane));
         join_lane = -1;
@@ -1026,7 +1039,7 @@ copse_status op_modswitch_cts(copse_ctx *c, const std::vector<const DCt *> &in, 
             f.outp[p] = out[a].data + (size_t)k * (ell - 1) * N;
         }
         bool done = false;
-        STATUS_TRY(ntt_inverse_gather(c, g, np, last, ell - 1, s, &done));
+        STATUS_TRY(ntt_inverse_gather(c, g, np, last, ell - 1, s, &done, c->ks.ms_scale + ell));
         STATUS_TRY(ntt_forward_modswitch(c, f, np, s, &done));
         if (!done) {
             u64 *W = nullptr;
