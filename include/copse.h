@@ -425,10 +425,12 @@ copse_status copse_tune_dnum(const copse_params *base, int device, copse_model *
 /* ---------------------------------------------------------------- kernel timing
  * Instrumentation, off by default.  When on, the library brackets every
  * kernel launch with two CUDA events on the launch stream and tags it with
- * its family ("ntt_fwd", "ntt_inv", "modup", "ks_inner", "moddown_conv",
- * "ks_finish", "matmul_mac", "tensor", "ms_conv", "ms_finish", "affine",
- * "add") and its algorithmic bytes (each operand read once, each result
- * written once).  The paper's own measurement is per-stage wall time
+ * its family (transforms: "ntt_fwd", "ntt_inv", "ntt_inv_copy" and the fused
+ * forms "ntt_fwd_ms", "ntt_fwd_md", "ntt_fwd_mu", "ntt_fwd_mdd"; key switching
+ * and products: "modup", "ks_inner", "mm_fused", "mm_finish", "rotsum",
+ * "sum_parts", "enc_mac", "moddown_conv", "ks_finish", "ms_conv", "ms_finish";
+ * elementwise: "tensor", "affine", "add") and its algorithmic bytes (each
+ * operand read once, each result written once).  The paper's own measurement is per-stage wall time
  * (Section 8.4); this gives the per-kernel view. */
 copse_status copse_stats_enable(int on);
 /* Wait for the device and clear every total. */

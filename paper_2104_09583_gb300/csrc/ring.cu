@@ -52,17 +52,6 @@ __global__ void k_add_plain(u64 *ct, const u64 *p, int level, int logN, const Pr
     ct[e] = add_mod(ct[e], p[e], pr[e >> logN].q);
 }
 
-__global__ void k_tensor(const u64 *a, const u64 *b, u64 *out, int level, int logN, const PrimeDev *pr) {
-    size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    size_t n = (size_t)level << logN;
-    if (e >= n) return;
-    const PrimeDev P = pr[e >> logN];
-    u64 a0 = a[e], a1 = a[n + e], b0 = b[e], b1 = b[n + e];
-    out[e] = mul_mod(a0, b0, P);
-    out[n + e] = add_mod(mul_mod(a0, b1, P), mul_mod(a1, b0, P), P.q);
-    out[2 * n + e] = mul_mod(a1, b1, P);
-}
-
 __global__ void k_affine(const u64 *x, const u64 *m, const u64 *addp, u64 *out, int level, int logN,
                          const PrimeDev *pr) {
     size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -431,16 +420,6 @@ __global__ void k_sum_parts(const u64 *part, size_t stride, int nparts, u64 *out
     u64 s = part[i];
     for (int y = 1; y < nparts; y++) s = add_mod(s, part[(size_t)y * stride + i], q);
     out[i] = s;
-}
-
-// out[c] += pt * v[c] for both components (pt: first ell residues of an extended-basis plaintext)
-__global__ void k_ident_mac(u64 *out, const u64 *v, const u64 *pt, int ell, int logN, const PrimeDev *pr) {
-    const size_t n = (size_t)ell << logN;
-    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= 2 * n) return;
-    const size_t k = e < n ? e : e - n;
-    const PrimeDev P = pr[k >> logN];
-    out[e] = add_mod(out[e], mul_mod(pt[k], v[e], P), P.q);
 }
 
 // The last step of matrix products for a batch of outputs (blockIdx.y = output a):
@@ -1249,7 +1228,7 @@ copse_status op_matmul(copse_ctx *c, const copse_evk *evk, const DCt &v, const s
             any |= tab.pt_mul[i] || tab.pt_add[i];
         }
         if (!any) continue;
-        TIMED("ident_mac", 8.0 * N * 5.0 * ell * na, s,
+        TIMED("mm_finish", 8.0 * N * 5.0 * ell * na, s,
               k_finish<<<dim3(nblk(per), na), TPB, 0, s>>>(tab, v.data, ell, c->logN, c->d_prime));
         LAUNCH_CHECK();
     }
