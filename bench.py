@@ -397,8 +397,8 @@ def run_cuda(args, ws, rank, local):
         "config": {"workload": W.name, "ring_degree": N, "ciphertext_primes": W.primes, "prime_bits": W.bits,
                    "dnum": dnum, "tuning": tuning, "trees": 4, "branches": info["b"], "leaves": L, "depth": info["depth"],
                    "features": nf, "precision": W.precision(), "queries_per_step": 1, "parallelism": f"replicas{ws}",
-                   "l2": "working set > L2 (rotation keys alone are %.1f GB)" % (
-                       (info["n_rot_reshuffle"] + info["n_rot_level"]) * 3 * 2 * (W.primes + 4) * N * 8 / 1e9)},
+                   "l2": "working set > L2 (rotation keys with their Shoup companions alone are about %.1f GB)" % (
+                       (info["n_rot_reshuffle"] + info["n_rot_level"]) * 3 * 2 * (W.primes + 4) * N * 8 * 2 / 1e9)},
         "labels_ok": ok, "path": "graph session", "batched": batched, "plain_ops": plain_ops, "e2e": e2e,
         "serving": serving, "batch3": batch3, "table6": table6, "encmodel": encmodel, "gpu_launches": launches_total,
         "roofline": roof, "kernels": kern, "clocks": ck, "cpu_baseline": cpu,
