@@ -38,10 +38,10 @@ UNIT = "inferences/s"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["cuda", "reference"], default="cuda")
-    ap.add_argument("--workload", default="forest100-n16384")
+    ap.add_argument("--workload", default="encmodel32-n32768")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-stats", action="store_true", help="skip the per-kernel event timers")
     ap.add_argument("--profile", action="store_true", help="bracket the timed region with cudaProfilerStart/Stop")
@@ -52,7 +52,9 @@ def parse():
     ap.add_argument("--schedule", default=None,
                     help="dnum,g_reshuffle,g_level,ntt_cluster_max[,ntt_fused_max] for the headline workload instead of tuning "
                          "(e.g. the values a tuned run printed, to profile that schedule)")
-    ap.add_argument("--no-encmodel", action="store_true", help="skip the encrypted-model leg")
+    ap.add_argument("--no-forest100", action="store_true", help="skip the N = 2^14 plaintext-model legs")
+    ap.add_argument("--forest100-steps", type=int, default=200,
+                    help="steps of each N = 2^14 plaintext-model leg (one query, batched, plain)")
     return ap.parse_args()
 
 
@@ -180,13 +182,234 @@ def ncu_traffic(family, workload, alg_bytes_per_launch, key="dram_bytes_per_unit
 
 
 # ---------------------------------------------------------------- CUDA arm
+# kernel families -> the measured integer rate their algorithmic operations are priced at
+PEAK_KIND = {"enc_mac": "mac", "ks_inner": "mac", "mm_mac": "mac", "mm_fused": "mac"}
+
+
+def int_peaks(K, local):
+    """Measured rates of the modular arithmetic on this GPU (register-only microbenchmarks,
+    best of 5 CUDA-event timed runs): exact products in lazily reduced sums, lazy Shoup
+    butterflies, Barrett products."""
+    ctx = K.copse_ctx_create(10, 55, 4, 2, device=local)
+    try:
+        out = {}
+        for kind in ("mac", "butterfly", "barrett"):
+            ops, ms = K.copse_measure_int_peak(ctx, kind, 5)
+            out[kind] = {"ops_per_s": ops, "best_ms": ms}
+        return out
+    finally:
+        K.copse_ctx_destroy(ctx)
+
+
+def family_roofline(fam, ops, peaks_hbm, how, ipk, workload, steps):
+    """Roofline of the dominant kernel family (largest summed CUDA-event time) of an
+    instrumented step: HBM bytes (algorithmic) and, where the family counts its modular
+    products, the integer roof from the measured rate of that arithmetic."""
+    top = max(fam, key=lambda k: fam[k]["ms"])
+    v = fam[top]
+    sec = v["ms"] * 1e-3
+    achieved = v["bytes"] / sec / 1e9
+    hbm = {"achieved": achieved, "peak": peaks_hbm, "unit": "GB/s", "frac": achieved / peaks_hbm,
+           "peak_source": f"{how} hbm_gbs (copy)"}
+    tr = ncu_traffic(top, workload, v["bytes"] / v["launches"])
+    kind = PEAK_KIND.get(top)
+    if ops.get(top) and kind and ipk:
+        ach = ops[top] / sec
+        peak = ipk[kind]["ops_per_s"]
+        roof = {"kernel": top, "bound": "alu", "achieved": ach / 1e9, "peak": peak / 1e9,
+                "unit": "G modular products/s", "frac": ach / peak, "traffic": tr, "hbm": hbm,
+                "peak_source": f"measured in this run: register-only microbenchmark of exact 64-bit residue "
+                               f"products in lazily reduced sums ({kind}), best of 5"}
+    else:
+        roof = {"kernel": top, "bound": "hbm", "achieved": achieved, "peak": peaks_hbm, "unit": "GB/s",
+                "frac": achieved / peaks_hbm, "traffic": tr, "peak_source": f"{how} hbm_gbs (copy)"}
+    roof.update({"algorithmic_bytes_per_launch": v["bytes"] / v["launches"],
+                 "avg_launch_us": v["ms"] * 1e3 / v["launches"], "launches_per_step": v["launches"] / steps,
+                 "measured_on": "instrumented replay of the timed step (CUDA events around every launch)"})
+    return roof
+
+
+def family_table(fam, steps):
+    tot = max(1e-9, sum(x["ms"] for x in fam.values()))
+    return {k: {"launches_per_step": v["launches"] / steps, "ms_per_step": v["ms"] / steps, "share": v["ms"] / tot,
+                "gbs": v["bytes"] / (v["ms"] * 1e-3) / 1e9 if v["ms"] else 0.0}
+            for k, v in sorted(fam.items(), key=lambda kv: -kv[1]["ms"]) if v["launches"]}
+
+
 def run_cuda(args, ws, rank, local):
+    from paper_2104_09583_gb300 import copse as K
+
+    ipk = int_peaks(K, local)
+    line = run_headline(args, ws, rank, local, ipk)
+    line["int_peaks"] = ipk
+    if not args.no_forest100:
+        line["forest100"] = run_forest100(args, ws, rank, local, ipk)
+    line["serving"] = None if args.no_serving else run_serving(local, tune=not args.no_tune)
+    line["batch3"] = None if args.no_serving else run_batch3(local, tune=not args.no_tune)
+    line["table6"] = None if args.no_table6 else run_table6(local)
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = oracle_baseline_encmodel(synth_workload(args.workload), args.cpu_budget)
+    return line
+
+
+def synth_workload(name):
+    from paper_2104_09583_gb300 import synth
+    return synth.WORKLOADS[name]
+
+
+def run_headline(args, ws, rank, local, ipk, g=(128, 256)):
+    """The encrypted-model workload (Maurice = Diane): every model ciphertext (threshold planes,
+    all reshuffle and level diagonals, masks) encrypted once; one step = the batch of queries
+    encrypted, Algorithm 1 over all their ciphertexts, and the leaf bits decrypted, on one
+    stream.  Baby-step sizes from a tuner sweep of this model (copse_tune_bsgs)."""
+    import torch
+
+    from paper_2104_09583_gb300 import copse as K
+
+    W = synth_workload(args.workload)
+    text = W.forest_texts()[0]
+    N = 1 << W.log_n
+    ctx = K.copse_ctx_create(W.log_n, W.bits, W.primes, W.dnum, device=local)
+    model = K.copse_compile_forest(text, W.precision(), W.n_features(), W.log_n)
+    K.copse_model_set_encrypted(model, True)
+    K.copse_model_set_bsgs(model, *g)
+    info = K.copse_model_info_get(model)
+    per_ct = N // (info["block"] * info["n_segments"])
+    t0 = time.perf_counter()
+    keys, evk = K.copse_keygen(ctx, 29 + rank, [model])
+    torch.cuda.synchronize()
+    t_keys = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    K.copse_encrypt_model(ctx, keys, model, 2024 + rank)
+    t_enc = time.perf_counter() - t0
+    nq = W.queries[0]
+    qs = W.query_arrays()[0]
+    want = K.copse_classify_plain(model, qs)
+    L = info["n_leaves"]
+    stream = torch.cuda.current_stream().cuda_stream
+    d_q = torch.from_numpy(qs.astype(np.int32)).cuda()
+    d_bits = torch.zeros(nq * L, dtype=torch.uint8, device="cuda")
+
+    def step(seed):
+        ct = K.copse_encrypt_features(ctx, keys, model, d_q.data_ptr(), seed, stream=stream, on_device=True,
+                                      n_queries=nq)
+        res = K.copse_infer(ctx, evk, model, ct, stream=stream)
+        K.copse_decrypt_labels(ctx, keys, model, res, nq, stream=stream, out_device_ptr=d_bits.data_ptr())
+        K.copse_ctbuf_destroy(res)
+        K.copse_ctbuf_destroy(ct)
+
+    for w in range(args.warmup):
+        step(500 + 100 * w)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = Clocks(local)
+    barrier(ws)
+    torch.cuda.synchronize()
+    clocks.start()
+    if args.profile:
+        torch.cuda.profiler.start()
+    for i in range(args.steps):
+        ev[i][0].record()
+        step(900 + 100 * i)
+        ev[i][1].record()
+    torch.cuda.synchronize()
+    if args.profile:
+        torch.cuda.profiler.stop()
+    ck = clocks.stop()
+    barrier(ws)
+    per = [ev[i][0].elapsed_time(ev[i][1]) for i in range(args.steps)]
+    total_ms = max_over_ranks(ev[0][0].elapsed_time(ev[-1][1]), ws)
+    ok = bool(np.array_equal(d_bits.cpu().numpy().reshape(nq, L), want))
+
+    # per-kernel event timers over one instrumented step (the same launches as a timed step)
+    fam, ops = {}, {}
+    if not args.no_stats:
+        K.copse_stats_reset()
+        K.copse_stats_enable(True)
+        step(7000)
+        torch.cuda.synchronize()
+        K.copse_stats_enable(False)
+        fam = {k: v for k, v in K.copse_stats_all().items() if v["launches"]}
+        ops = {k: K.copse_stats_get_ops(k) for k in fam}
+    peaks, how = measured_peaks()
+    roof = family_roofline(fam, ops, peaks["hbm_gbs"], how, ipk, W.name, 1) if fam else None
+    launches_step = int(sum(v["launches"] for v in fam.values()))
+
+    # end to end through the C ABI: pinned host features in, leaf bits back to pinned host memory
+    h_q = torch.from_numpy(qs.astype(np.int32)).pin_memory()
+    h_bits = torch.zeros(nq * L, dtype=torch.uint8).pin_memory()
+
+    def e2e_step(seed):
+        ct = K.copse_encrypt_features(ctx, keys, model, h_q.numpy().view(np.uint32), seed, stream=stream)
+        res = K.copse_infer(ctx, evk, model, ct, stream=stream)
+        K.copse_decrypt_labels(ctx, keys, model, res, nq, stream=stream, out=h_bits.numpy())
+        K.copse_ctbuf_destroy(res)
+        K.copse_ctbuf_destroy(ct)
+
+    e_steps = max(3, args.steps // 4)
+    e2e_step(3000)
+    barrier(ws)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for i in range(e_steps):
+        e2e_step(3100 + i)
+    e1.record()
+    torch.cuda.synchronize()
+    e_ms = max_over_ranks(e0.elapsed_time(e1), ws)
+    e2e = {"value": ws * nq * e_steps / (e_ms / 1e3), "unit": UNIT, "steps": e_steps,
+           "h2d_bytes_per_step": int(qs.astype(np.uint32).nbytes), "d2h_bytes_per_step": int(nq * L),
+           "labels_ok": bool(np.array_equal(h_bits.numpy().reshape(nq, L), want)),
+           "path": "copse_encrypt_features (pinned host features) + copse_infer + copse_decrypt_labels (pinned host bits)"}
+
+    n_ct, words = model_ciphertexts(info, W, N)
+    K.copse_keys_destroy(keys)
+    K.copse_evk_destroy(evk)
+    K.copse_model_destroy(model)
+    K.copse_ctx_destroy(ctx)
+    value = ws * nq * args.steps / (total_ms / 1e3)
+    return {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps, "p50_ms": float(np.percentile(per, 50)),
+        "p99_ms": float(np.percentile(per, 99)), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u64 (RNS residues mod 55-bit primes)", "data": "synthetic (seeded random forest and queries)",
+        "config": {"workload": W.name, "ring_degree": N, "ciphertext_primes": W.primes, "prime_bits": W.bits,
+                   "dnum": W.dnum, "model": "encrypted (thresholds, every reshuffle and level diagonal, masks)",
+                   "trees": info["n_trees"], "branches": info["b"], "leaves": L, "depth": info["depth"],
+                   "features": info["n_features"], "precision": info["precision"], "q": info["q"],
+                   "row_segments": info["n_segments"], "block": info["block"],
+                   "queries_per_step": nq, "queries_per_ciphertext": per_ct,
+                   "query_ciphertexts": (nq + per_ct - 1) // per_ct, "bsgs": list(g),
+                   "rotation_keys": info["n_rot_reshuffle"] + info["n_rot_level"], "parallelism": f"replicas{ws}",
+                   "model_ciphertexts": n_ct, "model_gb_on_device": round(words * 8 / 1e9, 1),
+                   "model_encryption_s": round(t_enc, 2), "keygen_s": round(t_keys, 2),
+                   "l2": "inputs larger than L2 (the encrypted model alone is %.0f GB)" % (words * 8 / 1e9)},
+        "labels_ok": ok, "path": "copse_encrypt_features + copse_infer + copse_decrypt_labels on one stream",
+        "e2e": e2e, "gpu_launches": launches_step * args.steps, "roofline": roof,
+        "kernels": family_table(fam, 1), "clocks": ck,
+    }
+
+
+def model_ciphertexts(info, W, N):
+    """Count and device words (c0 only) of the encrypted model: p threshold planes at the top level,
+    q reshuffle diagonals at the level of Decisions, d (b + 1) level diagonals and masks one level
+    lower, b the branch count of one slot block."""
+    b = info["block_branches"]
+    lvl_D = W.primes - 1 - (info["precision"] - 1).bit_length()
+    n_ct = info["precision"] + info["q"] + info["depth"] * (b + 1)
+    words = (info["precision"] * W.primes + info["q"] * lvl_D + info["depth"] * (b + 1) * (lvl_D - 1)) * N
+    return n_ct, words
+
+
+def run_forest100(args, ws, rank, local, ipk):
+    """The N = 2^14 plaintext-model forest (4 random trees, 90..110 branches): one query per step
+    through a recorded graph session, 32 queries per ciphertext batched, and the plain path
+    (every kernel launched from the host, no graph)."""
     import torch
 
     from paper_2104_09583_gb300 import copse as K
     from paper_2104_09583_gb300 import synth
 
-    W = synth.WORKLOADS[args.workload]
+    W = synth.WORKLOADS["forest100-n16384"]
     text = W.forest_texts()[0]
     N = 1 << W.log_n
     model = K.copse_compile_forest(text, W.precision(), W.n_features(), W.log_n)
@@ -211,6 +434,7 @@ def run_cuda(args, ws, rank, local):
     stream = torch.cuda.current_stream().cuda_stream
     per_ct = N // info["block"]
     nf, L = info["n_features"], info["n_leaves"]
+    steps = args.forest100_steps
 
     def make_inputs(nq, seed):
         q = synth.random_queries(seed, nq, nf, W.precision())
@@ -226,39 +450,28 @@ def run_cuda(args, ws, rank, local):
         K.copse_ctbuf_destroy(res)
         K.copse_ctbuf_destroy(ct)
 
-    def timed(nq, steps, warmup, seed0, stats=False, clocks=None, profile=False):
+    def timed(nq, steps, warmup, seed0, stats=False):
         q, d_feats, d_bits = make_inputs(nq, seed0 + rank)
         for w in range(warmup):
             step(nq, d_feats, d_bits, 1000 + w)
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-        barrier(ws)
         torch.cuda.synchronize()
         if stats:
             K.copse_stats_reset()
             K.copse_stats_enable(True)
-        if clocks:
-            clocks.start()
-        if profile:
-            torch.cuda.profiler.start()
         for i in range(steps):
             ev[i][0].record()
             step(nq, d_feats, d_bits, 2000 + i)
             ev[i][1].record()
         torch.cuda.synchronize()
-        if profile:
-            torch.cuda.profiler.stop()
-        ck = clocks.stop() if clocks else None
         if stats:
             K.copse_stats_enable(False)
-        barrier(ws)
         per = [ev[i][0].elapsed_time(ev[i][1]) for i in range(steps)]
         total_ms = ev[0][0].elapsed_time(ev[-1][1])
-        # decrypted bits of the last step against plaintext classification
         got = d_bits[: nq * L].cpu().numpy().reshape(nq, L)
-        ok = bool(np.array_equal(got, K.copse_classify_plain(model, q)))
-        return total_ms, per, ok, ck
+        return total_ms, per, bool(np.array_equal(got, K.copse_classify_plain(model, q)))
 
-    def timed_session(sess, nq, steps, warmup, seed0, clocks=None, profile=False):
+    def timed_session(sess, nq, steps, warmup, seed0):
         """Graph-replayed steps (copse_session_run) on device-resident features and bits."""
         q, d_feats, d_bits = make_inputs(nq, seed0 + rank)
         run = lambda seed: K.copse_session_run(sess, None, seed, stream=stream, feats_ptr=d_feats.data_ptr(),
@@ -266,144 +479,48 @@ def run_cuda(args, ws, rank, local):
         for w in range(warmup):
             run(5000 + w)
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-        barrier(ws)
         torch.cuda.synchronize()
-        if clocks:
-            clocks.start()
-        if profile:
-            torch.cuda.profiler.start()
         for i in range(steps):
             ev[i][0].record()
             run(6000 + i)
             ev[i][1].record()
         torch.cuda.synchronize()
-        if profile:
-            torch.cuda.profiler.stop()
-        ck = clocks.stop() if clocks else None
-        barrier(ws)
         per = [ev[i][0].elapsed_time(ev[i][1]) for i in range(steps)]
         total_ms = ev[0][0].elapsed_time(ev[-1][1])
         got = d_bits[: nq * L].cpu().numpy().reshape(nq, L)
-        ok = bool(np.array_equal(got, K.copse_classify_plain(model, q)))
-        return total_ms, per, ok, ck
+        return total_ms, per, bool(np.array_equal(got, K.copse_classify_plain(model, q)))
+
+    def leg(ms, per, ok, nq, n, path):
+        return {"queries_per_step": nq, "value": nq * n / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / n,
+                "p50_ms": float(np.percentile(per, 50)), "p99_ms": float(np.percentile(per, 99)),
+                "labels_ok": ok, "path": path}
 
     sess1 = K.copse_session_create(ctx, keys, evk, model, 1)
     sessB = K.copse_session_create(ctx, keys, evk, model, per_ct)
-    clocks = Clocks(local)
-    # headline: one query per step, the recorded graph replayed
-    total_ms, per, ok, ck = timed_session(sess1, 1, args.steps, args.warmup, 11, clocks=clocks, profile=args.profile)
-    total_ms = max_over_ranks(total_ms, ws)
-    value = ws * args.steps / (total_ms / 1e3)
-    # batched: every slot block of the ciphertext holds a query
-    b_steps = max(3, args.steps // 2)
-    b_ms, b_per, b_ok, _ = timed_session(sessB, per_ct, b_steps, args.warmup, 21)
-    b_ms = max_over_ranks(b_ms, ws)
-    batched = {"queries_per_step": per_ct, "value": ws * per_ct * b_steps / (b_ms / 1e3), "unit": UNIT,
-               "ms_per_step": b_ms / b_steps, "p50_ms": float(np.percentile(b_per, 50)),
-               "p99_ms": float(np.percentile(b_per, 99)), "labels_ok": b_ok, "path": "graph session"}
-    # the plain GPU path: one query, every kernel launched from the host, no graph
-    p_ms, p_per, p_ok, _ = timed(1, b_steps, args.warmup, 31)
-    p_ms = max_over_ranks(p_ms, ws)
-    plain_ops = {"queries_per_step": 1, "value": ws * b_steps / (p_ms / 1e3), "unit": UNIT,
-                 "ms_per_step": p_ms / b_steps, "p50_ms": float(np.percentile(p_per, 50)),
-                 "p99_ms": float(np.percentile(p_per, 99)), "labels_ok": p_ok, "path": "host-launched operations"}
-    # per-kernel event timers over an instrumented replay of the same step (host-launched)
-    fam = {}
-    if not args.no_stats:
-        timed(1, args.steps, 1, 41, stats=True)
-        fam = K.copse_stats_all()
-
-    # end to end through the C ABI: pinned host features in, leaf bits back to pinned host memory
-    q = synth.random_queries(31 + rank, 1, nf, W.precision())
-    h_feats = torch.from_numpy(q.copy()).pin_memory()
-    h_bits = torch.zeros((1, L), dtype=torch.uint8).pin_memory()
-
-    def e2e_step(seed):
-        K.copse_session_run(sess1, h_feats.numpy(), seed, out=h_bits.numpy(), stream=stream)
-
-    for w in range(args.warmup):
-        e2e_step(3000 + w)
-    barrier(ws)
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for i in range(args.steps):
-        e2e_step(4000 + i)
-    e1.record()
-    torch.cuda.synchronize()
-    e_ms = max_over_ranks(e0.elapsed_time(e1), ws)
-    e2e = {"value": ws * args.steps / (e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(q.nbytes) + 8,
-           "d2h_bytes_per_step": int(L), "labels_ok": bool(np.array_equal(h_bits.numpy(), K.copse_classify_plain(model, q)))}
+    one = leg(*timed_session(sess1, 1, steps, 3, 11), 1, steps, "graph session, one query per step")
+    batched = leg(*timed_session(sessB, per_ct, steps, 3, 21), per_ct, steps,
+                  f"graph session, {per_ct} queries per ciphertext")
+    plain = leg(*timed(1, steps, 3, 31), 1, steps, "host-launched operations, one query, no graph")
+    # per-kernel event timers over instrumented host-launched steps
+    timed(1, steps, 1, 41, stats=True)
+    fam = {k: v for k, v in K.copse_stats_all().items() if v["launches"]}
+    ops = {k: K.copse_stats_get_ops(k) for k in fam}
+    peaks, how = measured_peaks()
     K.copse_session_destroy(sess1)
     K.copse_session_destroy(sessB)
-
-    # roofline of the dominant kernel family (largest summed event time)
-    peaks, how = measured_peaks()
-    roof = None
-    launches_total = 0
-    kern = {}
-    if fam:
-        # the graph replays exactly the kernels of the instrumented host-launched step
-        launches_total = int(sum(v["launches"] for v in fam.values()))
-        for k, v in fam.items():
-            if v["launches"]:
-                kern[k] = {"launches_per_step": v["launches"] / args.steps, "ms_per_step": v["ms"] / args.steps,
-                           "share": v["ms"] / max(1e-9, sum(x["ms"] for x in fam.values())),
-                           "gbs": v["bytes"] / (v["ms"] * 1e-3) / 1e9 if v["ms"] else 0.0}
-        top = max(fam, key=lambda k: fam[k]["ms"])
-        v = fam[top]
-        achieved = v["bytes"] / (v["ms"] * 1e-3) / 1e9
-        tr = ncu_traffic(top, args.workload, v["bytes"] / v["launches"])
-        hbm = {"achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
-               "peak_source": f"{how} hbm_gbs (copy)"}
-        wi = ncu_traffic(top, args.workload, v["bytes"] / v["launches"], key="warp_instructions_per_unit")
-        if wi is not None:
-            # integer issue roof: 152 SMs x 4 schedulers x 1 warp instruction per clock at the
-            # maximum SM clock; achieved = the ncu instruction count per unit scaled to the
-            # average launch, over its CUDA-event duration
-            peak_wi = 152 * 4 * 2.07e9 / 1e9
-            ach_wi = wi / (v["ms"] * 1e-3 / v["launches"]) / 1e9
-            roof = {"kernel": top, "bound": "alu", "achieved": ach_wi, "peak": peak_wi,
-                    "unit": "G warp-instructions/s", "frac": ach_wi / peak_wi, "traffic": tr, "hbm": hbm,
-                    "peak_source": "152 SMs x 4 schedulers x 1 warp instruction/clock x 2.07 GHz"}
-        else:
-            roof = {"kernel": top, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                    "frac": achieved / peaks["hbm_gbs"], "traffic": tr, "peak_source": f"{how} hbm_gbs (copy)"}
-        roof.update({"algorithmic_bytes_per_launch": v["bytes"] / v["launches"],
-                     "avg_launch_us": v["ms"] * 1e3 / v["launches"],
-                     "measured_on": "instrumented host-launched replay of the timed step (CUDA events per launch)"})
-
-    serving = None if args.no_serving else run_serving(local, tune=not args.no_tune)
-    batch3 = None if args.no_serving else run_batch3(local, tune=not args.no_tune)
-    table6 = None if args.no_table6 else run_table6(local)
-    encmodel = None if args.no_encmodel else run_encmodel(local)
-
-    cpu = None
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cpu = oracle_baseline(W, text, args.cpu_budget)
-
-    for h in (keys,):
-        K.copse_keys_destroy(h)
+    K.copse_keys_destroy(keys)
     K.copse_evk_destroy(evk)
     K.copse_model_destroy(model)
     K.copse_ctx_destroy(ctx)
-
-    line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": total_ms / args.steps, "p50_ms": float(np.percentile(per, 50)),
-        "p99_ms": float(np.percentile(per, 99)), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "u64 (RNS residues mod 55-bit primes)", "data": "synthetic (seeded random forest and queries)",
-        "config": {"workload": W.name, "ring_degree": N, "ciphertext_primes": W.primes, "prime_bits": W.bits,
-                   "dnum": dnum, "tuning": tuning, "trees": 4, "branches": info["b"], "leaves": L, "depth": info["depth"],
-                   "features": nf, "precision": W.precision(), "queries_per_step": 1, "parallelism": f"replicas{ws}",
-                   "l2": "working set > L2 (rotation keys with their Shoup companions alone are about %.1f GB)" % (
-                       (info["n_rot_reshuffle"] + info["n_rot_level"]) * 3 * 2 * (W.primes + 4) * N * 8 * 2 / 1e9)},
-        "labels_ok": ok, "path": "graph session", "batched": batched, "plain_ops": plain_ops, "e2e": e2e,
-        "serving": serving, "batch3": batch3, "table6": table6, "encmodel": encmodel, "gpu_launches": launches_total,
-        "roofline": roof, "kernels": kern, "clocks": ck, "cpu_baseline": cpu,
-    }
-    return line
+    n_rot = info["n_rot_reshuffle"] + info["n_rot_level"]
+    alpha = -(-W.primes // dnum)
+    key_gb = n_rot * dnum * 2 * (W.primes + alpha) * N * 8 / 1e9
+    return {"workload": W.name, "ring_degree": N, "ciphertext_primes": W.primes, "dnum": dnum, "tuning": tuning,
+            "branches": info["b"], "leaves": L, "depth": info["depth"], "one_query": one, "batched": batched,
+            "plain_ops": plain, "kernels": family_table(fam, steps),
+            "roofline": family_roofline(fam, ops, peaks["hbm_gbs"], how, ipk, W.name, steps) if fam else None,
+            "rotation_keys": n_rot,
+            "key_working_set_gb": round(key_gb, 2), "l2": "working set > L2 (rotation keys %.1f GB)" % key_gb}
 
 
 def autotune(K, ctx, models, g_r=(0, 16, 32, 64), g_l=(0, 4, 8), nq=1):
@@ -583,93 +700,6 @@ def run_batch3(local, steps=3, warmup=1, tune=True):
                         f"rotations, {p} queries/ciphertext" for i, p in zip(infos, per)]}
 
 
-# ---------------------------------------------------------------- encrypted model
-def run_encmodel(local, steps=1, warmup=1, g=(128, 256)):
-    """The encrypted-model workload (Maurice = Diane): 32 random trees of depth <= 8, 32 features,
-    16-bit, 10 classes, N = 2^15 with 16 primes; every model ciphertext (thresholds, all reshuffle
-    and level diagonals, masks) encrypted once; one step = the 64 queries (2 per ciphertext, 32
-    ciphertexts) encrypted, inferred together and decrypted on one stream.  Baby-step sizes from
-    a tuner sweep of this model (copse_tune_bsgs: 128 / 256 fastest)."""
-    import torch
-
-    from paper_2104_09583_gb300 import copse as K
-    from paper_2104_09583_gb300 import synth
-
-    W = synth.WORKLOADS["encmodel32-n32768"]
-    text = W.forest_texts()[0]
-    N = 1 << W.log_n
-    ctx = K.copse_ctx_create(W.log_n, W.bits, W.primes, W.dnum, device=local)
-    model = K.copse_compile_forest(text, W.precision(), W.n_features(), W.log_n)
-    K.copse_model_set_encrypted(model, True)
-    K.copse_model_set_bsgs(model, *g)
-    info = K.copse_model_info_get(model)
-    per_ct = N // info["block"]
-    t0 = time.perf_counter()
-    keys, evk = K.copse_keygen(ctx, 29, [model])
-    torch.cuda.synchronize()
-    t_keys = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    K.copse_encrypt_model(ctx, keys, model, 2024)
-    t_enc = time.perf_counter() - t0
-    nq = W.queries[0]
-    qs = W.query_arrays()[0]
-    want = K.copse_classify_plain(model, qs)
-    L = info["n_leaves"]
-    stream = torch.cuda.current_stream().cuda_stream
-    d_q = torch.from_numpy(qs.astype(np.int32)).cuda()
-    d_bits = torch.zeros(nq * L, dtype=torch.uint8, device="cuda")
-
-    def step(seed):
-        # all query ciphertexts in one buffer: the products read each encrypted diagonal
-        # (and regenerate its mask) once per group of query ciphertexts
-        ct = K.copse_encrypt_features(ctx, keys, model, d_q.data_ptr(), seed, stream=stream, on_device=True,
-                                      n_queries=nq)
-        res = K.copse_infer(ctx, evk, model, ct, stream=stream)
-        K.copse_decrypt_labels(ctx, keys, model, res, nq, stream=stream, out_device_ptr=d_bits.data_ptr())
-        K.copse_ctbuf_destroy(res)
-        K.copse_ctbuf_destroy(ct)
-
-    for w in range(warmup):
-        step(500 + 100 * w)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for i in range(steps):
-        step(900 + 100 * i)
-    e1.record()
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / steps
-    ok = bool(np.array_equal(d_bits.cpu().numpy().reshape(nq, L), want))
-    # per-stage breakdown of one ciphertext's inference, then its kernels by family
-    ct = K.copse_encrypt_features(ctx, keys, model, qs[:per_ct], 77)
-    res, stages = K.copse_infer_timed(ctx, evk, model, ct)
-    K.copse_ctbuf_destroy(res)
-    K.copse_stats_reset()
-    K.copse_stats_enable(True)
-    res = K.copse_infer(ctx, evk, model, ct)
-    torch.cuda.synchronize()
-    K.copse_stats_enable(False)
-    fam = {k: {"launches": v["launches"], "ms": round(v["ms"], 3)} for k, v in K.copse_stats_all().items()
-           if v["launches"]}
-    fam = dict(sorted(fam.items(), key=lambda kv: -kv[1]["ms"])[:8])
-    K.copse_ctbuf_destroy(res)
-    K.copse_ctbuf_destroy(ct)
-    n_ct = info["precision"] + info["q"] + info["depth"] * (info["b"] + 1)
-    lvl_D = W.primes - 1 - (info["precision"] - 1).bit_length()
-    words = (info["precision"] * W.primes + info["q"] * lvl_D + info["depth"] * (info["b"] + 1) * (lvl_D - 1)) * N
-    K.copse_keys_destroy(keys)
-    K.copse_evk_destroy(evk)
-    K.copse_model_destroy(model)
-    K.copse_ctx_destroy(ctx)
-    return {"value": nq / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "queries_per_step": nq,
-            "ciphertexts_per_step": (nq + per_ct - 1) // per_ct, "labels_ok": ok,
-            "stage_ms_one_ciphertext": stages, "kernels_one_ciphertext": fam, "model_ciphertexts": n_ct,
-            "model_gb_on_device": round(words * 8 / 1e9, 1), "model_encryption_s": round(t_enc, 2),
-            "keygen_s": round(t_keys, 2), "bsgs": list(g), "rotation_keys": info["n_rot_reshuffle"] + info["n_rot_level"],
-            "model": f"{info['n_trees']} trees, {info['b']} branches, depth {info['depth']}, q {info['q']}, "
-                     f"{info['precision']}-bit, N = 2^{W.log_n}, {W.primes} primes"}
-
-
 # ---------------------------------------------------------------- Table 6 microbenchmarks
 def run_table6(local, reps=7, warmup=2, log_n=14, bits=55, primes=11, dnum=3):
     """The eight microbenchmark forests of Section 8.4 (Table 6; 2 features, 3 labels),
@@ -716,134 +746,127 @@ def run_table6(local, reps=7, warmup=2, log_n=14, bits=55, primes=11, dnum=3):
 
 # ---------------------------------------------------------------- CPU oracle (baseline / reference arm)
 class OracleBench:
-    """The oracle on the benchmark workload: operation counts of one inference
-    (exact, from the compiled model and the circuit's structure) and timed
-    samples of its operations at the levels where the circuit runs them."""
+    """The oracle on the encrypted-model workload: exact operation counts of one step (the
+    batch of queries through Algorithm 1 with the model encrypted, under the same baby-step
+    plan as the CUDA arm) and timed samples of each operation at the level where the circuit
+    runs it.  A whole step takes the oracle days (millions of ciphertext products at
+    N = 2^15), so the step time is extrapolated from the samples with the exact counts."""
 
-    def __init__(self, W, text):
+    def __init__(self, W, text, g=(128, 256)):
         from oracle import bgv as B
         from oracle import copse as Cp
 
-        self.B, self.Cp = B, Cp
-        self.m = m = Cp.compile_forest(text, W.precision(), W.n_features())
+        self.B, self.Cp, self.W = B, Cp, W
+        self.m = m = Cp.compile_forest(text, W.precision(), W.n_features(), slots_per_row=1 << (W.log_n - 1))
         self.P = P = B.Params(logN=W.log_n, L=W.primes, bits=W.bits, dnum=W.dnum)
         self.bgv = B.Bgv(P)
-        self.rs, self.ls = Cp.rotation_sets(m)
-        self.keys = self.bgv.keygen(7, [B.galois_rot(W.log_n, k) for k in self.rs[:2]])
-        self.qs = W.query_arrays()[0]
-        p = m.precision
-        self.n = {"affine": 2 * p, "mul": max(0, 2 * p - 3) + (m.d - 1), "rot": len(self.rs) + len(self.ls),
-                  "pt": len(Cp.reshuffle_diagonals(m)) + sum(len(Cp.level_diagonals(m, k, P.t))
-                                                             for k in range(1, m.d + 1))}
-        self.Rd = {i: Cp.tile_blocks(m, dg, P.N) for i, dg in Cp.reshuffle_diagonals(m).items()}
+        rs, ls = Cp.encrypted_rotation_sets(m, g)
+        self.keys = self.bgv.keygen(7, [B.galois_rot(W.log_n, rs[0])])
+        self.galois = B.galois_rot(W.log_n, rs[0])
+        p, d = m.precision, m.d
+        per_ct = (1 << W.log_n) // (m.block * m.n_seg)
+        self.n_ct = -(-W.queries[0] // per_ct)
+        gr, gl = g
+        babies_r, babies_l = len({i % gr for i in range(m.q)} - {0}), len({i % gl for i in range(m.b)} - {0})
+        giants_r, giants_l = len({i - i % gr for i in range(m.q)} - {0}), len({i - i % gl for i in range(m.b)} - {0})
+        acc_r, acc_l = giants_r + 1, d * (giants_l + 1)
+        c = self.n_ct
+        self.lvl_D = P.L - 1 - (p - 1).bit_length()
+        # per step: the operation counts of every query ciphertext
+        self.n = {"enc": c * p, "mul_hi": c * (p + 2 * p - 3), "tensor_D": c * m.q, "tensor_B": c * d * m.b,
+                  "relin": c * (acc_r + acc_l), "rot_D": c * (babies_r + giants_r),
+                  "rot_B": c * (babies_l + d * giants_l), "mul_lo": c * (d - 1)}
+        self._t = {}
 
     def _clock(self, f, *a):
         s = time.perf_counter()
-        r = f(*a)
-        return r, time.perf_counter() - s
+        f(*a)
+        return time.perf_counter() - s
 
     def _op(self, kind):
-        """Run and time one operation of the workload's inference (seconds)."""
-        Cp, bgv, m = self.Cp, self.bgv, self.m
-        if not hasattr(self, "_X"):
-            self._X = Cp.encrypt_queries(bgv, self.keys, m, self.qs, 99)
-            self._E = Cp.BgvEngine(bgv, self.keys)
-            self._Y = self._E.thresholds(m)
-            lvl_D = self.P.L - 1 - (m.precision - 1).bit_length()
-            self._v = bgv.to_level(self._X[0], lvl_D)
-        E, X, Y = self._E, self._X, self._Y
+        B, bgv, P, k = self.B, self.bgv, self.P, self.keys
+        if not hasattr(self, "_x"):
+            z = np.zeros(P.N, dtype=np.int64)
+            self._x = bgv.encrypt_slots(k.pk, z, 99, 0)
+            self._xD = bgv.to_level(self._x, self.lvl_D)
+            self._xB = bgv.to_level(self._x, self.lvl_D - 1)
+            self._dD = bgv.encrypt_sk(k.sk, B.encode(P, z), 5, 1, self.lvl_D)
+            self._dB = bgv.encrypt_sk(k.sk, B.encode(P, z), 5, 2, self.lvl_D - 1)
+            self._t3 = bgv.tensor(self._dD, self._xD)
         if kind == "enc":
-            return self._clock(Cp.encrypt_queries, bgv, self.keys, m, self.qs, 99)[1]
-        if kind == "affine":
-            return self._clock(E.affine, X[0], (-Y[0]) % E.t, Y[0])[1]
-        if kind == "mul":
-            return self._clock(E.mul, X[0], X[1 % len(X)])[1]
-        k = self.rs[0]
-        if kind == "rot":
-            return self._clock(E.rot, self._v, k)[1]
-        return self._clock(E.mul_plain, self._v, self.Rd[k])[1]
+            return self._clock(bgv.encrypt_slots, k.pk, np.zeros(P.N, dtype=np.int64), 99, 1)
+        if kind == "mul_hi":
+            return self._clock(bgv.mul, self._x, self._x, k.rlk)
+        if kind == "mul_lo":
+            return self._clock(bgv.mul, self._xB, self._xB, k.rlk)
+        if kind == "tensor_D":
+            return self._clock(bgv.tensor, self._dD, self._xD)
+        if kind == "tensor_B":
+            return self._clock(bgv.tensor, self._dB, self._xB)
+        if kind == "relin":
+            return self._clock(bgv.relin, self._t3, k.rlk)
+        if kind == "rot_D":
+            return self._clock(bgv.rotate, self._xD, self.galois, k.gk[self.galois])
+        return self._clock(bgv.rotate, self._xB, self.galois, k.gk[self.galois])
 
-    def sample_small(self):
-        """One step of the reference arm: one operation of the workload timed (round robin over
-        encrypt of all planes, affine leaf, multiply, rotation, plaintext product; every one
-        timed once first), the inference time extrapolated from the latest time of each with
-        the inference's exact counts -> seconds per inference."""
-        kinds = ("enc", "affine", "mul", "rot", "pt")
-        if not hasattr(self, "_t"):
-            self._t = {kd: self._op(kd) for kd in kinds}
-            self._next = 0
-        else:
-            kd = kinds[self._next % len(kinds)]
-            self._t[kd] = self._op(kd)
-            self._next += 1
-        t, n, m = self._t, self.n, self.m
-        est = t["enc"] + n["affine"] * t["affine"] + n["mul"] * t["mul"] + n["rot"] * t["rot"] + n["pt"] * t["pt"]
-        return est, (f"oracle, one operation of the workload timed per step (round robin over encrypt of "
-                     f"{m.precision} planes, affine leaf, multiply, rotation at the reshuffle level, plaintext "
-                     f"product); one inference extrapolated with its exact counts ({n['affine']} affine, "
-                     f"{n['mul']} multiplies, {n['rot']} rotations, {n['pt']} plaintext products)")
+    def estimate(self):
+        return sum(self.n[kd] * self._t[kd] for kd in self.n)
 
-    def sample_large(self, budget_s):
-        """Encrypt and the whole SecComp, then reshuffle terms while the budget lasts -> s/inference."""
-        Cp, bgv, m = self.Cp, self.bgv, self.m
+    def sample_all(self):
+        """Time every operation kind once -> (seconds per step, description)."""
         t0 = time.perf_counter()
-        X = Cp.encrypt_queries(bgv, self.keys, m, self.qs, 99)
-        t_enc = time.perf_counter() - t0
-        times = {"mul": []}
+        for kd in self.n:
+            self._t[kd] = self._op(kd)
+        return self.estimate(), self.describe(time.perf_counter() - t0)
 
-        class Timed(Cp.BgvEngine):
-            def mul(s_, a, b):
-                s = time.perf_counter()
-                r = Cp.BgvEngine.mul(s_, a, b)
-                times["mul"].append(time.perf_counter() - s)
-                return r
+    def sample_one(self, i):
+        """One step of the reference arm: the i-th operation kind (round robin) timed again."""
+        if not self._t:
+            return self.sample_all()
+        kinds = list(self.n)
+        t0 = time.perf_counter()
+        self._t[kinds[i % len(kinds)]] = self._op(kinds[i % len(kinds)])
+        return self.estimate(), self.describe(time.perf_counter() - t0)
 
-        E = Timed(bgv, self.keys)
-        t1 = time.perf_counter()
-        D = Cp.seccomp(E, X, E.thresholds(m), m.precision)
-        t_sec = time.perf_counter() - t1
-        t_rot, t_pt = [], []
-        for k in self.rs[:2]:
-            r, tr = self._clock(E.rot, D, k)
-            _, tp = self._clock(E.mul_plain, r, self.Rd[k])
-            t_rot.append(tr)
-            t_pt.append(tp)
-            if time.perf_counter() - t0 > budget_s:
-                break
+    def describe(self, cpu_s):
         n = self.n
-        est = (t_enc + t_sec + n["rot"] * statistics.mean(t_rot) + n["pt"] * statistics.mean(t_pt)
-               + (m.d - 1) * statistics.mean(times["mul"]))
-        return est, (f"oracle timed on encrypt ({m.precision} planes), the whole SecComp, {len(t_rot)} rotations and "
-                     f"plaintext products of the reshuffle ({time.perf_counter() - t0:.1f} s of CPU work); one "
-                     f"inference extrapolated with its exact counts ({n['rot']} rotations, {n['pt']} plaintext "
-                     f"products, {m.d - 1} more multiplies): {est:.1f} s/inference")
+        return (f"oracle ({self.B.oracle_threads()} threads) timed on one of each operation of the step at its "
+                f"level ({cpu_s:.1f} s of CPU work: encrypt, ciphertext product at the top and bottom of the chain, "
+                f"tensor with an encrypted diagonal at the reshuffle and level levels, relinearisation, rotation at "
+                f"both levels); one step of {self.W.queries[0]} queries ({self.n_ct} query ciphertexts) extrapolated "
+                f"with its exact counts: {n['enc']} encryptions, {n['mul_hi'] + n['mul_lo']} products, "
+                f"{n['tensor_D'] + n['tensor_B']} tensors, {n['relin']} relinearisations, "
+                f"{n['rot_D'] + n['rot_B']} rotations")
 
 
-def oracle_baseline(W, text, budget_s):
-    est, sample = OracleBench(W, text).sample_large(budget_s)
-    return {"value": 1.0 / est, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+def oracle_baseline_encmodel(W, budget_s):
+    ob = OracleBench(W, W.forest_texts()[0])
+    est, sample = ob.sample_all()
+    return {"value": W.queries[0] / est, "unit": UNIT, "cores": ob.B.oracle_threads(), "kind": "oracle",
+            "sample": sample, "seconds_per_step_extrapolated": est}
 
 
 def run_reference(args, ws, rank):
-    from paper_2104_09583_gb300 import synth
-
     if rank != 0:
         return None
-    W = synth.WORKLOADS[args.workload]
+    W = synth_workload(args.workload)
     ob = OracleBench(W, W.forest_texts()[0])
-    for _ in range(args.warmup):
-        ob.sample_small()
+    for i in range(args.warmup):
+        ob.sample_one(i)
     ests, sample = [], ""
-    for _ in range(args.steps):
-        est, sample = ob.sample_small()
+    for i in range(args.steps):
+        est, sample = ob.sample_one(i)
         ests.append(est)
     est = statistics.mean(ests)
-    value = 1.0 / est
+    value = W.queries[0] / est
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": est * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u64 (RNS residues mod 55-bit primes)",
             "data": "synthetic (seeded random forest and queries)", "config": {"workload": W.name},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "ms_per_step_note": "extrapolated: each reference step times one operation of the workload "
+                                "(round robin) and re-estimates the whole step from the exact operation counts",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": ob.B.oracle_threads(), "kind": "oracle",
+                             "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 

@@ -47,7 +47,7 @@ typedef int copse_status;
 #define COPSE_ENOKEY (-5)   /* a rotation key the model needs is missing        */
 #define COPSE_ELEVEL (-6)   /* the prime chain is too short for the circuit    */
 #define COPSE_EFIT (-7)     /* the model's slot block does not fit a slot row   */
-#define COPSE_EADMIT (-8)   /* the server's request queue is full (admission)  */
+#define COPSE_EADMIT (-8)   /* admission refused: device memory or a full queue */
 #define COPSE_ETIMEOUT (-9) /* a wait ran out before the result was ready      */
 
 /* Ring and RNS parameters.  All primes are = 1 mod 2*N*t and below
@@ -81,6 +81,10 @@ typedef struct copse_model_info {
     uint32_t n_rot_level;     /* nonzero rotation amounts shared by the level products */
     uint32_t levels_used; /* primes the circuit drops: 3 + ceil(log2 p) + ceil(log2 d) (+1 shuffled) */
     uint32_t n_out;       /* result slots per query: n_leaves, or the shuffled and padded length */
+    uint32_t n_segments;  /* row segments: 1, or the number of slot blocks one query spans when the
+                             forest is split into contiguous groups of trees (copse_compile_forest) */
+    uint32_t block_branches; /* branches and leaves one slot block is laid out for: b and */
+    uint32_t block_leaves;   /* n_leaves, or the largest segment's (level matrices: d of L x b) */
 } copse_model_info;
 
 /* Message for the last failed call on this thread (never NULL). */
@@ -107,8 +111,14 @@ copse_status copse_ctx_primes(const copse_ctx *ctx, uint64_t *out, size_t cap, s
  * the level matrices and masks (Section 4.2) for rings of degree 2^log_n.
  * Host only; touches no device.  n_features = 0 takes the largest feature
  * index + 1.  EPARSE on malformed text, EINVAL on a threshold >= 2^precision,
- * a feature >= n_features or a class index out of range, EFIT if the query
- * block exceeds a slot row (N/2). */
+ * a feature >= n_features or a class index out of range.
+ * Row segments: when one query block (a power of two >= L + b + q - 2 slots)
+ * would exceed a slot row (N/2), the trees are split into the smallest power of
+ * two S of contiguous groups (tree t in group floor(S * branches before t /
+ * all branches)) that are compiled alike with a common K and depth, such that
+ * the common block fits a row; query j then owns blocks j S .. j S + S - 1
+ * (block s: group s), N / (S block) queries per ciphertext, and its result bits
+ * are the groups' leaves in order.  EFIT if no such split exists. */
 copse_status copse_compile_forest(const char *text, size_t len, uint32_t precision, uint32_t n_features,
                                   uint32_t log_n, copse_model **out);
 void copse_model_destroy(copse_model *model);
@@ -290,17 +300,24 @@ void copse_session_destroy(copse_session *session);
  * requests into the slot blocks of that model's next launch (continuous
  * batching: requests that arrive while a launch is on the GPU join the next
  * one) and keeps up to two launches per model in flight.  Keys, model
- * plaintexts and the launches' device memory stay resident; device memory is
- * reserved at creation, and a request is admitted only while the pending
- * queue holds fewer than max_pending requests (0 = four times the slot
- * capacity of all in-flight launches).  The server is internally locked. */
+ * plaintexts and the launches' device memory stay resident.  Admission is by
+ * device memory: creation measures each launch's reservation (the drop in free
+ * device memory when its graph is recorded and replayed once), gives a model
+ * its second concurrent launch only while free memory holds another such
+ * reservation plus the admission floor, and fails with COPSE_EADMIT when not
+ * even one launch per model fits.  A request is then admitted only while free
+ * device memory is at least the floor (default: the largest launch
+ * reservation, room for one more launch's working set) and the pending queue
+ * holds fewer than max_pending requests (0 = four times the slot capacity of
+ * all launches).  The server is internally locked. */
 typedef struct copse_server copse_server;
 
 copse_status copse_server_create(copse_ctx *ctx, const copse_keys *keys, const copse_evk *evk,
                                  copse_model *const *models, size_t n_models, size_t max_pending,
                                  copse_server **out);
 /* Queue one query (feats[n_features], host) for models[model_id].  Returns a
- * ticket, or COPSE_EADMIT when the queue is full (nothing queued). */
+ * ticket, or COPSE_EADMIT when free device memory is below the admission floor
+ * or the queue is full (nothing queued). */
 copse_status copse_server_submit(copse_server *server, uint32_t model_id, const uint32_t *feats, uint64_t *ticket);
 /* Wait up to timeout_ms for a ticket: its leaf bits into out_bits[n_leaves]
  * (host) and, if latency_ms is not NULL, the time from submit to completion.
@@ -308,6 +325,15 @@ copse_status copse_server_submit(copse_server *server, uint32_t model_id, const 
  * by the successful poll. */
 copse_status copse_server_poll(copse_server *server, uint64_t ticket, uint8_t *out_bits, int timeout_ms,
                                double *latency_ms);
+/* Device memory of the server: bytes its launches reserved at creation, the
+ * largest single launch's reservation, the current admission floor (free
+ * device bytes a submit requires) and the number of concurrent launches all
+ * models together were given.  Any pointer may be NULL. */
+copse_status copse_server_memory(copse_server *server, size_t *reserved, size_t *launch_max, size_t *floor,
+                                 uint32_t *launches);
+/* Set the admission floor: submits fail with COPSE_EADMIT while free device
+ * memory is below `floor` bytes (0 = admit regardless of memory). */
+copse_status copse_server_set_memory_floor(copse_server *server, size_t floor);
 /* Requests waiting for a launch, and requests in launches on the GPU. */
 copse_status copse_server_pending(copse_server *server, size_t *queued, size_t *in_flight);
 /* Stops the worker after the launches in flight and frees everything. */
@@ -367,8 +393,9 @@ copse_status copse_poly_mul(copse_ctx *ctx, const uint64_t *a, const uint64_t *b
  * copse_poly_mul).  The two transform buffers are a fixed device array of
  * 2 x 2^18 words (4 MiB) that every GPU loading this library holds until the
  * process exits; n_res * N above 2^18 words fails with COPSE_EINVAL.  The
- * first call on a device looks up the array's device address (the context's
- * device must be current); make that first call before any stream capture.
+ * context's device must be current on every call (COPSE_EINVAL otherwise).
+ * The first call on a device looks up the array's device address; make that
+ * first call before any stream capture.
  * All calls on a device share the array: calls that overlap on the GPU race,
  * so order them on one stream.  Async. */
 copse_status copse_poly_mul_noalloc(copse_ctx *ctx, const uint64_t *a, const uint64_t *b, uint64_t *c,
@@ -438,8 +465,26 @@ copse_status copse_stats_reset(void);
 /* Wait for the device; totals of family `name` (NULL or "" = all families):
  * launches, summed event time in milliseconds, algorithmic bytes. */
 copse_status copse_stats_get(const char *name, uint64_t *launches, double *ms, double *bytes);
+/* Wait for the device; algorithmic modular products of family `name` (NULL or
+ * "" = all families): the 64-bit residue products the launches' method needs
+ * (a ciphertext tensor counts 4 per element), the unit of the integer roof. */
+copse_status copse_stats_get_ops(const char *name, double *ops);
 /* Newline-separated family names seen so far into buf[cap]. */
 copse_status copse_stats_names(char *buf, size_t cap);
+
+/* ---------------------------------------------------------------- integer peaks
+ * The roofline of integer kernels needs a measured rate of the modular
+ * arithmetic they are made of, not a spec-sheet figure.  Register-only
+ * microbenchmarks on the context's device, CUDA-event timed, best of `reps`
+ * runs after one warm-up run:
+ *   kind 0: exact products x*y of residues below 2^55 added to a lazily reduced
+ *           sum (split 28-bit multiply-adds), the unit of the dot-product kernels;
+ *   kind 1: lazy forward NTT butterflies with a constant twiddle (Shoup/Harvey);
+ *   kind 2: Barrett products of two residues, fully reduced.
+ * *ops_per_s: products (kind 0, 2) or butterflies (kind 1) per second over the
+ * whole device; *best_ms (may be NULL) the best run.  Allocates a small sink
+ * buffer; synchronous.  EINVAL on a bad kind or reps < 1. */
+copse_status copse_measure_int_peak(copse_ctx *ctx, int kind, int reps, double *ops_per_s, float *best_ms);
 
 #ifdef __cplusplus
 }

@@ -35,7 +35,7 @@ def build(force: bool = False) -> str:
     os.makedirs(_LIB_DIR, exist_ok=True)
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", _SRC, "-o", tmp])
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", _SRC, "-o", tmp])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -58,6 +58,7 @@ def lib():
         P = C.POINTER(_Params)
         sig = {
             "or_is_prime": (C.c_int, [C.c_uint64]),
+            "or_threads": (C.c_int, []),
             "or_find_primes": (C.c_int, [C.c_int, C.c_uint64, C.c_int, C.c_int, u64p]),
             "or_root_2n": (C.c_uint64, [C.c_uint64, C.c_int]),
             "or_mulmod": (C.c_uint64, [C.c_uint64, C.c_uint64, C.c_uint64]),
@@ -100,6 +101,11 @@ def lib():
             f.argtypes = args
         _lib = L
     return _lib
+
+
+def oracle_threads() -> int:
+    """Threads the oracle's C loops use (OpenMP; OMP_NUM_THREADS, default all host cores)."""
+    return int(lib().or_threads())
 
 
 # ---------------------------------------------------------------------------

@@ -29,6 +29,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 typedef uint64_t u64;
 typedef int64_t i64;
@@ -76,6 +79,18 @@ static i64 centred(u64 x, u64 q) { return x > (q - 1) / 2 ? (i64)x - (i64)q : (i
 
 u64 or_mulmod(u64 a, u64 b, u64 q) { return mulmod(a, b, q); }
 u64 or_powmod(u64 a, u64 e, u64 q) { return powmod(a, e, q); }
+
+/* Threads the oracle's loops over residues and coefficients run on (OpenMP when
+ * built with it; every thread computes whole, independent residues or
+ * coefficients, so results do not depend on the count). */
+int or_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
 
 /* Deterministic Miller-Rabin for 64-bit inputs (first twelve prime bases). */
 int or_is_prime(u64 n)
@@ -358,11 +373,12 @@ void or_keygen_switch(const or_params *P, u64 seed, u64 sb, const i64 *s, const 
 {
     int N = P->N, L = P->L, nb = P->L + P->alpha;
     i64 *e = malloc(sizeof(i64) * N);
-    u64 *a = malloc(sizeof(u64) * N), *sr = malloc(sizeof(u64) * N), *as = malloc(sizeof(u64) * N);
     for (int j = 0; j < P->ndig; j++) {
         or_sample_cbd(seed, sb + 2 * j + 1, N, e);
         int lo = j * P->alpha, hi = (j + 1) * P->alpha < L ? (j + 1) * P->alpha : L;
+#pragma omp parallel for schedule(dynamic)
         for (int r = 0; r < nb; r++) {
+            u64 *a = malloc(sizeof(u64) * N), *sr = malloc(sizeof(u64) * N), *as = malloc(sizeof(u64) * N);
             u64 q = P->primes[r];
             u64 Pmod = 1;
             for (int k = 0; k < P->alpha; k++) Pmod = mulmod(Pmod, P->primes[L + k] % q, q);
@@ -378,9 +394,10 @@ void or_keygen_switch(const or_params *P, u64 seed, u64 sb, const i64 *s, const 
                 k0[x] = v;
                 k1[x] = a[x];
             }
+            free(a); free(sr); free(as);
         }
     }
-    free(e); free(a); free(sr); free(as);
+    free(e);
 }
 
 /* Encrypt centred plaintext coefficients m at the top level L:
@@ -390,21 +407,23 @@ void or_encrypt(const or_params *P, const u64 *pk, const i64 *m, u64 seed, u64 s
 {
     int N = P->N, L = P->L;
     i64 *u = malloc(sizeof(i64) * N), *e0 = malloc(sizeof(i64) * N), *e1 = malloc(sizeof(i64) * N);
-    u64 *ur = malloc(sizeof(u64) * N), *p0u = malloc(sizeof(u64) * N), *p1u = malloc(sizeof(u64) * N);
     or_sample_ternary(seed, sb, N, u);
     or_sample_cbd(seed, sb + 1, N, e0);
     or_sample_cbd(seed, sb + 2, N, e1);
+#pragma omp parallel for schedule(dynamic)
     for (int r = 0; r < L; r++) {
         u64 q = P->primes[r], tq = P->t % q;
-        for (int j = 0; j < N; j++) ur[j] = from_signed(u[j], q);
-        or_negacyclic_mul(pk + (size_t)r * N, ur, P->logN, q, p0u);
-        or_negacyclic_mul(pk + (size_t)(L + r) * N, ur, P->logN, q, p1u);
+        u64 *urr = malloc(sizeof(u64) * N), *p0 = malloc(sizeof(u64) * N), *p1 = malloc(sizeof(u64) * N);
+        for (int j = 0; j < N; j++) urr[j] = from_signed(u[j], q);
+        or_negacyclic_mul(pk + (size_t)r * N, urr, P->logN, q, p0);
+        or_negacyclic_mul(pk + (size_t)(L + r) * N, urr, P->logN, q, p1);
         for (int j = 0; j < N; j++) {
-            ct[(size_t)r * N + j] = addmod(addmod(p0u[j], mulmod(tq, from_signed(e0[j], q), q), q), from_signed(m[j], q), q);
-            ct[(size_t)(L + r) * N + j] = addmod(p1u[j], mulmod(tq, from_signed(e1[j], q), q), q);
+            ct[(size_t)r * N + j] = addmod(addmod(p0[j], mulmod(tq, from_signed(e0[j], q), q), q), from_signed(m[j], q), q);
+            ct[(size_t)(L + r) * N + j] = addmod(p1[j], mulmod(tq, from_signed(e1[j], q), q), q);
         }
+        free(urr); free(p0); free(p1);
     }
-    free(u); free(e0); free(e1); free(ur); free(p0u); free(p1u);
+    free(u); free(e0); free(e1);
 }
 
 /* Secret-key encryption at level ell (the model owner holds the secret key
@@ -417,9 +436,10 @@ void or_encrypt_sk(const or_params *P, const i64 *s, const i64 *m, u64 seed, u64
 {
     int N = P->N;
     i64 *e = malloc(sizeof(i64) * N);
-    u64 *a = malloc(sizeof(u64) * N), *sr = malloc(sizeof(u64) * N), *as = malloc(sizeof(u64) * N);
     or_sample_cbd(seed, sb + 1, N, e);
+#pragma omp parallel for schedule(dynamic)
     for (int r = 0; r < ell; r++) {
+        u64 *a = malloc(sizeof(u64) * N), *sr = malloc(sizeof(u64) * N), *as = malloc(sizeof(u64) * N);
         u64 q = P->primes[r], tq = P->t % q;
         for (int j = 0; j < N; j++) a[j] = uniform_residue(seed, sb, N, r, j, q);
         or_ntt_inv(a, P->logN, q, or_root_2n(q, P->logN));
@@ -430,8 +450,9 @@ void or_encrypt_sk(const or_params *P, const i64 *s, const i64 *m, u64 seed, u64
             ct[(size_t)r * N + j] = submod(v, as[j], q);
             ct[(size_t)(ell + r) * N + j] = a[j];
         }
+        free(a); free(sr); free(as);
     }
-    free(e); free(a); free(sr); free(as);
+    free(e);
 }
 
 /* [c0 + c1*s] mod q_r for r < ell (no reduction mod t): used for noise measurement */
@@ -455,6 +476,7 @@ void or_modswitch(const or_params *P, const u64 *ct, int ncomp, int ell, u64 *ou
 {
     int N = P->N;
     u64 ql = P->primes[ell - 1], tinv = invmod(P->t % ql, ql);
+#pragma omp parallel for collapse(2) schedule(static)
     for (int c = 0; c < ncomp; c++)
         for (int j = 0; j < N; j++) {
             i64 w = centred(mulmod(ct[((size_t)c * ell + ell - 1) * N + j], tinv, ql), ql);
@@ -475,6 +497,7 @@ static void modup_digit(const or_params *P, const u64 *x, int ell, int j, u64 *y
 {
     int N = P->N, nx = ell + P->alpha;
     int lo = j * P->alpha, hi = (j + 1) * P->alpha < ell ? (j + 1) * P->alpha : ell;
+#pragma omp parallel for schedule(static)
     for (int n = 0; n < N; n++) {
         i64 yc[OR_MAXP];
         for (int i = lo; i < hi; i++) {
@@ -503,6 +526,7 @@ static void modup_digit(const or_params *P, const u64 *x, int ell, int j, u64 *y
 static void moddown(const or_params *P, const u64 *u, int ell, u64 *out)
 {
     int N = P->N, A = P->alpha, L = P->L;
+#pragma omp parallel for schedule(static)
     for (int n = 0; n < N; n++) {
         i64 yc[OR_MAXP];
         for (int k = 0; k < A; k++) {
@@ -537,6 +561,7 @@ static void keyswitch_raw(const or_params *P, const u64 *x, int ell, const u64 *
     memset(acc, 0, sizeof(u64) * 2 * nx * N);
     for (int j = 0; j < nd; j++) {
         modup_digit(P, x, ell, j, y);
+#pragma omp parallel for collapse(2) schedule(dynamic)
         for (int c = 0; c < 2; c++)
             for (int r = 0; r < nx; r++) {
                 int g = ext_prime(P, ell, r);
@@ -600,12 +625,15 @@ void or_matmul(const or_params *P, const u64 *ct, int ell, int nrot, const u64 *
         for (int a = 0; a < nacc; a++) {
             if (!present[a * nrot + k]) continue;
             const i64 *m = pts + ((size_t)a * nrot + k) * N;
+#pragma omp parallel for collapse(2) schedule(dynamic)
             for (int c = 0; c < 2; c++)
                 for (int r = 0; r < nx; r++) {
                     int gi = ext_prime(P, ell, r);
                     u64 q = P->primes[gi];
-                    for (int j = 0; j < N; j++) pr[j] = from_signed(m[j], q);
-                    poly_mul_acc(R + ((size_t)c * nx + r) * N, pr, P->logN, q, acc + (((size_t)a * 2 + c) * nx + r) * N);
+                    u64 *prr = malloc(sizeof(u64) * N);
+                    for (int j = 0; j < N; j++) prr[j] = from_signed(m[j], q);
+                    poly_mul_acc(R + ((size_t)c * nx + r) * N, prr, P->logN, q, acc + (((size_t)a * 2 + c) * nx + r) * N);
+                    free(prr);
                 }
         }
     }
@@ -691,6 +719,7 @@ void or_tensor(const or_params *P, const u64 *a, const u64 *b, int ell, u64 *out
 {
     int N = P->N;
     memset(out, 0, sizeof(u64) * 3 * ell * N);
+#pragma omp parallel for schedule(dynamic)
     for (int r = 0; r < ell; r++) {
         u64 q = P->primes[r];
         const u64 *a0 = a + (size_t)r * N, *a1 = a + (size_t)(ell + r) * N;
@@ -733,6 +762,7 @@ static void moddown_drop(const or_params *P, const u64 *u, int ell, u64 *out)
     bp[0] = P->primes[ell - 1];
     bres[0] = ell - 1;
     for (int k = 1; k < nb; k++) { bp[k] = P->primes[L + k - 1]; bres[k] = ell + k - 1; }
+#pragma omp parallel for schedule(static)
     for (int n = 0; n < N; n++) {
         i64 yc[OR_MAXP];
         for (int k = 0; k < nb; k++) {

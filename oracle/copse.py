@@ -106,6 +106,15 @@ class Model:
     mask: list                     # level masks, length L, k = 1..d
     block: int = 0                 # slots per query block
     extras: dict = field(default_factory=dict)
+    # Row segments (a layout reading of this implementation, not of the paper): a forest
+    # whose query block would not fit a slot row is split into n_seg contiguous groups of
+    # trees, each compiled alike with a common K, q and d; query j then owns blocks
+    # j*n_seg .. j*n_seg + n_seg - 1, block s holding segment s.  b and L are then the
+    # largest segment's (the block layout); b_total and L_total count the whole forest.
+    n_seg: int = 1
+    segs: list = None
+    b_total: int = 0
+    L_total: int = 0
 
     @property
     def m1(self):                  # rows of the extended reshuffle: L + b - 1
@@ -116,8 +125,84 @@ class Model:
         return self.m1 + self.q - 1
 
 
+def _branches(n) -> int:
+    return 0 if n.leaf else 1 + _branches(n.left) + _branches(n.right)
+
+
 def compile_forest(text: str, precision: int, n_features: int = 0, slots_per_row: int = 0) -> Model:
+    """Compile a forest (Sections 4.1-4.2).  With slots_per_row (= N/2) given, a forest whose
+    query block would exceed a slot row is compiled in row segments: the smallest power of
+    two S such that, with tree t in group floor(S * (branches of the trees before t) /
+    (all branches)), no group is empty and the common block fits a row (and S blocks fit
+    the ring)."""
     labels, trees = parse_forest(text)
+    if any(t < 0 or t >= (1 << precision) for t in _thresholds(trees)):
+        raise ValueError("threshold out of range for the precision")
+    feats = _features(trees)
+    if not feats:
+        raise ValueError("forest has no branches")
+    nf = n_features if n_features else max(feats) + 1
+    m = _build(trees, precision, nf)
+    m.b_total, m.L_total = m.b, m.L
+    if not slots_per_row or m.block <= slots_per_row:
+        if slots_per_row and m.block > slots_per_row:
+            raise ValueError("model does not fit one slot row")
+        return m
+    counts = [_branches(t) for t in trees]
+    total = sum(counts)
+    S = 2
+    while S <= min(64, len(trees)):
+        before = np.concatenate([[0], np.cumsum(counts)[:-1]])
+        gi = [min(S - 1, (S * int(b)) // total) for b in before]
+        groups = [[t for t, g in zip(trees, gi) if g == k] for k in range(S)]
+        if all(groups):
+            first = [_build(g, precision, nf) for g in groups]
+            K, d = max(x.K for x in first), max(x.d for x in first)
+            segs = [_build(g, precision, nf, K, d) for g in groups]
+            bp, Lp = max(x.b for x in segs), max(x.L for x in segs)
+            need = Lp + bp - 1 + K * nf - 1
+            blk = 1
+            while blk < need:
+                blk <<= 1
+            if blk <= slots_per_row and S * blk <= 2 * slots_per_row:
+                for x in segs:
+                    x.block = blk
+                    x.b_total, x.L_total = x.b, x.L
+                return Model(nf, precision, m.labels_per_leaf, m.br_feature, m.br_threshold, m.br_level, K, K * nf,
+                             bp, Lp, d, None, None, None, None, None, blk, n_seg=S, segs=segs,
+                             b_total=m.b, L_total=m.L)
+        S *= 2
+    raise ValueError("model does not fit one slot row")
+
+
+def _thresholds(trees):
+    out = []
+
+    def walk(n):
+        if not n.leaf:
+            out.append(n.threshold)
+            walk(n.left)
+            walk(n.right)
+    for t in trees:
+        walk(t)
+    return out
+
+
+def _features(trees):
+    out = []
+
+    def walk(n):
+        if not n.leaf:
+            out.append(n.feature)
+            walk(n.left)
+            walk(n.right)
+    for t in trees:
+        walk(t)
+    return out
+
+
+def _build(trees, precision: int, nf: int, K_min: int = 0, d_min: int = 0) -> Model:
+    """Sections 4.1.1-4.2.4 for a list of trees: K at least K_min, levels 1..max(d, d_min)."""
     # Section 4.1.1: branches and leaves indexed in preorder, continuing across trees.
     br_f, br_t, br_lvl, leaf_cls = [], [], [], []
     leaf_anc = []   # per leaf: list of (branch index, leaf is under its true child)
@@ -142,15 +227,12 @@ def compile_forest(text: str, precision: int, n_features: int = 0, slots_per_row
     b = len(br_f)
     if b == 0:
         raise ValueError("forest has no branches")
-    if any(t < 0 or t >= (1 << precision) for t in br_t):
-        raise ValueError("threshold out of range for the precision")
-    nf = n_features if n_features else max(br_f) + 1
     if max(br_f) >= nf or min(br_f) < 0:
         raise ValueError("feature index out of range")
-    L, d = len(leaf_cls), max(br_lvl)
+    L, d = len(leaf_cls), max(max(br_lvl), d_min)
     # Section 4.1.1: multiplicity, maximum multiplicity K, quantised branching q = K * n_features.
     kappa = [br_f.count(f) for f in range(nf)]
-    K = max(kappa)
+    K = max(max(kappa), K_min)
     q = K * nf
     # Section 4.2.1: thresholds grouped by feature, each group padded to K with S = 0.
     # Reading: within a group, branches keep their preorder order.
@@ -197,8 +279,6 @@ def compile_forest(text: str, precision: int, n_features: int = 0, slots_per_row
     while blk < need:
         blk <<= 1
     m.block = blk
-    if slots_per_row and blk > slots_per_row:
-        raise ValueError("model does not fit one slot row")
     return m
 
 
@@ -209,9 +289,16 @@ def compile_forest(text: str, precision: int, n_features: int = 0, slots_per_row
 # rotations by up to q-1 and b-1 stay inside the block (the cyclic extension
 # of the diagonal method, Section 4.1.2).
 # ---------------------------------------------------------------------------
+def parts(m: Model):
+    """The compiled forests whose blocks make up one query's slots: the model itself, or
+    its row segments in order."""
+    return m.segs if m.n_seg > 1 else [m]
+
+
 def feature_planes(m: Model, queries, N: int):
-    """p bit-planes (Section 4.1.2) of the replicated feature vectors."""
-    nb = N // m.block
+    """p bit-planes (Section 4.1.2) of the replicated feature vectors; query j's features
+    fill each of its blocks j*n_seg + s."""
+    nb = N // (m.block * m.n_seg)
     if len(queries) > nb:
         raise ValueError("too many queries for one ciphertext")
     planes = np.zeros((m.precision, N), dtype=np.int64)
@@ -220,21 +307,26 @@ def feature_planes(m: Model, queries, N: int):
     for j, x in enumerate(queries):
         x = np.asarray(x, dtype=np.int64)
         vals = x[feat_of]
-        for i in range(m.precision):
-            planes[i, j * m.block + pos] = (vals >> i) & 1
+        for s in range(m.n_seg):
+            for i in range(m.precision):
+                planes[i, (j * m.n_seg + s) * m.block + pos] = (vals >> i) & 1
     return planes
 
 
 def tile_blocks(m: Model, block_vec, N: int):
-    """Repeat a per-block slot pattern (length <= block) in every block."""
-    v = np.zeros(m.block, dtype=np.int64)
-    v[: len(block_vec)] = block_vec
-    return np.tile(v, N // m.block)
+    """Repeat a per-block slot pattern (length <= block) in every block.  For a model in row
+    segments the pattern is an array [n_seg, length]: row s goes to every block of segment s."""
+    v = np.asarray(block_vec, dtype=np.int64)
+    if v.ndim == 1:
+        v = np.broadcast_to(v, (m.n_seg, v.shape[0]))
+    blk = np.zeros((m.n_seg, m.block), dtype=np.int64)
+    blk[:, : v.shape[1]] = v
+    return np.tile(blk.reshape(-1), N // (m.block * m.n_seg))
 
 
 def threshold_planes(m: Model, N: int):
     pos = np.arange(m.pd)
-    vals = np.asarray(m.thr_slot, dtype=np.int64)[pos % m.q]
+    vals = np.stack([np.asarray(sg.thr_slot, dtype=np.int64)[pos % m.q] for sg in parts(m)])
     return np.stack([tile_blocks(m, (vals >> i) & 1, N) for i in range(m.precision)])
 
 
@@ -246,13 +338,46 @@ def generalized_diagonal(M: np.ndarray, i: int, rows: int) -> np.ndarray:
     return M[j % m, (j + i) % n]
 
 
+def _padded(M: np.ndarray, rows: int, cols: int) -> np.ndarray:
+    """A segment's matrix inside the common block layout: zero rows and columns appended."""
+    out = np.zeros((rows, cols), dtype=np.int64)
+    out[: M.shape[0], : M.shape[1]] = M
+    return out
+
+
+def reshuffle_diagonal(m: Model, i: int) -> np.ndarray:
+    """Diagonal i of the extended reshuffle R_ext (rows L+b-1, row j = R[j mod b]); for a model
+    in row segments an array [n_seg, L+b-1], segment s's R padded to b rows."""
+    if m.n_seg == 1:
+        return generalized_diagonal(m.R, i, m.m1)
+    return np.stack([generalized_diagonal(_padded(sg.R, m.b, m.q), i, m.m1) for sg in m.segs])
+
+
+def level_diagonal(m: Model, k: int, i: int, t: int) -> np.ndarray:
+    """Signed diagonal i of level k: (1 - 2 Mask_k) * d_i(Lvl_k), values in {0,1,t-1}; per
+    segment (array [n_seg, L]) for a model in row segments, each level matrix padded to
+    L x b with zeros."""
+    if m.n_seg == 1:
+        return ((1 - 2 * m.mask[k - 1]) * generalized_diagonal(m.lvl[k - 1], i, m.L)) % t
+    return np.stack([((1 - 2 * _padded(sg.mask[k - 1][:, None], m.L, 1)[:, 0]) *
+                      generalized_diagonal(_padded(sg.lvl[k - 1], m.L, m.b), i, m.L)) % t
+                     * (np.arange(m.L) < sg.L) for sg in m.segs])
+
+
+def mask_vector(m: Model, k: int) -> np.ndarray:
+    """Mask_k as a block pattern ([n_seg, L] for row segments, zero past a segment's leaves)."""
+    if m.n_seg == 1:
+        return m.mask[k - 1]
+    return np.stack([_padded(sg.mask[k - 1][:, None], m.L, 1)[:, 0] for sg in m.segs])
+
+
 def reshuffle_diagonals(m: Model):
     """Nonzero diagonals of the extended reshuffle R_ext (rows L+b-1, row j = R[j mod b]):
     multiplying by it leaves the branch vector repeated with period b, ready for
     the level products without further rotation."""
     out = {}
     for i in range(m.q):
-        dg = generalized_diagonal(m.R, i, m.m1)
+        dg = reshuffle_diagonal(m, i)
         if dg.any():
             out[i] = dg
     return out
@@ -263,11 +388,10 @@ def level_diagonals(m: Model, k: int, t: int):
     adding Mask_k afterwards computes Lvl_k * Branches XOR Mask_k (Section 4.2.4)
     as m + (1-2m) z."""
     out = {}
-    sgn = 1 - 2 * m.mask[k - 1]
     for i in range(m.b):
-        dg = generalized_diagonal(m.lvl[k - 1], i, m.L)
+        dg = level_diagonal(m, k, i, t)
         if dg.any():
-            out[i] = (sgn * dg) % t
+            out[i] = dg
     return out
 
 
@@ -283,9 +407,9 @@ def bsgs_split(diags: dict, g: int, block: int):
     for i in sorted(diags):
         k, j = divmod(i, g)
         d = np.asarray(diags[i])
-        assert k * g + len(d) <= block, "shifted diagonal leaves the block"
-        sh = np.zeros(k * g + len(d), dtype=np.int64)
-        sh[k * g:] = d
+        assert k * g + d.shape[-1] <= block, "shifted diagonal leaves the block"
+        sh = np.zeros(d.shape[:-1] + (k * g + d.shape[-1],), dtype=np.int64)
+        sh[..., k * g:] = d
         out.setdefault(k * g, {})[j] = sh
     return out
 
@@ -393,7 +517,7 @@ def infer(E, m: Model, X, N: int, g=(0, 0), shuffle=None):
     else:
         Br = matmul(E, D, [reshuffle_diagonals(m)], [None], m, N, g[0])[0]
         Ld = [level_diagonals(m, k, t) for k in range(1, m.d + 1)]
-        res = matmul(E, Br, Ld, [tile_blocks(m, m.mask[k - 1], N) for k in range(1, m.d + 1)], m, N, g[1])
+        res = matmul(E, Br, Ld, [tile_blocks(m, mask_vector(m, k), N) for k in range(1, m.d + 1)], m, N, g[1])
     out = pairwise(res, lambda a, b, root: E.mul(a, b))
     if shuffle is not None:
         out = matmul(E, out, [shuffle_diagonals(m, shuffle, N)], [None], m, N)[0]
@@ -460,20 +584,20 @@ def encrypt_model(bgv: B.Bgv, sk, m: Model, N: int, seed: int, g=(0, 0)):
 
     def shifted(d, i, gg):
         kg = i - i % gg if gg else 0
-        v = np.zeros(kg + len(d), dtype=np.int64)
-        v[kg:] = d
+        d = np.asarray(d)
+        v = np.zeros(d.shape[:-1] + (kg + d.shape[-1],), dtype=np.int64)
+        v[..., kg:] = d
         return v
 
     thr = [enc(y, model_ct_index(m, "thr", i=i), P.L) for i, y in enumerate(threshold_planes(m, N))]
-    R = {i: enc(tile_blocks(m, shifted(generalized_diagonal(m.R, i, m.m1), i, g[0]), N),
+    R = {i: enc(tile_blocks(m, shifted(reshuffle_diagonal(m, i), i, g[0]), N),
                 model_ct_index(m, "R", i=i), lvl_D) for i in range(m.q)}
     levels, masks = [], []
     for k in range(1, m.d + 1):
-        sgn = 1 - 2 * m.mask[k - 1]
-        levels.append({i: enc(tile_blocks(m, shifted((sgn * generalized_diagonal(m.lvl[k - 1], i, m.L)) % P.t,
-                                                     i, g[1]), N), model_ct_index(m, "lvl", k, i), lvl_B)
+        levels.append({i: enc(tile_blocks(m, shifted(level_diagonal(m, k, i, P.t), i, g[1]), N),
+                              model_ct_index(m, "lvl", k, i), lvl_B)
                        for i in range(m.b)})
-        masks.append(enc(tile_blocks(m, m.mask[k - 1], N), model_ct_index(m, "mask", k), lvl_B))
+        masks.append(enc(tile_blocks(m, mask_vector(m, k), N), model_ct_index(m, "mask", k), lvl_B))
     return {"thresholds": thr, "R": R, "levels": levels, "masks": masks, "g": tuple(g)}
 
 
@@ -665,10 +789,14 @@ def encrypt_queries(bgv: B.Bgv, keys: B.Keys, m: Model, queries, seed: int, inde
 def decode_labels(m: Model, slots, n_queries: int, n_out: int = 0):
     """Result slots -> per query, one bit per leaf (Section 4.1.2, Classification Result);
     n_out output slots per query when the result was shuffled and padded."""
-    n_out = n_out or m.L
     out = []
     for j in range(n_queries):
-        v = np.asarray(slots[j * m.block: j * m.block + n_out], dtype=np.int64)
+        if m.n_seg > 1:
+            v = np.concatenate([np.asarray(slots[(j * m.n_seg + s) * m.block: (j * m.n_seg + s) * m.block + sg.L],
+                                           dtype=np.int64) for s, sg in enumerate(m.segs)])
+        else:
+            n = n_out or m.L
+            v = np.asarray(slots[j * m.block: j * m.block + n], dtype=np.int64)
         out.append(v.tolist())
     return out
 

@@ -41,7 +41,8 @@ class copse_params(C.Structure):
 class copse_model_info(C.Structure):
     _fields_ = [(n, C.c_uint32) for n in (
         "n_features", "precision", "K", "q", "b", "n_leaves", "depth", "n_trees", "n_classes", "block",
-        "n_rot_reshuffle", "n_rot_level", "levels_used", "n_out")]
+        "n_rot_reshuffle", "n_rot_level", "levels_used", "n_out", "n_segments", "block_branches",
+        "block_leaves")]
 
 
 vp = C.c_void_p
@@ -106,6 +107,8 @@ _SIG = {
     "copse_stats_reset": (C.c_int, []),
     "copse_stats_get": (C.c_int, [C.c_char_p, C.POINTER(C.c_uint64), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "copse_stats_names": (C.c_int, [C.c_char_p, C.c_size_t]),
+    "copse_stats_get_ops": (C.c_int, [C.c_char_p, C.POINTER(C.c_double)]),
+    "copse_measure_int_peak": (C.c_int, [vp, C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_float)]),
 }
 for _n, (_r, _a) in _SIG.items():
     _f = getattr(_lib, _n)
@@ -352,13 +355,17 @@ def copse_infer_timed(ctx, evk, model, feats, stream=None):
     return h, dict(zip(STAGES, (float(v) for v in ms)))
 
 
-def copse_decrypt_labels(ctx, keys, model, result, n_queries, stream=None, out_device_ptr=None):
+def copse_decrypt_labels(ctx, keys, model, result, n_queries, stream=None, out_device_ptr=None, out=None):
+    """Leaf bits [n_queries, n_out]: into device memory at out_device_ptr (async), else into the
+    host array `out` (e.g. pinned memory; uint8, at least n_queries * n_out) or a new array."""
     if out_device_ptr is not None:
         _check(_lib.copse_decrypt_labels(ctx, keys, model, result, C.c_void_p(out_device_ptr), n_queries, 1,
                                          C.c_void_p(stream)))
         return None
     L = copse_model_info_get(model)["n_out"]
-    out = np.zeros(max(n_queries * L, 1), np.uint8)
+    if out is None:
+        out = np.zeros(max(n_queries * L, 1), np.uint8)
+    out = out.reshape(-1)
     _check(_lib.copse_decrypt_labels(ctx, keys, model, result, _ptr(out), n_queries, 0, C.c_void_p(stream)))
     return out[: n_queries * L].reshape(n_queries, L)
 
@@ -450,6 +457,23 @@ def copse_stats_get(name=None):
     return {"launches": n.value, "ms": ms.value, "bytes": by.value}
 
 
+def copse_stats_get_ops(name=None):
+    v = C.c_double()
+    _check(_lib.copse_stats_get_ops(name.encode() if name else None, C.byref(v)))
+    return v.value
+
+
+INT_PEAK_KINDS = {"mac": 0, "butterfly": 1, "barrett": 2}
+
+
+def copse_measure_int_peak(ctx, kind, reps=5):
+    """Measured device rate of one kind of modular arithmetic ("mac", "butterfly",
+    "barrett"): (operations per second, best run in ms)."""
+    ops, ms = C.c_double(), C.c_float()
+    _check(_lib.copse_measure_int_peak(ctx, INT_PEAK_KINDS[kind], reps, C.byref(ops), C.byref(ms)))
+    return ops.value, ms.value
+
+
 def copse_stats_names():
     buf = C.create_string_buffer(4096)
     _check(_lib.copse_stats_names(buf, 4096))
@@ -532,6 +556,11 @@ _lib.copse_server_pending.restype = C.c_int
 _lib.copse_server_pending.argtypes = [vp, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)]
 _lib.copse_server_destroy.restype = None
 _lib.copse_server_destroy.argtypes = [vp]
+_lib.copse_server_memory.restype = C.c_int
+_lib.copse_server_memory.argtypes = [vp, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t), C.POINTER(C.c_size_t),
+                                     C.POINTER(C.c_uint32)]
+_lib.copse_server_set_memory_floor.restype = C.c_int
+_lib.copse_server_set_memory_floor.argtypes = [vp, C.c_size_t]
 
 
 def copse_server_create(ctx, keys, evk, models, max_pending=0):
@@ -553,6 +582,17 @@ def copse_server_poll(server, ticket, n_leaves, timeout_ms=10000):
     lat = C.c_double()
     _check(_lib.copse_server_poll(server, ticket, out, timeout_ms, C.byref(lat)))
     return out, lat.value
+
+
+def copse_server_memory(server):
+    """(reserved bytes, largest launch bytes, admission floor bytes, concurrent launches)."""
+    a, b, c, n = C.c_size_t(), C.c_size_t(), C.c_size_t(), C.c_uint32()
+    _check(_lib.copse_server_memory(server, C.byref(a), C.byref(b), C.byref(c), C.byref(n)))
+    return a.value, b.value, c.value, n.value
+
+
+def copse_server_set_memory_floor(server, floor):
+    _check(_lib.copse_server_set_memory_floor(server, floor))
 
 
 def copse_server_pending(server):

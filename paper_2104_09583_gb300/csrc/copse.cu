@@ -104,6 +104,7 @@ static copse_status upload_model(copse_ctx *c, copse_model *m, cudaStream_t s) {
     D->ctx = c;
     D->ctx_serial = c->serial;
     const int N = c->N, L = c->L, A = c->alpha, p = (int)f.precision, B = (int)f.block;
+    const int SP = (int)f.span(), NS = (int)f.n_seg;  // slot patterns cover the n_seg blocks of a query
     D->lvl_D = L - 1 - (int)clog2u(f.precision);
     D->lvl_B = D->lvl_D - 1;
     const u64 t = c->t;
@@ -122,17 +123,17 @@ static copse_status upload_model(copse_ctx *c, copse_model *m, cudaStream_t s) {
     u64 *cur = D->store;
     // SecComp leaf plaintexts over whole blocks (threshold bit 0 past the decisions)
     {
-        std::vector<uint32_t> pat(nleaf * B);
+        std::vector<uint32_t> pat(nleaf * SP);
         for (int i = 0; i < p; i++) {
-            for (int x = 0; x < B; x++) {
-                uint32_t y = x < (int)f.pd() ? (f.thr_slot[x % f.q] >> i) & 1u : 0u;
-                pat[(0 * p + i) * (size_t)B + x] = y ? (uint32_t)(t - 1) : 0;    // lt: x * (-y) + y
-                pat[(1 * p + i) * (size_t)B + x] = y;
-                pat[(2 * p + i) * (size_t)B + x] = y ? 1u : (uint32_t)(t - 1);   // eq: x * (2y - 1) + (1 - y)
-                pat[(3 * p + i) * (size_t)B + x] = y ? 0u : 1u;
+            for (int x = 0; x < SP; x++) {
+                const uint32_t y = f.thr_bit((uint32_t)(x / B), (uint32_t)(x % B), (uint32_t)i);
+                pat[(0 * p + i) * (size_t)SP + x] = y ? (uint32_t)(t - 1) : 0;    // lt: x * (-y) + y
+                pat[(1 * p + i) * (size_t)SP + x] = y;
+                pat[(2 * p + i) * (size_t)SP + x] = y ? 1u : (uint32_t)(t - 1);   // eq: x * (2y - 1) + (1 - y)
+                pat[(3 * p + i) * (size_t)SP + x] = y ? 0u : 1u;
             }
         }
-        STATUS_TRY(encode_patterns(c, pat, (int)nleaf, B, B, L, 0, cur, s));
+        STATUS_TRY(encode_patterns(c, pat, (int)nleaf, SP, SP, L, 0, cur, s));
         for (int i = 0; i < p; i++) {
             D->lt_mul.push_back(cur + ((size_t)(0 * p + i) * L) * N);
             D->lt_add.push_back(cur + ((size_t)(1 * p + i) * L) * N);
@@ -145,7 +146,7 @@ static copse_status upload_model(copse_ctx *c, copse_model *m, cudaStream_t s) {
     // before the key switch's ModDown): diagonal giant + baby of matrix a, shifted by
     // the giant step inside the block; encoded in chunks to bound the staging memory.
     auto encode_group = [&](DeviceModel::Group &G, int level, int rows,
-                            const std::function<void(uint32_t, uint32_t, std::vector<uint32_t> &)> &diag) {
+                            const std::function<void(uint32_t, uint32_t, uint32_t, std::vector<uint32_t> &)> &diag) {
         const size_t w = (size_t)(level + A) * N;
         const size_t nacc = G.plan.acc.size(), nb = G.plan.baby.size();
         G.pt.assign(nacc, std::vector<const u64 *>(nb, nullptr));
@@ -162,15 +163,17 @@ static copse_status upload_model(copse_ctx *c, copse_model *m, cudaStream_t s) {
         std::vector<uint32_t> pat, dg;
         for (size_t i0 = 0; i0 < items.size(); i0 += CH) {
             const size_t n = std::min(CH, items.size() - i0);
-            pat.assign(n * (size_t)B, 0u);
+            pat.assign(n * (size_t)SP, 0u);
             for (size_t x = 0; x < n; x++) {
                 const auto &A_ = G.plan.acc[items[i0 + x].first];
                 const uint32_t giant = A_.giant, i = (uint32_t)A_.diag[items[i0 + x].second];
-                diag(A_.mat, i, dg);
-                for (int r = 0; r < rows; r++) pat[x * B + giant + r] = dg[r];
+                for (int sg = 0; sg < NS; sg++) {
+                    diag(A_.mat, i, (uint32_t)sg, dg);
+                    for (int r = 0; r < rows; r++) pat[x * SP + (size_t)sg * B + giant + r] = dg[r];
+                }
                 G.pt[items[i0 + x].first][items[i0 + x].second] = cur + (i0 + x) * w;
             }
-            STATUS_TRY(encode_patterns(c, pat, (int)n, B, B, level, A, cur + i0 * w, s));
+            STATUS_TRY(encode_patterns(c, pat, (int)n, SP, SP, level, A, cur + i0 * w, s));
         }
         cur += items.size() * w;
         return COPSE_OK;
@@ -182,25 +185,25 @@ static copse_status upload_model(copse_ctx *c, copse_model *m, cudaStream_t s) {
     // reshuffle diagonals at the level of Decisions
     {
         std::vector<uint8_t> dg8;
-        STATUS_TRY(encode_group(D->R, D->lvl_D, (int)f.m1(), [&](uint32_t, uint32_t i, std::vector<uint32_t> &out) {
-            f.reshuffle_diagonal(i, dg8);
+        STATUS_TRY(encode_group(D->R, D->lvl_D, (int)f.m1(), [&](uint32_t, uint32_t i, uint32_t sg, std::vector<uint32_t> &out) {
+            f.reshuffle_diagonal(i, dg8, sg);
             out.assign(dg8.begin(), dg8.end());
         }));
     }
     // level diagonals (signed, mask folded in) and masks at the level of Branches
     {
         std::vector<uint64_t> dg64;
-        STATUS_TRY(encode_group(D->Lv, D->lvl_B, (int)f.L, [&](uint32_t k, uint32_t i, std::vector<uint32_t> &out) {
-            f.level_diagonal(k + 1, i, t, dg64);
+        STATUS_TRY(encode_group(D->Lv, D->lvl_B, (int)f.L, [&](uint32_t k, uint32_t i, uint32_t sg, std::vector<uint32_t> &out) {
+            f.level_diagonal(k + 1, i, t, dg64, sg);
             out.assign(dg64.begin(), dg64.end());
         }));
-        const int Lf = (int)f.L;
-        std::vector<uint32_t> mpat((size_t)f.d * Lf);
+        std::vector<uint32_t> mpat((size_t)f.d * SP, 0u);
         for (uint32_t k = 1; k <= f.d; k++) {
-            for (int x = 0; x < Lf; x++) mpat[(size_t)(k - 1) * Lf + x] = f.mask[(size_t)(k - 1) * Lf + x];
+            for (int sg = 0; sg < NS; sg++)
+                for (uint32_t x = 0; x < f.L; x++) mpat[(size_t)(k - 1) * SP + (size_t)sg * B + x] = f.mask_at(k, x, (uint32_t)sg);
             D->mask.push_back(cur + (size_t)(k - 1) * D->lvl_B * N);
         }
-        STATUS_TRY(encode_patterns(c, mpat, (int)f.d, Lf, B, D->lvl_B, 0, cur, s));
+        STATUS_TRY(encode_patterns(c, mpat, (int)f.d, SP, SP, D->lvl_B, 0, cur, s));
     }
     CUDA_TRY(cudaStreamSynchronize(s));
     m->dev = std::move(D);
@@ -222,7 +225,21 @@ extern "C" copse_status copse_compile_forest(const char *text, size_t len, uint3
 
 extern "C" void copse_model_destroy(copse_model *m) { delete m; }
 
-uint32_t model_block(const copse_model *m) { return m->f.block; }
+uint32_t model_block(const copse_model *m) { return m->f.span(); }
+
+SegLayout seg_layout(const CompiledForest &f) {
+    SegLayout lay{};
+    lay.nseg = (int)f.n_seg;
+    lay.block = (int)f.block;
+    lay.off[0] = 0;
+    if (f.n_seg == 1) {
+        lay.off[1] = (int)f.n_out();
+    } else {
+        for (uint32_t sg = 0; sg < f.n_seg; sg++) lay.off[sg + 1] = lay.off[sg] + (int)f.seg[sg].L;
+    }
+    lay.total = lay.off[lay.nseg];
+    return lay;
+}
 uint32_t model_features(const copse_model *m) { return m->f.n_features; }
 uint32_t model_leaves(const copse_model *m) { return m->f.n_out(); }
 uint32_t model_precision(const copse_model *m) { return m->f.precision; }
@@ -235,8 +252,8 @@ extern "C" copse_status copse_model_info_get(const copse_model *m, copse_model_i
     info->precision = f.precision;
     info->K = f.K;
     info->q = f.q;
-    info->b = f.b;
-    info->n_leaves = f.L;
+    info->b = f.b_total;
+    info->n_leaves = f.L_total;
     info->depth = f.d;
     info->n_trees = (uint32_t)f.roots.size();
     info->n_classes = (uint32_t)f.classes.size();
@@ -248,6 +265,9 @@ extern "C" copse_status copse_model_info_get(const copse_model *m, copse_model_i
     info->n_rot_level = (uint32_t)ls.size();
     info->levels_used = f.levels_used();
     info->n_out = f.n_out();
+    info->n_segments = f.n_seg;
+    info->block_branches = f.b;
+    info->block_leaves = f.L;
     return COPSE_OK;
 }
 
@@ -255,6 +275,7 @@ extern "C" copse_status copse_model_export(const copse_model *m, uint32_t *thr_s
                                            uint8_t *R, uint8_t *lvl, uint8_t *mask, uint32_t *br_level) {
     if (!m) { set_error("null model"); return COPSE_EINVAL; }
     const CompiledForest &f = m->f;
+    if (f.n_seg > 1) { set_error("the model is compiled in row segments: its structures are per segment"); return COPSE_EINVAL; }
     if (thr_slot) std::copy(f.thr_slot.begin(), f.thr_slot.end(), thr_slot);
     if (slot_branch) std::copy(f.slot_branch.begin(), f.slot_branch.end(), slot_branch);
     if (R) std::copy(f.R.begin(), f.R.end(), R);
@@ -319,6 +340,7 @@ extern "C" copse_status copse_model_set_shuffle(copse_model *m, const int32_t *s
                                                 const uint32_t *codebook) {
     if (!m || (n_out && (!src || !codebook))) { set_error("null argument"); return COPSE_EINVAL; }
     CompiledForest &f = m->f;
+    if (n_out && f.n_seg > 1) { set_error("label shuffle needs a model in one query block (not in row segments)"); return COPSE_EINVAL; }
     if (n_out) {
         if (n_out < f.L || n_out > f.block) { set_error("shuffle output must hold every leaf and fit the query block"); return COPSE_EINVAL; }
         std::vector<char> seen(f.L, 0);
@@ -347,7 +369,7 @@ extern "C" copse_status copse_model_codebook(const copse_model *m, uint32_t *cla
     if (!m || !classes) { set_error("null argument"); return COPSE_EINVAL; }
     const CompiledForest &f = m->f;
     if (f.shuffle_src.empty())
-        for (uint32_t j = 0; j < f.L; j++) classes[j] = (uint32_t)f.leaf_class[j];
+        for (uint32_t j = 0; j < f.L_total; j++) classes[j] = (uint32_t)f.leaf_class[j];
     else
         std::copy(f.codebook.begin(), f.codebook.end(), classes);
     return COPSE_OK;
@@ -395,7 +417,7 @@ extern "C" copse_status copse_model_get_bsgs(const copse_model *m, uint32_t *g_r
 extern "C" copse_status copse_classify_plain(const copse_model *m, const uint32_t *feats, size_t n,
                                              uint8_t *out_bits) {
     if (!m || (n && (!feats || !out_bits))) { set_error("null argument"); return COPSE_EINVAL; }
-    for (size_t j = 0; j < n; j++) classify_plain(m->f, feats + j * m->f.n_features, out_bits + j * m->f.L);
+    for (size_t j = 0; j < n; j++) classify_plain(m->f, feats + j * m->f.n_features, out_bits + j * m->f.L_total);
     return COPSE_OK;
 }
 
@@ -475,7 +497,7 @@ extern "C" copse_status copse_encrypt_features(copse_ctx *c, const copse_keys *k
     if (!c || !k || !m || !out || (nq && !feats)) { set_error("null argument"); return COPSE_EINVAL; }
     const CompiledForest &f = m->f;
     if ((int)f.log_n != c->logN) { set_error("model compiled for another ring degree"); return COPSE_EINVAL; }
-    const size_t per_ct = (size_t)(c->N / f.block);
+    const size_t per_ct = (size_t)(c->N / f.span());
     if (nq > per_ct * 64) { set_error("more than 64 ciphertexts of queries"); return COPSE_EINVAL; }
     cudaStream_t s = as_stream(stream);
     const uint32_t *d_feats = feats;
@@ -496,7 +518,7 @@ extern "C" copse_status copse_encrypt_features(copse_ctx *c, const copse_keys *k
     for (size_t j0 = 0, q = 0; st == COPSE_OK && (j0 < nq || (nq == 0 && q == 0)); j0 += per_ct, q++) {
         const size_t n = std::min(per_ct, nq - j0);
         st = encrypt_planes(c, k, d_feats + j0 * f.n_features, (int)n, (int)f.n_features, (int)f.K, (int)f.q,
-                            (int)f.pd(), (int)f.block, (int)f.precision, seed, buf->cts, s, nullptr,
+                            (int)f.pd(), (int)f.block, (int)f.n_seg, (int)f.precision, seed, buf->cts, s, nullptr,
                             (int)(q * f.precision));
         if (nq == 0) break;
     }
@@ -763,7 +785,7 @@ extern "C" copse_status copse_decrypt_labels(copse_ctx *c, const copse_keys *k, 
                                              void *stream) {
     if (!c || !k || !m || !res || res->cts.empty() || (nq && !out_bits)) { set_error("null argument"); return COPSE_EINVAL; }
     const CompiledForest &f = m->f;
-    const size_t per_ct = (size_t)(c->N / f.block);
+    const size_t per_ct = (size_t)(c->N / f.span());
     if (nq > per_ct * res->cts.size()) { set_error("more queries than slot blocks"); return COPSE_EINVAL; }
     cudaStream_t s = as_stream(stream);
     u64 *slots = nullptr;
@@ -775,7 +797,7 @@ extern "C" copse_status copse_decrypt_labels(copse_ctx *c, const copse_keys *k, 
     for (size_t j0 = 0, q = 0; j0 < nq || (nq == 0 && q == 0); j0 += per_ct, q++) {
         const size_t n = std::min(per_ct, nq - j0);
         STATUS_TRY(decrypt_slots_dev(c, k, res->cts[q], slots, s));
-        STATUS_TRY(extract_bits(c, slots, (int)n, (int)f.block, (int)n_out, bits + j0 * n_out, s));
+        STATUS_TRY(extract_bits(c, slots, (int)n, seg_layout(f), bits + j0 * n_out, s));
         if (nq == 0) break;
     }
     if (!on_device) {
@@ -947,14 +969,14 @@ static copse_status item_body(copse_session *S, size_t i, cudaStream_t s, int la
     feats.ctx = c;
     feats.stream = s;
     STATUS_TRY(encrypt_planes(c, S->keys, S->d_feats + it.feat_off, (int)it.nq, (int)f.n_features, (int)f.K,
-                              (int)f.q, (int)f.pd(), (int)f.block, (int)f.precision, (u64)i, feats.cts, s,
+                              (int)f.q, (int)f.pd(), (int)f.block, (int)f.n_seg, (int)f.precision, (u64)i, feats.cts, s,
                               S->d_seed));
     DCt res;
     STATUS_TRY(infer_impl(c, S->evk, it.m, &feats, &res, s, lane));
     u64 *slots = nullptr;
     STATUS_TRY(dev_alloc(c, (void **)&slots, (size_t)c->N * 8, s));
     STATUS_TRY(decrypt_slots_dev(c, S->keys, res, slots, s));
-    STATUS_TRY(extract_bits(c, slots, (int)it.nq, (int)f.block, (int)f.n_out(), S->d_bits + it.bit_off, s));
+    STATUS_TRY(extract_bits(c, slots, (int)it.nq, seg_layout(f), S->d_bits + it.bit_off, s));
     dev_free(slots, s);
     ct_free(&res, s);
     return COPSE_OK;  // feats frees its ciphertexts on s when it goes out of scope
@@ -988,7 +1010,7 @@ extern "C" copse_status copse_session_create_batch(copse_ctx *c, const copse_key
         if (!m) { set_error("null model"); return COPSE_EINVAL; }
         const CompiledForest &f = m->f;
         if ((int)f.log_n != c->logN) { set_error("model compiled for another ring degree"); return COPSE_EINVAL; }
-        if (n_queries[i] > (size_t)(c->N / f.block)) { set_error("more queries than slot blocks"); return COPSE_EINVAL; }
+        if (n_queries[i] > (size_t)(c->N / f.span())) { set_error("more queries than slot blocks"); return COPSE_EINVAL; }
         SessItem it;
         it.m = m;
         it.nq = n_queries[i];

@@ -68,21 +68,163 @@ uint32_t CompiledForest::levels_used() const {
     return 1 + clog2(precision) + 2 + clog2(d) + (shuffle_src.empty() ? 0 : 1);
 }
 
-void CompiledForest::reshuffle_diagonal(uint32_t i, std::vector<uint8_t> &out) const {
-    // extended reshuffle: row x is R[x mod b]; diagonal entry x is R_ext[x][(x+i) mod q]
-    out.assign(m1(), 0);
-    for (uint32_t x = 0; x < m1(); x++) out[x] = R[(size_t)(x % b) * q + (x + i) % q];
+uint32_t CompiledForest::thr_bit(uint32_t s, uint32_t x, uint32_t i) const {
+    return x < pd() ? (part(s).thr_slot[x % q] >> i) & 1u : 0u;
 }
 
-void CompiledForest::level_diagonal(uint32_t k, uint32_t i, uint64_t t, std::vector<uint64_t> &out) const {
+void CompiledForest::reshuffle_diagonal(uint32_t i, std::vector<uint8_t> &out, uint32_t s) const {
+    // extended reshuffle: row x is R[x mod b] (zero for rows past the segment's branches);
+    // diagonal entry x is R_ext[x][(x+i) mod q]
+    const CompiledForest &P = part(s);
+    out.assign(m1(), 0);
+    for (uint32_t x = 0; x < m1(); x++) {
+        const uint32_t row = x % b;
+        if (row < P.b) out[x] = P.R[(size_t)row * q + (x + i) % q];
+    }
+}
+
+void CompiledForest::level_diagonal(uint32_t k, uint32_t i, uint64_t t, std::vector<uint64_t> &out,
+                                    uint32_t s) const {
+    // segment s's level matrix as L_s x b (zero columns past its branches), diagonal i
+    const CompiledForest &P = part(s);
     out.assign(L, 0);
-    const uint8_t *M = &lvl[(size_t)(k - 1) * L * b];
-    const uint8_t *mk = &mask[(size_t)(k - 1) * L];
-    for (uint32_t x = 0; x < L; x++) {
-        if (!M[(size_t)x * b + (x + i) % b]) continue;
+    const uint8_t *M = &P.lvl[(size_t)(k - 1) * P.L * P.b];
+    const uint8_t *mk = &P.mask[(size_t)(k - 1) * P.L];
+    for (uint32_t x = 0; x < P.L; x++) {
+        const uint32_t col = (x + i) % b;
+        if (col >= P.b || !M[(size_t)x * P.b + col]) continue;
         out[x] = mk[x] ? t - 1 : 1;  // (1 - 2 mask) * entry, mod t
     }
 }
+
+uint32_t CompiledForest::mask_at(uint32_t k, uint32_t x, uint32_t s) const {
+    const CompiledForest &P = part(s);
+    return x < P.L ? P.mask[(size_t)(k - 1) * P.L + x] : 0u;
+}
+
+namespace {
+
+// Sections 4.1.1-4.2.4 for the trees `roots` of f.nodes (f.n_features and f.precision set):
+// preorder indices, levels, K and q (at least forced_K), the padded threshold vector, the
+// reshuffling matrix, the level matrices and masks for levels 1..max(d, forced_d).
+int build_structures(CompiledForest &f, const std::vector<int> &roots, uint32_t forced_K, uint32_t forced_d,
+                     std::string &err) {
+    f.br_feature.clear();
+    f.br_threshold.clear();
+    f.br_level.clear();
+    f.leaf_class.clear();
+    // Section 4.1.1: preorder indices of branches and of labels, continued across trees
+    struct Anc { int br; bool right; };
+    std::vector<std::vector<Anc>> leaf_anc;
+    std::vector<int> node_br(f.nodes.size(), -1);
+    for (int root : roots) {
+        std::vector<std::pair<int, std::vector<Anc>>> stack;
+        stack.push_back({root, {}});
+        while (!stack.empty()) {
+            auto [n, anc] = stack.back();
+            stack.pop_back();
+            const ForestNode &nd = f.nodes[n];
+            if (nd.leaf) {
+                f.leaf_class.push_back(nd.label);
+                leaf_anc.push_back(anc);
+                continue;
+            }
+            int bi = (int)f.br_feature.size();
+            node_br[n] = bi;
+            f.br_feature.push_back(nd.feature);
+            f.br_threshold.push_back(nd.threshold);
+            f.br_level.push_back(0);
+            auto ra = anc, la = anc;
+            la.push_back({bi, false});
+            ra.push_back({bi, true});
+            stack.push_back({nd.right, ra});  // popped after the left subtree
+            stack.push_back({nd.left, la});
+        }
+    }
+    f.b = (uint32_t)f.br_feature.size();
+    f.L = (uint32_t)f.leaf_class.size();
+    if (f.b == 0) { err = "forest has no branches"; return COPSE_EINVAL; }
+    // level: branches on the longest path to a label, itself included (labels: 0)
+    {
+        std::vector<int> lev(f.nodes.size(), 0);
+        for (int n = (int)f.nodes.size() - 1; n >= 0; n--) {  // children follow parents in `nodes`
+            const ForestNode &nd = f.nodes[n];
+            if (!nd.leaf) lev[n] = 1 + std::max(lev[nd.left], lev[nd.right]);
+        }
+        for (size_t n = 0; n < f.nodes.size(); n++)
+            if (node_br[n] >= 0) f.br_level[node_br[n]] = lev[n];
+    }
+    f.d = std::max(forced_d, (uint32_t)*std::max_element(f.br_level.begin(), f.br_level.end()));
+    int maxf = *std::max_element(f.br_feature.begin(), f.br_feature.end());
+    if ((uint32_t)maxf >= f.n_features) { err = "feature index out of range"; return COPSE_EINVAL; }
+    for (uint32_t th : f.br_threshold)
+        if (f.precision < 32 && th >= (1u << f.precision)) { err = "threshold needs more bits than the precision"; return COPSE_EINVAL; }
+    for (int c : f.leaf_class)
+        if (c >= (int)f.classes.size()) { err = "class index out of range"; return COPSE_EINVAL; }
+    // multiplicities, K, q = K * n_features
+    std::vector<uint32_t> kappa(f.n_features, 0);
+    for (int fe : f.br_feature) kappa[fe]++;
+    f.K = std::max(forced_K, *std::max_element(kappa.begin(), kappa.end()));
+    f.q = f.K * f.n_features;
+    // Section 4.2.1: thresholds grouped by feature in preorder, padded to K with S = 0
+    f.thr_slot.assign(f.q, 0);
+    f.slot_branch.assign(f.q, -1);
+    std::vector<uint32_t> seen(f.n_features, 0);
+    for (uint32_t i = 0; i < f.b; i++) {
+        uint32_t fe = (uint32_t)f.br_feature[i];
+        uint32_t slot = f.K * fe + seen[fe]++;
+        f.thr_slot[slot] = f.br_threshold[i];
+        f.slot_branch[slot] = (int32_t)i;
+    }
+    // Section 4.2.2: R[i][j] = 1 iff padded slot j holds branch i
+    f.R.assign((size_t)f.b * f.q, 0);
+    for (uint32_t j = 0; j < f.q; j++)
+        if (f.slot_branch[j] >= 0) f.R[(size_t)f.slot_branch[j] * f.q + j] = 1;
+    // Section 4.2.3-4.2.4.  Branch for label l at level k: the ancestor at level k;
+    // else the ancestor with the greatest level below k; else (every ancestor above
+    // k) the parent.  A leaf that is a whole tree keeps an empty row and mask 1.
+    f.lvl.assign((size_t)f.d * f.L * f.b, 0);
+    f.mask.assign((size_t)f.d * f.L, 1);
+    for (uint32_t k = 1; k <= f.d; k++) {
+        for (uint32_t l = 0; l < f.L; l++) {
+            const auto &anc = leaf_anc[l];
+            if (anc.empty()) continue;
+            int pick = -1, best_below = -1;
+            for (size_t a = 0; a < anc.size(); a++) {
+                int lv = f.br_level[anc[a].br];
+                if ((uint32_t)lv == k) pick = (int)a;
+                else if ((uint32_t)lv < k && (best_below < 0 || lv > f.br_level[anc[best_below].br])) best_below = (int)a;
+            }
+            if (pick < 0) pick = best_below >= 0 ? best_below : (int)anc.size() - 1;
+            f.lvl[((size_t)(k - 1) * f.L + l) * f.b + anc[pick].br] = 1;
+            f.mask[(size_t)(k - 1) * f.L + l] = anc[pick].right ? 0 : 1;
+        }
+    }
+    return 0;
+}
+
+uint32_t pow2_at_least(uint32_t need) {
+    uint32_t blk = 1;
+    while (blk < need) blk <<= 1;
+    return blk;
+}
+
+// branch count of one tree
+uint32_t tree_branches(const CompiledForest &f, int root) {
+    uint32_t n = 0;
+    std::vector<int> st{root};
+    while (!st.empty()) {
+        const int c = st.back();
+        st.pop_back();
+        if (f.nodes[c].leaf) continue;
+        n++;
+        st.push_back(f.nodes[c].left);
+        st.push_back(f.nodes[c].right);
+    }
+    return n;
+}
+
+}  // namespace
 
 int compile_forest(const char *text, size_t len, uint32_t precision, uint32_t n_features, uint32_t log_n,
                    CompiledForest &f, std::string &err) {
@@ -120,116 +262,102 @@ int compile_forest(const char *text, size_t len, uint32_t precision, uint32_t n_
         if (p.pos != p.toks.size()) { err = "tree " + std::to_string(li) + ": trailing tokens"; return COPSE_EPARSE; }
         f.roots.push_back(root);
     }
-    // Section 4.1.1: preorder indices of branches and of labels, continued across trees
-    struct Anc { int br; bool right; };
-    std::vector<std::vector<Anc>> leaf_anc;
-    std::vector<int> node_br(f.nodes.size(), -1);
-    for (int root : f.roots) {
-        std::vector<std::pair<int, std::vector<Anc>>> stack;
-        stack.push_back({root, {}});
-        while (!stack.empty()) {
-            auto [n, anc] = stack.back();
-            stack.pop_back();
-            const ForestNode &nd = f.nodes[n];
-            if (nd.leaf) {
-                f.leaf_class.push_back(nd.label);
-                leaf_anc.push_back(anc);
-                continue;
-            }
-            int bi = (int)f.br_feature.size();
-            node_br[n] = bi;
-            f.br_feature.push_back(nd.feature);
-            f.br_threshold.push_back(nd.threshold);
-            f.br_level.push_back(0);
-            auto ra = anc, la = anc;
-            la.push_back({bi, false});
-            ra.push_back({bi, true});
-            stack.push_back({nd.right, ra});  // popped after the left subtree
-            stack.push_back({nd.left, la});
-        }
-    }
-    f.b = (uint32_t)f.br_feature.size();
-    f.L = (uint32_t)f.leaf_class.size();
-    if (f.b == 0) { err = "forest has no branches"; return COPSE_EINVAL; }
-    // level: branches on the longest path to a label, itself included (labels: 0)
-    {
-        std::vector<int> lev(f.nodes.size(), 0);
-        for (int n = (int)f.nodes.size() - 1; n >= 0; n--) {  // children follow parents in `nodes`
-            const ForestNode &nd = f.nodes[n];
-            if (!nd.leaf) lev[n] = 1 + std::max(lev[nd.left], lev[nd.right]);
-        }
-        for (size_t n = 0; n < f.nodes.size(); n++)
-            if (node_br[n] >= 0) f.br_level[node_br[n]] = lev[n];
-    }
-    f.d = (uint32_t)*std::max_element(f.br_level.begin(), f.br_level.end());
-    int maxf = *std::max_element(f.br_feature.begin(), f.br_feature.end());
-    f.n_features = n_features ? n_features : (uint32_t)maxf + 1;
-    if ((uint32_t)maxf >= f.n_features) { err = "feature index out of range"; return COPSE_EINVAL; }
     f.precision = precision;
-    for (uint32_t th : f.br_threshold)
-        if (precision < 32 && th >= (1u << precision)) { err = "threshold needs more bits than the precision"; return COPSE_EINVAL; }
-    for (int c : f.leaf_class)
-        if (c >= (int)f.classes.size()) { err = "class index out of range"; return COPSE_EINVAL; }
-    // multiplicities, K, q = K * n_features
-    std::vector<uint32_t> kappa(f.n_features, 0);
-    for (int fe : f.br_feature) kappa[fe]++;
-    f.K = *std::max_element(kappa.begin(), kappa.end());
-    f.q = f.K * f.n_features;
-    // Section 4.2.1: thresholds grouped by feature in preorder, padded to K with S = 0
-    f.thr_slot.assign(f.q, 0);
-    f.slot_branch.assign(f.q, -1);
-    std::vector<uint32_t> seen(f.n_features, 0);
-    for (uint32_t i = 0; i < f.b; i++) {
-        uint32_t fe = (uint32_t)f.br_feature[i];
-        uint32_t slot = f.K * fe + seen[fe]++;
-        f.thr_slot[slot] = f.br_threshold[i];
-        f.slot_branch[slot] = (int32_t)i;
-    }
-    // Section 4.2.2: R[i][j] = 1 iff padded slot j holds branch i
-    f.R.assign((size_t)f.b * f.q, 0);
-    for (uint32_t j = 0; j < f.q; j++)
-        if (f.slot_branch[j] >= 0) f.R[(size_t)f.slot_branch[j] * f.q + j] = 1;
-    // Section 4.2.3-4.2.4.  Branch for label l at level k: the ancestor at level k;
-    // else the ancestor with the greatest level below k; else (every ancestor above
-    // k) the parent.  A leaf that is a whole tree keeps an empty row and mask 1.
-    f.lvl.assign((size_t)f.d * f.L * f.b, 0);
-    f.mask.assign((size_t)f.d * f.L, 1);
-    for (uint32_t k = 1; k <= f.d; k++) {
-        for (uint32_t l = 0; l < f.L; l++) {
-            const auto &anc = leaf_anc[l];
-            if (anc.empty()) continue;
-            int pick = -1, best_below = -1;
-            for (size_t a = 0; a < anc.size(); a++) {
-                int lv = f.br_level[anc[a].br];
-                if ((uint32_t)lv == k) pick = (int)a;
-                else if ((uint32_t)lv < k && (best_below < 0 || lv > f.br_level[anc[best_below].br])) best_below = (int)a;
+    int maxf = -1;
+    for (const ForestNode &nd : f.nodes)
+        if (!nd.leaf) maxf = std::max(maxf, nd.feature);
+    f.n_features = n_features ? n_features : (uint32_t)(maxf + 1);
+    int st = build_structures(f, f.roots, 0, 0, err);
+    if (st) return st;
+    f.b_total = f.b;
+    f.L_total = f.L;
+    f.log_n = log_n;
+    const uint32_t row = 1u << (log_n - 1);
+    f.block = pow2_at_least(f.pd());
+    if (f.block > row) {
+        // row segments: the trees in n_seg contiguous groups, tree t in group
+        // floor(n_seg * (branches of the trees before t) / total branches); the smallest
+        // power of two whose common block fits a row (and whose blocks fit the ring)
+        std::vector<uint32_t> before(f.roots.size() + 1, 0);
+        for (size_t t = 0; t < f.roots.size(); t++) before[t + 1] = before[t] + tree_branches(f, f.roots[t]);
+        bool ok = false;
+        for (uint32_t S = 2; S <= 64 && S <= f.roots.size() && !ok; S *= 2) {
+            std::vector<std::vector<int>> groups(S);
+            for (size_t t = 0; t < f.roots.size(); t++)
+                groups[std::min<uint64_t>(S - 1, (uint64_t)S * before[t] / f.b_total)].push_back(f.roots[t]);
+            if (std::any_of(groups.begin(), groups.end(), [](const std::vector<int> &g) { return g.empty(); })) continue;
+            std::vector<CompiledForest> segs(S);
+            uint32_t K = 0, d = 0;
+            for (int pass = 0; pass < 2; pass++) {
+                for (uint32_t g = 0; g < S; g++) {
+                    CompiledForest &sg = segs[g];
+                    sg.classes = f.classes;
+                    sg.nodes = f.nodes;
+                    sg.roots = groups[g];
+                    sg.n_features = f.n_features;
+                    sg.precision = precision;
+                    sg.log_n = log_n;
+                    st = build_structures(sg, sg.roots, pass ? K : 0, pass ? d : 0, err);
+                    if (st) return st;
+                    if (!pass) {
+                        K = std::max(K, sg.K);
+                        d = std::max(d, sg.d);
+                    }
+                }
             }
-            if (pick < 0) pick = best_below >= 0 ? best_below : (int)anc.size() - 1;
-            f.lvl[((size_t)(k - 1) * f.L + l) * f.b + anc[pick].br] = 1;
-            f.mask[(size_t)(k - 1) * f.L + l] = anc[pick].right ? 0 : 1;
+            uint32_t bp = 0, Lp = 0;
+            for (const CompiledForest &sg : segs) {
+                bp = std::max(bp, sg.b);
+                Lp = std::max(Lp, sg.L);
+            }
+            const uint32_t blk = pow2_at_least(Lp + bp - 1 + K * f.n_features - 1);
+            if (blk > row || (uint64_t)S * blk > (1ull << log_n)) continue;
+            for (CompiledForest &sg : segs) {
+                sg.b_total = sg.b;
+                sg.L_total = sg.L;
+                sg.block = blk;
+            }
+            f.n_seg = S;
+            f.seg = std::move(segs);
+            f.K = K;
+            f.q = K * f.n_features;
+            f.d = d;
+            f.b = bp;
+            f.L = Lp;
+            f.block = blk;
+            // the whole-forest arrays are not the layout's: each segment holds its own
+            f.thr_slot.clear();
+            f.slot_branch.clear();
+            f.R.clear();
+            f.lvl.clear();
+            f.mask.clear();
+            ok = true;
+        }
+        if (!ok) {
+            err = "query block of " + std::to_string(f.block) + " slots exceeds a slot row";
+            return COPSE_EFIT;
         }
     }
-    // slot layout
-    f.log_n = log_n;
-    uint32_t need = f.pd(), blk = 1;
-    while (blk < need) blk <<= 1;
-    f.block = blk;
-    if ((uint64_t)blk > (1ull << (log_n - 1))) {
-        err = "query block of " + std::to_string(blk) + " slots exceeds a slot row";
-        return COPSE_EFIT;
-    }
-    // nonzero diagonals
+    // nonzero diagonals (of any segment)
     std::vector<uint8_t> dg;
     for (uint32_t i = 0; i < f.q; i++) {
-        f.reshuffle_diagonal(i, dg);
-        if (std::any_of(dg.begin(), dg.end(), [](uint8_t v) { return v != 0; })) f.rot_reshuffle.push_back(i);
+        bool nz = false;
+        for (uint32_t sgi = 0; sgi < f.n_seg && !nz; sgi++) {
+            f.reshuffle_diagonal(i, dg, sgi);
+            nz = std::any_of(dg.begin(), dg.end(), [](uint8_t v) { return v != 0; });
+        }
+        if (nz) f.rot_reshuffle.push_back(i);
     }
     f.lvl_nonzero.assign(f.d, {});
+    std::vector<uint64_t> dl;
     for (uint32_t i = 0; i < f.b; i++) {
         bool any = false;
         for (uint32_t k = 0; k < f.d; k++) {
             bool nz = false;
-            for (uint32_t x = 0; x < f.L && !nz; x++) nz = f.lvl[((size_t)k * f.L + x) * f.b + (x + i) % f.b] != 0;
+            for (uint32_t sgi = 0; sgi < f.n_seg && !nz; sgi++) {
+                f.level_diagonal(k + 1, i, 2, dl, sgi);
+                nz = std::any_of(dl.begin(), dl.end(), [](uint64_t v) { return v != 0; });
+            }
             if (nz) f.lvl_nonzero[k].push_back(i);
             any |= nz;
         }

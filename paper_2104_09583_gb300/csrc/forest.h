@@ -72,7 +72,7 @@ struct CompiledForest {
     // (-1 = padding, always 0); codebook[j] is its class.  Empty = no shuffle.
     std::vector<int32_t> shuffle_src;
     std::vector<uint32_t> codebook;
-    uint32_t n_out() const { return shuffle_src.empty() ? L : (uint32_t)shuffle_src.size(); }
+    uint32_t n_out() const { return shuffle_src.empty() ? L_total : (uint32_t)shuffle_src.size(); }
     // rotation amounts of the shuffle product (signed shifts src[j] - j taken mod N/2), ascending
     void shuffle_rotations(std::vector<uint32_t> &out) const;
     // its diagonal for one rotation amount, block-local over n_out() slots
@@ -81,10 +81,26 @@ struct CompiledForest {
     uint32_t m1() const { return L + b - 1; }       // rows of the extended reshuffle
     uint32_t pd() const { return m1() + q - 1; }    // slots carrying the periodic decisions
     uint32_t levels_used() const;
-    // diagonal i of the extended reshuffle matrix, as a block-local slot vector
-    void reshuffle_diagonal(uint32_t i, std::vector<uint8_t> &out) const;
-    // signed diagonal i of level k (1-based), values in {0, 1, t-1}; block-local
-    void level_diagonal(uint32_t k, uint32_t i, uint64_t t, std::vector<uint64_t> &out) const;
+
+    // Row segments.  When one query block of the whole forest would not fit a slot row,
+    // the trees are split into n_seg contiguous groups (segments) compiled alike: a common
+    // K (so q), a common depth d, and per-block sizes b, L = the largest segment's.  Query j
+    // then owns the n_seg blocks j n_seg + s, block s holding segment s; rotations never
+    // cross a block, so each block's diagonals are its segment's.  b_total and L_total count
+    // the whole forest (L_total leaf bits per query, in preorder across the trees).
+    uint32_t n_seg = 1;
+    std::vector<CompiledForest> seg;  // the segments when n_seg > 1
+    uint32_t b_total = 0, L_total = 0;
+    uint32_t span() const { return n_seg * block; }  // slots of one query (its blocks)
+    const CompiledForest &part(uint32_t s) const { return n_seg > 1 ? seg[s] : *this; }
+    // threshold bit of plane i at block-local slot x of segment s's block
+    uint32_t thr_bit(uint32_t s, uint32_t x, uint32_t i) const;
+    // diagonal i of segment s's extended reshuffle matrix (rows m1(), period b), block-local
+    void reshuffle_diagonal(uint32_t i, std::vector<uint8_t> &out, uint32_t s = 0) const;
+    // signed diagonal i of segment s's level k (1-based), values in {0, 1, t-1}; L rows, block-local
+    void level_diagonal(uint32_t k, uint32_t i, uint64_t t, std::vector<uint64_t> &out, uint32_t s = 0) const;
+    // level-k mask at block-local slot x of segment s's block (0 past the segment's leaves)
+    uint32_t mask_at(uint32_t k, uint32_t x, uint32_t s) const;
 };
 
 // 0 on success; otherwise a COPSE_E* code and a message in `err`.

@@ -45,11 +45,19 @@ void set_error(const std::string &msg);
 
 // kernel timing (stats.cu): brackets a launch with CUDA events when enabled
 int stats_begin(const char *name, double bytes, cudaStream_t s);
+int stats_begin_ops(const char *name, double bytes, double ops, cudaStream_t s);
 void stats_end(int token, cudaStream_t s);
 void stats_suspend(bool on);
 #define TIMED(name, bytes, s, ...)                                                               \
     do {                                                                                         \
         int tk__ = stats_begin(name, (double)(bytes), s);                                        \
+        __VA_ARGS__;                                                                             \
+        stats_end(tk__, s);                                                                      \
+    } while (0)
+// the same with the launch's algorithmic modular products (the integer roof's unit)
+#define TIMED_OPS(name, bytes, ops, s, ...)                                                      \
+    do {                                                                                         \
+        int tk__ = stats_begin_ops(name, (double)(bytes), (double)(ops), s);                     \
         __VA_ARGS__;                                                                             \
         stats_end(tk__, s);                                                                      \
     } while (0)
@@ -117,6 +125,35 @@ __device__ __forceinline__ void mac128(Acc128 &a, u64 x, u64 y) {
 }
 __device__ __forceinline__ u64 reduce128(const Acc128 &a, const PrimeDev &P) {
     return add_mod(mul_shoup(barrett_wide(0, a.hi, P), P.r64, P.r64_sh, P.q), barrett_wide(0, a.lo, P), P.q);
+}
+// Exact sums of products of operands below 2^56 (residues of primes below 2^55 and
+// sums of two of them) from 32 x 32 -> 64-bit multiply-adds: x = x1 2^28 + x0 with
+// x0, x1 < 2^28, so x y = x1 y1 2^56 + (x1 y0 + x0 y1) 2^28 + x0 y0 and every partial
+// product is below 2^56.  Three 64-bit partial sums hold 64 such products exactly
+// (lo, hi < 2^62, mid < 2^63); one reduction at the end gives the residue.
+struct Sp28 {
+    uint32_t lo, hi;
+};
+__device__ __forceinline__ Sp28 split28(u64 x) { return Sp28{(uint32_t)x & 0x0FFFFFFFu, (uint32_t)(x >> 28)}; }
+struct Acc3w {
+    u64 lo, mid, hi;
+};
+__device__ __forceinline__ void mac_sp(Acc3w &a, Sp28 x, Sp28 y) {
+    a.lo += (u64)x.lo * y.lo;
+    a.mid += (u64)x.lo * y.hi;
+    a.mid += (u64)x.hi * y.lo;
+    a.hi += (u64)x.hi * y.hi;
+}
+// lo + mid 2^28 + hi 2^56 (< 2^119) as a 128-bit value
+__device__ __forceinline__ Acc128 acc3w_value(const Acc3w &a) {
+    Acc128 v{a.lo, 0};
+    const u64 m = a.mid << 28;
+    v.lo += m;
+    v.hi += (a.mid >> 36) + (v.lo < m);
+    const u64 h = a.hi << 56;
+    v.lo += h;
+    v.hi += (a.hi >> 8) + (v.lo < h);
+    return v;
 }
 // a signed small integer (|v| < q) as a residue
 __device__ __forceinline__ u64 from_signed(i64 v, u64 q) { return v < 0 ? q - (u64)(-v) : (u64)v; }
@@ -438,6 +475,16 @@ struct EncModel {
     int lvl_D = 0, lvl_B = 0;
     int p = 0, q = 0, b = 0, d = 0;
     u64 *store = nullptr;
+    // per product kind (0 reshuffle, 1 levels): for every accumulator of the plan and every
+    // baby step, the c0 and mask stream of its diagonal (c0 null = none), [nacc][nbaby]
+    struct MacEntry {
+        const u64 *c0;
+        u64 stream;
+    };
+    MacEntry *d_tab[2] = {nullptr, nullptr};
+    // query ciphertexts per rotation group of each product kind, as last sized from free
+    // device memory outside graph capture (0 = not sized yet)
+    mutable int group_hint[2] = {0, 0};
     std::vector<size_t> off;         // word offset of each ciphertext's c0
     std::vector<int> level;
     BsgsGroup grpR, grpL;            // dense plans (every diagonal present)
@@ -486,11 +533,19 @@ copse_status keygen_dev(copse_ctx *c, u64 seed, const std::vector<u64> &galois, 
 // K, q, pd, block
 // (d_seed: when set, the seed is read from that device word instead of `seed`)
 copse_status encrypt_planes(copse_ctx *c, const copse_keys *k, const uint32_t *d_feats, int nq, int nf, int K,
-                            int q, int pd, int block, int p, u64 seed, std::vector<DCt> &out, cudaStream_t s,
-                            const u64 *d_seed = nullptr, int index0 = 0);
+                            int q, int pd, int block, int nseg, int p, u64 seed, std::vector<DCt> &out,
+                            cudaStream_t s, const u64 *d_seed = nullptr, int index0 = 0);
 // decrypt to N slot values (device output, NTT(mod t) order remapped to slot order)
 copse_status decrypt_slots_dev(copse_ctx *c, const copse_keys *k, const DCt &ct, u64 *d_slots, cudaStream_t s);
-copse_status extract_bits(copse_ctx *c, const u64 *d_slots, int nq, int block, int L, uint8_t *d_bits,
+// where each query's result bits sit: query j owns blocks j nseg .. j nseg + nseg - 1; its
+// output bits [off[s], off[s] + len[s]) are the first len[s] slots of block j nseg + s
+#define COPSE_MAX_SEG 64
+struct SegLayout {
+    int nseg, block, total;
+    int off[COPSE_MAX_SEG + 1];
+};
+SegLayout seg_layout(const CompiledForest &f);
+copse_status extract_bits(copse_ctx *c, const u64 *d_slots, int nq, const SegLayout &lay, uint8_t *d_bits,
                           cudaStream_t s);
 // sessions (copse.cu): asynchronous launch with feature/bit buffers in pinned host or
 // device memory; seed_slot is pinned host memory holding the run's seed until it completes

@@ -39,14 +39,16 @@ __global__ void k_pointwise_mul(const u64 *a, const u64 *b, u64 *out, int nres, 
 std::mutex scratch_mu;
 u64 *scratch_addr[NOALLOC_MAX_DEVICES] = {};
 
-// device address of the scratch array on `device` (which must be current)
+// device address of the scratch array on `device`, which must be the calling thread's
+// current device on every call: the cached address belongs to that device's copy of the
+// array, and a launch on another device with it would touch memory of the wrong GPU
 copse_status scratch_on(int device, u64 **out) {
     if (device < 0 || device >= NOALLOC_MAX_DEVICES) { set_error("device index out of range"); return COPSE_EINVAL; }
+    int cur = -1;
+    CUDA_TRY(cudaGetDevice(&cur));
+    if (cur != device) { set_error("the context's device is not the current device"); return COPSE_EINVAL; }
     std::lock_guard<std::mutex> g(scratch_mu);
     if (!scratch_addr[device]) {
-        int cur = -1;
-        CUDA_TRY(cudaGetDevice(&cur));
-        if (cur != device) { set_error("the context's device is not the current device"); return COPSE_EINVAL; }
         void *p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || !p) {

@@ -21,6 +21,8 @@
 // Small rings use one CTA per polynomial.
 #include <cooperative_groups.h>
 
+#include <atomic>
+
 #include "internal.cuh"
 
 namespace cg = cooperative_groups;
@@ -672,14 +674,24 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT2)
                  mul_shoup(S.colt[e], sc, q));
 }
 
+// The dynamic shared-memory limit is a per-device function attribute: each kernel
+// instantiation keeps one bit per device (set after the attribute is raised on that
+// device).  Threads that race here both raise it, which is harmless.
+inline bool attr_pending(std::atomic<uint64_t> &mask, int device) {
+    return device < 0 || device >= 64 || !(mask.load(std::memory_order_acquire) & (1ull << device));
+}
+inline void attr_done(std::atomic<uint64_t> &mask, int device) {
+    if (device >= 0 && device < 64) mask.fetch_or(1ull << device, std::memory_order_release);
+}
+
 template <int CL>
 copse_status launch_cluster(copse_ctx *ctx, const NttBatch &b, cudaStream_t s, bool inverse, double bytes) {
-    static bool attr_set = false;  // per instantiation; raising the limit twice is harmless
+    static std::atomic<uint64_t> attr_devices{0};
     const int smem = (int)sizeof(ClusterSmem);
-    if (!attr_set) {
+    if (attr_pending(attr_devices, ctx->device)) {
         CUDA_TRY(cudaFuncSetAttribute(k_ntt_fwd_cluster<CL, PlainIO>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
         CUDA_TRY(cudaFuncSetAttribute(k_ntt_inv_cluster<CL, PlainIO>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        attr_set = true;
+        attr_done(attr_devices, ctx->device);
     }
     const unsigned grid = (unsigned)b.npoly * (unsigned)b.nr * CL;
     const int a = ctx->logN / 2;
@@ -749,14 +761,14 @@ template <> constexpr const char *io_family<MddIO>(bool) { return "ntt_fwd_mdd";
 
 template <int CL, bool INV, class IO>
 copse_status launch_cluster_io(copse_ctx *ctx, const NttBatch &b, const IO &io, cudaStream_t s) {
-    static bool attr_set = false;
+    static std::atomic<uint64_t> attr_devices{0};
     const int smem = (int)sizeof(ClusterSmem);
-    if (!attr_set) {
+    if (attr_pending(attr_devices, ctx->device)) {
         if (INV)
             CUDA_TRY(cudaFuncSetAttribute(k_ntt_inv_cluster<CL, IO>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
         else
             CUDA_TRY(cudaFuncSetAttribute(k_ntt_fwd_cluster<CL, IO>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        attr_set = true;
+        attr_done(attr_devices, ctx->device);
     }
     const unsigned grid = (unsigned)b.npoly * (unsigned)b.nr * CL;
     const double bytes = (double)b.npoly * b.nr * ctx->N * 16.0;

@@ -549,11 +549,12 @@ __global__ void k_lift(const u64 *in, u64 *out, int npoly, int level, int nres, 
 }
 
 // bit-planes of the replicated, block-periodic feature vectors, NTT(mod t) order
-__global__ void k_feature_planes(const uint32_t *feats, int nq, int nf, int K, int q, int pd, int block, int p,
-                                 int logN, const uint32_t *slot_index, u64 *out) {
+// block beta of the ciphertext belongs to query beta / nseg (its segment beta mod nseg)
+__global__ void k_feature_planes(const uint32_t *feats, int nq, int nf, int K, int q, int pd, int block, int nseg,
+                                 int p, int logN, const uint32_t *slot_index, u64 *out) {
     size_t s = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= (1ull << logN)) return;
-    const int j = (int)(s / block), x = (int)(s % block);
+    const int j = (int)(s / block) / nseg, x = (int)(s % block);
     uint32_t val = 0;
     if (j < nq && x < pd) val = feats[(size_t)j * nf + (x % q) / K];
     const uint32_t pos = slot_index[s];
@@ -625,11 +626,16 @@ __global__ void k_gather_slots(const u64 *ntt_t, const uint32_t *slot_index, u64
     slots[s] = ntt_t[slot_index[s]];
 }
 
-__global__ void k_extract_bits(const u64 *slots, int nq, int block, int L, uint8_t *bits) {
+// output bit x of query j: segment s with off[s] <= x < off[s] + len[s], slot x - off[s] of
+// block j nseg + s
+__global__ void k_extract_bits(const u64 *slots, int nq, const SegLayout lay, uint8_t *bits) {
     size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= (size_t)nq * L) return;
-    const size_t j = e / L, x = e - j * L;
-    const u64 v = slots[j * block + x];
+    if (e >= (size_t)nq * lay.total) return;
+    const size_t j = e / lay.total;
+    const int x = (int)(e - j * lay.total);
+    int sg = 0;
+    while (sg + 1 < lay.nseg && x >= lay.off[sg + 1]) sg++;
+    const u64 v = slots[(j * lay.nseg + sg) * lay.block + (x - lay.off[sg])];
     bits[e] = v == 0 ? 0 : (v == 1 ? 1 : 2);
 }
 
@@ -1531,8 +1537,8 @@ copse_status keygen_dev(copse_ctx *c, u64 seed, const std::vector<u64> &galois, 
 }
 
 copse_status encrypt_planes(copse_ctx *c, const copse_keys *k, const uint32_t *d_feats, int nq, int nf, int K,
-                            int q, int pd, int block, int p, u64 seed, std::vector<DCt> &out, cudaStream_t s,
-                            const u64 *d_seed, int index0) {
+                            int q, int pd, int block, int nseg, int p, u64 seed, std::vector<DCt> &out,
+                            cudaStream_t s, const u64 *d_seed, int index0) {
     const int N = c->N, L = c->L;
     Scratch sc(s);
     u64 *mt = nullptr, *U = nullptr, *X0 = nullptr, *X1 = nullptr, *cts = nullptr;
@@ -1540,7 +1546,7 @@ copse_status encrypt_planes(copse_ctx *c, const copse_keys *k, const uint32_t *d
     STATUS_TRY(sc.get(c, &U, (size_t)p * L * N));
     STATUS_TRY(sc.get(c, &X0, (size_t)p * L * N));
     STATUS_TRY(sc.get(c, &X1, (size_t)p * L * N));
-    k_feature_planes<<<nblk(N), TPB, 0, s>>>(d_feats, nq, nf, K, q, pd, block, p, c->logN, c->d_slot_index, mt);
+    k_feature_planes<<<nblk(N), TPB, 0, s>>>(d_feats, nq, nf, K, q, pd, block, nseg, p, c->logN, c->d_slot_index, mt);
     LAUNCH_CHECK();
     STATUS_TRY(ntt_inverse(c, batch(mt, N, p, 0, 1, 0, c->t_index()), s));
     if (index0 < 0 || index0 + p > 0x100000) { set_error("encryption index out of range"); return COPSE_EINVAL; }
@@ -1587,10 +1593,10 @@ copse_status decrypt_slots_dev(copse_ctx *c, const copse_keys *k, const DCt &ct,
     return COPSE_OK;
 }
 
-copse_status extract_bits(copse_ctx *c, const u64 *d_slots, int nq, int block, int L, uint8_t *d_bits,
+copse_status extract_bits(copse_ctx *c, const u64 *d_slots, int nq, const SegLayout &lay, uint8_t *d_bits,
                           cudaStream_t s) {
-    if (nq * L == 0) return COPSE_OK;
-    k_extract_bits<<<nblk((size_t)nq * L), TPB, 0, s>>>(d_slots, nq, block, L, d_bits);
+    if (nq * lay.total == 0) return COPSE_OK;
+    k_extract_bits<<<nblk((size_t)nq * lay.total), TPB, 0, s>>>(d_slots, nq, lay, d_bits);
     LAUNCH_CHECK();
     return COPSE_OK;
 }

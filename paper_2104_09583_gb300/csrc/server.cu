@@ -4,11 +4,16 @@
 // batching: requests that arrive while a launch is on the GPU go into the
 // next one), runs up to two launches per model concurrently on their own
 // streams, and completes tickets as launches finish.  Evaluation keys,
-// model plaintexts and the graphs' memory stay on the device.  Admission:
-// the graphs' device memory is reserved when the server is created (each
-// model's two launches are replayed once), and while running a request is
-// admitted only if the pending queue -- host memory -- has room, else
-// COPSE_EADMIT.
+// model plaintexts and the graphs' memory stay on the device.  Admission is by
+// device memory: at creation every launch's reservation is measured (the drop
+// in free device memory when its graph is recorded and replayed once), a
+// model gets its second concurrent launch only if free memory still holds
+// another such reservation plus the admission floor, and creation fails with
+// COPSE_EADMIT if even one launch per model does not fit.  While running, a
+// request is admitted only if free device memory is at least the floor (by
+// default the largest launch reservation: room for one more launch's working
+// set, so memory taken by other work on the device stops admission) and the
+// pending queue has room; otherwise COPSE_EADMIT.
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -50,6 +55,7 @@ struct ModelSlot {
     copse_model *m = nullptr;
     size_t per_ct = 0, nf = 0, L = 0;
     uint32_t precision = 0;
+    int nbuf = 0;  // launches this model runs concurrently (1 or 2, by device memory)
     Buffer buf[2];
     std::deque<Request> pending;
 };
@@ -65,6 +71,9 @@ struct copse_server {
     std::thread worker;
     bool stop = false;
     size_t max_pending = 0, n_pending = 0;
+    size_t reserved = 0;    // device bytes the launches reserved at creation
+    size_t launch_max = 0;  // the largest single launch's reservation
+    size_t mem_floor = 0;   // free device bytes a submit requires
     uint64_t next_ticket = 1, seed = 0;
     copse_status worker_error = COPSE_OK;
     std::string worker_msg;
@@ -79,7 +88,8 @@ void copse_server::loop() {
         bool progressed = false;
         // complete finished launches
         for (ModelSlot &ms : models)
-            for (Buffer &b : ms.buf) {
+            for (int bi = 0; bi < ms.nbuf; bi++) {
+                Buffer &b = ms.buf[bi];
                 if (!b.busy || cudaEventQuery(b.done) != cudaSuccess) continue;
                 const Clock::time_point now = Clock::now();
                 for (size_t j = 0; j < b.tickets.size(); j++) {
@@ -96,7 +106,8 @@ void copse_server::loop() {
             }
         // start launches for models with pending requests and a free buffer
         for (ModelSlot &ms : models)
-            for (Buffer &b : ms.buf) {
+            for (int bi = 0; bi < ms.nbuf; bi++) {
+                Buffer &b = ms.buf[bi];
                 if (b.busy || ms.pending.empty()) continue;
                 const size_t n = std::min(ms.per_ct, ms.pending.size());
                 memset(b.h_feats, 0, ms.per_ct * ms.nf * 4);
@@ -149,9 +160,7 @@ extern "C" copse_status copse_server_create(copse_ctx *c, const copse_keys *keys
         ms.nf = model_features(ms.m);
         ms.L = model_leaves(ms.m);
         ms.precision = model_precision(ms.m);
-        total_slots += 2 * ms.per_ct;
     }
-    S->max_pending = max_pending ? max_pending : 4 * total_slots;
     auto cleanup = [&](copse_status st) {
         for (ModelSlot &ms : S->models)
             for (Buffer &b : ms.buf) {
@@ -165,10 +174,22 @@ extern "C" copse_status copse_server_create(copse_ctx *c, const copse_keys *keys
         return st;
     };
     CUDA_TRY(cudaSetDevice(c->device));
-    for (ModelSlot &ms : S->models)
-        for (Buffer &b : ms.buf) {
+    // first every model's one launch, then a second per model while device memory allows
+    for (int round = 0; round < 2; round++)
+        for (ModelSlot &ms : S->models) {
+            size_t free0 = 0, total = 0;
+            CUDA_TRY(cudaMemGetInfo(&free0, &total));
+            if (round == 1 && free0 < S->launch_max + S->launch_max / 8 + S->launch_max) continue;
+            Buffer &b = ms.buf[round];
             copse_status st = copse_session_create(c, keys, evk, ms.m, ms.per_ct, &b.sess);
-            if (st) return cleanup(st);
+            if (st) {
+                if (st == COPSE_ENOMEM || st == COPSE_ECUDA) {
+                    set_error(std::string("device memory cannot hold the server's launches: ") + copse_last_error());
+                    cudaGetLastError();
+                    return cleanup(round == 0 ? COPSE_EADMIT : st);
+                }
+                return cleanup(st);
+            }
             if (cudaStreamCreateWithFlags(&b.stream, cudaStreamNonBlocking) != cudaSuccess ||
                 cudaEventCreateWithFlags(&b.done, cudaEventDisableTiming) != cudaSuccess ||
                 cudaMallocHost(&b.h_feats, std::max<size_t>(ms.per_ct * ms.nf, 1) * 4) != cudaSuccess ||
@@ -179,13 +200,22 @@ extern "C" copse_status copse_server_create(copse_ctx *c, const copse_keys *keys
                 return cleanup(COPSE_ENOMEM);
             }
             memset(b.h_feats, 0, ms.per_ct * ms.nf * 4);
-            // reserve the graph's device memory now: admission afterwards only concerns the queue
+            // reserve the graph's device memory now and measure it
             st = session_launch(b.sess, b.h_feats, 1, b.h_bits, b.stream, b.h_seed);
             if (st || cudaStreamSynchronize(b.stream) != cudaSuccess) {
                 if (!st) set_error("server warm-up launch failed");
                 return cleanup(st ? st : COPSE_ECUDA);
             }
+            size_t free1 = 0;
+            CUDA_TRY(cudaMemGetInfo(&free1, &total));
+            const size_t used = free0 > free1 ? free0 - free1 : 0;
+            S->reserved += used;
+            S->launch_max = std::max(S->launch_max, used);
+            ms.nbuf = round + 1;
+            total_slots += ms.per_ct;
         }
+    S->max_pending = max_pending ? max_pending : 4 * total_slots;
+    S->mem_floor = S->launch_max;
     copse_server *raw = S.release();
     raw->worker = std::thread([raw] { raw->loop(); });
     *out = raw;
@@ -199,8 +229,19 @@ extern "C" copse_status copse_server_submit(copse_server *S, uint32_t model_id, 
     ModelSlot &ms = S->models[model_id];
     for (size_t k = 0; k < ms.nf; k++)
         if (ms.precision < 32 && feats[k] >= (1u << ms.precision)) { set_error("feature value needs more bits than the precision"); return COPSE_EINVAL; }
+    size_t free_b = 0, total_b = 0;
+    if (cudaSetDevice(S->c->device) != cudaSuccess || cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("device memory could not be queried");
+        return COPSE_ECUDA;
+    }
     std::lock_guard<std::mutex> g(S->mu);
     if (S->worker_error) { set_error("server stopped: " + S->worker_msg); return S->worker_error; }
+    if (free_b < S->mem_floor) {
+        set_error("free device memory (" + std::to_string(free_b) + " bytes) is below the admission floor (" +
+                  std::to_string(S->mem_floor) + " bytes)");
+        return COPSE_EADMIT;
+    }
     if (S->n_pending >= S->max_pending) { set_error("request queue is full"); return COPSE_EADMIT; }
     const uint64_t t = S->next_ticket++;
     Ticket tk;
@@ -234,12 +275,34 @@ extern "C" copse_status copse_server_poll(copse_server *S, uint64_t ticket, uint
     return COPSE_OK;
 }
 
+extern "C" copse_status copse_server_memory(copse_server *S, size_t *reserved, size_t *launch_max, size_t *floor,
+                                            uint32_t *launches) {
+    if (!S) { set_error("bad argument"); return COPSE_EINVAL; }
+    std::lock_guard<std::mutex> g(S->mu);
+    if (reserved) *reserved = S->reserved;
+    if (launch_max) *launch_max = S->launch_max;
+    if (floor) *floor = S->mem_floor;
+    if (launches) {
+        uint32_t n = 0;
+        for (const ModelSlot &ms : S->models) n += (uint32_t)ms.nbuf;
+        *launches = n;
+    }
+    return COPSE_OK;
+}
+
+extern "C" copse_status copse_server_set_memory_floor(copse_server *S, size_t floor) {
+    if (!S) { set_error("bad argument"); return COPSE_EINVAL; }
+    std::lock_guard<std::mutex> g(S->mu);
+    S->mem_floor = floor;
+    return COPSE_OK;
+}
+
 extern "C" copse_status copse_server_pending(copse_server *S, size_t *queued, size_t *in_flight) {
     if (!S) { set_error("bad argument"); return COPSE_EINVAL; }
     std::lock_guard<std::mutex> g(S->mu);
     size_t fl = 0;
     for (ModelSlot &ms : S->models)
-        for (Buffer &b : ms.buf) fl += b.tickets.size();
+        for (int bi = 0; bi < ms.nbuf; bi++) fl += ms.buf[bi].tickets.size();
     if (queued) *queued = S->n_pending;
     if (in_flight) *in_flight = fl;
     return COPSE_OK;

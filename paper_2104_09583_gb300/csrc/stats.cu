@@ -16,10 +16,11 @@ struct Rec {
     std::string name;
     int ev;        // index of the event pair
     double bytes;  // algorithmic bytes of the launch
+    double ops;    // algorithmic modular products of the launch (0 = not counted)
 };
 struct Totals {
     uint64_t launches = 0;
-    double ms = 0, bytes = 0;
+    double ms = 0, bytes = 0, ops = 0;
 };
 
 std::mutex mu;
@@ -38,6 +39,7 @@ void drain() {
             t.launches++;
             t.ms += ms;
             t.bytes += r.bytes;
+            t.ops += r.ops;
         }
     }
     pending.clear();
@@ -51,7 +53,9 @@ void drain() {
 static thread_local bool suspended = false;
 void stats_suspend(bool on) { suspended = on; }
 
-int stats_begin(const char *name, double bytes, cudaStream_t s) {
+int stats_begin(const char *name, double bytes, cudaStream_t s) { return stats_begin_ops(name, bytes, 0.0, s); }
+
+int stats_begin_ops(const char *name, double bytes, double ops, cudaStream_t s) {
     if (!enabled || suspended) return -1;
     std::lock_guard<std::mutex> g(mu);
     if (used == pool.size()) {
@@ -61,7 +65,7 @@ int stats_begin(const char *name, double bytes, cudaStream_t s) {
     }
     int ev = (int)used++;
     cudaEventRecord(pool[ev].first, s);
-    pending.push_back(Rec{name, ev, bytes});
+    pending.push_back(Rec{name, ev, bytes, ops});
     return ev;
 }
 
@@ -102,6 +106,18 @@ extern "C" copse_status copse_stats_get(const char *name, uint64_t *launches, do
     if (launches) *launches = t.launches;
     if (ms) *ms = t.ms;
     if (bytes) *bytes = t.bytes;
+    return COPSE_OK;
+}
+
+extern "C" copse_status copse_stats_get_ops(const char *name, double *ops) {
+    if (!ops) { set_error("null output"); return COPSE_EINVAL; }
+    CUDA_TRY(cudaDeviceSynchronize());
+    std::lock_guard<std::mutex> g(mu);
+    drain();
+    double v = 0;
+    for (auto &kv : totals)
+        if (!name || !*name || kv.first == name) v += kv.second.ops;
+    *ops = v;
     return COPSE_OK;
 }
 

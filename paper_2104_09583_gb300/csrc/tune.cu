@@ -50,7 +50,7 @@ copse_status time_model(copse_ctx *c, copse_model *m, size_t nq, int reps, float
     copse_model_info info;
     STATUS_TRY(copse_model_info_get(m, &info));
     if (nq < 1) nq = 1;
-    nq = std::min<size_t>(nq, (size_t)c->N / info.block);
+    nq = std::min<size_t>(nq, (size_t)c->N / ((size_t)info.block * info.n_segments));
     Handles h;
     const copse_model *ms[1] = {m};
     STATUS_TRY(copse_keygen(c, 0x5eed, ms, 1, &h.k, &h.e));

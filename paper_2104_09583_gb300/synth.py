@@ -179,10 +179,11 @@ WORKLOADS = {
     # N = 2^14, 55-bit primes; 1 query
     "forest100-n16384": Workload("forest100-n16384", 14, 55, 10, 3,
                                  ((2001, 4, 5, 8, 8, 4, False, (90, 110)),), (1,)),
-    # encrypted model: 32 random trees of depth <= 8 (~4.5k branches, the query block fits a
-    # slot row of N = 2^15), 32 features, 16-bit, 10 classes; 16 primes; 64 queries
+    # encrypted model: 32 complete trees of depth 8 (8160 branches, 8192 leaves; the query
+    # spans both slot rows of N = 2^15 as two row segments of 16 trees), 32 features, 16-bit,
+    # 10 classes; 16 primes; 64 queries
     "encmodel32-n32768": Workload("encmodel32-n32768", 15, 55, 16, 3,
-                                  ((4001, 32, 8, 32, 16, 10, False, None),), (64,)),
+                                  ((4001, 32, 8, 32, 16, 10, True, None),), (64,)),
     # batching: 256 queries over three forests (1 x depth 3, 4 x depth 5, 16 x depth 6)
     "batch3-n16384": Workload("batch3-n16384", 14, 55, 10, 3,
                               ((3001, 1, 3, 8, 8, 4, True, None),

@@ -87,3 +87,28 @@ def test_admission_and_errors(served):
         assert e.value.name == "EINVAL"
     finally:
         K.copse_server_destroy(srv)
+
+
+def test_admission_by_device_memory(served):
+    """Creation measures every launch's device reservation; a submit is refused with EADMIT
+    while free device memory is below the admission floor and admitted again once the floor
+    is back within what the device holds."""
+    ctx, models, keys, evk, infos, trees, precs = served
+    srv = K.copse_server_create(ctx, keys, evk, models)
+    try:
+        reserved, launch_max, floor, launches = K.copse_server_memory(srv)
+        assert 0 < launch_max <= reserved and floor == launch_max
+        assert len(models) <= launches <= 2 * len(models)
+        free, total = torch.cuda.mem_get_info()
+        q = synth.random_queries(77, 1, infos[0]["n_features"], precs[0])[0]
+        K.copse_server_set_memory_floor(srv, total + 1)  # more than the device has: nothing fits
+        with pytest.raises(K.CopseError) as e:
+            K.copse_server_submit(srv, 0, q)
+        assert e.value.name == "EADMIT"
+        assert K.copse_server_pending(srv) == (0, 0)
+        K.copse_server_set_memory_floor(srv, launch_max)
+        t = K.copse_server_submit(srv, 0, q)
+        bits, _ = K.copse_server_poll(srv, t, infos[0]["n_leaves"])
+        assert bits.tolist() == Cp.classify_plain(trees[0], q)
+    finally:
+        K.copse_server_destroy(srv)
