@@ -472,6 +472,33 @@ copse_status copse_stats_get_ops(const char *name, double *ops);
 /* Newline-separated family names seen so far into buf[cap]. */
 copse_status copse_stats_names(char *buf, size_t cap);
 
+/* ---------------------------------------------------------------- work lists
+ * Many independent or chained elementwise ciphertext operations in one
+ * persistent launch: as many CTAs as the device holds at once take the items'
+ * tiles in list order; an item waits for the items it depends on, each wait
+ * bounded by timeout_ms of the GPU's global timer.  (The encrypted-threshold
+ * comparison leaves of Section 4.1.2 run through the same kernel.)  Item i's
+ * operands a, b index `in` (r < count(in)) or the outputs of earlier items
+ * (r = count(in) + j, j < i), all two-component ciphertexts at one level; its
+ * result is ciphertext i of the new buffer *out:
+ *   COPSE_WL_ADD a + b, COPSE_WL_SUB a - b, COPSE_WL_TENSOR the 3-component
+ *   product (a0 b0, a0 b1 + a1 b0, a1 b1) before relinearisation.
+ * An item waits for every earlier output it reads and, when dep >= 0, also for
+ * item dep.  A list that waits for an item that cannot finish (dep naming the
+ * item itself, or a later one that no running CTA reaches) runs into the limit:
+ * the launch stops and the call returns COPSE_ETIMEOUT (no buffer made; the
+ * context stays usable).  At most 256 items; timeout_ms >= 1.  Synchronous. */
+#define COPSE_WL_ADD 0
+#define COPSE_WL_SUB 1
+#define COPSE_WL_TENSOR 3
+typedef struct copse_wl_item {
+    uint32_t kind;
+    uint32_t a, b;  /* operands: index into `in`, or count(in) + an earlier item */
+    int32_t dep;    /* an item to wait for besides the outputs read, -1 none  */
+} copse_wl_item;
+copse_status copse_worklist_run(copse_ctx *ctx, const copse_ctbuf *in, const copse_wl_item *items, size_t n,
+                                int timeout_ms, copse_ctbuf **out, void *stream);
+
 /* ---------------------------------------------------------------- integer peaks
  * The roofline of integer kernels needs a measured rate of the modular
  * arithmetic they are made of, not a spec-sheet figure.  Register-only

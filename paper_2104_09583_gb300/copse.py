@@ -463,6 +463,23 @@ def copse_stats_get_ops(name=None):
     return v.value
 
 
+class copse_wl_item(C.Structure):
+    _fields_ = [("kind", C.c_uint32), ("a", C.c_uint32), ("b", C.c_uint32), ("dep", C.c_int32)]
+
+
+WL_KINDS = {"add": 0, "sub": 1, "tensor": 3}
+_lib.copse_worklist_run.restype = C.c_int
+_lib.copse_worklist_run.argtypes = [vp, vp, C.POINTER(copse_wl_item), C.c_size_t, C.c_int, pvp, vp]
+
+
+def copse_worklist_run(ctx, inbuf, items, timeout_ms=1000, stream=None):
+    """items: (kind, a, b, dep) with kind in WL_KINDS; returns the buffer of the items' results."""
+    arr = (copse_wl_item * max(1, len(items)))(*[copse_wl_item(WL_KINDS[k], a, b, d) for k, a, b, d in items])
+    h = C.c_void_p()
+    _check(_lib.copse_worklist_run(ctx, inbuf, arr, len(items), timeout_ms, C.byref(h), C.c_void_p(stream)))
+    return h
+
+
 INT_PEAK_KINDS = {"mac": 0, "butterfly": 1, "barrett": 2}
 
 

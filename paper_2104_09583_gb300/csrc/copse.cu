@@ -560,30 +560,65 @@ static copse_status seccomp(copse_ctx *c, const copse_evk *evk, copse_model *m, 
         STATUS_TRY(op_affine_many(c, lj, s));
     } else {
         // encrypted thresholds y: xy = x * y (every plane together), lt = y - xy,
-        // eq = 2 xy - (x + y) + 1; the sums of each plane on a forked side stream,
-        // joined back onto s (every free on s after the join)
-        std::vector<DCt> Y(p), XY((size_t)nct * p), tmp(2 * (size_t)nct * p);
+        // eq = 2 xy - (x + y) + 1, where a binary operation first switches its higher
+        // operand down (y and x + y to the level of xy).  The elementwise steps of every
+        // (query ciphertext, plane) run as items of persistent work-list launches.
+        const int top = x[0].level, ell = top - 1, N = c->N;
+        std::vector<DCt> Y(p), XY((size_t)nct * p), S((size_t)nct * p), Yd, Sd;
         std::vector<MulJob> mj;
         for (int k = 0; k < p; k++) STATUS_TRY(enc_materialize(c, *m->enc, m->enc->idx_thr(p - 1 - k), &Y[k], s));
         for (int q = 0; q < nct; q++)
             for (int k = 0; k < p; k++)
                 mj.push_back(MulJob{&x[(size_t)q * p + p - 1 - k], &Y[k], &XY[(size_t)q * p + k]});
         STATUS_TRY(op_mul_many(c, evk, mj, s));
-        for (int q = 0; q < nct; q++) {
-            STATUS_TRY(fork_begin(c, s, p, lane));
+        // y at the products' level, once per plane
+        std::vector<const DCt *> yp;
+        for (int k = 0; k < p; k++) yp.push_back(&Y[k]);
+        STATUS_TRY(op_modswitch_cts(c, yp, Yd, s));
+        // x + y at the top level, then switched down together
+        std::vector<WlItem> wl;
+        std::vector<const DCt *> sp;
+        for (int q = 0; q < nct; q++)
             for (int k = 0; k < p; k++) {
-                const cudaStream_t fs = fork_stream(c, k, lane);
                 const size_t j = (size_t)q * p + k;
-                DCt &two = tmp[2 * j], &sum = tmp[2 * j + 1];
-                STATUS_TRY(op_add(c, Y[k], XY[j], &nodes[q][k].lt, true, fs));
-                STATUS_TRY(op_add(c, XY[j], XY[j], &two, false, fs));
-                STATUS_TRY(op_add(c, x[(size_t)q * p + p - 1 - k], Y[k], &sum, false, fs));
-                STATUS_TRY(op_add(c, two, sum, &nodes[q][k].eq, true, fs));
-                STATUS_TRY(op_add_one(c, nodes[q][k].eq, fs));
+                const DCt &xi = x[(size_t)q * p + p - 1 - k];
+                if (xi.level != top || Y[k].level != top || XY[j].level != ell) {
+                    set_error("internal: unexpected levels in the comparison leaves");
+                    return COPSE_EINVAL;
+                }
+                STATUS_TRY(ct_alloc(c, &S[j], top, 2, s));
+                WlItem w;
+                w.kind = WL_ADD;
+                w.level = top;
+                w.comp = (size_t)top * N;
+                w.x = xi.data;
+                w.y = Y[k].data;
+                w.o0 = S[j].data;
+                wl.push_back(w);
+                sp.push_back(&S[j]);
             }
-            STATUS_TRY(fork_join(c, s, p, lane));
-        }
-        for (auto *v : {&Y, &XY, &tmp})
+        STATUS_TRY(worklist_run(c, wl, 1000, s));
+        STATUS_TRY(op_modswitch_cts(c, sp, Sd, s));
+        // the leaves: lt = y - xy, eq = 2 xy - (x + y) + 1
+        wl.clear();
+        for (int q = 0; q < nct; q++)
+            for (int k = 0; k < p; k++) {
+                const size_t j = (size_t)q * p + k;
+                STATUS_TRY(ct_alloc(c, &nodes[q][k].lt, ell, 2, s));
+                STATUS_TRY(ct_alloc(c, &nodes[q][k].eq, ell, 2, s));
+                WlItem w;
+                w.kind = WL_LEAF;
+                w.level = ell;
+                w.comp = (size_t)ell * N;
+                w.x = Sd[j].data;
+                w.y = Yd[k].data;
+                w.z = XY[j].data;
+                w.o0 = nodes[q][k].lt.data;
+                w.o1 = nodes[q][k].eq.data;
+                wl.push_back(w);
+            }
+        STATUS_TRY(worklist_run(c, wl, 1000, s));
+        for (auto *v : {&Y, &XY, &S, &Yd, &Sd})
             for (DCt &t : *v)
                 if (t.data) ct_free(&t, s);
     }

@@ -559,6 +559,23 @@ uint32_t model_leaves(const copse_model *m);
 uint32_t model_precision(const copse_model *m);
 int model_log_n(const copse_model *m);
 
+// ---------------------------------------------------------------- persistent work lists (worklist.cu)
+// Elementwise ciphertext operations walked by one resident launch (see worklist.cu).
+// Polynomials are [level][N] per component, `comp` words apart; dep / dep2 = items whose
+// every tile must be done first (-1 none).
+#define WL_MAX 256
+enum { WL_ADD = 0, WL_SUB = 1, WL_LEAF = 2, WL_TENSOR = 3 };
+struct WlItem {
+    int kind = WL_ADD, level = 0, dep = -1, dep2 = -1;
+    size_t comp = 0;
+    const u64 *x = nullptr, *y = nullptr, *z = nullptr;
+    u64 *o0 = nullptr, *o1 = nullptr;
+};
+// runs the items in launches of at most WL_MAX; d_status (3 + WL_MAX ints, may be null):
+// [1] = 1 if a wait ran out (the launches after it are skipped), [2] = that item
+copse_status worklist_run(copse_ctx *c, const std::vector<WlItem> &items, int timeout_ms, cudaStream_t s,
+                          int *d_status = nullptr);
+
 // coefficient-form export/import of one ciphertext (device scratch, host buffer)
 copse_status ct_to_coeff_host(copse_ctx *c, const DCt &ct, u64 *host, cudaStream_t s);
 copse_status ct_from_coeff_host(copse_ctx *c, const u64 *host, int level, DCt *out, cudaStream_t s);
