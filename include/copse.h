@@ -152,6 +152,20 @@ copse_status copse_model_rotations(const copse_model *model, uint32_t *reshuffle
 copse_status copse_model_set_bsgs(copse_model *model, uint32_t g_reshuffle, uint32_t g_level);
 copse_status copse_model_get_bsgs(const copse_model *model, uint32_t *g_reshuffle, uint32_t *g_level);
 
+/* Fused level matrices: Algorithm 1 multiplies Decisions by the reshuffling
+ * matrix R (Section 4.2.2), then Branches by each level matrix (Section 4.2.3).
+ * With on != 0 the two products are folded into one per level: F_k = S_k R
+ * with S_k = (1 - 2 Mask_k) Lvl_k the signed level matrix (XOR folded in), an
+ * L x q matrix with one entry per row, applied to Decisions by the diagonal
+ * method; the rotations of Decisions serve every level.  No Branches vector,
+ * no reshuffle key switches, one prime fewer (levels_used); the decrypted leaf
+ * bits are the same.  The baby-step size of copse_model_set_bsgs' g_reshuffle
+ * applies to these q-wide products (g_level is unused).  Plaintext model only
+ * (EINVAL with an encrypted-mode model).  Set before copse_keygen; drops the
+ * model's device copy when it changes. */
+copse_status copse_model_set_fused(copse_model *model, int on);
+int copse_model_is_fused(const copse_model *model);  /* 1 when fused, else 0 */
+
 /* Encrypted-model mode (Section 3.1's model owner Maurice is the data owner
  * Diane, Section 8.3): the threshold planes, every diagonal of the reshuffle
  * and level matrices, zero ones included, and the level masks are encrypted,
@@ -301,8 +315,8 @@ void copse_session_destroy(copse_session *session);
  * batching: requests that arrive while a launch is on the GPU join the next
  * one) and keeps up to two launches per model in flight.  Keys, model
  * plaintexts and the launches' device memory stay resident.  Admission is by
- * device memory: creation measures each launch's reservation (the drop in free
- * device memory when its graph is recorded and replayed once), gives a model
+ * device memory: creation measures each launch's reservation (the peak of
+ * graph-allocated device memory while its graph is replayed once), gives a model
  * its second concurrent launch only while free memory holds another such
  * reservation plus the admission floor, and fails with COPSE_EADMIT when not
  * even one launch per model fits.  A request is then admitted only while free

@@ -371,6 +371,32 @@ def mask_vector(m: Model, k: int) -> np.ndarray:
     return np.stack([_padded(sg.mask[k - 1][:, None], m.L, 1)[:, 0] for sg in m.segs])
 
 
+def fused_matrix(m: Model, k: int, sg: Model = None) -> np.ndarray:
+    """The reshuffle folded into level k (Algorithm 1 multiplies Decisions by R, then
+    Branches by Lvl_k; the product is associative): F_k = S_k R, S_k = (1 - 2 Mask_k) Lvl_k,
+    an L x q matrix with entries in {0, 1, -1}.  For a model in row segments, segment sg's."""
+    sg = sg or m
+    return ((1 - 2 * sg.mask[k - 1])[:, None] * sg.lvl[k - 1]) @ sg.R
+
+
+def fused_diagonal(m: Model, k: int, i: int, t: int) -> np.ndarray:
+    """Diagonal i < q of F_k, values mod t (per segment [n_seg, L] for row segments, each F
+    padded to L x q)."""
+    if m.n_seg == 1:
+        return generalized_diagonal(fused_matrix(m, k), i, m.L) % t
+    return np.stack([generalized_diagonal(_padded(fused_matrix(m, k, sg), m.L, m.q), i, m.L) % t for sg in m.segs])
+
+
+def fused_diagonals(m: Model, k: int, t: int):
+    """Nonzero diagonals of the fused level-k matrix F_k = S_k R."""
+    out = {}
+    for i in range(m.q):
+        dg = fused_diagonal(m, k, i, t)
+        if dg.any():
+            out[i] = dg
+    return out
+
+
 def reshuffle_diagonals(m: Model):
     """Nonzero diagonals of the extended reshuffle R_ext (rows L+b-1, row j = R[j mod b]):
     multiplying by it leaves the branch vector repeated with period b, ready for
@@ -426,9 +452,12 @@ def _rots(diag_sets, g, block):
     return r
 
 
-def rotation_sets(m: Model, g=(0, 0)):
+def rotation_sets(m: Model, g=(0, 0), fused=False):
     """Rotation amounts used by the reshuffle and by the level products (0 excluded);
-    g = (baby-step size of the reshuffle, of the levels), 0 = the plain diagonal method."""
+    g = (baby-step size of the reshuffle, of the levels), 0 = the plain diagonal method.
+    fused: the fused level products over Decisions only (baby-step size g[0])."""
+    if fused:
+        return [], sorted(_rots([fused_diagonals(m, k, 65537) for k in range(1, m.d + 1)], g[0], m.block))
     rs = _rots([reshuffle_diagonals(m)], g[0], m.block)
     ls = _rots([level_diagonals(m, k, 65537) for k in range(1, m.d + 1)], g[1], m.block)
     return sorted(rs), sorted(ls)
@@ -501,16 +530,21 @@ def matmul(E, v, diag_sets, add_vecs, m: Model, N: int, g: int = 0):
     return out
 
 
-def infer(E, m: Model, X, N: int, g=(0, 0), shuffle=None):
+def infer(E, m: Model, X, N: int, g=(0, 0), shuffle=None, fused=False):
     """Algorithm 1: SecComp, reshuffle, per-level product XOR mask, MultAll.
     Reading: the level products use Branches (the reshuffled vector, as the
     text of Section 4.3 says), not Decisions as the listing prints.
     g = (baby-step size of the reshuffle, of the levels); 0 = plain diagonal method.
-    shuffle = src of a label shuffle (shuffle_diagonals), applied to the result."""
+    shuffle = src of a label shuffle (shuffle_diagonals), applied to the result.
+    fused: each level's product taken with F_k = S_k R on Decisions (fused_matrix), baby-step
+    size g[0]; no Branches vector."""
     t = E.t
     Y = E.thresholds(m)
     D = seccomp(E, X, Y, m.precision)
-    if E.encrypted_model:
+    if fused:
+        Fd = [fused_diagonals(m, k, t) for k in range(1, m.d + 1)]
+        res = matmul(E, D, Fd, [tile_blocks(m, mask_vector(m, k), N) for k in range(1, m.d + 1)], m, N, g[0])
+    elif E.encrypted_model:
         em = E.enc_model
         Br = matmul_enc(E, D, [em["R"]], [None], em["g"][0])[0]
         res = matmul_enc(E, Br, em["levels"], em["masks"], em["g"][1])
@@ -774,8 +808,8 @@ class BgvEngine:
         return self.b.modswitch(a)
 
 
-def galois_elements(m: Model, logN: int, g=(0, 0)):
-    rs, ls = rotation_sets(m, g)
+def galois_elements(m: Model, logN: int, g=(0, 0), fused=False):
+    rs, ls = rotation_sets(m, g, fused)
     return sorted(set(B.galois_rot(logN, i) for i in rs + ls))
 
 
@@ -801,9 +835,10 @@ def decode_labels(m: Model, slots, n_queries: int, n_out: int = 0):
     return out
 
 
-def levels_needed(m: Model, encrypted_model=False, shuffle=False) -> int:
+def levels_needed(m: Model, encrypted_model=False, shuffle=False, fused=False) -> int:
     """Primes dropped by the circuit under the canonical policy (plaintext model):
-    1 (SecComp leaves) + ceil(log2 p) + 1 (reshuffle) + 1 (levels) + ceil(log2 d)."""
+    1 (SecComp leaves) + ceil(log2 p) + 1 (reshuffle) + 1 (levels) + ceil(log2 d);
+    the fused level products drop the reshuffle's prime."""
     def clog2(x):
         return (x - 1).bit_length() if x > 1 else 0
-    return (1 if not encrypted_model else 1) + clog2(m.precision) + 2 + clog2(m.d) + (1 if shuffle else 0)
+    return 1 + clog2(m.precision) + (1 if fused else 2) + clog2(m.d) + (1 if shuffle else 0)

@@ -69,6 +69,8 @@ _SIG = {
     "copse_tune_fused": (C.c_int, [vp, vp, u32p, C.c_size_t, C.c_size_t, C.c_int, C.POINTER(C.c_float),
                                    C.POINTER(C.c_uint32)]),
     "copse_model_set_encrypted": (C.c_int, [vp, C.c_int]),
+    "copse_model_set_fused": (C.c_int, [vp, C.c_int]),
+    "copse_model_is_fused": (C.c_int, [vp]),
     "copse_model_set_shuffle": (C.c_int, [vp, vp, C.c_size_t, vp]),
     "copse_model_codebook": (C.c_int, [vp, u32p]),
     "copse_model_is_encrypted": (C.c_int, [vp]),
@@ -219,6 +221,14 @@ def copse_model_codebook(m):
 
 def copse_model_set_encrypted(m, on=True):
     _check(_lib.copse_model_set_encrypted(m, 1 if on else 0))
+
+
+def copse_model_set_fused(m, on=True):
+    _check(_lib.copse_model_set_fused(m, 1 if on else 0))
+
+
+def copse_model_is_fused(m):
+    return bool(_lib.copse_model_is_fused(m))
 
 
 def copse_encrypt_model(ctx, keys, m, seed):

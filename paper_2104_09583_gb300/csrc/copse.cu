@@ -65,7 +65,7 @@ struct copse_model {
 // level of Algorithm 1's result before the shuffle: Branches at lvl_D - 1, the level
 // products drop one more prime, MultAll ceil(log2 d)
 static int result_level(const copse_ctx *c, const CompiledForest &f) {
-    return c->L - 1 - (int)clog2u(f.precision) - 2 - (int)clog2u(f.d);
+    return c->L - 1 - (int)clog2u(f.precision) - (f.fused ? 1 : 2) - (int)clog2u(f.d);
 }
 
 static copse_status upload_shuffle(copse_ctx *c, copse_model *m, cudaStream_t s) {
@@ -118,7 +118,7 @@ static copse_status upload_model(copse_ctx *c, copse_model *m, cudaStream_t s) {
         return n;
     };
     const size_t nR = count_pt(D->R.plan), nLv = count_pt(D->Lv.plan);
-    const size_t words = (nleaf * L + nR * (D->lvl_D + A) + nLv * (D->lvl_B + A) + f.d * D->lvl_B) * (size_t)N;
+    const size_t words = (nleaf * L + nR * (D->lvl_D + A) + nLv * (D->lvl_D + A) + f.d * D->lvl_D) * (size_t)N;
     CUDA_TRY(cudaMalloc(&D->store, std::max<size_t>(words, 1) * sizeof(u64)));
     u64 *cur = D->store;
     // SecComp leaf plaintexts over whole blocks (threshold bit 0 past the decisions)
@@ -182,6 +182,8 @@ static copse_status upload_model(copse_ctx *c, copse_model *m, cudaStream_t s) {
         if (a.giant + f.m1() > (uint32_t)B) { set_error("internal: shifted reshuffle diagonal leaves the block"); return COPSE_EINVAL; }
     for (const auto &a : D->Lv.plan.acc)
         if (a.giant + f.L > (uint32_t)B) { set_error("internal: shifted level diagonal leaves the block"); return COPSE_EINVAL; }
+    // fused level products (reshuffle folded in) act on Decisions, one level higher
+    const int lvl_lv = f.fused ? D->lvl_D : D->lvl_B;
     // reshuffle diagonals at the level of Decisions
     {
         std::vector<uint8_t> dg8;
@@ -193,17 +195,18 @@ static copse_status upload_model(copse_ctx *c, copse_model *m, cudaStream_t s) {
     // level diagonals (signed, mask folded in) and masks at the level of Branches
     {
         std::vector<uint64_t> dg64;
-        STATUS_TRY(encode_group(D->Lv, D->lvl_B, (int)f.L, [&](uint32_t k, uint32_t i, uint32_t sg, std::vector<uint32_t> &out) {
-            f.level_diagonal(k + 1, i, t, dg64, sg);
+        STATUS_TRY(encode_group(D->Lv, lvl_lv, (int)f.L, [&](uint32_t k, uint32_t i, uint32_t sg, std::vector<uint32_t> &out) {
+            if (f.fused) f.fused_diagonal(k + 1, i, t, dg64, sg);
+            else f.level_diagonal(k + 1, i, t, dg64, sg);
             out.assign(dg64.begin(), dg64.end());
         }));
         std::vector<uint32_t> mpat((size_t)f.d * SP, 0u);
         for (uint32_t k = 1; k <= f.d; k++) {
             for (int sg = 0; sg < NS; sg++)
                 for (uint32_t x = 0; x < f.L; x++) mpat[(size_t)(k - 1) * SP + (size_t)sg * B + x] = f.mask_at(k, x, (uint32_t)sg);
-            D->mask.push_back(cur + (size_t)(k - 1) * D->lvl_B * N);
+            D->mask.push_back(cur + (size_t)(k - 1) * lvl_lv * N);
         }
-        STATUS_TRY(encode_patterns(c, mpat, (int)f.d, SP, SP, D->lvl_B, 0, cur, s));
+        STATUS_TRY(encode_patterns(c, mpat, (int)f.d, SP, SP, lvl_lv, 0, cur, s));
     }
     CUDA_TRY(cudaStreamSynchronize(s));
     m->dev = std::move(D);
@@ -305,7 +308,10 @@ extern "C" copse_status copse_model_set_bsgs(copse_model *m, uint32_t g_reshuffl
             if (a.giant + rows > f.block) return false;
         return true;
     };
-    if (!fits(bsgs_group({f.rot_reshuffle}, g_reshuffle), f.m1()) || !fits(bsgs_group(f.lvl_nonzero, g_level), f.L)) {
+    const bool ok = f.fused ? fits(bsgs_group(f.fused_nonzero, g_reshuffle), f.L)
+                            : fits(bsgs_group({f.rot_reshuffle}, g_reshuffle), f.m1()) &&
+                                  fits(bsgs_group(f.lvl_nonzero, g_level), f.L);
+    if (!ok) {
         set_error("baby-step size moves a diagonal out of the query block");
         return COPSE_EINVAL;
     }
@@ -321,8 +327,27 @@ extern "C" copse_status copse_model_set_bsgs(copse_model *m, uint32_t g_reshuffl
     return COPSE_OK;
 }
 
+extern "C" copse_status copse_model_set_fused(copse_model *m, int on) {
+    if (!m) { set_error("null model"); return COPSE_EINVAL; }
+    CompiledForest &f = m->f;
+    if (on && f.encrypted) { set_error("fused level matrices are a plaintext-model option"); return COPSE_EINVAL; }
+    if (f.fused != (on != 0)) {
+        if (on && f.fused_nonzero.empty()) f.build_fused();
+        f.fused = on != 0;
+        if (m->dev || m->shuf) {
+            cudaDeviceSynchronize();
+            m->dev.reset();
+            m->shuf.reset();
+        }
+    }
+    return COPSE_OK;
+}
+
+extern "C" int copse_model_is_fused(const copse_model *m) { return m && m->f.fused ? 1 : 0; }
+
 extern "C" copse_status copse_model_set_encrypted(copse_model *m, int on) {
     if (!m) { set_error("null model"); return COPSE_EINVAL; }
+    if (on && m->f.fused) { set_error("the encrypted model keeps the reshuffle and level matrices apart (Table 1d)"); return COPSE_EINVAL; }
     if (m->f.encrypted != (on != 0)) {
         m->f.encrypted = on != 0;
         if (m->dev || m->enc) {
@@ -681,6 +706,11 @@ static copse_status seccomp(copse_ctx *c, const copse_evk *evk, copse_model *m, 
 // ciphertext after another): one result ciphertext per query ciphertext.  With an
 // encrypted model the matrix products of all query ciphertexts run together, so
 // each encrypted diagonal is read and its mask regenerated once for all of them.
+template <class Mark>
+static copse_status aggregate(copse_ctx *c, const copse_evk *evk, copse_model *m,
+                              std::vector<std::vector<DCt>> &lvs, int nct, std::vector<DCt> &results, cudaStream_t s,
+                              Mark &mark);
+
 static copse_status infer_multi(copse_ctx *c, const copse_evk *evk, copse_model *m, const copse_ctbuf *feats,
                                 std::vector<DCt> &results, cudaStream_t s, int lane = 0,
                                 cudaEvent_t *stage_ev = nullptr) {
@@ -713,6 +743,15 @@ static copse_status infer_multi(copse_ctx *c, const copse_evk *evk, copse_model 
     std::vector<DCt> Dc;
     STATUS_TRY(seccomp(c, evk, m, feats->cts.data(), nct, Dc, s, lane));
     STATUS_TRY(mark(1));
+    std::vector<std::vector<DCt>> lvs(nct);
+    if (m->f.fused) {
+        // fused level products: (S_k R) * Decisions XOR Mask_k, no Branches vector
+        STATUS_TRY(mark(2));
+        for (int q = 0; q < nct; q++) STATUS_TRY(group_matmul(c, evk, Dc[q], D->Lv, D->mask, lvs[q], s));
+        for (DCt &x : Dc) ct_free(&x, s);
+        STATUS_TRY(mark(3));
+        return aggregate(c, evk, m, lvs, nct, results, s, mark);
+    }
     // reshuffle: Branches = R_ext * Decisions
     std::vector<std::vector<DCt>> br(nct);
     if (enc) {
@@ -723,7 +762,6 @@ static copse_status infer_multi(copse_ctx *c, const copse_evk *evk, copse_model 
     for (DCt &x : Dc) ct_free(&x, s);
     STATUS_TRY(mark(2));
     // levels: Lvl_k * Branches XOR Mask_k, rotations of Branches shared by every level
-    std::vector<std::vector<DCt>> lvs(nct);
     std::vector<DCt> B(nct);
     for (int q = 0; q < nct; q++) B[q] = br[q][0];
     if (enc) {
@@ -733,6 +771,14 @@ static copse_status infer_multi(copse_ctx *c, const copse_evk *evk, copse_model 
     }
     for (DCt &x : B) ct_free(&x, s);
     STATUS_TRY(mark(3));
+    return aggregate(c, evk, m, lvs, nct, results, s, mark);
+}
+
+// product across levels (MultAll), then the optional label shuffle; stage mark 4 at the end
+template <class Mark>
+static copse_status aggregate(copse_ctx *c, const copse_evk *evk, copse_model *m,
+                              std::vector<std::vector<DCt>> &lvs, int nct, std::vector<DCt> &results, cudaStream_t s,
+                              Mark &mark) {
     // product across levels, balanced; the products of every query ciphertext at one
     // tree level run together
     while (lvs[0].size() > 1) {

@@ -65,7 +65,47 @@ uint32_t clog2(uint32_t x) {
 }  // namespace
 
 uint32_t CompiledForest::levels_used() const {
-    return 1 + clog2(precision) + 2 + clog2(d) + (shuffle_src.empty() ? 0 : 1);
+    return 1 + clog2(precision) + (fused ? 1 : 2) + clog2(d) + (shuffle_src.empty() ? 0 : 1);
+}
+
+void CompiledForest::build_fused() {
+    for (uint32_t sgi = 0; sgi < n_seg; sgi++) {
+        CompiledForest &P = n_seg > 1 ? seg[sgi] : *this;
+        std::vector<int32_t> slot_of(P.b, -1);
+        for (uint32_t j = 0; j < q; j++)
+            if (P.slot_branch[j] >= 0) slot_of[P.slot_branch[j]] = (int32_t)j;
+        P.fslot.assign((size_t)d * P.L, -1);
+        for (uint32_t k = 1; k <= d; k++)
+            for (uint32_t x = 0; x < P.L; x++) {
+                const uint8_t *row = &P.lvl[((size_t)(k - 1) * P.L + x) * P.b];
+                for (uint32_t j = 0; j < P.b; j++)
+                    if (row[j]) { P.fslot[(size_t)(k - 1) * P.L + x] = slot_of[j]; break; }
+            }
+    }
+    fused_nonzero.assign(d, {});
+    for (uint32_t k = 1; k <= d; k++) {
+        std::vector<char> nz(q, 0);
+        for (uint32_t sgi = 0; sgi < n_seg; sgi++) {
+            const CompiledForest &P = part(sgi);
+            for (uint32_t x = 0; x < P.L; x++) {
+                const int32_t c = P.fslot[(size_t)(k - 1) * P.L + x];
+                if (c >= 0) nz[((uint32_t)c + q - x % q) % q] = 1;
+            }
+        }
+        for (uint32_t i = 0; i < q; i++)
+            if (nz[i]) fused_nonzero[k - 1].push_back(i);
+    }
+}
+
+void CompiledForest::fused_diagonal(uint32_t k, uint32_t i, uint64_t t, std::vector<uint64_t> &out,
+                                    uint32_t s) const {
+    const CompiledForest &P = part(s);
+    out.assign(L, 0);
+    for (uint32_t x = 0; x < P.L; x++) {
+        const int32_t c = P.fslot[(size_t)(k - 1) * P.L + x];
+        if (c < 0 || (x + i) % q != (uint32_t)c) continue;
+        out[x] = P.mask[(size_t)(k - 1) * P.L + x] ? t - 1 : 1;  // (1 - 2 mask) * entry, mod t
+    }
 }
 
 uint32_t CompiledForest::thr_bit(uint32_t s, uint32_t x, uint32_t i) const {
@@ -384,6 +424,7 @@ void CompiledForest::shuffle_diagonal(uint32_t amount, std::vector<uint32_t> &ou
 }
 
 BsgsGroup CompiledForest::group_reshuffle() const {
+    if (fused) return BsgsGroup();  // no reshuffle product: folded into the level matrices
     if (!encrypted) return bsgs_group({rot_reshuffle}, g_reshuffle);
     std::vector<uint32_t> all(q);
     for (uint32_t i = 0; i < q; i++) all[i] = i;
@@ -391,6 +432,7 @@ BsgsGroup CompiledForest::group_reshuffle() const {
 }
 
 BsgsGroup CompiledForest::group_level() const {
+    if (fused) return bsgs_group(fused_nonzero, g_reshuffle);
     if (!encrypted) return bsgs_group(lvl_nonzero, g_level);
     std::vector<uint32_t> all(b);
     for (uint32_t i = 0; i < b; i++) all[i] = i;

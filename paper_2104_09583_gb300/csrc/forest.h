@@ -101,6 +101,18 @@ struct CompiledForest {
     void level_diagonal(uint32_t k, uint32_t i, uint64_t t, std::vector<uint64_t> &out, uint32_t s = 0) const;
     // level-k mask at block-local slot x of segment s's block (0 past the segment's leaves)
     uint32_t mask_at(uint32_t k, uint32_t x, uint32_t s) const;
+
+    // Fused level products: the reshuffle folded into every level matrix, F_k = S_k R with
+    // S_k = (1 - 2 Mask_k) Lvl_k (L x q, entries 0 / +-1): one product per level over the
+    // rotations of Decisions, no Branches vector and one prime fewer.  Row x of F_k holds
+    // its one nonzero at the padded slot of the branch Lvl_k picks for leaf x.  Plaintext
+    // model only; the plan's baby-step size is g_reshuffle (the products are q wide).
+    bool fused = false;
+    std::vector<int32_t> fslot;                        // [d][L]: that slot, -1 = empty row
+    std::vector<std::vector<uint32_t>> fused_nonzero;  // per level: nonzero diagonals of F_k
+    void build_fused();                                // fslot of every part, fused_nonzero
+    // signed diagonal i < q of segment s's F_k, values {0, 1, t-1}; L rows, block-local
+    void fused_diagonal(uint32_t k, uint32_t i, uint64_t t, std::vector<uint64_t> &out, uint32_t s = 0) const;
 };
 
 // 0 on success; otherwise a COPSE_E* code and a message in `err`.

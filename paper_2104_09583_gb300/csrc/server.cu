@@ -5,8 +5,8 @@
 // next one), runs up to two launches per model concurrently on their own
 // streams, and completes tickets as launches finish.  Evaluation keys,
 // model plaintexts and the graphs' memory stay on the device.  Admission is by
-// device memory: at creation every launch's reservation is measured (the drop
-// in free device memory when its graph is recorded and replayed once), a
+// device memory: at creation every launch's reservation is measured (the high-
+// water mark of graph-allocated memory while its graph is replayed once), a
 // model gets its second concurrent launch only if free memory still holds
 // another such reservation plus the admission floor, and creation fails with
 // COPSE_EADMIT if even one launch per model does not fit.  While running, a
@@ -181,6 +181,9 @@ extern "C" copse_status copse_server_create(copse_ctx *c, const copse_keys *keys
             CUDA_TRY(cudaMemGetInfo(&free0, &total));
             if (round == 1 && free0 < S->launch_max + S->launch_max / 8 + S->launch_max) continue;
             Buffer &b = ms.buf[round];
+            // the graph's own peak allocation: reset the device's graph-memory high-water mark
+            uint64_t zero = 0;
+            CUDA_TRY(cudaDeviceSetGraphMemAttribute(c->device, cudaGraphMemAttrUsedMemHigh, &zero));
             copse_status st = copse_session_create(c, keys, evk, ms.m, ms.per_ct, &b.sess);
             if (st) {
                 if (st == COPSE_ENOMEM || st == COPSE_ECUDA) {
@@ -206,9 +209,9 @@ extern "C" copse_status copse_server_create(copse_ctx *c, const copse_keys *keys
                 if (!st) set_error("server warm-up launch failed");
                 return cleanup(st ? st : COPSE_ECUDA);
             }
-            size_t free1 = 0;
-            CUDA_TRY(cudaMemGetInfo(&free1, &total));
-            const size_t used = free0 > free1 ? free0 - free1 : 0;
+            uint64_t high = 0;
+            CUDA_TRY(cudaDeviceGetGraphMemAttribute(c->device, cudaGraphMemAttrUsedMemHigh, &high));
+            const size_t used = (size_t)high;
             S->reserved += used;
             S->launch_max = std::max(S->launch_max, used);
             ms.nbuf = round + 1;
