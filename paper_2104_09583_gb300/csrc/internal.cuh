@@ -244,6 +244,7 @@ struct copse_ctx {
     // batches of more residue polynomials than this take the two-launch form (autotuned)
     long ntt_cluster_max = 1L << 30;
     long ntt_fused_max = 1L << 30;    // the same crossover for the transforms fused with base conversions
+    bool ntt_cluster16 = false;       // N = 2^15: the device places 16-CTA clusters (non-portable size)
 
     int ext_prime(int ell, int r) const { return r < ell ? r : L + (r - ell); }
     int t_index() const { return L + alpha; }
@@ -364,7 +365,7 @@ struct MddFuse {
 };
 copse_status ntt_forward_moddown_drop(copse_ctx *ctx, const MddFuse &f, int npoly, cudaStream_t s, bool *done);
 copse_status moddown_drop_unfused(copse_ctx *ctx, const MddFuse &f, int npoly, cudaStream_t s);
-// The fused forms run on the cluster transform (2^12 <= N <= 2^14); *done = false
+// The fused forms run on the cluster transform (2^12 <= N <= 2^15); *done = false
 // (nothing launched) otherwise, and the caller takes the unfused sequence.
 copse_status ntt_forward_modswitch(copse_ctx *ctx, const MsFuse &f, int nc, cudaStream_t s, bool *done);
 copse_status ntt_forward_moddown(copse_ctx *ctx, const MdFuse &f, int njobs, cudaStream_t s, bool *done);

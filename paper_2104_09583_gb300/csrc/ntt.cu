@@ -354,7 +354,7 @@ __global__ void __launch_bounds__(NT2) k_ntt_inv_cols(NttBatch b, const PrimeDev
 }
 
 // ---------------------------------------------------------------- one launch per transform (clusters)
-// For 2^12 <= N <= 2^14 a thread-block cluster of CL = N / 2048 CTAs owns one
+// For 2^12 <= N <= 2^15 a thread-block cluster of CL = N / 2048 CTAs owns one
 // residue polynomial.  Each CTA runs the column stages on its column tile;
 // after a cluster barrier it gathers its row tile from the other CTAs' shared
 // memory (distributed shared memory), a second barrier keeps every tile alive
@@ -572,7 +572,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT2)
     const int rank = (int)cl.block_rank();
     // the cluster size fixes the ring degree (CL x 2048 coefficients): every tile shape is a
     // compile-time constant, so the radix-4 passes and their index arithmetic unroll
-    constexpr int logN = CL == 2 ? 12 : (CL == 4 ? 13 : 14), a = logN / 2;
+    constexpr int logN = CL == 2 ? 12 : (CL == 4 ? 13 : (CL == 8 ? 14 : 15)), a = logN / 2;
     constexpr int lb = logN - a, N2 = 1 << lb, lc = 11 - a, C = 1 << lc, lr = 11 - lb;
     const int pr = blockIdx.x / CL;
     const int p = pr / b.nr, r = b.r0 + pr % b.nr;
@@ -629,7 +629,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT2)
     ClusterSmem &S = *reinterpret_cast<ClusterSmem *>(dyn_smem);
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
-    constexpr int logN = CL == 2 ? 12 : (CL == 4 ? 13 : 14), a = logN / 2;
+    constexpr int logN = CL == 2 ? 12 : (CL == 4 ? 13 : (CL == 8 ? 14 : 15)), a = logN / 2;
     constexpr int lb = logN - a, lc = 11 - a, C = 1 << lc, lr = 11 - lb, R = 1 << lr;
     const int pr = blockIdx.x / CL;
     const int p = pr / b.nr, r = b.r0 + pr % b.nr;
@@ -684,13 +684,22 @@ inline void attr_done(std::atomic<uint64_t> &mask, int device) {
     if (device >= 0 && device < 64) mask.fetch_or(1ull << device, std::memory_order_release);
 }
 
+// the dynamic shared-memory limit, and for 16-CTA clusters (N = 2^15) the opt-in to a
+// cluster size above the portable 8
+template <class K>
+copse_status cluster_attrs(K kernel, int cl) {
+    CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ClusterSmem)));
+    if (cl > 8) CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    return COPSE_OK;
+}
+
 template <int CL>
 copse_status launch_cluster(copse_ctx *ctx, const NttBatch &b, cudaStream_t s, bool inverse, double bytes) {
     static std::atomic<uint64_t> attr_devices{0};
     const int smem = (int)sizeof(ClusterSmem);
     if (attr_pending(attr_devices, ctx->device)) {
-        CUDA_TRY(cudaFuncSetAttribute(k_ntt_fwd_cluster<CL, PlainIO>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        CUDA_TRY(cudaFuncSetAttribute(k_ntt_inv_cluster<CL, PlainIO>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        STATUS_TRY(cluster_attrs(k_ntt_fwd_cluster<CL, PlainIO>, CL));
+        STATUS_TRY(cluster_attrs(k_ntt_inv_cluster<CL, PlainIO>, CL));
         attr_done(attr_devices, ctx->device);
     }
     const unsigned grid = (unsigned)b.npoly * (unsigned)b.nr * CL;
@@ -719,6 +728,7 @@ copse_status launch(copse_ctx *ctx, const NttBatch &b, cudaStream_t s, bool inve
         if (logN == 12) return launch_cluster<2>(ctx, b, s, inverse, bytes);
         if (logN == 13) return launch_cluster<4>(ctx, b, s, inverse, bytes);
         if (logN == 14) return launch_cluster<8>(ctx, b, s, inverse, bytes);
+        if (logN == 15 && ctx->ntt_cluster16) return launch_cluster<16>(ctx, b, s, inverse, bytes);
     }
     if (logN >= 12) {
         const int a = logN / 2;  // column length 2^a, row length 2^(logN - a)
@@ -765,9 +775,9 @@ copse_status launch_cluster_io(copse_ctx *ctx, const NttBatch &b, const IO &io, 
     const int smem = (int)sizeof(ClusterSmem);
     if (attr_pending(attr_devices, ctx->device)) {
         if (INV)
-            CUDA_TRY(cudaFuncSetAttribute(k_ntt_inv_cluster<CL, IO>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+            STATUS_TRY(cluster_attrs(k_ntt_inv_cluster<CL, IO>, CL));
         else
-            CUDA_TRY(cudaFuncSetAttribute(k_ntt_fwd_cluster<CL, IO>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+            STATUS_TRY(cluster_attrs(k_ntt_fwd_cluster<CL, IO>, CL));
         attr_done(attr_devices, ctx->device);
     }
     const unsigned grid = (unsigned)b.npoly * (unsigned)b.nr * CL;
@@ -794,6 +804,7 @@ copse_status launch_fused(copse_ctx *ctx, const NttBatch &b, const IO &io, cudaS
     if (ctx->logN == 12) STATUS_TRY((launch_cluster_io<2, INV, IO>(ctx, b, io, s)));
     else if (ctx->logN == 13) STATUS_TRY((launch_cluster_io<4, INV, IO>(ctx, b, io, s)));
     else if (ctx->logN == 14) STATUS_TRY((launch_cluster_io<8, INV, IO>(ctx, b, io, s)));
+    else if (ctx->logN == 15 && ctx->ntt_cluster16) STATUS_TRY((launch_cluster_io<16, INV, IO>(ctx, b, io, s)));
     else return COPSE_OK;
     *done = true;
     return COPSE_OK;
@@ -877,6 +888,26 @@ __global__ void k_stage_tw(const u64 *W, const u64 *Wp, u64 *out, int np, int lo
 
 copse_status ntt_stage_tables(copse_ctx *ctx) {
     if (ctx->logN < 12) return COPSE_OK;   // one CTA per transform below 2^12: nothing staged
+    if (ctx->logN == 15) {
+        // 16-CTA clusters are above the portable size: use them only where the device
+        // can place at least one (otherwise N = 2^15 keeps the two-launch transforms)
+        STATUS_TRY(cluster_attrs(k_ntt_fwd_cluster<16, PlainIO>, 16));
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3(16);
+        cfg.blockDim = dim3(NT2);
+        cfg.dynamicSmemBytes = sizeof(ClusterSmem);
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = 16;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int nclusters = 0;
+        const cudaError_t e = cudaOccupancyMaxActiveClusters(&nclusters, k_ntt_fwd_cluster<16, PlainIO>, &cfg);
+        ctx->ntt_cluster16 = e == cudaSuccess && nclusters > 0;
+        cudaGetLastError();
+    }
     const size_t n = (size_t)ctx->NP * ctx->N;  // NP x (N / TILE) x TILE entries
     for (int inv = 0; inv < 2; inv++) {
         void *p = nullptr;

@@ -155,6 +155,33 @@ __global__ void k_modup(const u64 *x, const u64 *x_ntt, size_t xs, u64 *y, int e
     }
 }
 
+// sum_j y_j * k_j over the nd key-switching digits of one element and both key
+// components: exact split-28 products summed lazily and reduced once when every residue
+// is below 2^55 (split), Barrett products otherwise.  yh: digit j's value at
+// yh[j * ystride]; key component c of digit j at key[(2 j + c) * kstride].
+__device__ __forceinline__ void ks_dot(const u64 *yh, size_t ystride, const u64 *key, size_t kstride, int nd,
+                                       bool split, const PrimeDev &P, u64 &o0, u64 &o1) {
+    if (split) {
+        Acc3w a0{0, 0, 0}, a1{0, 0, 0};
+        for (int j = 0; j < nd; j++) {
+            const Sp28 y = split28(yh[(size_t)j * ystride]);
+            mac_sp(a0, y, split28(key[(size_t)(2 * j) * kstride]));
+            mac_sp(a1, y, split28(key[(size_t)(2 * j + 1) * kstride]));
+        }
+        o0 = reduce128(acc3w_value(a0), P);
+        o1 = reduce128(acc3w_value(a1), P);
+        return;
+    }
+    u64 s0 = 0, s1 = 0;
+    for (int j = 0; j < nd; j++) {
+        const u64 y = yh[(size_t)j * ystride];
+        s0 = add_mod(s0, mul_mod(y, key[(size_t)(2 * j) * kstride], P), P.q);
+        s1 = add_mod(s1, mul_mod(y, key[(size_t)(2 * j + 1) * kstride], P), P.q);
+    }
+    o0 = s0;
+    o1 = s1;
+}
+
 struct InnerJob {
     const u64 *ksk;          // [ndig][2][L+alpha][N]
     u64 *out;                // [2][ell+alpha][N]
@@ -170,7 +197,7 @@ struct InnerJobs {
 
 // (u0, u1)[r][n] = sum_j yhat[j][r][tau_g n] * ksk[j][c][ext_prime(r)][n]
 __global__ void k_ks_inner(const u64 *yhat, const InnerJobs jobs, int ell, int alpha, int L, int logN,
-                           const PrimeDev *pr, const u64 *mdP, size_t kw) {
+                           const PrimeDev *pr, const u64 *mdP, bool split) {
     const int N = 1 << logN;
     const int nx = ell + alpha, nd = (ell + alpha - 1) / alpha;
     const int NB = L + alpha;
@@ -183,14 +210,9 @@ __global__ void k_ks_inner(const u64 *yhat, const InnerJobs jobs, int ell, int a
     const PrimeDev P = pr[g];
     const uint32_t src = J.g == 1 ? n : galois_src(n, J.g, logN);
     const u64 *yh = J.y ? J.y : yhat;
-    u64 acc0 = 0, acc1 = 0;
-    for (int j = 0; j < nd; j++) {
-        const u64 y = yh[(((size_t)j * nx + r) << logN) + src];
-        const u64 *k0 = J.ksk + (((size_t)(2 * j) * NB + g) << logN);
-        const u64 *k1 = J.ksk + (((size_t)(2 * j + 1) * NB + g) << logN);
-        acc0 = add_mod(acc0, mul_shoup(y, k0[n], k0[kw + n], P.q), P.q);
-        acc1 = add_mod(acc1, mul_shoup(y, k1[n], k1[kw + n], P.q), P.q);
-    }
+    u64 acc0, acc1;
+    ks_dot(yh + ((size_t)r << logN) + src, (size_t)nx << logN, J.ksk + ((size_t)g << logN) + n, (size_t)NB << logN,
+           nd, split, P, acc0, acc1);
     if (J.pd && r < ell) {
         const u64 Pm = mdP[r];
         acc0 = add_mod(acc0, mul_mod(Pm, J.pd[((size_t)r << logN) + n], P), P.q);
@@ -254,7 +276,7 @@ struct MmTable {
 template <int NA>
 __global__ void __launch_bounds__(256) k_mm_fused(const u64 *yhat, const u64 *c0, int nrot, const MmTable tab,
                                                   size_t part_stride, int ell, int alpha, int L, int logN,
-                                                  const PrimeDev *pr, KsTables T, size_t kw) {
+                                                  const PrimeDev *pr, KsTables T, bool split) {
     const int N = 1 << logN;
     const int nx = ell + alpha, nd = (ell + alpha - 1) / alpha, NB = L + alpha;
     const size_t n_el = (size_t)nx << logN;
@@ -285,13 +307,8 @@ __global__ void __launch_bounds__(256) k_mm_fused(const u64 *yhat, const u64 *c0
             u1 = J.R[n_el + e];
         } else {
             const uint32_t src = galois_src(n, J.g, logN);
-            for (int j = 0; j < nd; j++) {
-                const u64 y = yhat[(((size_t)j * nx + r) << logN) + src];
-                const u64 *k0 = J.ksk + (((size_t)(2 * j) * NB + g) << logN);
-                const u64 *k1 = J.ksk + (((size_t)(2 * j + 1) * NB + g) << logN);
-                u0 = add_mod(u0, mul_shoup(y, k0[n], k0[kw + n], P.q), P.q);
-                u1 = add_mod(u1, mul_shoup(y, k1[n], k1[kw + n], P.q), P.q);
-            }
+            ks_dot(yhat + ((size_t)r << logN) + src, (size_t)nx << logN, J.ksk + ((size_t)g << logN) + n,
+                   (size_t)NB << logN, nd, split, P, u0, u1);
             if (r < ell) u0 = add_mod(u0, mul_mod(Pm, c0[((size_t)r << logN) + src], P), P.q);
         }
 #pragma unroll
@@ -381,7 +398,7 @@ struct RsTable {
 };
 
 __global__ void __launch_bounds__(256) k_rotsum(const RsTable tab, int nterm, u64 *acc, int ell, int alpha, int L,
-                                                int logN, const PrimeDev *pr, KsTables T, size_t kw) {
+                                                int logN, const PrimeDev *pr, KsTables T, bool split) {
     const int N = 1 << logN;
     const int nx = ell + alpha, nd = (ell + alpha - 1) / alpha, NB = L + alpha;
     const size_t n_el = (size_t)nx << logN;
@@ -396,13 +413,11 @@ __global__ void __launch_bounds__(256) k_rotsum(const RsTable tab, int nterm, u6
     for (int k = 0; k < nterm; k++) {
         const RsTerm J = tab.t[k];
         const uint32_t src = galois_src(n, J.g, logN);
-        for (int j = 0; j < nd; j++) {
-            const u64 y = J.yhat[(((size_t)j * nx + r) << logN) + src];
-            const u64 *k0 = J.ksk + (((size_t)(2 * j) * NB + g) << logN);
-            const u64 *k1 = J.ksk + (((size_t)(2 * j + 1) * NB + g) << logN);
-            a0 = add_mod(a0, mul_shoup(y, k0[n], k0[kw + n], P.q), P.q);
-            a1 = add_mod(a1, mul_shoup(y, k1[n], k1[kw + n], P.q), P.q);
-        }
+        u64 t0, t1;
+        ks_dot(J.yhat + ((size_t)r << logN) + src, (size_t)nx << logN, J.ksk + ((size_t)g << logN) + n,
+               (size_t)NB << logN, nd, split, P, t0, t1);
+        a0 = add_mod(a0, t0, P.q);
+        a1 = add_mod(a1, t1, P.q);
         if (r < ell) a0 = add_mod(a0, mul_mod(Pm, J.c0[((size_t)r << logN) + src], P), P.q);
     }
     acc[e] = a0;
@@ -731,7 +746,12 @@ copse_status ks_apply(copse_ctx *c, const u64 *yhat, int ell, const std::vector<
     InnerJobs jobs;
     for (int i = 0; i < nj; i++) jobs.j[i] = jobs_h[i];
     dim3 grid(nblk((size_t)nx * N), nj);
-    TIMED("ks_inner", 8.0 * N * ((double)((ell + A - 1) / A) * nx + (double)nj * (4.0 * ((ell + A - 1) / A) * nx + 2.0 * nx)), s, k_ks_inner<<<grid, TPB, 0, s>>>(yhat, jobs, ell, A, c->L, c->logN, c->d_prime, c->ks.md_P, ksk_words(c)));
+    const int ndg = (ell + A - 1) / A;
+    // algorithmic bytes: the digits once, per job the two key components of every digit and
+    // the output; products: two per digit and element
+    TIMED_OPS("ks_inner", 8.0 * N * ((double)ndg * nx + (double)nj * (2.0 * ndg * nx + 2.0 * nx)),
+              2.0 * N * (double)nj * ndg * nx, s,
+              k_ks_inner<<<grid, TPB, 0, s>>>(yhat, jobs, ell, A, c->L, c->logN, c->d_prime, c->ks.md_P, c->bits <= 55));
     LAUNCH_CHECK();
     return moddown_apply(c, U, ell, nj, f, sc, s);
 }
@@ -933,9 +953,9 @@ static copse_status mul_group(copse_ctx *c, const copse_evk *evk, const std::vec
     InnerJobs ij;
     for (int k = 0; k < nj; k++)
         ij.j[k] = InnerJob{evk->rlk, U + (size_t)k * 2 * nx * N, 1, yhat + (size_t)k * nd * nx * N, d + (size_t)k * per3};
-    TIMED("ks_inner", 8.0 * N * nj * (5.0 * nd * nx + 2.0 * nx + 2.0 * ell), s,
-          k_ks_inner<<<dim3(nblk((size_t)nx * N), nj), TPB, 0, s>>>(yhat, ij, ell, A, c->L, c->logN, c->d_prime,
-                                                                     c->ks.md_P, ksk_words(c)));
+    TIMED_OPS("ks_inner", 8.0 * N * nj * (3.0 * nd * nx + 2.0 * nx + 2.0 * ell), 2.0 * N * (double)nj * nd * nx, s,
+              k_ks_inner<<<dim3(nblk((size_t)nx * N), nj), TPB, 0, s>>>(yhat, ij, ell, A, c->L, c->logN, c->d_prime,
+                                                                         c->ks.md_P, c->bits <= 55));
     LAUNCH_CHECK();
     // the dropped prime's and the special residues to coefficients, then the fused
     // conversion + transform + finish (or conversion, transform, finish)
@@ -1161,9 +1181,9 @@ copse_status op_matmul(copse_ctx *c, const copse_evk *evk, const DCt &v, const s
                     const int r = ks_idx[k0 + i];
                     jobs.j[i] = InnerJob{evk->find(gal[r]), Rall + (k0 + i) * ext, gal[r], nullptr, nullptr, v.data};
                 }
-                TIMED("ks_inner", 8.0 * N * nj * (4.0 * nd * nx + 2.0 * nx + ell), s,
-                      k_ks_inner<<<dim3(nblk((size_t)nx * N), nj), TPB, 0, s>>>(yhat, jobs, ell, A, c->L, c->logN,
-                                                                                 c->d_prime, c->ks.md_P, ksk_words(c)));
+                TIMED_OPS("ks_inner", 8.0 * N * nj * (2.0 * nd * nx + 2.0 * nx + ell), 2.0 * N * (double)nj * nd * nx, s,
+                          k_ks_inner<<<dim3(nblk((size_t)nx * N), nj), TPB, 0, s>>>(yhat, jobs, ell, A, c->L, c->logN,
+                                                                                     c->d_prime, c->ks.md_P, c->bits <= 55));
                 LAUNCH_CHECK();
             }
         }
@@ -1183,12 +1203,11 @@ copse_status op_matmul(copse_ctx *c, const copse_evk *evk, const DCt &v, const s
                     }
                 }
                 for (int a = 0; a < na; a++) tab.acc[a] = part + (size_t)(a0 + a) * ext;
-                // algorithmic bytes: keys with their Shoup companions, diagonals, accumulators
-                // in and out, the rotated digits and c0 once
-                // (with R_k precomputed: R_k in place of the keys, digits and c0)
+                // algorithmic bytes: keys, diagonals, accumulators in and out, the rotated
+                // digits and c0 once (with R_k precomputed: R_k in place of the keys, digits and c0)
                 const double bytes = 8.0 * N * (nz_pt * (double)nx + 4.0 * na * nx * parts +
                                                 (Rall ? (double)nr * 2 * nx
-                                                      : (double)nr * 4 * nd * nx + (double)nd * nx + ell));
+                                                      : (double)nr * 2 * nd * nx + (double)nd * nx + ell));
                 const dim3 grid(nblk((size_t)nx * N), parts);
 #define MM_CASE(K)                                                                                        \
     case K:                                                                                               \
@@ -1198,7 +1217,7 @@ copse_status op_matmul(copse_ctx *c, const copse_evk *evk, const DCt &v, const s
         else                                                                                              \
             TIMED("mm_fused", bytes, s,                                                                   \
                   k_mm_fused<K><<<grid, TPB, 0, s>>>(yhat, v.data, nr, tab, part_stride, ell, A, c->L,      \
-                                                      c->logN, c->d_prime, c->ks, ksk_words(c)));           \
+                                                      c->logN, c->d_prime, c->ks, c->bits <= 55));          \
         break;
                 switch (na) {
                     MM_CASE(1) MM_CASE(2) MM_CASE(3) MM_CASE(4) MM_CASE(5) MM_CASE(6) MM_CASE(7) MM_CASE(8)
@@ -1292,10 +1311,10 @@ copse_status giant_phase(copse_ctx *c, const copse_evk *evk, const u64 *inner, i
                     tab.t[i] = RsTerm{yhat + (size_t)(x - x0) * nd * nx * N, inner + (size_t)x * per,
                                       evk->find(gal[x]), gal[x]};
                 }
-                const double bytes = 8.0 * N * ((double)nt * (4.0 * nd * nx + (double)nd * nx + ell) + 4.0 * nx);
+                const double bytes = 8.0 * N * ((double)nt * (2.0 * nd * nx + (double)nd * nx + ell) + 4.0 * nx);
                 TIMED("rotsum", bytes, s,
                       k_rotsum<<<nblk((size_t)nx * N), TPB, 0, s>>>(tab, nt, acc + (size_t)a * ext, ell, A, c->L,
-                                                                    c->logN, c->d_prime, c->ks, ksk_words(c)));
+                                                                    c->logN, c->d_prime, c->ks, c->bits <= 55));
                 LAUNCH_CHECK();
             }
         }
@@ -1427,24 +1446,6 @@ copse_status encode_patterns(copse_ctx *c, const std::vector<uint32_t> &patterns
     return COPSE_OK;
 }
 
-// Shoup companion floor(k 2^64 / q) of every key word (prime = the word's residue index
-// mod L + alpha), by restoring long division (k < q < 2^61: the remainder never overflows)
-__global__ void k_shoup_companions(const u64 *key, u64 *comp, size_t words, int NB, int logN, const PrimeDev *pr) {
-    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= words) return;
-    const u64 q = pr[(e >> logN) % NB].q;
-    u64 r = key[e], quo = 0;
-    for (int i = 0; i < 64; i++) {
-        r <<= 1;
-        quo <<= 1;
-        if (r >= q) {
-            r -= q;
-            quo |= 1;
-        }
-    }
-    comp[e] = quo;
-}
-
 static copse_status make_switch_key(copse_ctx *c, u64 seed, u64 sb, const u64 *s_hat, const u64 *sfrom, u64 *ksk,
                                     Scratch &sc, cudaStream_t s) {
     const int N = c->N, NB = c->L + c->alpha;
@@ -1501,26 +1502,19 @@ copse_status keygen_dev(copse_ctx *c, u64 seed, const std::vector<u64> &galois, 
     if ((st = ntt_forward(c, batch(te, (size_t)L * N, 1, 0, L, L), s))) return fail(st);
     k_pk<<<nblk((size_t)L * N), TPB, 0, s>>>(a, K->s_hat, te, K->pk, L, c->logN, c->d_prime);
     // relinearisation key: s' = s^2, streams 16 + 2j, 17 + 2j
-    // every key is followed by its Shoup companions (ksk_words words later): the key-switch
-    // inner products multiply by the fixed key words with Shoup products
     const size_t kw = ksk_words(c);
-    auto companions = [&](u64 *k) {
-        k_shoup_companions<<<nblk(kw), TPB, 0, s>>>(k, k + kw, kw, NB, c->logN, c->d_prime);
-    };
-    if ((st = dev_alloc(c, (void **)&E->rlk, kw * 2 * 8, s))) return fail(st);
+    if ((st = dev_alloc(c, (void **)&E->rlk, kw * 8, s))) return fail(st);
     k_mul_elem<<<nblk((size_t)NB * N), TPB, 0, s>>>(K->s_hat, K->s_hat, sf, NB, c->logN, c->d_prime);
     if ((st = make_switch_key(c, seed, 16, K->s_hat, sf, E->rlk, sc, s))) return fail(st);
-    companions(E->rlk);
     // rotation keys: s' = tau_g(s), streams 0x10000 + 64 g + (2j, 2j + 1)
     for (u64 g : galois) {
         if (g == 1 || E->find(g)) continue;
         u64 *k = nullptr;
-        if ((st = dev_alloc(c, (void **)&k, kw * 2 * 8, s))) return fail(st);
+        if ((st = dev_alloc(c, (void **)&k, kw * 8, s))) return fail(st);
         E->galois.push_back(g);
         E->gk.push_back(k);
         k_permute<<<nblk((size_t)NB * N), TPB, 0, s>>>(K->s_hat, sf, NB, g, c->logN);
         if ((st = make_switch_key(c, seed, 0x10000ull + 64ull * g, K->s_hat, sf, k, sc, s))) return fail(st);
-        companions(k);
     }
     if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) {
         set_error("key generation kernels failed");

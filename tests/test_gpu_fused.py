@@ -75,7 +75,12 @@ def test_fused_forest100_labels_and_savings():
         fz = K.copse_compile_forest(text, W.precision(), W.n_features(), W.log_n)
         K.copse_model_set_fused(fz, True)
         i2, i1 = K.copse_model_info_get(two), K.copse_model_info_get(fz)
-        assert i1["levels_used"] == i2["levels_used"] - 1
+        assert i1["levels_used"] == i2["levels_used"] - 1 and i1["n_rot_reshuffle"] == 0
+        # with baby-step plans the fused products need fewer rotation keys: one q-wide plan
+        # instead of a q-wide reshuffle plan plus a b-wide level plan
+        K.copse_model_set_bsgs(two, 16, 8)
+        K.copse_model_set_bsgs(fz, 16, 0)
+        i2, i1 = K.copse_model_info_get(two), K.copse_model_info_get(fz)
         assert i1["n_rot_level"] < i2["n_rot_reshuffle"] + i2["n_rot_level"]
         keys, evk = K.copse_keygen(ctx, 5, [fz])
         nq = (1 << W.log_n) // i1["block"]
