@@ -183,7 +183,10 @@ def ncu_traffic(family, workload, alg_bytes_per_launch, key="dram_bytes_per_unit
 
 # ---------------------------------------------------------------- CUDA arm
 # kernel families -> the measured integer rate their algorithmic operations are priced at
-PEAK_KIND = {"enc_mac": "mac", "ks_inner": "mac", "mm_mac": "mac", "mm_fused": "mac"}
+PEAK_KIND = {"enc_mac": "mac", "ks_inner": "mac", **{f: "butterfly" for f in (
+    "ntt_fwd", "ntt_inv", "ntt_inv_copy", "ntt_fwd_ms", "ntt_fwd_md", "ntt_fwd_mu", "ntt_fwd_mdd")}}
+PEAK_UNIT = {"mac": ("G modular products/s", "exact 64-bit residue products in lazily reduced sums"),
+             "butterfly": ("G butterflies/s", "lazy Shoup NTT butterflies")}
 
 
 def int_peaks(K, local):
@@ -216,10 +219,10 @@ def family_roofline(fam, ops, peaks_hbm, how, ipk, workload, steps):
     if ops.get(top) and kind and ipk:
         ach = ops[top] / sec
         peak = ipk[kind]["ops_per_s"]
+        unit, what = PEAK_UNIT[kind]
         roof = {"kernel": top, "bound": "alu", "achieved": ach / 1e9, "peak": peak / 1e9,
-                "unit": "G modular products/s", "frac": ach / peak, "traffic": tr, "hbm": hbm,
-                "peak_source": f"measured in this run: register-only microbenchmark of exact 64-bit residue "
-                               f"products in lazily reduced sums ({kind}), best of 5"}
+                "unit": unit, "frac": ach / peak, "traffic": tr, "hbm": hbm,
+                "peak_source": f"measured in this run: register-only microbenchmark of {what} ({kind}), best of 5"}
     else:
         roof = {"kernel": top, "bound": "hbm", "achieved": achieved, "peak": peaks_hbm, "unit": "GB/s",
                 "frac": achieved / peaks_hbm, "traffic": tr, "peak_source": f"{how} hbm_gbs (copy)"}
@@ -229,11 +232,26 @@ def family_roofline(fam, ops, peaks_hbm, how, ipk, workload, steps):
     return roof
 
 
-def family_table(fam, steps):
+def family_table(fam, steps, ops=None, ipk=None, hbm=None):
+    """Per kernel family: launches, time and share per step, HBM GB/s of its algorithmic bytes and,
+    where it counts modular operations, their rate and its fraction of the measured peak."""
     tot = max(1e-9, sum(x["ms"] for x in fam.values()))
-    return {k: {"launches_per_step": v["launches"] / steps, "ms_per_step": v["ms"] / steps, "share": v["ms"] / tot,
-                "gbs": v["bytes"] / (v["ms"] * 1e-3) / 1e9 if v["ms"] else 0.0}
-            for k, v in sorted(fam.items(), key=lambda kv: -kv[1]["ms"]) if v["launches"]}
+    out = {}
+    for k, v in sorted(fam.items(), key=lambda kv: -kv[1]["ms"]):
+        if not v["launches"]:
+            continue
+        row = {"launches_per_step": v["launches"] / steps, "ms_per_step": v["ms"] / steps, "share": v["ms"] / tot,
+               "gbs": v["bytes"] / (v["ms"] * 1e-3) / 1e9 if v["ms"] else 0.0}
+        if hbm:
+            row["hbm_frac"] = row["gbs"] / hbm
+        kind = PEAK_KIND.get(k)
+        if ops and ops.get(k) and kind and ipk and v["ms"]:
+            rate = ops[k] / (v["ms"] * 1e-3)
+            row["int_rate_g"] = rate / 1e9
+            row["int_frac"] = rate / ipk[kind]["ops_per_s"]
+            row["int_unit"] = PEAK_UNIT[kind][0]
+        out[k] = row
+    return out
 
 
 def run_cuda(args, ws, rank, local):
@@ -385,7 +403,7 @@ def run_headline(args, ws, rank, local, ipk, g=(128, 256)):
                    "l2": "inputs larger than L2 (the encrypted model alone is %.0f GB)" % (words * 8 / 1e9)},
         "labels_ok": ok, "path": "copse_encrypt_features + copse_infer + copse_decrypt_labels on one stream",
         "e2e": e2e, "gpu_launches": launches_step * args.steps, "roofline": roof,
-        "kernels": family_table(fam, 1), "clocks": ck,
+        "kernels": family_table(fam, 1, ops, ipk, peaks["hbm_gbs"]), "clocks": ck,
     }
 
 
@@ -517,7 +535,7 @@ def run_forest100(args, ws, rank, local, ipk):
     key_gb = n_rot * dnum * 2 * (W.primes + alpha) * N * 8 / 1e9
     return {"workload": W.name, "ring_degree": N, "ciphertext_primes": W.primes, "dnum": dnum, "tuning": tuning,
             "branches": info["b"], "leaves": L, "depth": info["depth"], "one_query": one, "batched": batched,
-            "plain_ops": plain, "kernels": family_table(fam, steps),
+            "plain_ops": plain, "kernels": family_table(fam, steps, ops, ipk, peaks["hbm_gbs"]),
             "roofline": family_roofline(fam, ops, peaks["hbm_gbs"], how, ipk, W.name, steps) if fam else None,
             "rotation_keys": n_rot,
             "key_working_set_gb": round(key_gb, 2), "l2": "working set > L2 (rotation keys %.1f GB)" % key_gb}

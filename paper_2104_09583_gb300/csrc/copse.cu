@@ -507,6 +507,7 @@ extern "C" copse_status copse_evk_export(const copse_evk *e, uint64_t galois, ui
     u64 *tmp = nullptr;
     STATUS_TRY(dev_alloc(c, (void **)&tmp, n * 8, 0));
     CUDA_TRY(cudaMemcpyAsync(tmp, key, n * 8, cudaMemcpyDeviceToDevice, 0));
+    STATUS_TRY(ksk_from_mont(c, tmp, 0));
     const int NB = c->L + c->alpha;
     STATUS_TRY(ntt_inverse(c, NttBatch{tmp, (size_t)NB * c->N, 2 * c->ndig, 0, NB, NB, -1}, 0));
     CUDA_TRY(cudaMemcpy(out, tmp, n * 8, cudaMemcpyDeviceToHost));

@@ -156,6 +156,10 @@ static copse_status build_tables(copse_ctx *c) {
         P.t_mod_sh = h_shoup(P.t_mod, q);
         P.r64 = (u64)(((u128)1 << 64) % q);
         P.r64_sh = h_shoup(P.r64, q);
+        P.one_sh = h_shoup(1, q);
+        u64 inv = 1;  // q^-1 mod 2^64 by Newton's iteration (q odd)
+        for (int i = 0; i < 6; i++) inv *= 2 - q * inv;
+        P.qinv_neg = (u64)0 - inv;
         // The slot structure needs the canonical root zeta = 3^((t-1)/2N) mod t;
         // for the RNS primes any primitive 2N-th root gives the same coefficients.
         u64 root = (g == c->t_index()) ? h_pow(3, (q - 1) / (2ull * N), q) : root_2n(q, c->logN);
@@ -299,7 +303,7 @@ static copse_status build_tables(copse_ctx *c) {
 extern "C" copse_status copse_ctx_create(const copse_params *pp, int device, copse_ctx **out) {
     if (!pp || !out) { set_error("null argument"); return COPSE_EINVAL; }
     *out = nullptr;
-    if (pp->log_n < 4 || pp->log_n > 15 || pp->prime_bits < 36 || pp->prime_bits > 60 || pp->n_primes < 1 ||
+    if (pp->log_n < 4 || pp->log_n > 15 || pp->prime_bits < 36 || pp->prime_bits > 58 || pp->n_primes < 1 ||
         pp->n_primes > 40 || pp->dnum < 1 || pp->dnum > pp->n_primes) {
         set_error("copse_params out of range");
         return COPSE_EINVAL;

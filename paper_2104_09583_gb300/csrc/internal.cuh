@@ -1,7 +1,7 @@
 // Internal declarations of the GB300 COPSE library: device modular arithmetic,
 // the context's device tables, device ciphertexts and the kernel launchers.
 //
-// Residues are 64-bit words modulo primes q < 2^60.  Products with a constant
+// Residues are 64-bit words modulo primes q < 2^58.  Products with a constant
 // operand use Shoup's precomputed quotient (V. Shoup, NTL; D. Harvey, "Faster
 // arithmetic for number-theoretic transforms", 2014); products of two data
 // words use Barrett reduction of the 128-bit product (Handbook of Applied
@@ -74,6 +74,8 @@ struct PrimeDev {
     u64 r64_sh;
     uint32_t bits;  // bit length of q
     uint32_t pad;
+    u64 one_sh;     // floor(2^64 / q): Shoup quotient of 1 (a reduction of any 64-bit value to [0, 2q))
+    u64 qinv_neg;   // -q^-1 mod 2^64 (Montgomery reduction)
 };
 
 // value and Shoup quotient of a constant multiplier
@@ -154,6 +156,16 @@ __device__ __forceinline__ Acc128 acc3w_value(const Acc3w &a) {
     v.lo += h;
     v.hi += (a.hi >> 8) + (v.lo < h);
     return v;
+}
+// Montgomery reduction (P. Montgomery, Math. Comp. 1985) of a 128-bit value x < q 2^64:
+// x 2^-64 mod q in [0, q).  Key-switching keys are stored in Montgomery form k 2^64 mod q,
+// so a dot product of residues with key words summed exactly in 128 bits (mac128; nd
+// products of values below q < 2^58 stay below q 2^64 for nd <= 64) reduces to the plain
+// residue sum with one reduction.
+__device__ __forceinline__ u64 mont_reduce(const Acc128 &x, const PrimeDev &P) {
+    const u64 m = x.lo * P.qinv_neg;
+    const u64 t = x.hi + __umul64hi(m, P.q) + (x.lo != 0);
+    return t >= P.q ? t - P.q : t;
 }
 // a signed small integer (|v| < q) as a residue
 __device__ __forceinline__ u64 from_signed(i64 v, u64 q) { return v < 0 ? q - (u64)(-v) : (u64)v; }
@@ -399,7 +411,7 @@ struct copse_keys {
 };
 struct copse_evk {
     copse_ctx *ctx = nullptr;
-    u64 *rlk = nullptr;                 // [ndig][2][L+alpha][N] NTT domain
+    u64 *rlk = nullptr;                 // [ndig][2][L+alpha][N] NTT domain, Montgomery form (x 2^64 mod q)
     std::vector<u64> galois;            // Galois elements with a key
     std::vector<u64 *> gk;              // matching keys, same layout as rlk
     const u64 *find(u64 g) const {
@@ -418,6 +430,8 @@ struct copse_ctbuf {
 // ---------------------------------------------------------------- BGV operations (ring.cu)
 // All allocate outputs from the pool on stream s and enqueue work on s.
 size_t ksk_words(const copse_ctx *c);
+// a key copy's words from Montgomery form (the stored form) to plain residues, in place
+copse_status ksk_from_mont(copse_ctx *c, u64 *k, cudaStream_t s);
 copse_status ct_alloc(copse_ctx *c, DCt *ct, int level, int ncomp, cudaStream_t s);
 void ct_free(DCt *ct, cudaStream_t s);
 copse_status ct_copy(copse_ctx *c, const DCt &in, DCt *out, cudaStream_t s);

@@ -22,6 +22,7 @@
 #include <cooperative_groups.h>
 
 #include <atomic>
+#include <cstdlib>
 
 #include "internal.cuh"
 
@@ -42,13 +43,21 @@ __device__ __forceinline__ bool ntt_skipped(const NttBatch &b, int p, int r) {
     return b.skip_alpha > 0 && r >= j * b.skip_alpha && r < min((j + 1) * b.skip_alpha, b.ell);
 }
 
-// forward butterfly, values in [0, 4q)
+// Forward butterfly without a correction step: the Shoup product V is below 2q for any
+// 64-bit input, so x' = U + V and y' = U - V + 2q only grow by 2q per stage.  From inputs
+// below q, values stay below (2 log2 N + 1) q <= 31 q < 2^64 for primes below 2^58 (the
+// context's limit); the final store reduces them once (fwd_reduce).
 __device__ __forceinline__ void bfv_fwd(u64 &x, u64 &y, u64 w, u64 wp, u64 q, u64 q2) {
-    u64 U = x;
-    if (U >= q2) U -= q2;
+    const u64 U = x;
     const u64 V = mul_shoup_lazy(y, w, wp, q);
     x = U + V;
     y = U - V + q2;
+}
+
+// a forward transform's output value (below 31 q) reduced to [0, q): a Shoup product by 1
+__device__ __forceinline__ u64 fwd_reduce(u64 v, u64 q, u64 one_sh) {
+    u64 r = mul_shoup_lazy(v, 1, one_sh, q);
+    return r >= q ? r - q : r;
 }
 
 // inverse butterfly, values in [0, 2q)
@@ -88,9 +97,7 @@ __global__ void __launch_bounds__(512) k_ntt_fwd(NttBatch b, const PrimeDev *__r
     }
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
         u64 v = sm[i];
-        if (v >= q2) v -= q2;
-        if (v >= q) v -= q;
-        data[i] = v;
+        data[i] = fwd_reduce(v, q, primes[g].one_sh);
     }
 }
 
@@ -289,10 +296,7 @@ __global__ void __launch_bounds__(NT2) k_ntt_fwd_rows(NttBatch b, const PrimeDev
     tile_fwd<false>(sm, stw, stwp, lb, t.q, t.q2, [&](int g, int i) { return (g << lb) + i; },
              [&](int u, int g, int il) { return ((1 << lr) * ((1 << u) - 1)) + (g << u) + il; });
     for (int e = threadIdx.x; e < TILE; e += NT2) {
-        u64 v = sm[e];
-        if (v >= t.q2) v -= t.q2;
-        if (v >= t.q) v -= t.q;
-        data[e] = v;
+        data[e] = fwd_reduce(sm[e], t.q, primes[t.g].one_sh);
     }
 }
 
@@ -581,7 +585,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT2)
         return;
     }
     const int g = ntt_prime(b, r, L);
-    const u64 q = primes[g].q, q2 = 2 * q;
+    const u64 q = primes[g].q, q2 = 2 * q, one_sh = primes[g].one_sh;
     const size_t N = (size_t)1 << logN;
     const u64 *W = tw + (size_t)g * N, *Wp = tw_sh + (size_t)g * N;
     // the tile, this CTA's row-stage twiddles (pre-staged, one 16-byte load each) and the
@@ -614,10 +618,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT2)
     tile_fwd<false>(S.rowt, S.stw, S.stwp, lb, q, q2, [&](int gg, int i) { return (gg << lb) + i; },
                     [&](int u, int gg, int il) { return ((1 << lr) * ((1 << u) - 1)) + (gg << u) + il; });
     for (int e = threadIdx.x; e < TILE; e += NT2) {
-        u64 v = S.rowt[e];
-        if (v >= q2) v -= q2;
-        if (v >= q) v -= q;
-        io.store(p, r, g, ((size_t)row0 << lb) + e, v);
+        io.store(p, r, g, ((size_t)row0 << lb) + e, fwd_reduce(S.rowt[e], q, one_sh));
     }
 }
 
@@ -693,6 +694,12 @@ copse_status cluster_attrs(K kernel, int cl) {
     return COPSE_OK;
 }
 
+// butterflies of a batch (N/2 log2 N per transformed residue polynomial): the integer
+// roof's unit for the transforms
+inline double butterflies(const copse_ctx *ctx, const NttBatch &b) {
+    return (double)b.npoly * b.nr * (ctx->N / 2) * ctx->logN;
+}
+
 template <int CL>
 copse_status launch_cluster(copse_ctx *ctx, const NttBatch &b, cudaStream_t s, bool inverse, double bytes) {
     static std::atomic<uint64_t> attr_devices{0};
@@ -705,13 +712,13 @@ copse_status launch_cluster(copse_ctx *ctx, const NttBatch &b, cudaStream_t s, b
     const unsigned grid = (unsigned)b.npoly * (unsigned)b.nr * CL;
     const int a = ctx->logN / 2;
     if (inverse)
-        TIMED("ntt_inv", bytes, s,
+        TIMED_OPS("ntt_inv", bytes, butterflies(ctx, b), s,
               k_ntt_inv_cluster<CL, PlainIO><<<grid, NT2, smem, s>>>(b, ctx->d_prime, ctx->d_ipsi, ctx->d_ipsi_sh,
                                                                      (const ulonglong2 *)ctx->d_stw_i, ctx->logN,
                                                                      ctx->L, a,
                                                                      PlainIO{b.data, b.stride, ctx->logN}));
     else
-        TIMED("ntt_fwd", bytes, s,
+        TIMED_OPS("ntt_fwd", bytes, butterflies(ctx, b), s,
               k_ntt_fwd_cluster<CL, PlainIO><<<grid, NT2, smem, s>>>(b, ctx->d_prime, ctx->d_psi, ctx->d_psi_sh,
                                                                      (const ulonglong2 *)ctx->d_stw_f, ctx->logN,
                                                                      ctx->L, a,
@@ -724,6 +731,7 @@ copse_status launch(copse_ctx *ctx, const NttBatch &b, cudaStream_t s, bool inve
     if (b.npoly <= 0 || b.nr <= 0) return COPSE_OK;
     const int N = ctx->N, logN = ctx->logN;
     const double bytes = (double)b.npoly * b.nr * N * 16.0;  // one read and one write of each residue polynomial
+    const double bfly = butterflies(ctx, b);
     if (ctx->ntt_clusters && (long)b.npoly * b.nr <= ctx->ntt_cluster_max) {
         if (logN == 12) return launch_cluster<2>(ctx, b, s, inverse, bytes);
         if (logN == 13) return launch_cluster<4>(ctx, b, s, inverse, bytes);
@@ -734,12 +742,12 @@ copse_status launch(copse_ctx *ctx, const NttBatch &b, cudaStream_t s, bool inve
         const int a = logN / 2;  // column length 2^a, row length 2^(logN - a)
         const unsigned grid = (unsigned)b.npoly * (unsigned)b.nr * (unsigned)(N / TILE);
         if (inverse) {
-            TIMED("ntt_inv", bytes, s, {
+            TIMED_OPS("ntt_inv", bytes, bfly, s, {
                 k_ntt_inv_rows<<<grid, NT2, 0, s>>>(b, ctx->d_prime, (const ulonglong2 *)ctx->d_stw_i, logN, ctx->L, a);
                 k_ntt_inv_cols<<<grid, NT2, 0, s>>>(b, ctx->d_prime, ctx->d_ipsi, ctx->d_ipsi_sh, logN, ctx->L, a);
             });
         } else {
-            TIMED("ntt_fwd", bytes, s, {
+            TIMED_OPS("ntt_fwd", bytes, bfly, s, {
                 k_ntt_fwd_cols<<<grid, NT2, 0, s>>>(b, ctx->d_prime, ctx->d_psi, ctx->d_psi_sh, logN, ctx->L, a);
                 k_ntt_fwd_rows<<<grid, NT2, 0, s>>>(b, ctx->d_prime, (const ulonglong2 *)ctx->d_stw_f, logN, ctx->L, a);
             });
@@ -751,10 +759,10 @@ copse_status launch(copse_ctx *ctx, const NttBatch &b, cudaStream_t s, bool inve
     const int threads = N / 2 < 512 ? N / 2 : 512;
     const unsigned grid = (unsigned)b.npoly * (unsigned)b.nr;
     if (inverse)
-        TIMED("ntt_inv", bytes, s,
+        TIMED_OPS("ntt_inv", bytes, bfly, s,
               k_ntt_inv<<<grid, threads, smem, s>>>(b, ctx->d_prime, ctx->d_ipsi, ctx->d_ipsi_sh, logN, ctx->L));
     else
-        TIMED("ntt_fwd", bytes, s,
+        TIMED_OPS("ntt_fwd", bytes, bfly, s,
               k_ntt_fwd<<<grid, threads, smem, s>>>(b, ctx->d_prime, ctx->d_psi, ctx->d_psi_sh, logN, ctx->L));
     LAUNCH_CHECK();
     return COPSE_OK;
@@ -783,12 +791,12 @@ copse_status launch_cluster_io(copse_ctx *ctx, const NttBatch &b, const IO &io, 
     const unsigned grid = (unsigned)b.npoly * (unsigned)b.nr * CL;
     const double bytes = (double)b.npoly * b.nr * ctx->N * 16.0;
     if (INV)
-        TIMED(io_family<IO>(true), bytes, s,
+        TIMED_OPS(io_family<IO>(true), bytes, butterflies(ctx, b), s,
               k_ntt_inv_cluster<CL, IO><<<grid, NT2, smem, s>>>(b, ctx->d_prime, ctx->d_ipsi, ctx->d_ipsi_sh,
                                                                 (const ulonglong2 *)ctx->d_stw_i, ctx->logN, ctx->L,
                                                                 ctx->logN / 2, io));
     else
-        TIMED(io_family<IO>(false), bytes, s,
+        TIMED_OPS(io_family<IO>(false), bytes, butterflies(ctx, b), s,
               k_ntt_fwd_cluster<CL, IO><<<grid, NT2, smem, s>>>(b, ctx->d_prime, ctx->d_psi, ctx->d_psi_sh,
                                                                 (const ulonglong2 *)ctx->d_stw_f, ctx->logN, ctx->L,
                                                                 ctx->logN / 2, io));
@@ -905,7 +913,10 @@ copse_status ntt_stage_tables(copse_ctx *ctx) {
         cfg.numAttrs = 1;
         int nclusters = 0;
         const cudaError_t e = cudaOccupancyMaxActiveClusters(&nclusters, k_ntt_fwd_cluster<16, PlainIO>, &cfg);
-        ctx->ntt_cluster16 = e == cudaSuccess && nclusters > 0;
+        // measured slower than the two-launch transforms on GB300 at N = 2^15 (the 16-CTA
+        // cluster barriers and cross-SM tile gathers): an option, COPSE_NTT_CLUSTER16=1
+        const char *opt = getenv("COPSE_NTT_CLUSTER16");
+        ctx->ntt_cluster16 = e == cudaSuccess && nclusters > 0 && opt && opt[0] == '1';
         cudaGetLastError();
     }
     const size_t n = (size_t)ctx->NP * ctx->N;  // NP x (N / TILE) x TILE entries

@@ -156,30 +156,19 @@ __global__ void k_modup(const u64 *x, const u64 *x_ntt, size_t xs, u64 *y, int e
 }
 
 // sum_j y_j * k_j over the nd key-switching digits of one element and both key
-// components: exact split-28 products summed lazily and reduced once when every residue
-// is below 2^55 (split), Barrett products otherwise.  yh: digit j's value at
+// components: the key words are in Montgomery form (k 2^64 mod q), the products are summed
+// exactly in 128 bits and reduced once (mont_reduce).  yh: digit j's value at
 // yh[j * ystride]; key component c of digit j at key[(2 j + c) * kstride].
 __device__ __forceinline__ void ks_dot(const u64 *yh, size_t ystride, const u64 *key, size_t kstride, int nd,
-                                       bool split, const PrimeDev &P, u64 &o0, u64 &o1) {
-    if (split) {
-        Acc3w a0{0, 0, 0}, a1{0, 0, 0};
-        for (int j = 0; j < nd; j++) {
-            const Sp28 y = split28(yh[(size_t)j * ystride]);
-            mac_sp(a0, y, split28(key[(size_t)(2 * j) * kstride]));
-            mac_sp(a1, y, split28(key[(size_t)(2 * j + 1) * kstride]));
-        }
-        o0 = reduce128(acc3w_value(a0), P);
-        o1 = reduce128(acc3w_value(a1), P);
-        return;
-    }
-    u64 s0 = 0, s1 = 0;
+                                       const PrimeDev &P, u64 &o0, u64 &o1) {
+    Acc128 a0{0, 0}, a1{0, 0};
     for (int j = 0; j < nd; j++) {
         const u64 y = yh[(size_t)j * ystride];
-        s0 = add_mod(s0, mul_mod(y, key[(size_t)(2 * j) * kstride], P), P.q);
-        s1 = add_mod(s1, mul_mod(y, key[(size_t)(2 * j + 1) * kstride], P), P.q);
+        mac128(a0, y, key[(size_t)(2 * j) * kstride]);
+        mac128(a1, y, key[(size_t)(2 * j + 1) * kstride]);
     }
-    o0 = s0;
-    o1 = s1;
+    o0 = mont_reduce(a0, P);
+    o1 = mont_reduce(a1, P);
 }
 
 struct InnerJob {
@@ -197,7 +186,7 @@ struct InnerJobs {
 
 // (u0, u1)[r][n] = sum_j yhat[j][r][tau_g n] * ksk[j][c][ext_prime(r)][n]
 __global__ void k_ks_inner(const u64 *yhat, const InnerJobs jobs, int ell, int alpha, int L, int logN,
-                           const PrimeDev *pr, const u64 *mdP, bool split) {
+                           const PrimeDev *pr, const u64 *mdP) {
     const int N = 1 << logN;
     const int nx = ell + alpha, nd = (ell + alpha - 1) / alpha;
     const int NB = L + alpha;
@@ -212,7 +201,7 @@ __global__ void k_ks_inner(const u64 *yhat, const InnerJobs jobs, int ell, int a
     const u64 *yh = J.y ? J.y : yhat;
     u64 acc0, acc1;
     ks_dot(yh + ((size_t)r << logN) + src, (size_t)nx << logN, J.ksk + ((size_t)g << logN) + n, (size_t)NB << logN,
-           nd, split, P, acc0, acc1);
+           nd, P, acc0, acc1);
     if (J.pd && r < ell) {
         const u64 Pm = mdP[r];
         acc0 = add_mod(acc0, mul_mod(Pm, J.pd[((size_t)r << logN) + n], P), P.q);
@@ -276,7 +265,7 @@ struct MmTable {
 template <int NA>
 __global__ void __launch_bounds__(256) k_mm_fused(const u64 *yhat, const u64 *c0, int nrot, const MmTable tab,
                                                   size_t part_stride, int ell, int alpha, int L, int logN,
-                                                  const PrimeDev *pr, KsTables T, bool split) {
+                                                  const PrimeDev *pr, KsTables T) {
     const int N = 1 << logN;
     const int nx = ell + alpha, nd = (ell + alpha - 1) / alpha, NB = L + alpha;
     const size_t n_el = (size_t)nx << logN;
@@ -308,7 +297,7 @@ __global__ void __launch_bounds__(256) k_mm_fused(const u64 *yhat, const u64 *c0
         } else {
             const uint32_t src = galois_src(n, J.g, logN);
             ks_dot(yhat + ((size_t)r << logN) + src, (size_t)nx << logN, J.ksk + ((size_t)g << logN) + n,
-                   (size_t)NB << logN, nd, split, P, u0, u1);
+                   (size_t)NB << logN, nd, P, u0, u1);
             if (r < ell) u0 = add_mod(u0, mul_mod(Pm, c0[((size_t)r << logN) + src], P), P.q);
         }
 #pragma unroll
@@ -398,7 +387,7 @@ struct RsTable {
 };
 
 __global__ void __launch_bounds__(256) k_rotsum(const RsTable tab, int nterm, u64 *acc, int ell, int alpha, int L,
-                                                int logN, const PrimeDev *pr, KsTables T, bool split) {
+                                                int logN, const PrimeDev *pr, KsTables T) {
     const int N = 1 << logN;
     const int nx = ell + alpha, nd = (ell + alpha - 1) / alpha, NB = L + alpha;
     const size_t n_el = (size_t)nx << logN;
@@ -415,7 +404,7 @@ __global__ void __launch_bounds__(256) k_rotsum(const RsTable tab, int nterm, u6
         const uint32_t src = galois_src(n, J.g, logN);
         u64 t0, t1;
         ks_dot(J.yhat + ((size_t)r << logN) + src, (size_t)nx << logN, J.ksk + ((size_t)g << logN) + n,
-               (size_t)NB << logN, nd, split, P, t0, t1);
+               (size_t)NB << logN, nd, P, t0, t1);
         a0 = add_mod(a0, t0, P.q);
         a1 = add_mod(a1, t1, P.q);
         if (r < ell) a0 = add_mod(a0, mul_mod(Pm, J.c0[((size_t)r << logN) + src], P), P.q);
@@ -533,8 +522,16 @@ __global__ void k_ksk(const u64 *a, const u64 *s, const u64 *te, const u64 *sfro
     const PrimeDev P = pr[r];
     u64 v = sub_mod(te[e], mul_mod(a[e], s[e], P), P.q);
     if (r >= lo && r < hi) v = add_mod(v, mul_mod(T.md_P[r], sfrom[e], P), P.q);
-    k[e] = v;
-    k[n + e] = a[e];
+    // stored in Montgomery form (x 2^64 mod q): the key-switch dot products reduce once
+    k[e] = mul_shoup(v, P.r64, P.r64_sh, P.q);
+    k[n + e] = mul_shoup(a[e], P.r64, P.r64_sh, P.q);
+}
+
+// key words back from Montgomery form (x 2^-64 mod q), residue r of NB per polynomial
+__global__ void k_from_mont(u64 *k, size_t words, int NB, int logN, const PrimeDev *pr) {
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= words) return;
+    k[e] = mont_reduce(Acc128{k[e], 0}, pr[(e >> logN) % NB]);
 }
 
 // slot patterns -> NTT(mod t) order: out[i][slot_index[s]] = pattern_i[s mod period] (0 past len)
@@ -751,7 +748,7 @@ copse_status ks_apply(copse_ctx *c, const u64 *yhat, int ell, const std::vector<
     // the output; products: two per digit and element
     TIMED_OPS("ks_inner", 8.0 * N * ((double)ndg * nx + (double)nj * (2.0 * ndg * nx + 2.0 * nx)),
               2.0 * N * (double)nj * ndg * nx, s,
-              k_ks_inner<<<grid, TPB, 0, s>>>(yhat, jobs, ell, A, c->L, c->logN, c->d_prime, c->ks.md_P, c->bits <= 55));
+              k_ks_inner<<<grid, TPB, 0, s>>>(yhat, jobs, ell, A, c->L, c->logN, c->d_prime, c->ks.md_P));
     LAUNCH_CHECK();
     return moddown_apply(c, U, ell, nj, f, sc, s);
 }
@@ -776,6 +773,13 @@ u64 galois_of_rotation(const copse_ctx *c, uint32_t k) {
 // (cudaMemcpyAsync on host memory the caller owns); callers synchronise.
 
 size_t ksk_words(const copse_ctx *c) { return (size_t)c->ndig * 2 * (c->L + c->alpha) * c->N; }
+
+copse_status ksk_from_mont(copse_ctx *c, u64 *k, cudaStream_t s) {
+    const size_t n = ksk_words(c);
+    k_from_mont<<<nblk(n), TPB, 0, s>>>(k, n, c->L + c->alpha, c->logN, c->d_prime);
+    LAUNCH_CHECK();
+    return COPSE_OK;
+}
 
 copse_ctbuf::~copse_ctbuf() {
     for (auto &ct : cts) ct_free(&ct, stream);
@@ -955,7 +959,7 @@ static copse_status mul_group(copse_ctx *c, const copse_evk *evk, const std::vec
         ij.j[k] = InnerJob{evk->rlk, U + (size_t)k * 2 * nx * N, 1, yhat + (size_t)k * nd * nx * N, d + (size_t)k * per3};
     TIMED_OPS("ks_inner", 8.0 * N * nj * (3.0 * nd * nx + 2.0 * nx + 2.0 * ell), 2.0 * N * (double)nj * nd * nx, s,
               k_ks_inner<<<dim3(nblk((size_t)nx * N), nj), TPB, 0, s>>>(yhat, ij, ell, A, c->L, c->logN, c->d_prime,
-                                                                         c->ks.md_P, c->bits <= 55));
+                                                                         c->ks.md_P));
     LAUNCH_CHECK();
     // the dropped prime's and the special residues to coefficients, then the fused
     // conversion + transform + finish (or conversion, transform, finish)
@@ -1183,7 +1187,7 @@ copse_status op_matmul(copse_ctx *c, const copse_evk *evk, const DCt &v, const s
                 }
                 TIMED_OPS("ks_inner", 8.0 * N * nj * (2.0 * nd * nx + 2.0 * nx + ell), 2.0 * N * (double)nj * nd * nx, s,
                           k_ks_inner<<<dim3(nblk((size_t)nx * N), nj), TPB, 0, s>>>(yhat, jobs, ell, A, c->L, c->logN,
-                                                                                     c->d_prime, c->ks.md_P, c->bits <= 55));
+                                                                                     c->d_prime, c->ks.md_P));
                 LAUNCH_CHECK();
             }
         }
@@ -1217,7 +1221,7 @@ copse_status op_matmul(copse_ctx *c, const copse_evk *evk, const DCt &v, const s
         else                                                                                              \
             TIMED("mm_fused", bytes, s,                                                                   \
                   k_mm_fused<K><<<grid, TPB, 0, s>>>(yhat, v.data, nr, tab, part_stride, ell, A, c->L,      \
-                                                      c->logN, c->d_prime, c->ks, c->bits <= 55));          \
+                                                      c->logN, c->d_prime, c->ks));          \
         break;
                 switch (na) {
                     MM_CASE(1) MM_CASE(2) MM_CASE(3) MM_CASE(4) MM_CASE(5) MM_CASE(6) MM_CASE(7) MM_CASE(8)
@@ -1314,7 +1318,7 @@ copse_status giant_phase(copse_ctx *c, const copse_evk *evk, const u64 *inner, i
                 const double bytes = 8.0 * N * ((double)nt * (2.0 * nd * nx + (double)nd * nx + ell) + 4.0 * nx);
                 TIMED("rotsum", bytes, s,
                       k_rotsum<<<nblk((size_t)nx * N), TPB, 0, s>>>(tab, nt, acc + (size_t)a * ext, ell, A, c->L,
-                                                                    c->logN, c->d_prime, c->ks, c->bits <= 55));
+                                                                    c->logN, c->d_prime, c->ks));
                 LAUNCH_CHECK();
             }
         }

@@ -1,6 +1,7 @@
 """Ring degree N = 2^15 (the largest with 2N | t - 1 at t = 65537): the NTT,
 keys and a whole inference against the oracle, coefficient for coefficient.
-At this degree the forward and inverse NTT take the two-pass tiled kernels."""
+At this degree the transforms take the two-pass tiled kernels by default, and
+the 16-CTA cluster kernels (with their fused forms) as an option."""
 import numpy as np
 import pytest
 
@@ -72,3 +73,25 @@ def test_inference_n32768(big):
     _, trees = Cp.parse_forest(big.text)
     for j in range(len(qs)):
         assert bits[j].tolist() == Cp.classify_plain(trees, qs[j]), f"query {j}"
+
+
+def test_inference_n32768_cluster16(monkeypatch):
+    """The one-launch 16-CTA cluster transforms and their fused forms (an option at N = 2^15,
+    COPSE_NTT_CLUSTER16=1, read when a context is made): the same inference as the oracle's."""
+    monkeypatch.setenv("COPSE_NTT_CLUSTER16", "1")
+    W = synth.WORKLOADS["toy-n1024"]
+    s = Setup(W.forest_texts()[0], W.precision(), W.n_features(), 15, 55, W.primes, W.dnum)
+    try:
+        qs = synth.random_queries(1516, 2, s.nf, s.p)
+        feats = K.copse_encrypt_features(s.ctx, s.keys, s.model, qs, 78)
+        res = K.copse_infer(s.ctx, s.evk, s.model, feats)
+        try:
+            got = K.copse_ctbuf_export(s.ctx, res, 0, s.N)
+        finally:
+            K.copse_ctbuf_destroy(res)
+            K.copse_ctbuf_destroy(feats)
+        X = Cp.encrypt_queries(s.bgv, s.okeys, s.om, qs, 78)
+        want = Cp.infer(Cp.BgvEngine(s.bgv, s.okeys), s.om, X, s.N)
+        assert_same(got, want, "inference at N = 2^15 with 16-CTA cluster transforms")
+    finally:
+        s.close()
