@@ -275,7 +275,7 @@ def synth_workload(name):
     return synth.WORKLOADS[name]
 
 
-def run_headline(args, ws, rank, local, ipk, g=(128, 256)):
+def run_headline(args, ws, rank, local, ipk):
     """The encrypted-model workload (Maurice = Diane): every model ciphertext (threshold planes,
     all reshuffle and level diagonals, masks) encrypted once; one step = the batch of queries
     encrypted, Algorithm 1 over all their ciphertexts, and the leaf bits decrypted, on one
@@ -285,6 +285,7 @@ def run_headline(args, ws, rank, local, ipk, g=(128, 256)):
     from paper_2104_09583_gb300 import copse as K
 
     W = synth_workload(args.workload)
+    g = W.bsgs
     text = W.forest_texts()[0]
     N = 1 << W.log_n
     ctx = K.copse_ctx_create(W.log_n, W.bits, W.primes, W.dnum, device=local)
@@ -770,7 +771,7 @@ class OracleBench:
     runs it.  A whole step takes the oracle days (millions of ciphertext products at
     N = 2^15), so the step time is extrapolated from the samples with the exact counts."""
 
-    def __init__(self, W, text, g=(128, 256)):
+    def __init__(self, W, text):
         from oracle import bgv as B
         from oracle import copse as Cp
 
@@ -778,6 +779,7 @@ class OracleBench:
         self.m = m = Cp.compile_forest(text, W.precision(), W.n_features(), slots_per_row=1 << (W.log_n - 1))
         self.P = P = B.Params(logN=W.log_n, L=W.primes, bits=W.bits, dnum=W.dnum)
         self.bgv = B.Bgv(P)
+        g = W.bsgs
         rs, ls = Cp.encrypted_rotation_sets(m, g)
         self.keys = self.bgv.keygen(7, [B.galois_rot(W.log_n, rs[0])])
         self.galois = B.galois_rot(W.log_n, rs[0])

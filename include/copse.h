@@ -55,7 +55,7 @@ typedef int copse_status;
  * alpha = ceil(n_primes / dnum) special primes for hybrid key switching. */
 typedef struct copse_params {
     uint32_t log_n;      /* ring degree N = 2^log_n, 4 <= log_n <= 15 (2N | t-1)  */
-    uint32_t prime_bits; /* bit length of every prime, 36 <= prime_bits <= 58     */
+    uint32_t prime_bits; /* bit length of every prime, 36 <= prime_bits <= 55     */
     uint32_t n_primes;   /* ciphertext primes L, 1 <= L <= 40                      */
     uint32_t dnum;       /* key-switching digits, 1 <= dnum <= L                   */
 } copse_params;

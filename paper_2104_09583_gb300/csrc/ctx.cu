@@ -303,7 +303,7 @@ static copse_status build_tables(copse_ctx *c) {
 extern "C" copse_status copse_ctx_create(const copse_params *pp, int device, copse_ctx **out) {
     if (!pp || !out) { set_error("null argument"); return COPSE_EINVAL; }
     *out = nullptr;
-    if (pp->log_n < 4 || pp->log_n > 15 || pp->prime_bits < 36 || pp->prime_bits > 58 || pp->n_primes < 1 ||
+    if (pp->log_n < 4 || pp->log_n > 15 || pp->prime_bits < 36 || pp->prime_bits > 55 || pp->n_primes < 1 ||
         pp->n_primes > 40 || pp->dnum < 1 || pp->dnum > pp->n_primes) {
         set_error("copse_params out of range");
         return COPSE_EINVAL;

@@ -1,7 +1,8 @@
 // Internal declarations of the GB300 COPSE library: device modular arithmetic,
 // the context's device tables, device ciphertexts and the kernel launchers.
 //
-// Residues are 64-bit words modulo primes q < 2^58.  Products with a constant
+// Residues are 64-bit words modulo primes q < 2^55 (the transforms and the exact
+// split-product sums keep their lazy values below 2^64 under that bound).  Products with a constant
 // operand use Shoup's precomputed quotient (V. Shoup, NTL; D. Harvey, "Faster
 // arithmetic for number-theoretic transforms", 2014); products of two data
 // words use Barrett reduction of the 128-bit product (Handbook of Applied

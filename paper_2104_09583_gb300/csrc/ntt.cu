@@ -45,7 +45,7 @@ __device__ __forceinline__ bool ntt_skipped(const NttBatch &b, int p, int r) {
 
 // Forward butterfly without a correction step: the Shoup product V is below 2q for any
 // 64-bit input, so x' = U + V and y' = U - V + 2q only grow by 2q per stage.  From inputs
-// below q, values stay below (2 log2 N + 1) q <= 31 q < 2^64 for primes below 2^58 (the
+// below q, values stay below (2 log2 N + 1) q <= 31 q < 2^60 for primes below 2^55 (the
 // context's limit); the final store reduces them once (fwd_reduce).
 __device__ __forceinline__ void bfv_fwd(u64 &x, u64 &y, u64 w, u64 wp, u64 q, u64 q2) {
     const u64 U = x;
@@ -67,6 +67,17 @@ __device__ __forceinline__ void bfv_inv(u64 &x, u64 &y, u64 w, u64 wp, u64 q, u6
     if (s >= q2) s -= q2;
     x = s;
     y = mul_shoup_lazy(U - V + q2, w, wp, q);
+}
+
+// Inverse butterfly without a correction step, for a stage whose inputs are below c (a
+// multiple of q): U - V + c is positive and below 2c, so the product is the same residue,
+// x' = U + V < 2c and y' < 2q.  From inputs below q, stage u of a pass takes c = 2^u q and
+// its outputs stay below 2^(u+1) q; a pass of at most 8 stages stays below 2^63 for primes
+// below 2^55 (the context's limit) and is reduced once before the next pass or the scaling.
+__device__ __forceinline__ void bfv_inv_lazy(u64 &x, u64 &y, u64 w, u64 wp, u64 q, u64 c) {
+    const u64 U = x, V = y;
+    x = U + V;
+    y = mul_shoup_lazy(U - V + c, w, wp, q);
 }
 
 __device__ __forceinline__ void bf_fwd(u64 *x, u64 *y, u64 w, u64 wp, u64 q, u64 q2) { bfv_fwd(*x, *y, w, wp, q, q2); }
@@ -205,11 +216,12 @@ __device__ __forceinline__ void tile_inv(u64 *sm, const u64 *tw, const u64 *twp,
             const int a0 = ix(g, i0), a1 = ix(g, i0 + tt), a2 = ix(g, i0 + 2 * tt), a3 = ix(g, i0 + 3 * tt);
             u64 v0 = sm[a0], v1 = sm[a1], v2 = sm[a2], v3 = sm[a3];
             const int ta = twi(u, g, 2 * il1), tb = twi(u, g, 2 * il1 + 1);
-            bfv_inv(v0, v1, tw[ta], twp[ta], q, q2);
-            bfv_inv(v2, v3, tw[tb], twp[tb], q, q2);
+            const u64 c0 = q << u, c1 = q << (u + 1);
+            bfv_inv_lazy(v0, v1, tw[ta], twp[ta], q, c0);
+            bfv_inv_lazy(v2, v3, tw[tb], twp[tb], q, c0);
             const int t1 = twi(u + 1, g, il1);
-            bfv_inv(v0, v2, tw[t1], twp[t1], q, q2);
-            bfv_inv(v1, v3, tw[t1], twp[t1], q, q2);
+            bfv_inv_lazy(v0, v2, tw[t1], twp[t1], q, c1);
+            bfv_inv_lazy(v1, v3, tw[t1], twp[t1], q, c1);
             sm[a0] = v0;
             sm[a1] = v1;
             sm[a2] = v2;
@@ -224,7 +236,7 @@ __device__ __forceinline__ void tile_inv(u64 *sm, const u64 *tw, const u64 *twp,
             split_item<SEQ_FAST>(x, ls, ls - 1, g, j);
             const int a0 = ix(g, j), a1 = ix(g, j + tt);
             const int t0 = twi(u, g, 0);
-            bf_inv(&sm[a0], &sm[a1], tw[t0], twp[t0], q, q2);
+            bfv_inv_lazy(sm[a0], sm[a1], tw[t0], twp[t0], q, q << u);
         }
         __syncthreads();
     }
@@ -328,7 +340,8 @@ __global__ void __launch_bounds__(NT2) k_ntt_inv_rows(NttBatch b, const PrimeDev
              [&](int u, int g, int il) {
                  return (1 << lr) * ((1 << lb) - (1 << (lb - u))) + (g << (lb - 1 - u)) + il;
              });
-    for (int e = threadIdx.x; e < TILE; e += NT2) data[e] = sm[e];
+    const u64 one_sh = primes[t.g].one_sh;
+    for (int e = threadIdx.x; e < TILE; e += NT2) data[e] = fwd_reduce(sm[e], t.q, one_sh);
 }
 
 // Inverse column pass: twiddle of stage u, group il is W[2^(a-1-u) + il]; then N^-1.
@@ -660,6 +673,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT2)
                     [&](int u, int gg, int il) {
                         return (1 << lr) * ((1 << lb) - (1 << (lb - u))) + (gg << (lb - 1 - u)) + il;
                     });
+    for (int e = threadIdx.x; e < TILE; e += NT2) S.rowt[e] = fwd_reduce(S.rowt[e], q, P.one_sh);
     cl.sync();
     for (int e = threadIdx.x; e < TILE; e += NT2) {
         const int row = e >> lc, col = (rank << lc) + (e & (C - 1));

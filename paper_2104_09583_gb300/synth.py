@@ -152,6 +152,7 @@ class Workload:
     dnum: int
     forests: tuple       # (seed, n_trees, depth, n_features, precision, n_classes, complete, branches)
     queries: tuple       # queries per forest
+    bsgs: tuple = (128, 256)  # baby-step sizes of an encrypted-model run (reshuffle, levels)
 
     def forest_texts(self):
         return [random_forest(s, nt, dp, nf, p, nc, complete=c, branches=br)
@@ -184,6 +185,11 @@ WORKLOADS = {
     # 10 classes; 16 primes; 64 queries
     "encmodel32-n32768": Workload("encmodel32-n32768", 15, 55, 16, 3,
                                   ((4001, 32, 8, 32, 16, 10, True, None),), (64,)),
+    # a small case of the encrypted-model products at the same ring and chain (1 complete tree of
+    # depth 6, 8 features, 16-bit; 16 query ciphertexts of 128 queries): a few GB on the device,
+    # for detailed counter captures of the multiply-accumulate kernel
+    "encmodel1-n32768": Workload("encmodel1-n32768", 15, 55, 16, 3,
+                                 ((4011, 1, 6, 8, 16, 10, True, None),), (2048,), (32, 32)),
     # batching: 256 queries over three forests (1 x depth 3, 4 x depth 5, 16 x depth 6)
     "batch3-n16384": Workload("batch3-n16384", 14, 55, 10, 3,
                               ((3001, 1, 3, 8, 8, 4, True, None),
