@@ -20,9 +20,7 @@
 namespace {
 
 constexpr int TPB = 256;
-constexpr int EM_ACC = 8;      // accumulators per MAC launch (the table's capacity)
-constexpr int EM_BABY = 16;    // baby steps per MAC launch
-constexpr int EM_GROUP = 8;    // query ciphertexts whose rotations are held at once
+constexpr int EM_GROUP = 8;    // query ciphertexts per rotation group while no free-memory sizing is known
 constexpr int EM_CHUNK = 256;  // model ciphertexts encrypted per batch
 constexpr u64 MODEL_STREAM = 0x800000ull;
 
@@ -82,120 +80,11 @@ __global__ void k_materialize(const u64 *c0, u64 *out, int ell, u64 seed, u64 st
 }
 
 // Ciphertext x ciphertext products summed per accumulator, before relinearisation:
-// for each element (r, k), every accumulator x and query ciphertext b of the
-// thread's tile and every baby step j of the launch,
-//   (acc0, acc1, acc2)[b][x] += (d0 R0, d0 R1 + d1 R0, d1 R1),
-// d = the encrypted diagonal of (x, j) (c0 read, c1 regenerated once for all
-// query ciphertexts), R = rot(v_b, j) (read once for all accumulators).
-struct EncMacTable {
-    const u64 *c0[EM_ACC * EM_BABY];  // [acc][baby], null = no such diagonal
-    u64 stream[EM_ACC * EM_BABY];
-};
-
-// 128-bit accumulator: the products of one launch (each < 4 q^2 < 2^122, at most
-// EM_BABY of them per accumulator, < 2^126) are summed exactly and reduced once.
-// R: rotations [query ct][baby][2][ell][N] from the launch's first baby (r_ct words per
-// query ciphertext); acc: [query ct][acc][3][ell][N] from the launch's first accumulator
-// (a_ct words per query ciphertext).  A thread holds a register tile of TA
-// accumulators x TQ query ciphertexts for one element; blockIdx.y = group of TQ
-// query ciphertexts, blockIdx.z = group of TA accumulators.  The next baby step's
-// rotations and diagonal words are loaded while the current one is multiplied.
-template <int TA, int TQ>
-__global__ void __launch_bounds__(128) k_enc_mac(const EncMacTable tab, int na, int nb, int nq, const u64 *R,
-                                                 size_t r_ct, u64 *acc, size_t a_ct, int ell, int logN, u64 seed,
-                                                 const PrimeDev *pr) {
-    const size_t n_el = (size_t)ell << logN;
-    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= n_el) return;
-    const int q0 = (int)blockIdx.y * TQ, nc = min(TQ, nq - q0);
-    const int x0 = (int)blockIdx.z * TA, nx = min(TA, na - x0);
-    const int r = (int)(e >> logN);
-    const uint32_t k = (uint32_t)(e & ((1ull << logN) - 1));
-    const PrimeDev P = pr[r];
-    // Karatsuba: P0 = sum d0 R0, P2 = sum d1 R1, S = sum (d0 + d1)(R0 + R1), and the
-    // middle component is S - P0 - P2 (sums < 2q, products < 2^122, at most EM_BABY terms)
-    Acc128 a[TQ][TA][3];
-#pragma unroll
-    for (int b = 0; b < TQ; b++)
-#pragma unroll
-        for (int x = 0; x < TA; x++)
-#pragma unroll
-            for (int c = 0; c < 3; c++) a[b][x][c] = Acc128{0, 0};
-    u64 R0[TQ], R1[TQ], D0[TA];
-    auto load = [&](int j, u64 *r0, u64 *r1, u64 *d0) {
-#pragma unroll
-        for (int b = 0; b < TQ; b++) {
-            const u64 *Rb = R + (size_t)(q0 + b) * r_ct + (size_t)j * 2 * n_el;
-            r0[b] = b < nc ? Rb[e] : 0;
-            r1[b] = b < nc ? Rb[n_el + e] : 0;
-        }
-#pragma unroll
-        for (int x = 0; x < TA; x++) {
-            const u64 *p = x < nx ? tab.c0[(x0 + x) * nb + j] : nullptr;
-            d0[x] = p ? p[e] : 0;
-        }
-    };
-    load(0, R0, R1, D0);
-    for (int j = 0; j < nb; j++) {
-        u64 N0[TQ], N1[TQ], ND[TA];
-        if (j + 1 < nb) load(j + 1, N0, N1, ND);
-        u64 RS[TQ];
-#pragma unroll
-        for (int b = 0; b < TQ; b++) RS[b] = R0[b] + R1[b];
-#pragma unroll
-        for (int x = 0; x < TA; x++) {
-            if (x >= nx || !tab.c0[(x0 + x) * nb + j]) continue;
-            const u64 d0 = D0[x];
-            const u64 d1 = seeded_mask(seed, tab.stream[(x0 + x) * nb + j], r, k, logN, P);
-            const u64 ds = d0 + d1;
-#pragma unroll
-            for (int b = 0; b < TQ; b++) {
-                mac128(a[b][x][0], d0, R0[b]);
-                mac128(a[b][x][1], ds, RS[b]);
-                mac128(a[b][x][2], d1, R1[b]);
-            }
-        }
-        if (j + 1 < nb) {
-#pragma unroll
-            for (int b = 0; b < TQ; b++) {
-                R0[b] = N0[b];
-                R1[b] = N1[b];
-            }
-#pragma unroll
-            for (int x = 0; x < TA; x++) D0[x] = ND[x];
-        }
-    }
-#pragma unroll
-    for (int b = 0; b < TQ; b++)
-#pragma unroll
-        for (int x = 0; x < TA; x++)
-            if (b < nc && x < nx) {
-                u64 *o = acc + (size_t)(q0 + b) * a_ct + (size_t)(x0 + x) * 3 * n_el + e;
-                const u64 p0 = reduce128(a[b][x][0], P), p2 = reduce128(a[b][x][2], P);
-                const u64 mid = sub_mod(sub_mod(reduce128(a[b][x][1], P), p0, P.q), p2, P.q);
-                o[0] = add_mod(o[0], p0, P.q);
-                o[n_el] = add_mod(o[n_el], mid, P.q);
-                o[2 * n_el] = add_mod(o[2 * n_el], p2, P.q);
-            }
-}
-
-// register tile by the number of query ciphertexts multiplied together
-template <int TA, int TQ>
-void launch_mac(const EncMacTable &tab, int na, int nb, int nq, const u64 *R, size_t r_ct, u64 *acc, size_t a_ct,
-                int ell, int logN, u64 seed, const PrimeDev *pr, cudaStream_t s) {
-    const size_t n_el = (size_t)ell << logN;
-    const dim3 grid((unsigned)((n_el + 127) / 128), (unsigned)((nq + TQ - 1) / TQ), (unsigned)((na + TA - 1) / TA));
-    k_enc_mac<TA, TQ><<<grid, 128, 0, s>>>(tab, na, nb, nq, R, r_ct, acc, a_ct, ell, logN, seed, pr);
-}
-
-void enc_mac(const EncMacTable &tab, int na, int nb, int nq, const u64 *R, size_t r_ct, u64 *acc, size_t a_ct,
-             int ell, int logN, u64 seed, const PrimeDev *pr, cudaStream_t s) {
-    if (nq == 1) launch_mac<4, 1>(tab, na, nb, nq, R, r_ct, acc, a_ct, ell, logN, seed, pr, s);
-    else if (nq == 2) launch_mac<2, 2>(tab, na, nb, nq, R, r_ct, acc, a_ct, ell, logN, seed, pr, s);
-    else launch_mac<1, 4>(tab, na, nb, nq, R, r_ct, acc, a_ct, ell, logN, seed, pr, s);
-}
-
-// ---- the MAC for primes below 2^55: one CTA per tile of 32 elements (one per lane) and
+// for each element, every accumulator x, query ciphertext b and baby step j,
+//   (acc0, acc1, acc2)[b][x] += (d0 R0, d0 R1 + d1 R0, d1 R1)
+// with d the encrypted diagonal of (x, j) (c0 read, c1 regenerated) and R = rot(v_b, j),
+// by Karatsuba: P0 = sum d0 R0, P2 = sum d1 R1, S = sum (d0 + d1)(R0 + R1), middle S - P0 - P2.
+// One CTA per tile of 32 elements (one per lane) and
 // TA accumulators, its W warps covering W * TQ query ciphertexts.  The CTA regenerates the
 // masks of its accumulators' diagonals once (shared memory) for every query ciphertext it
 // covers; the rotations stream through a STAGES-deep cp.async pipeline of shared-memory
@@ -205,10 +94,10 @@ void enc_mac(const EncMacTable &tab, int na, int nb, int nq, const u64 *R, size_
 // the sums are reduced and added to the accumulators in memory.  CTAs with the same
 // element tile and different accumulators are adjacent in the grid, so a tile of
 // rotations read from HBM is reused from L2 by the others.
-constexpr int M2_TA = 2;
-constexpr int M2_TQ = 4;
-constexpr int M2_RUN = 64;
-constexpr int M2_STAGES = 4;
+constexpr int MAC_TA = 2;
+constexpr int MAC_TQ = 4;
+constexpr int MAC_RUN = 64;
+constexpr int MAC_STAGES = 4;
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
@@ -221,8 +110,8 @@ __device__ __forceinline__ void cp_async_wait() {
 }
 
 template <int W>
-constexpr size_t mac2_smem() {
-    return (size_t)(2 * M2_TA * M2_RUN * 32 + M2_STAGES * W * M2_TQ * 2 * 32) * sizeof(u64);
+constexpr size_t mac_smem() {
+    return (size_t)(2 * MAC_TA * MAC_RUN * 32 + MAC_STAGES * W * MAC_TQ * 2 * 32) * sizeof(u64);
 }
 
 // tab: [nm][nb] diagonal entries of this launch's accumulators; R: [query ct][nb][2][ell][N]
@@ -230,19 +119,19 @@ constexpr size_t mac2_smem() {
 // ciphertext), added to.
 template <int W>
 __global__ void __launch_bounds__(W * 32, 1)
-    k_enc_mac2(const EncModel::MacEntry *__restrict__ tab, int nm, int nb, int nq, const u64 *__restrict__ R,
+    k_enc_mac(const EncModel::MacEntry *__restrict__ tab, int nm, int nb, int nq, const u64 *__restrict__ R,
                size_t r_ct, u64 *__restrict__ acc, size_t a_ct, int ell, int logN, u64 seed,
                const PrimeDev *__restrict__ pr, int n_ag) {
-    constexpr int NT = W * 32, CQ = W * M2_TQ, STAGE = CQ * 2 * 32;
+    constexpr int NT = W * 32, CQ = W * MAC_TQ, STAGE = CQ * 2 * 32;
     extern __shared__ __align__(16) u64 sm2[];
-    u64 *d0s = sm2, *d1s = sm2 + M2_TA * M2_RUN * 32, *rb = sm2 + 2 * M2_TA * M2_RUN * 32;
+    u64 *d0s = sm2, *d1s = sm2 + MAC_TA * MAC_RUN * 32, *rb = sm2 + 2 * MAC_TA * MAC_RUN * 32;
     const size_t n_el = (size_t)ell << logN;
     const uint32_t nmask = (1u << logN) - 1;
     const int ag = (int)(blockIdx.x % (unsigned)n_ag);
     const size_t e0 = (size_t)(blockIdx.x / (unsigned)n_ag) * 32;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int q0 = (int)blockIdx.y * CQ;
-    const int x0 = ag * M2_TA, nx = min(M2_TA, nm - x0);
+    const int x0 = ag * MAC_TA, nx = min(MAC_TA, nm - x0);
     const size_t e = e0 + lane;
     const bool valid = e < n_el, full = e0 + 32 <= n_el;
     const PrimeDev P = pr[valid ? (int)(e >> logN) : 0];
@@ -264,21 +153,21 @@ __global__ void __launch_bounds__(W * 32, 1)
         cp_async_commit();
     };
 
-    Acc3w a[M2_TA][M2_TQ][3];
-    for (int jr = 0; jr < nb; jr += M2_RUN) {
-        const int nr = min(M2_RUN, nb - jr);
+    Acc3w a[MAC_TA][MAC_TQ][3];
+    for (int jr = 0; jr < nb; jr += MAC_RUN) {
+        const int nr = min(MAC_RUN, nb - jr);
 #pragma unroll
-        for (int x = 0; x < M2_TA; x++)
+        for (int x = 0; x < MAC_TA; x++)
 #pragma unroll
-            for (int c = 0; c < M2_TQ; c++)
+            for (int c = 0; c < MAC_TQ; c++)
 #pragma unroll
                 for (int k = 0; k < 3; k++) a[x][c][k] = Acc3w{0, 0, 0};
-        for (int st = 0; st < M2_STAGES - 1; st++) {
+        for (int st = 0; st < MAC_STAGES - 1; st++) {
             if (st < nr) issue(jr + st, st);
             else cp_async_commit();
         }
         // the run's diagonal words and regenerated masks for the CTA's accumulators
-        for (int i = threadIdx.x; i < M2_TA * nr * 32; i += NT) {
+        for (int i = threadIdx.x; i < MAC_TA * nr * 32; i += NT) {
             const int x = i / (nr * 32), rem = i - x * nr * 32, j = rem >> 5, l = rem & 31;
             const size_t ee = e0 + l;
             u64 v0 = 0, v1 = 0;
@@ -290,29 +179,29 @@ __global__ void __launch_bounds__(W * 32, 1)
                     v1 = seeded_mask(seed, te.stream, rr, (uint32_t)(ee & nmask), logN, pr[rr]);
                 }
             }
-            d0s[(x * M2_RUN + j) * 32 + l] = v0;
-            d1s[(x * M2_RUN + j) * 32 + l] = v1;
+            d0s[(x * MAC_RUN + j) * 32 + l] = v0;
+            d1s[(x * MAC_RUN + j) * 32 + l] = v1;
         }
         for (int j = 0; j < nr; j++) {
-            cp_async_wait<M2_STAGES - 2>();
+            cp_async_wait<MAC_STAGES - 2>();
             __syncthreads();  // stage j (and the masks) visible; stage j-1 no longer read
-            if (j + M2_STAGES - 1 < nr) issue(jr + j + M2_STAGES - 1, (j + M2_STAGES - 1) % M2_STAGES);
+            if (j + MAC_STAGES - 1 < nr) issue(jr + j + MAC_STAGES - 1, (j + MAC_STAGES - 1) % MAC_STAGES);
             else cp_async_commit();
-            const u64 *st = rb + (size_t)(j % M2_STAGES) * STAGE + (size_t)w * M2_TQ * 64 + lane;
-            Sp28 r0[M2_TQ], r1[M2_TQ], rs[M2_TQ];
+            const u64 *st = rb + (size_t)(j % MAC_STAGES) * STAGE + (size_t)w * MAC_TQ * 64 + lane;
+            Sp28 r0[MAC_TQ], r1[MAC_TQ], rs[MAC_TQ];
 #pragma unroll
-            for (int c = 0; c < M2_TQ; c++) {
+            for (int c = 0; c < MAC_TQ; c++) {
                 const u64 v0 = st[c * 64], v1 = st[c * 64 + 32];
                 r0[c] = split28(v0);
                 r1[c] = split28(v1);
                 rs[c] = split28(v0 + v1);
             }
 #pragma unroll
-            for (int x = 0; x < M2_TA; x++) {
-                const u64 d0 = d0s[(x * M2_RUN + j) * 32 + lane], d1 = d1s[(x * M2_RUN + j) * 32 + lane];
+            for (int x = 0; x < MAC_TA; x++) {
+                const u64 d0 = d0s[(x * MAC_RUN + j) * 32 + lane], d1 = d1s[(x * MAC_RUN + j) * 32 + lane];
                 const Sp28 s0 = split28(d0), s1 = split28(d1), ss = split28(d0 + d1);
 #pragma unroll
-                for (int c = 0; c < M2_TQ; c++) {
+                for (int c = 0; c < MAC_TQ; c++) {
                     mac_sp(a[x][c][0], s0, r0[c]);
                     mac_sp(a[x][c][1], ss, rs[c]);
                     mac_sp(a[x][c][2], s1, r1[c]);
@@ -322,10 +211,10 @@ __global__ void __launch_bounds__(W * 32, 1)
         cp_async_wait<0>();
         __syncthreads();  // every read of this run's buffers is done before the next run refills them
 #pragma unroll
-        for (int x = 0; x < M2_TA; x++)
+        for (int x = 0; x < MAC_TA; x++)
 #pragma unroll
-            for (int c = 0; c < M2_TQ; c++) {
-                const int ct = q0 + w * M2_TQ + c;
+            for (int c = 0; c < MAC_TQ; c++) {
+                const int ct = q0 + w * MAC_TQ + c;
                 if (!valid || x >= nx || ct >= nq) continue;
                 u64 *o = acc + (size_t)ct * a_ct + (size_t)(x0 + x) * 3 * n_el + e;
                 const u64 p0 = reduce128(acc3w_value(a[x][c][0]), P);
@@ -340,33 +229,33 @@ __global__ void __launch_bounds__(W * 32, 1)
 
 // per-device raise of the dynamic shared-memory limit of each instantiation
 template <int W>
-copse_status mac2_attr(int device) {
+copse_status mac_attr(int device) {
     static std::atomic<uint64_t> done{0};
     if (device >= 0 && device < 64 && (done.load(std::memory_order_acquire) & (1ull << device))) return COPSE_OK;
-    CUDA_TRY(cudaFuncSetAttribute(k_enc_mac2<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mac2_smem<W>()));
+    CUDA_TRY(cudaFuncSetAttribute(k_enc_mac<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mac_smem<W>()));
     if (device >= 0 && device < 64) done.fetch_or(1ull << device, std::memory_order_release);
     return COPSE_OK;
 }
 
 template <int W>
-copse_status launch_mac2(int device, const EncModel::MacEntry *tab, int nm, int nb, int nq, const u64 *R, size_t r_ct,
+copse_status launch_mac(int device, const EncModel::MacEntry *tab, int nm, int nb, int nq, const u64 *R, size_t r_ct,
                          u64 *acc, size_t a_ct, int ell, int logN, u64 seed, const PrimeDev *pr, cudaStream_t s) {
-    STATUS_TRY(mac2_attr<W>(device));
+    STATUS_TRY(mac_attr<W>(device));
     const size_t n_el = (size_t)ell << logN;
-    const int n_ag = (nm + M2_TA - 1) / M2_TA;
+    const int n_ag = (nm + MAC_TA - 1) / MAC_TA;
     const size_t tiles = (n_el + 31) / 32;
-    const dim3 grid((unsigned)(tiles * n_ag), (unsigned)((nq + W * M2_TQ - 1) / (W * M2_TQ)));
-    k_enc_mac2<W><<<grid, W * 32, mac2_smem<W>(), s>>>(tab, nm, nb, nq, R, r_ct, acc, a_ct, ell, logN, seed, pr, n_ag);
+    const dim3 grid((unsigned)(tiles * n_ag), (unsigned)((nq + W * MAC_TQ - 1) / (W * MAC_TQ)));
+    k_enc_mac<W><<<grid, W * 32, mac_smem<W>(), s>>>(tab, nm, nb, nq, R, r_ct, acc, a_ct, ell, logN, seed, pr, n_ag);
     LAUNCH_CHECK();
     return COPSE_OK;
 }
 
-copse_status enc_mac2(int device, const EncModel::MacEntry *tab, int nm, int nb, int nq, const u64 *R, size_t r_ct,
+copse_status enc_mac(int device, const EncModel::MacEntry *tab, int nm, int nb, int nq, const u64 *R, size_t r_ct,
                       u64 *acc, size_t a_ct, int ell, int logN, u64 seed, const PrimeDev *pr, cudaStream_t s) {
-    if (nq > 4 * M2_TQ) return launch_mac2<8>(device, tab, nm, nb, nq, R, r_ct, acc, a_ct, ell, logN, seed, pr, s);
-    if (nq > 2 * M2_TQ) return launch_mac2<4>(device, tab, nm, nb, nq, R, r_ct, acc, a_ct, ell, logN, seed, pr, s);
-    if (nq > M2_TQ) return launch_mac2<2>(device, tab, nm, nb, nq, R, r_ct, acc, a_ct, ell, logN, seed, pr, s);
-    return launch_mac2<1>(device, tab, nm, nb, nq, R, r_ct, acc, a_ct, ell, logN, seed, pr, s);
+    if (nq > 4 * MAC_TQ) return launch_mac<8>(device, tab, nm, nb, nq, R, r_ct, acc, a_ct, ell, logN, seed, pr, s);
+    if (nq > 2 * MAC_TQ) return launch_mac<4>(device, tab, nm, nb, nq, R, r_ct, acc, a_ct, ell, logN, seed, pr, s);
+    if (nq > MAC_TQ) return launch_mac<2>(device, tab, nm, nb, nq, R, r_ct, acc, a_ct, ell, logN, seed, pr, s);
+    return launch_mac<1>(device, tab, nm, nb, nq, R, r_ct, acc, a_ct, ell, logN, seed, pr, s);
 }
 
 }  // namespace
@@ -458,10 +347,10 @@ copse_status enc_model_build(copse_ctx *c, const copse_keys *keys, const Compile
     }));
     // the MAC kernels' shared-memory limit, raised here so that no attribute call falls inside
     // a graph recording
-    STATUS_TRY(mac2_attr<1>(c->device));
-    STATUS_TRY(mac2_attr<2>(c->device));
-    STATUS_TRY(mac2_attr<4>(c->device));
-    STATUS_TRY(mac2_attr<8>(c->device));
+    STATUS_TRY(mac_attr<1>(c->device));
+    STATUS_TRY(mac_attr<2>(c->device));
+    STATUS_TRY(mac_attr<4>(c->device));
+    STATUS_TRY(mac_attr<8>(c->device));
     // diagonal tables of the two products, [accumulator][baby step] in plan order
     for (int kind = 0; kind < 2; kind++) {
         const BsgsGroup &G = kind == 0 ? E.grpR : E.grpL;
@@ -509,14 +398,13 @@ copse_status enc_matmul(copse_ctx *c, const copse_evk *evk, const EncModel &E, c
         masks.assign(E.d, DCt());
         for (int k = 1; k <= E.d && st == COPSE_OK; k++) st = enc_materialize(c, E, E.idx_mask(k), &masks[k - 1], s);
     }
-    // query ciphertexts whose rotations are held at once: up to 32 for the shared-mask MAC
-    // (primes below 2^55), bounded by the device memory the group's buffers take
-    const bool mac2 = c->bits <= 55;
-    int group = mac2 ? 32 : EM_GROUP;
-    if (mac2 && c->capturing) {
+    // query ciphertexts whose rotations are held at once: up to 32 (the MAC kernel's CTA covers
+    // 32), bounded by the device memory the group's buffers take
+    int group = 32;
+    if (c->capturing) {
         // memory queries are not allowed while a graph is recorded: the last sizing
         group = E.group_hint[kind] > 0 ? E.group_hint[kind] : EM_GROUP;
-    } else if (mac2) {
+    } else {
         size_t free_b = 0, total_b = 0;
         CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
         size_t pool_idle = 0;
@@ -560,41 +448,16 @@ copse_status enc_matmul(copse_ctx *c, const copse_evk *evk, const EncModel &E, c
                 st = COPSE_ECUDA;
                 break;
             }
-            if (mac2) {
+            {
                 // every accumulator and baby step of the matrix in one launch
                 size_t present = 0;
                 for (int y = 0; y < nm; y++)
                     for (int j = 0; j < nb; j++) present += G.acc[x0 + y].diag[j] >= 0;
                 const double bytes = 8.0 * (double)n_el * ((double)present + 2.0 * nb * ng + 3.0 * nm * ng);
                 TIMED_OPS("enc_mac", bytes, 4.0 * (double)present * ng * n_el, s,
-                          st = enc_mac2(c->device, E.d_tab[kind] + (size_t)x0 * nb, nm, nb, ng, Rb, (size_t)nb * per,
+                          st = enc_mac(c->device, E.d_tab[kind] + (size_t)x0 * nb, nm, nb, ng, Rb, (size_t)nb * per,
                                         acc3, (size_t)nm * per3, ell, c->logN, E.seed, c->d_prime, s));
                 if (st) break;
-            }
-            for (int y0 = 0; !mac2 && y0 < nm; y0 += EM_ACC) {
-                const int na = std::min(EM_ACC, nm - y0);
-                for (int j0 = 0; j0 < nb; j0 += EM_BABY) {
-                    const int nbb = std::min(EM_BABY, nb - j0);
-                    EncMacTable tab;
-                    memset(&tab, 0, sizeof(tab));
-                    int present = 0;
-                    for (int y = 0; y < na; y++) {
-                        const BsgsGroup::Acc &A = G.acc[x0 + y0 + y];
-                        for (int j = 0; j < nbb; j++) {
-                            const int i = A.diag[j0 + j];
-                            if (i < 0) continue;
-                            const int idx = kind == 0 ? E.idx_R(i) : E.idx_lvl((int)A.mat + 1, i);
-                            tab.c0[y * nbb + j] = E.c0(idx);
-                            tab.stream[y * nbb + j] = MODEL_STREAM + 2ull * (u64)idx;
-                            present++;
-                        }
-                    }
-                    if (!present) continue;
-                    TIMED("enc_mac", 8.0 * (double)n_el * ((double)present + 2.0 * nbb * ng + 6.0 * na * ng), s,
-                          enc_mac(tab, na, nbb, ng, Rb + (size_t)j0 * per, (size_t)nb * per, acc3 + (size_t)y0 * per3,
-                                  (size_t)nm * per3, ell, c->logN, E.seed, c->d_prime, s));
-                    LAUNCH_CHECK();
-                }
             }
             // one relinearisation per (query ciphertext, accumulator), then the giant steps
             if ((st = relin_batch(c, evk, acc3, ng * nm, ell, inner, s))) break;

@@ -782,6 +782,132 @@ copse_status launch(copse_ctx *ctx, const NttBatch &b, cudaStream_t s, bool inve
     return COPSE_OK;
 }
 
+// ---------------------------------------------------------------- two passes fused with the IO
+// Where the cluster transform does not run (N = 2^15 by default) the fused transforms take
+// the two-pass tiled kernels: the first pass loads through the IO functor (the base
+// conversion) and writes its partial transform to scratch [npoly][nr][N]; the second pass
+// reads scratch and stores through the functor (the finish).  Residues a batch skips (the
+// ModUp digits' own primes) are copied by the first pass, one tile's part each.
+template <class IO>
+__global__ void __launch_bounds__(NT2) k_ntt_fwd_cols_io(NttBatch b, const PrimeDev *__restrict__ primes,
+                                                         const u64 *__restrict__ tw, const u64 *__restrict__ tw_sh,
+                                                         int logN, int L, int a, IO io, u64 *scratch) {
+    __shared__ u64 sm[TILE], stw[TILE], stwp[TILE];
+    const int N = 1 << logN, lb = logN - a, lc = 11 - a, C = 1 << lc, tiles = (1 << lb) >> lc;
+    const int pr = blockIdx.x / tiles, tile = blockIdx.x % tiles;
+    const int p = pr / b.nr, r = b.r0 + pr % b.nr;
+    if (ntt_skipped(b, p, r)) {
+        io.skip(p, r, tile, tiles);
+        return;
+    }
+    const int g = ntt_prime(b, r, L);
+    const u64 q = primes[g].q, q2 = 2 * q;
+    const u64 *W = tw + (size_t)g * N, *Wp = tw_sh + (size_t)g * N;
+    for (int e = threadIdx.x; e < TILE; e += NT2) {
+        sm[e] = io.load(p, r, g, ((size_t)(e >> lc) << lb) + (tile << lc) + (e & (C - 1)));
+        if (e < (1 << a)) {
+            stw[e] = W[e];
+            stwp[e] = Wp[e];
+        }
+    }
+    __syncthreads();
+    tile_fwd<true>(sm, stw, stwp, a, q, q2, [&](int gg, int i) { return (i << lc) + gg; },
+                   [&](int u, int, int il) { return (1 << u) + il; });
+    u64 *out = scratch + ((size_t)pr << logN) + (tile << lc);
+    for (int e = threadIdx.x; e < TILE; e += NT2) out[((size_t)(e >> lc) << lb) + (e & (C - 1))] = sm[e];
+}
+
+template <class IO>
+__global__ void __launch_bounds__(NT2) k_ntt_fwd_rows_io(NttBatch b, const PrimeDev *__restrict__ primes,
+                                                         const ulonglong2 *__restrict__ stg, int logN, int L, int a,
+                                                         IO io, const u64 *scratch) {
+    __shared__ u64 sm[TILE], stw[TILE], stwp[TILE];
+    const int N = 1 << logN, lb = logN - a, lr = 11 - lb, tiles = 1 << (a - lr);
+    const int pr = blockIdx.x / tiles, tile = blockIdx.x % tiles;
+    const int p = pr / b.nr, r = b.r0 + pr % b.nr;
+    if (ntt_skipped(b, p, r)) return;
+    const int g = ntt_prime(b, r, L);
+    const u64 q = primes[g].q, q2 = 2 * q;
+    const int row0 = tile << lr;
+    const u64 *in = scratch + ((size_t)pr << logN) + ((size_t)row0 << lb);
+    const ulonglong2 *st = stg + ((size_t)g * (N / TILE) + tile) * TILE;
+    const int nst = TILE - (1 << lr);
+    for (int e = threadIdx.x; e < TILE; e += NT2) {
+        sm[e] = in[e];
+        if (e < nst) {
+            const ulonglong2 v = st[e];
+            stw[e] = v.x;
+            stwp[e] = v.y;
+        }
+    }
+    __syncthreads();
+    tile_fwd<false>(sm, stw, stwp, lb, q, q2, [&](int gg, int i) { return (gg << lb) + i; },
+                    [&](int u, int gg, int il) { return ((1 << lr) * ((1 << u) - 1)) + (gg << u) + il; });
+    const u64 one_sh = primes[g].one_sh;
+    for (int e = threadIdx.x; e < TILE; e += NT2) io.store(p, r, g, ((size_t)row0 << lb) + e, fwd_reduce(sm[e], q, one_sh));
+}
+
+template <class IO>
+__global__ void __launch_bounds__(NT2) k_ntt_inv_rows_io(NttBatch b, const PrimeDev *__restrict__ primes,
+                                                         const ulonglong2 *__restrict__ stg, int logN, int L, int a,
+                                                         IO io, u64 *scratch) {
+    __shared__ u64 sm[TILE], stw[TILE], stwp[TILE];
+    const int N = 1 << logN, lb = logN - a, lr = 11 - lb, tiles = 1 << (a - lr);
+    const int pr = blockIdx.x / tiles, tile = blockIdx.x % tiles;
+    const int p = pr / b.nr, r = b.r0 + pr % b.nr;
+    if (ntt_skipped(b, p, r)) return;
+    const int g = ntt_prime(b, r, L);
+    const u64 q = primes[g].q, q2 = 2 * q;
+    const int row0 = tile << lr;
+    const ulonglong2 *st = stg + ((size_t)g * (N / TILE) + tile) * TILE;
+    const int nst = TILE - (1 << lr);
+    for (int e = threadIdx.x; e < TILE; e += NT2) {
+        sm[e] = io.load(p, r, g, ((size_t)row0 << lb) + e);
+        if (e < nst) {
+            const ulonglong2 v = st[e];
+            stw[e] = v.x;
+            stwp[e] = v.y;
+        }
+    }
+    __syncthreads();
+    tile_inv<false>(sm, stw, stwp, lb, q, q2, [&](int gg, int i) { return (gg << lb) + i; },
+                    [&](int u, int gg, int il) {
+                        return (1 << lr) * ((1 << lb) - (1 << (lb - u))) + (gg << (lb - 1 - u)) + il;
+                    });
+    const u64 one_sh = primes[g].one_sh;
+    u64 *out = scratch + ((size_t)pr << logN) + ((size_t)row0 << lb);
+    for (int e = threadIdx.x; e < TILE; e += NT2) out[e] = fwd_reduce(sm[e], q, one_sh);
+}
+
+template <class IO>
+__global__ void __launch_bounds__(NT2) k_ntt_inv_cols_io(NttBatch b, const PrimeDev *__restrict__ primes,
+                                                         const u64 *__restrict__ tw, const u64 *__restrict__ tw_sh,
+                                                         int logN, int L, int a, IO io, const u64 *scratch) {
+    __shared__ u64 sm[TILE], stw[TILE], stwp[TILE];
+    const int N = 1 << logN, lb = logN - a, lc = 11 - a, C = 1 << lc, tiles = (1 << lb) >> lc;
+    const int pr = blockIdx.x / tiles, tile = blockIdx.x % tiles;
+    const int p = pr / b.nr, r = b.r0 + pr % b.nr;
+    if (ntt_skipped(b, p, r)) return;
+    const int g = ntt_prime(b, r, L);
+    const PrimeDev P = primes[g];
+    const u64 q = P.q, q2 = 2 * q;
+    const u64 *W = tw + (size_t)g * N, *Wp = tw_sh + (size_t)g * N;
+    const u64 *in = scratch + ((size_t)pr << logN) + (tile << lc);
+    for (int e = threadIdx.x; e < TILE; e += NT2) {
+        sm[e] = in[((size_t)(e >> lc) << lb) + (e & (C - 1))];
+        if (e < (1 << a)) {
+            stw[e] = W[e];
+            stwp[e] = Wp[e];
+        }
+    }
+    __syncthreads();
+    tile_inv<true>(sm, stw, stwp, a, q, q2, [&](int gg, int i) { return (i << lc) + gg; },
+                   [&](int u, int, int il) { return (1 << (a - 1 - u)) + il; });
+    const Shoup sc = b.scale ? b.scale[r - b.r0] : Shoup{P.ninv, P.ninv_sh};
+    for (int e = threadIdx.x; e < TILE; e += NT2)
+        io.store(p, r, g, ((size_t)(e >> lc) << lb) + (tile << lc) + (e & (C - 1)), mul_shoup(sm[e], sc, q));
+}
+
 // kernel-timer family of each transform variant
 template <class IO> constexpr const char *io_family(bool inv) { return inv ? "ntt_inv" : "ntt_fwd"; }
 template <> constexpr const char *io_family<CopyIO>(bool) { return "ntt_inv_copy"; }
@@ -818,15 +944,54 @@ copse_status launch_cluster_io(copse_ctx *ctx, const NttBatch &b, const IO &io, 
     return COPSE_OK;
 }
 
+// the fused transform as two tiled launches through a scratch buffer
+template <bool INV, class IO>
+copse_status launch_tiled_io(copse_ctx *ctx, const NttBatch &b, const IO &io, cudaStream_t s) {
+    const int logN = ctx->logN, a = logN / 2;
+    const size_t words = (size_t)b.npoly * b.nr << logN;
+    u64 *scratch = nullptr;
+    STATUS_TRY(dev_alloc(ctx, (void **)&scratch, words * sizeof(u64), s));
+    const unsigned grid = (unsigned)b.npoly * (unsigned)b.nr * (unsigned)(ctx->N / TILE);
+    const double bytes = (double)b.npoly * b.nr * ctx->N * 16.0;
+    if (INV)
+        TIMED_OPS(io_family<IO>(true), bytes, butterflies(ctx, b), s, {
+            k_ntt_inv_rows_io<IO><<<grid, NT2, 0, s>>>(b, ctx->d_prime, (const ulonglong2 *)ctx->d_stw_i, logN, ctx->L,
+                                                       a, io, scratch);
+            k_ntt_inv_cols_io<IO><<<grid, NT2, 0, s>>>(b, ctx->d_prime, ctx->d_ipsi, ctx->d_ipsi_sh, logN, ctx->L, a,
+                                                       io, scratch);
+        });
+    else
+        TIMED_OPS(io_family<IO>(false), bytes, butterflies(ctx, b), s, {
+            k_ntt_fwd_cols_io<IO><<<grid, NT2, 0, s>>>(b, ctx->d_prime, ctx->d_psi, ctx->d_psi_sh, logN, ctx->L, a,
+                                                       io, scratch);
+            k_ntt_fwd_rows_io<IO><<<grid, NT2, 0, s>>>(b, ctx->d_prime, (const ulonglong2 *)ctx->d_stw_f, logN, ctx->L,
+                                                       a, io, scratch);
+        });
+    const cudaError_t e = cudaGetLastError();
+    dev_free(scratch, s);
+    if (e != cudaSuccess) {
+        set_error(std::string("fused two-pass transform: ") + cudaGetErrorString(e));
+        return COPSE_ECUDA;
+    }
+    return COPSE_OK;
+}
+
 template <bool INV = false, class IO>
 copse_status launch_fused(copse_ctx *ctx, const NttBatch &b, const IO &io, cudaStream_t s, bool *done) {
     *done = false;
     if (b.npoly <= 0 || b.nr <= 0) { *done = true; return COPSE_OK; }
-    if (!ctx->ntt_clusters || (long)b.npoly * b.nr > ctx->ntt_fused_max) return COPSE_OK;
+    if (!ctx->ntt_clusters) return COPSE_OK;
+    if (ctx->logN == 15 && !ctx->ntt_cluster16) {
+        // N = 2^15 without 16-CTA clusters: the two-pass transform fused with the IO
+        STATUS_TRY((launch_tiled_io<INV, IO>(ctx, b, io, s)));
+        *done = true;
+        return COPSE_OK;
+    }
+    if ((long)b.npoly * b.nr > ctx->ntt_fused_max) return COPSE_OK;
     if (ctx->logN == 12) STATUS_TRY((launch_cluster_io<2, INV, IO>(ctx, b, io, s)));
     else if (ctx->logN == 13) STATUS_TRY((launch_cluster_io<4, INV, IO>(ctx, b, io, s)));
     else if (ctx->logN == 14) STATUS_TRY((launch_cluster_io<8, INV, IO>(ctx, b, io, s)));
-    else if (ctx->logN == 15 && ctx->ntt_cluster16) STATUS_TRY((launch_cluster_io<16, INV, IO>(ctx, b, io, s)));
+    else if (ctx->logN == 15) STATUS_TRY((launch_cluster_io<16, INV, IO>(ctx, b, io, s)));
     else return COPSE_OK;
     *done = true;
     return COPSE_OK;
