@@ -53,6 +53,8 @@ def parse():
                     help="dnum,g_reshuffle,g_level,ntt_cluster_max[,ntt_fused_max] for the headline workload instead of tuning "
                          "(e.g. the values a tuned run printed, to profile that schedule)")
     ap.add_argument("--no-forest100", action="store_true", help="skip the N = 2^14 plaintext-model legs")
+    ap.add_argument("--forest100-only", action="store_true",
+                    help="run only the N = 2^14 plaintext-model legs and print them (counter captures of that step)")
     ap.add_argument("--forest100-steps", type=int, default=200,
                     help="steps of each N = 2^14 plaintext-model leg (one query, batched, plain)")
     return ap.parse_args()
@@ -258,6 +260,8 @@ def run_cuda(args, ws, rank, local):
     from paper_2104_09583_gb300 import copse as K
 
     ipk = int_peaks(K, local)
+    if args.forest100_only:
+        return run_forest100(args, ws, rank, local, ipk)
     line = run_headline(args, ws, rank, local, ipk)
     line["int_peaks"] = ipk
     if not args.no_forest100:
@@ -490,7 +494,7 @@ def run_forest100(args, ws, rank, local, ipk):
         got = d_bits[: nq * L].cpu().numpy().reshape(nq, L)
         return total_ms, per, bool(np.array_equal(got, K.copse_classify_plain(model, q)))
 
-    def timed_session(sess, nq, steps, warmup, seed0):
+    def timed_session(sess, nq, steps, warmup, seed0, profile=False):
         """Graph-replayed steps (copse_session_run) on device-resident features and bits."""
         q, d_feats, d_bits = make_inputs(nq, seed0 + rank)
         run = lambda seed: K.copse_session_run(sess, None, seed, stream=stream, feats_ptr=d_feats.data_ptr(),
@@ -499,11 +503,15 @@ def run_forest100(args, ws, rank, local, ipk):
             run(5000 + w)
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         torch.cuda.synchronize()
+        if profile:
+            torch.cuda.profiler.start()
         for i in range(steps):
             ev[i][0].record()
             run(6000 + i)
             ev[i][1].record()
         torch.cuda.synchronize()
+        if profile:
+            torch.cuda.profiler.stop()
         per = [ev[i][0].elapsed_time(ev[i][1]) for i in range(steps)]
         total_ms = ev[0][0].elapsed_time(ev[-1][1])
         got = d_bits[: nq * L].cpu().numpy().reshape(nq, L)
@@ -516,7 +524,8 @@ def run_forest100(args, ws, rank, local, ipk):
 
     sess1 = K.copse_session_create(ctx, keys, evk, model, 1)
     sessB = K.copse_session_create(ctx, keys, evk, model, per_ct)
-    one = leg(*timed_session(sess1, 1, steps, 3, 11), 1, steps, "graph session, one query per step")
+    one = leg(*timed_session(sess1, 1, steps, 3, 11, profile=args.profile and args.forest100_only), 1, steps,
+              "graph session, one query per step")
     batched = leg(*timed_session(sessB, per_ct, steps, 3, 21), per_ct, steps,
                   f"graph session, {per_ct} queries per ciphertext")
     plain = leg(*timed(1, steps, 3, 31), 1, steps, "host-launched operations, one query, no graph")
