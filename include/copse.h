@@ -98,6 +98,15 @@ const char *copse_last_error(void);
 copse_status copse_ctx_create(const copse_params *params, int device, copse_ctx **out);
 void copse_ctx_destroy(copse_ctx *ctx);
 
+/* Device status of the context: bits that kernels with bounded waits set when a
+ * wait ran out (COPSE_DEV_*), read after the device finished all queued work and
+ * then cleared.  COPSE_OK with *status = 0 when nothing ran out; COPSE_ETIMEOUT
+ * with the bits in *status otherwise (the results of the affected calls are
+ * not valid).  A wait of the encrypted-model multiply-accumulate (the tensor-core
+ * kernel of copse_infer on an encrypted model) gives up after 2 s. */
+#define COPSE_DEV_MAC_WAIT 1 /* the encrypted-model multiply-accumulate */
+copse_status copse_ctx_device_status(copse_ctx *ctx, int *status);
+
 /* The n_primes + alpha primes (ciphertext primes first) into out[0..cap). */
 copse_status copse_ctx_primes(const copse_ctx *ctx, uint64_t *out, size_t cap, size_t *count);
 

@@ -10,7 +10,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libcopse_gb300.so")
-SOURCES = ["ctx.cu", "ntt.cu", "ring.cu", "copse.cu", "stats.cu", "server.cu", "noalloc.cu", "tune.cu", "encmodel.cu", "peak.cu", "worklist.cu", "forest.cpp"]
+SOURCES = ["ctx.cu", "ntt.cu", "ring.cu", "copse.cu", "stats.cu", "server.cu", "noalloc.cu", "tune.cu", "encmodel.cu", "encmac.cu", "peak.cu", "worklist.cu", "forest.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall"]
 

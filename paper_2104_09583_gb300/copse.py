@@ -111,6 +111,7 @@ _SIG = {
     "copse_stats_names": (C.c_int, [C.c_char_p, C.c_size_t]),
     "copse_stats_get_ops": (C.c_int, [C.c_char_p, C.POINTER(C.c_double)]),
     "copse_measure_int_peak": (C.c_int, [vp, C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_float)]),
+    "copse_ctx_device_status": (C.c_int, [vp, C.POINTER(C.c_int)]),
 }
 for _n, (_r, _a) in _SIG.items():
     _f = getattr(_lib, _n)
@@ -149,6 +150,19 @@ def copse_ctx_create(log_n, prime_bits, n_primes, dnum=3, device=0):
 
 def copse_ctx_destroy(ctx):
     _lib.copse_ctx_destroy(ctx)
+
+
+COPSE_DEV_MAC_WAIT = 1
+
+
+def copse_ctx_device_status(ctx):
+    """The context's device status bits (COPSE_DEV_*), read after all queued work and then
+    cleared; 0 when no kernel's bounded wait ran out."""
+    st = C.c_int(0)
+    rc = _lib.copse_ctx_device_status(ctx, C.byref(st))
+    if rc not in (0, -9):  # COPSE_ETIMEOUT: the bits say which wait
+        _check(rc)
+    return st.value
 
 
 def copse_ctx_primes(ctx):

@@ -189,6 +189,7 @@ static copse_status build_tables(copse_ctx *c) {
         p3 = p3 * 3 % twoN;
     }
     STATUS_TRY(upload(c, &c->d_slot_index, slot));
+    STATUS_TRY(upload(c, &c->d_status, std::vector<int>(1, 0)));
 
     // base conversion constants
     std::vector<Shoup> modup_inv((size_t)(L + 1) * L), modup_hat((size_t)(L + 1) * L * NP);
@@ -376,6 +377,21 @@ extern "C" void copse_ctx_destroy(copse_ctx *c) {
     for (void *p : c->owned) cudaFree(p);
     if (c->pool) cudaMemPoolDestroy(c->pool);
     delete c;
+}
+
+extern "C" copse_status copse_ctx_device_status(copse_ctx *c, int *status) {
+    if (!c || !status) { set_error("null argument"); return COPSE_EINVAL; }
+    CUDA_TRY(cudaSetDevice(c->device));
+    CUDA_TRY(cudaDeviceSynchronize());
+    int v = 0;
+    CUDA_TRY(cudaMemcpy(&v, c->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    CUDA_TRY(cudaMemset(c->d_status, 0, sizeof(int)));
+    *status = v;
+    if (v) {
+        set_error("a kernel's bounded wait ran out (device status " + std::to_string(v) + ")");
+        return COPSE_ETIMEOUT;
+    }
+    return COPSE_OK;
 }
 
 extern "C" copse_status copse_ctx_primes(const copse_ctx *c, uint64_t *out, size_t cap, size_t *count) {

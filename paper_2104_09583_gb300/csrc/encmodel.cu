@@ -5,11 +5,12 @@
 // Algorithm 1 with ciphertext x ciphertext products.
 //
 // Layout: each model ciphertext is a secret-key encryption whose mask c1 = a
-// is drawn from the counter generator in evaluation form, so only c0 is kept
-// in HBM and c1 is regenerated where it is consumed (half the bytes of a full
-// ciphertext).  At NTT position k of prime r (evaluation point
-// psi_r^(2 brev(k) + 1)) a = uniform residue number (r N + brev(k)) of the
-// ciphertext's stream; c0 = m + t e - a s.
+// is drawn from the counter generator in evaluation form (seeded_mask), so only
+// c0 is kept in HBM and c1 is regenerated where it is consumed (half the bytes of
+// a full ciphertext); c0 = m + t e - a s.  The threshold planes and the level
+// masks are stored one after another ([ell][N] each); the diagonals are stored
+// element-major per matrix of the baby-step / giant-step plan ([ell N][accumulator]
+// [baby step]), the layout of the tensor-core multiply-accumulate (encmac.cu).
 #include <algorithm>
 #include <atomic>
 #include <cstring>
@@ -22,7 +23,7 @@ namespace {
 constexpr int TPB = 256;
 constexpr int EM_GROUP = 8;    // query ciphertexts per rotation group while no free-memory sizing is known
 constexpr int EM_CHUNK = 256;  // model ciphertexts encrypted per batch
-constexpr u64 MODEL_STREAM = 0x800000ull;
+constexpr int EM_GROUP_MAX = 64;  // query ciphertexts per rotation group at most
 
 unsigned nblk(size_t n) { return (unsigned)((n + TPB - 1) / TPB); }
 
@@ -30,14 +31,6 @@ uint32_t clog2u(uint32_t x) {
     uint32_t r = 0;
     while ((1u << r) < x) r++;
     return r;
-}
-
-// the mask a at NTT position pos of prime r for a ciphertext's stream
-__device__ __forceinline__ u64 seeded_mask(u64 seed, u64 stream, int r, uint32_t pos, int logN, const PrimeDev &P) {
-    const u64 j = bit_reverse(pos, logN);
-    const u64 idx = 2 * (((u64)r << logN) + j);
-    const u64 hi = rng_word(seed, stream, idx), lo = rng_word(seed, stream, idx + 1);
-    return add_mod(mul_shoup(barrett_wide(0, hi, P), P.r64, P.r64_sh, P.q), barrett_wide(0, lo, P), P.q);
 }
 
 // te[i][r][j] = t * e_i[j] mod q_r, e_i centred binomial (eta 21) from stream stream0 + 2 i + 1
@@ -79,192 +72,18 @@ __global__ void k_materialize(const u64 *c0, u64 *out, int ell, u64 seed, u64 st
     out[per + e] = seeded_mask(seed, stream, r, (uint32_t)(e & ((1ull << logN) - 1)), logN, pr[r]);
 }
 
-// Ciphertext x ciphertext products summed per accumulator, before relinearisation:
-// for each element, every accumulator x, query ciphertext b and baby step j,
-//   (acc0, acc1, acc2)[b][x] += (d0 R0, d0 R1 + d1 R0, d1 R1)
-// with d the encrypted diagonal of (x, j) (c0 read, c1 regenerated) and R = rot(v_b, j),
-// by Karatsuba: P0 = sum d0 R0, P2 = sum d1 R1, S = sum (d0 + d1)(R0 + R1), middle S - P0 - P2.
-// One CTA per tile of 32 elements (one per lane) and
-// TA accumulators, its W warps covering W * TQ query ciphertexts.  The CTA regenerates the
-// masks of its accumulators' diagonals once (shared memory) for every query ciphertext it
-// covers; the rotations stream through a STAGES-deep cp.async pipeline of shared-memory
-// tiles (32 elements x 2 components per query ciphertext and baby step); each thread
-// keeps TA x TQ Karatsuba triples as exact split-28 partial sums (Acc3w) in registers.
-// Baby steps are taken in runs of RUN (the partial sums' exact capacity); after each run
-// the sums are reduced and added to the accumulators in memory.  CTAs with the same
-// element tile and different accumulators are adjacent in the grid, so a tile of
-// rotations read from HBM is reused from L2 by the others.
-constexpr int MAC_TA = 2;
-constexpr int MAC_TQ = 4;
-constexpr int MAC_RUN = 64;
-constexpr int MAC_STAGES = 4;
-
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
-
-template <int W>
-constexpr size_t mac_smem() {
-    return (size_t)(2 * MAC_TA * MAC_RUN * 32 + MAC_STAGES * W * MAC_TQ * 2 * 32) * sizeof(u64);
-}
-
-// tab: [nm][nb] diagonal entries of this launch's accumulators; R: [query ct][nb][2][ell][N]
-// (r_ct words per query ciphertext); acc: [query ct][nm][3][ell][N] (a_ct words per query
-// ciphertext), added to.
-template <int W>
-__global__ void __launch_bounds__(W * 32, 1)
-    k_enc_mac(const EncModel::MacEntry *__restrict__ tab, int nm, int nb, int nq, const u64 *__restrict__ R,
-               size_t r_ct, u64 *__restrict__ acc, size_t a_ct, int ell, int logN, u64 seed,
-               const PrimeDev *__restrict__ pr, int n_ag) {
-    constexpr int NT = W * 32, CQ = W * MAC_TQ, STAGE = CQ * 2 * 32;
-    extern __shared__ __align__(16) u64 sm2[];
-    u64 *d0s = sm2, *d1s = sm2 + MAC_TA * MAC_RUN * 32, *rb = sm2 + 2 * MAC_TA * MAC_RUN * 32;
-    const size_t n_el = (size_t)ell << logN;
-    const uint32_t nmask = (1u << logN) - 1;
-    const int ag = (int)(blockIdx.x % (unsigned)n_ag);
-    const size_t e0 = (size_t)(blockIdx.x / (unsigned)n_ag) * 32;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int q0 = (int)blockIdx.y * CQ;
-    const int x0 = ag * MAC_TA, nx = min(MAC_TA, nm - x0);
-    const size_t e = e0 + lane;
-    const bool valid = e < n_el, full = e0 + 32 <= n_el;
-    const PrimeDev P = pr[valid ? (int)(e >> logN) : 0];
-
-    // rotation tile of baby step j into stage buffer `st`: rows (query ct, component) of 32 words
-    auto issue = [&](int j, int st) {
-        u64 *dst = rb + (size_t)st * STAGE;
-        for (int c = threadIdx.x; c < CQ * 2 * 16; c += NT) {
-            const int row = c >> 4, part = c & 15, ct = q0 + (row >> 1), comp = row & 1;
-            u64 *d = dst + row * 32 + part * 2;
-            const u64 *src = R + (size_t)ct * r_ct + ((size_t)j * 2 + comp) * n_el + e0 + part * 2;
-            if (ct < nq && full) {
-                cp_async16(d, src);
-            } else {
-                d[0] = (ct < nq && e0 + part * 2 < n_el) ? src[0] : 0;
-                d[1] = (ct < nq && e0 + part * 2 + 1 < n_el) ? src[1] : 0;
-            }
-        }
-        cp_async_commit();
-    };
-
-    Acc3w a[MAC_TA][MAC_TQ][3];
-    for (int jr = 0; jr < nb; jr += MAC_RUN) {
-        const int nr = min(MAC_RUN, nb - jr);
-#pragma unroll
-        for (int x = 0; x < MAC_TA; x++)
-#pragma unroll
-            for (int c = 0; c < MAC_TQ; c++)
-#pragma unroll
-                for (int k = 0; k < 3; k++) a[x][c][k] = Acc3w{0, 0, 0};
-        for (int st = 0; st < MAC_STAGES - 1; st++) {
-            if (st < nr) issue(jr + st, st);
-            else cp_async_commit();
-        }
-        // the run's diagonal words and regenerated masks for the CTA's accumulators
-        for (int i = threadIdx.x; i < MAC_TA * nr * 32; i += NT) {
-            const int x = i / (nr * 32), rem = i - x * nr * 32, j = rem >> 5, l = rem & 31;
-            const size_t ee = e0 + l;
-            u64 v0 = 0, v1 = 0;
-            if (x < nx && ee < n_el) {
-                const EncModel::MacEntry te = tab[(size_t)(x0 + x) * nb + jr + j];
-                if (te.c0) {
-                    const int rr = (int)(ee >> logN);
-                    v0 = te.c0[ee];
-                    v1 = seeded_mask(seed, te.stream, rr, (uint32_t)(ee & nmask), logN, pr[rr]);
-                }
-            }
-            d0s[(x * MAC_RUN + j) * 32 + l] = v0;
-            d1s[(x * MAC_RUN + j) * 32 + l] = v1;
-        }
-        for (int j = 0; j < nr; j++) {
-            cp_async_wait<MAC_STAGES - 2>();
-            __syncthreads();  // stage j (and the masks) visible; stage j-1 no longer read
-            if (j + MAC_STAGES - 1 < nr) issue(jr + j + MAC_STAGES - 1, (j + MAC_STAGES - 1) % MAC_STAGES);
-            else cp_async_commit();
-            const u64 *st = rb + (size_t)(j % MAC_STAGES) * STAGE + (size_t)w * MAC_TQ * 64 + lane;
-            Sp28 r0[MAC_TQ], r1[MAC_TQ], rs[MAC_TQ];
-#pragma unroll
-            for (int c = 0; c < MAC_TQ; c++) {
-                const u64 v0 = st[c * 64], v1 = st[c * 64 + 32];
-                r0[c] = split28(v0);
-                r1[c] = split28(v1);
-                rs[c] = split28(v0 + v1);
-            }
-#pragma unroll
-            for (int x = 0; x < MAC_TA; x++) {
-                const u64 d0 = d0s[(x * MAC_RUN + j) * 32 + lane], d1 = d1s[(x * MAC_RUN + j) * 32 + lane];
-                const Sp28 s0 = split28(d0), s1 = split28(d1), ss = split28(d0 + d1);
-#pragma unroll
-                for (int c = 0; c < MAC_TQ; c++) {
-                    mac_sp(a[x][c][0], s0, r0[c]);
-                    mac_sp(a[x][c][1], ss, rs[c]);
-                    mac_sp(a[x][c][2], s1, r1[c]);
-                }
-            }
-        }
-        cp_async_wait<0>();
-        __syncthreads();  // every read of this run's buffers is done before the next run refills them
-#pragma unroll
-        for (int x = 0; x < MAC_TA; x++)
-#pragma unroll
-            for (int c = 0; c < MAC_TQ; c++) {
-                const int ct = q0 + w * MAC_TQ + c;
-                if (!valid || x >= nx || ct >= nq) continue;
-                u64 *o = acc + (size_t)ct * a_ct + (size_t)(x0 + x) * 3 * n_el + e;
-                const u64 p0 = reduce128(acc3w_value(a[x][c][0]), P);
-                const u64 sv = reduce128(acc3w_value(a[x][c][1]), P);
-                const u64 p2 = reduce128(acc3w_value(a[x][c][2]), P);
-                o[0] = add_mod(o[0], p0, P.q);
-                o[n_el] = add_mod(o[n_el], sub_mod(sub_mod(sv, p0, P.q), p2, P.q), P.q);
-                o[2 * n_el] = add_mod(o[2 * n_el], p2, P.q);
-            }
-    }
-}
-
-// per-device raise of the dynamic shared-memory limit of each instantiation
-template <int W>
-copse_status mac_attr(int device) {
-    static std::atomic<uint64_t> done{0};
-    if (device >= 0 && device < 64 && (done.load(std::memory_order_acquire) & (1ull << device))) return COPSE_OK;
-    CUDA_TRY(cudaFuncSetAttribute(k_enc_mac<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mac_smem<W>()));
-    if (device >= 0 && device < 64) done.fetch_or(1ull << device, std::memory_order_release);
-    return COPSE_OK;
-}
-
-template <int W>
-copse_status launch_mac(int device, const EncModel::MacEntry *tab, int nm, int nb, int nq, const u64 *R, size_t r_ct,
-                         u64 *acc, size_t a_ct, int ell, int logN, u64 seed, const PrimeDev *pr, cudaStream_t s) {
-    STATUS_TRY(mac_attr<W>(device));
-    const size_t n_el = (size_t)ell << logN;
-    const int n_ag = (nm + MAC_TA - 1) / MAC_TA;
-    const size_t tiles = (n_el + 31) / 32;
-    const dim3 grid((unsigned)(tiles * n_ag), (unsigned)((nq + W * MAC_TQ - 1) / (W * MAC_TQ)));
-    k_enc_mac<W><<<grid, W * 32, mac_smem<W>(), s>>>(tab, nm, nb, nq, R, r_ct, acc, a_ct, ell, logN, seed, pr, n_ag);
-    LAUNCH_CHECK();
-    return COPSE_OK;
-}
-
-copse_status enc_mac(int device, const EncModel::MacEntry *tab, int nm, int nb, int nq, const u64 *R, size_t r_ct,
-                      u64 *acc, size_t a_ct, int ell, int logN, u64 seed, const PrimeDev *pr, cudaStream_t s) {
-    if (nq > 4 * MAC_TQ) return launch_mac<8>(device, tab, nm, nb, nq, R, r_ct, acc, a_ct, ell, logN, seed, pr, s);
-    if (nq > 2 * MAC_TQ) return launch_mac<4>(device, tab, nm, nb, nq, R, r_ct, acc, a_ct, ell, logN, seed, pr, s);
-    if (nq > MAC_TQ) return launch_mac<2>(device, tab, nm, nb, nq, R, r_ct, acc, a_ct, ell, logN, seed, pr, s);
-    return launch_mac<1>(device, tab, nm, nb, nq, R, r_ct, acc, a_ct, ell, logN, seed, pr, s);
-}
-
 }  // namespace
 
 EncModel::~EncModel() {
     if (store) cudaFree(store);
-    for (MacEntry *t : d_tab)
-        if (t) cudaFree(t);
+    for (auto &mats : mac)
+        for (MacMat &M : mats) {
+            if (M.c0) cudaFree(M.c0);
+            if (M.idx) cudaFree(M.idx);
+        }
 }
+
+copse_status enc_mac_tc_attr(int device);
 
 copse_status enc_model_build(copse_ctx *c, const copse_keys *keys, const CompiledForest &f, u64 seed, EncModel &E,
                              cudaStream_t s) {
@@ -284,24 +103,63 @@ copse_status enc_model_build(copse_ctx *c, const copse_keys *keys, const Compile
     const int n_ct = E.p + E.q + E.d * E.b + E.d;
     E.level.assign(n_ct, 0);
     E.off.assign(n_ct, 0);
+    E.at.assign(n_ct, EncModel::DiagAt{});
+    for (int i = 0; i < n_ct; i++) E.level[i] = i < E.p ? L : (i < E.p + E.q ? E.lvl_D : E.lvl_B);
+    // the diagonals' blocks: one per matrix of each plan, [ell N][nm][nb]
+    for (int kind = 0; kind < 2; kind++) {
+        const BsgsGroup &G = kind == 0 ? E.grpR : E.grpL;
+        const int nb = (int)G.baby.size(), ell = kind == 0 ? E.lvl_D : E.lvl_B;
+        E.mac[kind].assign(G.n_mat, EncModel::MacMat{});
+        for (int x = 0; x < (int)G.acc.size(); x++) {
+            EncModel::MacMat &M = E.mac[kind][G.acc[x].mat];
+            if (M.nm == 0) M.x0 = x;
+            M.nm++;
+        }
+        for (int a = 0; a < (int)G.n_mat; a++) {
+            EncModel::MacMat &M = E.mac[kind][a];
+            M.nb = nb;
+            M.ell = ell;
+            if (M.nm == 0 || nb == 0) continue;
+            std::vector<uint32_t> idx((size_t)M.nm * nb, ~0u);
+            for (int y = 0; y < M.nm; y++)
+                for (int j = 0; j < nb; j++) {
+                    const int i = G.acc[M.x0 + y].diag[j];
+                    if (i < 0) continue;
+                    const int id = kind == 0 ? E.idx_R(i) : E.idx_lvl(a + 1, i);
+                    idx[(size_t)y * nb + j] = (uint32_t)id;
+                    E.at[id] = EncModel::DiagAt{kind, a, (uint32_t)(y * nb + j)};
+                }
+            const size_t words = ((size_t)ell * N) * M.nm * nb;
+            CUDA_TRY(cudaMalloc(&M.c0, words * sizeof(u64)));
+            CUDA_TRY(cudaMemsetAsync(M.c0, 0, words * sizeof(u64), s));
+            CUDA_TRY(cudaMalloc(&M.idx, idx.size() * sizeof(uint32_t)));
+            CUDA_TRY(cudaMemcpy(M.idx, idx.data(), idx.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
+        }
+    }
+    for (int i = 0; i < n_ct; i++)
+        if (E.at[i].kind < 0 && i >= E.p && i < E.p + E.q + E.d * E.b) {
+            set_error("internal: a diagonal outside the baby-step / giant-step plan");
+            return COPSE_EINVAL;
+        }
     size_t words = 0;
     for (int i = 0; i < n_ct; i++) {
-        E.level[i] = i < E.p ? L : (i < E.p + E.q ? E.lvl_D : E.lvl_B);
+        if (E.at[i].kind >= 0) continue;
         E.off[i] = words;
         words += (size_t)E.level[i] * N;
     }
     CUDA_TRY(cudaMalloc(&E.store, std::max<size_t>(words, 1) * sizeof(u64)));
     const u64 t = c->t;
-    // runs of consecutive indices at one level, encoded and encrypted in batches
+    // runs of consecutive indices at one level, encoded and encrypted in batches; diagonals are
+    // scattered from the batch into their matrix's block
     auto run = [&](int idx0, int n, const std::function<void(int, uint32_t *)> &fill) -> copse_status {
         const int ell = E.level[idx0];
-        std::vector<uint32_t> pat;
+        std::vector<uint32_t> pat, pos;
         for (int i0 = 0; i0 < n; i0 += EM_CHUNK) {
             const int nc = std::min(EM_CHUNK, n - i0);
             pat.assign((size_t)nc * SP, 0u);
             for (int i = 0; i < nc; i++) fill(i0 + i, pat.data() + (size_t)i * SP);
             Scratch sc(s);
-            u64 *mt = nullptr, *te = nullptr;
+            u64 *mt = nullptr, *te = nullptr, *c0 = nullptr;
             STATUS_TRY(sc.get(c, &mt, (size_t)nc * ell * N));
             STATUS_TRY(sc.get(c, &te, (size_t)nc * ell * N));
             STATUS_TRY(encode_patterns(c, pat, nc, SP, SP, ell, 0, mt, s));
@@ -309,9 +167,32 @@ copse_status enc_model_build(copse_ctx *c, const copse_keys *keys, const Compile
             k_model_noise<<<nblk((size_t)nc * ell * N), TPB, 0, s>>>(te, nc, ell, seed, stream0, c->logN, c->d_prime);
             LAUNCH_CHECK();
             STATUS_TRY(ntt_forward(c, NttBatch{te, (size_t)ell * N, nc, 0, ell, ell, -1}, s));
-            k_sk_c0<<<nblk((size_t)nc * ell * N), TPB, 0, s>>>(mt, te, keys->s_hat, E.store + E.off[idx0 + i0], nc, ell,
-                                                               seed, stream0, c->logN, c->d_prime);
+            const EncModel::DiagAt &at = E.at[idx0 + i0];
+            if (at.kind < 0) {
+                c0 = E.store + E.off[idx0 + i0];
+            } else {
+                STATUS_TRY(sc.get(c, &c0, (size_t)nc * ell * N));
+            }
+            k_sk_c0<<<nblk((size_t)nc * ell * N), TPB, 0, s>>>(mt, te, keys->s_hat, c0, nc, ell, seed, stream0,
+                                                               c->logN, c->d_prime);
             LAUNCH_CHECK();
+            if (at.kind >= 0) {
+                pos.resize(nc);
+                for (int i = 0; i < nc; i++) {
+                    const EncModel::DiagAt &ai = E.at[idx0 + i0 + i];
+                    if (ai.kind != at.kind || ai.mat != at.mat) {
+                        set_error("internal: a batch of diagonals spans two matrices");
+                        return COPSE_EINVAL;
+                    }
+                    pos[i] = ai.pos;
+                }
+                u64 *pw = nullptr;
+                STATUS_TRY(sc.get(c, &pw, (size_t)(nc + 1) / 2));
+                uint32_t *d_pos = (uint32_t *)pw;
+                CUDA_TRY(cudaMemcpyAsync(d_pos, pos.data(), nc * sizeof(uint32_t), cudaMemcpyHostToDevice, s));
+                STATUS_TRY(mac_scatter(c, c0, d_pos, nc, E.mac[at.kind][at.mat], s));
+                CUDA_TRY(cudaStreamSynchronize(s));  // pos is reused by the next batch
+            }
         }
         return COPSE_OK;
     };
@@ -345,27 +226,9 @@ copse_status enc_model_build(copse_ctx *c, const copse_keys *keys, const Compile
         for (int sg = 0; sg < NS; sg++)
             for (uint32_t x = 0; x < f.L; x++) pat[(size_t)sg * B + x] = f.mask_at((uint32_t)k0 + 1, x, (uint32_t)sg);
     }));
-    // the MAC kernels' shared-memory limit, raised here so that no attribute call falls inside
-    // a graph recording
-    STATUS_TRY(mac_attr<1>(c->device));
-    STATUS_TRY(mac_attr<2>(c->device));
-    STATUS_TRY(mac_attr<4>(c->device));
-    STATUS_TRY(mac_attr<8>(c->device));
-    // diagonal tables of the two products, [accumulator][baby step] in plan order
-    for (int kind = 0; kind < 2; kind++) {
-        const BsgsGroup &G = kind == 0 ? E.grpR : E.grpL;
-        const size_t nb = G.baby.size();
-        std::vector<EncModel::MacEntry> h(G.acc.size() * nb, EncModel::MacEntry{nullptr, 0});
-        for (size_t x = 0; x < G.acc.size(); x++)
-            for (size_t j = 0; j < nb; j++) {
-                const int i = G.acc[x].diag[j];
-                if (i < 0) continue;
-                const int idx = kind == 0 ? E.idx_R(i) : E.idx_lvl((int)G.acc[x].mat + 1, i);
-                h[x * nb + j] = EncModel::MacEntry{E.c0(idx), MODEL_STREAM + 2ull * (u64)idx};
-            }
-        CUDA_TRY(cudaMalloc(&E.d_tab[kind], std::max<size_t>(h.size(), 1) * sizeof(EncModel::MacEntry)));
-        CUDA_TRY(cudaMemcpy(E.d_tab[kind], h.data(), h.size() * sizeof(EncModel::MacEntry), cudaMemcpyHostToDevice));
-    }
+    // the multiply-accumulate kernel's shared-memory limit, raised here so that no attribute call
+    // falls inside a graph recording
+    STATUS_TRY(enc_mac_tc_attr(c->device));
     CUDA_TRY(cudaStreamSynchronize(s));
     return COPSE_OK;
 }
@@ -374,8 +237,19 @@ copse_status enc_materialize(copse_ctx *c, const EncModel &E, int idx, DCt *out,
     if (idx < 0 || idx >= (int)E.level.size()) { set_error("model ciphertext index out of range"); return COPSE_EINVAL; }
     const int ell = E.level[idx];
     STATUS_TRY(ct_alloc(c, out, ell, 2, s));
-    k_materialize<<<nblk((size_t)ell * c->N), TPB, 0, s>>>(E.c0(idx), out->data, ell, E.seed,
-                                                           MODEL_STREAM + 2ull * (u64)idx, c->logN, c->d_prime);
+    const EncModel::DiagAt &at = E.at[idx];
+    Scratch sc(s);
+    const u64 *c0 = nullptr;
+    if (at.kind < 0) {
+        c0 = E.c0(idx);
+    } else {
+        u64 *g = nullptr;
+        STATUS_TRY(sc.get(c, &g, (size_t)ell * c->N));
+        STATUS_TRY(mac_gather(c, E.mac[at.kind][at.mat], at.pos, g, s));
+        c0 = g;
+    }
+    k_materialize<<<nblk((size_t)ell * c->N), TPB, 0, s>>>(c0, out->data, ell, E.seed, MODEL_STREAM + 2ull * (u64)idx,
+                                                           c->logN, c->d_prime);
     LAUNCH_CHECK();
     return COPSE_OK;
 }
@@ -398,9 +272,10 @@ copse_status enc_matmul(copse_ctx *c, const copse_evk *evk, const EncModel &E, c
         masks.assign(E.d, DCt());
         for (int k = 1; k <= E.d && st == COPSE_OK; k++) st = enc_materialize(c, E, E.idx_mask(k), &masks[k - 1], s);
     }
-    // query ciphertexts whose rotations are held at once: up to 32 (the MAC kernel's CTA covers
-    // 32), bounded by the device memory the group's buffers take
-    int group = 32;
+    // query ciphertexts whose rotations are held at once: up to EM_GROUP_MAX (every diagonal and
+    // its regenerated mask is read once per group), bounded by the device memory the group's
+    // buffers take
+    int group = EM_GROUP_MAX;
     if (c->capturing) {
         // memory queries are not allowed while a graph is recorded: the last sizing
         group = E.group_hint[kind] > 0 ? E.group_hint[kind] : EM_GROUP;
@@ -421,17 +296,26 @@ copse_status enc_matmul(copse_ctx *c, const copse_evk *evk, const EncModel &E, c
             max_acc = std::max(max_acc, n);
         }
         const size_t per_ct = ((size_t)nb * per + max_acc * (per3 + per)) * sizeof(u64);
+        const size_t rot_tmp = (size_t)nb * per * sizeof(u64);  // one query ciphertext's rotations
         const size_t budget = (free_b + pool_idle) / 10 * 7;
-        while (group > 1 && (size_t)group * per_ct > budget) group /= 2;
+        while (group > 1 && (size_t)group * per_ct + rot_tmp > budget) group /= 2;
         E.group_hint[kind] = group;
     }
     for (int g0 = 0; g0 < nv && st == COPSE_OK; g0 += group) {
         const int ng = std::min(group, nv - g0);
         Scratch sc(s);
-        // baby steps: rotations of every query ciphertext of the group (one ModUp each)
-        u64 *Rb = nullptr;
+        // baby steps: rotations of every query ciphertext of the group (one ModUp each), moved
+        // into the element-major layout [ell N][ng][nb][2] of the multiply-accumulate
+        u64 *Rb = nullptr, *rot = nullptr;
         if ((st = sc.get(c, &Rb, (size_t)ng * nb * per))) break;
-        for (int q = 0; q < ng && st == COPSE_OK; q++) st = op_rotations(c, evk, v[g0 + q], G.baby, Rb + (size_t)q * nb * per, s);
+        {
+            Scratch sr(s);
+            if ((st = sr.get(c, &rot, (size_t)nb * per))) break;
+            for (int q = 0; q < ng && st == COPSE_OK; q++) {
+                st = op_rotations(c, evk, v[g0 + q], G.baby, rot, s);
+                if (st == COPSE_OK) st = rot_to_elements(c, rot, nb, ng, q, ell, Rb, s);
+            }
+        }
         // matrix by matrix: products, relinearisation, giant steps (+ mask)
         for (int a = 0; a < n_mat && st == COPSE_OK; a++) {
             int x0 = 0;
@@ -450,13 +334,18 @@ copse_status enc_matmul(copse_ctx *c, const copse_evk *evk, const EncModel &E, c
             }
             {
                 // every accumulator and baby step of the matrix in one launch
+                const EncModel::MacMat &M = E.mac[kind][a];
+                if (M.nm != nm || M.x0 != x0 || M.ell != ell) {
+                    set_error("internal: diagonal block does not match the plan");
+                    st = COPSE_EINVAL;
+                    break;
+                }
                 size_t present = 0;
                 for (int y = 0; y < nm; y++)
                     for (int j = 0; j < nb; j++) present += G.acc[x0 + y].diag[j] >= 0;
                 const double bytes = 8.0 * (double)n_el * ((double)present + 2.0 * nb * ng + 3.0 * nm * ng);
-                TIMED_OPS("enc_mac", bytes, 4.0 * (double)present * ng * n_el, s,
-                          st = enc_mac(c->device, E.d_tab[kind] + (size_t)x0 * nb, nm, nb, ng, Rb, (size_t)nb * per,
-                                        acc3, (size_t)nm * per3, ell, c->logN, E.seed, c->d_prime, s));
+                TIMED_OPS("enc_mac", bytes, enc_mac_tc_flops(M, ng, c->logN), s,
+                          st = enc_mac_tc(c, M, Rb, ng, acc3, (size_t)nm * per3, E.seed, s));
                 if (st) break;
             }
             // one relinearisation per (query ciphertext, accumulator), then the giant steps

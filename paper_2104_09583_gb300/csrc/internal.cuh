@@ -188,6 +188,35 @@ __device__ __forceinline__ u64 rng_word(u64 seed, u64 stream, u64 idx) {
     return z ^ (z >> 31);
 }
 
+// Encrypted-model ciphertexts are secret-key encryptions whose mask a is drawn from the
+// counter generator in evaluation form: stream MODEL_STREAM + 2 i for model ciphertext i
+// (its noise from stream MODEL_STREAM + 2 i + 1).  At NTT position pos of prime r
+// (evaluation point psi_r^(2 brev(pos) + 1)) a is the uniform residue number r N + brev(pos)
+// of the stream: two 64-bit words hi, lo give (hi 2^64 + lo) mod q.
+constexpr u64 MODEL_STREAM = 0x800000ull;
+__device__ __forceinline__ u64 seeded_mask(u64 seed, u64 stream, int r, uint32_t pos, int logN, const PrimeDev &P) {
+    const u64 j = bit_reverse(pos, logN);
+    const u64 idx = 2 * (((u64)r << logN) + j);
+    const u64 hi = rng_word(seed, stream, idx), lo = rng_word(seed, stream, idx + 1);
+    return add_mod(mul_shoup(barrett_wide(0, hi, P), P.r64, P.r64_sh, P.q), barrett_wide(0, lo, P), P.q);
+}
+
+// 16-byte asynchronous copies global -> shared (cp.async, grouped per thread)
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
 // ---------------------------------------------------------------- context
 // Base-conversion constants.  Primes are addressed by a global index g:
 // 0..L-1 ciphertext primes, L..L+alpha-1 special primes, L+alpha = t.
@@ -258,6 +287,9 @@ struct copse_ctx {
     long ntt_cluster_max = 1L << 30;
     long ntt_fused_max = 1L << 30;    // the same crossover for the transforms fused with base conversions
     bool ntt_cluster16 = false;       // N = 2^15: the device places 16-CTA clusters (non-portable size)
+    // device status word: kernels whose bounded waits ran out set bits here (COPSE_DEV_*);
+    // read and cleared by copse_ctx_device_status
+    int *d_status = nullptr;
 
     int ext_prime(int ell, int r) const { return r < ell ? r : L + (r - ell); }
     int t_index() const { return L + alpha; }
@@ -490,18 +522,29 @@ struct EncModel {
     uint32_t g_r = 0, g_l = 0;       // baby-step plan the diagonals were shifted for
     int lvl_D = 0, lvl_B = 0;
     int p = 0, q = 0, b = 0, d = 0;
-    u64 *store = nullptr;
-    // per product kind (0 reshuffle, 1 levels): for every accumulator of the plan and every
-    // baby step, the c0 and mask stream of its diagonal (c0 null = none), [nacc][nbaby]
-    struct MacEntry {
-        const u64 *c0;
-        u64 stream;
+    u64 *store = nullptr;            // c0 of the threshold planes and the level masks, [ell][N] each
+    // The diagonals of the two products (kind 0 reshuffle, 1 levels) in the layout of the
+    // tensor-core multiply-accumulate, one block per matrix of the plan: c0 element-major
+    // [ell N][nm][nb] (zero where the plan has no diagonal) and the model ciphertext index of
+    // each (accumulator, baby step), [nm][nb] (~0u = none), which names its mask stream.
+    struct MacMat {
+        u64 *c0 = nullptr;
+        uint32_t *idx = nullptr;
+        int nm = 0, nb = 0, ell = 0;
+        int x0 = 0;                  // the matrix's first accumulator in the plan
     };
-    MacEntry *d_tab[2] = {nullptr, nullptr};
+    std::vector<MacMat> mac[2];
+    // where each model ciphertext's c0 lives: kind -1 in `store` at off[i], else in
+    // mac[kind][mat] at position pos = x nb + j of every element
+    struct DiagAt {
+        int kind = -1, mat = 0;
+        uint32_t pos = 0;
+    };
+    std::vector<DiagAt> at;
     // query ciphertexts per rotation group of each product kind, as last sized from free
     // device memory outside graph capture (0 = not sized yet)
     mutable int group_hint[2] = {0, 0};
-    std::vector<size_t> off;         // word offset of each ciphertext's c0
+    std::vector<size_t> off;         // word offset of each stored ciphertext's c0
     std::vector<int> level;
     BsgsGroup grpR, grpL;            // dense plans (every diagonal present)
     int idx_thr(int i) const { return i; }
@@ -519,6 +562,24 @@ copse_status enc_materialize(copse_ctx *c, const EncModel &E, int idx, DCt *out,
 // (kind 1): out[i][matrix]; the query ciphertexts share every diagonal read
 copse_status enc_matmul(copse_ctx *c, const copse_evk *evk, const EncModel &E, const std::vector<DCt> &v, int kind,
                         std::vector<std::vector<DCt>> &out, cudaStream_t s);
+// Tensor-core multiply-accumulate of one matrix (encmac.cu): for every element e, query
+// ciphertext b < nq and accumulator x of M,
+//   (acc0, acc1, acc2)[b][x][e] += sum_j (d0 R0, d0 R1 + d1 R0, d1 R1)
+// with d the diagonal (x, j) (c0 from M, c1 regenerated from its stream) and R the rotation
+// j of query ciphertext b, R element-major [ell N][nq][nb][2]; acc [nq][nm][3][ell N]
+// (a_ct words per query ciphertext).
+copse_status enc_mac_tc(copse_ctx *c, const EncModel::MacMat &M, const u64 *R, int nq, u64 *acc, size_t a_ct,
+                        u64 seed, cudaStream_t s);
+// rotations [nb][2][ell N] of query ciphertext b into the element-major layout of enc_mac_tc
+// f16 multiply-add operations (2 per digit product) the tensor cores issue for one enc_mac_tc
+// launch of nq query ciphertexts (padding rows, columns and baby steps included)
+double enc_mac_tc_flops(const EncModel::MacMat &M, int nq, int logN);
+copse_status rot_to_elements(copse_ctx *c, const u64 *rot, int nb, int nq, int b, int ell, u64 *R, cudaStream_t s);
+// c0 of nc model ciphertexts [nc][ell N] into matrix M at positions pos[i] (device array)
+copse_status mac_scatter(copse_ctx *c, const u64 *c0, const uint32_t *pos, int nc, const EncModel::MacMat &M,
+                         cudaStream_t s);
+// c0 [ell N] of the diagonal at position pos of matrix M
+copse_status mac_gather(copse_ctx *c, const EncModel::MacMat &M, uint32_t pos, u64 *c0, cudaStream_t s);
 
 // Giant steps over per-accumulator ciphertexts inner [nacc][2][ell][N] (accumulators of
 // one matrix contiguous, giant steps ascending): per matrix a

@@ -34,12 +34,6 @@ struct WlDev {
     WlItem it[WL_MAX];
 };
 
-__device__ __forceinline__ unsigned long long global_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
 __global__ void __launch_bounds__(WL_TPB) k_worklist(const WlDev L, int *counters, int logN,
                                                      const PrimeDev *__restrict__ pr, unsigned long long timeout_ns) {
     // counters: [0] next tile, [1] error flag, [2] item of the failed wait, [2 + 1 + i] tiles done of item i
