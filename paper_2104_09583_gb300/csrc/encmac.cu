@@ -9,32 +9,39 @@
 // of residues mod q.  Every element has its own matrices, so the GEMMs are batched over
 // the elements, one at a time per CTA.
 //
-// Exactness.  A residue v < q < 2^55 is written in eight base-256 digits,
-// v = sum_{i<8} s_i 256^i: with w = v + C, C = 0x0080808080808080 (128 in bytes 0-6),
-// s_i = byte i of w minus 128 for i < 7 (in [-128, 127]) and s_7 = byte 7 of w, which is 0
-// or 1 (w < 2^55 + C < 2^57; it is 1 for the top 1/256 of the residues of a prime near
-// 2^55).  A digit is exact in fp16 and the product of two digits is at most 2^14 in
-// magnitude, so the f32 accumulator of the MMA holds a sum of up to 256 such products
-// exactly (|sum| <= 2^22).  The diagonals' digits sit in the M dimension (row 8 x + a for
-// digit a of accumulator x) and the rotations' digits in the N dimension (column
-// 8 (2 b + c) + a' for digit a' of component c of query b), so the accumulator holds, for
-// every digit pair (a, a'), the exact partial sum D_aa' = sum_j s_a(d[x][j]) s_a'(R_c[j][b]),
-// and the product sum is sum_aa' D_aa' 256^(a + a'): rebuilt in 128-bit integers and
-// reduced mod q once.
+// Exactness.  A residue v of q < 2^55 is taken centred, v' = v or v - q in (-q/2, q/2), and
+// written in seven balanced base-256 digits, v' = sum_{i<7} s_i 256^i with s_i in [-128, 127]:
+// s_i = byte i of w = v' + C minus 128, C = 0x0080808080808080 (128 in bytes 0-6); w lies in
+// (C - 2^54, C + 2^54), so byte 7 of w is 0 and no carry is lost.  A digit is exact in fp16
+// and the product of two digits is at most 2^14 in magnitude, so the f32 accumulator of the
+// MMA holds a sum of up to 256 such products exactly (|sum| <= 2^22).  The diagonals' digits
+// sit in the M dimension (row 8 x + a for digit a of accumulator x; row 8 x + 7 zero) and
+// the rotations' digits in the N dimension (column 8 (2 b + c) + a' for digit a' of component
+// c of query b; column a' = 7 zero), so the accumulator holds, for every digit pair (a, a'),
+// the exact partial sum D_aa' = sum_j s_a(d[x][j]) s_a'(R_c[j][b]), and the product sum
+// sum_j d'[x][j] R'_c[j][b] = sum_aa' D_aa' 256^(a + a') (|.| < 2^116, congruent mod q to the
+// product sum of the residues) is rebuilt in 128-bit integers and reduced mod q once.
 //
-// One CTA per SM, persistent over work items (element, accumulator tile of 16, run of up
-// to 256 baby steps).  Per item the CTA writes the digits of both components of its
-// diagonals (c0 read element-major, c1 regenerated from its seed) into shared memory once
-// and then, for each pass of 16 query ciphertexts, streams the digits of the rotations
-// through a ring of stages (cp.async prefetch of the raw words, digit conversion, one
-// elected thread issuing two M 128 x N 256 x K 16 MMAs per stage into the two accumulators
-// d0 x [R0 | R1] and d1 x [R0 | R1] of 256 TMEM columns each).  After the pass the eight
-// warps read the accumulators back (tcgen05.ld), rebuild the three outputs
-// (d0 R0, d0 R1 + d1 R0, d1 R1) exactly, reduce them and add them to acc.
+// One CTA per SM, persistent over work items (element, tile of 16 accumulators, run of up
+// to 256 baby steps), its warps specialised and handing work on through mbarriers:
+//   warp 0       allocates the tensor memory; one thread issues the MMAs
+//   warp 1       one thread streams the rotations' raw words, one chunk (8 query
+//                ciphertexts x 16 baby steps x 2 components, contiguous) per bulk copy
+//                (cp.async.bulk with transaction-count completion) into a ring of stages
+//   warps 2-9    producers: per item the digits of both components of every diagonal (c0
+//                read element-major, c1 regenerated from its seed) into shared memory, then
+//                the digits of the rotations into a ring of operand stages, each warp
+//                converting whole chunks in turn
+//   warps 10-17  epilogue: per pass (8 query ciphertexts) the accumulators back from tensor
+//                memory (tcgen05.ld), the exact outputs rebuilt, reduced and stored in acc;
+//                warps 10-13 take d0 R0 and d1 R1, warps 14-17 d0 R1 + d1 R0
+// Per chunk two M 128 x N 128 x K 16 MMAs accumulate d0 x [R0 | R1] and d1 x [R0 | R1] into
+// one of two tensor-memory buffers (2 x 2 x 128 columns), so the epilogue of one pass
+// overlaps the products of the next.
 //
-// Every wait on an MMA completion is bounded by the global timer: a wait that runs out sets
-// COPSE_DEV_MAC_WAIT in the context's device status word, and the CTA stops taking work,
-// waits (bounded) for its issued MMAs, releases its tensor memory and exits.
+// Every wait is bounded by the global timer: a wait that runs out sets COPSE_DEV_MAC_WAIT in
+// the context's device status word and every role of the CTA stops; the copies and MMAs in
+// flight are waited for (bounded), the tensor memory released and the CTA exits.
 #include <algorithm>
 #include <atomic>
 
@@ -42,23 +49,31 @@
 
 namespace {
 
-constexpr int TC_THREADS = 256;  // 8 warps
-constexpr int TC_MX = 16;        // accumulators per tile: 16 x 8 digit rows = M 128
-constexpr int TC_QP = 16;        // query ciphertexts per pass: 16 x 2 components x 8 digits = N 256
-constexpr int TC_KR = 256;       // baby steps per run: exact f32 partial sums
-constexpr int TC_KS = 16;        // baby steps per MMA (K of kind::f16)
-constexpr int TC_NST = 4;        // digit stages of the rotations
-constexpr int TC_NRAW = 4;       // raw stages (prefetch distance + 1)
+constexpr int TC_MX = 16;         // accumulators per tile: 16 x 8 digit rows = M 128
+constexpr int TC_QP = 8;          // query ciphertexts per pass: 8 x 2 components x 8 digits = N 128
+constexpr int TC_KR = 256;        // baby steps per run: exact f32 partial sums
+constexpr int TC_KS = 16;         // baby steps per MMA (K of kind::f16) and per chunk
+constexpr int TC_NB = 8;          // operand stages of the rotations' digits
+constexpr int TC_NR = 16;         // raw stages of the rotations
+constexpr int TC_PROD_WARPS = 8, TC_EPI_WARPS = 8;
+constexpr int TC_THREADS = 32 * (2 + TC_PROD_WARPS + TC_EPI_WARPS);  // 576
 constexpr int TC_TMEM_COLS = 512;
 constexpr unsigned long long TC_WAIT_NS = 2000000000ull;  // 2 s per wait
 
 constexpr uint32_t A_SET = TC_MX * 8 * TC_KR * 2;        // digits of one diagonal component: 64 KB
-constexpr uint32_t B_STAGE = TC_QP * 2 * 8 * TC_KS * 2;  // digits of one chunk of rotations: 8 KB
-constexpr uint32_t RAW_STAGE = TC_QP * TC_KS * 2 * 8;    // raw words of one chunk: 4 KB
-constexpr uint32_t OFF_A0 = 0, OFF_A1 = A_SET, OFF_B = 2 * A_SET, OFF_RAW = OFF_B + TC_NST * B_STAGE,
-                   OFF_TAB = OFF_RAW + TC_NRAW * RAW_STAGE, OFF_BAR = OFF_TAB + TC_MX * TC_KR * 4,
-                   OFF_MISC = OFF_BAR + (TC_NST + 2) * 8, SMEM_TC = OFF_MISC + 16;
-static_assert(RAW_STAGE == TC_THREADS * 16, "one 16-byte raw copy per thread and chunk");
+constexpr uint32_t B_STAGE = TC_QP * 2 * 8 * TC_KS * 2;  // digits of one chunk of rotations: 4 KB
+constexpr uint32_t RAW_STAGE = TC_QP * TC_KS * 2 * 8;    // raw words of one chunk: 2 KB
+// barriers: raw full / empty, operand full / empty, diagonals full / empty, accumulators full /
+// empty (two buffers), drain
+constexpr int BAR_RAW_FULL = 0, BAR_RAW_EMPTY = TC_NR, BAR_B_FULL = 2 * TC_NR, BAR_B_EMPTY = 2 * TC_NR + TC_NB,
+              BAR_A_FULL = 2 * TC_NR + 2 * TC_NB, BAR_A_EMPTY = BAR_A_FULL + 1, BAR_T_FULL = BAR_A_FULL + 2,
+              BAR_T_EMPTY = BAR_T_FULL + 2, BAR_DRAIN = BAR_T_EMPTY + 2, N_BAR = BAR_DRAIN + 1;
+constexpr uint32_t C0_STAGE = TC_MX * TC_KR * 8;        // c0 words of one run: 32 KB
+constexpr uint32_t OFF_A0 = 0, OFF_A1 = A_SET, OFF_B = 2 * A_SET, OFF_RAW = OFF_B + TC_NB * B_STAGE,
+                   OFF_C0 = OFF_RAW + TC_NR * RAW_STAGE, OFF_BAR = OFF_C0 + C0_STAGE, OFF_MISC = OFF_BAR + N_BAR * 8,
+                   SMEM_TC = OFF_MISC + 16;
+static_assert(TC_QP * TC_KS == 4 * 32, "four (query, baby step) pairs per lane of the warp that converts a chunk");
+static_assert(TC_NB == TC_PROD_WARPS && TC_NR % TC_PROD_WARPS == 0, "a producer warp keeps to its own stages");
 static_assert(SMEM_TC <= 227 * 1024, "shared memory");
 
 // kind::f16 instruction descriptor: f32 accumulator (bits 4-5 = 1), f16 A and B (formats 0),
@@ -66,7 +81,7 @@ static_assert(SMEM_TC <= 227 * 1024, "shared memory");
 constexpr uint32_t idesc_f16(int M, int N) {
     return (1u << 4) | (1u << 15) | (1u << 16) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
-constexpr uint32_t IDESC = idesc_f16(128, TC_QP * 2 * 8);
+constexpr uint32_t IDESC = idesc_f16(128, TC_QP * 2 * 8);  // M 128, N 128
 
 __device__ __forceinline__ uint32_t sh_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -94,18 +109,29 @@ __device__ __forceinline__ void tc_commit(uint64_t *bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(sh_addr(bar))
                  : "memory");
 }
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr)
-        : "memory");
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr)
+                 : "memory");
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-__device__ __forceinline__ void bar_init(uint64_t *bar) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sh_addr(bar)) : "memory");
+__device__ __forceinline__ void bar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(sh_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void bar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(sh_addr(bar)) : "memory");
+}
+__device__ __forceinline__ void bar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(sh_addr(bar)), "r"(bytes) : "memory");
+}
+// bytes (a multiple of 16, both addresses 16-byte aligned) global -> shared, completing on bar
+__device__ __forceinline__ void bulk_copy(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     sh_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(sh_addr(bar))
+                 : "memory");
 }
 __device__ __forceinline__ bool bar_test(uint64_t *bar, uint32_t parity) {
     uint32_t done;
@@ -116,12 +142,24 @@ __device__ __forceinline__ bool bar_test(uint64_t *bar, uint32_t parity) {
         : "memory");
     return done != 0;
 }
+// the same, the thread suspended until the phase completes or about TC_SUSPEND_NS pass (a
+// waiting warp then takes no issue slots)
+constexpr uint32_t TC_SUSPEND_NS = 20000;
+__device__ __forceinline__ bool bar_test_suspend(uint64_t *bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(sh_addr(bar)), "r"(parity), "r"(TC_SUSPEND_NS)
+        : "memory");
+    return done != 0;
+}
 // wait for the completion of the phase with this parity, at most TC_WAIT_NS; false (and the
-// CTA's failure flag and the device status set) when the wait ran out or another thread's did
+// CTA's failure flag and the device status set) when the wait ran out or another one did
 __device__ bool bar_wait(uint64_t *bar, uint32_t parity, volatile int *fail, int *status) {
     unsigned long long t0 = 0;
     for (int it = 0;; it++) {
-        if (bar_test(bar, parity)) return true;
+        if (bar_test_suspend(bar, parity)) return true;
         if (*fail) return false;
         if (it == 0) {
             t0 = global_ns();
@@ -132,17 +170,22 @@ __device__ bool bar_wait(uint64_t *bar, uint32_t parity, volatile int *fail, int
         }
     }
 }
+// the same for a whole warp: every lane waits (no divergence), the warp agrees on the outcome
+__device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, volatile int *fail, int *status) {
+    const bool ok = bar_wait(bar, parity, fail, status);
+    return __all_sync(0xffffffffu, ok) != 0;
+}
 
 __device__ __forceinline__ uint32_t hsub2(uint32_t a, uint32_t b) {
     uint32_t d;
     asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
     return d;
 }
-// The eight base-256 digits of v < 2^55 as eight fp16 (digit i in half i): byte i of
-// v + 0x0080808080808080 with 0x64 above it is the fp16 of 1024 + byte, less 1152 = 1024 + 128
-// for bytes 0-6 and less 1024 for byte 7 (0 or 1).
-__device__ __forceinline__ uint4 digits8(u64 v) {
-    const u64 w = v + 0x0080808080808080ull;
+// The seven balanced base-256 digits of the centred residue of v (v < q) and a zero eighth, as
+// eight fp16 (digit i in half i): byte i of v' + 0x0080808080808080 with 0x64 above it is the
+// fp16 of 1024 + byte, less 1152 = 1024 + 128 for bytes 0-6 and less 1024 for byte 7 (zero).
+__device__ __forceinline__ uint4 digits8(u64 v, u64 q) {
+    const u64 w = (v > (q >> 1) ? v - q : v) + 0x0080808080808080ull;  // v' = v - q above q / 2
     const uint32_t lo = (uint32_t)w, hi = (uint32_t)(w >> 32);
     constexpr uint32_t C = 0x64806480u, C7 = 0x64006480u;  // (1152, 1152), (1152 low, 1024 high)
     uint4 r;
@@ -152,40 +195,113 @@ __device__ __forceinline__ uint4 digits8(u64 v) {
     r.w = hsub2(__byte_perm(hi, 0x64u, 0x4342), C7);
     return r;
 }
-// an integer-valued f32 in [-2^22, 2^22] (its bits) as an int: x + 1.5 2^23 lies in
-// [2^23, 2^24], where the f32 spacing is 1, so the sum is exact and its bits are linear in x
-__device__ __forceinline__ int f32_int(uint32_t bits) {
-    return __float_as_int(__uint_as_float(bits) + 12582912.0f) - 0x4B400000;
-}
+// An integer-valued f32 x in [-2^22, 2^22] plus 1.5 2^23 lies in [2^23, 2^24], where the f32
+// spacing is 1: the sum is exact and its bits are the integer x + 0x4B400000.
+constexpr float MAGIC = 12582912.0f;
+constexpr uint32_t MAGIC_BITS = 0x4B400000u;
+__device__ __forceinline__ uint32_t f32_biased(uint32_t bits) { return __float_as_uint(__uint_as_float(bits) + MAGIC); }
 
 using u128 = unsigned __int128;
 __device__ __forceinline__ u128 shfl_xor_u128(u128 v, int m) {
     const u64 lo = __shfl_xor_sync(0xffffffffu, (u64)v, m), hi = __shfl_xor_sync(0xffffffffu, (u64)(v >> 64), m);
     return ((u128)hi << 64) | lo;
 }
+// sum_{b<7} u_b 256^b for u_b < 2^32 (below 2^81)
+__device__ __forceinline__ u128 row_value(const uint32_t (&u)[8]) {
+    const u64 L = (u64)u[0] + ((u64)u[1] << 8) + ((u64)u[2] << 16) + ((u64)u[3] << 24);
+    const u64 H = (u64)u[4] + ((u64)u[5] << 8) + ((u64)u[6] << 16);
+    return (u128)L + ((u128)H << 32);
+}
+// The biases: an output rebuilt from biased digit sums over a < 8, b < 7,
+// sum_{a,b} (D_ab + m MAGIC_BITS) 256^(a+b) with m conversions per (a, b), exceeds the product
+// sum by m MAGIC_BITS S8 S7, S_n = sum_{i<n} 256^i (all mod 2^128).
+__host__ __device__ constexpr u128 bias_rows() {
+    u128 S8 = 0, S7 = 0;
+    for (int i = 0; i < 8; i++) S8 += (u128)1 << (8 * i);
+    for (int i = 0; i < 7; i++) S7 += (u128)1 << (8 * i);
+    return (u128)MAGIC_BITS * S8 * S7;
+}
+
+// sum_a V_a 256^a over the 8 lanes of a digit group (lanes differing in bits 0-2; V_a the row
+// value of digit a = lane % 8), scattered: lane a of the group ends with the total for v[a].
+// The round on bit s pairs a lane holding the lower digits with one holding digits 2^s higher,
+// so their sum is lo + hi 256^(2^s); after the three rounds no digit offset is left.
+__device__ __forceinline__ u128 reduce_scatter8(u128 (&v)[8], int lane) {
+    const bool b2 = (lane >> 2) & 1, b1 = (lane >> 1) & 1, b0 = lane & 1;
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        const u128 send = b2 ? v[i] : v[4 + i], keep = b2 ? v[4 + i] : v[i];
+        const u128 got = shfl_xor_u128(send, 4);
+        v[i] = b2 ? got + (keep << 32) : keep + (got << 32);
+    }
+#pragma unroll
+    for (int i = 0; i < 2; i++) {
+        const u128 send = b1 ? v[i] : v[2 + i], keep = b1 ? v[2 + i] : v[i];
+        const u128 got = shfl_xor_u128(send, 2);
+        v[i] = b1 ? got + (keep << 16) : keep + (got << 16);
+    }
+    const u128 send = b0 ? v[0] : v[1], keep = b0 ? v[1] : v[0];
+    const u128 got = shfl_xor_u128(send, 1);
+    return b0 ? got + (keep << 8) : keep + (got << 8);
+}
+// (t mod 2^128, read as a signed value) mod q
+__device__ __forceinline__ u64 reduce_signed128(u128 t, const PrimeDev &pd) {
+    if ((u64)(t >> 64) >> 63) {
+        const u128 n = (u128)0 - t;
+        const u64 r = reduce128(Acc128{(u64)n, (u64)(n >> 64)}, pd);
+        return r ? pd.q - r : 0;
+    }
+    return reduce128(Acc128{(u64)t, (u64)(t >> 64)}, pd);
+}
 
 struct TcArgs {
-    const u64 *mac;       // [n_el][nm][nb] diagonals' c0
+    const u64 *mac;       // [n_el][nm][nb16] diagonals' c0 (rows of nb16 = nb rounded up to 16 words)
     const uint32_t *idx;  // [nm][nb] model ciphertext index (mask stream), ~0u = none
-    const u64 *R;         // [n_el][nq][nb][2] rotations
-    u64 *acc;             // [nq][nm][3][n_el], added to
+    const u64 *R;         // [n_el][nks][nq][16][2] rotations (nks = baby steps / 16, rounded up)
+    u64 *acc;             // [nq][nm][3][n_el], written by the first run, added to by later ones
     size_t a_ct;          // words per query ciphertext in acc
-    int nm, nb, nq, ell, logN, n_mt, n_kr;
+    int nm, nb, nb16, nq, ell, logN, n_mt, n_kr, nks;
     u64 seed;
     const PrimeDev *pr;
     int *status;
 };
 
+// A work item is (tile of accumulators, element); its baby steps run in runs of up to 256
+// (each run its own accumulation: the f32 sums stay exact), taken in order by the same CTA.
+struct Item {
+    size_t e;
+    int x0, nx;
+};
+__device__ __forceinline__ Item item_at(const TcArgs &P, size_t it, size_t n_el) {
+    Item I;
+    const int mt = (int)(it / n_el);
+    I.e = it - (size_t)mt * n_el;
+    I.x0 = mt * TC_MX;
+    I.nx = min(TC_MX, P.nm - I.x0);
+    return I;
+}
+struct Run {
+    int j0, nj, nk;  // first baby step, baby steps, chunks of 16
+};
+__device__ __forceinline__ Run run_at(const TcArgs &P, int kr) {
+    Run R;
+    R.j0 = kr * TC_KR;
+    R.nj = min(TC_KR, P.nb - R.j0);
+    R.nk = (R.nj + TC_KS - 1) / TC_KS;
+    return R;
+}
+
 __global__ void __launch_bounds__(TC_THREADS, 1) k_enc_mac_tc(const TcArgs P) {
     extern __shared__ __align__(1024) uint8_t sm[];
-    uint8_t *A0 = sm + OFF_A0, *A1 = sm + OFF_A1, *Bst = sm + OFF_B, *Raw = sm + OFF_RAW;
-    uint32_t *tab = (uint32_t *)(sm + OFF_TAB);
-    uint64_t *bar = (uint64_t *)(sm + OFF_BAR);  // [0, NST) stages, NST: pass, NST + 1: final drain
+    uint8_t *A0 = sm + OFF_A0, *A1 = sm + OFF_A1, *Bst = sm + OFF_B, *Raw = sm + OFF_RAW, *C0s = sm + OFF_C0;
+    uint64_t *bar = (uint64_t *)(sm + OFF_BAR);
     uint32_t *tslot = (uint32_t *)(sm + OFF_MISC);
     volatile int *fail = (volatile int *)(sm + OFF_MISC + 4);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const size_t n_el = (size_t)P.ell << P.logN;
     const uint32_t nmask = (1u << P.logN) - 1;
+    const int nqp = (P.nq + TC_QP - 1) / TC_QP;
+    const size_t n_items = (size_t)P.n_mt * n_el;
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sh_addr(tslot)),
@@ -193,8 +309,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_enc_mac_tc(const TcArgs P) {
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    if (tid == 0) {
-        for (int i = 0; i < TC_NST + 2; i++) bar_init(&bar[i]);
+    if (tid == 32) {
+        for (int i = 0; i < TC_NR; i++) {
+            bar_init(&bar[BAR_RAW_FULL + i], 1);
+            bar_init(&bar[BAR_RAW_EMPTY + i], 1);
+        }
+        for (int i = 0; i < TC_NB; i++) {
+            bar_init(&bar[BAR_B_FULL + i], 1);
+            bar_init(&bar[BAR_B_EMPTY + i], 1);
+        }
+        bar_init(&bar[BAR_A_FULL], TC_PROD_WARPS);
+        bar_init(&bar[BAR_A_EMPTY], 1);
+        for (int i = 0; i < 2; i++) {
+            bar_init(&bar[BAR_T_FULL + i], 1);
+            bar_init(&bar[BAR_T_EMPTY + i], TC_EPI_WARPS);
+        }
+        bar_init(&bar[BAR_DRAIN], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         *fail = 0;
     }
@@ -203,157 +333,230 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_enc_mac_tc(const TcArgs P) {
     tc_fence_after();
     const uint32_t tmem = *tslot;
 
-    const int nqp = (P.nq + TC_QP - 1) / TC_QP;
-    const size_t n_items = (size_t)P.n_mt * P.n_kr * n_el;
-    uint32_t gchunk = 0, npass = 0;  // chunks and passes of this CTA so far (barrier phases)
-    int cur_mk = -1;                 // (tile, run) whose index table is in shared memory
-    bool issued = false;             // MMAs issued (the final drain waits for them)
-    for (size_t it = blockIdx.x; it < n_items; it += gridDim.x) {
-        const int mk = (int)(it / n_el);
-        const size_t e = it - (size_t)mk * n_el;
-        const int mt = mk / P.n_kr, kr = mk - mt * P.n_kr;
-        const int x0 = mt * TC_MX, nx = min(TC_MX, P.nm - x0);
-        const int j0 = kr * TC_KR, nj = min(TC_KR, P.nb - j0), nk = (nj + TC_KS - 1) / TC_KS, nj16 = nk * TC_KS;
-        const uint32_t a_mn = (uint32_t)nj16 * 16;  // bytes between accumulators' core-matrix rows
-        const int r = (int)(e >> P.logN);
-        const PrimeDev pd = P.pr[r];
-        const uint32_t pos = (uint32_t)(e & nmask);
-        const int nchunks = nqp * nk;
-
-        // raw rotations of chunk c (pass c / nk, baby steps of MMA c % nk) of this item: thread
-        // t copies (R0, R1) of query t / 16 and baby step t % 16
-        auto issue = [&](int c) {
-            uint8_t *dst = Raw + ((gchunk + (uint32_t)c) % TC_NRAW) * RAW_STAGE + tid * 16;
-            if (c < nchunks) {
-                const int qp = c / nk, ks = c - qp * nk;
-                const int q = qp * TC_QP + (tid >> 4), j = ks * TC_KS + (tid & 15);
-                if (q < P.nq && j < nj)
-                    cp_async16(dst, P.R + (((e * P.nq + q) * P.nb + j0 + j) << 1));
-                else
-                    *(uint4 *)dst = make_uint4(0, 0, 0, 0);
+    if (warp == 0) {
+        // ---------------------------------------------------------------- MMA issue
+        if (lane == 0) {
+            uint32_t nb_c = 0, np_c = 0, na = 0;  // operand stages, passes, runs consumed
+            bool ok = true, issued = false;
+            for (size_t it = blockIdx.x; it < n_items && ok; it += gridDim.x)
+                for (int kr = 0; kr < P.n_kr && ok; kr++, na++) {
+                    const Run R = run_at(P, kr);
+                    const uint32_t a_mn = (uint32_t)R.nk * TC_KS * 16;  // bytes between accumulators' core-matrix rows
+                    if (!(ok = bar_wait(&bar[BAR_A_FULL], na & 1, fail, P.status))) break;
+                    for (int p = 0; p < nqp && ok; p++, np_c++) {
+                        const uint32_t buf = np_c & 1;
+                        if (np_c >= 2 &&
+                            !(ok = bar_wait(&bar[BAR_T_EMPTY + buf], ((np_c >> 1) - 1) & 1, fail, P.status)))
+                            break;
+                        tc_fence_after();
+                        const uint32_t d0 = tmem + buf * 256, d1 = d0 + 128;
+                        for (int ks = 0; ks < R.nk; ks++, nb_c++) {
+                            const int st = (int)(nb_c % TC_NB);
+                            if (!(ok = bar_wait(&bar[BAR_B_FULL + st], (nb_c / TC_NB) & 1, fail, P.status))) break;
+                            tc_fence_after();
+                            const uint64_t bd = smem_desc(sh_addr(Bst + st * B_STAGE), 128, 256);
+                            tc_mma(d0, smem_desc(sh_addr(A0) + (uint32_t)ks * 256, 128, a_mn), bd, ks > 0);
+                            tc_mma(d1, smem_desc(sh_addr(A1) + (uint32_t)ks * 256, 128, a_mn), bd, ks > 0);
+                            tc_commit(&bar[BAR_B_EMPTY + st]);
+                            issued = true;
+                        }
+                        if (ok) tc_commit(&bar[BAR_T_FULL + buf]);
+                    }
+                    if (ok) tc_commit(&bar[BAR_A_EMPTY]);
+                }
+            if (issued && *fail) {  // wait (bounded) for the MMAs in flight before the memory goes
+                tc_commit(&bar[BAR_DRAIN]);
+                const unsigned long long t0 = global_ns();
+                while (!bar_test(&bar[BAR_DRAIN], 0) && global_ns() - t0 < TC_WAIT_NS) {
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ---------------------------------------------------------------- rotation loader
+        if (lane == 0) {
+            uint32_t nr_c = 0;
+            bool ok = true;
+            for (size_t it = blockIdx.x; it < n_items && ok; it += gridDim.x) {
+                const Item I = item_at(P, it, n_el);
+                for (int kr = 0; kr < P.n_kr && ok; kr++) {
+                    const Run R = run_at(P, kr);
+                    for (int p = 0; p < nqp && ok; p++)
+                        for (int ks = 0; ks < R.nk; ks++, nr_c++) {
+                            const int st = (int)(nr_c % TC_NR);
+                            if (nr_c >= TC_NR &&
+                                !(ok = bar_wait(&bar[BAR_RAW_EMPTY + st], ((nr_c / TC_NR) - 1) & 1, fail, P.status)))
+                                break;
+                            const int nqq = min(TC_QP, P.nq - p * TC_QP);
+                            const uint32_t bytes = (uint32_t)nqq * TC_KS * 2 * 8;
+                            bar_expect_tx(&bar[BAR_RAW_FULL + st], bytes);
+                            bulk_copy(Raw + st * RAW_STAGE,
+                                      P.R + (((I.e * P.nks + R.j0 / TC_KS + ks) * P.nq + (size_t)p * TC_QP) * TC_KS * 2),
+                                      bytes, &bar[BAR_RAW_FULL + st]);
+                        }
+                }
+            }
+            // no copy may land after the CTA is gone: wait (bounded) for the last stages issued
+            if (*fail)
+                for (uint32_t k = nr_c > TC_NR ? nr_c - TC_NR : 0; k < nr_c; k++) {
+                    const unsigned long long t0 = global_ns();
+                    while (!bar_test(&bar[BAR_RAW_FULL + k % TC_NR], (k / TC_NR) & 1) && global_ns() - t0 < TC_WAIT_NS) {
+                    }
+                }
+        }
+    } else if (warp < 2 + TC_PROD_WARPS) {
+        // ---------------------------------------------------------------- producers
+        // Thread pt builds the digits of the (accumulator, baby step) pairs 2 (pt + 256 k) and the
+        // next one of each run, from the c0 words it copied itself (cp.async, issued while the
+        // previous run's products run).  Producer warp pw converts the rotations of the chunks
+        // with index pw modulo 8 (so it keeps to operand stage pw), four (query, baby step) pairs
+        // per lane.
+        const int pt = tid - 64, pw = warp - 2;
+        uint32_t nb_c = 0, nr_c = 0, na = 0;
+        bool ok = true;
+        // c0 of the run (it, kr) into the staging area: row x of the tile at x * nj16 words
+        auto fetch_c0 = [&](size_t it, int kr) {
+            const Item I = item_at(P, it, n_el);
+            const Run R = run_at(P, kr);
+            const int nj16 = R.nk * TC_KS;
+            for (int i = 2 * pt; i < TC_MX * nj16; i += 2 * TC_PROD_WARPS * 32) {
+                const int x = i / nj16, j = i - x * nj16;
+                if (x < I.nx)
+                    cp_async16(C0s + (size_t)i * 8, P.mac + (I.e * P.nm + I.x0 + x) * P.nb16 + R.j0 + j);
             }
             cp_async_commit();
         };
-        for (int c = 0; c < TC_NRAW - 1; c++) issue(c);
-
-        if (mk != cur_mk) {
-            __syncthreads();  // the previous table's readers are done
-            for (int i = tid; i < TC_MX * TC_KR; i += TC_THREADS) {
-                const int x = i / TC_KR, j = i - x * TC_KR;
-                tab[i] = (x < nx && j < nj) ? P.idx[(size_t)(x0 + x) * P.nb + j0 + j] : ~0u;
-            }
-            cur_mk = mk;
-            __syncthreads();
-        }
-        // digits of both components of every (accumulator, baby step) of the item: the 16 bytes
-        // of accumulator x at baby step j are row j % 8 of core matrix (x, j / 8)
-        for (int i = tid; i < TC_MX * nj16; i += TC_THREADS) {
-            const int x = i / nj16, j = i - x * nj16;
-            const uint32_t id = tab[x * TC_KR + j];
-            u64 d0 = 0, d1 = 0;
-            if (id != ~0u) {
-                d0 = P.mac[(e * P.nm + x0 + x) * P.nb + j0 + j];
-                d1 = seeded_mask(P.seed, MODEL_STREAM + 2ull * id, r, pos, P.logN, pd);
-            }
-            const uint32_t off = (uint32_t)x * a_mn + (uint32_t)(j >> 3) * 128 + (uint32_t)(j & 7) * 16;
-            *(uint4 *)(A0 + off) = digits8(d0);
-            *(uint4 *)(A1 + off) = digits8(d1);
-        }
-        fence_async_smem();
-        __syncthreads();
-
-        bool ok = true;
-        for (int qp = 0; qp < nqp && ok; qp++) {
-            for (int ks = 0; ks < nk; ks++) {
-                const int c = qp * nk + ks;
-                const uint32_t g = gchunk + (uint32_t)c;
-                const int st = (int)(g % TC_NST);
-                // stage st is free once the MMAs of chunk g - NST have completed
-                if (g >= TC_NST) bar_wait(&bar[st], ((g / TC_NST) - 1) & 1, fail, P.status);
-                cp_async_wait<TC_NRAW - 2>();
-                __syncthreads();
-                if (*fail) {
-                    ok = false;
-                    break;
-                }
-                {
-                    const ulonglong2 v = *(const ulonglong2 *)(Raw + (g % TC_NRAW) * RAW_STAGE + tid * 16);
-                    const int q = tid >> 4, j = tid & 15;
-                    uint8_t *B = Bst + st * B_STAGE + (j >> 3) * 128 + (j & 7) * 16;
-                    *(uint4 *)(B + (2 * q) * 256) = digits8(v.x);
-                    *(uint4 *)(B + (2 * q + 1) * 256) = digits8(v.y);
+        if ((size_t)blockIdx.x < n_items) fetch_c0(blockIdx.x, 0);
+        for (size_t it = blockIdx.x; it < n_items && ok; it += gridDim.x) {
+            const Item I = item_at(P, it, n_el);
+            const int r = (int)(I.e >> P.logN);
+            const PrimeDev pd = P.pr[r];
+            const uint32_t pos = (uint32_t)(I.e & nmask);
+            for (int kr = 0; kr < P.n_kr && ok; kr++, na++) {
+                const Run R = run_at(P, kr);
+                const int nj16 = R.nk * TC_KS;
+                const uint32_t a_mn = (uint32_t)nj16 * 16;
+                // the diagonals' digits, once the previous run's products are done with them: the 16
+                // bytes of accumulator x at baby step j are row j % 8 of core matrix (x, j / 8)
+                if (na > 0 && !(ok = warp_wait(&bar[BAR_A_EMPTY], (na - 1) & 1, fail, P.status))) break;
+                cp_async_wait<0>();
+                for (int i = 2 * pt; i < TC_MX * nj16; i += 2 * TC_PROD_WARPS * 32) {
+                    const int x = i / nj16, j = i - x * nj16;
+#pragma unroll
+                    for (int h = 0; h < 2; h++) {
+                        const uint32_t id =
+                            (x < I.nx && j + h < R.nj) ? __ldg(P.idx + (size_t)(I.x0 + x) * P.nb + R.j0 + j + h) : ~0u;
+                        u64 d0 = 0, d1 = 0;
+                        if (id != ~0u) {
+                            d0 = *(const u64 *)(C0s + (size_t)(i + h) * 8);
+                            d1 = seeded_mask(P.seed, MODEL_STREAM + 2ull * id, r, pos, P.logN, pd);
+                        }
+                        const uint32_t off =
+                            (uint32_t)x * a_mn + (uint32_t)((j + h) >> 3) * 128 + (uint32_t)((j + h) & 7) * 16;
+                        *(uint4 *)(A0 + off) = digits8(d0, pd.q);
+                        *(uint4 *)(A1 + off) = digits8(d1, pd.q);
+                    }
                 }
                 fence_async_smem();
-                __syncthreads();
-                issue(c + TC_NRAW - 1);  // into the raw stage read by the previous chunk
-                if (tid == 0) {
-                    tc_fence_after();
-                    const uint64_t bd = smem_desc(sh_addr(Bst + st * B_STAGE), 128, 256);
-                    const uint64_t a0 = smem_desc(sh_addr(A0) + (uint32_t)ks * 256, 128, a_mn);
-                    const uint64_t a1 = smem_desc(sh_addr(A1) + (uint32_t)ks * 256, 128, a_mn);
-                    tc_mma(tmem, a0, bd, ks > 0);
-                    tc_mma(tmem + TC_TMEM_COLS / 2, a1, bd, ks > 0);
-                    tc_commit(&bar[st]);
-                    if (ks == nk - 1) tc_commit(&bar[TC_NST]);
-                    issued = true;
-                }
-            }
-            if (!ok) break;
-            bar_wait(&bar[TC_NST], npass & 1, fail, P.status);
-            npass++;
-            __syncthreads();
-            if (*fail) {
-                ok = false;
-                break;
-            }
-            tc_fence_after();
-            // Accumulators back: TMEM lane m = 32 (warp % 4) + lane is digit row a = m % 8 of
-            // accumulator x = m / 8; warps 0-3 take queries 0-7 of the pass, warps 4-7 queries 8-15.
-            {
-                const int m = 32 * (warp & 3) + lane, x = m >> 3, a = m & 7;
-                const uint32_t trow = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
-                for (int qq = 0; qq < 8; qq++) {
-                    const int q = (warp >> 2) * 8 + qq, gq = qp * TC_QP + q;
-                    uint32_t v0[16], v1[16];
-                    tmem_ld16(trow + (uint32_t)(q * 16), v0);                     // d0 x (R0 | R1)
-                    tmem_ld16(trow + (uint32_t)(TC_TMEM_COLS / 2 + q * 16), v1);  // d1 x (R0 | R1)
-                    tmem_wait_ld();
-                    u128 s0 = 0, s1 = 0, s2 = 0;
+                __syncwarp();
+                if (lane == 0) bar_arrive(&bar[BAR_A_FULL]);
+                // the next run's c0, while this run's products run
+                if (kr + 1 < P.n_kr)
+                    fetch_c0(it, kr + 1);
+                else if (it + gridDim.x < n_items)
+                    fetch_c0(it + gridDim.x, 0);
+                // the rotations' digits, chunk by chunk
+                for (int p = 0; p < nqp && ok; p++)
+                    for (int ks = 0; ks < R.nk; ks++, nb_c++, nr_c++) {
+                        if ((int)(nb_c % TC_PROD_WARPS) != pw) continue;
+                        const int st = (int)(nb_c % TC_NB), rs = (int)(nr_c % TC_NR);
+                        if (nb_c >= TC_NB &&
+                            !(ok = warp_wait(&bar[BAR_B_EMPTY + st], ((nb_c / TC_NB) - 1) & 1, fail, P.status)))
+                            break;
+                        if (!(ok = warp_wait(&bar[BAR_RAW_FULL + rs], (nr_c / TC_NR) & 1, fail, P.status))) break;
+                        const uint8_t *raw = Raw + rs * RAW_STAGE;
+                        uint8_t *Bs = Bst + st * B_STAGE;
 #pragma unroll
-                    for (int b = 0; b < 8; b++) {
-                        s0 += (u128)(__int128)(long long)f32_int(v0[b]) << (8 * b);
-                        s1 += (u128)(__int128)(long long)(f32_int(v0[8 + b]) + f32_int(v1[b])) << (8 * b);
-                        s2 += (u128)(__int128)(long long)f32_int(v1[8 + b]) << (8 * b);
+                        for (int u = 0; u < 4; u++) {
+                            const int pr = lane + 32 * u, q = pr >> 4, j = pr & 15;
+                            ulonglong2 v = make_ulonglong2(0, 0);
+                            if (p * TC_QP + q < P.nq && ks * TC_KS + j < R.nj) v = *(const ulonglong2 *)(raw + pr * 16);
+                            uint8_t *B = Bs + (j >> 3) * 128 + (j & 7) * 16;
+                            *(uint4 *)(B + (2 * q) * 256) = digits8(v.x, pd.q);
+                            *(uint4 *)(B + (2 * q + 1) * 256) = digits8(v.y, pd.q);
+                        }
+                        fence_async_smem();
+                        __syncwarp();
+                        if (lane == 0) {
+                            bar_arrive(&bar[BAR_B_FULL + st]);
+                            bar_arrive(&bar[BAR_RAW_EMPTY + rs]);
+                        }
                     }
-                    s0 <<= 8 * a;
-                    s1 <<= 8 * a;
-                    s2 <<= 8 * a;
-#pragma unroll
-                    for (int o = 1; o < 8; o <<= 1) {
-                        s0 += shfl_xor_u128(s0, o);
-                        s1 += shfl_xor_u128(s1, o);
-                        s2 += shfl_xor_u128(s2, o);
-                    }
-                    if (a < 3 && x < nx && gq < P.nq) {
-                        const u128 t = a == 0 ? s0 : (a == 1 ? s1 : s2);
-                        const u64 v = reduce128(Acc128{(u64)t, (u64)(t >> 64)}, pd);
-                        u64 *o = P.acc + (size_t)gq * P.a_ct + ((size_t)(x0 + x) * 3 + a) * n_el + e;
-                        *o = add_mod(*o, v, pd.q);
-                    }
-                }
             }
-            tc_fence_before();
-            __syncthreads();  // the accumulators are free for the next pass
         }
-        gchunk += (uint32_t)nchunks;
-        if (!ok) break;
-    }
-    cp_async_wait<0>();
-    // release: every MMA this CTA issued has completed (bounded wait after a failure)
-    if (tid == 0 && issued && *fail) {
-        tc_commit(&bar[TC_NST + 1]);
-        const unsigned long long t0 = global_ns();
-        while (!bar_test(&bar[TC_NST + 1], 0) && global_ns() - t0 < TC_WAIT_NS) {
+        cp_async_wait<0>();
+    } else {
+        // ---------------------------------------------------------------- epilogue
+        // TMEM lane m = 32 (warp % 4) + lane is digit row a = m % 8 of accumulator x = m / 8
+        const int m = 32 * (warp & 3) + lane, x = m >> 3, a = m & 7;
+        const bool mid = warp >= 2 + TC_PROD_WARPS + 4;  // warps 14-17: d0 R1 + d1 R0
+        const uint32_t trow = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
+        uint32_t np_c = 0;
+        bool ok = true;
+        for (size_t it = blockIdx.x; it < n_items && ok; it += gridDim.x) {
+            const Item I = item_at(P, it, n_el);
+            const PrimeDev pd = P.pr[(int)(I.e >> P.logN)];
+            for (int kr = 0; kr < P.n_kr && ok; kr++)
+                for (int p = 0; p < nqp && ok; p++, np_c++) {
+                    const uint32_t buf = np_c & 1;
+                    if (!(ok = warp_wait(&bar[BAR_T_FULL + buf], (np_c >> 1) & 1, fail, P.status))) break;
+                    tc_fence_after();
+                    const uint32_t tb = trow + buf * 256;  // d0 x (R0 | R1) at tb, d1 x (R0 | R1) at tb + 128
+                    const int gq = p * TC_QP + a;           // this lane's query ciphertext after the scatter
+                    for (int k = mid ? 1 : 0; k < 3; k += 2) {
+                        u128 v[TC_QP];
+                        if (k == 1) {
+#pragma unroll
+                            for (int h = 0; h < 2; h++) {
+                                uint32_t w0[4][8], w1[4][8];
+#pragma unroll
+                                for (int qq = 0; qq < 4; qq++) {
+                                    tmem_ld8(tb + (uint32_t)((4 * h + qq) * 16 + 8), w0[qq]);    // d0 R1
+                                    tmem_ld8(tb + (uint32_t)(128 + (4 * h + qq) * 16), w1[qq]);  // d1 R0
+                                }
+                                tmem_wait_ld();
+#pragma unroll
+                                for (int qq = 0; qq < 4; qq++) {
+                                    uint32_t u[8];
+#pragma unroll
+                                    for (int b = 0; b < 8; b++) u[b] = f32_biased(w0[qq][b]) + f32_biased(w1[qq][b]);
+                                    v[4 * h + qq] = row_value(u);
+                                }
+                            }
+                        } else {
+                            uint32_t w[TC_QP][8];
+#pragma unroll
+                            for (int qq = 0; qq < TC_QP; qq++)
+                                tmem_ld8(tb + (uint32_t)(k == 0 ? qq * 16 : 128 + qq * 16 + 8), w[qq]);  // d0 R0, d1 R1
+                            tmem_wait_ld();
+#pragma unroll
+                            for (int qq = 0; qq < TC_QP; qq++) {
+                                uint32_t u[8];
+#pragma unroll
+                                for (int b = 0; b < 8; b++) u[b] = f32_biased(w[qq][b]);
+                                v[qq] = row_value(u);
+                            }
+                        }
+                        const u128 t = reduce_scatter8(v, lane) - (k == 1 ? 2 : 1) * bias_rows();
+                        if (x < I.nx && gq < P.nq) {
+                            const u64 val = reduce_signed128(t, pd);
+                            u64 *o = P.acc + (size_t)gq * P.a_ct + ((size_t)(I.x0 + x) * 3 + k) * n_el + I.e;
+                            *o = kr == 0 ? val : add_mod(*o, val, pd.q);  // the first run writes, later runs add
+                        }
+                    }
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) bar_arrive(&bar[BAR_T_EMPTY + buf]);
+                }
         }
     }
     tc_fence_before();
@@ -364,14 +567,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_enc_mac_tc(const TcArgs P) {
     }
 }
 
-// rot [nb][2][n_el] of query ciphertext b -> R [n_el][nq][nb][2]: 32 elements x 32 rows
-// (j, c) per block through shared memory, reads coalesced along the elements, writes along
-// the rows
+// rot [nb][2][n_el] of query ciphertext b -> R [n_el][nks][nq][16][2] (baby step j in chunk
+// j / 16 at j % 16): 32 elements x 32 rows (j, c) per block through shared memory, reads
+// coalesced along the elements, writes along the rows
 __global__ void k_rot_to_elements(const u64 *__restrict__ rot, u64 *__restrict__ R, int nb, int nq, int b,
                                   size_t n_el) {
     __shared__ u64 t[32][33];
     const size_t e0 = (size_t)blockIdx.x * 32;
-    const int row0 = blockIdx.y * 32, rows = 2 * nb;
+    const int row0 = blockIdx.y * 32, rows = 2 * nb, nks = (nb + TC_KS - 1) / TC_KS;
     for (int i = threadIdx.y; i < 32; i += blockDim.y) {
         const int row = row0 + i;
         const size_t e = e0 + threadIdx.x;
@@ -381,7 +584,10 @@ __global__ void k_rot_to_elements(const u64 *__restrict__ rot, u64 *__restrict__
     for (int i = threadIdx.y; i < 32; i += blockDim.y) {
         const size_t e = e0 + i;
         const int row = row0 + threadIdx.x;
-        if (e < n_el && row < rows) R[(e * nq + b) * rows + row] = t[threadIdx.x][i];
+        if (e < n_el && row < rows) {
+            const int j = row >> 1;
+            R[((e * nks + j / TC_KS) * nq + b) * (TC_KS * 2) + (j % TC_KS) * 2 + (row & 1)] = t[threadIdx.x][i];
+        }
     }
 }
 
@@ -447,10 +653,12 @@ copse_status enc_mac_tc(copse_ctx *c, const EncModel::MacMat &M, const u64 *R, i
     P.logN = c->logN;
     P.n_mt = (M.nm + TC_MX - 1) / TC_MX;
     P.n_kr = (M.nb + TC_KR - 1) / TC_KR;
+    P.nks = (M.nb + TC_KS - 1) / TC_KS;
+    P.nb16 = P.nks * TC_KS;
     P.seed = seed;
     P.pr = c->d_prime;
     P.status = c->d_status;
-    const size_t n_items = (size_t)P.n_mt * P.n_kr * ((size_t)M.ell << c->logN);
+    const size_t n_items = (size_t)P.n_mt * ((size_t)M.ell << c->logN);
     const unsigned grid = (unsigned)std::min<size_t>(n_items, (size_t)tc_grid(c->device));
     k_enc_mac_tc<<<grid, TC_THREADS, SMEM_TC, s>>>(P);
     LAUNCH_CHECK();
@@ -478,14 +686,14 @@ copse_status mac_scatter(copse_ctx *c, const u64 *c0, const uint32_t *pos, int n
                          cudaStream_t s) {
     const size_t n_el = (size_t)M.ell << c->logN;
     const dim3 grid((unsigned)((n_el + 31) / 32), (unsigned)((nc + 31) / 32));
-    k_mac_scatter<<<grid, dim3(32, 8), 0, s>>>(c0, pos, M.c0, nc, n_el, (size_t)M.nm * M.nb);
+    k_mac_scatter<<<grid, dim3(32, 8), 0, s>>>(c0, pos, M.c0, nc, n_el, (size_t)M.nm * mac_row(M.nb));
     LAUNCH_CHECK();
     return COPSE_OK;
 }
 
 copse_status mac_gather(copse_ctx *c, const EncModel::MacMat &M, uint32_t pos, u64 *c0, cudaStream_t s) {
     const size_t n_el = (size_t)M.ell << c->logN;
-    k_mac_gather<<<(unsigned)((n_el + 255) / 256), 256, 0, s>>>(M.c0, (size_t)M.nm * M.nb, pos, c0, n_el);
+    k_mac_gather<<<(unsigned)((n_el + 255) / 256), 256, 0, s>>>(M.c0, (size_t)M.nm * mac_row(M.nb), pos, c0, n_el);
     LAUNCH_CHECK();
     return COPSE_OK;
 }

@@ -516,6 +516,9 @@ copse_status op_matmul(copse_ctx *c, const copse_evk *evk, const DCt &v, const s
 // The model's ciphertexts in canonical order (threshold planes, reshuffle diagonals,
 // level-k diagonals for k = 1..d, masks), each a secret-key encryption at its level
 // of use with only c0 stored; c1 is regenerated from (seed, stream of the index).
+// words per accumulator row of the element-major diagonal blocks: baby steps rounded up to 16
+inline int mac_row(int nb) { return (nb + 15) / 16 * 16; }
+
 struct EncModel {
     uint64_t ctx_serial = 0;
     u64 seed = 0;
@@ -525,8 +528,9 @@ struct EncModel {
     u64 *store = nullptr;            // c0 of the threshold planes and the level masks, [ell][N] each
     // The diagonals of the two products (kind 0 reshuffle, 1 levels) in the layout of the
     // tensor-core multiply-accumulate, one block per matrix of the plan: c0 element-major
-    // [ell N][nm][nb] (zero where the plan has no diagonal) and the model ciphertext index of
-    // each (accumulator, baby step), [nm][nb] (~0u = none), which names its mask stream.
+    // [ell N][nm][mac_row(nb)] (zero where the plan has no diagonal and in the row padding)
+    // and the model ciphertext index of each (accumulator, baby step), [nm][nb] (~0u = none),
+    // which names its mask stream.
     struct MacMat {
         u64 *c0 = nullptr;
         uint32_t *idx = nullptr;
@@ -535,7 +539,7 @@ struct EncModel {
     };
     std::vector<MacMat> mac[2];
     // where each model ciphertext's c0 lives: kind -1 in `store` at off[i], else in
-    // mac[kind][mat] at position pos = x nb + j of every element
+    // mac[kind][mat] at position pos = x mac_row(nb) + j of every element
     struct DiagAt {
         int kind = -1, mat = 0;
         uint32_t pos = 0;
@@ -564,10 +568,11 @@ copse_status enc_matmul(copse_ctx *c, const copse_evk *evk, const EncModel &E, c
                         std::vector<std::vector<DCt>> &out, cudaStream_t s);
 // Tensor-core multiply-accumulate of one matrix (encmac.cu): for every element e, query
 // ciphertext b < nq and accumulator x of M,
-//   (acc0, acc1, acc2)[b][x][e] += sum_j (d0 R0, d0 R1 + d1 R0, d1 R1)
+//   (acc0, acc1, acc2)[b][x][e] = sum_j (d0 R0, d0 R1 + d1 R0, d1 R1)
 // with d the diagonal (x, j) (c0 from M, c1 regenerated from its stream) and R the rotation
-// j of query ciphertext b, R element-major [ell N][nq][nb][2]; acc [nq][nm][3][ell N]
-// (a_ct words per query ciphertext).
+// j of query ciphertext b, R element-major [ell N][ceil(nb / 16)][nq][16][2] (baby step j in
+// chunk j / 16 at j % 16); acc [nq][nm][3][ell N] (a_ct words per query ciphertext) is
+// written (not added to).
 copse_status enc_mac_tc(copse_ctx *c, const EncModel::MacMat &M, const u64 *R, int nq, u64 *acc, size_t a_ct,
                         u64 seed, cudaStream_t s);
 // rotations [nb][2][ell N] of query ciphertext b into the element-major layout of enc_mac_tc
