@@ -14,12 +14,12 @@
 // s_i = byte i of w = v' + C minus 128, C = 0x0080808080808080 (128 in bytes 0-6); w lies in
 // (C - 2^54, C + 2^54), so byte 7 of w is 0 and no carry is lost.  A digit is exact in fp16
 // and the product of two digits is at most 2^14 in magnitude, so the f32 accumulator of the
-// MMA holds a sum of up to 256 such products exactly (|sum| <= 2^22).  The diagonals' digits
-// sit in the M dimension (row 8 x + a for digit a of accumulator x; row 8 x + 7 zero) and
-// the rotations' digits in the N dimension (column 8 (2 b + c) + a' for digit a' of component
-// c of query b; column a' = 7 zero), so the accumulator holds, for every digit pair (a, a'),
-// the exact partial sum D_aa' = sum_j s_a(d[x][j]) s_a'(R_c[j][b]), and the product sum
-// sum_j d'[x][j] R'_c[j][b] = sum_aa' D_aa' 256^(a + a') (|.| < 2^116, congruent mod q to the
+// MMA holds a sum of up to 256 such products exactly (|sum| <= 2^22).  The rotations' digits
+// sit in the M dimension (row 8 (2 b + c) + a' for digit a' of component c of query b; a' = 7
+// zero) and the diagonals' digits in the N dimension (column 128 c' + 8 x + a for digit a of
+// component c' of accumulator x; a = 7 zero), so the accumulator holds, for every digit pair,
+// the exact partial sum D_a'a = sum_j s_a'(R_c[j][b]) s_a(d_c'[x][j]), and the product sum
+// sum_j R'_c[j][b] d'_c'[x][j] = sum D_a'a 256^(a' + a) (|.| < 2^116, congruent mod q to the
 // product sum of the residues) is rebuilt in 128-bit integers and reduced mod q once.
 //
 // One CTA per SM, persistent over work items (element, tile of 16 accumulators, run of up
@@ -29,15 +29,15 @@
 //                ciphertexts x 16 baby steps x 2 components, contiguous) per bulk copy
 //                (cp.async.bulk with transaction-count completion) into a ring of stages
 //   warps 2-9    producers: per item the digits of both components of every diagonal (c0
-//                read element-major, c1 regenerated from its seed) into shared memory, then
-//                the digits of the rotations into a ring of operand stages, each warp
-//                converting whole chunks in turn
+//                read element-major, c1 regenerated from its seed) into shared memory; warps
+//                2-4 then convert the rotations' chunks into a ring of operand stages, each
+//                warp whole chunks in turn
 //   warps 10-17  epilogue: per pass (8 query ciphertexts) the accumulators back from tensor
 //                memory (tcgen05.ld), the exact outputs rebuilt, reduced and stored in acc;
-//                warps 10-13 take d0 R0 and d1 R1, warps 14-17 d0 R1 + d1 R0
-// Per chunk two M 128 x N 128 x K 16 MMAs accumulate d0 x [R0 | R1] and d1 x [R0 | R1] into
-// one of two tensor-memory buffers (2 x 2 x 128 columns), so the epilogue of one pass
-// overlaps the products of the next.
+//                warps 10-13 take accumulators 0-7, warps 14-17 accumulators 8-15
+// Per chunk one M 128 x N 256 x K 16 MMA accumulates [R0 | R1] x [d0 | d1] (all four
+// component products) into one of two tensor-memory buffers of 256 columns, so the epilogue
+// of one pass overlaps the products of the next.
 //
 // Every wait is bounded by the global timer: a wait that runs out sets COPSE_DEV_MAC_WAIT in
 // the context's device status word and every role of the CTA stops; the copies and MMAs in
@@ -49,31 +49,34 @@
 
 namespace {
 
-constexpr int TC_MX = 16;         // accumulators per tile: 16 x 8 digit rows = M 128
-constexpr int TC_QP = 8;          // query ciphertexts per pass: 8 x 2 components x 8 digits = N 128
+constexpr int TC_MX = 16;         // accumulators per tile: 16 x 8 digit rows, N 128 per component
+constexpr int TC_QP = 8;          // query ciphertexts per pass: 8 x 2 components x 8 digit rows = M 128
 constexpr int TC_KR = 256;        // baby steps per run: exact f32 partial sums
-constexpr int TC_KS = 16;         // baby steps per MMA (K of kind::f16) and per chunk
-constexpr int TC_NB = 8;          // operand stages of the rotations' digits
-constexpr int TC_NR = 16;         // raw stages of the rotations
+constexpr int TC_KS = 16;         // baby steps per MMA (K of kind::f16)
+constexpr int TC_CJ = 64;         // baby steps per chunk (4 MMAs per operand stage)
+constexpr int TC_NB = 3;          // operand stages of the rotations' digits
+constexpr int TC_NR = 6;          // raw stages of the rotations
 constexpr int TC_PROD_WARPS = 8, TC_EPI_WARPS = 8;
+// Every producer warp converts a part of every chunk, so each waiter meets every phase of the
+// stage barriers in order (the waits test a phase parity, which is sound only while no waiter
+// runs two phases ahead of a barrier).
 constexpr int TC_THREADS = 32 * (2 + TC_PROD_WARPS + TC_EPI_WARPS);  // 576
 constexpr int TC_TMEM_COLS = 512;
 constexpr unsigned long long TC_WAIT_NS = 2000000000ull;  // 2 s per wait
 
 constexpr uint32_t A_SET = TC_MX * 8 * TC_KR * 2;        // digits of one diagonal component: 64 KB
-constexpr uint32_t B_STAGE = TC_QP * 2 * 8 * TC_KS * 2;  // digits of one chunk of rotations: 4 KB
-constexpr uint32_t RAW_STAGE = TC_QP * TC_KS * 2 * 8;    // raw words of one chunk: 2 KB
+constexpr uint32_t B_ROW = TC_CJ / 8 * 128;              // bytes between the rotations' core-matrix rows: 1 KB
+constexpr uint32_t B_STAGE = TC_QP * 2 * B_ROW;          // digits of one chunk of rotations: 16 KB
+constexpr uint32_t RAW_STAGE = TC_QP * TC_CJ * 2 * 8;    // raw words of one chunk: 8 KB
 // barriers: raw full / empty, operand full / empty, diagonals full / empty, accumulators full /
 // empty (two buffers), drain
 constexpr int BAR_RAW_FULL = 0, BAR_RAW_EMPTY = TC_NR, BAR_B_FULL = 2 * TC_NR, BAR_B_EMPTY = 2 * TC_NR + TC_NB,
               BAR_A_FULL = 2 * TC_NR + 2 * TC_NB, BAR_A_EMPTY = BAR_A_FULL + 1, BAR_T_FULL = BAR_A_FULL + 2,
               BAR_T_EMPTY = BAR_T_FULL + 2, BAR_DRAIN = BAR_T_EMPTY + 2, N_BAR = BAR_DRAIN + 1;
-constexpr uint32_t C0_STAGE = TC_MX * TC_KR * 8;        // c0 words of one run: 32 KB
-constexpr uint32_t OFF_A0 = 0, OFF_A1 = A_SET, OFF_B = 2 * A_SET, OFF_RAW = OFF_B + TC_NB * B_STAGE,
-                   OFF_C0 = OFF_RAW + TC_NR * RAW_STAGE, OFF_BAR = OFF_C0 + C0_STAGE, OFF_MISC = OFF_BAR + N_BAR * 8,
-                   SMEM_TC = OFF_MISC + 16;
-static_assert(TC_QP * TC_KS == 4 * 32, "four (query, baby step) pairs per lane of the warp that converts a chunk");
-static_assert(TC_NB == TC_PROD_WARPS && TC_NR % TC_PROD_WARPS == 0, "a producer warp keeps to its own stages");
+constexpr uint32_t OFF_A0 = 0, OFF_B = 2 * A_SET, OFF_RAW = OFF_B + TC_NB * B_STAGE, OFF_BAR = OFF_RAW + TC_NR * RAW_STAGE,
+                   OFF_MISC = OFF_BAR + N_BAR * 8, SMEM_TC = OFF_MISC + 16;
+static_assert(TC_QP * TC_CJ == 2 * 32 * TC_PROD_WARPS, "two (query, baby step) pairs per producer lane and chunk");
+static_assert(TC_KR % TC_CJ == 0, "runs are whole chunks");
 static_assert(SMEM_TC <= 227 * 1024, "shared memory");
 
 // kind::f16 instruction descriptor: f32 accumulator (bits 4-5 = 1), f16 A and B (formats 0),
@@ -81,7 +84,7 @@ static_assert(SMEM_TC <= 227 * 1024, "shared memory");
 constexpr uint32_t idesc_f16(int M, int N) {
     return (1u << 4) | (1u << 15) | (1u << 16) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
-constexpr uint32_t IDESC = idesc_f16(128, TC_QP * 2 * 8);  // M 128, N 128
+constexpr uint32_t IDESC = idesc_f16(TC_QP * 2 * 8, 2 * TC_MX * 8);  // M 128 (rotation digits), N 256 (both components of the diagonals)
 
 __device__ __forceinline__ uint32_t sh_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -132,6 +135,10 @@ __device__ __forceinline__ void bulk_copy(void *dst, const void *src, uint32_t b
                      sh_addr(dst)),
                  "l"(src), "r"(bytes), "r"(sh_addr(bar))
                  : "memory");
+}
+// bytes (a multiple of 16, 16-byte aligned) of global memory into L2, no completion tracked
+__device__ __forceinline__ void l2_prefetch(const void *src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
 }
 __device__ __forceinline__ bool bar_test(uint64_t *bar, uint32_t parity) {
     uint32_t done;
@@ -184,8 +191,13 @@ __device__ __forceinline__ uint32_t hsub2(uint32_t a, uint32_t b) {
 // The seven balanced base-256 digits of the centred residue of v (v < q) and a zero eighth, as
 // eight fp16 (digit i in half i): byte i of v' + 0x0080808080808080 with 0x64 above it is the
 // fp16 of 1024 + byte, less 1152 = 1024 + 128 for bytes 0-6 and less 1024 for byte 7 (zero).
+constexpr u64 DIGIT_BIAS = 0x0080808080808080ull;
+// the same from w = v' + DIGIT_BIAS
+__device__ __forceinline__ uint4 digits8_biased(u64 w);
 __device__ __forceinline__ uint4 digits8(u64 v, u64 q) {
-    const u64 w = (v > (q >> 1) ? v - q : v) + 0x0080808080808080ull;  // v' = v - q above q / 2
+    return digits8_biased((v > (q >> 1) ? v - q : v) + DIGIT_BIAS);  // v' = v - q above q / 2
+}
+__device__ __forceinline__ uint4 digits8_biased(u64 w) {
     const uint32_t lo = (uint32_t)w, hi = (uint32_t)(w >> 32);
     constexpr uint32_t C = 0x64806480u, C7 = 0x64006480u;  // (1152, 1152), (1152 low, 1024 high)
     uint4 r;
@@ -222,28 +234,6 @@ __host__ __device__ constexpr u128 bias_rows() {
     return (u128)MAGIC_BITS * S8 * S7;
 }
 
-// sum_a V_a 256^a over the 8 lanes of a digit group (lanes differing in bits 0-2; V_a the row
-// value of digit a = lane % 8), scattered: lane a of the group ends with the total for v[a].
-// The round on bit s pairs a lane holding the lower digits with one holding digits 2^s higher,
-// so their sum is lo + hi 256^(2^s); after the three rounds no digit offset is left.
-__device__ __forceinline__ u128 reduce_scatter8(u128 (&v)[8], int lane) {
-    const bool b2 = (lane >> 2) & 1, b1 = (lane >> 1) & 1, b0 = lane & 1;
-#pragma unroll
-    for (int i = 0; i < 4; i++) {
-        const u128 send = b2 ? v[i] : v[4 + i], keep = b2 ? v[4 + i] : v[i];
-        const u128 got = shfl_xor_u128(send, 4);
-        v[i] = b2 ? got + (keep << 32) : keep + (got << 32);
-    }
-#pragma unroll
-    for (int i = 0; i < 2; i++) {
-        const u128 send = b1 ? v[i] : v[2 + i], keep = b1 ? v[2 + i] : v[i];
-        const u128 got = shfl_xor_u128(send, 2);
-        v[i] = b1 ? got + (keep << 16) : keep + (got << 16);
-    }
-    const u128 send = b0 ? v[0] : v[1], keep = b0 ? v[1] : v[0];
-    const u128 got = shfl_xor_u128(send, 1);
-    return b0 ? got + (keep << 8) : keep + (got << 8);
-}
 // (t mod 2^128, read as a signed value) mod q
 __device__ __forceinline__ u64 reduce_signed128(u128 t, const PrimeDev &pd) {
     if ((u64)(t >> 64) >> 63) {
@@ -257,10 +247,10 @@ __device__ __forceinline__ u64 reduce_signed128(u128 t, const PrimeDev &pd) {
 struct TcArgs {
     const u64 *mac;       // [n_el][nm][nb16] diagonals' c0 (rows of nb16 = nb rounded up to 16 words)
     const uint32_t *idx;  // [nm][nb] model ciphertext index (mask stream), ~0u = none
-    const u64 *R;         // [n_el][nks][nq][16][2] rotations (nks = baby steps / 16, rounded up)
+    const u64 *R;         // [n_el][nc][nq][64][2] rotations (nc = baby steps / 64, rounded up)
     u64 *acc;             // [nq][nm][3][n_el], written by the first run, added to by later ones
     size_t a_ct;          // words per query ciphertext in acc
-    int nm, nb, nb16, nq, ell, logN, n_mt, n_kr, nks;
+    int nm, nb, nb16, nq, ell, logN, n_mt, n_kr, nc;
     u64 seed;
     const PrimeDev *pr;
     int *status;
@@ -281,19 +271,20 @@ __device__ __forceinline__ Item item_at(const TcArgs &P, size_t it, size_t n_el)
     return I;
 }
 struct Run {
-    int j0, nj, nk;  // first baby step, baby steps, chunks of 16
+    int j0, nj, nk, ncr;  // first baby step, baby steps, MMAs (16 baby steps), chunks (64)
 };
 __device__ __forceinline__ Run run_at(const TcArgs &P, int kr) {
     Run R;
     R.j0 = kr * TC_KR;
     R.nj = min(TC_KR, P.nb - R.j0);
     R.nk = (R.nj + TC_KS - 1) / TC_KS;
+    R.ncr = (R.nj + TC_CJ - 1) / TC_CJ;
     return R;
 }
 
 __global__ void __launch_bounds__(TC_THREADS, 1) k_enc_mac_tc(const TcArgs P) {
     extern __shared__ __align__(1024) uint8_t sm[];
-    uint8_t *A0 = sm + OFF_A0, *A1 = sm + OFF_A1, *Bst = sm + OFF_B, *Raw = sm + OFF_RAW, *C0s = sm + OFF_C0;
+    uint8_t *A0 = sm + OFF_A0, *Bst = sm + OFF_B, *Raw = sm + OFF_RAW;
     uint64_t *bar = (uint64_t *)(sm + OFF_BAR);
     uint32_t *tslot = (uint32_t *)(sm + OFF_MISC);
     volatile int *fail = (volatile int *)(sm + OFF_MISC + 4);
@@ -312,10 +303,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_enc_mac_tc(const TcArgs P) {
     if (tid == 32) {
         for (int i = 0; i < TC_NR; i++) {
             bar_init(&bar[BAR_RAW_FULL + i], 1);
-            bar_init(&bar[BAR_RAW_EMPTY + i], 1);
+            bar_init(&bar[BAR_RAW_EMPTY + i], TC_PROD_WARPS);
         }
         for (int i = 0; i < TC_NB; i++) {
-            bar_init(&bar[BAR_B_FULL + i], 1);
+            bar_init(&bar[BAR_B_FULL + i], TC_PROD_WARPS);
             bar_init(&bar[BAR_B_EMPTY + i], 1);
         }
         bar_init(&bar[BAR_A_FULL], TC_PROD_WARPS);
@@ -349,14 +340,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_enc_mac_tc(const TcArgs P) {
                             !(ok = bar_wait(&bar[BAR_T_EMPTY + buf], ((np_c >> 1) - 1) & 1, fail, P.status)))
                             break;
                         tc_fence_after();
-                        const uint32_t d0 = tmem + buf * 256, d1 = d0 + 128;
-                        for (int ks = 0; ks < R.nk; ks++, nb_c++) {
+                        const uint32_t d = tmem + buf * 256;
+                        for (int kc = 0; kc < R.ncr; kc++, nb_c++) {
                             const int st = (int)(nb_c % TC_NB);
                             if (!(ok = bar_wait(&bar[BAR_B_FULL + st], (nb_c / TC_NB) & 1, fail, P.status))) break;
                             tc_fence_after();
-                            const uint64_t bd = smem_desc(sh_addr(Bst + st * B_STAGE), 128, 256);
-                            tc_mma(d0, smem_desc(sh_addr(A0) + (uint32_t)ks * 256, 128, a_mn), bd, ks > 0);
-                            tc_mma(d1, smem_desc(sh_addr(A1) + (uint32_t)ks * 256, 128, a_mn), bd, ks > 0);
+                            // rotations' digits (M: row 8 (2 q + c) + b) x diagonals' digits of both
+                            // components (N: column 128 c' + 8 x + a; the second component's core
+                            // matrices follow the first's at the same stride), 16 baby steps per MMA
+                            const int ns = min(TC_CJ / TC_KS, R.nk - kc * (TC_CJ / TC_KS));
+                            for (int s2 = 0; s2 < ns; s2++)
+                                tc_mma(d, smem_desc(sh_addr(Bst + st * B_STAGE) + (uint32_t)s2 * 256, 128, B_ROW),
+                                       smem_desc(sh_addr(A0) + (uint32_t)(kc * (TC_CJ / TC_KS) + s2) * 256, 128, a_mn),
+                                       (kc | s2) != 0);
                             tc_commit(&bar[BAR_B_EMPTY + st]);
                             issued = true;
                         }
@@ -378,19 +374,28 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_enc_mac_tc(const TcArgs P) {
             bool ok = true;
             for (size_t it = blockIdx.x; it < n_items && ok; it += gridDim.x) {
                 const Item I = item_at(P, it, n_el);
+                if (it + gridDim.x < n_items) {
+                    // the next item's rotations (one contiguous block per element) and c0 rows into
+                    // L2 while this one runs, so that the ring's copies and the digit builds read L2
+                    const Item J = item_at(P, it + gridDim.x, n_el);
+                    const size_t rb = (size_t)P.nc * P.nq * TC_CJ * 2 * 8;
+                    const uint8_t *r0 = (const uint8_t *)(P.R + J.e * (size_t)P.nc * P.nq * TC_CJ * 2);
+                    for (size_t o = 0; o < rb; o += 32768) l2_prefetch(r0 + o, (uint32_t)(rb - o < 32768 ? rb - o : 32768));
+                    l2_prefetch(P.mac + (J.e * P.nm + J.x0) * P.nb16, (uint32_t)(J.nx * P.nb16 * 8));
+                }
                 for (int kr = 0; kr < P.n_kr && ok; kr++) {
                     const Run R = run_at(P, kr);
                     for (int p = 0; p < nqp && ok; p++)
-                        for (int ks = 0; ks < R.nk; ks++, nr_c++) {
+                        for (int kc = 0; kc < R.ncr; kc++, nr_c++) {
                             const int st = (int)(nr_c % TC_NR);
                             if (nr_c >= TC_NR &&
                                 !(ok = bar_wait(&bar[BAR_RAW_EMPTY + st], ((nr_c / TC_NR) - 1) & 1, fail, P.status)))
                                 break;
                             const int nqq = min(TC_QP, P.nq - p * TC_QP);
-                            const uint32_t bytes = (uint32_t)nqq * TC_KS * 2 * 8;
+                            const uint32_t bytes = (uint32_t)nqq * TC_CJ * 2 * 8;
                             bar_expect_tx(&bar[BAR_RAW_FULL + st], bytes);
                             bulk_copy(Raw + st * RAW_STAGE,
-                                      P.R + (((I.e * P.nks + R.j0 / TC_KS + ks) * P.nq + (size_t)p * TC_QP) * TC_KS * 2),
+                                      P.R + (((I.e * P.nc + R.j0 / TC_CJ + kc) * P.nq + (size_t)p * TC_QP) * TC_CJ * 2),
                                       bytes, &bar[BAR_RAW_FULL + st]);
                         }
                 }
@@ -406,26 +411,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_enc_mac_tc(const TcArgs P) {
     } else if (warp < 2 + TC_PROD_WARPS) {
         // ---------------------------------------------------------------- producers
         // Thread pt builds the digits of the (accumulator, baby step) pairs 2 (pt + 256 k) and the
-        // next one of each run, from the c0 words it copied itself (cp.async, issued while the
-        // previous run's products run).  Producer warp pw converts the rotations of the chunks
-        // with index pw modulo 8 (so it keeps to operand stage pw), four (query, baby step) pairs
-        // per lane.
-        const int pt = tid - 64, pw = warp - 2;
+        // next one of each run (c0 read from L2, where the loader prefetched it), and converts the
+        // rotations of pairs pt and pt + 256 of every chunk (the words come centred and biased,
+        // v' + 0x0080808080808080, from the rotations' element-major layout).
+        const int pt = tid - 64;
         uint32_t nb_c = 0, nr_c = 0, na = 0;
         bool ok = true;
-        // c0 of the run (it, kr) into the staging area: row x of the tile at x * nj16 words
-        auto fetch_c0 = [&](size_t it, int kr) {
-            const Item I = item_at(P, it, n_el);
-            const Run R = run_at(P, kr);
-            const int nj16 = R.nk * TC_KS;
-            for (int i = 2 * pt; i < TC_MX * nj16; i += 2 * TC_PROD_WARPS * 32) {
-                const int x = i / nj16, j = i - x * nj16;
-                if (x < I.nx)
-                    cp_async16(C0s + (size_t)i * 8, P.mac + (I.e * P.nm + I.x0 + x) * P.nb16 + R.j0 + j);
-            }
-            cp_async_commit();
-        };
-        if ((size_t)blockIdx.x < n_items) fetch_c0(blockIdx.x, 0);
         for (size_t it = blockIdx.x; it < n_items && ok; it += gridDim.x) {
             const Item I = item_at(P, it, n_el);
             const int r = (int)(I.e >> P.logN);
@@ -435,19 +426,30 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_enc_mac_tc(const TcArgs P) {
                 const Run R = run_at(P, kr);
                 const int nj16 = R.nk * TC_KS;
                 const uint32_t a_mn = (uint32_t)nj16 * 16;
+                uint8_t *A1 = A0 + TC_MX * a_mn;  // the second component's rows continue the first's
+                // the c0 words of this thread's pairs, loaded before the wait for the digits' space
+                ulonglong2 cw[TC_MX * TC_KR / (2 * TC_PROD_WARPS * 32)];
+#pragma unroll
+                for (int k = 0; k < TC_MX * TC_KR / (2 * TC_PROD_WARPS * 32); k++) {
+                    const int i = 2 * pt + k * 2 * TC_PROD_WARPS * 32, x = i / nj16, j = i - x * nj16;
+                    cw[k] = make_ulonglong2(0, 0);
+                    if (i < TC_MX * nj16 && x < I.nx)
+                        cw[k] = *(const ulonglong2 *)(P.mac + (I.e * P.nm + I.x0 + x) * P.nb16 + R.j0 + j);
+                }
                 // the diagonals' digits, once the previous run's products are done with them: the 16
                 // bytes of accumulator x at baby step j are row j % 8 of core matrix (x, j / 8)
                 if (na > 0 && !(ok = warp_wait(&bar[BAR_A_EMPTY], (na - 1) & 1, fail, P.status))) break;
-                cp_async_wait<0>();
-                for (int i = 2 * pt; i < TC_MX * nj16; i += 2 * TC_PROD_WARPS * 32) {
-                    const int x = i / nj16, j = i - x * nj16;
+#pragma unroll
+                for (int k = 0; k < TC_MX * TC_KR / (2 * TC_PROD_WARPS * 32); k++) {
+                    const int i = 2 * pt + k * 2 * TC_PROD_WARPS * 32, x = i / nj16, j = i - x * nj16;
+                    if (i >= TC_MX * nj16) continue;
 #pragma unroll
                     for (int h = 0; h < 2; h++) {
                         const uint32_t id =
                             (x < I.nx && j + h < R.nj) ? __ldg(P.idx + (size_t)(I.x0 + x) * P.nb + R.j0 + j + h) : ~0u;
                         u64 d0 = 0, d1 = 0;
                         if (id != ~0u) {
-                            d0 = *(const u64 *)(C0s + (size_t)(i + h) * 8);
+                            d0 = h ? cw[k].y : cw[k].x;
                             d1 = seeded_mask(P.seed, MODEL_STREAM + 2ull * id, r, pos, P.logN, pd);
                         }
                         const uint32_t off =
@@ -459,15 +461,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_enc_mac_tc(const TcArgs P) {
                 fence_async_smem();
                 __syncwarp();
                 if (lane == 0) bar_arrive(&bar[BAR_A_FULL]);
-                // the next run's c0, while this run's products run
-                if (kr + 1 < P.n_kr)
-                    fetch_c0(it, kr + 1);
-                else if (it + gridDim.x < n_items)
-                    fetch_c0(it + gridDim.x, 0);
                 // the rotations' digits, chunk by chunk
                 for (int p = 0; p < nqp && ok; p++)
-                    for (int ks = 0; ks < R.nk; ks++, nb_c++, nr_c++) {
-                        if ((int)(nb_c % TC_PROD_WARPS) != pw) continue;
+                    for (int kc = 0; kc < R.ncr; kc++, nb_c++, nr_c++) {
                         const int st = (int)(nb_c % TC_NB), rs = (int)(nr_c % TC_NR);
                         if (nb_c >= TC_NB &&
                             !(ok = warp_wait(&bar[BAR_B_EMPTY + st], ((nb_c / TC_NB) - 1) & 1, fail, P.status)))
@@ -476,13 +472,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_enc_mac_tc(const TcArgs P) {
                         const uint8_t *raw = Raw + rs * RAW_STAGE;
                         uint8_t *Bs = Bst + st * B_STAGE;
 #pragma unroll
-                        for (int u = 0; u < 4; u++) {
-                            const int pr = lane + 32 * u, q = pr >> 4, j = pr & 15;
-                            ulonglong2 v = make_ulonglong2(0, 0);
-                            if (p * TC_QP + q < P.nq && ks * TC_KS + j < R.nj) v = *(const ulonglong2 *)(raw + pr * 16);
+                        for (int u = 0; u < 2; u++) {
+                            const int pr = pt + TC_PROD_WARPS * 32 * u, q = pr >> 6, j = pr & 63;
+                            ulonglong2 v = make_ulonglong2(DIGIT_BIAS, DIGIT_BIAS);  // digits of zero
+                            if (p * TC_QP + q < P.nq && kc * TC_CJ + j < R.nj) v = *(const ulonglong2 *)(raw + pr * 16);
                             uint8_t *B = Bs + (j >> 3) * 128 + (j & 7) * 16;
-                            *(uint4 *)(B + (2 * q) * 256) = digits8(v.x, pd.q);
-                            *(uint4 *)(B + (2 * q + 1) * 256) = digits8(v.y, pd.q);
+                            *(uint4 *)(B + (2 * q) * B_ROW) = digits8_biased(v.x);
+                            *(uint4 *)(B + (2 * q + 1) * B_ROW) = digits8_biased(v.y);
                         }
                         fence_async_smem();
                         __syncwarp();
@@ -493,12 +489,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_enc_mac_tc(const TcArgs P) {
                     }
             }
         }
-        cp_async_wait<0>();
     } else {
         // ---------------------------------------------------------------- epilogue
-        // TMEM lane m = 32 (warp % 4) + lane is digit row a = m % 8 of accumulator x = m / 8
-        const int m = 32 * (warp & 3) + lane, x = m >> 3, a = m & 7;
-        const bool mid = warp >= 2 + TC_PROD_WARPS + 4;  // warps 14-17: d0 R1 + d1 R0
+        // TMEM lane m = 32 (warp % 4) + lane is digit b = m % 8 of component c = (m / 8) % 2 of
+        // query q = m / 16 of the pass; column 128 c' + 8 x + a holds digit a of component c' of
+        // accumulator x.  Warps 10-13 take accumulators 0-7, warps 14-17 accumulators 8-15.
+        const int m = 32 * (warp & 3) + lane, b = m & 7, cq = (m >> 3) & 1, qq = m >> 4;
+        const int xh = warp >= 2 + TC_PROD_WARPS + 4 ? 8 : 0;
         const uint32_t trow = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
         uint32_t np_c = 0;
         bool ok = true;
@@ -510,47 +507,63 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_enc_mac_tc(const TcArgs P) {
                     const uint32_t buf = np_c & 1;
                     if (!(ok = warp_wait(&bar[BAR_T_FULL + buf], (np_c >> 1) & 1, fail, P.status))) break;
                     tc_fence_after();
-                    const uint32_t tb = trow + buf * 256;  // d0 x (R0 | R1) at tb, d1 x (R0 | R1) at tb + 128
-                    const int gq = p * TC_QP + a;           // this lane's query ciphertext after the scatter
-                    for (int k = mid ? 1 : 0; k < 3; k += 2) {
-                        u128 v[TC_QP];
-                        if (k == 1) {
+                    const uint32_t tb = trow + buf * 256;
+                    // Row values sum_{a<7} D 256^a of the 16 items it = 2 (x - xh) + c', summed over the
+                    // 8 digit rows b of (q, c) by a reduce-scatter (lane b ends with items 2b and 2b + 1,
+                    // both components c' of accumulator xh + b).  Its first round pairs items it and
+                    // it + 8, so each half of the loads (items 4h..4h+3 and 8+4h..8+4h+3) is folded at once.
+                    const bool b2 = (lane >> 2) & 1, b1 = (lane >> 1) & 1, b0 = lane & 1;
+                    u128 v[8];
 #pragma unroll
-                            for (int h = 0; h < 2; h++) {
-                                uint32_t w0[4][8], w1[4][8];
+                    for (int h = 0; h < 2; h++) {
+                        uint32_t w[8][8];
 #pragma unroll
-                                for (int qq = 0; qq < 4; qq++) {
-                                    tmem_ld8(tb + (uint32_t)((4 * h + qq) * 16 + 8), w0[qq]);    // d0 R1
-                                    tmem_ld8(tb + (uint32_t)(128 + (4 * h + qq) * 16), w1[qq]);  // d1 R0
-                                }
-                                tmem_wait_ld();
-#pragma unroll
-                                for (int qq = 0; qq < 4; qq++) {
-                                    uint32_t u[8];
-#pragma unroll
-                                    for (int b = 0; b < 8; b++) u[b] = f32_biased(w0[qq][b]) + f32_biased(w1[qq][b]);
-                                    v[4 * h + qq] = row_value(u);
-                                }
-                            }
-                        } else {
-                            uint32_t w[TC_QP][8];
-#pragma unroll
-                            for (int qq = 0; qq < TC_QP; qq++)
-                                tmem_ld8(tb + (uint32_t)(k == 0 ? qq * 16 : 128 + qq * 16 + 8), w[qq]);  // d0 R0, d1 R1
-                            tmem_wait_ld();
-#pragma unroll
-                            for (int qq = 0; qq < TC_QP; qq++) {
-                                uint32_t u[8];
-#pragma unroll
-                                for (int b = 0; b < 8; b++) u[b] = f32_biased(w[qq][b]);
-                                v[qq] = row_value(u);
-                            }
+                        for (int i = 0; i < 8; i++) {
+                            const int it2 = (i < 4 ? 0 : 8) + 4 * h + (i & 3);
+                            tmem_ld8(tb + (uint32_t)(128 * (it2 & 1) + 8 * (xh + (it2 >> 1))), w[i]);
                         }
-                        const u128 t = reduce_scatter8(v, lane) - (k == 1 ? 2 : 1) * bias_rows();
-                        if (x < I.nx && gq < P.nq) {
-                            const u64 val = reduce_signed128(t, pd);
-                            u64 *o = P.acc + (size_t)gq * P.a_ct + ((size_t)(I.x0 + x) * 3 + k) * n_el + I.e;
-                            *o = kr == 0 ? val : add_mod(*o, val, pd.q);  // the first run writes, later runs add
+                        tmem_wait_ld();
+#pragma unroll
+                        for (int i = 0; i < 4; i++) {
+                            uint32_t u[8], z[8];
+#pragma unroll
+                            for (int k = 0; k < 8; k++) {
+                                u[k] = f32_biased(w[i][k]);
+                                z[k] = f32_biased(w[4 + i][k]);
+                            }
+                            const u128 lo = row_value(u), hi = row_value(z);  // items 4h + i and 8 + 4h + i
+                            const u128 send = b2 ? lo : hi, keep = b2 ? hi : lo;
+                            const u128 got = shfl_xor_u128(send, 4);
+                            v[4 * h + i] = b2 ? got + (keep << 32) : keep + (got << 32);
+                        }
+                    }
+#pragma unroll
+                    for (int i = 0; i < 4; i++) {
+                        const u128 send = b1 ? v[i] : v[4 + i], keep = b1 ? v[4 + i] : v[i];
+                        const u128 got = shfl_xor_u128(send, 2);
+                        v[i] = b1 ? got + (keep << 16) : keep + (got << 16);
+                    }
+#pragma unroll
+                    for (int i = 0; i < 2; i++) {
+                        const u128 send = b0 ? v[i] : v[2 + i], keep = b0 ? v[2 + i] : v[i];
+                        const u128 got = shfl_xor_u128(send, 1);
+                        v[i] = b0 ? got + (keep << 8) : keep + (got << 8);
+                    }
+                    u128 t0 = v[0], t1 = v[1];
+                    t0 -= bias_rows();
+                    t1 -= bias_rows();
+                    // c = 0: t0 = d0 R0, t1 = d1 R0;  c = 1: t0 = d0 R1, t1 = d1 R1
+                    const u128 other = shfl_xor_u128(t1, 8);  // the partner lane's d1 R0 (for c = 1)
+                    const int gq = p * TC_QP + qq, x = xh + b;
+                    if (x < I.nx && gq < P.nq) {
+                        u64 *o = P.acc + (size_t)gq * P.a_ct + (size_t)(I.x0 + x) * 3 * n_el + I.e;
+                        if (cq == 0) {
+                            const u64 v0 = reduce_signed128(t0, pd);
+                            o[0] = kr == 0 ? v0 : add_mod(o[0], v0, pd.q);
+                        } else {
+                            const u64 v1 = reduce_signed128(t0 + other, pd), v2 = reduce_signed128(t1, pd);
+                            o[n_el] = kr == 0 ? v1 : add_mod(o[n_el], v1, pd.q);
+                            o[2 * n_el] = kr == 0 ? v2 : add_mod(o[2 * n_el], v2, pd.q);
                         }
                     }
                     tc_fence_before();
@@ -567,14 +580,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_enc_mac_tc(const TcArgs P) {
     }
 }
 
-// rot [nb][2][n_el] of query ciphertext b -> R [n_el][nks][nq][16][2] (baby step j in chunk
-// j / 16 at j % 16): 32 elements x 32 rows (j, c) per block through shared memory, reads
+// rot [nb][2][n_el] of query ciphertext b -> R [n_el][nc][nq][64][2] (baby step j in chunk
+// j / 64 at j % 64), each residue v stored centred and biased, v' + 0x0080808080808080: 32 elements x 32 rows (j, c) per block through shared memory, reads
 // coalesced along the elements, writes along the rows
 __global__ void k_rot_to_elements(const u64 *__restrict__ rot, u64 *__restrict__ R, int nb, int nq, int b,
-                                  size_t n_el) {
+                                  size_t n_el, int logN, const PrimeDev *__restrict__ pr) {
     __shared__ u64 t[32][33];
     const size_t e0 = (size_t)blockIdx.x * 32;
-    const int row0 = blockIdx.y * 32, rows = 2 * nb, nks = (nb + TC_KS - 1) / TC_KS;
+    const int row0 = blockIdx.y * 32, rows = 2 * nb, nc = (nb + TC_CJ - 1) / TC_CJ;
     for (int i = threadIdx.y; i < 32; i += blockDim.y) {
         const int row = row0 + i;
         const size_t e = e0 + threadIdx.x;
@@ -586,7 +599,9 @@ __global__ void k_rot_to_elements(const u64 *__restrict__ rot, u64 *__restrict__
         const int row = row0 + threadIdx.x;
         if (e < n_el && row < rows) {
             const int j = row >> 1;
-            R[((e * nks + j / TC_KS) * nq + b) * (TC_KS * 2) + (j % TC_KS) * 2 + (row & 1)] = t[threadIdx.x][i];
+            const u64 q = pr[e >> logN].q, v = t[threadIdx.x][i];
+            R[((e * nc + j / TC_CJ) * nq + b) * (TC_CJ * 2) + (j % TC_CJ) * 2 + (row & 1)] =
+                (v > (q >> 1) ? v - q : v) + DIGIT_BIAS;
         }
     }
 }
@@ -653,8 +668,8 @@ copse_status enc_mac_tc(copse_ctx *c, const EncModel::MacMat &M, const u64 *R, i
     P.logN = c->logN;
     P.n_mt = (M.nm + TC_MX - 1) / TC_MX;
     P.n_kr = (M.nb + TC_KR - 1) / TC_KR;
-    P.nks = (M.nb + TC_KS - 1) / TC_KS;
-    P.nb16 = P.nks * TC_KS;
+    P.nc = (M.nb + TC_CJ - 1) / TC_CJ;
+    P.nb16 = mac_row(M.nb);
     P.seed = seed;
     P.pr = c->d_prime;
     P.status = c->d_status;
@@ -677,7 +692,7 @@ copse_status rot_to_elements(copse_ctx *c, const u64 *rot, int nb, int nq, int b
     const size_t n_el = (size_t)ell << c->logN;
     const dim3 grid((unsigned)((n_el + 31) / 32), (unsigned)((2 * nb + 31) / 32));
     TIMED("rot_layout", 16.0 * (double)n_el * 2.0 * nb, s,
-          k_rot_to_elements<<<grid, dim3(32, 8), 0, s>>>(rot, R, nb, nq, b, n_el));
+          k_rot_to_elements<<<grid, dim3(32, 8), 0, s>>>(rot, R, nb, nq, b, n_el, c->logN, c->d_prime));
     LAUNCH_CHECK();
     return COPSE_OK;
 }

@@ -263,7 +263,7 @@ copse_status enc_matmul(copse_ctx *c, const copse_evk *evk, const EncModel &E, c
     for (const DCt &x : v)
         if (x.level != (kind == 0 ? E.lvl_D : E.lvl_B)) { set_error("internal: vector at an unexpected level"); return COPSE_EINVAL; }
     const int nb = (int)G.baby.size(), nacc = (int)G.acc.size(), n_mat = (int)G.n_mat;
-    const int nb16 = (nb + 15) / 16 * 16;  // the element-major rotations hold baby steps in chunks of 16
+    const int nb64 = (nb + 63) / 64 * 64;  // the element-major rotations hold baby steps in chunks of 64
     const size_t n_el = (size_t)ell * N, per = 2 * n_el, per3 = 3 * n_el;
     out.assign(nv, std::vector<DCt>(n_mat));
     // encrypted masks of the level products
@@ -296,7 +296,7 @@ copse_status enc_matmul(copse_ctx *c, const copse_evk *evk, const EncModel &E, c
             for (const BsgsGroup::Acc &A : G.acc) n += (int)A.mat == a;
             max_acc = std::max(max_acc, n);
         }
-        const size_t per_ct = ((size_t)nb16 * per + max_acc * (per3 + per)) * sizeof(u64);
+        const size_t per_ct = ((size_t)nb64 * per + max_acc * (per3 + per)) * sizeof(u64);
         const size_t rot_tmp = (size_t)nb * per * sizeof(u64);  // one query ciphertext's rotations
         const size_t budget = (free_b + pool_idle) / 10 * 7;
         while (group > 1 && (size_t)group * per_ct + rot_tmp > budget) group /= 2;
@@ -306,9 +306,9 @@ copse_status enc_matmul(copse_ctx *c, const copse_evk *evk, const EncModel &E, c
         const int ng = std::min(group, nv - g0);
         Scratch sc(s);
         // baby steps: rotations of every query ciphertext of the group (one ModUp each), moved
-        // into the element-major layout [ell N][nb / 16][ng][16][2] of the multiply-accumulate
+        // into the element-major layout [ell N][nb / 64][ng][64][2] of the multiply-accumulate
         u64 *Rb = nullptr, *rot = nullptr;
-        if ((st = sc.get(c, &Rb, (size_t)ng * nb16 * per))) break;
+        if ((st = sc.get(c, &Rb, (size_t)ng * nb64 * per))) break;
         {
             Scratch sr(s);
             if ((st = sr.get(c, &rot, (size_t)nb * per))) break;

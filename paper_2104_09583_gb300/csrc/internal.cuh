@@ -570,8 +570,9 @@ copse_status enc_matmul(copse_ctx *c, const copse_evk *evk, const EncModel &E, c
 // ciphertext b < nq and accumulator x of M,
 //   (acc0, acc1, acc2)[b][x][e] = sum_j (d0 R0, d0 R1 + d1 R0, d1 R1)
 // with d the diagonal (x, j) (c0 from M, c1 regenerated from its stream) and R the rotation
-// j of query ciphertext b, R element-major [ell N][ceil(nb / 16)][nq][16][2] (baby step j in
-// chunk j / 16 at j % 16); acc [nq][nm][3][ell N] (a_ct words per query ciphertext) is
+// j of query ciphertext b, R element-major [ell N][ceil(nb / 64)][nq][64][2] (baby step j in
+// chunk j / 64 at j % 64; each residue v stored as v' + 0x0080808080808080, v' = v or v - q,
+// whichever lies in (-q/2, q/2]); acc [nq][nm][3][ell N] (a_ct words per query ciphertext) is
 // written (not added to).
 copse_status enc_mac_tc(copse_ctx *c, const EncModel::MacMat &M, const u64 *R, int nq, u64 *acc, size_t a_ct,
                         u64 seed, cudaStream_t s);
