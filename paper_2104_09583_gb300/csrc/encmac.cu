@@ -333,6 +333,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_enc_mac_tc(const TcArgs P) {
                 for (int kr = 0; kr < P.n_kr && ok; kr++, na++) {
                     const Run R = run_at(P, kr);
                     const uint32_t a_mn = (uint32_t)R.nk * TC_KS * 16;  // bytes between accumulators' core-matrix rows
+                    // descriptors of the first 16 baby steps; 16 baby steps further is 256 bytes, 16 in
+                    // the descriptor's address field
+                    const uint64_t dA = smem_desc(sh_addr(A0), 128, a_mn), dB = smem_desc(sh_addr(Bst), 128, B_ROW);
                     if (!(ok = bar_wait(&bar[BAR_A_FULL], na & 1, fail, P.status))) break;
                     for (int p = 0; p < nqp && ok; p++, np_c++) {
                         const uint32_t buf = np_c & 1;
@@ -349,10 +352,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_enc_mac_tc(const TcArgs P) {
                             // components (N: column 128 c' + 8 x + a; the second component's core
                             // matrices follow the first's at the same stride), 16 baby steps per MMA
                             const int ns = min(TC_CJ / TC_KS, R.nk - kc * (TC_CJ / TC_KS));
-                            for (int s2 = 0; s2 < ns; s2++)
-                                tc_mma(d, smem_desc(sh_addr(Bst + st * B_STAGE) + (uint32_t)s2 * 256, 128, B_ROW),
-                                       smem_desc(sh_addr(A0) + (uint32_t)(kc * (TC_CJ / TC_KS) + s2) * 256, 128, a_mn),
-                                       (kc | s2) != 0);
+                            const uint64_t b0 = dB + (uint64_t)(st * (B_STAGE >> 4)), a0 = dA + (uint64_t)(kc * (TC_CJ / TC_KS) * 16);
+                            for (int s2 = 0; s2 < ns; s2++) tc_mma(d, b0 + (uint64_t)(16 * s2), a0 + (uint64_t)(16 * s2), (kc | s2) != 0);
                             tc_commit(&bar[BAR_B_EMPTY + st]);
                             issued = true;
                         }
