@@ -34,7 +34,8 @@
 //                warp whole chunks in turn
 //   warps 10-17  epilogue: per pass (8 query ciphertexts) the accumulators back from tensor
 //                memory (tcgen05.ld), the exact outputs rebuilt, reduced and stored in acc;
-//                warps 10-13 take accumulators 0-7, warps 14-17 accumulators 8-15
+//                warps 10-13 take accumulators 0-7, warps 14-17 accumulators 8-15; between
+//                runs they build half of the next run's diagonal digits with the producers
 // Per chunk one M 128 x N 256 x K 16 MMA accumulates [R0 | R1] x [d0 | d1] (all four
 // component products) into one of two tensor-memory buffers of 256 columns, so the epilogue
 // of one pass overlaps the products of the next.
@@ -54,12 +55,14 @@ constexpr int TC_QP = 8;          // query ciphertexts per pass: 8 x 2 component
 constexpr int TC_KR = 256;        // baby steps per run: exact f32 partial sums
 constexpr int TC_KS = 16;         // baby steps per MMA (K of kind::f16)
 constexpr int TC_CJ = 64;         // baby steps per chunk (4 MMAs per operand stage)
-constexpr int TC_NB = 3;          // operand stages of the rotations' digits
-constexpr int TC_NR = 6;          // raw stages of the rotations
+constexpr int TC_NB = 4;          // operand stages of the rotations' digits
+constexpr int TC_NR = 4;          // raw stages of the rotations
 constexpr int TC_PROD_WARPS = 8, TC_EPI_WARPS = 8;
-// Every producer warp converts a part of every chunk, so each waiter meets every phase of the
-// stage barriers in order (the waits test a phase parity, which is sound only while no waiter
-// runs two phases ahead of a barrier).
+// The producer warps form two groups of four; group g converts the chunks with index g modulo 2
+// (a quarter of each per warp).  The barrier waits test a phase parity, which is sound only
+// while no waiter runs two phases ahead of a barrier: with the stage counts even, a stage is
+// only ever used by one group, whose warps meet every phase of it in order.
+constexpr int TC_GROUPS = 2, TC_GROUP_WARPS = TC_PROD_WARPS / TC_GROUPS;
 constexpr int TC_THREADS = 32 * (2 + TC_PROD_WARPS + TC_EPI_WARPS);  // 576
 constexpr int TC_TMEM_COLS = 512;
 constexpr unsigned long long TC_WAIT_NS = 2000000000ull;  // 2 s per wait
@@ -75,7 +78,8 @@ constexpr int BAR_RAW_FULL = 0, BAR_RAW_EMPTY = TC_NR, BAR_B_FULL = 2 * TC_NR, B
               BAR_T_EMPTY = BAR_T_FULL + 2, BAR_DRAIN = BAR_T_EMPTY + 2, N_BAR = BAR_DRAIN + 1;
 constexpr uint32_t OFF_A0 = 0, OFF_B = 2 * A_SET, OFF_RAW = OFF_B + TC_NB * B_STAGE, OFF_BAR = OFF_RAW + TC_NR * RAW_STAGE,
                    OFF_MISC = OFF_BAR + N_BAR * 8, SMEM_TC = OFF_MISC + 16;
-static_assert(TC_QP * TC_CJ == 2 * 32 * TC_PROD_WARPS, "two (query, baby step) pairs per producer lane and chunk");
+static_assert(TC_QP * TC_CJ == 4 * 32 * TC_GROUP_WARPS, "four (query, baby step) pairs per lane of a group's warps and chunk");
+static_assert(TC_NB % TC_GROUPS == 0 && TC_NR % TC_GROUPS == 0, "a stage belongs to one group");
 static_assert(TC_KR % TC_CJ == 0, "runs are whole chunks");
 static_assert(SMEM_TC <= 227 * 1024, "shared memory");
 
@@ -303,13 +307,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_enc_mac_tc(const TcArgs P) {
     if (tid == 32) {
         for (int i = 0; i < TC_NR; i++) {
             bar_init(&bar[BAR_RAW_FULL + i], 1);
-            bar_init(&bar[BAR_RAW_EMPTY + i], TC_PROD_WARPS);
+            bar_init(&bar[BAR_RAW_EMPTY + i], TC_GROUP_WARPS);
         }
         for (int i = 0; i < TC_NB; i++) {
-            bar_init(&bar[BAR_B_FULL + i], TC_PROD_WARPS);
+            bar_init(&bar[BAR_B_FULL + i], TC_GROUP_WARPS);
             bar_init(&bar[BAR_B_EMPTY + i], 1);
         }
-        bar_init(&bar[BAR_A_FULL], TC_PROD_WARPS);
+        bar_init(&bar[BAR_A_FULL], TC_PROD_WARPS + TC_EPI_WARPS);
         bar_init(&bar[BAR_A_EMPTY], 1);
         for (int i = 0; i < 2; i++) {
             bar_init(&bar[BAR_T_FULL + i], 1);
@@ -323,6 +327,52 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_enc_mac_tc(const TcArgs P) {
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tslot;
+
+    // The diagonals' digits of run (it, kr), by the producer and epilogue warps together (thread
+    // t = tid - 64 of 512): entries 2 (t + 512 k) and the next, k < 4 (entry x nj16 + j for
+    // accumulator x, baby step j), c0 read from L2 (where the loader prefetched it), the mask
+    // regenerated from its seed; the 16 bytes of accumulator x at baby step j are row j % 8 of
+    // core matrix (x, j / 8), the second component's rows following the first's.  Waits until
+    // the previous run's products are done with the space (na = runs built so far).
+    constexpr int AB_THREADS = 32 * (TC_PROD_WARPS + TC_EPI_WARPS), AB_PAIRS = TC_MX * TC_KR / (2 * AB_THREADS);
+    auto build_a = [&](size_t it, int kr, uint32_t na) -> bool {
+        const int t = tid - 64;
+        const Item I = item_at(P, it, n_el);
+        const Run R = run_at(P, kr);
+        const int nj16 = R.nk * TC_KS, r = (int)(I.e >> P.logN);
+        const uint32_t a_mn = (uint32_t)nj16 * 16, pos = (uint32_t)(I.e & nmask);
+        const PrimeDev pd = P.pr[r];
+        uint8_t *A1 = A0 + TC_MX * a_mn;
+        ulonglong2 cw[AB_PAIRS];
+#pragma unroll
+        for (int k = 0; k < AB_PAIRS; k++) {
+            const int i = 2 * (t + k * AB_THREADS), x = i / nj16, j = i - x * nj16;
+            cw[k] = make_ulonglong2(0, 0);
+            if (i < TC_MX * nj16 && x < I.nx) cw[k] = *(const ulonglong2 *)(P.mac + (I.e * P.nm + I.x0 + x) * P.nb16 + R.j0 + j);
+        }
+        if (na > 0 && !warp_wait(&bar[BAR_A_EMPTY], (na - 1) & 1, fail, P.status)) return false;
+#pragma unroll
+        for (int k = 0; k < AB_PAIRS; k++) {
+            const int i = 2 * (t + k * AB_THREADS), x = i / nj16, j = i - x * nj16;
+            if (i >= TC_MX * nj16) continue;
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const uint32_t id = (x < I.nx && j + h < R.nj) ? __ldg(P.idx + (size_t)(I.x0 + x) * P.nb + R.j0 + j + h) : ~0u;
+                u64 d0 = 0, d1 = 0;
+                if (id != ~0u) {
+                    d0 = h ? cw[k].y : cw[k].x;
+                    d1 = seeded_mask(P.seed, MODEL_STREAM + 2ull * id, r, pos, P.logN, pd);
+                }
+                const uint32_t off = (uint32_t)x * a_mn + (uint32_t)((j + h) >> 3) * 128 + (uint32_t)((j + h) & 7) * 16;
+                *(uint4 *)(A0 + off) = digits8(d0, pd.q);
+                *(uint4 *)(A1 + off) = digits8(d1, pd.q);
+            }
+        }
+        fence_async_smem();
+        __syncwarp();
+        if (lane == 0) bar_arrive(&bar[BAR_A_FULL]);
+        return true;
+    };
 
     if (warp == 0) {
         // ---------------------------------------------------------------- MMA issue
@@ -411,11 +461,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_enc_mac_tc(const TcArgs P) {
         }
     } else if (warp < 2 + TC_PROD_WARPS) {
         // ---------------------------------------------------------------- producers
-        // Thread pt builds the digits of the (accumulator, baby step) pairs 2 (pt + 256 k) and the
-        // next one of each run (c0 read from L2, where the loader prefetched it), and converts the
-        // rotations of pairs pt and pt + 256 of every chunk (the words come centred and biased,
-        // v' + 0x0080808080808080, from the rotations' element-major layout).
-        const int pt = tid - 64;
+        // The producers build their part of each run's diagonal digits (build_a) first.  Their group
+        // (pt / 128) converts every other chunk, the thread pairs gt + 128 u, u < 4, gt = pt % 128
+        // (the words come centred and biased, v' + 0x0080808080808080, from the rotations'
+        // element-major layout).
+        const int pt = tid - 64, grp = pt / (TC_GROUP_WARPS * 32), gt = pt % (TC_GROUP_WARPS * 32);
         uint32_t nb_c = 0, nr_c = 0, na = 0;
         bool ok = true;
         for (size_t it = blockIdx.x; it < n_items && ok; it += gridDim.x) {
@@ -425,46 +475,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_enc_mac_tc(const TcArgs P) {
             const uint32_t pos = (uint32_t)(I.e & nmask);
             for (int kr = 0; kr < P.n_kr && ok; kr++, na++) {
                 const Run R = run_at(P, kr);
-                const int nj16 = R.nk * TC_KS;
-                const uint32_t a_mn = (uint32_t)nj16 * 16;
-                uint8_t *A1 = A0 + TC_MX * a_mn;  // the second component's rows continue the first's
-                // the c0 words of this thread's pairs, loaded before the wait for the digits' space
-                ulonglong2 cw[TC_MX * TC_KR / (2 * TC_PROD_WARPS * 32)];
-#pragma unroll
-                for (int k = 0; k < TC_MX * TC_KR / (2 * TC_PROD_WARPS * 32); k++) {
-                    const int i = 2 * pt + k * 2 * TC_PROD_WARPS * 32, x = i / nj16, j = i - x * nj16;
-                    cw[k] = make_ulonglong2(0, 0);
-                    if (i < TC_MX * nj16 && x < I.nx)
-                        cw[k] = *(const ulonglong2 *)(P.mac + (I.e * P.nm + I.x0 + x) * P.nb16 + R.j0 + j);
-                }
-                // the diagonals' digits, once the previous run's products are done with them: the 16
-                // bytes of accumulator x at baby step j are row j % 8 of core matrix (x, j / 8)
-                if (na > 0 && !(ok = warp_wait(&bar[BAR_A_EMPTY], (na - 1) & 1, fail, P.status))) break;
-#pragma unroll
-                for (int k = 0; k < TC_MX * TC_KR / (2 * TC_PROD_WARPS * 32); k++) {
-                    const int i = 2 * pt + k * 2 * TC_PROD_WARPS * 32, x = i / nj16, j = i - x * nj16;
-                    if (i >= TC_MX * nj16) continue;
-#pragma unroll
-                    for (int h = 0; h < 2; h++) {
-                        const uint32_t id =
-                            (x < I.nx && j + h < R.nj) ? __ldg(P.idx + (size_t)(I.x0 + x) * P.nb + R.j0 + j + h) : ~0u;
-                        u64 d0 = 0, d1 = 0;
-                        if (id != ~0u) {
-                            d0 = h ? cw[k].y : cw[k].x;
-                            d1 = seeded_mask(P.seed, MODEL_STREAM + 2ull * id, r, pos, P.logN, pd);
-                        }
-                        const uint32_t off =
-                            (uint32_t)x * a_mn + (uint32_t)((j + h) >> 3) * 128 + (uint32_t)((j + h) & 7) * 16;
-                        *(uint4 *)(A0 + off) = digits8(d0, pd.q);
-                        *(uint4 *)(A1 + off) = digits8(d1, pd.q);
-                    }
-                }
-                fence_async_smem();
-                __syncwarp();
-                if (lane == 0) bar_arrive(&bar[BAR_A_FULL]);
+                if (!(ok = build_a(it, kr, na))) break;
                 // the rotations' digits, chunk by chunk
                 for (int p = 0; p < nqp && ok; p++)
                     for (int kc = 0; kc < R.ncr; kc++, nb_c++, nr_c++) {
+                        if ((int)(nb_c % TC_GROUPS) != grp) continue;
                         const int st = (int)(nb_c % TC_NB), rs = (int)(nr_c % TC_NR);
                         if (nb_c >= TC_NB &&
                             !(ok = warp_wait(&bar[BAR_B_EMPTY + st], ((nb_c / TC_NB) - 1) & 1, fail, P.status)))
@@ -473,8 +488,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_enc_mac_tc(const TcArgs P) {
                         const uint8_t *raw = Raw + rs * RAW_STAGE;
                         uint8_t *Bs = Bst + st * B_STAGE;
 #pragma unroll
-                        for (int u = 0; u < 2; u++) {
-                            const int pr = pt + TC_PROD_WARPS * 32 * u, q = pr >> 6, j = pr & 63;
+                        for (int u = 0; u < 4; u++) {
+                            const int pr = gt + TC_GROUP_WARPS * 32 * u, q = pr >> 6, j = pr & 63;
                             ulonglong2 v = make_ulonglong2(DIGIT_BIAS, DIGIT_BIAS);  // digits of zero
                             if (p * TC_QP + q < P.nq && kc * TC_CJ + j < R.nj) v = *(const ulonglong2 *)(raw + pr * 16);
                             uint8_t *B = Bs + (j >> 3) * 128 + (j & 7) * 16;
@@ -498,12 +513,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_enc_mac_tc(const TcArgs P) {
         const int m = 32 * (warp & 3) + lane, b = m & 7, cq = (m >> 3) & 1, qq = m >> 4;
         const int xh = warp >= 2 + TC_PROD_WARPS + 4 ? 8 : 0;
         const uint32_t trow = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
-        uint32_t np_c = 0;
+        uint32_t np_c = 0, na = 0;
         bool ok = true;
+        // the epilogue warps build their part of each run's diagonal digits too: the first run's
+        // before their first pass, each next one after their last pass of the run before
+        if ((size_t)blockIdx.x < n_items) ok = build_a(blockIdx.x, 0, na++);
         for (size_t it = blockIdx.x; it < n_items && ok; it += gridDim.x) {
             const Item I = item_at(P, it, n_el);
             const PrimeDev pd = P.pr[(int)(I.e >> P.logN)];
-            for (int kr = 0; kr < P.n_kr && ok; kr++)
+            for (int kr = 0; kr < P.n_kr && ok; kr++) {
                 for (int p = 0; p < nqp && ok; p++, np_c++) {
                     const uint32_t buf = np_c & 1;
                     if (!(ok = warp_wait(&bar[BAR_T_FULL + buf], (np_c >> 1) & 1, fail, P.status))) break;
@@ -571,6 +589,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_enc_mac_tc(const TcArgs P) {
                     __syncwarp();
                     if (lane == 0) bar_arrive(&bar[BAR_T_EMPTY + buf]);
                 }
+                if (!ok) break;
+                if (kr + 1 < P.n_kr)
+                    ok = build_a(it, kr + 1, na++);
+                else if (it + gridDim.x < n_items)
+                    ok = build_a(it + gridDim.x, 0, na++);
+            }
         }
     }
     tc_fence_before();
