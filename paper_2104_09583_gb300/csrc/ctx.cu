@@ -270,6 +270,30 @@ static copse_status build_tables(copse_ctx *c) {
             mdd_Binv[(size_t)ell * L + i] = mk_shoup(h_inv(B, qi), qi);
         }
     }
+    // Montgomery forms of the conversion factors and of the negated corrections
+    auto mont = [&](u64 x, int g) { return h_mul(x % c->primes[g], c->hprime[g].r64, c->primes[g]); };
+    auto neg = [&](u64 x, int g) { const u64 q = c->primes[g], r = x % q; return r ? q - r : 0; };
+    std::vector<u64> modup_hat_m(modup_hat.size()), modup_negq_m(modup_qhat.size());
+    for (int ell = 1; ell <= L; ell++)
+        for (int i = 0; i < ell; i++)
+            for (int g = 0; g < NP; g++) {
+                const size_t ti = ((size_t)ell * L + i) * NP + g;
+                modup_hat_m[ti] = mont(modup_hat[ti].w, g);
+                modup_negq_m[ti] = mont(neg(modup_qhat[ti], g), g);
+            }
+    std::vector<u64> md_hat_m(md_hat.size()), md_negP_m(L);
+    for (int k = 0; k < A; k++)
+        for (int i = 0; i < L; i++) md_hat_m[(size_t)k * L + i] = mont(md_hat[(size_t)k * L + i].w, i);
+    for (int i = 0; i < L; i++) md_negP_m[i] = mont(neg(md_P[i], i), i);
+    std::vector<u64> mdd_hat_m(mdd_hat.size()), mdd_negB_m(mdd_B.size());
+    for (size_t x = 0; x < mdd_hat.size(); x++) mdd_hat_m[x] = mont(mdd_hat[x].w, (int)(x % L));
+    for (size_t x = 0; x < mdd_B.size(); x++) mdd_negB_m[x] = mont(neg(mdd_B[x], (int)(x % L)), (int)(x % L));
+    STATUS_TRY(upload(c, &c->ks.modup_hat_m, modup_hat_m));
+    STATUS_TRY(upload(c, &c->ks.modup_negq_m, modup_negq_m));
+    STATUS_TRY(upload(c, &c->ks.md_hat_m, md_hat_m));
+    STATUS_TRY(upload(c, &c->ks.md_negP_m, md_negP_m));
+    STATUS_TRY(upload(c, &c->ks.mdd_hat_m, mdd_hat_m));
+    STATUS_TRY(upload(c, &c->ks.mdd_negB_m, mdd_negB_m));
     // first-step factors times N^-1: the scales of the inverse transforms feeding the conversions
     auto scaled = [&](const Shoup &f, int g) { return mk_shoup(h_mul(f.w, c->hprime[g].ninv, c->primes[g]), c->primes[g]); };
     std::vector<Shoup> mu_scale(modup_inv.size()), md_scale(A), ms_scale(L + 1), mdd_scale(mdd_inv.size());

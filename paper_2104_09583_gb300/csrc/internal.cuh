@@ -251,6 +251,11 @@ struct KsTables {
     Shoup *mdd_hat;     // [(L+1) * (alpha+1) * L]
     u64 *mdd_B;         // [(L+1) * L]
     Shoup *mdd_Binv;    // [(L+1) * L]
+    // The conversion factors in Montgomery form (x 2^64 mod the target prime), indexed like
+    // the factors above, for the fused transforms' loads: a conversion sums its products
+    // exactly in 128 bits, adds the negated correction of every centred negative digit
+    // (modup_negq_m = -modup_qhat, md_negP_m = -P, mdd_negB_m = -B) and reduces once.
+    u64 *modup_hat_m, *modup_negq_m, *md_hat_m, *md_negP_m, *mdd_hat_m, *mdd_negB_m;
     // gadget factor of key-switching keys: P mod q_i (i < L)
 };
 

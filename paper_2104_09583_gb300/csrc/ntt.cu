@@ -579,6 +579,187 @@ struct MddIO {
     __device__ __forceinline__ void skip(int, int, int, int) const {}
 };
 
+// ---------------------------------------------------------------- a thread's coefficients of a tile
+// A thread of the forward kernels loads K coefficients n0 + i dn (i < K) of one residue
+// polynomial and stores K results k0 + i dk.  By default each goes through the functor's
+// load / store; the fused conversions and finishes below take all K together, their
+// per-tile constants loaded once and every global load of a step in flight at once.
+template <int K, class IO>
+__device__ __forceinline__ void load_n(const IO &io, int p, int r, int g, size_t n0, size_t dn, u64 (&v)[K]) {
+#pragma unroll
+    for (int i = 0; i < K; i++) v[i] = io.load(p, r, g, n0 + (size_t)i * dn);
+}
+template <int K, class IO>
+__device__ __forceinline__ void store_n(const IO &io, int p, int r, int g, size_t k0, size_t dk, const u64 (&v)[K]) {
+#pragma unroll
+    for (int i = 0; i < K; i++) io.store(p, r, g, k0 + (size_t)i * dk, v[i]);
+}
+
+// A base conversion sum_k [y_k]_centred * f_k mod q as one lazy sum: with f_k in Montgomery form
+// F_k = f_k 2^64 mod q and C = (-c) 2^64 mod q for the correction c of a centred negative digit,
+// S = sum_k (y_k F_k + [y_k > (b_k - 1) / 2] C) is summed exactly in 128 bits and reduced once,
+// S 2^-64 mod q (Montgomery).  S < m 2^(2 bits) + m q < q 2^64 for m < 2^(63 - bits) terms of
+// residues below 2^bits (bits <= 55: any m up to 256).
+__device__ __forceinline__ void add128(Acc128 &a, u64 x) {
+    a.lo += x;
+    a.hi += a.lo < x;
+}
+template <int K>
+__device__ __forceinline__ void conv_term(Acc128 (&s)[K], const u64 (&y)[K], u64 F, u64 C, u64 half) {
+#pragma unroll
+    for (int i = 0; i < K; i++) {
+        mac128(s[i], y[i], F);
+        add128(s[i], y[i] > half ? C : 0);
+    }
+}
+
+template <int K>
+__device__ __forceinline__ void load_n(const MuIO &io, int p, int, int g, size_t n0, size_t dn, u64 (&v)[K]) {
+    const int item = p / io.nd, j = p - item * io.nd;
+    const int lo = j * io.alpha, hi = min(lo + io.alpha, io.ell);
+    const u64 *x = io.xc + (size_t)item * io.ell * ((size_t)1 << io.logN) + n0;
+    Acc128 s[K];
+#pragma unroll
+    for (int i = 0; i < K; i++) s[i] = Acc128{0, 0};
+    for (int i = lo; i < hi; i++) {
+        const size_t ti = ((size_t)io.ell * io.L + i) * io.NP + g;
+        const u64 *xi = x + ((size_t)i << io.logN);
+        u64 y[K];
+#pragma unroll
+        for (int k = 0; k < K; k++) y[k] = xi[(size_t)k * dn];  // already times modup_inv (the inverse transform's scale)
+        conv_term(s, y, io.T.modup_hat_m[ti], io.T.modup_negq_m[ti], (io.pr[i].q - 1) / 2);
+    }
+    const PrimeDev P = io.pr[g];
+#pragma unroll
+    for (int i = 0; i < K; i++) v[i] = mont_reduce(s[i], P);
+}
+
+template <int K>
+__device__ __forceinline__ void load_n(const MdIO &io, int p, int r, int, size_t n0, size_t dn, u64 (&v)[K]) {
+    const u64 *up = io.f.U + (size_t)p * io.f.ustride + ((size_t)io.f.ell << io.logN) + n0;
+    const u64 C = io.T.md_negP_m[r];
+    Acc128 s[K];
+#pragma unroll
+    for (int i = 0; i < K; i++) s[i] = Acc128{0, 0};
+    for (int k = 0; k < io.alpha; k++) {
+        const u64 *yk = up + ((size_t)k << io.logN);
+        u64 y[K];
+#pragma unroll
+        for (int i = 0; i < K; i++) y[i] = yk[(size_t)i * dn];  // already times md_inv[k] (the inverse transform's scale)
+        conv_term(s, y, io.T.md_hat_m[(size_t)k * io.L + r], C, (io.pr[io.L + k].q - 1) / 2);
+    }
+    const PrimeDev P = io.pr[r];
+#pragma unroll
+    for (int i = 0; i < K; i++) v[i] = mont_reduce(s[i], P);
+}
+
+template <int K>
+__device__ __forceinline__ void load_n(const MddIO &io, int p, int r, int, size_t n0, size_t dn, u64 (&v)[K]) {
+    const int ell = io.f.ell, nb = io.alpha + 1;
+    const u64 *up = io.f.U + (size_t)p * io.f.ustride + ((size_t)(ell - 1) << io.logN) + n0;
+    const u64 C = io.T.mdd_negB_m[(size_t)ell * io.L + r];
+    Acc128 s[K];
+#pragma unroll
+    for (int i = 0; i < K; i++) s[i] = Acc128{0, 0};
+    for (int k = 0; k < nb; k++) {
+        const u64 bk = k == 0 ? io.pr[ell - 1].q : io.pr[io.L + k - 1].q;
+        const u64 *yk = up + ((size_t)k << io.logN);
+        u64 y[K];
+#pragma unroll
+        for (int i = 0; i < K; i++) y[i] = yk[(size_t)i * dn];  // scaled by the inverse transform
+        conv_term(s, y, io.T.mdd_hat_m[((size_t)ell * nb + k) * io.L + r], C, (bk - 1) / 2);
+    }
+    const PrimeDev P = io.pr[r];
+#pragma unroll
+    for (int i = 0; i < K; i++) v[i] = mont_reduce(s[i], P);
+}
+
+template <int K>
+__device__ __forceinline__ void load_n(const MsIO &io, int p, int r, int, size_t n0, size_t dn, u64 (&v)[K]) {
+    const u64 ql = io.pr[io.f.ell - 1].q, qr = io.pr[r].q, half = (ql - 1) / 2;
+    const u64 *w = io.f.last + ((size_t)p << io.logN) + n0;  // already times t^-1
+#pragma unroll
+    for (int i = 0; i < K; i++) {
+        const u64 x = w[(size_t)i * dn];
+        v[i] = x > half ? qr - (ql - x) : x;  // |centred x| < q_{ell-1} / 2 < q_r
+    }
+}
+
+// the finishes of ms_store, md_store and mdd_store for K positions of one residue
+template <int K>
+__device__ __forceinline__ void store_n(const MsIO &io, int p, int r, int, size_t k0, size_t dk, const u64 (&v)[K]) {
+    const MsFuse &f = io.f;
+    const u64 q = io.pr[r].q;
+    const Shoup tm{io.pr[r].t_mod, io.pr[r].t_mod_sh}, qinv = io.T.ms_qinv[(size_t)f.ell * io.L + r];
+    const u64 *x = (f.xp[0] ? f.xp[p] : f.x + (size_t)p * f.ell * ((size_t)1 << io.logN)) + ((size_t)r << io.logN);
+    u64 *o = (f.outp[0] ? f.outp[p] : f.out + (size_t)p * (f.ell - 1) * ((size_t)1 << io.logN)) + ((size_t)r << io.logN);
+    u64 xv[K];
+#pragma unroll
+    for (int i = 0; i < K; i++) xv[i] = x[k0 + (size_t)i * dk];
+#pragma unroll
+    for (int i = 0; i < K; i++) o[k0 + (size_t)i * dk] = mul_shoup(sub_mod(xv[i], mul_shoup(v[i], tm, q), q), qinv, q);
+}
+
+template <int K>
+__device__ __forceinline__ void store_n(const MdIO &io, int p, int r, int, size_t k0, size_t dk, const u64 (&v)[K]) {
+    const MdFuse &f = io.f;
+    const int job = p >> 1, c = p & 1;
+    const u64 q = io.pr[r].q;
+    const Shoup tm{io.pr[r].t_mod, io.pr[r].t_mod_sh}, pinv = io.T.md_Pinv[r];
+    const u64 *U = f.U + (size_t)p * f.ustride + ((size_t)r << io.logN);
+    u64 res[K];
+#pragma unroll
+    for (int i = 0; i < K; i++) res[i] = U[k0 + (size_t)i * dk];
+#pragma unroll
+    for (int i = 0; i < K; i++) res[i] = mul_shoup(sub_mod(res[i], mul_shoup(v[i], tm, q), q), pinv, q);
+    if (c < f.add_comps && f.add[job]) {
+        const u64 *a = f.add[job] + (size_t)c * f.acomp + ((size_t)r << io.logN);
+        const u64 gal = f.gal[job];
+        u64 av[K];
+#pragma unroll
+        for (int i = 0; i < K; i++) {
+            const size_t k = k0 + (size_t)i * dk;
+            av[i] = a[(c == 0 && gal != 1) ? (size_t)galois_src((uint32_t)k, gal, io.logN) : k];
+        }
+#pragma unroll
+        for (int i = 0; i < K; i++) res[i] = add_mod(res[i], av[i], q);
+    }
+    u64 *out = f.out[job] + (size_t)c * f.ocomp + ((size_t)r << io.logN);
+#pragma unroll
+    for (int i = 0; i < K; i++) out[k0 + (size_t)i * dk] = res[i];
+}
+
+template <int K>
+__device__ __forceinline__ void store_n(const MddIO &io, int p, int r, int, size_t k0, size_t dk, const u64 (&v)[K]) {
+    const MddFuse &f = io.f;
+    const u64 q = io.pr[r].q;
+    const size_t n = (size_t)1 << io.logN;
+    const Shoup tm{io.pr[r].t_mod, io.pr[r].t_mod_sh}, binv = io.T.mdd_Binv[(size_t)f.ell * io.L + r];
+    const u64 *U = f.U + (size_t)p * f.ustride + ((size_t)r << io.logN);
+    u64 res[K];
+#pragma unroll
+    for (int i = 0; i < K; i++) res[i] = U[k0 + (size_t)i * dk];
+#pragma unroll
+    for (int i = 0; i < K; i++) res[i] = mul_shoup(sub_mod(res[i], mul_shoup(v[i], tm, q), q), binv, q);
+    u64 *out;
+    if (!f.outp[0]) {
+        out = f.out + ((size_t)p * (f.ell - 1) + r) * n;
+    } else {
+        const size_t at = ((size_t)(p & 1) * (f.ell - 1) + r) * n;
+        const u64 *add = f.addp[p >> 1];
+        if (add) {
+            u64 av[K];
+#pragma unroll
+            for (int i = 0; i < K; i++) av[i] = add[at + k0 + (size_t)i * dk];
+#pragma unroll
+            for (int i = 0; i < K; i++) res[i] = add_mod(res[i], av[i], q);
+        }
+        out = f.outp[p >> 1] + at;
+    }
+#pragma unroll
+    for (int i = 0; i < K; i++) out[k0 + (size_t)i * dk] = res[i];
+}
+
 template <int CL, class IO>
 __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT2)
     k_ntt_fwd_cluster(NttBatch b, const PrimeDev *__restrict__ primes, const u64 *__restrict__ tw,
@@ -605,8 +786,15 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT2)
     // column-stage twiddles, all loads of a thread in flight together
     const ulonglong2 *st = stg + ((size_t)g * CL + rank) * TILE;
     const int nst = TILE - (1 << lr);
+    {
+        // coefficient e + i NT2 of the tile is n0 + i dn (NT2 is a multiple of the tile's width C)
+        const int e = threadIdx.x;
+        u64 v[TILE / NT2];
+        load_n(io, p, r, g, (size_t)(rank << lc) + ((size_t)(e >> lc) << lb) + (e & (C - 1)), (size_t)(NT2 >> lc) << lb, v);
+#pragma unroll
+        for (int i = 0; i < TILE / NT2; i++) S.colt[e + i * NT2] = v[i];
+    }
     for (int e = threadIdx.x; e < TILE; e += NT2) {
-        S.colt[e] = io.load(p, r, g, (size_t)(rank << lc) + ((size_t)(e >> lc) << lb) + (e & (C - 1)));
         if (e < nst) {
             const ulonglong2 v = st[e];
             S.stw[e] = v.x;
@@ -630,8 +818,11 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT2)
     cl.sync();
     tile_fwd<false>(S.rowt, S.stw, S.stwp, lb, q, q2, [&](int gg, int i) { return (gg << lb) + i; },
                     [&](int u, int gg, int il) { return ((1 << lr) * ((1 << u) - 1)) + (gg << u) + il; });
-    for (int e = threadIdx.x; e < TILE; e += NT2) {
-        io.store(p, r, g, ((size_t)row0 << lb) + e, fwd_reduce(S.rowt[e], q, one_sh));
+    {
+        u64 v[TILE / NT2];
+#pragma unroll
+        for (int i = 0; i < TILE / NT2; i++) v[i] = fwd_reduce(S.rowt[threadIdx.x + i * NT2], q, one_sh);
+        store_n(io, p, r, g, ((size_t)row0 << lb) + threadIdx.x, NT2, v);
     }
 }
 
@@ -803,12 +994,17 @@ __global__ void __launch_bounds__(NT2) k_ntt_fwd_cols_io(NttBatch b, const Prime
     const int g = ntt_prime(b, r, L);
     const u64 q = primes[g].q, q2 = 2 * q;
     const u64 *W = tw + (size_t)g * N, *Wp = tw_sh + (size_t)g * N;
-    for (int e = threadIdx.x; e < TILE; e += NT2) {
-        sm[e] = io.load(p, r, g, ((size_t)(e >> lc) << lb) + (tile << lc) + (e & (C - 1)));
-        if (e < (1 << a)) {
-            stw[e] = W[e];
-            stwp[e] = Wp[e];
-        }
+    {
+        // coefficient e + i NT2 of the tile is n0 + i dn (NT2 is a multiple of the tile's width C)
+        const int e = threadIdx.x;
+        u64 v[TILE / NT2];
+        load_n(io, p, r, g, ((size_t)(e >> lc) << lb) + (tile << lc) + (e & (C - 1)), (size_t)(NT2 >> lc) << lb, v);
+#pragma unroll
+        for (int i = 0; i < TILE / NT2; i++) sm[e + i * NT2] = v[i];
+    }
+    for (int e = threadIdx.x; e < (1 << a); e += NT2) {
+        stw[e] = W[e];
+        stwp[e] = Wp[e];
     }
     __syncthreads();
     tile_fwd<true>(sm, stw, stwp, a, q, q2, [&](int gg, int i) { return (i << lc) + gg; },
@@ -844,7 +1040,10 @@ __global__ void __launch_bounds__(NT2) k_ntt_fwd_rows_io(NttBatch b, const Prime
     tile_fwd<false>(sm, stw, stwp, lb, q, q2, [&](int gg, int i) { return (gg << lb) + i; },
                     [&](int u, int gg, int il) { return ((1 << lr) * ((1 << u) - 1)) + (gg << u) + il; });
     const u64 one_sh = primes[g].one_sh;
-    for (int e = threadIdx.x; e < TILE; e += NT2) io.store(p, r, g, ((size_t)row0 << lb) + e, fwd_reduce(sm[e], q, one_sh));
+    u64 v[TILE / NT2];
+#pragma unroll
+    for (int i = 0; i < TILE / NT2; i++) v[i] = fwd_reduce(sm[threadIdx.x + i * NT2], q, one_sh);
+    store_n(io, p, r, g, ((size_t)row0 << lb) + threadIdx.x, NT2, v);
 }
 
 template <class IO>
