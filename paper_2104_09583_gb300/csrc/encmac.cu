@@ -29,9 +29,9 @@
 //                ciphertexts x 16 baby steps x 2 components, contiguous) per bulk copy
 //                (cp.async.bulk with transaction-count completion) into a ring of stages
 //   warps 2-9    producers: per item the digits of both components of every diagonal (c0
-//                read element-major, c1 regenerated from its seed) into shared memory; warps
-//                2-4 then convert the rotations' chunks into a ring of operand stages, each
-//                warp whole chunks in turn
+//                read element-major, c1 regenerated from its seed) into shared memory; then,
+//                in two groups of four (warps 2-5, 6-9) taking alternate chunks, they convert
+//                the rotations' raw words into a ring of operand stages
 //   warps 10-17  epilogue: per pass (8 query ciphertexts) the accumulators back from tensor
 //                memory (tcgen05.ld), the exact outputs rebuilt, reduced and stored in acc;
 //                warps 10-13 take accumulators 0-7, warps 14-17 accumulators 8-15; between
@@ -426,12 +426,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_enc_mac_tc(const TcArgs P) {
             for (size_t it = blockIdx.x; it < n_items && ok; it += gridDim.x) {
                 const Item I = item_at(P, it, n_el);
                 if (it + gridDim.x < n_items) {
-                    // the next item's rotations (one contiguous block per element) and c0 rows into
-                    // L2 while this one runs, so that the ring's copies and the digit builds read L2
+                    // the next item's c0 rows and the chunks of its first pass into L2 while this
+                    // one runs (the later chunks stream in through the ring in time; prefetching the
+                    // whole rotation block only doubled its DRAM reads, evicted before use)
                     const Item J = item_at(P, it + gridDim.x, n_el);
-                    const size_t rb = (size_t)P.nc * P.nq * TC_CJ * 2 * 8;
                     const uint8_t *r0 = (const uint8_t *)(P.R + J.e * (size_t)P.nc * P.nq * TC_CJ * 2);
-                    for (size_t o = 0; o < rb; o += 32768) l2_prefetch(r0 + o, (uint32_t)(rb - o < 32768 ? rb - o : 32768));
+                    const uint32_t first = (uint32_t)min(TC_QP, P.nq) * TC_CJ * 2 * 8;
+                    for (int kc = 0; kc < P.nc && kc < TC_KR / TC_CJ; kc++)
+                        l2_prefetch(r0 + (size_t)kc * P.nq * TC_CJ * 2 * 8, first);
                     l2_prefetch(P.mac + (J.e * P.nm + J.x0) * P.nb16, (uint32_t)(J.nx * P.nb16 * 8));
                 }
                 for (int kr = 0; kr < P.n_kr && ok; kr++) {
