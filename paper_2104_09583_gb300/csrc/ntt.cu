@@ -31,7 +31,8 @@ namespace cg = cooperative_groups;
 namespace {
 
 constexpr int TILE = 2048;  // coefficients per CTA in the two-pass kernels
-constexpr int NT2 = 512;    // threads per CTA in the two-pass and cluster kernels
+constexpr int NT2 = 512;    // threads per CTA in the cluster and most two-pass kernels (radix-4 passes: one unit of 4 per thread)
+constexpr int NTT = 256;    // threads per CTA in the forward row passes (radix-8 passes: one unit of 8 per thread)
 
 __device__ __forceinline__ int ntt_prime(const NttBatch &b, int r, int L) {
     return b.fixed >= 0 ? b.fixed : (r < b.ell ? r : L + (r - b.ell));
@@ -161,14 +162,61 @@ __device__ __forceinline__ void split_item(int x, int ls, int nb, int &g, int &j
     }
 }
 
-template <bool SEQ_FAST, class IX, class TWI>
+// One radix-8 pass of the forward transform: stages u, u + 1, u + 2 (half-distances 4 q8, 2 q8,
+// q8 with q8 = 2^(ls - 3 - u)) of every sequence, eight coefficients i0 + m q8 in registers;
+// the butterflies and twiddles are those of three radix-2 stages.
+template <bool SEQ_FAST, int NT, class IX, class TWI>
+__device__ __forceinline__ void pass_fwd8(u64 *sm, const u64 *tw, const u64 *twp, int ls, int u, u64 q, u64 q2, IX ix,
+                                          TWI twi) {
+    const int lt = ls - 1 - u, q8 = 1 << (lt - 2);
+    for (int x = threadIdx.x; x < TILE / 8; x += NT) {
+        int g, jq;
+        split_item<SEQ_FAST>(x, ls, ls - 3, g, jq);
+        const int il = jq >> (lt - 2), jj = jq & (q8 - 1);
+        const int i0 = (il << (lt + 1)) + jj;
+        int a[8];
+        u64 v[8];
+#pragma unroll
+        for (int m = 0; m < 8; m++) {
+            a[m] = ix(g, i0 + m * q8);
+            v[m] = sm[a[m]];
+        }
+        {
+            const int t = twi(u, g, il);
+            const u64 w = tw[t], wp = twp[t];
+#pragma unroll
+            for (int m = 0; m < 4; m++) bfv_fwd(v[m], v[m + 4], w, wp, q, q2);
+        }
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const int t = twi(u + 1, g, 2 * il + h);
+            const u64 w = tw[t], wp = twp[t];
+            bfv_fwd(v[4 * h], v[4 * h + 2], w, wp, q, q2);
+            bfv_fwd(v[4 * h + 1], v[4 * h + 3], w, wp, q, q2);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const int t = twi(u + 2, g, 4 * il + k);
+            bfv_fwd(v[2 * k], v[2 * k + 1], tw[t], twp[t], q, q2);
+        }
+#pragma unroll
+        for (int m = 0; m < 8; m++) sm[a[m]] = v[m];
+    }
+    __syncthreads();
+}
+
+// forward stages 0 .. ls-1 of every sequence: radix-8 passes (R8), then radix-4 pairs of stages,
+// then a radix-2 stage if one is left; NT threads
+template <bool SEQ_FAST, int NT, bool R8, class IX, class TWI>
 __device__ __forceinline__ void tile_fwd(u64 *sm, const u64 *tw, const u64 *twp, int ls, u64 q, u64 q2, IX ix,
                                          TWI twi) {
     int u = 0;
+    if (R8)
+        for (; u + 2 < ls; u += 3) pass_fwd8<SEQ_FAST, NT>(sm, tw, twp, ls, u, q, q2, ix, twi);
 #pragma unroll
     for (; u + 1 < ls; u += 2) {
         const int lt = ls - 1 - u, tt = 1 << lt, h2 = tt >> 1;
-        for (int x = threadIdx.x; x < TILE / 4; x += NT2) {
+        for (int x = threadIdx.x; x < TILE / 4; x += NT) {
             int g, jq;
             split_item<SEQ_FAST>(x, ls, ls - 2, g, jq);
             const int il = jq >> (lt - 1), jj = jq & (h2 - 1);
@@ -189,7 +237,7 @@ __device__ __forceinline__ void tile_fwd(u64 *sm, const u64 *tw, const u64 *twp,
         __syncthreads();
     }
     if (u < ls) {  // last stage, distance 1
-        for (int x = threadIdx.x; x < TILE / 2; x += NT2) {
+        for (int x = threadIdx.x; x < TILE / 2; x += NT) {
             int g, il;
             split_item<SEQ_FAST>(x, ls, ls - 1, g, il);
             const int a0 = ix(g, 2 * il), a1 = ix(g, 2 * il + 1);
@@ -200,15 +248,60 @@ __device__ __forceinline__ void tile_fwd(u64 *sm, const u64 *tw, const u64 *twp,
     }
 }
 
-// inverse stages (distances 1, 2, .., S/2) of every sequence, radix-4 pairs then radix-2
-template <bool SEQ_FAST, class IX, class TWI>
+// One radix-8 pass of the inverse transform: stages u, u + 1, u + 2 (distances 2^u, 2^(u+1),
+// 2^(u+2)), eight coefficients i0 + m 2^u in registers; stage u + k subtracts against 2^(u+k) q.
+template <bool SEQ_FAST, int NT, class IX, class TWI>
+__device__ __forceinline__ void pass_inv8(u64 *sm, const u64 *tw, const u64 *twp, int ls, int u, u64 q, IX ix,
+                                          TWI twi) {
+    const int tt = 1 << u;
+    for (int x = threadIdx.x; x < TILE / 8; x += NT) {
+        int g, jq;
+        split_item<SEQ_FAST>(x, ls, ls - 3, g, jq);
+        const int il = jq >> u, jj = jq & (tt - 1);
+        const int i0 = (il << (u + 3)) + jj;
+        int a[8];
+        u64 v[8];
+#pragma unroll
+        for (int m = 0; m < 8; m++) {
+            a[m] = ix(g, i0 + m * tt);
+            v[m] = sm[a[m]];
+        }
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const int t = twi(u, g, 4 * il + k);
+            bfv_inv_lazy(v[2 * k], v[2 * k + 1], tw[t], twp[t], q, q << u);
+        }
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const int t = twi(u + 1, g, 2 * il + h);
+            const u64 w = tw[t], wp = twp[t];
+            bfv_inv_lazy(v[4 * h], v[4 * h + 2], w, wp, q, q << (u + 1));
+            bfv_inv_lazy(v[4 * h + 1], v[4 * h + 3], w, wp, q, q << (u + 1));
+        }
+        {
+            const int t = twi(u + 2, g, il);
+            const u64 w = tw[t], wp = twp[t];
+#pragma unroll
+            for (int m = 0; m < 4; m++) bfv_inv_lazy(v[m], v[m + 4], w, wp, q, q << (u + 2));
+        }
+#pragma unroll
+        for (int m = 0; m < 8; m++) sm[a[m]] = v[m];
+    }
+    __syncthreads();
+}
+
+// inverse stages (distances 1, 2, .., S/2) of every sequence: radix-8 passes (R8), then radix-4,
+// then radix-2; NT threads
+template <bool SEQ_FAST, int NT, bool R8, class IX, class TWI>
 __device__ __forceinline__ void tile_inv(u64 *sm, const u64 *tw, const u64 *twp, int ls, u64 q, u64 q2, IX ix,
                                          TWI twi) {
     int u = 0;
+    if (R8)
+        for (; u + 2 < ls; u += 3) pass_inv8<SEQ_FAST, NT>(sm, tw, twp, ls, u, q, ix, twi);
 #pragma unroll
     for (; u + 1 < ls; u += 2) {
         const int tt = 1 << u;
-        for (int x = threadIdx.x; x < TILE / 4; x += NT2) {
+        for (int x = threadIdx.x; x < TILE / 4; x += NT) {
             int g, jq;
             split_item<SEQ_FAST>(x, ls, ls - 2, g, jq);
             const int il1 = jq >> u, jj = jq & (tt - 1);
@@ -231,7 +324,7 @@ __device__ __forceinline__ void tile_inv(u64 *sm, const u64 *tw, const u64 *twp,
     }
     if (u < ls) {  // last stage, distance S/2, one group
         const int tt = 1 << u;
-        for (int x = threadIdx.x; x < TILE / 2; x += NT2) {
+        for (int x = threadIdx.x; x < TILE / 2; x += NT) {
             int g, j;
             split_item<SEQ_FAST>(x, ls, ls - 1, g, j);
             const int a0 = ix(g, j), a1 = ix(g, j + tt);
@@ -277,14 +370,14 @@ __global__ void __launch_bounds__(NT2) k_ntt_fwd_cols(NttBatch b, const PrimeDev
         }
     }
     __syncthreads();
-    tile_fwd<true>(sm, stw, stwp, a, t.q, t.q2, [&](int g, int i) { return (i << lc) + g; },
+    tile_fwd<true, NT2, false>(sm, stw, stwp, a, t.q, t.q2, [&](int g, int i) { return (i << lc) + g; },
              [&](int u, int, int il) { return (1 << u) + il; });
     for (int e = threadIdx.x; e < TILE; e += NT2) data[((size_t)(e >> lc) << lb) + (e & (C - 1))] = sm[e];
 }
 
 // Row pass: tile = R consecutive rows of N2 contiguous coefficients; the twiddle
 // of row g, stage u, group il is W[2^(a+u) + ((row0 + g) << u) + il].
-__global__ void __launch_bounds__(NT2) k_ntt_fwd_rows(NttBatch b, const PrimeDev *__restrict__ primes,
+__global__ void __launch_bounds__(NTT, 4) k_ntt_fwd_rows(NttBatch b, const PrimeDev *__restrict__ primes,
                                                       const ulonglong2 *__restrict__ stg, int logN, int L, int a) {
     __shared__ u64 sm[TILE], stw[TILE], stwp[TILE];
     const int N = 1 << logN, lb = logN - a, lr = 11 - lb;
@@ -296,7 +389,7 @@ __global__ void __launch_bounds__(NT2) k_ntt_fwd_rows(NttBatch b, const PrimeDev
     // pre-staged per tile, loaded together with the data
     const ulonglong2 *st = stg + ((size_t)t.g * (N / TILE) + t.tile) * TILE;
     const int nst = TILE - (1 << lr);
-    for (int e = threadIdx.x; e < TILE; e += NT2) {
+    for (int e = threadIdx.x; e < TILE; e += NTT) {
         sm[e] = data[e];
         if (e < nst) {
             const ulonglong2 v = st[e];
@@ -305,9 +398,9 @@ __global__ void __launch_bounds__(NT2) k_ntt_fwd_rows(NttBatch b, const PrimeDev
         }
     }
     __syncthreads();
-    tile_fwd<false>(sm, stw, stwp, lb, t.q, t.q2, [&](int g, int i) { return (g << lb) + i; },
+    tile_fwd<false, NTT, true>(sm, stw, stwp, lb, t.q, t.q2, [&](int g, int i) { return (g << lb) + i; },
              [&](int u, int g, int il) { return ((1 << lr) * ((1 << u) - 1)) + (g << u) + il; });
-    for (int e = threadIdx.x; e < TILE; e += NT2) {
+    for (int e = threadIdx.x; e < TILE; e += NTT) {
         data[e] = fwd_reduce(sm[e], t.q, primes[t.g].one_sh);
     }
 }
@@ -336,7 +429,7 @@ __global__ void __launch_bounds__(NT2) k_ntt_inv_rows(NttBatch b, const PrimeDev
     }
     __syncthreads();
     // offset of stage u: sum_{v<u} R 2^(lb-1-v) = R (2^lb - 2^(lb-u))
-    tile_inv<false>(sm, stw, stwp, lb, t.q, t.q2, [&](int g, int i) { return (g << lb) + i; },
+    tile_inv<false, NT2, false>(sm, stw, stwp, lb, t.q, t.q2, [&](int g, int i) { return (g << lb) + i; },
              [&](int u, int g, int il) {
                  return (1 << lr) * ((1 << lb) - (1 << (lb - u))) + (g << (lb - 1 - u)) + il;
              });
@@ -363,7 +456,7 @@ __global__ void __launch_bounds__(NT2) k_ntt_inv_cols(NttBatch b, const PrimeDev
         }
     }
     __syncthreads();
-    tile_inv<true>(sm, stw, stwp, a, t.q, t.q2, [&](int g, int i) { return (i << lc) + g; },
+    tile_inv<true, NT2, false>(sm, stw, stwp, a, t.q, t.q2, [&](int g, int i) { return (i << lc) + g; },
              [&](int u, int, int il) { return (1 << (a - 1 - u)) + il; });
     const Shoup sc = b.scale ? b.scale[t.r - b.r0] : Shoup{P.ninv, P.ninv_sh};
     for (int e = threadIdx.x; e < TILE; e += NT2)
@@ -807,7 +900,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT2)
     }
     const int row0 = rank << lr;
     __syncthreads();
-    tile_fwd<true>(S.colt, S.ctw, S.ctwp, a, q, q2, [&](int gg, int i) { return (i << lc) + gg; },
+    tile_fwd<true, NT2, false>(S.colt, S.ctw, S.ctwp, a, q, q2, [&](int gg, int i) { return (i << lc) + gg; },
                    [&](int u, int, int il) { return (1 << u) + il; });
     cl.sync();
     for (int e = threadIdx.x; e < TILE; e += NT2) {
@@ -816,7 +909,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT2)
         S.rowt[e] = rc[(row << lc) + (col & (C - 1))];
     }
     cl.sync();
-    tile_fwd<false>(S.rowt, S.stw, S.stwp, lb, q, q2, [&](int gg, int i) { return (gg << lb) + i; },
+    tile_fwd<false, NT2, false>(S.rowt, S.stw, S.stwp, lb, q, q2, [&](int gg, int i) { return (gg << lb) + i; },
                     [&](int u, int gg, int il) { return ((1 << lr) * ((1 << u) - 1)) + (gg << u) + il; });
     {
         u64 v[TILE / NT2];
@@ -860,7 +953,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT2)
         }
     }
     __syncthreads();
-    tile_inv<false>(S.rowt, S.stw, S.stwp, lb, q, q2, [&](int gg, int i) { return (gg << lb) + i; },
+    tile_inv<false, NT2, false>(S.rowt, S.stw, S.stwp, lb, q, q2, [&](int gg, int i) { return (gg << lb) + i; },
                     [&](int u, int gg, int il) {
                         return (1 << lr) * ((1 << lb) - (1 << (lb - u))) + (gg << (lb - 1 - u)) + il;
                     });
@@ -872,7 +965,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT2)
         S.colt[e] = rc[((row & (R - 1)) << lb) + col];
     }
     cl.sync();
-    tile_inv<true>(S.colt, S.ctw, S.ctwp, a, q, q2, [&](int gg, int i) { return (i << lc) + gg; },
+    tile_inv<true, NT2, false>(S.colt, S.ctw, S.ctwp, a, q, q2, [&](int gg, int i) { return (i << lc) + gg; },
                    [&](int u, int, int il) { return (1 << (a - 1 - u)) + il; });
     const Shoup sc = b.scale ? b.scale[r - b.r0] : Shoup{P.ninv, P.ninv_sh};
     for (int e = threadIdx.x; e < TILE; e += NT2)
@@ -954,7 +1047,7 @@ copse_status launch(copse_ctx *ctx, const NttBatch &b, cudaStream_t s, bool inve
         } else {
             TIMED_OPS("ntt_fwd", bytes, bfly, s, {
                 k_ntt_fwd_cols<<<grid, NT2, 0, s>>>(b, ctx->d_prime, ctx->d_psi, ctx->d_psi_sh, logN, ctx->L, a);
-                k_ntt_fwd_rows<<<grid, NT2, 0, s>>>(b, ctx->d_prime, (const ulonglong2 *)ctx->d_stw_f, logN, ctx->L, a);
+                k_ntt_fwd_rows<<<grid, NTT, 0, s>>>(b, ctx->d_prime, (const ulonglong2 *)ctx->d_stw_f, logN, ctx->L, a);
             });
         }
         LAUNCH_CHECK();
@@ -1007,14 +1100,14 @@ __global__ void __launch_bounds__(NT2) k_ntt_fwd_cols_io(NttBatch b, const Prime
         stwp[e] = Wp[e];
     }
     __syncthreads();
-    tile_fwd<true>(sm, stw, stwp, a, q, q2, [&](int gg, int i) { return (i << lc) + gg; },
+    tile_fwd<true, NT2, false>(sm, stw, stwp, a, q, q2, [&](int gg, int i) { return (i << lc) + gg; },
                    [&](int u, int, int il) { return (1 << u) + il; });
     u64 *out = scratch + ((size_t)pr << logN) + (tile << lc);
     for (int e = threadIdx.x; e < TILE; e += NT2) out[((size_t)(e >> lc) << lb) + (e & (C - 1))] = sm[e];
 }
 
 template <class IO>
-__global__ void __launch_bounds__(NT2) k_ntt_fwd_rows_io(NttBatch b, const PrimeDev *__restrict__ primes,
+__global__ void __launch_bounds__(NTT, 4) k_ntt_fwd_rows_io(NttBatch b, const PrimeDev *__restrict__ primes,
                                                          const ulonglong2 *__restrict__ stg, int logN, int L, int a,
                                                          IO io, const u64 *scratch) {
     __shared__ u64 sm[TILE], stw[TILE], stwp[TILE];
@@ -1028,7 +1121,7 @@ __global__ void __launch_bounds__(NT2) k_ntt_fwd_rows_io(NttBatch b, const Prime
     const u64 *in = scratch + ((size_t)pr << logN) + ((size_t)row0 << lb);
     const ulonglong2 *st = stg + ((size_t)g * (N / TILE) + tile) * TILE;
     const int nst = TILE - (1 << lr);
-    for (int e = threadIdx.x; e < TILE; e += NT2) {
+    for (int e = threadIdx.x; e < TILE; e += NTT) {
         sm[e] = in[e];
         if (e < nst) {
             const ulonglong2 v = st[e];
@@ -1037,13 +1130,13 @@ __global__ void __launch_bounds__(NT2) k_ntt_fwd_rows_io(NttBatch b, const Prime
         }
     }
     __syncthreads();
-    tile_fwd<false>(sm, stw, stwp, lb, q, q2, [&](int gg, int i) { return (gg << lb) + i; },
+    tile_fwd<false, NTT, true>(sm, stw, stwp, lb, q, q2, [&](int gg, int i) { return (gg << lb) + i; },
                     [&](int u, int gg, int il) { return ((1 << lr) * ((1 << u) - 1)) + (gg << u) + il; });
     const u64 one_sh = primes[g].one_sh;
-    u64 v[TILE / NT2];
+    u64 v[TILE / NTT];
 #pragma unroll
-    for (int i = 0; i < TILE / NT2; i++) v[i] = fwd_reduce(sm[threadIdx.x + i * NT2], q, one_sh);
-    store_n(io, p, r, g, ((size_t)row0 << lb) + threadIdx.x, NT2, v);
+    for (int i = 0; i < TILE / NTT; i++) v[i] = fwd_reduce(sm[threadIdx.x + i * NTT], q, one_sh);
+    store_n(io, p, r, g, ((size_t)row0 << lb) + threadIdx.x, NTT, v);
 }
 
 template <class IO>
@@ -1069,7 +1162,7 @@ __global__ void __launch_bounds__(NT2) k_ntt_inv_rows_io(NttBatch b, const Prime
         }
     }
     __syncthreads();
-    tile_inv<false>(sm, stw, stwp, lb, q, q2, [&](int gg, int i) { return (gg << lb) + i; },
+    tile_inv<false, NT2, false>(sm, stw, stwp, lb, q, q2, [&](int gg, int i) { return (gg << lb) + i; },
                     [&](int u, int gg, int il) {
                         return (1 << lr) * ((1 << lb) - (1 << (lb - u))) + (gg << (lb - 1 - u)) + il;
                     });
@@ -1100,7 +1193,7 @@ __global__ void __launch_bounds__(NT2) k_ntt_inv_cols_io(NttBatch b, const Prime
         }
     }
     __syncthreads();
-    tile_inv<true>(sm, stw, stwp, a, q, q2, [&](int gg, int i) { return (i << lc) + gg; },
+    tile_inv<true, NT2, false>(sm, stw, stwp, a, q, q2, [&](int gg, int i) { return (i << lc) + gg; },
                    [&](int u, int, int il) { return (1 << (a - 1 - u)) + il; });
     const Shoup sc = b.scale ? b.scale[r - b.r0] : Shoup{P.ninv, P.ninv_sh};
     for (int e = threadIdx.x; e < TILE; e += NT2)
@@ -1163,7 +1256,7 @@ copse_status launch_tiled_io(copse_ctx *ctx, const NttBatch &b, const IO &io, cu
         TIMED_OPS(io_family<IO>(false), bytes, butterflies(ctx, b), s, {
             k_ntt_fwd_cols_io<IO><<<grid, NT2, 0, s>>>(b, ctx->d_prime, ctx->d_psi, ctx->d_psi_sh, logN, ctx->L, a,
                                                        io, scratch);
-            k_ntt_fwd_rows_io<IO><<<grid, NT2, 0, s>>>(b, ctx->d_prime, (const ulonglong2 *)ctx->d_stw_f, logN, ctx->L,
+            k_ntt_fwd_rows_io<IO><<<grid, NTT, 0, s>>>(b, ctx->d_prime, (const ulonglong2 *)ctx->d_stw_f, logN, ctx->L,
                                                        a, io, scratch);
         });
     const cudaError_t e = cudaGetLastError();
