@@ -24,7 +24,7 @@
 //
 // One CTA per SM, persistent over work items (element, tile of 16 accumulators, run of up
 // to 256 baby steps), its warps specialised and handing work on through mbarriers:
-//   warp 0       allocates the tensor memory; one thread issues the MMAs
+//   warp 0       allocates the tensor memory; runs the MMA loop, one elected lane issuing
 //   warp 1       one thread streams the rotations' raw words, one chunk (8 query
 //                ciphertexts x 16 baby steps x 2 components, contiguous) per bulk copy
 //                (cp.async.bulk with transaction-count completion) into a ring of stages
@@ -100,6 +100,12 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t k_stride, 
            ((uint64_t)((mn_stride & 0x3FFFF) >> 4) << 32) | (1ull << 46);
 }
 
+// one lane of the (converged) warp: the lowest active one
+__device__ __forceinline__ bool elect_one() {
+    uint32_t pred;
+    asm volatile("{\n.reg .pred p;\nelect.sync _|p, 0xffffffff;\nselp.u32 %0, 1, 0, p;\n}\n" : "=r"(pred));
+    return pred != 0;
+}
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
@@ -376,7 +382,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_enc_mac_tc(const TcArgs P) {
 
     if (warp == 0) {
         // ---------------------------------------------------------------- MMA issue
-        if (lane == 0) {
+        // The whole warp runs the loop (its descriptors and counters are warp-uniform) and waits;
+        // one elected lane, always the same one, issues the MMAs and the commits that track them.
+        {
             uint32_t nb_c = 0, np_c = 0, na = 0;  // operand stages, passes, runs consumed
             bool ok = true, issued = false;
             for (size_t it = blockIdx.x; it < n_items && ok; it += gridDim.x)
@@ -386,32 +394,37 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_enc_mac_tc(const TcArgs P) {
                     // descriptors of the first 16 baby steps; 16 baby steps further is 256 bytes, 16 in
                     // the descriptor's address field
                     const uint64_t dA = smem_desc(sh_addr(A0), 128, a_mn), dB = smem_desc(sh_addr(Bst), 128, B_ROW);
-                    if (!(ok = bar_wait(&bar[BAR_A_FULL], na & 1, fail, P.status))) break;
+                    if (!(ok = warp_wait(&bar[BAR_A_FULL], na & 1, fail, P.status))) break;
                     for (int p = 0; p < nqp && ok; p++, np_c++) {
                         const uint32_t buf = np_c & 1;
                         if (np_c >= 2 &&
-                            !(ok = bar_wait(&bar[BAR_T_EMPTY + buf], ((np_c >> 1) - 1) & 1, fail, P.status)))
+                            !(ok = warp_wait(&bar[BAR_T_EMPTY + buf], ((np_c >> 1) - 1) & 1, fail, P.status)))
                             break;
                         tc_fence_after();
                         const uint32_t d = tmem + buf * 256;
                         for (int kc = 0; kc < R.ncr; kc++, nb_c++) {
                             const int st = (int)(nb_c % TC_NB);
-                            if (!(ok = bar_wait(&bar[BAR_B_FULL + st], (nb_c / TC_NB) & 1, fail, P.status))) break;
+                            if (!(ok = warp_wait(&bar[BAR_B_FULL + st], (nb_c / TC_NB) & 1, fail, P.status))) break;
                             tc_fence_after();
                             // rotations' digits (M: row 8 (2 q + c) + b) x diagonals' digits of both
                             // components (N: column 128 c' + 8 x + a; the second component's core
                             // matrices follow the first's at the same stride), 16 baby steps per MMA
                             const int ns = min(TC_CJ / TC_KS, R.nk - kc * (TC_CJ / TC_KS));
                             const uint64_t b0 = dB + (uint64_t)(st * (B_STAGE >> 4)), a0 = dA + (uint64_t)(kc * (TC_CJ / TC_KS) * 16);
-                            for (int s2 = 0; s2 < ns; s2++) tc_mma(d, b0 + (uint64_t)(16 * s2), a0 + (uint64_t)(16 * s2), (kc | s2) != 0);
-                            tc_commit(&bar[BAR_B_EMPTY + st]);
+                            if (elect_one()) {
+                                for (int s2 = 0; s2 < ns; s2++) tc_mma(d, b0 + (uint64_t)(16 * s2), a0 + (uint64_t)(16 * s2), (kc | s2) != 0);
+                                tc_commit(&bar[BAR_B_EMPTY + st]);
+                            }
+                            __syncwarp();
                             issued = true;
                         }
-                        if (ok) tc_commit(&bar[BAR_T_FULL + buf]);
+                        if (ok && elect_one()) tc_commit(&bar[BAR_T_FULL + buf]);
+                        __syncwarp();
                     }
-                    if (ok) tc_commit(&bar[BAR_A_EMPTY]);
+                    if (ok && elect_one()) tc_commit(&bar[BAR_A_EMPTY]);
+                    __syncwarp();
                 }
-            if (issued && *fail) {  // wait (bounded) for the MMAs in flight before the memory goes
+            if (issued && *fail && elect_one()) {  // the issuing lane waits (bounded) for its MMAs in flight before the memory goes
                 tc_commit(&bar[BAR_DRAIN]);
                 const unsigned long long t0 = global_ns();
                 while (!bar_test(&bar[BAR_DRAIN], 0) && global_ns() - t0 < TC_WAIT_NS) {
