@@ -63,7 +63,24 @@ def parse_forest(text: str):
         if pos != len(toks):
             raise ValueError("trailing tokens in tree line")
         trees.append(t)
+    # a leaf names its class by its index in the label line (Section 5, Input Representation)
+    if any(not 0 <= c < len(labels) for c in _leaf_labels(trees)):
+        raise ValueError("class index out of range")
     return labels, trees
+
+
+def _leaf_labels(trees):
+    out = []
+
+    def walk(n):
+        if n.leaf:
+            out.append(n.label)
+        else:
+            walk(n.left)
+            walk(n.right)
+    for t in trees:
+        walk(t)
+    return out
 
 
 def classify_plain(trees, x):
