@@ -146,3 +146,14 @@ def test_shuffle_plan_validation_and_codebook():
         assert K.copse_model_info_get(h)["n_out"] == om.L
     finally:
         K.copse_model_destroy(h)
+
+
+def test_no_device_fails_loudly():
+    """Without a usable CUDA device the library refuses to make a context (ECUDA): there is
+    no host fallback for any step of the path."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    with pytest.raises(K.CopseError) as e:
+        K.copse_ctx_create(10, 50, 8)
+    assert e.value.name == "ECUDA"
