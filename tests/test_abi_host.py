@@ -157,3 +157,39 @@ def test_no_device_fails_loudly():
     with pytest.raises(K.CopseError) as e:
         K.copse_ctx_create(10, 50, 8)
     assert e.value.name == "ECUDA"
+
+
+_NULL_CALLS = r'''
+import ctypes as C, sys
+sys.path.insert(0, sys.argv[1])
+import paper_2104_09583_gb300.copse as K
+lib = K.library()
+SCALARS = (C.c_int, C.c_uint32, C.c_int32, C.c_uint64, C.c_int64, C.c_size_t, C.c_double, C.c_float)
+for name in K.declared_functions():
+    f = getattr(lib, name)
+    types = list(f.argtypes or [])
+    f.argtypes = [t if t in SCALARS else C.c_void_p for t in types]
+    r = f(*[0 if t in SCALARS else None for t in types])
+    print(name, r if isinstance(r, int) or r is None else "value", flush=True)
+'''
+
+
+def test_every_entry_point_refuses_null_arguments():
+    """Every function include/copse.h declares, called with null handles and pointers and zero
+    sizes, returns (an error status where it returns one) without touching memory: the
+    process survives all of them.  Destroy functions take NULL as a no-op."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", _NULL_CALLS, root], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stdout[-2000:] + r.stderr[-2000:]
+    got = dict(ln.rsplit(" ", 1) for ln in r.stdout.splitlines())
+    assert sorted(got) == sorted(K.declared_functions())
+    # not statuses: a count, flags, the error text, the switch for the kernel timers
+    not_status = {"copse_ctbuf_count", "copse_model_is_encrypted", "copse_model_is_fused", "copse_last_error",
+                  "copse_stats_enable"}
+    for name, ret in got.items():
+        if name in not_status or name.endswith("_destroy"):
+            continue
+        assert int(ret) < 0, f"{name} returned {ret} for null arguments"
