@@ -820,7 +820,7 @@ class OracleBench:
         self.n = {"enc": c * p, "mul_hi": c * (p + 2 * p - 3), "tensor_D": c * m.q, "tensor_B": c * d * m.b,
                   "relin": c * (acc_r + acc_l), "rot_D": c * (babies_r + giants_r),
                   "rot_B": c * (babies_l + d * giants_l), "mul_lo": c * (d - 1)}
-        self._t = {}
+        self._t = {}            # operation kind -> its timings (seconds); the estimate takes the median
 
     def _clock(self, f, *a):
         s = time.perf_counter()
@@ -854,13 +854,13 @@ class OracleBench:
         return self._clock(bgv.rotate, self._xB, self.galois, k.gk[self.galois])
 
     def estimate(self):
-        return sum(self.n[kd] * self._t[kd] for kd in self.n)
+        return sum(self.n[kd] * statistics.median(self._t[kd]) for kd in self.n)
 
     def sample_all(self):
         """Time every operation kind once -> (seconds per step, description)."""
         t0 = time.perf_counter()
         for kd in self.n:
-            self._t[kd] = self._op(kd)
+            self._t.setdefault(kd, []).append(self._op(kd))
         return self.estimate(), self.describe(time.perf_counter() - t0)
 
     def sample_one(self, i):
@@ -869,23 +869,34 @@ class OracleBench:
             return self.sample_all()
         kinds = list(self.n)
         t0 = time.perf_counter()
-        self._t[kinds[i % len(kinds)]] = self._op(kinds[i % len(kinds)])
+        self._t[kinds[i % len(kinds)]].append(self._op(kinds[i % len(kinds)]))
         return self.estimate(), self.describe(time.perf_counter() - t0)
 
     def describe(self, cpu_s):
         n = self.n
-        return (f"oracle ({self.B.oracle_threads()} threads) timed on one of each operation of the step at its "
-                f"level ({cpu_s:.1f} s of CPU work: encrypt, ciphertext product at the top and bottom of the chain, "
-                f"tensor with an encrypted diagonal at the reshuffle and level levels, relinearisation, rotation at "
-                f"both levels); one step of {self.W.queries[0]} queries ({self.n_ct} query ciphertexts) extrapolated "
-                f"with its exact counts: {n['enc']} encryptions, {n['mul_hi'] + n['mul_lo']} products, "
+        runs = sum(len(v) for v in self._t.values())
+        return (f"oracle ({self.B.oracle_threads()} threads) timed on the step's operations at their levels "
+                f"({runs} timings over the {len(self.n)} kinds, median per kind; {cpu_s:.1f} s of CPU work in this "
+                f"sample: encrypt, ciphertext product at the top and bottom of the chain, tensor with an encrypted "
+                f"diagonal at the reshuffle and level levels, relinearisation, rotation at both levels); one step of "
+                f"{self.W.queries[0]} queries ({self.n_ct} query ciphertexts) extrapolated with its exact counts: "
+                f"{n['enc']} encryptions, {n['mul_hi'] + n['mul_lo']} products, "
                 f"{n['tensor_D'] + n['tensor_B']} tensors, {n['relin']} relinearisations, "
                 f"{n['rot_D'] + n['rot_B']} rotations")
 
 
 def oracle_baseline_encmodel(W, budget_s):
+    """Every operation kind timed once, then again round robin until about budget_s seconds of
+    oracle work are spent (at least one timing per kind); the step estimate takes each kind's
+    median."""
     ob = OracleBench(W, W.forest_texts()[0])
-    est, sample = ob.sample_all()
+    t0 = time.perf_counter()
+    est, _ = ob.sample_all()
+    i = 0
+    while time.perf_counter() - t0 + statistics.median(ob._t[list(ob.n)[i % len(ob.n)]]) <= budget_s:
+        est, _ = ob.sample_one(i)
+        i += 1
+    sample = ob.describe(time.perf_counter() - t0)
     return {"value": W.queries[0] / est, "unit": UNIT, "cores": ob.B.oracle_threads(), "kind": "oracle",
             "sample": sample, "seconds_per_step_extrapolated": est}
 
