@@ -173,17 +173,25 @@ extern "C" copse_status copse_server_create(copse_ctx *c, const copse_keys *keys
             }
         return st;
     };
-    CUDA_TRY(cudaSetDevice(c->device));
+    // a failed runtime call releases what the earlier rounds made
+    auto cuda_fail = [&](cudaError_t e, const char *what) {
+        set_error(std::string(what) + ": " + cudaGetErrorString(e));
+        cudaGetLastError();
+        return cleanup(COPSE_ECUDA);
+    };
+    cudaError_t ce = cudaSetDevice(c->device);
+    if (ce != cudaSuccess) return cuda_fail(ce, "cudaSetDevice");
     // first every model's one launch, then a second per model while device memory allows
     for (int round = 0; round < 2; round++)
         for (ModelSlot &ms : S->models) {
             size_t free0 = 0, total = 0;
-            CUDA_TRY(cudaMemGetInfo(&free0, &total));
+            if ((ce = cudaMemGetInfo(&free0, &total)) != cudaSuccess) return cuda_fail(ce, "cudaMemGetInfo");
             if (round == 1 && free0 < S->launch_max + S->launch_max / 8 + S->launch_max) continue;
             Buffer &b = ms.buf[round];
             // the graph's own peak allocation: reset the device's graph-memory high-water mark
             uint64_t zero = 0;
-            CUDA_TRY(cudaDeviceSetGraphMemAttribute(c->device, cudaGraphMemAttrUsedMemHigh, &zero));
+            if ((ce = cudaDeviceSetGraphMemAttribute(c->device, cudaGraphMemAttrUsedMemHigh, &zero)) != cudaSuccess)
+                return cuda_fail(ce, "cudaDeviceSetGraphMemAttribute");
             copse_status st = copse_session_create(c, keys, evk, ms.m, ms.per_ct, &b.sess);
             if (st) {
                 if (st == COPSE_ENOMEM || st == COPSE_ECUDA) {
@@ -210,7 +218,8 @@ extern "C" copse_status copse_server_create(copse_ctx *c, const copse_keys *keys
                 return cleanup(st ? st : COPSE_ECUDA);
             }
             uint64_t high = 0;
-            CUDA_TRY(cudaDeviceGetGraphMemAttribute(c->device, cudaGraphMemAttrUsedMemHigh, &high));
+            if ((ce = cudaDeviceGetGraphMemAttribute(c->device, cudaGraphMemAttrUsedMemHigh, &high)) != cudaSuccess)
+                return cuda_fail(ce, "cudaDeviceGetGraphMemAttribute");
             const size_t used = (size_t)high;
             S->reserved += used;
             S->launch_max = std::max(S->launch_max, used);
@@ -263,18 +272,23 @@ extern "C" copse_status copse_server_poll(copse_server *S, uint64_t ticket, uint
                                           double *latency_ms) {
     if (!S || !out_bits) { set_error("bad argument"); return COPSE_EINVAL; }
     std::unique_lock<std::mutex> lk(S->mu);
-    auto it = S->tickets.find(ticket);
-    if (it == S->tickets.end()) { set_error("unknown ticket"); return COPSE_EINVAL; }
-    auto done = [&] { return S->worker_error != COPSE_OK || S->tickets[ticket].state == 2; };
+    if (S->tickets.find(ticket) == S->tickets.end()) { set_error("unknown ticket"); return COPSE_EINVAL; }
+    // looked up afresh on every wake: another thread polling the same ticket may have collected it
+    auto done = [&] {
+        auto f = S->tickets.find(ticket);
+        return S->worker_error != COPSE_OK || f == S->tickets.end() || f->second.state == 2;
+    };
     if (!S->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms < 0 ? 0 : timeout_ms), done)) {
         set_error("result not ready");
         return COPSE_ETIMEOUT;
     }
     if (S->worker_error) { set_error("server stopped: " + S->worker_msg); return S->worker_error; }
-    Ticket &tk = S->tickets[ticket];
+    auto it = S->tickets.find(ticket);
+    if (it == S->tickets.end()) { set_error("ticket already collected"); return COPSE_EINVAL; }
+    Ticket &tk = it->second;
     memcpy(out_bits, tk.bits.data(), tk.bits.size());
     if (latency_ms) latency_ms[0] = std::chrono::duration<double, std::milli>(tk.t_done - tk.t_submit).count();
-    S->tickets.erase(ticket);
+    S->tickets.erase(it);
     return COPSE_OK;
 }
 
