@@ -886,9 +886,9 @@ class OracleBench:
 
 
 def oracle_baseline_encmodel(W, budget_s):
-    """Every operation kind timed once, then again round robin until about budget_s seconds of
-    oracle work are spent (at least one timing per kind); the step estimate takes each kind's
-    median."""
+    """On all host cores: every operation kind timed once, then again round robin until about
+    budget_s seconds of oracle work are spent; the step estimate takes each kind's median.  Then
+    one timing of every kind on a single thread, for the same estimate at one core."""
     ob = OracleBench(W, W.forest_texts()[0])
     t0 = time.perf_counter()
     est, _ = ob.sample_all()
@@ -897,8 +897,21 @@ def oracle_baseline_encmodel(W, budget_s):
         est, _ = ob.sample_one(i)
         i += 1
     sample = ob.describe(time.perf_counter() - t0)
-    return {"value": W.queries[0] / est, "unit": UNIT, "cores": ob.B.oracle_threads(), "kind": "oracle",
-            "sample": sample, "seconds_per_step_extrapolated": est}
+    cores = ob.B.oracle_threads()
+    line = {"value": W.queries[0] / est, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+            "seconds_per_step_extrapolated": est}
+    ob._t = {}
+    ob.B.set_oracle_threads(1)
+    try:
+        t1 = time.perf_counter()
+        est1, _ = ob.sample_all()
+        line["one_core"] = {"value": W.queries[0] / est1, "unit": UNIT, "cores": 1,
+                            "seconds_per_step_extrapolated": est1,
+                            "sample": f"one timing of each of the {len(ob.n)} operation kinds on one thread "
+                                      f"({time.perf_counter() - t1:.1f} s), extrapolated as above"}
+    finally:
+        ob.B.set_oracle_threads(cores)
+    return line
 
 
 def run_reference(args, ws, rank):

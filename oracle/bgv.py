@@ -59,6 +59,7 @@ def lib():
         sig = {
             "or_is_prime": (C.c_int, [C.c_uint64]),
             "or_threads": (C.c_int, []),
+            "or_set_threads": (C.c_int, [C.c_int]),
             "or_find_primes": (C.c_int, [C.c_int, C.c_uint64, C.c_int, C.c_int, u64p]),
             "or_root_2n": (C.c_uint64, [C.c_uint64, C.c_int]),
             "or_mulmod": (C.c_uint64, [C.c_uint64, C.c_uint64, C.c_uint64]),
@@ -106,6 +107,12 @@ def lib():
 def oracle_threads() -> int:
     """Threads the oracle's C loops use (OpenMP; OMP_NUM_THREADS, default all host cores)."""
     return int(lib().or_threads())
+
+
+def set_oracle_threads(n: int) -> int:
+    """Run the oracle's C loops on n threads from now on (results do not depend on it);
+    returns the count in force."""
+    return int(lib().or_set_threads(int(n)))
 
 
 # ---------------------------------------------------------------------------

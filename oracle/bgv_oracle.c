@@ -92,6 +92,19 @@ int or_threads(void)
 #endif
 }
 
+/* Set that thread count for the calling thread's later calls (n > 0; the benchmark
+ * times the oracle on one thread and on all host cores); returns the count in force. */
+int or_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
+
 /* Deterministic Miller-Rabin for 64-bit inputs (first twelve prime bases). */
 int or_is_prime(u64 n)
 {
