@@ -285,6 +285,7 @@ def run_cuda(args, ws, rank, local):
     line["table6"] = None if args.no_table6 else run_table6(local)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = oracle_baseline_encmodel(synth_workload(args.workload), args.cpu_budget)
+        line["cpu_baseline"]["direct"] = oracle_direct("forest100-n16384")
     return line
 
 
@@ -912,6 +913,34 @@ def oracle_baseline_encmodel(W, budget_s):
     finally:
         ob.B.set_oracle_threads(cores)
     return line
+
+
+def oracle_direct(name, seed=1):
+    """The oracle's whole inference of one full query ciphertext of a plaintext-model workload,
+    timed directly (no extrapolation): encrypt the queries' bit-planes, Algorithm 1, decrypt the
+    leaf bits; keys are made before the timed region, as on the GPU."""
+    from oracle import bgv as B
+    from oracle import copse as Cp
+    from paper_2104_09583_gb300 import synth
+
+    W = synth.WORKLOADS[name]
+    text = W.forest_texts()[0]
+    m = Cp.compile_forest(text, W.precision(), W.n_features())
+    P = B.Params(logN=W.log_n, L=W.primes, bits=W.bits, dnum=W.dnum)
+    bgv = B.Bgv(P)
+    keys = bgv.keygen(7, Cp.galois_elements(m, W.log_n))
+    nq = P.N // m.block
+    qs = synth.random_queries(seed, nq, W.n_features(), W.precision())
+    t0 = time.perf_counter()
+    X = Cp.encrypt_queries(bgv, keys, m, qs, 9)
+    out = Cp.infer(Cp.BgvEngine(bgv, keys), m, X, P.N)
+    bits = Cp.decode_labels(m, bgv.decrypt_slots(keys.sk, out), nq)
+    dt = time.perf_counter() - t0
+    _, trees = Cp.parse_forest(text)
+    return {"workload": name, "value": nq / dt, "unit": UNIT, "cores": B.oracle_threads(), "queries": nq,
+            "seconds": dt, "labels_ok": all(bits[j] == Cp.classify_plain(trees, qs[j]) for j in range(nq)),
+            "sample": f"the oracle's whole inference of one query ciphertext ({nq} queries, N = {P.N}, "
+                      f"{W.primes} primes): encryption, Algorithm 1 and decryption timed directly"}
 
 
 def run_reference(args, ws, rank):
