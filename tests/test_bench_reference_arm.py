@@ -56,3 +56,12 @@ def test_reference_arm_two_ranks_prints_once():
     assert len(lines) == 1, r.stdout
     _check(lines[0])
     assert lines[0]["n_gpus"] == 2
+
+
+def test_direct_oracle_timing_small_workload():
+    """The directly timed oracle leg (whole inference of one query ciphertext) on the smallest
+    workload: every query's labels equal the plaintext walk."""
+    sys.path.insert(0, ROOT)
+    import bench
+    r = bench.oracle_direct("toy-n1024")
+    assert r["labels_ok"] and r["queries"] == 32 and r["value"] > 0 and r["cores"] >= 1
