@@ -345,7 +345,8 @@ copse_status copse_server_submit(copse_server *server, uint32_t model_id, const 
 /* Wait up to timeout_ms for a ticket: its leaf bits into out_bits[n_leaves]
  * (host) and, if latency_ms is not NULL, the time from submit to completion.
  * COPSE_ETIMEOUT if not ready (the ticket stays valid); a ticket is released
- * by the successful poll. */
+ * by the successful poll, so another poll of it (also one that was waiting in
+ * another thread) fails with COPSE_EINVAL. */
 copse_status copse_server_poll(copse_server *server, uint64_t ticket, uint8_t *out_bits, int timeout_ms,
                                double *latency_ms);
 /* Device memory of the server: bytes its launches reserved at creation, the
