@@ -65,3 +65,14 @@ def test_direct_oracle_timing_small_workload():
     import bench
     r = bench.oracle_direct("toy-n1024")
     assert r["labels_ok"] and r["queries"] == 32 and r["value"] > 0 and r["cores"] >= 1
+
+
+def test_step_roofline_sums_families_at_their_binding_roofs():
+    sys.path.insert(0, ROOT)
+    import bench
+    kernels = {"a": {"ms_per_step": 100.0, "hbm_frac": 0.2, "int_frac": 0.5},   # integer-bound: 50 ms at its roof
+               "b": {"ms_per_step": 40.0, "hbm_frac": 0.75},                  # HBM-bound: 30 ms
+               "c": {"ms_per_step": 10.0, "hbm_frac": 1.3}}                   # above its roof: counted at 10 ms
+    r = bench.step_roofline(kernels, 200.0)
+    assert abs(r["ms_at_roofs"] - 90.0) < 1e-9 and abs(r["frac"] - 0.45) < 1e-12
+    assert bench.step_roofline({}, 200.0) is None and bench.step_roofline(None, 200.0) is None
