@@ -3,14 +3,16 @@
 
 A step is one pass of the whole path over one batch of queries: encode and
 encrypt the feature bit-planes, SecComp, reshuffle product, level products
-with masks, product across levels, decrypt the leaf bits.  The default
-workload is the N = 2^14, 10-prime forest (4 random trees, 90..110 branches,
-8 features, 8-bit) with one query per step; the batched line packs the 32
-queries one ciphertext holds.  ``value`` is measured with the queries'
-feature words already in device memory; ``e2e`` goes through the C ABI with
-pinned host buffers (host-to-device copy of the features and device-to-host
-copy of the leaf bits inside every step).  ``--impl reference`` times the
-CPU oracle on the host instead.
+with masks, product across levels, decrypt the leaf bits.  The headline
+workload is the encrypted model (Section 8.3) of 32 complete depth-8 trees
+(8160 branches, 32 features, 16-bit) at N = 2^15 with 16 primes, 64 queries
+per step; further keys time the N = 2^14 plaintext-model forest (4 random
+trees, 90..110 branches; one query per step, and the 32 queries one
+ciphertext holds), batching, serving and the Table 6 forests.  ``value`` is
+measured with the queries' feature words already in device memory; ``e2e``
+goes through the C ABI with pinned host buffers (host-to-device copy of the
+features and device-to-host copy of the leaf bits inside every step).
+``cpu_baseline`` and ``--impl reference`` time the CPU oracle on the host.
 
 Under torchrun (N > 1) every rank runs an independent replica (the method
 has no exchange step); value = all ranks' inferences / the slowest rank's time.
