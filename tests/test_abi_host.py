@@ -193,3 +193,21 @@ def test_every_entry_point_refuses_null_arguments():
         if name in not_status or name.endswith("_destroy"):
             continue
         assert int(ret) < 0, f"{name} returned {ret} for null arguments"
+
+
+def test_fused_mode_key_sets_and_levels_match_oracle():
+    """Fused level products (F_k = S_k R on Decisions): the host's rotation sets under plain and
+    baby-step / giant-step plans and its prime count equal the oracle's."""
+    for s in range(6):
+        text = synth.random_forest(300 + s, 1 + s % 4, 2 + s % 5, 1 + s % 6, 6, 3, complete=(s % 3 == 0))
+        om = Cp.compile_forest(text, 6, 0)
+        h = K.copse_compile_forest(text, 6, 0, 12)
+        try:
+            K.copse_model_set_fused(h, 1)
+            assert K.copse_model_is_fused(h)
+            assert K.copse_model_info_get(h)["levels_used"] == Cp.levels_needed(om, fused=True)
+            for g in [(0, 0), (2, 3), (5, 4), (om.q, om.b)]:
+                K.copse_model_set_bsgs(h, *g)
+                assert tuple(K.copse_model_rotations(h)) == tuple(Cp.rotation_sets(om, g, fused=True)), (s, g)
+        finally:
+            K.copse_model_destroy(h)
